@@ -1,0 +1,207 @@
+/*
+ * ia.h — C ABI of the B300 (sm_103a) articulated radiance-field render path.
+ *
+ * The library computes InstantAvatar's per-sample render path (arXiv
+ * 2212.10550): a canonical radiance field f: x -> (sigma, c) held in a
+ * multiresolution hash grid decoded by a small MLP (Sec. 3.1, Eq. 1-2), a
+ * skinning-weight voxel grid with linear blend skinning x' = sum_i w_i(x) B_i x
+ * (Sec. 3.1, Eq. 3-5), the canonical correspondence x* of a posed point found by
+ * bone-wise Broyden root finding (Sec. 3.1, Fast-SNARF), volume rendering
+ * C = sum_i alpha_i prod_{j<i}(1 - alpha_j) c_i with alpha_i = 1 - exp(-sigma_i
+ * delta_i) (Sec. 3.2, Eq. 6; the sign of the exponent is printed without its
+ * minus in the paper), and a per-pose occupancy grid that skips empty space in a
+ * normalised space with the root's rigid motion removed (Sec. 3.3).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an ia_status and never aborts; on failure
+ *    ia_last_error(ctx) holds a message.  Arguments are checked on the host
+ *    before any launch; invalid ones return IA_ERR_ARG and launch nothing.
+ *  - Pointers marked "host or device" may point to either (the library copies
+ *    through unified addressing).  Pointers marked "device" must be device
+ *    memory of the context's GPU.  Output pointers of ia_render may be host
+ *    memory: the call then renders into library scratch, copies back and
+ *    synchronises the stream before returning.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Device work is enqueued on it; calls returning device results do not
+ *    synchronise unless stated.
+ *  - The caller keeps ownership of everything it passes; the library copies what
+ *    it keeps.  Parameters (hash table, MLP) and per-pose state are owned by the
+ *    context and freed by ia_destroy.
+ *  - Device loops are bounded by construction (starts <= n_bones, Broyden
+ *    iterations <= broyden_max_iter, slots <= max_samples); non-convergence of a
+ *    start is a normal outcome, counted in ia_render_stats, not an error.
+ *  - Layouts are row-major.  A 3x4 transform [R | t] is 12 floats, row by row.
+ */
+#ifndef IA_H
+#define IA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IA_MAX_BONES 32
+#define IA_MAX_LEVELS 16
+
+typedef struct ia_ctx ia_ctx;
+
+typedef enum ia_status {
+  IA_OK = 0,
+  IA_ERR_ARG = 1,   /* invalid argument (checked on the host) */
+  IA_ERR_STATE = 2, /* call out of order (e.g. render before set_pose) */
+  IA_ERR_CUDA = 3,  /* a CUDA runtime error; message in ia_last_error */
+  IA_ERR_OOM = 4,   /* device allocation failed */
+  IA_ERR_LIMIT = 5  /* a documented size limit was exceeded */
+} ia_status;
+
+typedef enum ia_precision { IA_FP32 = 0, IA_FP16 = 1, IA_BF16 = 2 } ia_precision;
+
+typedef enum ia_occ_mode {
+  IA_OCC_POSE = 0,  /* rebuild the render grid for one pose (Sec. 3.3, inference) */
+  IA_OCC_UNION = 1  /* OR one pose's grid into the training grid (union over frames) */
+} ia_occ_mode;
+
+/* Sizes of the path.  level_res[l] = floor(N_min * b^l) is computed by the
+ * caller once (the paper defers the schedule to Instant-NGP) so that every
+ * consumer agrees on the integers. */
+typedef struct ia_config {
+  int n_levels;                  /* L, 1..16 */
+  int n_features;                /* F per level; must be 2 */
+  int log2_table;                /* T = 2^log2_table entries per hashed level, 10..24 */
+  int level_res[IA_MAX_LEVELS];  /* grid resolution N_l per level, >= 2 */
+  int mlp_width;                 /* hidden width; must be 64 (two hidden layers, ReLU) */
+  int max_samples;               /* ray slots N, 1..1024 */
+  int broyden_max_iter;          /* Broyden updates per start, 1..64 */
+  float broyden_tol;             /* converged when |LBS(x) - x'|_2 < tol */
+  int occ_res;                   /* occupancy cells per axis R, multiple of 4, 4..256 */
+  float occ_tau;                 /* occupied when density > tau */
+  int occ_dilate;                /* dilation radius in cells (Chebyshev), 0..4 */
+  float early_stop_T;            /* stop a ray once transmittance < this; <= 0 disables */
+  int precision;                 /* ia_precision of the MLP and hash features */
+} ia_config;
+
+typedef struct ia_camera {
+  float fx, fy, cx, cy;          /* pinhole intrinsics (pixels) */
+  int width, height;             /* image size; pixel (u, v) has ray id v * width + u */
+  float c2w[12];                 /* camera-to-world [R | centre], OpenCV axes */
+} ia_camera;
+
+/* Counters of one ia_render / ia_update_occupancy call (summed over the grid). */
+typedef struct ia_render_stats {
+  int64_t rays;              /* rays launched */
+  int64_t hit_rays;          /* rays whose clipped interval is non-empty */
+  int64_t marched_slots;     /* slots tested against the occupancy grid */
+  int64_t occupied_samples;  /* slots in occupied cells that were evaluated */
+  int64_t starts;            /* Broyden starts run */
+  int64_t broyden_iters;     /* Broyden updates run (summed over starts) */
+  int64_t converged;         /* starts that converged inside the canonical box */
+  int64_t roots;             /* distinct roots kept (one field evaluation each) */
+  int64_t early_stopped;     /* rays stopped by the transmittance threshold */
+} ia_render_stats;
+
+/* Create a context on the current CUDA device.  cfg is copied. */
+ia_status ia_create(const ia_config *cfg, ia_ctx **out);
+/* Free everything the context owns (NULL is allowed).  Waits for its work. */
+void ia_destroy(ia_ctx *ctx);
+/* Message of the last failed call on this context (or of the last failed
+ * ia_create when ctx is NULL).  Library-owned, valid until the next call. */
+const char *ia_last_error(const ia_ctx *ctx);
+/* Library version string. */
+const char *ia_version(void);
+
+/* Skeleton and skinning-weight grid (Sec. 3.1, Eq. 3-5).
+ *  parent      [n_bones] int32, host; -1 for bone 0 (the root), parent[k] < k.
+ *  rest_joints [n_bones][3] fp64, host; canonical rest-pose joint positions.
+ *  skin_grid   [skin_res]^3 x [n_bones] fp32, host or device, index
+ *              ((z * skin_res + y) * skin_res + x) * n_bones + i; vertex (x,y,z)
+ *              sits at canon_min + (x,y,z) / (skin_res - 1) * (canon_max - canon_min).
+ *  canon_min/max  canonical box: skinning grid corners, hash-grid unit cube, and
+ *              the region where a root counts as valid.
+ *  norm_min/max   normalised-space box: the occupancy grid's extent; rays are
+ *              clipped to it.
+ * n_bones 1..32, skin_res 2..256.  Invalidates per-pose state. */
+ia_status ia_set_skeleton(ia_ctx *ctx, int n_bones, const int32_t *parent,
+                          const double *rest_joints, const float *skin_grid, int skin_res,
+                          const float canon_min[3], const float canon_max[3],
+                          const float norm_min[3], const float norm_max[3]);
+
+/* Number of fp32 values of the hash table ([entries][F], levels concatenated;
+ * level l holds min((N_l+1)^3, T) entries, dense vertex (i,j,k) at
+ * i + (N_l+1)(j + (N_l+1) k), hashed vertex at (i ^ 2654435761 j ^ 805459861 k)
+ * mod T) and of the packed MLP (W1 [64][L*F], b1 [64], W2 [64][64], b2 [64],
+ * W3 [4][64], b3 [4], each row-major [out][in]). */
+ia_status ia_param_sizes(const ia_ctx *ctx, int64_t *table_floats, int64_t *mlp_floats);
+/* Load / read the canonical field's parameters (Eq. 1-2); host or device. */
+ia_status ia_set_params(ia_ctx *ctx, const float *table, const float *mlp, void *stream);
+ia_status ia_get_params(ia_ctx *ctx, float *table, float *mlp, void *stream);
+
+/* Bone transforms for n_poses poses (Sec. 3.1 B, Sec. 3.3 normalised space),
+ * composed down the kinematic tree in fp64 on the GPU:
+ *   R_k = Rodrigues(axis_angle[p][k]);  G_0 = [R_0 | j_0];
+ *   G_k = G_parent(k) [R_k | j_k - j_parent(k)];  B_k = G_k [I | -j_k] + t_root;
+ *   N_k = B_0^-1 B_k  (normalised space), stored fp32 with N_k^-1 and B_0^-1.
+ * Also builds, per pose, the blended transform grid M(v) = sum_i W(v, i) N_i
+ * (fp32, 12 floats per skinning-grid vertex), exact under trilinear
+ * interpolation because LBS is linear in the weights.
+ *  axis_angle [n_poses][n_bones][3] fp64, root_trans [n_poses][3] fp64, host.
+ * n_poses 1..4096.  Replaces previously set poses. */
+ia_status ia_set_pose(ia_ctx *ctx, int n_poses, const double *axis_angle,
+                      const double *root_trans, void *stream);
+/* Read back pose p's transforms: N and Ninv [n_bones][12], B0inv [12] (any may
+ * be NULL); host or device.  Synchronises the stream. */
+ia_status ia_get_transforms(ia_ctx *ctx, int pose, float *N, float *Ninv, float *B0inv,
+                            void *stream);
+
+/* Occupancy grid of pose p (Sec. 3.3): density of the posed field at every cell
+ * centre norm_min + (c + 1/2) * (norm_max - norm_min) / R (fp32, fixed order),
+ * then occupied = density > occ_tau, dilated by occ_dilate cells, packed so that
+ * cell b = x + R (y + R z) is bit b % 32 of word b / 32.  IA_OCC_POSE replaces
+ * the render grid; IA_OCC_UNION ORs the result into the training grid.
+ *  sigma_out [R^3] fp32 device or NULL; bits_out [R^3 / 32] uint32 device or NULL. */
+ia_status ia_update_occupancy(ia_ctx *ctx, int pose, int mode, float *sigma_out,
+                              uint32_t *bits_out, ia_render_stats *stats, void *stream);
+/* Threshold + dilation + packing alone, from a caller density array.
+ *  sigma [R^3] fp32 device; bits_out [R^3 / 32] uint32 device.  Also installs
+ *  the result as the render grid. */
+ia_status ia_occupancy_from_density(ia_ctx *ctx, const float *sigma, uint32_t *bits_out,
+                                    void *stream);
+/* Install caller bits as the render grid ([R^3 / 32] uint32, host or device). */
+ia_status ia_set_occupancy(ia_ctx *ctx, const uint32_t *bits, void *stream);
+
+/* Posed field f'(x') = f(x*) at n normalised-space points of pose p (Sec. 3.1):
+ * bone-wise Broyden starts x0 = N_k^-1 x', validity = converged and inside the
+ * canonical box, one Newton polish of each distinct root, the root with the
+ * highest density selected.  x [n][3] fp32 device; sigma [n], rgb [n][3],
+ * x_canon [n][3], start [n] int32 (bone of the selected root, -1 if none) device,
+ * any output may be NULL. */
+ia_status ia_query_posed(ia_ctx *ctx, int pose, int n, const float *x, float *sigma,
+                         float *rgb, float *x_canon, int32_t *start, void *stream);
+/* Canonical field f(x) (Eq. 1-2) at n canonical points; x [n][3], sigma [n],
+ * rgb [n][3] fp32 device. */
+ia_status ia_query_canonical(ia_ctx *ctx, int n, const float *x, float *sigma, float *rgb,
+                             void *stream);
+
+/* Render pose p through camera cam (Sec. 3.2-3.3): for pixel (u, v) the ray
+ * d = normalize(R_c [(u + 1/2 - cx)/fx, (v + 1/2 - cy)/fy, 1]) from the camera
+ * centre, mapped to normalised space, clipped to the normalised box [t_n, t_f],
+ * N midpoint slots t_i = t_n + (i + 1/2) delta, delta = (t_f - t_n) / N (all
+ * fp32, fixed order, no contraction); slots in empty cells are skipped; the
+ * others are composited front to back with alpha_i = 1 - exp(-sigma_i delta);
+ * a ray stops once its transmittance falls below early_stop_T.
+ *  rgb [H*W][3], alpha [H*W] fp32 (alpha = 1 - final transmittance), device or
+ *  host (see conventions).  stats may be NULL (host struct). */
+ia_status ia_render(ia_ctx *ctx, int pose, const ia_camera *cam, float *rgb, float *alpha,
+                    ia_render_stats *stats, void *stream);
+
+/* The sample set of ia_render without evaluating it (the indexing contract):
+ * bit i of slot_mask[(v * W + u) * ceil(N / 32) + i / 32] is set iff slot i of
+ * pixel (u, v) lies in an occupied cell of the render grid.  Without early
+ * termination these are exactly the samples ia_render evaluates.
+ *  slot_mask [H*W][ceil(N/32)] uint32 device. */
+ia_status ia_march_mask(ia_ctx *ctx, int pose, const ia_camera *cam, uint32_t *slot_mask, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IA_H */

@@ -29,7 +29,7 @@ _HDR = os.path.join(_HERE, "oracle.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
 MAX_BONES = 32
 
-FLAG_CONV, FLAG_BOX, FLAG_DUP, FLAG_TIE, FLAG_SING = 1, 2, 4, 8, 16
+FLAG_CONV, FLAG_BOX, FLAG_DUP, FLAG_TIE, FLAG_SING, FLAG_TERM = 1, 2, 4, 8, 16, 32
 
 
 def build(force: bool = False) -> str:
@@ -119,6 +119,8 @@ def _declare(L):
         "or_render": (None, [PM, PP, PC, PU32, PD, PD, PI32, PI32, PI64, C.c_int]),
         "or_render_pixels": (None, [PM, PP, PC, PU32, C.c_int, PI32, PD, PD, PI32, PI32, C.c_int]),
         "or_occupancy": (None, [PM, PP, PD, PU32, C.c_int]),
+        "or_march_mask": (None, [PM, PP, PC, PU32, PU32]),
+        "or_occupancy_cells": (None, [PM, PP, C.c_int, PI32, PD, C.c_int]),
         "or_occ_bits": (None, [C.c_int, C.c_int, C.c_double, PD, PU32]),
         "or_occ_bits_f32": (None, [C.c_int, C.c_int, C.c_float, PF, PU32]),
         "or_bruteforce_roots": (C.c_int, [PM, PP, PD, C.c_int, C.c_double, PD, C.c_int]),
@@ -344,6 +346,23 @@ class OracleModel:
                                 _p(pix, C.c_int32), _p(rgb, C.c_double), _p(alpha, C.c_double),
                                 _p(flags, C.c_int32), _p(nsamp, C.c_int32), nthreads)
         return dict(rgb=rgb, alpha=alpha, flags=flags, nsamp=nsamp)
+
+    def march_mask(self, p, cam, occ_bits):
+        W, H = int(cam["width"]), int(cam["height"])
+        words = (self.m.n_slots + 31) // 32
+        mask = np.zeros((H * W, words), dtype=np.uint32)
+        occ = np.ascontiguousarray(occ_bits, dtype=np.uint32)
+        c = self.camera(cam)
+        self.L.or_march_mask(C.byref(self.m), C.byref(p), C.byref(c), _p(occ, C.c_uint32),
+                             _p(mask, C.c_uint32))
+        return mask
+
+    def occupancy_cells(self, p, cells, nthreads=0):
+        cells = np.ascontiguousarray(cells, dtype=np.int32)
+        sigma = np.zeros(len(cells))
+        self.L.or_occupancy_cells(C.byref(self.m), C.byref(p), len(cells), _p(cells, C.c_int32),
+                                  _p(sigma, C.c_double), nthreads)
+        return sigma
 
     def occupancy(self, p, nthreads=0):
         R = self.scene.occ_res

@@ -200,12 +200,20 @@ void or_lbs(const or_model *m, const or_pose *p, const double x[3], double y[3],
 /* Correspondence search (Fast-SNARF style Broyden, Sec. 3.1)                 */
 /* ------------------------------------------------------------------------- */
 
+/* Broyden's method on g(x) = LBS(x) - x' from x0.  The initial inverse Jacobian
+   is that of LBS with the skinning weights held at their value at x0, i.e.
+   (sum_i w_i(x0) R_i)^-1; the good-Broyden rank-one updates then correct it. */
 int or_broyden(const or_model *m, const or_pose *p, const double xn[3], const double x0[3],
                double x[3], int *iters, double *res_norm, int *flags) {
-  double y[3], J[9], H[9], r[3], det;
+  double y[3], J[9], H[9], r[3], det, w[OR_MAX_BONES];
   int fl = 0;
   for (int a = 0; a < 3; ++a) x[a] = x0[a];
-  or_lbs(m, p, x, y, J);
+  or_lbs(m, p, x, y, NULL);
+  or_skin(m, x, w, NULL);
+  for (int i = 0; i < 9; ++i) J[i] = 0.0;
+  for (int i = 0; i < m->nb; ++i)
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) J[a * 3 + b] += w[i] * p->N[i][a * 4 + b];
   for (int a = 0; a < 3; ++a) r[a] = y[a] - xn[a];
   int ok = inv3(J, H, &det);
   if (fabs(det) > 0.5e-6 && fabs(det) < 2e-6) fl |= OR_FLAG_SING;
@@ -304,7 +312,7 @@ static int roots_impl(const or_model *m, const or_pose *p, const double xn[3], d
   for (int k = 0; k < m->nb; ++k) {
     if (!conv[k]) continue;
     double *x = xs[k];
-    if (box_margin(m, x) < 1e-5) fl |= OR_FLAG_BOX;
+    if (box_margin(m, x) < 1e-4) fl |= OR_FLAG_BOX;
     if (!in_box(m, x)) continue;
     nc++;
     int dup = 0;
@@ -543,6 +551,7 @@ static void render_ray(const or_model *m, const or_pose *p, const or_camera *c, 
         for (int k = 0; k < 3; ++k) C[k] += T * a * s.rgb[k];
         T *= 1.0 - a;
       }
+      if (m->early_T > 0.0 && fabs(T / m->early_T - 1.0) < 1e-3) fl |= OR_FLAG_TERM;
       if (m->early_T > 0.0 && T < m->early_T) break;
     }
   }
@@ -592,6 +601,24 @@ void or_render_pixels(const or_model *m, const or_pose *p, const or_camera *c,
   }
 }
 
+void or_march_mask(const or_model *m, const or_pose *p, const or_camera *c, const uint32_t *occ,
+                   uint32_t *mask) {
+  int W = c->width, H = c->height, words = (m->n_slots + 31) / 32;
+  for (int r = 0; r < W * H; ++r) {
+    uint32_t *mk = mask + (long)r * words;
+    for (int w = 0; w < words; ++w) mk[w] = 0u;
+    float o[3], d[3], tn, tf;
+    if (!or_ray(m, p, c, r % W, r / W, o, d, &tn, &tf)) continue;
+    float dt = (tf - tn) / (float)m->n_slots;
+    for (int i = 0; i < m->n_slots; ++i) {
+      float x[3];
+      slot_position(o, d, tn, dt, i, x);
+      int cell = or_cell(m, x);
+      if ((occ[cell >> 5] >> (cell & 31)) & 1u) mk[i >> 5] |= 1u << (i & 31);
+    }
+  }
+}
+
 /* ------------------------------------------------------------------------- */
 /* Occupancy grid, inference mode (Sec. 3.3)                                  */
 /* ------------------------------------------------------------------------- */
@@ -638,6 +665,20 @@ void or_occupancy(const or_model *m, const or_pose *p, double *sigma, uint32_t *
     sigma[cell] = s.start >= 0 ? s.sigma : 0.0;
   }
   if (bits) or_occ_bits(R, m->dilate, m->tau, sigma, bits);
+}
+
+void or_occupancy_cells(const or_model *m, const or_pose *p, int n, const int32_t *cells,
+                        double *sigma, int nthreads) {
+  set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int i = 0; i < n; ++i) {
+    float x[3];
+    or_cell_center(m, cells[i], x);
+    double xn[3] = {(double)x[0], (double)x[1], (double)x[2]};
+    or_sample s;
+    or_posed_field(m, p, xn, &s);
+    sigma[i] = s.start >= 0 ? s.sigma : 0.0;
+  }
 }
 
 /* ------------------------------------------------------------------------- */

@@ -72,10 +72,11 @@ typedef struct or_camera {
 /* Per-sample diagnostics of the posed field f'(x') = f(x*). */
 enum {
   OR_FLAG_CONV = 1,   /* a start's last residual check is within 2x of tol */
-  OR_FLAG_BOX = 2,    /* a converged root lies within 1e-5 of the canonical box */
+  OR_FLAG_BOX = 2,    /* a converged root lies within 1e-4 of the canonical box */
   OR_FLAG_DUP = 4,    /* two roots at a distance near the 1e-4 merge radius */
   OR_FLAG_TIE = 8,    /* best and runner-up density within 1e-3 relative */
   OR_FLAG_SING = 16,  /* a start's Jacobian determinant near the 1e-6 cutoff */
+  OR_FLAG_TERM = 32,  /* transmittance within 1e-3 relative of the stopping threshold */
 };
 
 typedef struct or_sample {
@@ -125,9 +126,16 @@ void or_render(const or_model *m, const or_pose *p, const or_camera *c, const ui
 void or_render_pixels(const or_model *m, const or_pose *p, const or_camera *c,
                       const uint32_t *occ, int n, const int32_t *pix, double *rgb,
                       double *alpha, int *ray_flags, int *ray_nsamp, int nthreads);
+/* Per pixel, a bitmask of the slots that fall in occupied cells:
+ * bit i of mask[pixel * ceil(N/32) + i/32]. */
+void or_march_mask(const or_model *m, const or_pose *p, const or_camera *c, const uint32_t *occ,
+                   uint32_t *mask);
 /* Sec. 3.3: density at every cell centre, then threshold + dilation + packing. */
 void or_occupancy(const or_model *m, const or_pose *p, double *sigma, uint32_t *bits,
                   int nthreads);
+/* Density at the centres of n given cells (a bounded part of the grid). */
+void or_occupancy_cells(const or_model *m, const or_pose *p, int n, const int32_t *cells,
+                        double *sigma, int nthreads);
 void or_occ_bits(int R, int dilate, double tau, const double *sigma, uint32_t *bits);
 void or_occ_bits_f32(int R, int dilate, float tau, const float *sigma, uint32_t *bits);
 /* Brute-force root set: Newton from every point of an n^3 canonical lattice. */

@@ -1,0 +1,228 @@
+"""Thin Python binding of libia.so, the sm_103a articulated radiance-field render path.
+
+Argument marshalling only: every step of the path runs in the CUDA library
+(include/ia.h documents each call).  PyTorch provides device memory and streams.
+The binding refuses to work without the compiled library: there is no CPU or
+PyTorch fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libia.so")
+
+IA_OK, IA_ERR_ARG, IA_ERR_STATE, IA_ERR_CUDA, IA_ERR_OOM, IA_ERR_LIMIT = range(6)
+IA_FP32, IA_FP16, IA_BF16 = 0, 1, 2
+IA_OCC_POSE, IA_OCC_UNION = 0, 1
+MAX_LEVELS = 16
+
+
+class IAError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"ia status {status}: {msg}")
+        self.status = status
+
+
+class Config(C.Structure):
+    _fields_ = [("n_levels", C.c_int), ("n_features", C.c_int), ("log2_table", C.c_int),
+                ("level_res", C.c_int * MAX_LEVELS), ("mlp_width", C.c_int), ("max_samples", C.c_int),
+                ("broyden_max_iter", C.c_int), ("broyden_tol", C.c_float), ("occ_res", C.c_int),
+                ("occ_tau", C.c_float), ("occ_dilate", C.c_int), ("early_stop_T", C.c_float),
+                ("precision", C.c_int)]
+
+
+class Camera(C.Structure):
+    _fields_ = [("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float),
+                ("width", C.c_int), ("height", C.c_int), ("c2w", C.c_float * 12)]
+
+
+class RenderStats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("rays", "hit_rays", "marched_slots", "occupied_samples", "starts",
+                                         "broyden_iters", "converged", "roots", "early_stopped")]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libia.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                              "(nvcc -gencode arch=compute_103a,code=sm_103a)")
+        L = C.CDLL(LIB_PATH)
+        P, I, V = C.c_void_p, C.c_int, C.c_void_p
+        sigs = {
+            "ia_create": [C.POINTER(Config), C.POINTER(C.c_void_p)],
+            "ia_set_skeleton": [P, I, P, P, P, I, P, P, P, P],
+            "ia_param_sizes": [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
+            "ia_set_params": [P, P, P, V],
+            "ia_get_params": [P, P, P, V],
+            "ia_set_pose": [P, I, P, P, V],
+            "ia_get_transforms": [P, I, P, P, P, V],
+            "ia_update_occupancy": [P, I, I, P, P, C.POINTER(RenderStats), V],
+            "ia_occupancy_from_density": [P, P, P, V],
+            "ia_set_occupancy": [P, P, V],
+            "ia_query_posed": [P, I, I, P, P, P, P, P, V],
+            "ia_query_canonical": [P, I, P, P, P, V],
+            "ia_render": [P, I, C.POINTER(Camera), P, P, C.POINTER(RenderStats), V],
+            "ia_march_mask": [P, I, C.POINTER(Camera), P, V],
+        }
+        for name, args in sigs.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.ia_destroy.argtypes = [C.c_void_p]
+        L.ia_destroy.restype = None
+        L.ia_last_error.argtypes = [C.c_void_p]
+        L.ia_last_error.restype = C.c_char_p
+        L.ia_version.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(st, ctx):
+    if st != IA_OK:
+        msg = lib().ia_last_error(ctx)
+        raise IAError(st, msg.decode() if msg else "")
+
+
+def _ptr(t):
+    """Device or host address of a tensor / ndarray (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        assert t.flags["C_CONTIGUOUS"]
+        return t.ctypes.data
+    assert t.is_contiguous(), "tensors passed to libia must be contiguous"
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def make_config(*, n_levels, log2_table, level_res, max_samples, broyden_max_iter=10, broyden_tol=1e-5,
+                occ_res=64, occ_tau=0.01, occ_dilate=1, early_stop_T=1e-4, precision=IA_FP32, n_features=2,
+                mlp_width=64):
+    cfg = Config()
+    cfg.n_levels, cfg.n_features, cfg.log2_table = n_levels, n_features, log2_table
+    for i, r in enumerate(level_res):
+        cfg.level_res[i] = int(r)
+    cfg.mlp_width, cfg.max_samples = mlp_width, max_samples
+    cfg.broyden_max_iter, cfg.broyden_tol = broyden_max_iter, broyden_tol
+    cfg.occ_res, cfg.occ_tau, cfg.occ_dilate = occ_res, occ_tau, occ_dilate
+    cfg.early_stop_T, cfg.precision = early_stop_T, precision
+    return cfg
+
+
+def make_camera(fx, fy, cx, cy, width, height, c2w):
+    cam = Camera()
+    cam.fx, cam.fy, cam.cx, cam.cy = float(fx), float(fy), float(cx), float(cy)
+    cam.width, cam.height = int(width), int(height)
+    for i, v in enumerate(np.asarray(c2w, dtype=np.float32).reshape(-1)):
+        cam.c2w[i] = float(v)
+    return cam
+
+
+# --------------------------------------------------------------- C ABI names
+
+def ia_create(cfg: Config) -> C.c_void_p:
+    ctx = C.c_void_p()
+    st = lib().ia_create(C.byref(cfg), C.byref(ctx))
+    _check(st, None)
+    return ctx
+
+
+def ia_destroy(ctx):
+    lib().ia_destroy(ctx)
+
+
+def ia_last_error(ctx):
+    return lib().ia_last_error(ctx).decode()
+
+
+def ia_version():
+    return lib().ia_version().decode()
+
+
+def ia_set_skeleton(ctx, parents, rest_joints, skin_grid, canon_min, canon_max, norm_min, norm_max):
+    parents = np.ascontiguousarray(parents, dtype=np.int32)
+    rest = np.ascontiguousarray(rest_joints, dtype=np.float64)
+    skin = skin_grid if not isinstance(skin_grid, np.ndarray) else np.ascontiguousarray(skin_grid, np.float32)
+    boxes = [np.ascontiguousarray(b, dtype=np.float32) for b in (canon_min, canon_max, norm_min, norm_max)]
+    res = int(skin.shape[0])
+    _check(lib().ia_set_skeleton(ctx, len(parents), _ptr(parents), _ptr(rest), _ptr(skin), res,
+                                 *[_ptr(b) for b in boxes]), ctx)
+
+
+def ia_param_sizes(ctx):
+    a, b = C.c_int64(), C.c_int64()
+    _check(lib().ia_param_sizes(ctx, C.byref(a), C.byref(b)), ctx)
+    return a.value, b.value
+
+
+def ia_set_params(ctx, table, mlp, stream=None):
+    _check(lib().ia_set_params(ctx, _ptr(table), _ptr(mlp), _stream(stream)), ctx)
+
+
+def ia_get_params(ctx, table, mlp, stream=None):
+    _check(lib().ia_get_params(ctx, _ptr(table), _ptr(mlp), _stream(stream)), ctx)
+
+
+def ia_set_pose(ctx, axis_angle, root_trans, stream=None):
+    th = np.ascontiguousarray(axis_angle, dtype=np.float64)
+    tr = np.ascontiguousarray(root_trans, dtype=np.float64)
+    n = th.shape[0] if th.ndim == 3 else 1
+    _check(lib().ia_set_pose(ctx, n, _ptr(th), _ptr(tr), _stream(stream)), ctx)
+
+
+def ia_get_transforms(ctx, pose, N=None, Ninv=None, B0inv=None, stream=None):
+    _check(lib().ia_get_transforms(ctx, pose, _ptr(N), _ptr(Ninv), _ptr(B0inv), _stream(stream)), ctx)
+
+
+def ia_update_occupancy(ctx, pose, mode=IA_OCC_POSE, sigma_out=None, bits_out=None, stats=False, stream=None):
+    s = RenderStats() if stats else None
+    _check(lib().ia_update_occupancy(ctx, pose, mode, _ptr(sigma_out), _ptr(bits_out),
+                                     C.byref(s) if s is not None else None, _stream(stream)), ctx)
+    return s.as_dict() if s is not None else None
+
+
+def ia_occupancy_from_density(ctx, sigma, bits_out=None, stream=None):
+    _check(lib().ia_occupancy_from_density(ctx, _ptr(sigma), _ptr(bits_out), _stream(stream)), ctx)
+
+
+def ia_set_occupancy(ctx, bits, stream=None):
+    _check(lib().ia_set_occupancy(ctx, _ptr(bits), _stream(stream)), ctx)
+
+
+def ia_query_posed(ctx, pose, x, sigma=None, rgb=None, x_canon=None, start=None, stream=None):
+    n = int(x.shape[0])
+    _check(lib().ia_query_posed(ctx, pose, n, _ptr(x), _ptr(sigma), _ptr(rgb), _ptr(x_canon), _ptr(start),
+                                _stream(stream)), ctx)
+
+
+def ia_query_canonical(ctx, x, sigma, rgb, stream=None):
+    _check(lib().ia_query_canonical(ctx, int(x.shape[0]), _ptr(x), _ptr(sigma), _ptr(rgb), _stream(stream)), ctx)
+
+
+def ia_render(ctx, pose, cam: Camera, rgb, alpha, stats=False, stream=None):
+    s = RenderStats() if stats else None
+    _check(lib().ia_render(ctx, pose, C.byref(cam), _ptr(rgb), _ptr(alpha), C.byref(s) if s is not None else None,
+                           _stream(stream)), ctx)
+    return s.as_dict() if s is not None else None
+
+
+def ia_march_mask(ctx, pose, cam: Camera, slot_mask, stream=None):
+    _check(lib().ia_march_mask(ctx, pose, C.byref(cam), _ptr(slot_mask), _stream(stream)), ctx)

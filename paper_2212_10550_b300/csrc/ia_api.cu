@@ -1,0 +1,540 @@
+// C ABI of the articulated radiance-field render path (see include/ia.h).
+//
+// Host side only: argument checks, device memory owned by the context, and
+// kernel launches.  Every entry point returns an ia_status and records a
+// message on failure; nothing here aborts the process.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ia.h"
+#include "ia_internal.h"
+
+using namespace ia;
+
+struct ia_ctx {
+  ia_config cfg{};
+  int device = 0;
+  int num_sms = 0;
+  std::string err;
+  // skeleton
+  int nb = 0;
+  int Rw = 0;
+  float cmin[3]{}, cmax[3]{}, nmin[3]{}, nmax[3]{};
+  int* d_parent = nullptr;
+  double* d_rest = nullptr;
+  float* d_skin = nullptr;
+  // canonical field
+  int n_in = 0;
+  int64_t n_entries = 0;
+  Level levels[kMaxLevels]{};
+  float* d_table = nullptr;
+  float* d_mlp = nullptr;
+  bool have_params = false;
+  // poses
+  int n_poses = 0, pose_cap = 0;
+  float* d_N = nullptr;
+  float* d_Ninv = nullptr;
+  float* d_B0inv = nullptr;
+  float4* d_M = nullptr;
+  double* d_theta = nullptr;
+  double* d_trans = nullptr;
+  // occupancy
+  uint32_t* d_occ = nullptr;
+  uint32_t* d_occ_train = nullptr;
+  float* d_sigma = nullptr;
+  bool have_occ = false;
+  // counters
+  unsigned long long* d_stats = nullptr;
+  unsigned int* d_counter = nullptr;
+  // scratch for host-memory outputs of ia_render
+  float* d_out = nullptr;
+  size_t out_cap = 0;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+ia_status fail(ia_ctx* c, ia_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf; else g_create_err = buf;
+  return st;
+}
+
+ia_status cuda_fail(ia_ctx* c, cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear a sticky-free error so the next call starts clean
+  if (e == cudaErrorMemoryAllocation) return fail(c, IA_ERR_OOM, "%s: out of device memory", what);
+  return fail(c, IA_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define IA_CUDA(c, call, what)                      \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_fail((c), e_, (what)); \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+  if (*p) { cudaFree(*p); *p = nullptr; }
+  if (count == 0) return cudaSuccess;
+  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+template <class T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+bool finite3(const float v[3]) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+FieldDev field_dev(const ia_ctx* c) {
+  FieldDev F{};
+  F.table = reinterpret_cast<const float2*>(c->d_table);
+  F.L = c->cfg.n_levels;
+  for (int l = 0; l < kMaxLevels; ++l) F.lv[l] = c->levels[l];
+  for (int a = 0; a < 3; ++a) {
+    F.cmin[a] = c->cmin[a];
+    F.inv_ext[a] = 1.0f / (c->cmax[a] - c->cmin[a]);
+  }
+  return F;
+}
+
+PosedArgs posed_args(const ia_ctx* c, int pose) {
+  PosedArgs a{};
+  a.S.M = c->d_M + (size_t)pose * c->Rw * c->Rw * c->Rw * 3;
+  a.S.Rw = c->Rw;
+  for (int i = 0; i < 3; ++i) {
+    a.S.cmin[i] = c->cmin[i];
+    a.S.cmax[i] = c->cmax[i];
+    a.S.scale[i] = (float)(c->Rw - 1) / (c->cmax[i] - c->cmin[i]);
+  }
+  a.F = field_dev(c);
+  a.cfg.nb = c->nb;
+  a.cfg.max_iter = c->cfg.broyden_max_iter;
+  a.cfg.tol2 = c->cfg.broyden_tol * c->cfg.broyden_tol;
+  a.Ninv = c->d_Ninv + (size_t)pose * c->nb * 12;
+  a.mlp = c->d_mlp;
+  a.n_in = c->n_in;
+  return a;
+}
+
+BoxDev box_dev(const ia_ctx* c) {
+  BoxDev b{};
+  b.R = c->cfg.occ_res;
+  for (int a = 0; a < 3; ++a) {
+    b.nmin[a] = c->nmin[a];
+    b.nmax[a] = c->nmax[a];
+    const float ext = c->nmax[a] - c->nmin[a];  // fp32, as the documented indexing
+    b.cell_scale[a] = (float)b.R / ext;
+    b.cell_size[a] = ext / (float)b.R;
+  }
+  return b;
+}
+
+ia_status need_ready(ia_ctx* c, int pose, bool need_occ) {
+  if (!c) return fail(nullptr, IA_ERR_ARG, "null context");
+  if (c->nb == 0) return fail(c, IA_ERR_STATE, "ia_set_skeleton has not been called");
+  if (!c->have_params) return fail(c, IA_ERR_STATE, "ia_set_params has not been called");
+  if (c->n_poses == 0) return fail(c, IA_ERR_STATE, "ia_set_pose has not been called");
+  if (pose < 0 || pose >= c->n_poses) return fail(c, IA_ERR_ARG, "pose %d out of range [0, %d)", pose, c->n_poses);
+  if (need_occ && !c->have_occ) return fail(c, IA_ERR_STATE, "no occupancy grid (ia_update_occupancy first)");
+  return IA_OK;
+}
+
+void read_stats(ia_ctx* c, ia_render_stats* out, cudaStream_t s) {
+  unsigned long long h[ST_COUNT];
+  cudaMemcpyAsync(h, c->d_stats, sizeof(h), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  out->rays = (int64_t)h[ST_RAYS];
+  out->hit_rays = (int64_t)h[ST_HIT];
+  out->marched_slots = (int64_t)h[ST_MARCHED];
+  out->occupied_samples = (int64_t)h[ST_OCC];
+  out->starts = (int64_t)h[ST_STARTS];
+  out->broyden_iters = (int64_t)h[ST_ITERS];
+  out->converged = (int64_t)h[ST_CONV];
+  out->roots = (int64_t)h[ST_ROOTS];
+  out->early_stopped = (int64_t)h[ST_EARLY];
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ia_version(void) { return "ia-b300 0.1 (sm_103a)"; }
+
+const char* ia_last_error(const ia_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
+
+ia_status ia_create(const ia_config* cfg, ia_ctx** out) {
+  if (!cfg || !out) return fail(nullptr, IA_ERR_ARG, "null argument");
+  *out = nullptr;
+  const ia_config& g = *cfg;
+  if (g.n_levels < 1 || g.n_levels > IA_MAX_LEVELS) return fail(nullptr, IA_ERR_ARG, "n_levels must be 1..16");
+  if (g.n_features != 2) return fail(nullptr, IA_ERR_ARG, "n_features must be 2");
+  if (g.log2_table < 10 || g.log2_table > 24) return fail(nullptr, IA_ERR_ARG, "log2_table must be 10..24");
+  for (int l = 0; l < g.n_levels; ++l)
+    if (g.level_res[l] < 2 || g.level_res[l] > (1 << 20))
+      return fail(nullptr, IA_ERR_ARG, "level_res[%d] = %d outside 2..2^20", l, g.level_res[l]);
+  if (g.mlp_width != 64) return fail(nullptr, IA_ERR_ARG, "mlp_width must be 64");
+  if (g.max_samples < 1 || g.max_samples > 1024) return fail(nullptr, IA_ERR_ARG, "max_samples must be 1..1024");
+  if (g.broyden_max_iter < 1 || g.broyden_max_iter > 64)
+    return fail(nullptr, IA_ERR_ARG, "broyden_max_iter must be 1..64");
+  if (!(g.broyden_tol > 0.f) || !std::isfinite(g.broyden_tol)) return fail(nullptr, IA_ERR_ARG, "broyden_tol must be > 0");
+  if (g.occ_res < 2 || g.occ_res > 256) return fail(nullptr, IA_ERR_ARG, "occ_res must be 2..256");
+  if (!std::isfinite(g.occ_tau)) return fail(nullptr, IA_ERR_ARG, "occ_tau must be finite");
+  if (g.occ_dilate < 0 || g.occ_dilate > 4) return fail(nullptr, IA_ERR_ARG, "occ_dilate must be 0..4");
+  if (!std::isfinite(g.early_stop_T) || g.early_stop_T >= 1.f)
+    return fail(nullptr, IA_ERR_ARG, "early_stop_T must be finite and < 1");
+  if (g.precision != IA_FP32) return fail(nullptr, IA_ERR_ARG, "precision %d not available", g.precision);
+
+  ia_ctx* c = new ia_ctx();
+  c->cfg = g;
+  cudaGetDevice(&c->device);
+  if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return fail(nullptr, IA_ERR_CUDA, "no usable CUDA device");
+  }
+  const int64_t T = 1LL << g.log2_table;
+  int64_t off = 0;
+  for (int l = 0; l < g.n_levels; ++l) {
+    const int64_t r1 = (int64_t)g.level_res[l] + 1;
+    const int64_t dense = r1 * r1 * r1;
+    Level& lv = c->levels[l];
+    lv.res = g.level_res[l];
+    lv.dense = dense <= T ? 1 : 0;
+    lv.size = (uint32_t)(dense <= T ? dense : T);
+    lv.offset = (uint32_t)off;
+    off += lv.size;
+  }
+  c->n_entries = off;
+  c->n_in = 2 * g.n_levels;
+  const int R = g.occ_res;
+  const size_t words = ((size_t)R * R * R + 31) / 32;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = dalloc(&c->d_table, (size_t)off * 2);
+  if (e == cudaSuccess) e = dalloc(&c->d_mlp, (size_t)kWidth * c->n_in + kWidth + kWidth * kWidth + kWidth + 4 * kWidth + 4);
+  if (e == cudaSuccess) e = dalloc(&c->d_occ, words);
+  if (e == cudaSuccess) e = dalloc(&c->d_occ_train, words);
+  if (e == cudaSuccess) e = dalloc(&c->d_sigma, (size_t)R * R * R);
+  if (e == cudaSuccess) e = dalloc(&c->d_stats, (size_t)ST_COUNT);
+  if (e == cudaSuccess) e = dalloc(&c->d_counter, (size_t)1);
+  if (e == cudaSuccess) e = cudaMemset(c->d_occ_train, 0, words * sizeof(uint32_t));
+  if (e != cudaSuccess) {
+    ia_status st = cuda_fail(nullptr, e, "ia_create");
+    ia_destroy(c);
+    return st;
+  }
+  *out = c;
+  return IA_OK;
+}
+
+void ia_destroy(ia_ctx* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  dfree(c->d_parent);
+  dfree(c->d_rest);
+  dfree(c->d_skin);
+  dfree(c->d_table);
+  dfree(c->d_mlp);
+  dfree(c->d_N);
+  dfree(c->d_Ninv);
+  dfree(c->d_B0inv);
+  dfree(c->d_M);
+  dfree(c->d_theta);
+  dfree(c->d_trans);
+  dfree(c->d_occ);
+  dfree(c->d_occ_train);
+  dfree(c->d_sigma);
+  dfree(c->d_stats);
+  dfree(c->d_counter);
+  dfree(c->d_out);
+  delete c;
+}
+
+ia_status ia_set_skeleton(ia_ctx* c, int n_bones, const int32_t* parent, const double* rest_joints,
+                          const float* skin_grid, int skin_res, const float canon_min[3], const float canon_max[3],
+                          const float norm_min[3], const float norm_max[3]) {
+  if (!c) return fail(nullptr, IA_ERR_ARG, "null context");
+  if (n_bones < 1 || n_bones > IA_MAX_BONES) return fail(c, IA_ERR_ARG, "n_bones must be 1..%d", IA_MAX_BONES);
+  if (!parent || !rest_joints || !skin_grid || !canon_min || !canon_max || !norm_min || !norm_max)
+    return fail(c, IA_ERR_ARG, "null argument");
+  if (skin_res < 2 || skin_res > 256) return fail(c, IA_ERR_ARG, "skin_res must be 2..256");
+  if (parent[0] != -1) return fail(c, IA_ERR_ARG, "parent[0] must be -1 (bone 0 is the root)");
+  for (int k = 1; k < n_bones; ++k)
+    if (parent[k] < 0 || parent[k] >= k)
+      return fail(c, IA_ERR_ARG, "parent[%d] = %d: parents must precede children", k, parent[k]);
+  for (int i = 0; i < 3 * n_bones; ++i)
+    if (!std::isfinite(rest_joints[i])) return fail(c, IA_ERR_ARG, "rest_joints must be finite");
+  if (!finite3(canon_min) || !finite3(canon_max) || !finite3(norm_min) || !finite3(norm_max))
+    return fail(c, IA_ERR_ARG, "boxes must be finite");
+  for (int a = 0; a < 3; ++a)
+    if (!(canon_max[a] > canon_min[a]) || !(norm_max[a] > norm_min[a]))
+      return fail(c, IA_ERR_ARG, "box max must exceed min on every axis");
+  const size_t V = (size_t)skin_res * skin_res * skin_res;
+  IA_CUDA(c, dalloc(&c->d_parent, (size_t)n_bones), "ia_set_skeleton");
+  IA_CUDA(c, dalloc(&c->d_rest, (size_t)3 * n_bones), "ia_set_skeleton");
+  IA_CUDA(c, dalloc(&c->d_skin, V * n_bones), "ia_set_skeleton");
+  IA_CUDA(c, cudaMemcpy(c->d_parent, parent, sizeof(int) * n_bones, cudaMemcpyHostToDevice), "ia_set_skeleton");
+  IA_CUDA(c, cudaMemcpy(c->d_rest, rest_joints, sizeof(double) * 3 * n_bones, cudaMemcpyHostToDevice),
+          "ia_set_skeleton");
+  IA_CUDA(c, cudaMemcpy(c->d_skin, skin_grid, sizeof(float) * V * n_bones, cudaMemcpyDefault), "ia_set_skeleton");
+  c->nb = n_bones;
+  c->Rw = skin_res;
+  for (int a = 0; a < 3; ++a) {
+    c->cmin[a] = canon_min[a];
+    c->cmax[a] = canon_max[a];
+    c->nmin[a] = norm_min[a];
+    c->nmax[a] = norm_max[a];
+  }
+  c->n_poses = 0;  // per-pose state depends on the skeleton
+  c->have_occ = false;
+  return IA_OK;
+}
+
+ia_status ia_param_sizes(const ia_ctx* c, int64_t* table_floats, int64_t* mlp_floats) {
+  if (!c) return fail(nullptr, IA_ERR_ARG, "null context");
+  if (table_floats) *table_floats = c->n_entries * 2;
+  if (mlp_floats) *mlp_floats = (int64_t)kWidth * c->n_in + kWidth + kWidth * kWidth + kWidth + 4 * kWidth + 4;
+  return IA_OK;
+}
+
+ia_status ia_set_params(ia_ctx* c, const float* table, const float* mlp, void* stream) {
+  if (!c) return fail(nullptr, IA_ERR_ARG, "null context");
+  if (!table || !mlp) return fail(c, IA_ERR_ARG, "null argument");
+  int64_t nt = 0, nm = 0;
+  ia_param_sizes(c, &nt, &nm);
+  cudaStream_t s = (cudaStream_t)stream;
+  IA_CUDA(c, cudaMemcpyAsync(c->d_table, table, sizeof(float) * nt, cudaMemcpyDefault, s), "ia_set_params");
+  IA_CUDA(c, cudaMemcpyAsync(c->d_mlp, mlp, sizeof(float) * nm, cudaMemcpyDefault, s), "ia_set_params");
+  c->have_params = true;
+  return IA_OK;
+}
+
+ia_status ia_get_params(ia_ctx* c, float* table, float* mlp, void* stream) {
+  if (!c) return fail(nullptr, IA_ERR_ARG, "null context");
+  if (!c->have_params) return fail(c, IA_ERR_STATE, "ia_set_params has not been called");
+  int64_t nt = 0, nm = 0;
+  ia_param_sizes(c, &nt, &nm);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (table) IA_CUDA(c, cudaMemcpyAsync(table, c->d_table, sizeof(float) * nt, cudaMemcpyDefault, s), "ia_get_params");
+  if (mlp) IA_CUDA(c, cudaMemcpyAsync(mlp, c->d_mlp, sizeof(float) * nm, cudaMemcpyDefault, s), "ia_get_params");
+  IA_CUDA(c, cudaStreamSynchronize(s), "ia_get_params");
+  return IA_OK;
+}
+
+ia_status ia_set_pose(ia_ctx* c, int n_poses, const double* axis_angle, const double* root_trans, void* stream) {
+  if (!c) return fail(nullptr, IA_ERR_ARG, "null context");
+  if (c->nb == 0) return fail(c, IA_ERR_STATE, "ia_set_skeleton has not been called");
+  if (n_poses < 1 || n_poses > 4096) return fail(c, IA_ERR_ARG, "n_poses must be 1..4096");
+  if (!axis_angle || !root_trans) return fail(c, IA_ERR_ARG, "null argument");
+  const size_t nth = (size_t)n_poses * c->nb * 3;
+  for (size_t i = 0; i < nth; ++i)
+    if (!std::isfinite(axis_angle[i])) return fail(c, IA_ERR_ARG, "axis_angle must be finite");
+  for (int i = 0; i < 3 * n_poses; ++i)
+    if (!std::isfinite(root_trans[i])) return fail(c, IA_ERR_ARG, "root_trans must be finite");
+  const size_t V = (size_t)c->Rw * c->Rw * c->Rw;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n_poses > c->pose_cap) {
+    IA_CUDA(c, cudaStreamSynchronize(s), "ia_set_pose");
+    c->pose_cap = 0;
+    IA_CUDA(c, dalloc(&c->d_N, (size_t)n_poses * c->nb * 12), "ia_set_pose");
+    IA_CUDA(c, dalloc(&c->d_Ninv, (size_t)n_poses * c->nb * 12), "ia_set_pose");
+    IA_CUDA(c, dalloc(&c->d_B0inv, (size_t)n_poses * 12), "ia_set_pose");
+    IA_CUDA(c, dalloc(&c->d_M, (size_t)n_poses * V * 3), "ia_set_pose");
+    IA_CUDA(c, dalloc(&c->d_theta, nth), "ia_set_pose");
+    IA_CUDA(c, dalloc(&c->d_trans, (size_t)n_poses * 3), "ia_set_pose");
+    c->pose_cap = n_poses;
+  }
+  IA_CUDA(c, cudaMemcpyAsync(c->d_theta, axis_angle, sizeof(double) * nth, cudaMemcpyHostToDevice, s), "ia_set_pose");
+  IA_CUDA(c, cudaMemcpyAsync(c->d_trans, root_trans, sizeof(double) * 3 * n_poses, cudaMemcpyHostToDevice, s),
+          "ia_set_pose");
+  IA_CUDA(c, launch_pose_chain(n_poses, c->nb, c->d_parent, c->d_rest, c->d_theta, c->d_trans, c->d_N, c->d_Ninv,
+                               c->d_B0inv, s),
+          "ia_set_pose: pose chain");
+  IA_CUDA(c, launch_blend(n_poses, (int)V, c->nb, c->d_skin, c->d_N, c->d_M, s), "ia_set_pose: blend grid");
+  c->n_poses = n_poses;
+  return IA_OK;
+}
+
+ia_status ia_get_transforms(ia_ctx* c, int pose, float* N, float* Ninv, float* B0inv, void* stream) {
+  if (!c) return fail(nullptr, IA_ERR_ARG, "null context");
+  if (c->n_poses == 0) return fail(c, IA_ERR_STATE, "ia_set_pose has not been called");
+  if (pose < 0 || pose >= c->n_poses) return fail(c, IA_ERR_ARG, "pose out of range");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = (size_t)c->nb * 12;
+  if (N) IA_CUDA(c, cudaMemcpyAsync(N, c->d_N + pose * n, n * 4, cudaMemcpyDefault, s), "ia_get_transforms");
+  if (Ninv) IA_CUDA(c, cudaMemcpyAsync(Ninv, c->d_Ninv + pose * n, n * 4, cudaMemcpyDefault, s), "ia_get_transforms");
+  if (B0inv)
+    IA_CUDA(c, cudaMemcpyAsync(B0inv, c->d_B0inv + pose * 12, 48, cudaMemcpyDefault, s), "ia_get_transforms");
+  IA_CUDA(c, cudaStreamSynchronize(s), "ia_get_transforms");
+  return IA_OK;
+}
+
+ia_status ia_update_occupancy(ia_ctx* c, int pose, int mode, float* sigma_out, uint32_t* bits_out,
+                              ia_render_stats* stats, void* stream) {
+  ia_status st = need_ready(c, pose, false);
+  if (st != IA_OK) return st;
+  if (mode != IA_OCC_POSE && mode != IA_OCC_UNION) return fail(c, IA_ERR_ARG, "unknown occupancy mode %d", mode);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int R = c->cfg.occ_res;
+  const size_t words = ((size_t)R * R * R + 31) / 32;
+  float* sig = sigma_out ? sigma_out : c->d_sigma;
+  IA_CUDA(c, cudaMemsetAsync(c->d_stats, 0, sizeof(unsigned long long) * ST_COUNT, s), "ia_update_occupancy");
+  IA_CUDA(c, launch_occ_density(posed_args(c, pose), box_dev(c), sig, c->d_stats, s), "ia_update_occupancy: density");
+  if (mode == IA_OCC_POSE) {
+    IA_CUDA(c, launch_occ_bits(sig, R, c->cfg.occ_dilate, c->cfg.occ_tau, c->d_occ, nullptr, s),
+            "ia_update_occupancy: bits");
+    c->have_occ = true;
+    if (bits_out)
+      IA_CUDA(c, cudaMemcpyAsync(bits_out, c->d_occ, words * 4, cudaMemcpyDeviceToDevice, s), "ia_update_occupancy");
+  } else {
+    IA_CUDA(c, launch_occ_bits(sig, R, c->cfg.occ_dilate, c->cfg.occ_tau, bits_out, c->d_occ_train, s),
+            "ia_update_occupancy: union");
+  }
+  if (stats) read_stats(c, stats, s);
+  return IA_OK;
+}
+
+ia_status ia_occupancy_from_density(ia_ctx* c, const float* sigma, uint32_t* bits_out, void* stream) {
+  if (!c) return fail(nullptr, IA_ERR_ARG, "null context");
+  if (!sigma) return fail(c, IA_ERR_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int R = c->cfg.occ_res;
+  const size_t words = ((size_t)R * R * R + 31) / 32;
+  IA_CUDA(c, launch_occ_bits(sigma, R, c->cfg.occ_dilate, c->cfg.occ_tau, c->d_occ, nullptr, s),
+          "ia_occupancy_from_density");
+  c->have_occ = true;
+  if (bits_out)
+    IA_CUDA(c, cudaMemcpyAsync(bits_out, c->d_occ, words * 4, cudaMemcpyDeviceToDevice, s), "ia_occupancy_from_density");
+  return IA_OK;
+}
+
+ia_status ia_set_occupancy(ia_ctx* c, const uint32_t* bits, void* stream) {
+  if (!c) return fail(nullptr, IA_ERR_ARG, "null context");
+  if (!bits) return fail(c, IA_ERR_ARG, "null argument");
+  const int R = c->cfg.occ_res;
+  const size_t words = ((size_t)R * R * R + 31) / 32;
+  IA_CUDA(c, cudaMemcpyAsync(c->d_occ, bits, words * 4, cudaMemcpyDefault, (cudaStream_t)stream), "ia_set_occupancy");
+  c->have_occ = true;
+  return IA_OK;
+}
+
+ia_status ia_query_posed(ia_ctx* c, int pose, int n, const float* x, float* sigma, float* rgb, float* x_canon,
+                         int32_t* start, void* stream) {
+  ia_status st = need_ready(c, pose, false);
+  if (st != IA_OK) return st;
+  if (n < 0 || (n > 0 && !x)) return fail(c, IA_ERR_ARG, "bad point array");
+  if (n == 0) return IA_OK;
+  IA_CUDA(c, launch_query_posed(posed_args(c, pose), n, x, sigma, rgb, x_canon, start, (cudaStream_t)stream),
+          "ia_query_posed");
+  return IA_OK;
+}
+
+ia_status ia_query_canonical(ia_ctx* c, int n, const float* x, float* sigma, float* rgb, void* stream) {
+  if (!c) return fail(nullptr, IA_ERR_ARG, "null context");
+  if (c->nb == 0) return fail(c, IA_ERR_STATE, "ia_set_skeleton has not been called");
+  if (!c->have_params) return fail(c, IA_ERR_STATE, "ia_set_params has not been called");
+  if (n < 0 || (n > 0 && (!x || !sigma || !rgb))) return fail(c, IA_ERR_ARG, "bad arrays");
+  if (n == 0) return IA_OK;
+  IA_CUDA(c, launch_query_canonical(field_dev(c), c->d_mlp, c->n_in, n, x, sigma, rgb, (cudaStream_t)stream),
+          "ia_query_canonical");
+  return IA_OK;
+}
+
+static ia_status check_camera(ia_ctx* c, const ia_camera* cam) {
+  if (!cam) return fail(c, IA_ERR_ARG, "null camera");
+  if (cam->width < 1 || cam->height < 1 || (int64_t)cam->width * cam->height > (1LL << 28))
+    return fail(c, IA_ERR_ARG, "image size out of range");
+  if (!(cam->fx != 0.f) || !(cam->fy != 0.f) || !std::isfinite(cam->fx) || !std::isfinite(cam->fy) ||
+      !std::isfinite(cam->cx) || !std::isfinite(cam->cy))
+    return fail(c, IA_ERR_ARG, "bad intrinsics");
+  for (int i = 0; i < 12; ++i)
+    if (!std::isfinite(cam->c2w[i])) return fail(c, IA_ERR_ARG, "c2w must be finite");
+  return IA_OK;
+}
+
+static RenderArgs render_args(ia_ctx* c, int pose, const ia_camera* cam) {
+  RenderArgs a{};
+  a.P = posed_args(c, pose);
+  a.B0inv = c->d_B0inv + (size_t)pose * 12;
+  a.occ = c->d_occ;
+  a.box = box_dev(c);
+  a.cam.fx = cam->fx;
+  a.cam.fy = cam->fy;
+  a.cam.cx = cam->cx;
+  a.cam.cy = cam->cy;
+  a.cam.width = cam->width;
+  a.cam.height = cam->height;
+  for (int i = 0; i < 12; ++i) a.cam.c2w[i] = cam->c2w[i];
+  a.n_slots = c->cfg.max_samples;
+  a.early_T = c->cfg.early_stop_T;
+  a.tiles_x = (cam->width + kTile - 1) / kTile;
+  const int tiles_y = (cam->height + kTile - 1) / kTile;
+  a.n_ray_ids = a.tiles_x * tiles_y * kTile * kTile;
+  a.counter = c->d_counter;
+  a.stats = c->d_stats;
+  return a;
+}
+
+ia_status ia_march_mask(ia_ctx* c, int pose, const ia_camera* cam, uint32_t* slot_mask, void* stream) {
+  ia_status st = need_ready(c, pose, true);
+  if (st != IA_OK) return st;
+  if ((st = check_camera(c, cam)) != IA_OK) return st;
+  if (!slot_mask) return fail(c, IA_ERR_ARG, "null argument");
+  IA_CUDA(c, launch_march_mask(render_args(c, pose, cam), slot_mask, (cudaStream_t)stream), "ia_march_mask");
+  return IA_OK;
+}
+
+ia_status ia_render(ia_ctx* c, int pose, const ia_camera* cam, float* rgb, float* alpha, ia_render_stats* stats,
+                    void* stream) {
+  ia_status st = need_ready(c, pose, true);
+  if (st != IA_OK) return st;
+  if ((st = check_camera(c, cam)) != IA_OK) return st;
+  if (!rgb || !alpha) return fail(c, IA_ERR_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t npix = (size_t)cam->width * cam->height;
+  const bool dev_rgb = is_device_ptr(rgb), dev_alpha = is_device_ptr(alpha);
+  float* o_rgb = rgb;
+  float* o_alpha = alpha;
+  if (!dev_rgb || !dev_alpha) {
+    if (c->out_cap < npix * 4) {
+      IA_CUDA(c, cudaStreamSynchronize(s), "ia_render");
+      c->out_cap = 0;
+      IA_CUDA(c, dalloc(&c->d_out, npix * 4), "ia_render: output scratch");
+      c->out_cap = npix * 4;
+    }
+    if (!dev_rgb) o_rgb = c->d_out;
+    if (!dev_alpha) o_alpha = c->d_out + 3 * npix;
+  }
+  RenderArgs a = render_args(c, pose, cam);
+  a.rgb = o_rgb;
+  a.alpha = o_alpha;
+  IA_CUDA(c, cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned int), s), "ia_render");
+  IA_CUDA(c, cudaMemsetAsync(c->d_stats, 0, sizeof(unsigned long long) * ST_COUNT, s), "ia_render");
+  IA_CUDA(c, launch_render(a, c->num_sms, s), "ia_render: kernel");
+  if (!dev_rgb) IA_CUDA(c, cudaMemcpyAsync(rgb, o_rgb, npix * 12, cudaMemcpyDeviceToHost, s), "ia_render: copy");
+  if (!dev_alpha) IA_CUDA(c, cudaMemcpyAsync(alpha, o_alpha, npix * 4, cudaMemcpyDeviceToHost, s), "ia_render: copy");
+  if (!dev_rgb || !dev_alpha) IA_CUDA(c, cudaStreamSynchronize(s), "ia_render");
+  if (stats) read_stats(c, stats, s);
+  return IA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,485 @@
+// Device building blocks of the articulated radiance-field render path (sm_103a).
+//
+//   blend_value / blend_value_jac   LBS in normalised space through the blended
+//                                   transform grid M(v) = sum_i W(v,i) N_i
+//                                   (Sec. 3.1, Eq. 5)
+//   posed_field_warp                Fast-SNARF style correspondence search: bone-wise
+//                                   Broyden starts, one sample per lane, flattened
+//                                   so that all lanes gather M at the same step,
+//                                   then one Newton polish and a field evaluation
+//                                   per distinct root, max-density selection
+//   encode / mlp_fp32               multiresolution hash encoding + MLP (Eq. 1-2)
+//
+// Everything here is fp32 (the root-finding and skinning precision); the bone
+// chain is fp64 in the pose kernel.  Indexing arithmetic that decides which
+// samples exist lives in ia_index.cuh and uses explicitly rounded intrinsics.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ia {
+
+constexpr int kMaxBones = 32;
+constexpr int kMaxLevels = 16;
+constexpr int kWidth = 64;
+constexpr int kIn = 32;          // MLP input, zero-padded to 16 levels x 2 features
+constexpr int kMaxRoots = 4;     // distinct roots remembered per sample for merging
+constexpr unsigned kFull = 0xffffffffu;
+
+// MLP weights staged in shared memory (fp32): W1 [64][32] (zero-padded
+// columns), b1 [64], W2 [64][64], b2 [64], W3^T [64][4], b3 [4].
+constexpr int kOffW1 = 0;
+constexpr int kOffB1 = kOffW1 + kWidth * kIn;
+constexpr int kOffW2 = kOffB1 + kWidth;
+constexpr int kOffB2 = kOffW2 + kWidth * kWidth;
+constexpr int kOffW3T = kOffB2 + kWidth;
+constexpr int kOffB3 = kOffW3T + kWidth * 4;
+constexpr int kMlpSmemFloats = kOffB3 + 4;
+
+struct Level {
+  int res;          // grid resolution N_l
+  int dense;        // (N_l + 1)^3 <= T: row-major vertex index, else spatial hash
+  uint32_t size;    // entries in the level
+  uint32_t offset;  // first entry of the level
+};
+
+struct FieldDev {
+  const float2* table;  // [entries] (F = 2)
+  int L;
+  Level lv[kMaxLevels];
+  float cmin[3];
+  float inv_ext[3];     // 1 / (cmax - cmin)
+};
+
+struct SkinDev {
+  const float4* M;      // blended grid of one pose: [Rw^3][3] float4 = rows of N(v)
+  int Rw;
+  float cmin[3], cmax[3];
+  float scale[3];       // (Rw - 1) / (cmax - cmin)
+};
+
+struct SolveCfg {
+  int nb;
+  int max_iter;
+  float tol2;           // tol^2
+};
+
+struct SampleStats {
+  long long starts = 0, iters = 0, converged = 0, roots = 0;
+};
+
+// ---------------------------------------------------------------------------
+// LBS through the blended grid
+// ---------------------------------------------------------------------------
+
+struct CellCoord {
+  int base;       // linear index of the lower corner
+  float f[3];     // fractional position in the cell
+  float live[3];  // 0 where the coordinate was clamped to the border
+};
+
+__device__ __forceinline__ CellCoord skin_cell(const SkinDev& S, float3 x) {
+  CellCoord c;
+  const float xs[3] = {x.x, x.y, x.z};
+  int i0[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float u = (xs[a] - S.cmin[a]) * S.scale[a];
+    float hi = (float)(S.Rw - 1);
+    c.live[a] = 1.f;
+    if (!(u >= 0.f)) { u = 0.f; c.live[a] = 0.f; }
+    if (u > hi) { u = hi; c.live[a] = 0.f; }
+    int q = (int)floorf(u);
+    q = min(q, S.Rw - 2);
+    i0[a] = q;
+    c.f[a] = u - (float)q;
+  }
+  c.base = (i0[2] * S.Rw + i0[1]) * S.Rw + i0[0];
+  return c;
+}
+
+__device__ __forceinline__ int corner_index(const SkinDev& S, int base, int corner) {
+  return base + (corner & 1) + S.Rw * (((corner >> 1) & 1) + S.Rw * ((corner >> 2) & 1));
+}
+
+// M(x) = sum_c w_c M_c  (12 values, rows of a 3x4 matrix)
+__device__ __forceinline__ void blend_value(const SkinDev& S, float3 x, float Mx[12]) {
+  CellCoord c = skin_cell(S, x);
+#pragma unroll
+  for (int q = 0; q < 12; ++q) Mx[q] = 0.f;
+#pragma unroll
+  for (int corner = 0; corner < 8; ++corner) {
+    int v = corner_index(S, c.base, corner);
+    float w = ((corner & 1) ? c.f[0] : 1.f - c.f[0]) * (((corner >> 1) & 1) ? c.f[1] : 1.f - c.f[1]) *
+              (((corner >> 2) & 1) ? c.f[2] : 1.f - c.f[2]);
+    const float4* p = S.M + 3 * v;
+    float4 r0 = __ldg(p), r1 = __ldg(p + 1), r2 = __ldg(p + 2);
+    Mx[0] = fmaf(w, r0.x, Mx[0]); Mx[1] = fmaf(w, r0.y, Mx[1]);
+    Mx[2] = fmaf(w, r0.z, Mx[2]); Mx[3] = fmaf(w, r0.w, Mx[3]);
+    Mx[4] = fmaf(w, r1.x, Mx[4]); Mx[5] = fmaf(w, r1.y, Mx[5]);
+    Mx[6] = fmaf(w, r1.z, Mx[6]); Mx[7] = fmaf(w, r1.w, Mx[7]);
+    Mx[8] = fmaf(w, r2.x, Mx[8]); Mx[9] = fmaf(w, r2.y, Mx[9]);
+    Mx[10] = fmaf(w, r2.z, Mx[10]); Mx[11] = fmaf(w, r2.w, Mx[11]);
+  }
+}
+
+__device__ __forceinline__ float3 apply34(const float A[12], float3 x) {
+  return make_float3(fmaf(A[0], x.x, fmaf(A[1], x.y, fmaf(A[2], x.z, A[3]))),
+                     fmaf(A[4], x.x, fmaf(A[5], x.y, fmaf(A[6], x.z, A[7]))),
+                     fmaf(A[8], x.x, fmaf(A[9], x.y, fmaf(A[10], x.z, A[11]))));
+}
+
+// M(x) and the full Jacobian J = M(x)[:, :3] + sum_c (M_c [x;1]) grad(w_c)^T
+__device__ __forceinline__ void blend_value_jac(const SkinDev& S, float3 x, float Mx[12], float J[9]) {
+  CellCoord c = skin_cell(S, x);
+#pragma unroll
+  for (int q = 0; q < 12; ++q) Mx[q] = 0.f;
+  float G[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) G[q] = 0.f;
+#pragma unroll
+  for (int corner = 0; corner < 8; ++corner) {
+    int v = corner_index(S, c.base, corner);
+    const int cx = corner & 1, cy = (corner >> 1) & 1, cz = (corner >> 2) & 1;
+    float wx = cx ? c.f[0] : 1.f - c.f[0];
+    float wy = cy ? c.f[1] : 1.f - c.f[1];
+    float wz = cz ? c.f[2] : 1.f - c.f[2];
+    float w = wx * wy * wz;
+    float gx = (cx ? 1.f : -1.f) * wy * wz * S.scale[0] * c.live[0];
+    float gy = (cy ? 1.f : -1.f) * wx * wz * S.scale[1] * c.live[1];
+    float gz = (cz ? 1.f : -1.f) * wx * wy * S.scale[2] * c.live[2];
+    const float4* p = S.M + 3 * v;
+    float4 r[3] = {__ldg(p), __ldg(p + 1), __ldg(p + 2)};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      Mx[4 * a + 0] = fmaf(w, r[a].x, Mx[4 * a + 0]);
+      Mx[4 * a + 1] = fmaf(w, r[a].y, Mx[4 * a + 1]);
+      Mx[4 * a + 2] = fmaf(w, r[a].z, Mx[4 * a + 2]);
+      Mx[4 * a + 3] = fmaf(w, r[a].w, Mx[4 * a + 3]);
+      float mc = fmaf(r[a].x, x.x, fmaf(r[a].y, x.y, fmaf(r[a].z, x.z, r[a].w)));
+      G[3 * a + 0] = fmaf(mc, gx, G[3 * a + 0]);
+      G[3 * a + 1] = fmaf(mc, gy, G[3 * a + 1]);
+      G[3 * a + 2] = fmaf(mc, gz, G[3 * a + 2]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) J[3 * a + b] = Mx[4 * a + b] + G[3 * a + b];
+}
+
+// 3x3 inverse by the adjugate; false if |det| < 1e-6 (treated as singular)
+__device__ __forceinline__ bool inv3(const float J[9], float H[9]) {
+  float c00 = J[4] * J[8] - J[5] * J[7];
+  float c01 = J[5] * J[6] - J[3] * J[8];
+  float c02 = J[3] * J[7] - J[4] * J[6];
+  float det = J[0] * c00 + J[1] * c01 + J[2] * c02;
+  if (!(fabsf(det) >= 1e-6f)) return false;
+  float id = 1.f / det;
+  H[0] = c00 * id;
+  H[1] = (J[2] * J[7] - J[1] * J[8]) * id;
+  H[2] = (J[1] * J[5] - J[2] * J[4]) * id;
+  H[3] = c01 * id;
+  H[4] = (J[0] * J[8] - J[2] * J[6]) * id;
+  H[5] = (J[2] * J[3] - J[0] * J[5]) * id;
+  H[6] = c02 * id;
+  H[7] = (J[1] * J[6] - J[0] * J[7]) * id;
+  H[8] = (J[0] * J[4] - J[1] * J[3]) * id;
+  return true;
+}
+
+__device__ __forceinline__ bool in_box(const SkinDev& S, float3 x) {
+  return x.x >= S.cmin[0] && x.x <= S.cmax[0] && x.y >= S.cmin[1] && x.y <= S.cmax[1] &&
+         x.z >= S.cmin[2] && x.z <= S.cmax[2];
+}
+
+// ---------------------------------------------------------------------------
+// Canonical field: hash encoding + MLP (fp32)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t vertex_index(const Level& lv, int i, int j, int k) {
+  if (lv.dense) {
+    uint32_t r1 = (uint32_t)lv.res + 1u;
+    return (uint32_t)i + r1 * ((uint32_t)j + r1 * (uint32_t)k);
+  }
+  uint32_t h = (uint32_t)i ^ ((uint32_t)j * 2654435761u) ^ ((uint32_t)k * 805459861u);
+  return h & (lv.size - 1u);  // hashed levels hold T = 2^log2_table entries
+}
+
+__device__ __forceinline__ void encode(const FieldDev& F, float3 x, float feat[kIn]) {
+  const float u[3] = {(x.x - F.cmin[0]) * F.inv_ext[0], (x.y - F.cmin[1]) * F.inv_ext[1],
+                      (x.z - F.cmin[2]) * F.inv_ext[2]};
+#pragma unroll
+  for (int l = 0; l < kMaxLevels; ++l) {
+    feat[2 * l] = 0.f;
+    feat[2 * l + 1] = 0.f;
+    if (l < F.L) {
+      const Level lv = F.lv[l];
+      int p0[3];
+      float f[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        float pos = u[a] * (float)lv.res;
+        int c = (int)floorf(pos);
+        c = min(max(c, 0), lv.res - 1);
+        p0[a] = c;
+        f[a] = pos - (float)c;
+      }
+      float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+      for (int corner = 0; corner < 8; ++corner) {
+        const int cx = corner & 1, cy = (corner >> 1) & 1, cz = (corner >> 2) & 1;
+        float w = (cx ? f[0] : 1.f - f[0]) * (cy ? f[1] : 1.f - f[1]) * (cz ? f[2] : 1.f - f[2]);
+        uint32_t e = lv.offset + vertex_index(lv, p0[0] + cx, p0[1] + cy, p0[2] + cz);
+        float2 t = __ldg(F.table + e);
+        a0 = fmaf(w, t.x, a0);
+        a1 = fmaf(w, t.y, a1);
+      }
+      feat[2 * l] = a0;
+      feat[2 * l + 1] = a1;
+    }
+  }
+}
+
+// [32] -> 64 -> ReLU -> 64 -> ReLU -> 4, weights broadcast from shared memory
+__device__ __forceinline__ void mlp_fp32(const float* __restrict__ sw, const float feat[kIn], float out[4]) {
+  float h1[kWidth];
+#pragma unroll
+  for (int j = 0; j < kWidth; ++j) {
+    float acc = sw[kOffB1 + j];
+    const float4* row = reinterpret_cast<const float4*>(sw + kOffW1 + j * kIn);
+#pragma unroll
+    for (int i = 0; i < kIn / 4; ++i) {
+      float4 w = row[i];
+      acc = fmaf(w.x, feat[4 * i], acc);
+      acc = fmaf(w.y, feat[4 * i + 1], acc);
+      acc = fmaf(w.z, feat[4 * i + 2], acc);
+      acc = fmaf(w.w, feat[4 * i + 3], acc);
+    }
+    h1[j] = fmaxf(acc, 0.f);
+  }
+  float o0 = sw[kOffB3], o1 = sw[kOffB3 + 1], o2 = sw[kOffB3 + 2], o3 = sw[kOffB3 + 3];
+#pragma unroll 4
+  for (int j = 0; j < kWidth; ++j) {
+    float acc = sw[kOffB2 + j];
+    const float4* row = reinterpret_cast<const float4*>(sw + kOffW2 + j * kWidth);
+#pragma unroll
+    for (int i = 0; i < kWidth / 4; ++i) {
+      float4 w = row[i];
+      acc = fmaf(w.x, h1[4 * i], acc);
+      acc = fmaf(w.y, h1[4 * i + 1], acc);
+      acc = fmaf(w.z, h1[4 * i + 2], acc);
+      acc = fmaf(w.w, h1[4 * i + 3], acc);
+    }
+    float h = fmaxf(acc, 0.f);
+    float4 w3 = reinterpret_cast<const float4*>(sw + kOffW3T)[j];
+    o0 = fmaf(w3.x, h, o0);
+    o1 = fmaf(w3.y, h, o1);
+    o2 = fmaf(w3.z, h, o2);
+    o3 = fmaf(w3.w, h, o3);
+  }
+  out[0] = o0; out[1] = o1; out[2] = o2; out[3] = o3;
+}
+
+// density = exp(clamp(o0, -15, 15)), colour = sigmoid(o1..3)
+__device__ __forceinline__ void activate(const float o[4], float& sigma, float3& rgb) {
+  sigma = expf(fminf(fmaxf(o[0], -15.f), 15.f));
+  rgb = make_float3(1.f / (1.f + expf(-o[1])), 1.f / (1.f + expf(-o[2])), 1.f / (1.f + expf(-o[3])));
+}
+
+__device__ __forceinline__ void field_fp32(const FieldDev& F, const float* sw, float3 x, float& sigma,
+                                           float3& rgb) {
+  float feat[kIn], o[4];
+  encode(F, x, feat);
+  mlp_fp32(sw, feat, o);
+  activate(o, sigma, rgb);
+}
+
+// Stage the packed MLP (W1 [64][n_in], b1, W2, b2, W3 [4][64], b3) into the
+// shared-memory layout above.
+__device__ __forceinline__ void stage_mlp(const float* __restrict__ g, int n_in, float* sw) {
+  const int nW1 = kWidth * n_in;
+  for (int t = threadIdx.x; t < kMlpSmemFloats; t += blockDim.x) {
+    float v = 0.f;
+    if (t < kOffB1) {
+      int j = t / kIn, i = t % kIn;
+      v = (i < n_in) ? g[j * n_in + i] : 0.f;
+    } else if (t < kOffW2) {
+      v = g[nW1 + (t - kOffB1)];
+    } else if (t < kOffB2) {
+      v = g[nW1 + kWidth + (t - kOffW2)];
+    } else if (t < kOffW3T) {
+      v = g[nW1 + kWidth + kWidth * kWidth + (t - kOffB2)];
+    } else if (t < kOffB3) {
+      int q = t - kOffW3T, j = q / 4, o = q % 4;  // W3^T[j][o] = W3[o][j]
+      v = g[nW1 + 2 * kWidth + kWidth * kWidth + o * kWidth + j];
+    } else {
+      v = g[nW1 + 2 * kWidth + kWidth * kWidth + 4 * kWidth + (t - kOffB3)];
+    }
+    sw[t] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Posed field f'(x') = f(x*): one sample per lane, all 32 lanes must call.
+// ---------------------------------------------------------------------------
+
+struct PosedOut {
+  float sigma;   // 0 when no valid root
+  float3 rgb;
+  float3 xstar;
+  int start;     // -1 when no valid root
+};
+
+// One Newton step x <- x - J(x)^-1 (LBS(x) - x') with the analytic Jacobian.
+__device__ __forceinline__ float3 polish_root(const SkinDev& S, float3 xs, float3 xn) {
+  float Mx[12], J[9], Hn[9];
+  blend_value_jac(S, xs, Mx, J);
+  float3 y = apply34(Mx, xs);
+  float3 rr = make_float3(y.x - xn.x, y.y - xn.y, y.z - xn.z);
+  if (inv3(J, Hn)) {
+    xs.x -= Hn[0] * rr.x + Hn[1] * rr.y + Hn[2] * rr.z;
+    xs.y -= Hn[3] * rr.x + Hn[4] * rr.y + Hn[5] * rr.z;
+    xs.z -= Hn[6] * rr.x + Hn[7] * rr.y + Hn[8] * rr.z;
+  }
+  return xs;
+}
+
+// keep the root with the highest density; equal densities keep the earlier start
+__device__ __forceinline__ void take_best(PosedOut& out, float sig, float3 rgb, float3 xs, int start) {
+  if (sig > out.sigma || (sig == out.sigma && out.start >= 0 && start < out.start) || out.start < 0) {
+    out.sigma = sig;
+    out.rgb = rgb;
+    out.xstar = xs;
+    out.start = start;
+  }
+}
+
+// roots: this CTA's float4 [kMaxRoots][blockDim.x] scratch (x, y, z, start bits).
+// The first kMaxRoots distinct roots of a sample are evaluated together by the
+// warp after the search; any further distinct root (rare) is evaluated on the
+// spot so that no root is ever dropped.
+__device__ __forceinline__ PosedOut posed_field_warp(const SkinDev& S, const FieldDev& F, const SolveCfg& cfg,
+                                                     const float* __restrict__ sNinv, const float* sw,
+                                                     float4* roots, bool active, float3 xn,
+                                                     SampleStats& st) {
+  const int tid = threadIdx.x, stride = blockDim.x;
+  PosedOut out;
+  out.sigma = 0.f;
+  out.rgb = make_float3(0.f, 0.f, 0.f);
+  out.xstar = out.rgb;
+  out.start = -1;
+  // ---- flattened multi-start Broyden: every loop step evaluates M at one point per lane
+  int k = 0, it = 0, nroots = 0;
+  int phase = active ? 0 : 2;  // 0 = start k, 1 = iterate, 2 = done
+  float3 x = make_float3(0.f, 0.f, 0.f), r = x, dx = x;
+  float H[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) H[q] = 0.f;
+  while (__any_sync(kFull, phase != 2)) {
+    float3 q = x;
+    if (phase == 0) {
+      const float* A = sNinv + 12 * k;
+      q = make_float3(A[0] * xn.x + A[1] * xn.y + A[2] * xn.z + A[3],
+                      A[4] * xn.x + A[5] * xn.y + A[6] * xn.z + A[7],
+                      A[8] * xn.x + A[9] * xn.y + A[10] * xn.z + A[11]);
+    } else if (phase == 1) {
+      q = make_float3(x.x + dx.x, x.y + dx.y, x.z + dx.z);
+    }
+    float Mx[12];
+    if (phase != 2) blend_value(S, q, Mx);
+    bool finish = false, conv = false;
+    if (phase == 0) {
+      st.starts++;
+      float3 y = apply34(Mx, q);
+      x = q;
+      r = make_float3(y.x - xn.x, y.y - xn.y, y.z - xn.z);
+      // initial inverse Jacobian: LBS with the weights frozen at x0, (sum_i w_i R_i)^-1
+      const float J0[9] = {Mx[0], Mx[1], Mx[2], Mx[4], Mx[5], Mx[6], Mx[8], Mx[9], Mx[10]};
+      it = 0;
+      if (!inv3(J0, H)) finish = true;
+    } else if (phase == 1) {
+      float3 y = apply34(Mx, q);
+      float3 rn = make_float3(y.x - xn.x, y.y - xn.y, y.z - xn.z);
+      float3 dr = make_float3(rn.x - r.x, rn.y - r.y, rn.z - r.z);
+      x = q;
+      r = rn;
+      ++it;
+      st.iters++;
+      // good Broyden: H += (dx - H dr)(dx^T H) / (dx^T H dr)
+      float u0 = H[0] * dr.x + H[1] * dr.y + H[2] * dr.z;
+      float u1 = H[3] * dr.x + H[4] * dr.y + H[5] * dr.z;
+      float u2 = H[6] * dr.x + H[7] * dr.y + H[8] * dr.z;
+      float den = dx.x * u0 + dx.y * u1 + dx.z * u2;
+      if (fabsf(den) > 1e-12f) {
+        float a0 = (dx.x - u0) / den, a1 = (dx.y - u1) / den, a2 = (dx.z - u2) / den;
+        float b0 = dx.x * H[0] + dx.y * H[3] + dx.z * H[6];
+        float b1 = dx.x * H[1] + dx.y * H[4] + dx.z * H[7];
+        float b2 = dx.x * H[2] + dx.y * H[5] + dx.z * H[8];
+        H[0] += a0 * b0; H[1] += a0 * b1; H[2] += a0 * b2;
+        H[3] += a1 * b0; H[4] += a1 * b1; H[5] += a1 * b2;
+        H[6] += a2 * b0; H[7] += a2 * b1; H[8] += a2 * b2;
+      }
+    }
+    if (phase != 2 && !finish) {
+      float rr = r.x * r.x + r.y * r.y + r.z * r.z;
+      if (rr < cfg.tol2) {
+        conv = true;
+        finish = true;
+      } else if (it >= cfg.max_iter) {
+        finish = true;
+      } else {
+        dx = make_float3(-(H[0] * r.x + H[1] * r.y + H[2] * r.z), -(H[3] * r.x + H[4] * r.y + H[5] * r.z),
+                         -(H[6] * r.x + H[7] * r.y + H[8] * r.z));
+        phase = 1;
+      }
+    }
+    if (finish) {
+      if (conv && in_box(S, x)) {
+        st.converged++;
+        bool dup = false;
+        for (int j = 0; j < min(nroots, kMaxRoots); ++j) {
+          float4 o = roots[j * stride + tid];
+          float ddx = x.x - o.x, ddy = x.y - o.y, ddz = x.z - o.z;
+          if (ddx * ddx + ddy * ddy + ddz * ddz < 1e-8f) { dup = true; break; }
+        }
+        if (!dup) {
+          st.roots++;
+          if (nroots < kMaxRoots) {
+            roots[nroots * stride + tid] = make_float4(x.x, x.y, x.z, __int_as_float(k));
+          } else {
+            float3 xs = polish_root(S, x, xn);
+            float sig;
+            float3 rgb;
+            field_fp32(F, sw, xs, sig, rgb);
+            take_best(out, sig, rgb, xs, k);
+          }
+          nroots++;
+        }
+      }
+      ++k;
+      phase = (k < cfg.nb) ? 0 : 2;
+    }
+  }
+  // ---- one Newton polish per stored root, field evaluation, max-density root
+  int nr = min(nroots, kMaxRoots);
+  int nmax = __reduce_max_sync(kFull, nr);
+  for (int j = 0; j < nmax; ++j) {
+    bool has = j < nr;
+    float3 xs = make_float3(S.cmin[0], S.cmin[1], S.cmin[2]);
+    int start = -1;
+    if (has) {
+      float4 o = roots[j * stride + tid];
+      start = __float_as_int(o.w);
+      xs = polish_root(S, make_float3(o.x, o.y, o.z), xn);
+    }
+    float sig;
+    float3 rgb;
+    field_fp32(F, sw, xs, sig, rgb);
+    if (has) take_best(out, sig, rgb, xs, start);
+  }
+  return out;
+}
+
+}  // namespace ia

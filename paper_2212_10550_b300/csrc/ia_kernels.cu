@@ -1,0 +1,544 @@
+// Kernels of the articulated radiance-field render path (sm_103a).
+//
+//   pose_chain_kernel     fp64 kinematic chain -> fp32 normalised-space transforms
+//   blend_kernel          per-pose blended transform grid M(v) = sum_i W(v,i) N_i
+//   occ_density_kernel    posed-field density at every occupancy cell centre
+//   occ_bits_kernel       threshold + dilation + packing (+ union into the training grid)
+//   query_*_kernel        posed / canonical field at caller points
+//   render_kernel         persistent fused march -> correspondence search -> hash
+//                         encoding -> MLP -> front-to-back compositing
+#include "ia_internal.h"
+
+namespace ia {
+
+// ---------------------------------------------------------------------------
+// Pose chain (fp64, explicitly rounded so the fp32 results are reproducible)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double DM(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double DA(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double DS(double a, double b) { return __dsub_rn(a, b); }
+
+__device__ void mat34_mul_d(const double* a, const double* b, double* c) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double s = DA(DA(DM(a[i * 4 + 0], b[0 * 4 + j]), DM(a[i * 4 + 1], b[1 * 4 + j])), DM(a[i * 4 + 2], b[2 * 4 + j]));
+      if (j == 3) s = DA(s, a[i * 4 + 3]);
+      c[i * 4 + j] = s;
+    }
+}
+
+__device__ void rigid_inv_d(const double* a, double* c) {
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) c[i * 4 + j] = a[j * 4 + i];
+    c[i * 4 + 3] = -DA(DA(DM(a[0 * 4 + i], a[3]), DM(a[1 * 4 + i], a[7])), DM(a[2 * 4 + i], a[11]));
+  }
+}
+
+__global__ void pose_chain_kernel(int P, int nb, const int* __restrict__ parent, const double* __restrict__ rest,
+                                  const double* __restrict__ theta, const double* __restrict__ trans,
+                                  float* __restrict__ N, float* __restrict__ Ninv, float* __restrict__ B0inv) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  double G[kMaxBones][12];
+  double B0i[12];
+  for (int k = 0; k < nb; ++k) {
+    const double* th = theta + ((size_t)p * nb + k) * 3;
+    double R[9];
+    double a = __dsqrt_rn(DA(DA(DM(th[0], th[0]), DM(th[1], th[1])), DM(th[2], th[2])));
+    if (a == 0.0) {
+      for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0) ? 1.0 : 0.0;
+    } else {
+      double k0 = __ddiv_rn(th[0], a), k1 = __ddiv_rn(th[1], a), k2 = __ddiv_rn(th[2], a);
+      double c = cos(a), s = sin(a), C = DS(1.0, c);
+      R[0] = DA(c, DM(DM(C, k0), k0));
+      R[1] = DS(DM(DM(C, k0), k1), DM(s, k2));
+      R[2] = DA(DM(DM(C, k0), k2), DM(s, k1));
+      R[3] = DA(DM(DM(C, k1), k0), DM(s, k2));
+      R[4] = DA(c, DM(DM(C, k1), k1));
+      R[5] = DS(DM(DM(C, k1), k2), DM(s, k0));
+      R[6] = DS(DM(DM(C, k2), k0), DM(s, k1));
+      R[7] = DA(DM(DM(C, k2), k1), DM(s, k0));
+      R[8] = DA(c, DM(DM(C, k2), k2));
+    }
+    const int par = parent[k];
+    double L[12];
+    for (int i = 0; i < 3; ++i) {
+      for (int j = 0; j < 3; ++j) L[i * 4 + j] = R[i * 3 + j];
+      L[i * 4 + 3] = (par < 0) ? rest[3 * k + i] : DS(rest[3 * k + i], rest[3 * par + i]);
+    }
+    if (par < 0) {
+      for (int q = 0; q < 12; ++q) G[k][q] = L[q];
+    } else {
+      mat34_mul_d(G[par], L, G[k]);
+    }
+    // rest-relative bone transform B_k = G_k [I | -j_k] + root translation
+    double B[12];
+    for (int i = 0; i < 3; ++i) {
+      for (int j = 0; j < 3; ++j) B[i * 4 + j] = G[k][i * 4 + j];
+      double Rj = DA(DA(DM(G[k][i * 4 + 0], rest[3 * k + 0]), DM(G[k][i * 4 + 1], rest[3 * k + 1])),
+                     DM(G[k][i * 4 + 2], rest[3 * k + 2]));
+      B[i * 4 + 3] = DA(DS(G[k][i * 4 + 3], Rj), trans[(size_t)p * 3 + i]);
+    }
+    if (k == 0) rigid_inv_d(B, B0i);  // the root is bone 0 (parents precede children)
+    double Nk[12], Ni[12];
+    mat34_mul_d(B0i, B, Nk);
+    rigid_inv_d(Nk, Ni);
+    float* No = N + ((size_t)p * nb + k) * 12;
+    float* Nio = Ninv + ((size_t)p * nb + k) * 12;
+    for (int q = 0; q < 12; ++q) {
+      No[q] = (float)Nk[q];
+      Nio[q] = (float)Ni[q];
+    }
+  }
+  for (int q = 0; q < 12; ++q) B0inv[(size_t)p * 12 + q] = (float)B0i[q];
+}
+
+cudaError_t launch_pose_chain(int P, int nb, const int* parent, const double* rest, const double* theta,
+                              const double* trans, float* N, float* Ninv, float* B0inv, cudaStream_t s) {
+  pose_chain_kernel<<<(P + 63) / 64, 64, 0, s>>>(P, nb, parent, rest, theta, trans, N, Ninv, B0inv);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Blended transform grid M(v) = sum_i W(v, i) N_i, one pose per blockIdx.y
+// ---------------------------------------------------------------------------
+
+__global__ void blend_kernel(int V, int nb, const float* __restrict__ W, const float* __restrict__ N,
+                             float4* __restrict__ M) {
+  __shared__ float sN[kMaxBones * 12];
+  const int p = blockIdx.y;
+  for (int t = threadIdx.x; t < nb * 12; t += blockDim.x) sN[t] = N[(size_t)p * nb * 12 + t];
+  __syncthreads();
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
+    float acc[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) acc[q] = 0.f;
+    const float* w = W + (size_t)v * nb;
+    for (int i = 0; i < nb; ++i) {
+      float wi = __ldg(w + i);
+#pragma unroll
+      for (int q = 0; q < 12; ++q) acc[q] = fmaf(wi, sN[i * 12 + q], acc[q]);
+    }
+    float4* out = M + ((size_t)p * V + v) * 3;
+    out[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    out[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+    out[2] = make_float4(acc[8], acc[9], acc[10], acc[11]);
+  }
+}
+
+cudaError_t launch_blend(int P, int V, int nb, const float* W, const float* N, float4* M, cudaStream_t s) {
+  dim3 grid((V + 255) / 256, P);
+  if (grid.x > 4096) grid.x = 4096;
+  blend_kernel<<<grid, 256, 0, s>>>(V, nb, W, N, M);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory layout of kernels that evaluate the posed field
+// ---------------------------------------------------------------------------
+
+constexpr int kMlpPad = (kMlpSmemFloats + 3) / 4 * 4;
+
+size_t posed_smem_bytes(int threads) {
+  return sizeof(float) * (kMlpPad + kMaxBones * 12) + sizeof(float4) * kMaxRoots * threads;
+}
+
+struct PosedSmem {
+  float* sw;
+  float* sNinv;
+  float4* roots;
+};
+
+__device__ __forceinline__ PosedSmem stage_posed(const PosedArgs& a, float4* smem4) {
+  PosedSmem p;
+  p.sw = reinterpret_cast<float*>(smem4);
+  p.sNinv = p.sw + kMlpPad;
+  p.roots = reinterpret_cast<float4*>(p.sNinv + kMaxBones * 12);
+  stage_mlp(a.mlp, a.n_in, p.sw);
+  for (int t = threadIdx.x; t < a.cfg.nb * 12; t += blockDim.x) p.sNinv[t] = a.Ninv[t];
+  __syncthreads();
+  return p;
+}
+
+__device__ __forceinline__ void flush_stats(unsigned long long* stats, int idx, long long v) {
+  // warp-reduce then one atomic per warp
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+  if ((threadIdx.x & 31) == 0 && v != 0) atomicAdd(stats + idx, (unsigned long long)v);
+}
+
+// ---------------------------------------------------------------------------
+// Occupancy grid (Sec. 3.3, inference mode)
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) occ_density_kernel(const PosedArgs a, const BoxDev box,
+                                                          float* __restrict__ sigma,
+                                                          unsigned long long* __restrict__ stats) {
+  extern __shared__ float4 smem4[];
+  PosedSmem sm = stage_posed(a, smem4);
+  const int n = box.R * box.R * box.R;
+  SampleStats st;
+  // grid-stride over whole warps so every lane takes part in the warp-level search
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int cell = base + threadIdx.x;
+    const bool active = cell < n;
+    float3 xn = active ? cell_center(box, cell) : make_float3(0.f, 0.f, 0.f);
+    PosedOut o = posed_field_warp(a.S, a.F, a.cfg, sm.sNinv, sm.sw, sm.roots, active, xn, st);
+    if (active) sigma[cell] = o.start >= 0 ? o.sigma : 0.f;
+  }
+  if (stats) {
+    flush_stats(stats, ST_STARTS, st.starts);
+    flush_stats(stats, ST_ITERS, st.iters);
+    flush_stats(stats, ST_CONV, st.converged);
+    flush_stats(stats, ST_ROOTS, st.roots);
+  }
+}
+
+cudaError_t launch_occ_density(const PosedArgs& a, const BoxDev& box, float* sigma, unsigned long long* stats,
+                               cudaStream_t s) {
+  const int n = box.R * box.R * box.R;
+  int blocks = (n + 255) / 256;
+  size_t smem = posed_smem_bytes(256);
+  cudaError_t e = cudaFuncSetAttribute(occ_density_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  occ_density_kernel<<<blocks, 256, smem, s>>>(a, box, sigma, stats);
+  return cudaGetLastError();
+}
+
+// occupied = sigma > tau, dilated by a (2 dilate + 1)^3 cube clipped to the grid;
+// cell b = x + R (y + R z) is bit b % 32 of word b / 32
+__global__ void occ_bits_kernel(const float* __restrict__ sigma, int R, int dilate, float tau,
+                                uint32_t* __restrict__ bits, uint32_t* __restrict__ union_bits) {
+  const int n = R * R * R;
+  const int words = (n + 31) / 32;
+  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < words; w += gridDim.x * blockDim.x) {
+    uint32_t word = 0;
+    for (int b = 0; b < 32; ++b) {
+      const int cell = w * 32 + b;
+      if (cell >= n) break;
+      const int x = cell % R, y = (cell / R) % R, z = cell / (R * R);
+      bool on = false;
+      for (int dz = -dilate; dz <= dilate && !on; ++dz) {
+        const int zz = z + dz;
+        if (zz < 0 || zz >= R) continue;
+        for (int dy = -dilate; dy <= dilate && !on; ++dy) {
+          const int yy = y + dy;
+          if (yy < 0 || yy >= R) continue;
+          for (int dx = -dilate; dx <= dilate && !on; ++dx) {
+            const int xx = x + dx;
+            if (xx < 0 || xx >= R) continue;
+            if (sigma[xx + R * (yy + R * zz)] > tau) on = true;
+          }
+        }
+      }
+      if (on) word |= 1u << b;
+    }
+    if (bits) bits[w] = word;
+    if (union_bits) union_bits[w] |= word;
+  }
+}
+
+cudaError_t launch_occ_bits(const float* sigma, int R, int dilate, float tau, uint32_t* bits, uint32_t* union_bits,
+                            cudaStream_t s) {
+  const int words = (R * R * R + 31) / 32;
+  occ_bits_kernel<<<(words + 127) / 128, 128, 0, s>>>(sigma, R, dilate, tau, bits, union_bits);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Queries
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) query_posed_kernel(const PosedArgs a, int n, const float* __restrict__ x,
+                                                          float* sigma, float* rgb, float* xc, int* start) {
+  extern __shared__ float4 smem4[];
+  PosedSmem sm = stage_posed(a, smem4);
+  SampleStats st;
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int i = base + threadIdx.x;
+    const bool active = i < n;
+    float3 xn = active ? make_float3(x[3 * i], x[3 * i + 1], x[3 * i + 2]) : make_float3(0.f, 0.f, 0.f);
+    PosedOut o = posed_field_warp(a.S, a.F, a.cfg, sm.sNinv, sm.sw, sm.roots, active, xn, st);
+    if (active) {
+      if (sigma) sigma[i] = o.start >= 0 ? o.sigma : 0.f;
+      if (rgb) { rgb[3 * i] = o.rgb.x; rgb[3 * i + 1] = o.rgb.y; rgb[3 * i + 2] = o.rgb.z; }
+      if (xc) { xc[3 * i] = o.xstar.x; xc[3 * i + 1] = o.xstar.y; xc[3 * i + 2] = o.xstar.z; }
+      if (start) start[i] = o.start;
+    }
+  }
+}
+
+cudaError_t launch_query_posed(const PosedArgs& a, int n, const float* x, float* sigma, float* rgb, float* xc,
+                               int* start, cudaStream_t s) {
+  size_t smem = posed_smem_bytes(256);
+  cudaError_t e = cudaFuncSetAttribute(query_posed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  query_posed_kernel<<<(n + 255) / 256, 256, smem, s>>>(a, n, x, sigma, rgb, xc, start);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) query_canonical_kernel(const FieldDev F, const float* __restrict__ mlp,
+                                                              int n_in, int n, const float* __restrict__ x,
+                                                              float* sigma, float* rgb) {
+  __shared__ __align__(16) float sw[kMlpPad];
+  stage_mlp(mlp, n_in, sw);
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float s;
+  float3 c;
+  field_fp32(F, sw, make_float3(x[3 * i], x[3 * i + 1], x[3 * i + 2]), s, c);
+  sigma[i] = s;
+  rgb[3 * i] = c.x;
+  rgb[3 * i + 1] = c.y;
+  rgb[3 * i + 2] = c.z;
+}
+
+cudaError_t launch_query_canonical(const FieldDev& F, const float* mlp, int n_in, int n, const float* x, float* sigma,
+                                   float* rgb, cudaStream_t s) {
+  query_canonical_kernel<<<(n + 255) / 256, 256, 0, s>>>(F, mlp, n_in, n, x, sigma, rgb);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Persistent fused render kernel
+//
+// Each CTA keeps a pool of 256 rays, one per thread.  A round:
+//  1. march: every ray advances its slot cursor until it has found up to K
+//     slots in occupied cells (empty-space skipping); exhausted rays write
+//     their pixel and take the next ray from a global counter (warp-aggregated);
+//  2. a block scan packs the found (ray, slot) samples into shared memory;
+//  3. every warp evaluates 32 samples at a time: bone-wise Broyden search,
+//     polish, hash encoding, MLP, max-density root;
+//  4. every ray composites its own samples front to back and stops once its
+//     transmittance is below the threshold.
+// ---------------------------------------------------------------------------
+
+size_t render_smem_bytes(int K) {
+  return posed_smem_bytes(kRenderThreads) + sizeof(float4) * (2 * kRenderThreads + K * kRenderThreads) +
+         sizeof(int) * (2 * K * kRenderThreads + 32);
+}
+
+__device__ __forceinline__ void tile_pixel(int id, int tiles_x, int W, int H, int& u, int& v, bool& valid) {
+  const int tile = id / (kTile * kTile), i = id % (kTile * kTile);
+  u = (tile % tiles_x) * kTile + i % kTile;
+  v = (tile / tiles_x) * kTile + i / kTile;
+  valid = u < W && v < H;
+}
+
+template <int K>
+__global__ void __launch_bounds__(kRenderThreads) render_kernel(const RenderArgs a) {
+  extern __shared__ float4 smem4[];
+  PosedSmem sm = stage_posed(a.P, smem4);
+  float4* ray_o = sm.roots + kMaxRoots * kRenderThreads;  // (o.xyz, delta)
+  float4* ray_d = ray_o + kRenderThreads;                 // (d.xyz, t_near)
+  float4* s_res = ray_d + kRenderThreads;                 // (sigma, r, g, b) per sample
+  int* s_ray = reinterpret_cast<int*>(s_res + K * kRenderThreads);
+  int* s_slot = s_ray + K * kRenderThreads;
+  int* s_warp = s_slot + K * kRenderThreads;
+  __shared__ float sB0inv[12];
+  if (threadIdx.x < 12) sB0inv[threadIdx.x] = a.B0inv[threadIdx.x];
+  __syncthreads();
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int W = a.cam.width, H = a.cam.height;
+  const float log_stop = a.early_T > 0.f ? -logf(a.early_T) : __int_as_float(0x7f800000);
+
+  // per-ray state of this thread's pool slot
+  bool has_ray = false, queue_empty = false;
+  int pix = 0, cursor = 0;
+  float depth = 0.f;                      // optical depth sum sigma_i delta
+  float cr = 0.f, cg = 0.f, cb = 0.f;
+  long long n_rays = 0, n_hit = 0, n_marched = 0, n_occ = 0, n_early = 0;
+  SampleStats st;
+
+  while (true) {
+    // ---- 1. march
+    int nfound = 0;
+    int slots[K];
+    while (true) {
+      if (has_ray) {
+        float4 ro = ray_o[tid], rd = ray_d[tid];
+        const float o[3] = {ro.x, ro.y, ro.z}, d[3] = {rd.x, rd.y, rd.z};
+        while (cursor < a.n_slots && nfound < K) {
+          float3 x = slot_position(o, d, rd.w, ro.w, cursor);
+          int cell = cell_of(a.box, x);
+          ++n_marched;
+          if ((__ldg(a.occ + (cell >> 5)) >> (cell & 31)) & 1u) slots[nfound++] = cursor;
+          ++cursor;
+        }
+        if (nfound == 0) {  // exhausted: write the pixel
+          a.rgb[3 * pix] = cr;
+          a.rgb[3 * pix + 1] = cg;
+          a.rgb[3 * pix + 2] = cb;
+          a.alpha[pix] = -expm1f(-depth);
+          has_ray = false;
+        }
+      }
+      const bool need = !has_ray && !queue_empty;
+      const unsigned m = __ballot_sync(kFull, need);
+      if (m == 0) break;
+      unsigned base = 0;
+      const int leader = __ffs(m) - 1;
+      if (lane == leader) base = atomicAdd(a.counter, (unsigned)__popc(m));
+      base = __shfl_sync(kFull, base, leader);
+      if (need) {
+        const int id = (int)(base + __popc(m & ((1u << lane) - 1u)));
+        if (id >= a.n_ray_ids) {
+          queue_empty = true;
+        } else {
+          int u, v;
+          bool valid;
+          tile_pixel(id, a.tiles_x, W, H, u, v, valid);
+          if (valid) {
+            ++n_rays;
+            float o[3], d[3], tn, tf;
+            pix = v * W + u;
+            cr = cg = cb = 0.f;
+            depth = 0.f;
+            cursor = 0;
+            if (make_ray(a.cam, sB0inv, a.box, u, v, o, d, tn, tf)) {
+              ++n_hit;
+              ray_o[tid] = make_float4(o[0], o[1], o[2], slot_delta(tn, tf, a.n_slots));
+              ray_d[tid] = make_float4(d[0], d[1], d[2], tn);
+              has_ray = true;
+            } else {
+              a.rgb[3 * pix] = 0.f;
+              a.rgb[3 * pix + 1] = 0.f;
+              a.rgb[3 * pix + 2] = 0.f;
+              a.alpha[pix] = 0.f;
+            }
+          }
+        }
+      }
+    }
+    // ---- 2. pack samples (block exclusive scan of nfound)
+    int incl = nfound;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (tid < 32) {
+      int v = tid < kRenderThreads / 32 ? s_warp[tid] : 0;
+      int inc = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(kFull, inc, o);
+        if (tid >= o) inc += t;
+      }
+      if (tid < kRenderThreads / 32) s_warp[tid] = inc - v;
+      if (tid == kRenderThreads / 32 - 1) s_warp[kRenderThreads / 32] = inc;
+    }
+    __syncthreads();
+    const int total = s_warp[kRenderThreads / 32];
+    const int offset = s_warp[warp] + incl - nfound;
+    if (total == 0) break;  // no ray in this CTA has work and the queue is drained
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      if (j < nfound) {
+        s_ray[offset + j] = tid;
+        s_slot[offset + j] = slots[j];
+      }
+    n_occ += nfound;
+    __syncthreads();
+    // ---- 3. evaluate samples, 32 per warp step
+    for (int base = warp * 32; base < total; base += kRenderThreads) {
+      const int sidx = base + lane;
+      const bool active = sidx < total;
+      float3 xn = make_float3(0.f, 0.f, 0.f);
+      if (active) {
+        const int owner = s_ray[sidx];
+        float4 ro = ray_o[owner], rd = ray_d[owner];
+        const float o[3] = {ro.x, ro.y, ro.z}, d[3] = {rd.x, rd.y, rd.z};
+        xn = slot_position(o, d, rd.w, ro.w, s_slot[sidx]);
+      }
+      PosedOut r = posed_field_warp(a.P.S, a.P.F, a.P.cfg, sm.sNinv, sm.sw, sm.roots, active, xn, st);
+      if (active) s_res[sidx] = make_float4(r.start >= 0 ? r.sigma : 0.f, r.rgb.x, r.rgb.y, r.rgb.z);
+    }
+    __syncthreads();
+    // ---- 4. composite this ray's samples, alpha_i = 1 - exp(-sigma_i delta)
+    if (nfound > 0) {
+      const float dt = ray_o[tid].w;
+      for (int j = 0; j < nfound; ++j) {
+        float4 sres = s_res[offset + j];
+        if (sres.x > 0.f) {
+          const float sd = sres.x * dt;
+          const float w = expf(-depth) * -expm1f(-sd);  // T_i alpha_i
+          cr = fmaf(w, sres.y, cr);
+          cg = fmaf(w, sres.z, cg);
+          cb = fmaf(w, sres.w, cb);
+          depth += sd;
+        }
+        if (depth > log_stop) {  // transmittance below the threshold: stop the ray
+          ++n_early;
+          cursor = a.n_slots;
+          break;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (a.stats) {
+    flush_stats(a.stats, ST_RAYS, n_rays);
+    flush_stats(a.stats, ST_HIT, n_hit);
+    flush_stats(a.stats, ST_MARCHED, n_marched);
+    flush_stats(a.stats, ST_OCC, n_occ);
+    flush_stats(a.stats, ST_STARTS, st.starts);
+    flush_stats(a.stats, ST_ITERS, st.iters);
+    flush_stats(a.stats, ST_CONV, st.converged);
+    flush_stats(a.stats, ST_ROOTS, st.roots);
+    flush_stats(a.stats, ST_EARLY, n_early);
+  }
+}
+
+template <int K>
+static cudaError_t launch_render_k(const RenderArgs& a, int num_sms, cudaStream_t s) {
+  size_t smem = render_smem_bytes(K);
+  cudaError_t e = cudaFuncSetAttribute(render_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel<K>, kRenderThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  int want = (a.n_ray_ids + kRenderThreads - 1) / kRenderThreads;
+  int grid = num_sms * per_sm;
+  if (grid > want) grid = want;
+  if (grid < 1) grid = 1;
+  render_kernel<K><<<grid, kRenderThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_render(const RenderArgs& a, int num_sms, cudaStream_t s) {
+  // with early termination, few samples per ray per round bound the work done
+  // past the stopping sample; without it, larger rounds amortise the scans
+  if (a.early_T > 0.f) return launch_render_k<2>(a, num_sms, s);
+  return launch_render_k<8>(a, num_sms, s);
+}
+
+// One thread per pixel: the slots the render kernel's march would keep.
+__global__ void march_mask_kernel(const RenderArgs a, uint32_t* __restrict__ mask) {
+  const int W = a.cam.width, H = a.cam.height;
+  const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= W * H) return;
+  const int words = (a.n_slots + 31) / 32;
+  uint32_t* m = mask + (size_t)pix * words;
+  for (int w = 0; w < words; ++w) m[w] = 0u;
+  float o[3], d[3], tn, tf;
+  if (!make_ray(a.cam, a.B0inv, a.box, pix % W, pix / W, o, d, tn, tf)) return;
+  const float dt = slot_delta(tn, tf, a.n_slots);
+  for (int i = 0; i < a.n_slots; ++i) {
+    const int cell = cell_of(a.box, slot_position(o, d, tn, dt, i));
+    if ((__ldg(a.occ + (cell >> 5)) >> (cell & 31)) & 1u) m[i >> 5] |= 1u << (i & 31);
+  }
+}
+
+cudaError_t launch_march_mask(const RenderArgs& a, uint32_t* mask, cudaStream_t s) {
+  const int n = a.cam.width * a.cam.height;
+  march_mask_kernel<<<(n + 127) / 128, 128, 0, s>>>(a, mask);
+  return cudaGetLastError();
+}
+
+}  // namespace ia

@@ -1,0 +1,342 @@
+"""GPU parity: the CUDA path through the C ABI against the fp64 oracle.
+
+Bit-exact: bone transforms as stored (fp32 casts of the fp64 chain), occupancy
+bits from a shared density array, the per-ray set of evaluated slots.
+Within tolerance (gpu_helpers): canonical field, posed field, occupancy
+densities, rendered colour and opacity.  Rays or samples the oracle flags as
+marginal (an fp decision within rounding of its threshold) are excluded from
+the strict comparison and counted.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic as S
+from gpu_helpers import (ATOL_RGB, ATOL_XSTAR, RTOL_RGB, RTOL_SIGMA, bits_to_bool, camera, close,
+                         err_report, make_ctx, points_near_body)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ia():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2212_10550_b300 as ia
+    ia.lib()
+    return ia
+
+
+@pytest.fixture(scope="module", params=["tiny", "full"])
+def scene(request):
+    sc = S.make_scene(request.param, 0)
+    table, mlp = S.make_field(sc, 0)
+    return sc, table, mlp
+
+
+def _pose_ctx(ia, sc, table, mlp, seeds, early_T=0.0):
+    ctx = make_ctx(ia, torch, sc, table, mlp, early_T=early_T)
+    poses = [S.make_pose(sc, s) for s in seeds]
+    ia.ia_set_pose(ctx, np.stack([p[0] for p in poses]), np.stack([p[1] for p in poses]))
+    return ctx, poses
+
+
+def test_transforms_bit_exact(ia, scene):
+    sc, table, mlp = scene
+    seeds = [0, 1, 2, 3, 4]
+    ctx, poses = _pose_ctx(ia, sc, table, mlp, seeds)
+    om = O.OracleModel(sc, table, mlp)
+    nb = sc.n_bones
+    for i, (th, tr) in enumerate(poses):
+        N = np.zeros((nb, 12), np.float32)
+        Ni = np.zeros((nb, 12), np.float32)
+        B0 = np.zeros(12, np.float32)
+        ia.ia_get_transforms(ctx, i, N, Ni, B0)
+        T = om.transforms(om.pose(th, tr))
+        np.testing.assert_array_equal(N, T["N"].reshape(nb, 12).astype(np.float32))
+        np.testing.assert_array_equal(Ni, T["Ninv"].reshape(nb, 12).astype(np.float32))
+        np.testing.assert_array_equal(B0, T["B0inv"].reshape(12))
+    ia.ia_destroy(ctx)
+
+
+def test_canonical_field(ia, scene):
+    sc, table, mlp = scene
+    ctx = make_ctx(ia, torch, sc, table, mlp)
+    om = O.OracleModel(sc, table, mlp)
+    x = S.random_points(sc, 2048, seed=1, box="canon")
+    # and points near the body, where the field varies
+    rng = np.random.default_rng(2)
+    s = rng.integers(len(sc.seg_a), size=2048)
+    t = rng.uniform(size=(2048, 1))
+    near = (sc.seg_a[s] + t * (sc.seg_b[s] - sc.seg_a[s]) + rng.normal(0, 0.05, (2048, 3)))
+    near = np.clip(near, sc.canon_min, sc.canon_max).astype(np.float32)
+    x = np.concatenate([x, near])
+    xd = torch.from_numpy(x).cuda()
+    sig = torch.zeros(len(x), device="cuda")
+    rgb = torch.zeros(len(x), 3, device="cuda")
+    ia.ia_query_canonical(ctx, xd, sig, rgb)
+    torch.cuda.synchronize()
+    ref = [om.field(p) for p in x.astype(np.float64)]
+    rs = np.array([r[0] for r in ref])
+    rc = np.array([r[1] for r in ref])
+    err_report("canonical sigma", sig.cpu().numpy(), rs)
+    err_report("canonical rgb", rgb.cpu().numpy(), rc)
+    assert close(sig.cpu().numpy(), rs, 1e-5, 1e-9).all()
+    assert close(rgb.cpu().numpy(), rc, RTOL_RGB, ATOL_RGB).all()
+    ia.ia_destroy(ctx)
+
+
+def test_posed_field(ia, scene):
+    sc, table, mlp = scene
+    ctx, poses = _pose_ctx(ia, sc, table, mlp, [3])
+    om = O.OracleModel(sc, table, mlp)
+    p = om.pose(*poses[0])
+    n = 1500 if sc.name == "full" else 3000
+    pts = np.concatenate([points_near_body(sc, om, p, n, 5), S.random_points(sc, n // 3, seed=6)])
+    xd = torch.from_numpy(pts).cuda()
+    sig = torch.zeros(len(pts), device="cuda")
+    rgb = torch.zeros(len(pts), 3, device="cuda")
+    xc = torch.zeros(len(pts), 3, device="cuda")
+    st = torch.zeros(len(pts), dtype=torch.int32, device="cuda")
+    ia.ia_query_posed(ctx, 0, xd, sig, rgb, xc, st)
+    torch.cuda.synchronize()
+    ref = om.posed_field_many(p, pts)
+    ok = ref["flags"] == 0
+    print(f"posed field: {len(pts)} points, {np.sum(~ok)} flagged marginal, "
+          f"{np.sum(ref['start'] >= 0)} with a root, {np.sum(ref['n_unique'] > 1)} with several")
+    g_start = st.cpu().numpy()
+    assert np.sum(~ok) <= 0.01 * len(pts)
+    np.testing.assert_array_equal(g_start[ok], ref["start"][ok])
+    has = ok & (ref["start"] >= 0)
+    g_sig, g_rgb, g_xc = sig.cpu().numpy(), rgb.cpu().numpy(), xc.cpu().numpy()
+    err_report("posed sigma", g_sig[has], ref["sigma"][has])
+    err_report("posed rgb", g_rgb[has], ref["rgb"][has])
+    err_report("posed x*", g_xc[has], ref["xstar"][has])
+    assert np.all(np.abs(g_xc[has] - ref["xstar"][has]) <= ATOL_XSTAR)
+    assert close(g_sig[has], ref["sigma"][has], RTOL_SIGMA, 1e-9).all()
+    assert close(g_rgb[has], ref["rgb"][has], 1e-4, ATOL_RGB).all()
+    assert np.all(g_sig[ok & (ref["start"] < 0)] == 0)
+    ia.ia_destroy(ctx)
+
+
+def test_occupancy_bits_from_shared_density_bit_exact(ia):
+    sc = S.make_scene("tiny", 0)
+    table, mlp = S.make_field(sc, 0)
+    ctx = make_ctx(ia, torch, sc, table, mlp)
+    R = sc.occ_res
+    rng = np.random.default_rng(7)
+    sig = (sc.occ_tau * np.exp(rng.normal(-3.0, 2.0, R ** 3))).astype(np.float32)
+    sig[rng.integers(R ** 3, size=50)] = np.float32(sc.occ_tau)  # exactly at the threshold: not occupied
+    bits = torch.zeros((R ** 3 + 31) // 32, dtype=torch.int32, device="cuda")
+    ia.ia_occupancy_from_density(ctx, torch.from_numpy(sig).cuda(), bits)
+    torch.cuda.synchronize()
+    ref = O.occ_bits_f32(R, sc.occ_dilate, sc.occ_tau, sig)
+    np.testing.assert_array_equal(bits.cpu().numpy().view(np.uint32), ref)
+    ia.ia_destroy(ctx)
+
+
+def test_occupancy_end_to_end(ia, scene):
+    sc, table, mlp = scene
+    ctx, poses = _pose_ctx(ia, sc, table, mlp, [1])
+    om = O.OracleModel(sc, table, mlp)
+    p = om.pose(*poses[0])
+    R = sc.occ_res
+    sig = torch.zeros(R ** 3, device="cuda")
+    bits = torch.zeros((R ** 3 + 31) // 32, dtype=torch.int32, device="cuda")
+    stats = ia.ia_update_occupancy(ctx, 0, ia.IA_OCC_POSE, sig, bits, stats=True)
+    ref_sig, ref_bits = om.occupancy(p)
+    g_sig = sig.cpu().numpy()
+    pos = ref_sig > 0
+    err_report("occupancy sigma", g_sig[pos], ref_sig[pos])
+    print("occupancy stats", stats)
+    # densities agree where the oracle sees a root; bits agree except where a cell's
+    # dilation neighbourhood holds a density within 1e-3 relative of tau
+    amb = np.abs(ref_sig - sc.occ_tau) < 1e-3 * sc.occ_tau
+    amb3 = amb.reshape(R, R, R)
+    near = np.zeros_like(amb3)
+    d = sc.occ_dilate
+    for dz in range(-d, d + 1):
+        for dy in range(-d, d + 1):
+            for dx in range(-d, d + 1):
+                near |= np.roll(amb3, (dz, dy, dx), axis=(0, 1, 2))
+    near = near.reshape(-1)
+    g_occ = bits_to_bool(bits.cpu().numpy().view(np.uint32), R ** 3)
+    r_occ = bits_to_bool(ref_bits, R ** 3)
+    mism = (g_occ != r_occ) & ~near
+    print(f"occupancy: {g_occ.sum()} occupied, {near.sum()} cells excluded as ambiguous")
+    assert mism.sum() == 0
+    assert g_occ.sum() > 0
+    ia.ia_destroy(ctx)
+
+
+def _render_case(ia, sc, table, mlp, seed, early_T, width=None, height=None):
+    ctx, poses = _pose_ctx(ia, sc, table, mlp, [seed], early_T=early_T)
+    om = O.OracleModel(sc, table, mlp, early_T=early_T)
+    p = om.pose(*poses[0])
+    R = sc.occ_res
+    bits = torch.zeros((R ** 3 + 31) // 32, dtype=torch.int32, device="cuda")
+    ia.ia_update_occupancy(ctx, 0, ia.IA_OCC_POSE, None, bits)
+    occ = bits.cpu().numpy().view(np.uint32).copy()
+    cam = S.make_camera(sc, width, height)
+    return ctx, om, p, occ, cam
+
+
+def test_march_mask_bit_exact(ia, scene):
+    sc, table, mlp = scene
+    ctx, om, p, occ, cam = _render_case(ia, sc, table, mlp, 2, 0.0)
+    W, H = cam["width"], cam["height"]
+    words = (sc.max_samples + 31) // 32
+    mask = torch.zeros(H * W * words, dtype=torch.int32, device="cuda")
+    ia.ia_march_mask(ctx, 0, camera(ia, cam), mask)
+    torch.cuda.synchronize()
+    ref = om.march_mask(p, cam, occ)
+    got = mask.cpu().numpy().view(np.uint32).reshape(H * W, words)
+    print(f"march mask: {np.unpackbits(ref.view(np.uint8)).sum()} occupied samples over {H * W} rays")
+    np.testing.assert_array_equal(got, ref)
+    ia.ia_destroy(ctx)
+
+
+def test_render_tiny_full_frame(ia):
+    sc = S.make_scene("tiny", 0)
+    table, mlp = S.make_field(sc, 0)
+    for seed in (0, 1):
+        ctx, om, p, occ, cam = _render_case(ia, sc, table, mlp, seed, 0.0)
+        W, H = cam["width"], cam["height"]
+        rgb = torch.zeros(H * W, 3, device="cuda")
+        alpha = torch.zeros(H * W, device="cuda")
+        stats = ia.ia_render(ctx, 0, camera(ia, cam), rgb, alpha, stats=True)
+        ref = om.render(p, cam, occ)
+        ok = ref["flags"] == 0
+        print("render stats", stats, "flagged rays", np.sum(~ok))
+        assert stats["occupied_samples"] == int(ref["nsamp"].sum())
+        assert stats["rays"] == W * H
+        g_rgb, g_a = rgb.cpu().numpy(), alpha.cpu().numpy()
+        err_report("tiny rgb", g_rgb[ok], ref["rgb"][ok])
+        err_report("tiny alpha", g_a[ok], ref["alpha"][ok])
+        assert np.sum(~ok) <= 0.01 * W * H
+        assert close(g_rgb[ok], ref["rgb"][ok], RTOL_RGB, ATOL_RGB).all()
+        assert close(g_a[ok], ref["alpha"][ok], RTOL_RGB, ATOL_RGB).all()
+        ia.ia_destroy(ctx)
+
+
+def test_render_early_termination(ia, scene):
+    sc, table, mlp = scene
+    early = 1e-4
+    if sc.name == "tiny":
+        ctx, om, p, occ, cam = _render_case(ia, sc, table, mlp, 4, early)
+        pix = np.arange(cam["width"] * cam["height"])
+    else:
+        # full 540 x 540 frame in the benchmark's configuration; pixels sampled
+        ctx, om, p, occ, cam = _render_case(ia, sc, table, mlp, 4, early)
+        rng = np.random.default_rng(8)
+        pix = rng.choice(cam["width"] * cam["height"], 4000, replace=False)
+    W, H = cam["width"], cam["height"]
+    rgb = torch.zeros(H * W, 3, device="cuda")
+    alpha = torch.zeros(H * W, device="cuda")
+    stats = ia.ia_render(ctx, 0, camera(ia, cam), rgb, alpha, stats=True)
+    print("render stats", stats)
+    ref = om.render_pixels(p, cam, occ, pix)
+    if sc.name == "full":  # the sampled pixels should include plenty of hits
+        hit = ref["alpha"] > 0.01
+        assert hit.sum() >= 100, hit.sum()
+    ok = ref["flags"] == 0
+    g_rgb, g_a = rgb.cpu().numpy()[pix], alpha.cpu().numpy()[pix]
+    err_report(f"{sc.name} rgb (early stop)", g_rgb[ok], ref["rgb"][ok])
+    err_report(f"{sc.name} alpha (early stop)", g_a[ok], ref["alpha"][ok])
+    assert np.sum(~ok) <= 0.01 * len(pix)
+    assert close(g_rgb[ok], ref["rgb"][ok], RTOL_RGB, ATOL_RGB).all()
+    assert close(g_a[ok], ref["alpha"][ok], RTOL_RGB, ATOL_RGB).all()
+    ia.ia_destroy(ctx)
+
+
+@pytest.mark.parametrize("size", [(1, 1), (37, 23), (17, 64)])
+def test_render_ragged_sizes(ia, size):
+    sc = S.make_scene("tiny", 0)
+    table, mlp = S.make_field(sc, 0)
+    W, H = size
+    ctx, om, p, occ, _ = _render_case(ia, sc, table, mlp, 0, 0.0)
+    cam = S.make_camera(sc)
+    cam = dict(cam, width=W, height=H, cx=np.float32(cam["cx"] * W / 64), cy=np.float32(cam["cy"] * H / 64))
+    rgb = torch.full((H * W, 3), -1.0, device="cuda")
+    alpha = torch.full((H * W,), -1.0, device="cuda")
+    stats = ia.ia_render(ctx, 0, camera(ia, cam), rgb, alpha, stats=True)
+    ref = om.render(p, cam, occ)
+    assert stats["rays"] == W * H
+    ok = ref["flags"] == 0
+    assert close(rgb.cpu().numpy()[ok], ref["rgb"][ok], RTOL_RGB, ATOL_RGB).all()
+    assert close(alpha.cpu().numpy()[ok], ref["alpha"][ok], RTOL_RGB, ATOL_RGB).all()
+    ia.ia_destroy(ctx)
+
+
+def test_render_degenerate_cases(ia):
+    sc = S.make_scene("tiny", 0)
+    table, mlp = S.make_field(sc, 0)
+    ctx, om, p, occ, cam = _render_case(ia, sc, table, mlp, 0, 1e-4)
+    W, H = cam["width"], cam["height"]
+    rgb = torch.full((H * W, 3), -1.0, device="cuda")
+    alpha = torch.full((H * W,), -1.0, device="cuda")
+    # camera looking away from the subject: every ray misses the box
+    away = dict(cam, c2w=cam["c2w"] * np.array([[1, 1, -1, 1]] * 3, dtype=np.float32))
+    st = ia.ia_render(ctx, 0, camera(ia, away), rgb, alpha, stats=True)
+    assert st["hit_rays"] == 0 and st["occupied_samples"] == 0
+    assert torch.all(rgb == 0) and torch.all(alpha == 0)
+    # an empty occupancy grid: every slot is skipped
+    R = sc.occ_res
+    ia.ia_set_occupancy(ctx, np.zeros((R ** 3 + 31) // 32, np.uint32))
+    st = ia.ia_render(ctx, 0, camera(ia, cam), rgb, alpha, stats=True)
+    assert st["occupied_samples"] == 0 and torch.all(alpha == 0)
+    # a full grid: every slot of every hit ray is a sample
+    ia.ia_set_occupancy(ctx, np.full((R ** 3 + 31) // 32, 0xFFFFFFFF, np.uint32))
+    st = ia.ia_render(ctx, 0, camera(ia, cam), rgb, alpha, stats=True)
+    assert st["marched_slots"] >= st["occupied_samples"] > 0
+    ia.ia_destroy(ctx)
+
+
+def test_render_into_host_buffers(ia):
+    sc = S.make_scene("tiny", 0)
+    table, mlp = S.make_field(sc, 0)
+    ctx, om, p, occ, cam = _render_case(ia, sc, table, mlp, 1, 1e-4)
+    W, H = cam["width"], cam["height"]
+    rgb = torch.zeros(H * W, 3, device="cuda")
+    alpha = torch.zeros(H * W, device="cuda")
+    ia.ia_render(ctx, 0, camera(ia, cam), rgb, alpha)
+    h_rgb = np.zeros((H * W, 3), np.float32)
+    h_a = np.zeros(H * W, np.float32)
+    ia.ia_render(ctx, 0, camera(ia, cam), h_rgb, h_a)
+    np.testing.assert_array_equal(h_rgb, rgb.cpu().numpy())
+    np.testing.assert_array_equal(h_a, alpha.cpu().numpy())
+    ia.ia_destroy(ctx)
+
+
+def test_errors_are_status_codes(ia):
+    sc = S.make_scene("tiny", 0)
+    table, mlp = S.make_field(sc, 0)
+    ctx = make_ctx(ia, torch, sc, table, mlp)
+    cam = camera(ia, S.make_camera(sc))
+    rgb = torch.zeros(64 * 64, 3, device="cuda")
+    a = torch.zeros(64 * 64, device="cuda")
+    with pytest.raises(ia.IAError) as e:
+        ia.ia_render(ctx, 0, cam, rgb, a)
+    assert e.value.status == ia.IA_ERR_STATE  # no pose yet
+    th, tr = S.make_pose(sc, 0)
+    bad = th.copy()
+    bad[2, 1] = np.nan
+    with pytest.raises(ia.IAError) as e:
+        ia.ia_set_pose(ctx, bad[None], tr[None])
+    assert e.value.status == ia.IA_ERR_ARG
+    ia.ia_set_pose(ctx, th[None], tr[None])
+    with pytest.raises(ia.IAError) as e:
+        ia.ia_render(ctx, 0, cam, rgb, a)
+    assert e.value.status == ia.IA_ERR_STATE  # no occupancy grid yet
+    with pytest.raises(ia.IAError) as e:
+        ia.ia_update_occupancy(ctx, 3)
+    assert e.value.status == ia.IA_ERR_ARG
+    parents = sc.parents.copy()
+    parents[3] = 5  # child before parent
+    with pytest.raises(ia.IAError) as e:
+        ia.ia_set_skeleton(ctx, parents, sc.rest_joints, sc.skin_grid, sc.canon_min, sc.canon_max,
+                           sc.norm_min, sc.norm_max)
+    assert e.value.status == ia.IA_ERR_ARG
+    ia.ia_destroy(ctx)

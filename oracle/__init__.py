@@ -129,7 +129,7 @@ def _declare(L):
         f = getattr(L, name)
         f.restype = res
         f.argtypes = args
-    if hasattr(L, "or_train_grad"):
+    if hasattr(L, "or_train"):
         _declare_grad(L)
 
 

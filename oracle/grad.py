@@ -1,0 +1,56 @@
+"""ctypes wrapper of the oracle's training step (oracle_grad.c).  TEST
+INFRASTRUCTURE ONLY: L2 photometric loss over a ray batch and its fp64
+reverse-mode gradient (compositing, MLP, hash table, and the implicit-function
+gradient through the root to the skinning grid and bone transforms)."""
+import ctypes as C
+
+import numpy as np
+
+
+def declare(L):
+    from . import Model, Pose
+    P = C.POINTER
+    L.or_train.restype = C.c_double
+    L.or_train.argtypes = [P(Model), P(Pose), C.c_int, P(C.c_uint32), C.c_int, P(C.c_float), P(C.c_float),
+                           P(C.c_int32), P(C.c_double), P(C.c_double), P(C.c_int32), P(C.c_double),
+                           P(C.c_double), P(C.c_double), P(C.c_double), C.c_int]
+
+
+def pose_array(poses):
+    from . import Pose
+    arr = (Pose * len(poses))()
+    for i, p in enumerate(poses):
+        C.memmove(C.byref(arr[i]), C.byref(p), C.sizeof(Pose))
+    return arr
+
+
+def mlp_size(sc):
+    W = sc.mlp_width
+    return W * sc.mlp_in() + W + W * W + W + 4 * W + 4
+
+
+def train(om, poses, occ_bits, origin, direction, pose_id, target, grad=True, nthreads=0):
+    """Loss, per-ray colour and flags, and (if grad) the gradients as a dict:
+    table [entries, F], mlp (packed W1, b1, W2, b2, W3, b3), skin [R, R, R, nb],
+    bones [n_poses, nb, 12] (gradient w.r.t. the normalised-space N_k)."""
+    from . import _p
+    sc = om.scene
+    n = len(pose_id)
+    arr = pose_array(poses) if isinstance(poses, (list, tuple)) else poses
+    n_poses = len(arr)
+    o = np.ascontiguousarray(origin, dtype=np.float32)
+    d = np.ascontiguousarray(direction, dtype=np.float32)
+    pid = np.ascontiguousarray(pose_id, dtype=np.int32)
+    tgt = np.ascontiguousarray(target, dtype=np.float64)
+    occ = np.ascontiguousarray(occ_bits, dtype=np.uint32)
+    rgb = np.zeros((n, 3))
+    flags = np.zeros(n, dtype=np.int32)
+    g = None
+    if grad:
+        g = dict(table=np.zeros((sc.n_table_entries(), sc.n_features)), mlp=np.zeros(mlp_size(sc)),
+                 skin=np.zeros(om.skin.shape), bones=np.zeros((n_poses, sc.n_bones, 12)))
+    args = [g[k] if g else None for k in ("table", "mlp", "skin", "bones")]
+    loss = om.L.or_train(C.byref(om.m), arr, n_poses, _p(occ, C.c_uint32), n, _p(o, C.c_float),
+                         _p(d, C.c_float), _p(pid, C.c_int32), _p(tgt, C.c_double), _p(rgb, C.c_double),
+                         _p(flags, C.c_int32), *[_p(a, C.c_double) for a in args], nthreads)
+    return loss, rgb, flags, g

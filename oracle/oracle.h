@@ -138,6 +138,13 @@ void or_occupancy_cells(const or_model *m, const or_pose *p, int n, const int32_
                         double *sigma, int nthreads);
 void or_occ_bits(int R, int dilate, double tau, const double *sigma, uint32_t *bits);
 void or_occ_bits_f32(int R, int dilate, float tau, const float *sigma, uint32_t *bits);
+/* Training step (oracle_grad.c): L2 loss over world rays of several poses and
+ * its fp64 reverse-mode gradient, including the implicit-function gradient
+ * through the root to the skinning grid and the bone transforms N. */
+double or_train(const or_model *m, const or_pose *poses, int n_poses, const uint32_t *occ, int n,
+                const float *o, const float *d, const int32_t *pose_id, const double *target,
+                double *rgb_out, int *ray_flags, double *g_table, double *g_mlp, double *g_skin,
+                double *g_bones, int nthreads);
 /* Brute-force root set: Newton from every point of an n^3 canonical lattice. */
 int or_bruteforce_roots(const or_model *m, const or_pose *p, const double xn[3], int n,
                         double seed_thresh, double *roots, int max_roots);

@@ -194,6 +194,40 @@ ia_status ia_query_canonical(ia_ctx *ctx, int n, const float *x, float *sigma, f
 ia_status ia_render(ia_ctx *ctx, int pose, const ia_camera *cam, float *rgb, float *alpha,
                     ia_render_stats *stats, void *stream);
 
+/* A batch of training rays (all device pointers). */
+typedef struct ia_batch {
+  int n_rays;                /* 1..2^24 */
+  const float *origin;       /* [n][3] world-space ray origins */
+  const float *direction;    /* [n][3] world-space unit directions */
+  const int32_t *pose;       /* [n] index of a pose set by ia_set_pose */
+  const float *target;       /* [n][3] target colours */
+} ia_batch;
+
+/* Gradient buffers (device, caller-owned, overwritten by each step). */
+typedef struct ia_grads {
+  float *table;   /* [entries][F], same layout as the hash table */
+  float *mlp;     /* packed like the MLP of ia_set_params */
+  float *skin;    /* [skin_res^3][n_bones], same layout as the skinning grid */
+  float *bones;   /* [n_poses][n_bones][12]: d loss / d N_k of each pose (row-major [R | t]) */
+} ia_grads;
+
+/* One differentiable training step (Sec. 3.2, Sec. 3.4 with an L2 photometric
+ * loss): every ray is mapped into the normalised space of its pose, its slots
+ * in occupied cells (occ_grid: IA_OCC_POSE = the render grid, IA_OCC_UNION = the
+ * training grid) are evaluated with the posed field and composited front to
+ * back (no early termination), and
+ *   loss = (1 / n) sum_rays sum_channels (C - target)^2
+ * is added to *loss (device scalar; the caller zeroes it).  The backward is
+ * exact reverse mode: compositing, activations, MLP, hash-table scatter-add, and
+ * the implicit-function gradient through the root x* of LBS(x*) = x' (Eq. 5):
+ * with lambda = J(x*)^-T dL/dx* (J the analytic Jacobian),
+ *   dL/dN_k = -lambda w_k(x*) [x*;1]^T,  dL/dW(v, k) = -c_v(x*) lambda . N_k [x*;1].
+ * The selected root is treated as constant.  rgb_out [n][3] (device) may be
+ * NULL.  Workspace for n_rays * max_samples samples (about 1.2 KB each) is
+ * allocated by the context on first use and grown when a larger batch comes. */
+ia_status ia_train_step(ia_ctx *ctx, const ia_batch *batch, int occ_grid, float *loss, float *rgb_out,
+                        const ia_grads *grads, void *stream);
+
 /* The sample set of ia_render without evaluating it (the indexing contract):
  * bit i of slot_mask[(v * W + u) * ceil(N / 32) + i / 32] is set iff slot i of
  * pixel (u, v) lies in an occupied cell of the render grid.  Without early

@@ -48,6 +48,15 @@ class RenderStats(C.Structure):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
 
 
+class Batch(C.Structure):
+    _fields_ = [("n_rays", C.c_int), ("origin", C.c_void_p), ("direction", C.c_void_p), ("pose", C.c_void_p),
+                ("target", C.c_void_p)]
+
+
+class Grads(C.Structure):
+    _fields_ = [("table", C.c_void_p), ("mlp", C.c_void_p), ("skin", C.c_void_p), ("bones", C.c_void_p)]
+
+
 _lib = None
 
 
@@ -75,6 +84,7 @@ def lib():
             "ia_query_canonical": [P, I, P, P, P, V],
             "ia_render": [P, I, C.POINTER(Camera), P, P, C.POINTER(RenderStats), V],
             "ia_march_mask": [P, I, C.POINTER(Camera), P, V],
+            "ia_train_step": [P, C.POINTER(Batch), I, P, P, C.POINTER(Grads), V],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -226,3 +236,15 @@ def ia_render(ctx, pose, cam: Camera, rgb, alpha, stats=False, stream=None):
 
 def ia_march_mask(ctx, pose, cam: Camera, slot_mask, stream=None):
     _check(lib().ia_march_mask(ctx, pose, C.byref(cam), _ptr(slot_mask), _stream(stream)), ctx)
+
+
+def ia_train_step(ctx, origin, direction, pose, target, loss, grads, occ_grid=IA_OCC_UNION, rgb_out=None,
+                  stream=None):
+    """grads: dict of device tensors table, mlp, skin, bones (overwritten); loss: device scalar (added to)."""
+    b = Batch()
+    b.n_rays = int(pose.shape[0])
+    b.origin, b.direction, b.pose, b.target = _ptr(origin), _ptr(direction), _ptr(pose), _ptr(target)
+    g = Grads()
+    g.table, g.mlp, g.skin, g.bones = (_ptr(grads[k]) for k in ("table", "mlp", "skin", "bones"))
+    _check(lib().ia_train_step(ctx, C.byref(b), occ_grid, _ptr(loss), _ptr(rgb_out), C.byref(g),
+                               _stream(stream)), ctx)

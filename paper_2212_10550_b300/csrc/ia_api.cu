@@ -53,6 +53,18 @@ struct ia_ctx {
   // scratch for host-memory outputs of ia_render
   float* d_out = nullptr;
   size_t out_cap = 0;
+  // training-step workspace
+  int ray_cap = 0;
+  int* d_ray_n = nullptr;
+  float* d_ray_dt = nullptr;
+  int* d_ray_idx = nullptr;
+  int* d_count = nullptr;
+  size_t s_cap = 0;
+  float4* d_s_pos = nullptr;
+  float4* d_s_out = nullptr;
+  float4* d_s_x = nullptr;
+  float4* d_s_grad = nullptr;
+  float* d_act = nullptr;
 };
 
 namespace {
@@ -266,6 +278,15 @@ void ia_destroy(ia_ctx* c) {
   dfree(c->d_stats);
   dfree(c->d_counter);
   dfree(c->d_out);
+  dfree(c->d_ray_n);
+  dfree(c->d_ray_dt);
+  dfree(c->d_ray_idx);
+  dfree(c->d_count);
+  dfree(c->d_s_pos);
+  dfree(c->d_s_out);
+  dfree(c->d_s_x);
+  dfree(c->d_s_grad);
+  dfree(c->d_act);
   delete c;
 }
 
@@ -534,6 +555,76 @@ ia_status ia_render(ia_ctx* c, int pose, const ia_camera* cam, float* rgb, float
   if (!dev_alpha) IA_CUDA(c, cudaMemcpyAsync(alpha, o_alpha, npix * 4, cudaMemcpyDeviceToHost, s), "ia_render: copy");
   if (!dev_rgb || !dev_alpha) IA_CUDA(c, cudaStreamSynchronize(s), "ia_render");
   if (stats) read_stats(c, stats, s);
+  return IA_OK;
+}
+
+ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss, float* rgb_out,
+                        const ia_grads* g, void* stream) {
+  ia_status st = need_ready(c, 0, false);
+  if (st != IA_OK) return st;
+  if (!b || !loss || !g || !g->table || !g->mlp || !g->skin || !g->bones) return fail(c, IA_ERR_ARG, "null argument");
+  if (b->n_rays < 1 || b->n_rays > (1 << 24)) return fail(c, IA_ERR_ARG, "n_rays must be 1..2^24");
+  if (!b->origin || !b->direction || !b->pose || !b->target) return fail(c, IA_ERR_ARG, "null batch array");
+  if (occ_grid != IA_OCC_POSE && occ_grid != IA_OCC_UNION) return fail(c, IA_ERR_ARG, "unknown occupancy grid");
+  if (occ_grid == IA_OCC_POSE && !c->have_occ) return fail(c, IA_ERR_STATE, "no render grid (ia_update_occupancy)");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = b->n_rays, N = c->cfg.max_samples;
+  const size_t cap = (size_t)n * N;
+  if (n > c->ray_cap || cap > c->s_cap) {
+    IA_CUDA(c, cudaStreamSynchronize(s), "ia_train_step");
+    c->ray_cap = 0;
+    c->s_cap = 0;
+    IA_CUDA(c, dalloc(&c->d_ray_n, (size_t)n), "ia_train_step: workspace");
+    IA_CUDA(c, dalloc(&c->d_ray_dt, (size_t)n), "ia_train_step: workspace");
+    IA_CUDA(c, dalloc(&c->d_ray_idx, cap), "ia_train_step: workspace");
+    IA_CUDA(c, dalloc(&c->d_count, (size_t)1), "ia_train_step: workspace");
+    IA_CUDA(c, dalloc(&c->d_s_pos, cap), "ia_train_step: workspace");
+    IA_CUDA(c, dalloc(&c->d_s_out, cap), "ia_train_step: workspace");
+    IA_CUDA(c, dalloc(&c->d_s_x, cap), "ia_train_step: workspace");
+    IA_CUDA(c, dalloc(&c->d_s_grad, cap), "ia_train_step: workspace");
+    IA_CUDA(c, dalloc(&c->d_act, cap * kActStride), "ia_train_step: workspace");
+    c->ray_cap = n;
+    c->s_cap = cap;
+  }
+  int64_t nt = 0, nm = 0;
+  ia_param_sizes(c, &nt, &nm);
+  const size_t V = (size_t)c->Rw * c->Rw * c->Rw;
+  IA_CUDA(c, cudaMemsetAsync(c->d_count, 0, sizeof(int), s), "ia_train_step");
+  IA_CUDA(c, cudaMemsetAsync(g->table, 0, sizeof(float) * nt, s), "ia_train_step");
+  IA_CUDA(c, cudaMemsetAsync(g->mlp, 0, sizeof(float) * nm, s), "ia_train_step");
+  IA_CUDA(c, cudaMemsetAsync(g->skin, 0, sizeof(float) * V * c->nb, s), "ia_train_step");
+  IA_CUDA(c, cudaMemsetAsync(g->bones, 0, sizeof(float) * c->n_poses * c->nb * 12, s), "ia_train_step");
+  TrainArgs a{};
+  a.P = posed_args(c, 0);
+  a.V = (int)V;
+  a.B0inv = c->d_B0inv;
+  a.N = c->d_N;
+  a.skin = c->d_skin;
+  a.occ = occ_grid == IA_OCC_POSE ? c->d_occ : c->d_occ_train;
+  a.box = box_dev(c);
+  a.n_slots = N;
+  a.n_rays = n;
+  a.origin = b->origin;
+  a.direction = b->direction;
+  a.pose = b->pose;
+  a.n_poses = c->n_poses;
+  a.target = b->target;
+  a.count = c->d_count;
+  a.ray_n = c->d_ray_n;
+  a.ray_dt = c->d_ray_dt;
+  a.ray_idx = c->d_ray_idx;
+  a.s_pos = c->d_s_pos;
+  a.s_out = c->d_s_out;
+  a.s_x = c->d_s_x;
+  a.s_grad = c->d_s_grad;
+  a.act = c->d_act;
+  a.loss = loss;
+  a.rgb_out = rgb_out;
+  a.g_table = g->table;
+  a.g_mlp = g->mlp;
+  a.g_skin = g->skin;
+  a.g_bones = g->bones;
+  IA_CUDA(c, launch_train(a, c->num_sms, s), "ia_train_step: kernels");
   return IA_OK;
 }
 

@@ -25,6 +25,7 @@ constexpr int kMaxLevels = 16;
 constexpr int kWidth = 64;
 constexpr int kIn = 32;          // MLP input, zero-padded to 16 levels x 2 features
 constexpr int kMaxRoots = 4;     // distinct roots remembered per sample for merging
+constexpr int kNS = 1;           // samples per lane in the correspondence search (2 measured slower)
 constexpr unsigned kFull = 0xffffffffu;
 
 // MLP weights staged in shared memory (fp32): W1 [64][32] (zero-padded
@@ -103,8 +104,9 @@ __device__ __forceinline__ int corner_index(const SkinDev& S, int base, int corn
   return base + (corner & 1) + S.Rw * (((corner >> 1) & 1) + S.Rw * ((corner >> 2) & 1));
 }
 
-// M(x) = sum_c w_c M_c  (12 values, rows of a 3x4 matrix)
-__device__ __forceinline__ void blend_value(const SkinDev& S, float3 x, float Mx[12]) {
+// M(x) = sum_c w_c M_c  (12 values, rows of a 3x4 matrix); M = one pose's grid
+__device__ __forceinline__ void blend_value(const SkinDev& S, const float4* __restrict__ M, float3 x,
+                                            float Mx[12]) {
   CellCoord c = skin_cell(S, x);
 #pragma unroll
   for (int q = 0; q < 12; ++q) Mx[q] = 0.f;
@@ -113,7 +115,7 @@ __device__ __forceinline__ void blend_value(const SkinDev& S, float3 x, float Mx
     int v = corner_index(S, c.base, corner);
     float w = ((corner & 1) ? c.f[0] : 1.f - c.f[0]) * (((corner >> 1) & 1) ? c.f[1] : 1.f - c.f[1]) *
               (((corner >> 2) & 1) ? c.f[2] : 1.f - c.f[2]);
-    const float4* p = S.M + 3 * v;
+    const float4* p = M + 3 * v;
     float4 r0 = __ldg(p), r1 = __ldg(p + 1), r2 = __ldg(p + 2);
     Mx[0] = fmaf(w, r0.x, Mx[0]); Mx[1] = fmaf(w, r0.y, Mx[1]);
     Mx[2] = fmaf(w, r0.z, Mx[2]); Mx[3] = fmaf(w, r0.w, Mx[3]);
@@ -131,7 +133,8 @@ __device__ __forceinline__ float3 apply34(const float A[12], float3 x) {
 }
 
 // M(x) and the full Jacobian J = M(x)[:, :3] + sum_c (M_c [x;1]) grad(w_c)^T
-__device__ __forceinline__ void blend_value_jac(const SkinDev& S, float3 x, float Mx[12], float J[9]) {
+__device__ __forceinline__ void blend_value_jac(const SkinDev& S, const float4* __restrict__ M, float3 x,
+                                                float Mx[12], float J[9]) {
   CellCoord c = skin_cell(S, x);
 #pragma unroll
   for (int q = 0; q < 12; ++q) Mx[q] = 0.f;
@@ -149,7 +152,7 @@ __device__ __forceinline__ void blend_value_jac(const SkinDev& S, float3 x, floa
     float gx = (cx ? 1.f : -1.f) * wy * wz * S.scale[0] * c.live[0];
     float gy = (cy ? 1.f : -1.f) * wx * wz * S.scale[1] * c.live[1];
     float gz = (cz ? 1.f : -1.f) * wx * wy * S.scale[2] * c.live[2];
-    const float4* p = S.M + 3 * v;
+    const float4* p = M + 3 * v;
     float4 r[3] = {__ldg(p), __ldg(p + 1), __ldg(p + 2)};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -333,9 +336,10 @@ struct PosedOut {
 };
 
 // One Newton step x <- x - J(x)^-1 (LBS(x) - x') with the analytic Jacobian.
-__device__ __forceinline__ float3 polish_root(const SkinDev& S, float3 xs, float3 xn) {
+__device__ __forceinline__ float3 polish_root(const SkinDev& S, const float4* __restrict__ M, float3 xs,
+                                              float3 xn) {
   float Mx[12], J[9], Hn[9];
-  blend_value_jac(S, xs, Mx, J);
+  blend_value_jac(S, M, xs, Mx, J);
   float3 y = apply34(Mx, xs);
   float3 rr = make_float3(y.x - xn.x, y.y - xn.y, y.z - xn.z);
   if (inv3(J, Hn)) {
@@ -356,130 +360,191 @@ __device__ __forceinline__ void take_best(PosedOut& out, float sig, float3 rgb, 
   }
 }
 
-// roots: this CTA's float4 [kMaxRoots][blockDim.x] scratch (x, y, z, start bits).
+// Multi-start correspondence search and field evaluation for NS samples per
+// lane (NS independent Broyden chains interleaved, so that each loop step has
+// NS gathers of the blended grid in flight per lane).  All 32 lanes must call.
+//   M[s]: sample s's pose's blended grid; Ninv[s]: that pose's N_k^-1 ([nb][12]);
+//   roots: this CTA's float4 scratch of kMaxRoots * NS * blockDim.x entries
+//   (x, y, z, start bits).
 // The first kMaxRoots distinct roots of a sample are evaluated together by the
 // warp after the search; any further distinct root (rare) is evaluated on the
 // spot so that no root is ever dropped.
-__device__ __forceinline__ PosedOut posed_field_warp(const SkinDev& S, const FieldDev& F, const SolveCfg& cfg,
-                                                     const float* __restrict__ sNinv, const float* sw,
-                                                     float4* roots, bool active, float3 xn,
-                                                     SampleStats& st) {
+template <int NS>
+__device__ __forceinline__ void posed_field_warp_n(const SkinDev& S, const float4* const* M, const FieldDev& F,
+                                                   const SolveCfg& cfg, const float* const* Ninv, const float* sw,
+                                                   float4* roots, const bool* active, const float3* xn,
+                                                   PosedOut* out, SampleStats& st) {
   const int tid = threadIdx.x, stride = blockDim.x;
-  PosedOut out;
-  out.sigma = 0.f;
-  out.rgb = make_float3(0.f, 0.f, 0.f);
-  out.xstar = out.rgb;
-  out.start = -1;
-  // ---- flattened multi-start Broyden: every loop step evaluates M at one point per lane
-  int k = 0, it = 0, nroots = 0;
-  int phase = active ? 0 : 2;  // 0 = start k, 1 = iterate, 2 = done
-  float3 x = make_float3(0.f, 0.f, 0.f), r = x, dx = x;
-  float H[9];
+  int k[NS], it[NS], nroots[NS], phase[NS];  // phase 0 = start k, 1 = iterate, 2 = done
+  float3 x[NS], r[NS], dx[NS];
+  float H[NS][9];
 #pragma unroll
-  for (int q = 0; q < 9; ++q) H[q] = 0.f;
-  while (__any_sync(kFull, phase != 2)) {
-    float3 q = x;
-    if (phase == 0) {
-      const float* A = sNinv + 12 * k;
-      q = make_float3(A[0] * xn.x + A[1] * xn.y + A[2] * xn.z + A[3],
-                      A[4] * xn.x + A[5] * xn.y + A[6] * xn.z + A[7],
-                      A[8] * xn.x + A[9] * xn.y + A[10] * xn.z + A[11]);
-    } else if (phase == 1) {
-      q = make_float3(x.x + dx.x, x.y + dx.y, x.z + dx.z);
-    }
-    float Mx[12];
-    if (phase != 2) blend_value(S, q, Mx);
-    bool finish = false, conv = false;
-    if (phase == 0) {
-      st.starts++;
-      float3 y = apply34(Mx, q);
-      x = q;
-      r = make_float3(y.x - xn.x, y.y - xn.y, y.z - xn.z);
-      // initial inverse Jacobian: LBS with the weights frozen at x0, (sum_i w_i R_i)^-1
-      const float J0[9] = {Mx[0], Mx[1], Mx[2], Mx[4], Mx[5], Mx[6], Mx[8], Mx[9], Mx[10]};
-      it = 0;
-      if (!inv3(J0, H)) finish = true;
-    } else if (phase == 1) {
-      float3 y = apply34(Mx, q);
-      float3 rn = make_float3(y.x - xn.x, y.y - xn.y, y.z - xn.z);
-      float3 dr = make_float3(rn.x - r.x, rn.y - r.y, rn.z - r.z);
-      x = q;
-      r = rn;
-      ++it;
-      st.iters++;
-      // good Broyden: H += (dx - H dr)(dx^T H) / (dx^T H dr)
-      float u0 = H[0] * dr.x + H[1] * dr.y + H[2] * dr.z;
-      float u1 = H[3] * dr.x + H[4] * dr.y + H[5] * dr.z;
-      float u2 = H[6] * dr.x + H[7] * dr.y + H[8] * dr.z;
-      float den = dx.x * u0 + dx.y * u1 + dx.z * u2;
-      if (fabsf(den) > 1e-12f) {
-        float a0 = (dx.x - u0) / den, a1 = (dx.y - u1) / den, a2 = (dx.z - u2) / den;
-        float b0 = dx.x * H[0] + dx.y * H[3] + dx.z * H[6];
-        float b1 = dx.x * H[1] + dx.y * H[4] + dx.z * H[7];
-        float b2 = dx.x * H[2] + dx.y * H[5] + dx.z * H[8];
-        H[0] += a0 * b0; H[1] += a0 * b1; H[2] += a0 * b2;
-        H[3] += a1 * b0; H[4] += a1 * b1; H[5] += a1 * b2;
-        H[6] += a2 * b0; H[7] += a2 * b1; H[8] += a2 * b2;
+  for (int s = 0; s < NS; ++s) {
+    out[s].sigma = 0.f;
+    out[s].rgb = make_float3(0.f, 0.f, 0.f);
+    out[s].xstar = out[s].rgb;
+    out[s].start = -1;
+    k[s] = 0; it[s] = 0; nroots[s] = 0;
+    phase[s] = active[s] ? 0 : 2;
+    x[s] = make_float3(0.f, 0.f, 0.f); r[s] = x[s]; dx[s] = x[s];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) H[s][q] = 0.f;
+  }
+  auto busy = [&]() {
+    bool b = false;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) b |= phase[s] != 2;
+    return b;
+  };
+  // ---- flattened multi-start Broyden: every loop step evaluates M once per chain
+  while (__any_sync(kFull, busy())) {
+    float3 q[NS];
+    float Mx[NS][12];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      q[s] = x[s];
+      if (phase[s] == 0) {
+        const float* A = Ninv[s] + 12 * k[s];
+        const float3 p = xn[s];
+        q[s] = make_float3(A[0] * p.x + A[1] * p.y + A[2] * p.z + A[3], A[4] * p.x + A[5] * p.y + A[6] * p.z + A[7],
+                           A[8] * p.x + A[9] * p.y + A[10] * p.z + A[11]);
+      } else if (phase[s] == 1) {
+        q[s] = make_float3(x[s].x + dx[s].x, x[s].y + dx[s].y, x[s].z + dx[s].z);
       }
     }
-    if (phase != 2 && !finish) {
-      float rr = r.x * r.x + r.y * r.y + r.z * r.z;
-      if (rr < cfg.tol2) {
-        conv = true;
-        finish = true;
-      } else if (it >= cfg.max_iter) {
-        finish = true;
-      } else {
-        dx = make_float3(-(H[0] * r.x + H[1] * r.y + H[2] * r.z), -(H[3] * r.x + H[4] * r.y + H[5] * r.z),
-                         -(H[6] * r.x + H[7] * r.y + H[8] * r.z));
-        phase = 1;
-      }
-    }
-    if (finish) {
-      if (conv && in_box(S, x)) {
-        st.converged++;
-        bool dup = false;
-        for (int j = 0; j < min(nroots, kMaxRoots); ++j) {
-          float4 o = roots[j * stride + tid];
-          float ddx = x.x - o.x, ddy = x.y - o.y, ddz = x.z - o.z;
-          if (ddx * ddx + ddy * ddy + ddz * ddz < 1e-8f) { dup = true; break; }
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+      if (phase[s] != 2) blend_value(S, M[s], q[s], Mx[s]);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      bool finish = false, conv = false;
+      if (phase[s] == 0) {
+        st.starts++;
+        const float3 y = apply34(Mx[s], q[s]);
+        x[s] = q[s];
+        r[s] = make_float3(y.x - xn[s].x, y.y - xn[s].y, y.z - xn[s].z);
+        // initial inverse Jacobian: LBS with the weights frozen at x0, (sum_i w_i R_i)^-1
+        const float J0[9] = {Mx[s][0], Mx[s][1], Mx[s][2], Mx[s][4], Mx[s][5], Mx[s][6], Mx[s][8], Mx[s][9], Mx[s][10]};
+        it[s] = 0;
+        if (!inv3(J0, H[s])) finish = true;
+      } else if (phase[s] == 1) {
+        const float3 y = apply34(Mx[s], q[s]);
+        const float3 rn = make_float3(y.x - xn[s].x, y.y - xn[s].y, y.z - xn[s].z);
+        const float3 dr = make_float3(rn.x - r[s].x, rn.y - r[s].y, rn.z - r[s].z);
+        x[s] = q[s];
+        r[s] = rn;
+        ++it[s];
+        st.iters++;
+        // good Broyden: H += (dx - H dr)(dx^T H) / (dx^T H dr)
+        float* h = H[s];
+        const float3 d = dx[s];
+        const float u0 = h[0] * dr.x + h[1] * dr.y + h[2] * dr.z;
+        const float u1 = h[3] * dr.x + h[4] * dr.y + h[5] * dr.z;
+        const float u2 = h[6] * dr.x + h[7] * dr.y + h[8] * dr.z;
+        const float den = d.x * u0 + d.y * u1 + d.z * u2;
+        if (fabsf(den) > 1e-12f) {
+          const float a0 = (d.x - u0) / den, a1 = (d.y - u1) / den, a2 = (d.z - u2) / den;
+          const float b0 = d.x * h[0] + d.y * h[3] + d.z * h[6];
+          const float b1 = d.x * h[1] + d.y * h[4] + d.z * h[7];
+          const float b2 = d.x * h[2] + d.y * h[5] + d.z * h[8];
+          h[0] += a0 * b0; h[1] += a0 * b1; h[2] += a0 * b2;
+          h[3] += a1 * b0; h[4] += a1 * b1; h[5] += a1 * b2;
+          h[6] += a2 * b0; h[7] += a2 * b1; h[8] += a2 * b2;
         }
-        if (!dup) {
-          st.roots++;
-          if (nroots < kMaxRoots) {
-            roots[nroots * stride + tid] = make_float4(x.x, x.y, x.z, __int_as_float(k));
-          } else {
-            float3 xs = polish_root(S, x, xn);
-            float sig;
-            float3 rgb;
-            field_fp32(F, sw, xs, sig, rgb);
-            take_best(out, sig, rgb, xs, k);
+      }
+      if (phase[s] != 2 && !finish) {
+        const float rr = r[s].x * r[s].x + r[s].y * r[s].y + r[s].z * r[s].z;
+        if (rr < cfg.tol2) {
+          conv = true;
+          finish = true;
+        } else if (it[s] >= cfg.max_iter) {
+          finish = true;
+        } else {
+          const float* h = H[s];
+          dx[s] = make_float3(-(h[0] * r[s].x + h[1] * r[s].y + h[2] * r[s].z),
+                              -(h[3] * r[s].x + h[4] * r[s].y + h[5] * r[s].z),
+                              -(h[6] * r[s].x + h[7] * r[s].y + h[8] * r[s].z));
+          phase[s] = 1;
+        }
+      }
+      if (finish) {
+        if (conv && in_box(S, x[s])) {
+          st.converged++;
+          bool dup = false;
+          for (int j = 0; j < min(nroots[s], kMaxRoots); ++j) {
+            const float4 o = roots[((s * kMaxRoots) + j) * stride + tid];
+            const float ddx = x[s].x - o.x, ddy = x[s].y - o.y, ddz = x[s].z - o.z;
+            if (ddx * ddx + ddy * ddy + ddz * ddz < 1e-8f) { dup = true; break; }
           }
-          nroots++;
+          if (!dup) {
+            st.roots++;
+            if (nroots[s] < kMaxRoots) {
+              roots[((s * kMaxRoots) + nroots[s]) * stride + tid] = make_float4(x[s].x, x[s].y, x[s].z, __int_as_float(k[s]));
+            } else {
+              const float3 xs = polish_root(S, M[s], x[s], xn[s]);
+              float sig;
+              float3 rgb;
+              field_fp32(F, sw, xs, sig, rgb);
+              take_best(out[s], sig, rgb, xs, k[s]);
+            }
+            nroots[s]++;
+          }
         }
+        ++k[s];
+        phase[s] = (k[s] < cfg.nb) ? 0 : 2;
       }
-      ++k;
-      phase = (k < cfg.nb) ? 0 : 2;
     }
   }
-  // ---- one Newton polish per stored root, field evaluation, max-density root
-  int nr = min(nroots, kMaxRoots);
-  int nmax = __reduce_max_sync(kFull, nr);
-  for (int j = 0; j < nmax; ++j) {
-    bool has = j < nr;
+  // ---- one Newton polish per stored root, field evaluation, max-density root;
+  //      the lane's (sample, root) pairs are evaluated one per warp step
+  int nr[NS], total = 0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    nr[s] = min(nroots[s], kMaxRoots);
+    total += nr[s];
+  }
+  const int nmax = __reduce_max_sync(kFull, total);
+  for (int e = 0; e < nmax; ++e) {
+    const bool has = e < total;
+    int si = 0, j = e;
+#pragma unroll
+    for (int s = 0; s + 1 < NS; ++s)
+      if (si == s && j >= nr[s]) { j -= nr[s]; si = s + 1; }
     float3 xs = make_float3(S.cmin[0], S.cmin[1], S.cmin[2]);
     int start = -1;
+    float3 xq = xn[0];
+    const float4* Mq = M[0];
+#pragma unroll
+    for (int s = 1; s < NS; ++s)
+      if (si == s) { xq = xn[s]; Mq = M[s]; }
     if (has) {
-      float4 o = roots[j * stride + tid];
+      const float4 o = roots[((si * kMaxRoots) + j) * stride + tid];
       start = __float_as_int(o.w);
-      xs = polish_root(S, make_float3(o.x, o.y, o.z), xn);
+      xs = polish_root(S, Mq, make_float3(o.x, o.y, o.z), xq);
     }
     float sig;
     float3 rgb;
     field_fp32(F, sw, xs, sig, rgb);
-    if (has) take_best(out, sig, rgb, xs, start);
+    if (has) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+        if (si == s) take_best(out[s], sig, rgb, xs, start);
+    }
   }
-  return out;
+}
+
+// One sample per lane (see posed_field_warp_n).
+__device__ __forceinline__ PosedOut posed_field_warp(const SkinDev& S, const float4* __restrict__ M,
+                                                     const FieldDev& F, const SolveCfg& cfg,
+                                                     const float* __restrict__ sNinv, const float* sw,
+                                                     float4* roots, bool active, float3 xn, SampleStats& st) {
+  const float4* Ms[1] = {M};
+  const float* Ns[1] = {sNinv};
+  const bool act[1] = {active};
+  const float3 x[1] = {xn};
+  PosedOut out[1];
+  posed_field_warp_n<1>(S, Ms, F, cfg, Ns, sw, roots, act, x, out, st);
+  return out[0];
 }
 
 }  // namespace ia

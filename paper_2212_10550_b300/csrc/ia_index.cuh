@@ -35,20 +35,11 @@ __device__ __forceinline__ float dot3_rn(float a0, float a1, float a2, float b0,
   return __fadd_rn(__fadd_rn(__fmul_rn(a0, b0), __fmul_rn(a1, b1)), __fmul_rn(a2, b2));
 }
 
-// Normalised-space ray of pixel (u, v); returns true if it meets the box.
-__device__ __forceinline__ bool make_ray(const CamDev& c, const float* __restrict__ B0inv, const BoxDev& bx,
-                                         int u, int v, float o[3], float d[3], float& tn, float& tf) {
-  const float dc0 = __fdiv_rn(__fsub_rn(__fadd_rn((float)u, 0.5f), c.cx), c.fx);
-  const float dc1 = __fdiv_rn(__fsub_rn(__fadd_rn((float)v, 0.5f), c.cy), c.fy);
-  float dw[3], ow[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    dw[i] = dot3_rn(c.c2w[i * 4 + 0], c.c2w[i * 4 + 1], c.c2w[i * 4 + 2], dc0, dc1, 1.0f);
-    ow[i] = c.c2w[i * 4 + 3];
-  }
-  const float nrm = __fsqrt_rn(dot3_rn(dw[0], dw[1], dw[2], dw[0], dw[1], dw[2]));
-#pragma unroll
-  for (int i = 0; i < 3; ++i) dw[i] = __fdiv_rn(dw[i], nrm);
+// World ray (ow, dw) -> normalised space through B_0^-1, then the slab clip
+// against the normalised box; returns true if the ray meets the box.
+__device__ __forceinline__ bool normalise_and_clip(const float* __restrict__ B0inv, const BoxDev& bx,
+                                                   const float ow[3], const float dw[3], float o[3], float d[3],
+                                                   float& tn, float& tf) {
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     o[i] = __fadd_rn(dot3_rn(B0inv[i * 4 + 0], B0inv[i * 4 + 1], B0inv[i * 4 + 2], ow[0], ow[1], ow[2]),
@@ -67,6 +58,23 @@ __device__ __forceinline__ bool make_ray(const CamDev& c, const float* __restric
   tn = tmin;
   tf = tmax;
   return tmax > tmin;
+}
+
+// Normalised-space ray of pixel (u, v); returns true if it meets the box.
+__device__ __forceinline__ bool make_ray(const CamDev& c, const float* __restrict__ B0inv, const BoxDev& bx,
+                                         int u, int v, float o[3], float d[3], float& tn, float& tf) {
+  const float dc0 = __fdiv_rn(__fsub_rn(__fadd_rn((float)u, 0.5f), c.cx), c.fx);
+  const float dc1 = __fdiv_rn(__fsub_rn(__fadd_rn((float)v, 0.5f), c.cy), c.fy);
+  float dw[3], ow[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    dw[i] = dot3_rn(c.c2w[i * 4 + 0], c.c2w[i * 4 + 1], c.c2w[i * 4 + 2], dc0, dc1, 1.0f);
+    ow[i] = c.c2w[i * 4 + 3];
+  }
+  const float nrm = __fsqrt_rn(dot3_rn(dw[0], dw[1], dw[2], dw[0], dw[1], dw[2]));
+#pragma unroll
+  for (int i = 0; i < 3; ++i) dw[i] = __fdiv_rn(dw[i], nrm);
+  return normalise_and_clip(B0inv, bx, ow, dw, o, d, tn, tf);
 }
 
 __device__ __forceinline__ float slot_delta(float tn, float tf, int n_slots) {

@@ -42,6 +42,46 @@ struct RenderArgs {
   unsigned long long* stats;
 };
 
+// Training step (ia_train.cu).  Per-sample workspace: one row of kActStride
+// floats holds the recomputed features, hidden activations and their gradients
+// (F [32], H1 [64], H2 [64], dH1 [64], dH2 [64], dO [4]).
+constexpr int kActStride = kIn + 4 * kWidth + 4;
+constexpr int kMlpPadT = (kMlpSmemFloats + 3) / 4 * 4;
+
+struct TrainArgs {
+  PosedArgs P;           // P.S.M and P.Ninv point at pose 0 of the per-pose arrays
+  int V;                 // skinning-grid vertices (one pose's blended grid = 3V float4)
+  const float* B0inv;    // [n_poses][12]
+  const float* N;        // [n_poses][nb][12]
+  const float* skin;     // [V][nb]
+  const uint32_t* occ;
+  BoxDev box;
+  int n_slots;
+  int n_rays;
+  const float* origin;   // [n][3] world
+  const float* direction;
+  const int* pose;       // [n]; indices outside [0, n_poses) make an empty ray
+  int n_poses;
+  const float* target;   // [n][3]
+  int* count;            // device scalar: samples
+  int* ray_n;            // [n] samples per ray
+  float* ray_dt;         // [n] slot spacing
+  int* ray_idx;          // [n][n_slots] sample index of the ray's j-th sample
+  float4* s_pos;         // [cap] normalised position, pose bits
+  float4* s_out;         // [cap] sigma (0 without a root), rgb
+  float4* s_x;           // [cap] x*, has-root
+  float4* s_grad;        // [cap] dL/dsigma, dL/dc
+  float* act;            // [cap][kActStride]
+  float* loss;           // device scalar (accumulated)
+  float* rgb_out;        // [n][3] or null
+  float* g_table;
+  float* g_mlp;
+  float* g_skin;
+  float* g_bones;
+};
+
+cudaError_t launch_train(const TrainArgs& a, int num_sms, cudaStream_t s);
+
 size_t posed_smem_bytes(int threads);
 size_t render_smem_bytes(int K);
 

@@ -9,6 +9,15 @@
 //                         encoding -> MLP -> front-to-back compositing
 #include "ia_internal.h"
 
+// minimum resident CTAs per SM the compiler must fit (a register cap)
+#ifndef IA_RENDER_MIN_BLOCKS
+#define IA_RENDER_MIN_BLOCKS 1
+#endif
+#ifndef IA_POSED_MIN_BLOCKS
+#define IA_POSED_MIN_BLOCKS 1
+#endif
+
+
 namespace ia {
 
 // ---------------------------------------------------------------------------
@@ -141,7 +150,7 @@ cudaError_t launch_blend(int P, int V, int nb, const float* W, const float* N, f
 constexpr int kMlpPad = (kMlpSmemFloats + 3) / 4 * 4;
 
 size_t posed_smem_bytes(int threads) {
-  return sizeof(float) * (kMlpPad + kMaxBones * 12) + sizeof(float4) * kMaxRoots * threads;
+  return sizeof(float) * (kMlpPad + kMaxBones * 12) + sizeof(float4) * kMaxRoots * kNS * threads;
 }
 
 struct PosedSmem {
@@ -171,20 +180,35 @@ __device__ __forceinline__ void flush_stats(unsigned long long* stats, int idx, 
 // Occupancy grid (Sec. 3.3, inference mode)
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256) occ_density_kernel(const PosedArgs a, const BoxDev box,
+__global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS) occ_density_kernel(const PosedArgs a, const BoxDev box,
                                                           float* __restrict__ sigma,
                                                           unsigned long long* __restrict__ stats) {
   extern __shared__ float4 smem4[];
   PosedSmem sm = stage_posed(a, smem4);
   const int n = box.R * box.R * box.R;
   SampleStats st;
-  // grid-stride over whole warps so every lane takes part in the warp-level search
-  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
-    const int cell = base + threadIdx.x;
-    const bool active = cell < n;
-    float3 xn = active ? cell_center(box, cell) : make_float3(0.f, 0.f, 0.f);
-    PosedOut o = posed_field_warp(a.S, a.F, a.cfg, sm.sNinv, sm.sw, sm.roots, active, xn, st);
-    if (active) sigma[cell] = o.start >= 0 ? o.sigma : 0.f;
+  // grid-stride over whole warps so every lane takes part in the warp-level search;
+  // each lane carries kNS cells through the search
+  for (int base = blockIdx.x * blockDim.x * kNS; base < n; base += gridDim.x * blockDim.x * kNS) {
+    bool act[kNS];
+    float3 xn[kNS];
+    const float4* Ms[kNS];
+    const float* Ns[kNS];
+    PosedOut o[kNS];
+#pragma unroll
+    for (int q = 0; q < kNS; ++q) {
+      const int cell = base + q * blockDim.x + threadIdx.x;
+      act[q] = cell < n;
+      xn[q] = act[q] ? cell_center(box, cell) : make_float3(0.f, 0.f, 0.f);
+      Ms[q] = a.S.M;
+      Ns[q] = sm.sNinv;
+    }
+    posed_field_warp_n<kNS>(a.S, Ms, a.F, a.cfg, Ns, sm.sw, sm.roots, act, xn, o, st);
+#pragma unroll
+    for (int q = 0; q < kNS; ++q) {
+      const int cell = base + q * blockDim.x + threadIdx.x;
+      if (act[q]) sigma[cell] = o[q].start >= 0 ? o[q].sigma : 0.f;
+    }
   }
   if (stats) {
     flush_stats(stats, ST_STARTS, st.starts);
@@ -197,7 +221,7 @@ __global__ void __launch_bounds__(256) occ_density_kernel(const PosedArgs a, con
 cudaError_t launch_occ_density(const PosedArgs& a, const BoxDev& box, float* sigma, unsigned long long* stats,
                                cudaStream_t s) {
   const int n = box.R * box.R * box.R;
-  int blocks = (n + 255) / 256;
+  int blocks = (n + 256 * kNS - 1) / (256 * kNS);
   size_t smem = posed_smem_bytes(256);
   cudaError_t e = cudaFuncSetAttribute(occ_density_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -249,21 +273,34 @@ cudaError_t launch_occ_bits(const float* sigma, int R, int dilate, float tau, ui
 // Queries
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256) query_posed_kernel(const PosedArgs a, int n, const float* __restrict__ x,
+__global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS) query_posed_kernel(const PosedArgs a, int n, const float* __restrict__ x,
                                                           float* sigma, float* rgb, float* xc, int* start) {
   extern __shared__ float4 smem4[];
   PosedSmem sm = stage_posed(a, smem4);
   SampleStats st;
-  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
-    const int i = base + threadIdx.x;
-    const bool active = i < n;
-    float3 xn = active ? make_float3(x[3 * i], x[3 * i + 1], x[3 * i + 2]) : make_float3(0.f, 0.f, 0.f);
-    PosedOut o = posed_field_warp(a.S, a.F, a.cfg, sm.sNinv, sm.sw, sm.roots, active, xn, st);
-    if (active) {
-      if (sigma) sigma[i] = o.start >= 0 ? o.sigma : 0.f;
-      if (rgb) { rgb[3 * i] = o.rgb.x; rgb[3 * i + 1] = o.rgb.y; rgb[3 * i + 2] = o.rgb.z; }
-      if (xc) { xc[3 * i] = o.xstar.x; xc[3 * i + 1] = o.xstar.y; xc[3 * i + 2] = o.xstar.z; }
-      if (start) start[i] = o.start;
+  for (int base = blockIdx.x * blockDim.x * kNS; base < n; base += gridDim.x * blockDim.x * kNS) {
+    bool act[kNS];
+    float3 xn[kNS];
+    const float4* Ms[kNS];
+    const float* Ns[kNS];
+    PosedOut o[kNS];
+#pragma unroll
+    for (int q = 0; q < kNS; ++q) {
+      const int i = base + q * blockDim.x + threadIdx.x;
+      act[q] = i < n;
+      xn[q] = act[q] ? make_float3(x[3 * i], x[3 * i + 1], x[3 * i + 2]) : make_float3(0.f, 0.f, 0.f);
+      Ms[q] = a.S.M;
+      Ns[q] = sm.sNinv;
+    }
+    posed_field_warp_n<kNS>(a.S, Ms, a.F, a.cfg, Ns, sm.sw, sm.roots, act, xn, o, st);
+#pragma unroll
+    for (int q = 0; q < kNS; ++q) {
+      const int i = base + q * blockDim.x + threadIdx.x;
+      if (!act[q]) continue;
+      if (sigma) sigma[i] = o[q].start >= 0 ? o[q].sigma : 0.f;
+      if (rgb) { rgb[3 * i] = o[q].rgb.x; rgb[3 * i + 1] = o[q].rgb.y; rgb[3 * i + 2] = o[q].rgb.z; }
+      if (xc) { xc[3 * i] = o[q].xstar.x; xc[3 * i + 1] = o[q].xstar.y; xc[3 * i + 2] = o[q].xstar.z; }
+      if (start) start[i] = o[q].start;
     }
   }
 }
@@ -273,7 +310,7 @@ cudaError_t launch_query_posed(const PosedArgs& a, int n, const float* x, float*
   size_t smem = posed_smem_bytes(256);
   cudaError_t e = cudaFuncSetAttribute(query_posed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  query_posed_kernel<<<(n + 255) / 256, 256, smem, s>>>(a, n, x, sigma, rgb, xc, start);
+  query_posed_kernel<<<(n + 256 * kNS - 1) / (256 * kNS), 256, smem, s>>>(a, n, x, sigma, rgb, xc, start);
   return cudaGetLastError();
 }
 
@@ -303,20 +340,22 @@ cudaError_t launch_query_canonical(const FieldDev& F, const float* mlp, int n_in
 // ---------------------------------------------------------------------------
 // Persistent fused render kernel
 //
-// Each CTA keeps a pool of 256 rays, one per thread.  A round:
+// Every warp runs on its own: it keeps a pool of 32 rays, one per lane, and
+// loops over rounds with warp-level synchronisation only.  A round:
 //  1. march: every ray advances its slot cursor until it has found up to K
 //     slots in occupied cells (empty-space skipping); exhausted rays write
-//     their pixel and take the next ray from a global counter (warp-aggregated);
-//  2. a block scan packs the found (ray, slot) samples into shared memory;
-//  3. every warp evaluates 32 samples at a time: bone-wise Broyden search,
-//     polish, hash encoding, MLP, max-density root;
+//     their pixel and take the next ray from a global counter (one atomic per
+//     warp);
+//  2. a warp scan packs the found (ray, slot) samples into shared memory;
+//  3. the warp evaluates them 32 at a time: bone-wise Broyden search, polish,
+//     hash encoding, MLP, max-density root;
 //  4. every ray composites its own samples front to back and stops once its
 //     transmittance is below the threshold.
 // ---------------------------------------------------------------------------
 
 size_t render_smem_bytes(int K) {
   return posed_smem_bytes(kRenderThreads) + sizeof(float4) * (2 * kRenderThreads + K * kRenderThreads) +
-         sizeof(int) * (2 * K * kRenderThreads + 32);
+         sizeof(int) * (2 * K * kRenderThreads);
 }
 
 __device__ __forceinline__ void tile_pixel(int id, int tiles_x, int W, int H, int& u, int& v, bool& valid) {
@@ -327,27 +366,28 @@ __device__ __forceinline__ void tile_pixel(int id, int tiles_x, int W, int H, in
 }
 
 template <int K>
-__global__ void __launch_bounds__(kRenderThreads) render_kernel(const RenderArgs a) {
+__global__ void __launch_bounds__(kRenderThreads, IA_RENDER_MIN_BLOCKS) render_kernel(const RenderArgs a) {
   extern __shared__ float4 smem4[];
   PosedSmem sm = stage_posed(a.P, smem4);
-  float4* ray_o = sm.roots + kMaxRoots * kRenderThreads;  // (o.xyz, delta)
-  float4* ray_d = ray_o + kRenderThreads;                 // (d.xyz, t_near)
-  float4* s_res = ray_d + kRenderThreads;                 // (sigma, r, g, b) per sample
-  int* s_ray = reinterpret_cast<int*>(s_res + K * kRenderThreads);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // this warp's slices of the shared arrays
+  float4* const after_roots = sm.roots + kMaxRoots * kNS * kRenderThreads;
+  float4* ray_o = after_roots + warp * 32;                             // (o.xyz, delta)
+  float4* ray_d = ray_o + kRenderThreads;                              // (d.xyz, t_near)
+  float4* s_res = after_roots + 2 * kRenderThreads + warp * 32 * K;    // (sigma, r, g, b)
+  int* s_ray = reinterpret_cast<int*>(after_roots + (2 + K) * kRenderThreads) + warp * 32 * K;
   int* s_slot = s_ray + K * kRenderThreads;
-  int* s_warp = s_slot + K * kRenderThreads;
   __shared__ float sB0inv[12];
-  if (threadIdx.x < 12) sB0inv[threadIdx.x] = a.B0inv[threadIdx.x];
+  if (tid < 12) sB0inv[tid] = a.B0inv[tid];
   __syncthreads();
 
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int W = a.cam.width, H = a.cam.height;
   const float log_stop = a.early_T > 0.f ? -logf(a.early_T) : __int_as_float(0x7f800000);
 
-  // per-ray state of this thread's pool slot
+  // per-ray state of this lane's pool slot
   bool has_ray = false, queue_empty = false;
   int pix = 0, cursor = 0;
-  float depth = 0.f;                      // optical depth sum sigma_i delta
+  float depth = 0.f;  // optical depth sum sigma_i delta
   float cr = 0.f, cg = 0.f, cb = 0.f;
   long long n_rays = 0, n_hit = 0, n_marched = 0, n_occ = 0, n_early = 0;
   SampleStats st;
@@ -358,13 +398,18 @@ __global__ void __launch_bounds__(kRenderThreads) render_kernel(const RenderArgs
     int slots[K];
     while (true) {
       if (has_ray) {
-        float4 ro = ray_o[tid], rd = ray_d[tid];
+        const float4 ro = ray_o[lane], rd = ray_d[lane];
         const float o[3] = {ro.x, ro.y, ro.z}, d[3] = {rd.x, rd.y, rd.z};
         while (cursor < a.n_slots && nfound < K) {
-          float3 x = slot_position(o, d, rd.w, ro.w, cursor);
-          int cell = cell_of(a.box, x);
+          const float3 x = slot_position(o, d, rd.w, ro.w, cursor);
+          const int cell = cell_of(a.box, x);
           ++n_marched;
-          if ((__ldg(a.occ + (cell >> 5)) >> (cell & 31)) & 1u) slots[nfound++] = cursor;
+          if ((__ldg(a.occ + (cell >> 5)) >> (cell & 31)) & 1u) {
+#pragma unroll
+            for (int q = 0; q < K; ++q)
+              if (q == nfound) slots[q] = cursor;
+            ++nfound;
+          }
           ++cursor;
         }
         if (nfound == 0) {  // exhausted: write the pixel
@@ -399,8 +444,8 @@ __global__ void __launch_bounds__(kRenderThreads) render_kernel(const RenderArgs
             cursor = 0;
             if (make_ray(a.cam, sB0inv, a.box, u, v, o, d, tn, tf)) {
               ++n_hit;
-              ray_o[tid] = make_float4(o[0], o[1], o[2], slot_delta(tn, tf, a.n_slots));
-              ray_d[tid] = make_float4(d[0], d[1], d[2], tn);
+              ray_o[lane] = make_float4(o[0], o[1], o[2], slot_delta(tn, tf, a.n_slots));
+              ray_d[lane] = make_float4(d[0], d[1], d[2], tn);
               has_ray = true;
             } else {
               a.rgb[3 * pix] = 0.f;
@@ -412,58 +457,58 @@ __global__ void __launch_bounds__(kRenderThreads) render_kernel(const RenderArgs
         }
       }
     }
-    // ---- 2. pack samples (block exclusive scan of nfound)
+    // ---- 2. pack samples (warp exclusive scan of nfound)
     int incl = nfound;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      int t = __shfl_up_sync(kFull, incl, o);
+      const int t = __shfl_up_sync(kFull, incl, o);
       if (lane >= o) incl += t;
     }
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    if (tid < 32) {
-      int v = tid < kRenderThreads / 32 ? s_warp[tid] : 0;
-      int inc = v;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        int t = __shfl_up_sync(kFull, inc, o);
-        if (tid >= o) inc += t;
-      }
-      if (tid < kRenderThreads / 32) s_warp[tid] = inc - v;
-      if (tid == kRenderThreads / 32 - 1) s_warp[kRenderThreads / 32] = inc;
-    }
-    __syncthreads();
-    const int total = s_warp[kRenderThreads / 32];
-    const int offset = s_warp[warp] + incl - nfound;
-    if (total == 0) break;  // no ray in this CTA has work and the queue is drained
+    const int total = __shfl_sync(kFull, incl, 31);
+    const int offset = incl - nfound;
+    if (total == 0) break;  // no ray of this warp has work and the queue is drained
 #pragma unroll
     for (int j = 0; j < K; ++j)
       if (j < nfound) {
-        s_ray[offset + j] = tid;
+        s_ray[offset + j] = lane;
         s_slot[offset + j] = slots[j];
       }
     n_occ += nfound;
-    __syncthreads();
-    // ---- 3. evaluate samples, 32 per warp step
-    for (int base = warp * 32; base < total; base += kRenderThreads) {
-      const int sidx = base + lane;
-      const bool active = sidx < total;
-      float3 xn = make_float3(0.f, 0.f, 0.f);
-      if (active) {
-        const int owner = s_ray[sidx];
-        float4 ro = ray_o[owner], rd = ray_d[owner];
-        const float o[3] = {ro.x, ro.y, ro.z}, d[3] = {rd.x, rd.y, rd.z};
-        xn = slot_position(o, d, rd.w, ro.w, s_slot[sidx]);
+    __syncwarp();
+    // ---- 3. evaluate samples, 32 * kNS per step (kNS per lane)
+    for (int base = 0; base < total; base += 32 * kNS) {
+      bool act[kNS];
+      float3 xn[kNS];
+      const float4* Ms[kNS];
+      const float* Ns[kNS];
+      PosedOut r[kNS];
+#pragma unroll
+      for (int q = 0; q < kNS; ++q) {
+        const int sidx = base + q * 32 + lane;
+        act[q] = sidx < total;
+        xn[q] = make_float3(0.f, 0.f, 0.f);
+        if (act[q]) {
+          const int owner = s_ray[sidx];
+          const float4 ro = ray_o[owner], rd = ray_d[owner];
+          const float o[3] = {ro.x, ro.y, ro.z}, d[3] = {rd.x, rd.y, rd.z};
+          xn[q] = slot_position(o, d, rd.w, ro.w, s_slot[sidx]);
+        }
+        Ms[q] = a.P.S.M;
+        Ns[q] = sm.sNinv;
       }
-      PosedOut r = posed_field_warp(a.P.S, a.P.F, a.P.cfg, sm.sNinv, sm.sw, sm.roots, active, xn, st);
-      if (active) s_res[sidx] = make_float4(r.start >= 0 ? r.sigma : 0.f, r.rgb.x, r.rgb.y, r.rgb.z);
+      posed_field_warp_n<kNS>(a.P.S, Ms, a.P.F, a.P.cfg, Ns, sm.sw, sm.roots, act, xn, r, st);
+#pragma unroll
+      for (int q = 0; q < kNS; ++q) {
+        const int sidx = base + q * 32 + lane;
+        if (act[q]) s_res[sidx] = make_float4(r[q].start >= 0 ? r[q].sigma : 0.f, r[q].rgb.x, r[q].rgb.y, r[q].rgb.z);
+      }
     }
-    __syncthreads();
+    __syncwarp();
     // ---- 4. composite this ray's samples, alpha_i = 1 - exp(-sigma_i delta)
     if (nfound > 0) {
-      const float dt = ray_o[tid].w;
+      const float dt = ray_o[lane].w;
       for (int j = 0; j < nfound; ++j) {
-        float4 sres = s_res[offset + j];
+        const float4 sres = s_res[offset + j];
         if (sres.x > 0.f) {
           const float sd = sres.x * dt;
           const float w = expf(-depth) * -expm1f(-sd);  // T_i alpha_i
@@ -479,7 +524,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_kernel(const RenderArgs
         }
       }
     }
-    __syncthreads();
+    __syncwarp();
   }
   if (a.stats) {
     flush_stats(a.stats, ST_RAYS, n_rays);

@@ -1,0 +1,445 @@
+// Training step of the articulated radiance-field path: L2 photometric loss and
+// its hand-written backward (sm_103a, fp32).
+//
+//   train_march_kernel      world rays -> normalised space of each ray's pose,
+//                           occupied slots, compacted sample list
+//   train_sample_kernel     posed field f'(x') at every sample (same warp-level
+//                           correspondence search as rendering, per-lane pose)
+//   train_composite_kernel  per ray: front-to-back compositing, loss, and its
+//                           reverse: dL/dsigma_i, dL/dc_i (Sec. 3.2, Eq. 6)
+//   train_backward_kernel   per sample: recomputed hash encoding and MLP
+//                           activations, MLP backward to the features, hash-table
+//                           scatter-add, canonical-position gradient, and the
+//                           implicit-function gradient through the root
+//                           (lambda = J^-T dL/dx*) to bone transforms and the
+//                           skinning-weight grid
+//   mlp_grad_kernel         weight gradients dW = sum_s dH_s^T A_s as split-K
+//                           reductions over the samples
+//
+// Per-sample activations are recomputed from x* in the backward (nothing of the
+// MLP is kept from the forward); the backward writes them once, next to their
+// gradients, for the weight-gradient reduction.
+#include "ia_internal.h"
+
+namespace ia {
+
+constexpr int kActF = 0, kActH1 = kIn, kActH2 = kActH1 + kWidth, kActD1 = kActH2 + kWidth,
+              kActD2 = kActD1 + kWidth, kActDO = kActD2 + kWidth;
+
+// ---------------------------------------------------------------------------
+
+__global__ void train_march_kernel(const TrainArgs a) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= a.n_rays) return;
+  const int pose = a.pose[r];
+  a.ray_n[r] = 0;
+  a.ray_dt[r] = 0.f;
+  if (pose < 0 || pose >= a.n_poses) return;
+  const float ow[3] = {a.origin[3 * r], a.origin[3 * r + 1], a.origin[3 * r + 2]};
+  const float dw[3] = {a.direction[3 * r], a.direction[3 * r + 1], a.direction[3 * r + 2]};
+  float o[3], d[3], tn, tf;
+  if (!normalise_and_clip(a.B0inv + 12 * (size_t)pose, a.box, ow, dw, o, d, tn, tf)) return;
+  const float dt = slot_delta(tn, tf, a.n_slots);
+  int n = 0;
+  for (int i = 0; i < a.n_slots; ++i) {
+    const int cell = cell_of(a.box, slot_position(o, d, tn, dt, i));
+    n += (__ldg(a.occ + (cell >> 5)) >> (cell & 31)) & 1u;
+  }
+  a.ray_n[r] = n;
+  a.ray_dt[r] = dt;
+  if (n == 0) return;
+  int base = atomicAdd(a.count, n), j = 0;
+  for (int i = 0; i < a.n_slots; ++i) {
+    const float3 x = slot_position(o, d, tn, dt, i);
+    const int cell = cell_of(a.box, x);
+    if ((__ldg(a.occ + (cell >> 5)) >> (cell & 31)) & 1u) {
+      a.s_pos[base + j] = make_float4(x.x, x.y, x.z, __int_as_float(pose));
+      a.ray_idx[(size_t)r * a.n_slots + j] = base + j;
+      ++j;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) train_sample_kernel(const TrainArgs a) {
+  extern __shared__ float4 smem4[];
+  float* sw = reinterpret_cast<float*>(smem4);
+  float4* roots = reinterpret_cast<float4*>(sw + kMlpPadT);
+  stage_mlp(a.P.mlp, a.P.n_in, sw);
+  __syncthreads();
+  const int n = *a.count;
+  const int lane = threadIdx.x & 31;
+  SampleStats st;
+  const int warp_id = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int n_warps = gridDim.x * (blockDim.x >> 5);
+  for (int base = warp_id * 32 * kNS; base < n; base += n_warps * 32 * kNS) {
+    bool act[kNS];
+    float3 xn[kNS];
+    const float4* Ms[kNS];
+    const float* Ns[kNS];
+    PosedOut o[kNS];
+#pragma unroll
+    for (int q = 0; q < kNS; ++q) {
+      const int s = base + q * 32 + lane;
+      act[q] = s < n;
+      const float4 p = act[q] ? a.s_pos[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const int pose = act[q] ? __float_as_int(p.w) : 0;
+      xn[q] = make_float3(p.x, p.y, p.z);
+      Ms[q] = a.P.S.M + (size_t)pose * a.V * 3;
+      Ns[q] = a.P.Ninv + (size_t)pose * a.P.cfg.nb * 12;
+    }
+    posed_field_warp_n<kNS>(a.P.S, Ms, a.P.F, a.P.cfg, Ns, sw, roots, act, xn, o, st);
+#pragma unroll
+    for (int q = 0; q < kNS; ++q) {
+      const int s = base + q * 32 + lane;
+      if (!act[q]) continue;
+      const bool has = o[q].start >= 0;
+      a.s_out[s] = make_float4(has ? o[q].sigma : 0.f, o[q].rgb.x, o[q].rgb.y, o[q].rgb.z);
+      a.s_x[s] = make_float4(o[q].xstar.x, o[q].xstar.y, o[q].xstar.z, has ? 1.f : 0.f);
+    }
+  }
+}
+
+// front-to-back compositing of one ray, the loss, and the reverse sweep
+//   dL/dc_i = T_i alpha_i g,  dL/dsigma_i = delta (T_{i+1} c_i.g - g.(C - C_{<=i}))
+__global__ void train_composite_kernel(const TrainArgs a) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = r < a.n_rays;
+  const int n = active ? a.ray_n[r] : 0;
+  const float dt = active ? a.ray_dt[r] : 0.f;
+  const int* idx = a.ray_idx + (size_t)(active ? r : 0) * a.n_slots;
+  float C[3] = {0.f, 0.f, 0.f}, depth = 0.f;
+  for (int j = 0; j < n; ++j) {
+    const float4 o = a.s_out[idx[j]];
+    if (o.x > 0.f) {
+      const float sd = o.x * dt;
+      const float w = expf(-depth) * -expm1f(-sd);
+      C[0] = fmaf(w, o.y, C[0]);
+      C[1] = fmaf(w, o.z, C[1]);
+      C[2] = fmaf(w, o.w, C[2]);
+      depth += sd;
+    }
+  }
+  const float inv_n = 1.f / (float)a.n_rays;
+  float g[3], l = 0.f;
+  for (int k = 0; k < 3; ++k) {
+    const float e = active ? C[k] - a.target[3 * r + k] : 0.f;
+    l = fmaf(e, e, l);
+    g[k] = 2.f * e * inv_n;
+    if (active && a.rgb_out) a.rgb_out[3 * r + k] = C[k];
+  }
+  float lw = l * inv_n;  // loss = (1/n) sum_rays sum_channels (C - C_target)^2
+  for (int o = 16; o > 0; o >>= 1) lw += __shfl_down_sync(kFull, lw, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(a.loss, lw);
+  if (!active) return;
+  float Cle[3] = {0.f, 0.f, 0.f};
+  depth = 0.f;
+  for (int j = 0; j < n; ++j) {
+    const int s = idx[j];
+    const float4 o = a.s_out[s];
+    if (!(o.x > 0.f)) {
+      a.s_grad[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
+    }
+    const float sd = o.x * dt;
+    const float T = expf(-depth), Tn = expf(-(depth + sd)), w = T * -expm1f(-sd);
+    Cle[0] = fmaf(w, o.y, Cle[0]);
+    Cle[1] = fmaf(w, o.z, Cle[1]);
+    Cle[2] = fmaf(w, o.w, Cle[2]);
+    const float cg = o.y * g[0] + o.z * g[1] + o.w * g[2];
+    const float rest = g[0] * (C[0] - Cle[0]) + g[1] * (C[1] - Cle[1]) + g[2] * (C[2] - Cle[2]);
+    a.s_grad[s] = make_float4(dt * (Tn * cg - rest), w * g[0], w * g[1], w * g[2]);
+    depth += sd;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Per-sample backward
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(128) train_backward_kernel(const TrainArgs a) {
+  __shared__ __align__(16) float sw[kMlpPadT];
+  stage_mlp(a.P.mlp, a.P.n_in, sw);
+  __syncthreads();
+  const int n = *a.count;
+  const FieldDev& F = a.P.F;
+  const int nb = a.P.cfg.nb;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    float* act = a.act + (size_t)s * kActStride;
+    const float4 xs4 = a.s_x[s];
+    if (!(xs4.w > 0.f)) {  // no root: no gradient; zero rows keep the reduction exact
+      for (int q = 0; q < kActStride; ++q) act[q] = 0.f;
+      continue;
+    }
+    const float3 xs = make_float3(xs4.x, xs4.y, xs4.z);
+    const float4 gr = a.s_grad[s];
+    // ---- recompute the forward activations
+    float feat[kIn];
+    encode(F, xs, feat);
+#pragma unroll
+    for (int i = 0; i < kIn; ++i) act[kActF + i] = feat[i];
+    float h1[kWidth];
+    uint64_t m1 = 0;  // h1 > 0 mask
+#pragma unroll
+    for (int j = 0; j < kWidth; ++j) {
+      float acc = sw[kOffB1 + j];
+      const float4* row = reinterpret_cast<const float4*>(sw + kOffW1 + j * kIn);
+#pragma unroll
+      for (int i = 0; i < kIn / 4; ++i) {
+        float4 w = row[i];
+        acc = fmaf(w.x, feat[4 * i], fmaf(w.y, feat[4 * i + 1], fmaf(w.z, feat[4 * i + 2], fmaf(w.w, feat[4 * i + 3], acc))));
+      }
+      h1[j] = fmaxf(acc, 0.f);
+      if (acc > 0.f) m1 |= 1ull << j;
+      act[kActH1 + j] = h1[j];
+    }
+    float o0 = sw[kOffB3], o1 = sw[kOffB3 + 1], o2 = sw[kOffB3 + 2], o3 = sw[kOffB3 + 3];
+    uint64_t m2 = 0;  // h2 > 0 mask
+    for (int j = 0; j < kWidth; ++j) {
+      float acc = sw[kOffB2 + j];
+      const float4* row = reinterpret_cast<const float4*>(sw + kOffW2 + j * kWidth);
+#pragma unroll
+      for (int i = 0; i < kWidth / 4; ++i) {
+        float4 w = row[i];
+        acc = fmaf(w.x, h1[4 * i], fmaf(w.y, h1[4 * i + 1], fmaf(w.z, h1[4 * i + 2], fmaf(w.w, h1[4 * i + 3], acc))));
+      }
+      const float h = fmaxf(acc, 0.f);
+      act[kActH2 + j] = h;
+      if (acc > 0.f) m2 |= 1ull << j;
+      const float4 w3 = reinterpret_cast<const float4*>(sw + kOffW3T)[j];
+      o0 = fmaf(w3.x, h, o0);
+      o1 = fmaf(w3.y, h, o1);
+      o2 = fmaf(w3.z, h, o2);
+      o3 = fmaf(w3.w, h, o3);
+    }
+    // ---- activations: sigma = exp(clamp(o0)), c = sigmoid
+    float dO[4];
+    {
+      const float sig = expf(fminf(fmaxf(o0, -15.f), 15.f));
+      dO[0] = (o0 > -15.f && o0 < 15.f) ? gr.x * sig : 0.f;
+      const float oc[3] = {o1, o2, o3}, gc[3] = {gr.y, gr.z, gr.w};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float sg = 1.f / (1.f + expf(-oc[c]));
+        dO[1 + c] = gc[c] * sg * (1.f - sg);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) act[kActDO + q] = dO[q];
+    // ---- MLP backward to the features
+    float dh2[kWidth];
+#pragma unroll
+    for (int j = 0; j < kWidth; ++j) {
+      const float4 w3 = reinterpret_cast<const float4*>(sw + kOffW3T)[j];
+      const float v = w3.x * dO[0] + w3.y * dO[1] + w3.z * dO[2] + w3.w * dO[3];
+      dh2[j] = ((m2 >> j) & 1ull) ? v : 0.f;
+      act[kActD2 + j] = dh2[j];
+    }
+    float dh1[kWidth];
+#pragma unroll
+    for (int i = 0; i < kWidth; ++i) dh1[i] = 0.f;
+#pragma unroll
+    for (int j = 0; j < kWidth; ++j) {
+      const float4* row = reinterpret_cast<const float4*>(sw + kOffW2 + j * kWidth);
+      const float d = dh2[j];
+#pragma unroll
+      for (int i = 0; i < kWidth / 4; ++i) {
+        float4 w = row[i];
+        dh1[4 * i] = fmaf(w.x, d, dh1[4 * i]);
+        dh1[4 * i + 1] = fmaf(w.y, d, dh1[4 * i + 1]);
+        dh1[4 * i + 2] = fmaf(w.z, d, dh1[4 * i + 2]);
+        dh1[4 * i + 3] = fmaf(w.w, d, dh1[4 * i + 3]);
+      }
+    }
+    float dfeat[kIn];
+#pragma unroll
+    for (int i = 0; i < kIn; ++i) dfeat[i] = 0.f;
+#pragma unroll
+    for (int j = 0; j < kWidth; ++j) {
+      const float d = ((m1 >> j) & 1ull) ? dh1[j] : 0.f;
+      act[kActD1 + j] = d;
+      const float4* row = reinterpret_cast<const float4*>(sw + kOffW1 + j * kIn);
+#pragma unroll
+      for (int i = 0; i < kIn / 4; ++i) {
+        float4 w = row[i];
+        dfeat[4 * i] = fmaf(w.x, d, dfeat[4 * i]);
+        dfeat[4 * i + 1] = fmaf(w.y, d, dfeat[4 * i + 1]);
+        dfeat[4 * i + 2] = fmaf(w.z, d, dfeat[4 * i + 2]);
+        dfeat[4 * i + 3] = fmaf(w.w, d, dfeat[4 * i + 3]);
+      }
+    }
+    // ---- hash encoding backward: scatter-add into the table gradient, and dL/dx*
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    {
+      const float u[3] = {(xs.x - F.cmin[0]) * F.inv_ext[0], (xs.y - F.cmin[1]) * F.inv_ext[1],
+                          (xs.z - F.cmin[2]) * F.inv_ext[2]};
+#pragma unroll
+      for (int l = 0; l < kMaxLevels; ++l) {
+        if (l < F.L) {
+          const Level lv = F.lv[l];
+          int p0[3];
+          float f[3];
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            const float pos = u[q] * (float)lv.res;
+            int c = (int)floorf(pos);
+            c = min(max(c, 0), lv.res - 1);
+            p0[q] = c;
+            f[q] = pos - (float)c;
+          }
+          const float d0 = dfeat[2 * l], d1 = dfeat[2 * l + 1];
+          const float sx = (float)lv.res * F.inv_ext[0], sy = (float)lv.res * F.inv_ext[1],
+                      sz = (float)lv.res * F.inv_ext[2];
+#pragma unroll
+          for (int corner = 0; corner < 8; ++corner) {
+            const int cx = corner & 1, cy = (corner >> 1) & 1, cz = (corner >> 2) & 1;
+            const float wx = cx ? f[0] : 1.f - f[0], wy = cy ? f[1] : 1.f - f[1], wz = cz ? f[2] : 1.f - f[2];
+            const uint32_t e = lv.offset + vertex_index(lv, p0[0] + cx, p0[1] + cy, p0[2] + cz);
+            const float w = wx * wy * wz;
+            atomicAdd(a.g_table + 2 * (size_t)e, w * d0);
+            atomicAdd(a.g_table + 2 * (size_t)e + 1, w * d1);
+            const float2 t = __ldg(F.table + e);
+            const float proj = t.x * d0 + t.y * d1;
+            gx = fmaf(proj * (cx ? 1.f : -1.f) * wy * wz, sx, gx);
+            gy = fmaf(proj * (cy ? 1.f : -1.f) * wx * wz, sy, gy);
+            gz = fmaf(proj * (cz ? 1.f : -1.f) * wx * wy, sz, gz);
+          }
+        }
+      }
+    }
+    // ---- implicit function theorem: lambda = J(x*)^-T dL/dx*
+    const int pose = __float_as_int(a.s_pos[s].w);
+    const float4* M = a.P.S.M + (size_t)pose * a.V * 3;
+    float Mx[12], J[9], Hi[9];
+    blend_value_jac(a.P.S, M, xs, Mx, J);
+    if (!inv3(J, Hi)) continue;
+    const float l0 = Hi[0] * gx + Hi[3] * gy + Hi[6] * gz;
+    const float l1 = Hi[1] * gx + Hi[4] * gy + Hi[7] * gz;
+    const float l2 = Hi[2] * gx + Hi[5] * gy + Hi[8] * gz;
+    const float xb[4] = {xs.x, xs.y, xs.z, 1.f};
+    // trilinear coefficients of x* in the skinning grid (as the forward blends them)
+    CellCoord cc = skin_cell(a.P.S, xs);
+    const float* Np = a.N + (size_t)pose * nb * 12;
+    float* gB = a.g_bones + (size_t)pose * nb * 12;
+    for (int k = 0; k < nb; ++k) {
+      float wk = 0.f;
+#pragma unroll
+      for (int corner = 0; corner < 8; ++corner) {
+        const int v = corner_index(a.P.S, cc.base, corner);
+        const float cw = ((corner & 1) ? cc.f[0] : 1.f - cc.f[0]) * (((corner >> 1) & 1) ? cc.f[1] : 1.f - cc.f[1]) *
+                         (((corner >> 2) & 1) ? cc.f[2] : 1.f - cc.f[2]);
+        wk = fmaf(cw, __ldg(a.skin + (size_t)v * nb + k), wk);
+      }
+      // dL/dN_k[a][b] = -lambda_a w_k [x*;1]_b
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        atomicAdd(gB + k * 12 + b, -l0 * wk * xb[b]);
+        atomicAdd(gB + k * 12 + 4 + b, -l1 * wk * xb[b]);
+        atomicAdd(gB + k * 12 + 8 + b, -l2 * wk * xb[b]);
+      }
+      // dL/dW(v, k) = -c_v lambda . (N_k [x*;1])
+      const float* Nk = Np + 12 * k;
+      const float ln = l0 * (Nk[0] * xb[0] + Nk[1] * xb[1] + Nk[2] * xb[2] + Nk[3]) +
+                       l1 * (Nk[4] * xb[0] + Nk[5] * xb[1] + Nk[6] * xb[2] + Nk[7]) +
+                       l2 * (Nk[8] * xb[0] + Nk[9] * xb[1] + Nk[10] * xb[2] + Nk[11]);
+#pragma unroll
+      for (int corner = 0; corner < 8; ++corner) {
+        const int v = corner_index(a.P.S, cc.base, corner);
+        const float cw = ((corner & 1) ? cc.f[0] : 1.f - cc.f[0]) * (((corner >> 1) & 1) ? cc.f[1] : 1.f - cc.f[1]) *
+                         (((corner >> 2) & 1) ? cc.f[2] : 1.f - cc.f[2]);
+        atomicAdd(a.g_skin + (size_t)v * nb + k, -cw * ln);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradients: gW1 = sum_s dH1_s^T F_s, gW2 = sum_s dH2_s^T H1_s,
+// gW3 = sum_s dO_s^T H2_s, biases = sums of dH1, dH2, dO.  Split-K over samples:
+// each block reduces a contiguous chunk in registers (32-sample tiles staged in
+// shared memory) and adds its partial sums to the gradient once.
+// ---------------------------------------------------------------------------
+
+constexpr int kTileS = 32;
+
+__global__ void __launch_bounds__(256) mlp_grad_kernel(const TrainArgs a) {
+  __shared__ float tile[kTileS][kActStride + 1];
+  const int n = *a.count;
+  const int chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int s0 = blockIdx.x * chunk, s1 = min(n, s0 + chunk);
+  const int t = threadIdx.x;
+  const int n_in = a.P.n_in;
+  // ownership: gW2 4x4 block, gW1 4x2 block, gW3 one entry, one bias entry
+  const int i2 = (t / 16) * 4, j2 = (t % 16) * 4;
+  const int i1 = (t / 16) * 4, j1 = (t % 16) * 2;
+  const int o3 = t / 64, j3 = t % 64;
+  float acc2[16], acc1[8], acc3 = 0.f, accb = 0.f;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) acc2[q] = 0.f;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) acc1[q] = 0.f;
+  for (int base = s0; base < s1; base += kTileS) {
+    const int m = min(kTileS, s1 - base);
+    __syncthreads();
+    for (int q = t; q < m * kActStride; q += blockDim.x) {
+      const int r = q / kActStride, c = q % kActStride;
+      tile[r][c] = a.act[(size_t)(base + r) * kActStride + c];
+    }
+    __syncthreads();
+    for (int r = 0; r < m; ++r) {
+      const float* T = tile[r];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        const float d = T[kActD2 + i2 + x];
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc2[4 * x + y] = fmaf(d, T[kActH1 + j2 + y], acc2[4 * x + y]);
+        const float d1 = T[kActD1 + i1 + x];
+#pragma unroll
+        for (int y = 0; y < 2; ++y) acc1[2 * x + y] = fmaf(d1, T[kActF + j1 + y], acc1[2 * x + y]);
+      }
+      acc3 = fmaf(T[kActDO + o3], T[kActH2 + j3], acc3);
+      if (t < kWidth) accb += T[kActD1 + t];
+      else if (t < 2 * kWidth) accb += T[kActD2 + t - kWidth];
+      else if (t < 2 * kWidth + 4) accb += T[kActDO + t - 2 * kWidth];
+    }
+  }
+  if (s0 >= s1) return;
+  float* gW1 = a.g_mlp;
+  float* gb1 = gW1 + kWidth * n_in;
+  float* gW2 = gb1 + kWidth;
+  float* gb2 = gW2 + kWidth * kWidth;
+  float* gW3 = gb2 + kWidth;
+  float* gb3 = gW3 + 4 * kWidth;
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+#pragma unroll
+    for (int y = 0; y < 4; ++y) atomicAdd(gW2 + (i2 + x) * kWidth + j2 + y, acc2[4 * x + y]);
+#pragma unroll
+    for (int y = 0; y < 2; ++y)
+      if (j1 + y < n_in) atomicAdd(gW1 + (i1 + x) * n_in + j1 + y, acc1[2 * x + y]);
+  }
+  atomicAdd(gW3 + o3 * kWidth + j3, acc3);
+  if (t < kWidth) atomicAdd(gb1 + t, accb);
+  else if (t < 2 * kWidth) atomicAdd(gb2 + t - kWidth, accb);
+  else if (t < 2 * kWidth + 4) atomicAdd(gb3 + t - 2 * kWidth, accb);
+}
+
+cudaError_t launch_train(const TrainArgs& a, int num_sms, cudaStream_t s) {
+  cudaError_t e;
+  const int rb = (a.n_rays + 127) / 128;
+  train_march_kernel<<<rb, 128, 0, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const size_t smem = sizeof(float) * kMlpPadT + sizeof(float4) * kMaxRoots * kNS * 256;
+  if ((e = cudaFuncSetAttribute(train_sample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+      cudaSuccess)
+    return e;
+  train_sample_kernel<<<num_sms * 2, 256, smem, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  train_composite_kernel<<<rb, 128, 0, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  train_backward_kernel<<<num_sms * 4, 128, 0, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  mlp_grad_kernel<<<num_sms * 2, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace ia

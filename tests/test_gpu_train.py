@@ -1,0 +1,113 @@
+"""GPU training step (ia_train_step) against the fp64 oracle's loss and gradient.
+
+Both sides composite every occupied sample (no early termination) over the same
+occupancy grid (the oracle's union over the batch's poses, installed on the GPU
+as the render grid) and the same seeded rays.  Rays the oracle flags as marginal
+are removed from the batch before the comparison.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic as S
+from gpu_helpers import ATOL_RGB, RTOL_RGB, close, make_ctx
+from oracle import grad as G
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+# Gradient tolerance: fp32 accumulation in a different order (atomics) and fp32
+# roots/activations against fp64; compared per parameter group as a relative L2
+# error and per element against the group's scale.
+GRAD_REL_L2 = 2e-3
+GRAD_ELEM = 1e-3
+
+
+@pytest.fixture(scope="module")
+def ia():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2212_10550_b300 as ia
+    ia.lib()
+    return ia
+
+
+def _case(config, n_poses, n_rays):
+    sc = S.make_scene(config, 0)
+    table, mlp = S.make_field(sc, 0)
+    om = O.OracleModel(sc, table, mlp)
+    poses = [S.make_pose(sc, i) for i in range(n_poses)]
+    op = [om.pose(*p) for p in poses]
+    occ = np.zeros((sc.occ_res ** 3 + 31) // 32, np.uint32)
+    for p in op:
+        occ |= om.occupancy(p)[1]
+    rb = S.make_ray_batch(sc, n_rays, n_poses, seed=2)
+    _, _, flags, _ = G.train(om, op, occ, rb["origin"], rb["direction"], rb["pose"], rb["target"], grad=False)
+    keep = flags == 0
+    rays = {k: rb[k][keep] for k in ("origin", "direction", "pose", "target")}
+    return sc, table, mlp, om, poses, op, occ, rays, int((~keep).sum())
+
+
+def _run_gpu(ia, sc, table, mlp, poses, occ, rays):
+    ctx = make_ctx(ia, torch, sc, table, mlp)
+    ia.ia_set_pose(ctx, np.stack([p[0] for p in poses]), np.stack([p[1] for p in poses]))
+    ia.ia_set_occupancy(ctx, occ)
+    nt, nm = ia.ia_param_sizes(ctx)
+    g = dict(table=torch.zeros(nt, device="cuda"), mlp=torch.zeros(nm, device="cuda"),
+             skin=torch.zeros(sc.skin_res ** 3 * sc.n_bones, device="cuda"),
+             bones=torch.zeros(len(poses) * sc.n_bones * 12, device="cuda"))
+    dev = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in rays.items()}
+    loss = torch.zeros(1, device="cuda")
+    rgb = torch.zeros(len(rays["pose"]), 3, device="cuda")
+    ia.ia_train_step(ctx, dev["origin"], dev["direction"], dev["pose"], dev["target"], loss, g,
+                     occ_grid=ia.IA_OCC_POSE, rgb_out=rgb)
+    torch.cuda.synchronize()
+    out = {k: v.cpu().numpy().astype(np.float64) for k, v in g.items()}
+    # a second step on the same inputs overwrites the gradients with the same values
+    loss2 = torch.zeros(1, device="cuda")
+    ia.ia_train_step(ctx, dev["origin"], dev["direction"], dev["pose"], dev["target"], loss2, g,
+                     occ_grid=ia.IA_OCC_POSE)
+    torch.cuda.synchronize()
+    again = {k: v.cpu().numpy().astype(np.float64) for k, v in g.items()}
+    ia.ia_destroy(ctx)
+    return float(loss.item()), float(loss2.item()), rgb.cpu().numpy(), out, again
+
+
+def _compare(sc, om, op, occ, rays, gpu):
+    loss, loss2, rgb, g, g2 = gpu
+    ref_loss, ref_rgb, _, ref = G.train(om, op, occ, rays["origin"], rays["direction"], rays["pose"],
+                                        rays["target"])
+    print(f"loss gpu {loss:.8e} oracle {ref_loss:.8e}")
+    assert abs(loss - ref_loss) <= 1e-5 * ref_loss
+    assert abs(loss2 - loss) <= 1e-6 * loss
+    assert close(rgb, ref_rgb, RTOL_RGB, ATOL_RGB).all()
+    ref_flat = {k: v.reshape(-1) for k, v in ref.items()}
+    for k in ("table", "mlp", "skin", "bones"):
+        a, b = g[k], ref_flat[k]
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        worst = np.abs(a - b).max() / max(np.abs(b).max(), 1e-30)
+        print(f"grad {k}: rel L2 {rel:.2e}, worst element / scale {worst:.2e}, nonzero {np.count_nonzero(b)}")
+        assert np.count_nonzero(b) > 0
+        assert rel <= GRAD_REL_L2, k
+        assert worst <= GRAD_ELEM, k
+        np.testing.assert_allclose(g2[k], a, rtol=1e-3, atol=1e-6 * max(np.abs(b).max(), 1e-30))
+
+
+def test_train_step_tiny(ia):
+    sc, table, mlp, om, poses, op, occ, rays, dropped = _case("tiny", 2, 3000)
+    print(f"{len(rays['pose'])} rays, {dropped} flagged rays dropped")
+    _compare(sc, om, op, occ, rays, _run_gpu(ia, sc, table, mlp, poses, occ, rays))
+
+
+def test_train_step_full_size(ia):
+    sc, table, mlp, om, poses, op, occ, rays, dropped = _case("full", 4, 2048)
+    print(f"{len(rays['pose'])} rays, {dropped} flagged rays dropped")
+    _compare(sc, om, op, occ, rays, _run_gpu(ia, sc, table, mlp, poses, occ, rays))
+
+
+def test_train_step_bad_pose_index_is_an_empty_ray(ia):
+    sc, table, mlp, om, poses, op, occ, rays, _ = _case("tiny", 2, 500)
+    rays = {k: v.copy() for k, v in rays.items()}
+    rays["pose"][:10] = 7  # only poses 0 and 1 exist
+    _, _, rgb, _, _ = _run_gpu(ia, sc, table, mlp, poses, occ, rays)
+    assert np.all(rgb[:10] == 0)

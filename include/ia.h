@@ -5,10 +5,10 @@
  * 2212.10550): a canonical radiance field f: x -> (sigma, c) held in a
  * multiresolution hash grid decoded by a small MLP (Sec. 3.1, Eq. 1-2), a
  * skinning-weight voxel grid with linear blend skinning x' = sum_i w_i(x) B_i x
- * (Sec. 3.1, Eq. 3-5), the canonical correspondence x* of a posed point found by
+ * (Sec. 3.1, Eq. 5-7), the canonical correspondence x* of a posed point found by
  * bone-wise Broyden root finding (Sec. 3.1, Fast-SNARF), volume rendering
  * C = sum_i alpha_i prod_{j<i}(1 - alpha_j) c_i with alpha_i = 1 - exp(-sigma_i
- * delta_i) (Sec. 3.2, Eq. 6; the sign of the exponent is printed without its
+ * delta_i) (Sec. 3.2, Eq. 8; the sign of the exponent is printed without its
  * minus in the paper), and a per-pose occupancy grid that skips empty space in a
  * normalised space with the root's rigid motion removed (Sec. 3.3).
  *
@@ -110,7 +110,7 @@ const char *ia_last_error(const ia_ctx *ctx);
 /* Library version string. */
 const char *ia_version(void);
 
-/* Skeleton and skinning-weight grid (Sec. 3.1, Eq. 3-5).
+/* Skeleton and skinning-weight grid (Sec. 3.1, Eq. 5-7).
  *  parent      [n_bones] int32, host; -1 for bone 0 (the root), parent[k] < k.
  *  rest_joints [n_bones][3] fp64, host; canonical rest-pose joint positions.
  *  skin_grid   [skin_res]^3 x [n_bones] fp32, host or device, index
@@ -219,7 +219,7 @@ typedef struct ia_grads {
  *   loss = (1 / n) sum_rays sum_channels (C - target)^2
  * is added to *loss (device scalar; the caller zeroes it).  The backward is
  * exact reverse mode: compositing, activations, MLP, hash-table scatter-add, and
- * the implicit-function gradient through the root x* of LBS(x*) = x' (Eq. 5):
+ * the implicit-function gradient through the root x* of LBS(x*) = x' (Eq. 7):
  * with lambda = J(x*)^-T dL/dx* (J the analytic Jacobian),
  *   dL/dN_k = -lambda w_k(x*) [x*;1]^T,  dL/dW(v, k) = -c_v(x*) lambda . N_k [x*;1].
  * The selected root is treated as constant.  rgb_out [n][3] (device) may be

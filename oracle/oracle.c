@@ -178,7 +178,7 @@ void or_skin(const or_model *m, const double x[3], double *w, double *dw) {
   }
 }
 
-/* Eq. 5 with the normalised-space transforms; J = sum w_i R_i + sum (N_i x) dw_i^T */
+/* Eq. 7 with the normalised-space transforms; J = sum w_i R_i + sum (N_i x) dw_i^T */
 void or_lbs(const or_model *m, const or_pose *p, const double x[3], double y[3], double *J) {
   double w[OR_MAX_BONES], dw[OR_MAX_BONES * 3];
   or_skin(m, x, w, J ? dw : NULL);
@@ -523,7 +523,7 @@ static void slot_position(const float o[3], const float d[3], float tn, float dt
 }
 
 /* ------------------------------------------------------------------------- */
-/* Volume rendering (Eq. 6, with alpha = 1 - exp(-sigma delta))               */
+/* Volume rendering (Eq. 8, with alpha = 1 - exp(-sigma delta))               */
 /* ------------------------------------------------------------------------- */
 
 static void render_ray(const or_model *m, const or_pose *p, const or_camera *c, const uint32_t *occ,

@@ -7,9 +7,9 @@
  * Every function follows the paper's definition step by step, in fp64, with the
  * readings the paper leaves open written out where they are used:
  *   Sec. 3.1, Eq. 1-2        canonical field f: x -> (sigma, c), hash grid + MLP
- *   Sec. 3.1, Eq. 3-5        skinning-weight voxel grid, linear blend skinning
- *   Sec. 3.1 (Fast-SNARF)    correspondence x* by root finding of Eq. 5
- *   Sec. 3.2, Eq. 6          ray samples and front-to-back compositing
+ *   Sec. 3.1, Eq. 5-7        skinning-weight voxel grid, linear blend skinning
+ *   Sec. 3.1 (Fast-SNARF)    correspondence x* by root finding of Eq. 7
+ *   Sec. 3.2, Eq. 8          ray samples and front-to-back compositing
  *   Sec. 3.3                 per-pose occupancy grid (threshold + dilation),
  *                            empty-space skipping, normalised space
  *
@@ -33,7 +33,7 @@ extern "C" {
 /* Everything the path reads.  Arrays are caller-owned, fp64 copies of the fp32
  * inputs the library receives (exact), except the skeleton rest pose (fp64). */
 typedef struct or_model {
-  int nb;                    /* number of bones n_b (Eq. 3) */
+  int nb;                    /* number of bones n_b (Eq. 5) */
   const int32_t *parent;     /* [nb]; -1 for the root; parents precede children */
   const double *rest;        /* [nb][3] rest-pose joint positions (canonical) */
   int rw;                    /* skinning grid vertices per axis */
@@ -92,9 +92,9 @@ typedef struct or_sample {
 
 /* Sec. 3.1 / Sec. 3.3: bone transforms from axis-angle pose and root translation. */
 void or_pose_chain(const or_model *m, const double *theta, const double *trans, or_pose *out);
-/* Eq. 3-4: trilinear skinning weights at canonical x (and d w / d x, [nb][3]). */
+/* Eq. 5-6: trilinear skinning weights at canonical x (and d w / d x, [nb][3]). */
 void or_skin(const or_model *m, const double x[3], double *w, double *dw);
-/* Eq. 5 in normalised space: y = sum_i w_i(x) N_i [x;1], and its Jacobian. */
+/* Eq. 7 in normalised space: y = sum_i w_i(x) N_i [x;1], and its Jacobian. */
 void or_lbs(const or_model *m, const or_pose *p, const double x[3], double y[3], double *J);
 /* Broyden root search of LBS(x) = xn from x0; returns 1 if it converged. */
 int or_broyden(const or_model *m, const or_pose *p, const double xn[3], const double x0[3],

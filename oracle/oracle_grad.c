@@ -6,11 +6,11 @@
  * mapped into the normalised space of the ray's pose.  Loss
  *   L = (1 / n) sum_rays sum_channels (C - C_target)^2.
  * Backward, in the reverse order of the forward:
- *   compositing (Eq. 6):  dL/dc_i = T_i alpha_i g,
+ *   compositing (Eq. 8):  dL/dc_i = T_i alpha_i g,
  *                         dL/dsigma_i = delta (T_{i+1} c_i.g - g.(C - C_{<=i}))
  *   activations, MLP (Eq. 1-2), hash-table entries (trilinear weights) and the
  *   canonical position x*;
- *   the root x* of g(x*, theta) = LBS(x*) - x' = 0 (Eq. 5) by the implicit
+ *   the root x* of g(x*, theta) = LBS(x*) - x' = 0 (Eq. 7) by the implicit
  *   function theorem: d(x*) / d(theta) = -J^-1 d(g) / d(theta), J the analytic
  *   Jacobian at x*, so with lambda = J^-T dL/dx*:
  *     dL/dN_k[a][b]  = -lambda_a w_k(x*) [x*;1]_b

@@ -248,3 +248,4 @@ def ia_train_step(ctx, origin, direction, pose, target, loss, grads, occ_grid=IA
     g.table, g.mlp, g.skin, g.bones = (_ptr(grads[k]) for k in ("table", "mlp", "skin", "bones"))
     _check(lib().ia_train_step(ctx, C.byref(b), occ_grid, _ptr(loss), _ptr(rgb_out), C.byref(g),
                                _stream(stream)), ctx)
+

@@ -2,7 +2,7 @@
 //
 //   blend_value / blend_value_jac   LBS in normalised space through the blended
 //                                   transform grid M(v) = sum_i W(v,i) N_i
-//                                   (Sec. 3.1, Eq. 5)
+//                                   (Sec. 3.1, Eq. 7)
 //   posed_field_warp                Fast-SNARF style correspondence search: bone-wise
 //                                   Broyden starts, one sample per lane, flattened
 //                                   so that all lanes gather M at the same step,

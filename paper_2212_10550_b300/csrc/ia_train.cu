@@ -6,7 +6,7 @@
 //   train_sample_kernel     posed field f'(x') at every sample (same warp-level
 //                           correspondence search as rendering, per-lane pose)
 //   train_composite_kernel  per ray: front-to-back compositing, loss, and its
-//                           reverse: dL/dsigma_i, dL/dc_i (Sec. 3.2, Eq. 6)
+//                           reverse: dL/dsigma_i, dL/dc_i (Sec. 3.2, Eq. 8)
 //   train_backward_kernel   per sample: recomputed hash encoding and MLP
 //                           activations, MLP backward to the features, hash-table
 //                           scatter-add, canonical-position gradient, and the

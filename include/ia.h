@@ -228,6 +228,26 @@ typedef struct ia_grads {
 ia_status ia_train_step(ia_ctx *ctx, const ia_batch *batch, int occ_grid, float *loss, float *rgb_out,
                         const ia_grads *grads, void *stream);
 
+/* Same result as ia_update_occupancy(ctx, pose, IA_OCC_POSE, NULL, bits_out,
+ * NULL, stream), for callers that cannot allocate device memory while they run:
+ * code whose device memory is owned by another allocator (a framework's caching
+ * pool, a fixed arena sized at start-up) or a frame loop in which a cudaMalloc,
+ * with its implicit device-wide synchronisation, would stall other streams.
+ * This call allocates nothing: the per-cell density scratch is a fixed array of
+ * 64^3 floats (1 MiB) compiled into the library, which every GPU that loads the
+ * library holds until the process exits.  The paper has no counterpart of this
+ * call; it is an interface convenience.
+ *  - occ_res above 64 returns IA_ERR_LIMIT (use ia_update_occupancy).
+ *  - The context's device must be current.  The first call on a device looks up
+ *    the array's device address (cudaGetSymbolAddress); make that first call
+ *    before any stream capture.
+ *  - All calls share the one array and it keeps the last call's densities:
+ *    every call rewrites the cells it reads before reading them, but calls that
+ *    overlap on the GPU (different streams, or different contexts on the same
+ *    device) race on it and must be serialised by the caller.
+ *  bits_out [R^3 / 32] uint32 device or NULL; the render grid is replaced. */
+ia_status ia_update_occupancy_static(ia_ctx *ctx, int pose, uint32_t *bits_out, void *stream);
+
 /* The sample set of ia_render without evaluating it (the indexing contract):
  * bit i of slot_mask[(v * W + u) * ceil(N / 32) + i / 32] is set iff slot i of
  * pixel (u, v) lies in an occupied cell of the render grid.  Without early

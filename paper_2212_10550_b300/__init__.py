@@ -85,6 +85,7 @@ def lib():
             "ia_render": [P, I, C.POINTER(Camera), P, P, C.POINTER(RenderStats), V],
             "ia_march_mask": [P, I, C.POINTER(Camera), P, V],
             "ia_train_step": [P, C.POINTER(Batch), I, P, P, C.POINTER(Grads), V],
+            "ia_update_occupancy_static": [P, I, P, V],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -249,3 +250,7 @@ def ia_train_step(ctx, origin, direction, pose, target, loss, grads, occ_grid=IA
     _check(lib().ia_train_step(ctx, C.byref(b), occ_grid, _ptr(loss), _ptr(rgb_out), C.byref(g),
                                _stream(stream)), ctx)
 
+
+def ia_update_occupancy_static(ctx, pose, bits_out=None, stream=None):
+    """Occupancy refresh that allocates nothing (fixed 64^3-cell scratch in the library)."""
+    _check(lib().ia_update_occupancy_static(ctx, pose, _ptr(bits_out), _stream(stream)), ctx)

@@ -5,6 +5,7 @@
 // message on failure; nothing here aborts the process.
 #include <cmath>
 #include <cstdarg>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -625,6 +626,67 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
   a.g_skin = g->skin;
   a.g_bones = g->bones;
   IA_CUDA(c, launch_train(a, c->num_sms, s), "ia_train_step: kernels");
+  return IA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Occupancy update without any allocation: the per-cell density scratch lives
+// in a fixed, file-scope device array instead of context memory.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr int kStaticOccRes = 64;  // largest grid the static scratch holds: 64^3 cells, 1 MiB
+static __device__ __align__(256) float g_occ_sigma_scratch[kStaticOccRes * kStaticOccRes * kStaticOccRes];
+
+constexpr int kMaxDevices = 64;
+float* g_occ_scratch_addr[kMaxDevices] = {};
+std::mutex g_occ_scratch_mu;
+
+// Device address of the static scratch on the current device, looked up once per
+// device.  In host code the array's name only stands in for the symbol, so the
+// address has to come from the runtime.
+cudaError_t static_scratch(int dev, float** out) {
+  std::lock_guard<std::mutex> lock(g_occ_scratch_mu);
+  if (!g_occ_scratch_addr[dev]) {
+    float* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_occ_sigma_scratch);
+    if (e != cudaSuccess) return e;
+    g_occ_scratch_addr[dev] = p;
+  }
+  *out = g_occ_scratch_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+ia_status ia_update_occupancy_static(ia_ctx* c, int pose, uint32_t* bits_out, void* stream) {
+  ia_status st = need_ready(c, pose, false);
+  if (st != IA_OK) return st;
+  const int R = c->cfg.occ_res;
+  if (R > kStaticOccRes)
+    return fail(c, IA_ERR_LIMIT, "occ_res %d exceeds the static scratch limit of %d (use ia_update_occupancy)", R,
+                kStaticOccRes);
+  int dev = -1;
+  IA_CUDA(c, cudaGetDevice(&dev), "ia_update_occupancy_static");
+  if (dev != c->device)
+    return fail(c, IA_ERR_STATE, "device %d is current but the context lives on device %d", dev, c->device);
+  if (dev < 0 || dev >= kMaxDevices) return fail(c, IA_ERR_LIMIT, "device index %d beyond %d", dev, kMaxDevices);
+  float* sigma = nullptr;
+  IA_CUDA(c, static_scratch(dev, &sigma), "ia_update_occupancy_static: cudaGetSymbolAddress");
+  cudaStream_t s = (cudaStream_t)stream;
+  // the density kernel writes all R^3 cells before the bits kernel reads them, so
+  // the scratch needs no clearing; cells past R^3 are never read
+  IA_CUDA(c, launch_occ_density(posed_args(c, pose), box_dev(c), sigma, nullptr, s),
+          "ia_update_occupancy_static: density");
+  IA_CUDA(c, launch_occ_bits(sigma, R, c->cfg.occ_dilate, c->cfg.occ_tau, c->d_occ, nullptr, s),
+          "ia_update_occupancy_static: bits");
+  c->have_occ = true;
+  if (bits_out) {
+    const size_t words = ((size_t)R * R * R + 31) / 32;
+    IA_CUDA(c, cudaMemcpyAsync(bits_out, c->d_occ, words * 4, cudaMemcpyDeviceToDevice, s),
+            "ia_update_occupancy_static");
+  }
   return IA_OK;
 }
 

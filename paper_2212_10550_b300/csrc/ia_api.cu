@@ -33,6 +33,7 @@ struct ia_ctx {
   int64_t n_entries = 0;
   Level levels[kMaxLevels]{};
   float* d_table = nullptr;
+  __half2* d_table_h = nullptr;  // fp16 shadow (reduced-precision field only)
   float* d_mlp = nullptr;
   bool have_params = false;
   // poses
@@ -146,6 +147,19 @@ PosedArgs posed_args(const ia_ctx* c, int pose) {
   a.Ninv = c->d_Ninv + (size_t)pose * c->nb * 12;
   a.mlp = c->d_mlp;
   a.n_in = c->n_in;
+  a.prec = c->cfg.precision;
+  a.table_h = c->d_table_h;
+  return a;
+}
+
+// field-only arguments (no pose needed)
+PosedArgs posed_args_params(const ia_ctx* c) {
+  PosedArgs a{};
+  a.F = field_dev(c);
+  a.mlp = c->d_mlp;
+  a.n_in = c->n_in;
+  a.prec = c->cfg.precision;
+  a.table_h = c->d_table_h;
   return a;
 }
 
@@ -215,7 +229,8 @@ ia_status ia_create(const ia_config* cfg, ia_ctx** out) {
   if (g.occ_dilate < 0 || g.occ_dilate > 4) return fail(nullptr, IA_ERR_ARG, "occ_dilate must be 0..4");
   if (!std::isfinite(g.early_stop_T) || g.early_stop_T >= 1.f)
     return fail(nullptr, IA_ERR_ARG, "early_stop_T must be finite and < 1");
-  if (g.precision != IA_FP32) return fail(nullptr, IA_ERR_ARG, "precision %d not available", g.precision);
+  if (g.precision != IA_FP32 && g.precision != IA_FP16 && g.precision != IA_BF16)
+    return fail(nullptr, IA_ERR_ARG, "precision %d not available", g.precision);
 
   ia_ctx* c = new ia_ctx();
   c->cfg = g;
@@ -243,6 +258,7 @@ ia_status ia_create(const ia_config* cfg, ia_ctx** out) {
   const size_t words = ((size_t)R * R * R + 31) / 32;
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = dalloc(&c->d_table, (size_t)off * 2);
+  if (e == cudaSuccess && g.precision != IA_FP32) e = dalloc(&c->d_table_h, (size_t)off);
   if (e == cudaSuccess) e = dalloc(&c->d_mlp, (size_t)kWidth * c->n_in + kWidth + kWidth * kWidth + kWidth + 4 * kWidth + 4);
   if (e == cudaSuccess) e = dalloc(&c->d_occ, words);
   if (e == cudaSuccess) e = dalloc(&c->d_occ_train, words);
@@ -266,6 +282,7 @@ void ia_destroy(ia_ctx* c) {
   dfree(c->d_rest);
   dfree(c->d_skin);
   dfree(c->d_table);
+  dfree(c->d_table_h);
   dfree(c->d_mlp);
   dfree(c->d_N);
   dfree(c->d_Ninv);
@@ -346,6 +363,7 @@ ia_status ia_set_params(ia_ctx* c, const float* table, const float* mlp, void* s
   cudaStream_t s = (cudaStream_t)stream;
   IA_CUDA(c, cudaMemcpyAsync(c->d_table, table, sizeof(float) * nt, cudaMemcpyDefault, s), "ia_set_params");
   IA_CUDA(c, cudaMemcpyAsync(c->d_mlp, mlp, sizeof(float) * nm, cudaMemcpyDefault, s), "ia_set_params");
+  if (c->d_table_h) IA_CUDA(c, launch_table_to_half(c->d_table, c->d_table_h, c->n_entries, s), "ia_set_params");
   c->have_params = true;
   return IA_OK;
 }
@@ -476,8 +494,8 @@ ia_status ia_query_canonical(ia_ctx* c, int n, const float* x, float* sigma, flo
   if (!c->have_params) return fail(c, IA_ERR_STATE, "ia_set_params has not been called");
   if (n < 0 || (n > 0 && (!x || !sigma || !rgb))) return fail(c, IA_ERR_ARG, "bad arrays");
   if (n == 0) return IA_OK;
-  IA_CUDA(c, launch_query_canonical(field_dev(c), c->d_mlp, c->n_in, n, x, sigma, rgb, (cudaStream_t)stream),
-          "ia_query_canonical");
+  PosedArgs a = posed_args_params(c);
+  IA_CUDA(c, launch_query_canonical(a, n, x, sigma, rgb, (cudaStream_t)stream), "ia_query_canonical");
   return IA_OK;
 }
 
@@ -563,6 +581,7 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
                         const ia_grads* g, void* stream) {
   ia_status st = need_ready(c, 0, false);
   if (st != IA_OK) return st;
+  if (c->cfg.precision != IA_FP32) return fail(c, IA_ERR_ARG, "the training step runs in fp32 only");
   if (!b || !loss || !g || !g->table || !g->mlp || !g->skin || !g->bones) return fail(c, IA_ERR_ARG, "null argument");
   if (b->n_rays < 1 || b->n_rays > (1 << 24)) return fail(c, IA_ERR_ARG, "n_rays must be 1..2^24");
   if (!b->origin || !b->direction || !b->pose || !b->target) return fail(c, IA_ERR_ARG, "null batch array");

@@ -6,6 +6,7 @@
 
 #include "ia_device.cuh"
 #include "ia_index.cuh"
+#include "ia_posed.cuh"
 
 namespace ia {
 
@@ -22,8 +23,10 @@ struct PosedArgs {
   FieldDev F;
   SolveCfg cfg;
   const float* Ninv;   // [nb][12] of the pose
-  const float* mlp;    // packed MLP (fp32)
+  const float* mlp;    // packed MLP (fp32 master)
   int n_in;
+  int prec;            // ia_precision of the field evaluation
+  const __half2* table_h;  // fp16 shadow of the hash table (prec != fp32)
 };
 
 struct RenderArgs {
@@ -94,8 +97,9 @@ cudaError_t launch_occ_bits(const float* sigma, int R, int dilate, float tau, ui
                             uint32_t* union_bits, cudaStream_t s);
 cudaError_t launch_query_posed(const PosedArgs& a, int n, const float* x, float* sigma, float* rgb,
                                float* xc, int* start, cudaStream_t s);
-cudaError_t launch_query_canonical(const FieldDev& F, const float* mlp, int n_in, int n, const float* x,
-                                   float* sigma, float* rgb, cudaStream_t s);
+cudaError_t launch_query_canonical(const PosedArgs& a, int n, const float* x, float* sigma, float* rgb,
+                                   cudaStream_t s);
+cudaError_t launch_table_to_half(const float* table, __half2* th, int64_t entries, cudaStream_t s);
 cudaError_t launch_render(const RenderArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_march_mask(const RenderArgs& a, uint32_t* mask, cudaStream_t s);
 

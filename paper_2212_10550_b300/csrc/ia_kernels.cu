@@ -144,27 +144,51 @@ cudaError_t launch_blend(int P, int V, int nb, const float* W, const float* N, f
 }
 
 // ---------------------------------------------------------------------------
-// Shared-memory layout of kernels that evaluate the posed field
+// Shared-memory layout of kernels that evaluate the posed field:
+//   MLP (fp32 layout, or reduced-precision layout + per-warp staging), the
+//   pose's N_k^-1, and the per-lane root lists.
 // ---------------------------------------------------------------------------
 
 constexpr int kMlpPad = (kMlpSmemFloats + 3) / 4 * 4;
 
-size_t posed_smem_bytes(int threads) {
-  return sizeof(float) * (kMlpPad + kMaxBones * 12) + sizeof(float4) * kMaxRoots * kNS * threads;
+__host__ __device__ constexpr int mlp_smem_words(Prec P, int threads) {
+  return P == Prec::F32 ? kMlpPad : ((kMlpHWords + 3) / 4 * 4 + (threads / 32) * kWarpXWords);
 }
 
+template <Prec P>
+size_t posed_smem_bytes_p(int threads) {
+  return sizeof(float) * (mlp_smem_words(P, threads) + kMaxBones * 12) + sizeof(float4) * kMaxRoots * kNS * threads;
+}
+
+size_t posed_smem_bytes(int threads) { return posed_smem_bytes_p<Prec::F32>(threads); }
+
 struct PosedSmem {
-  float* sw;
+  FieldSmem fs;
   float* sNinv;
   float4* roots;
 };
 
+template <Prec P>
 __device__ __forceinline__ PosedSmem stage_posed(const PosedArgs& a, float4* smem4) {
   PosedSmem p;
-  p.sw = reinterpret_cast<float*>(smem4);
-  p.sNinv = p.sw + kMlpPad;
+  float* base = reinterpret_cast<float*>(smem4);
+  p.fs.gmlp = a.mlp;
+  p.fs.n_in = a.n_in;
+  p.fs.table_h = a.table_h;
+  if constexpr (P == Prec::F32) {
+    p.fs.sw = base;
+    p.fs.swh = nullptr;
+    p.fs.xstage = nullptr;
+    stage_mlp(a.mlp, a.n_in, base);
+  } else {
+    uint32_t* w = reinterpret_cast<uint32_t*>(base);
+    p.fs.sw = nullptr;
+    p.fs.swh = w;
+    p.fs.xstage = w + (kMlpHWords + 3) / 4 * 4 + (threadIdx.x >> 5) * kWarpXWords;
+    stage_mlp_h<P>(a.mlp, a.n_in, w);
+  }
+  p.sNinv = base + mlp_smem_words(P, blockDim.x);
   p.roots = reinterpret_cast<float4*>(p.sNinv + kMaxBones * 12);
-  stage_mlp(a.mlp, a.n_in, p.sw);
   for (int t = threadIdx.x; t < a.cfg.nb * 12; t += blockDim.x) p.sNinv[t] = a.Ninv[t];
   __syncthreads();
   return p;
@@ -176,15 +200,21 @@ __device__ __forceinline__ void flush_stats(unsigned long long* stats, int idx, 
   if ((threadIdx.x & 31) == 0 && v != 0) atomicAdd(stats + idx, (unsigned long long)v);
 }
 
+template <typename Kern>
+static cudaError_t set_smem(Kern k, size_t smem) {
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
 // ---------------------------------------------------------------------------
 // Occupancy grid (Sec. 3.3, inference mode)
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS) occ_density_kernel(const PosedArgs a, const BoxDev box,
-                                                          float* __restrict__ sigma,
-                                                          unsigned long long* __restrict__ stats) {
+template <Prec P>
+__global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS)
+    occ_density_kernel(const PosedArgs a, const BoxDev box, float* __restrict__ sigma,
+                       unsigned long long* __restrict__ stats) {
   extern __shared__ float4 smem4[];
-  PosedSmem sm = stage_posed(a, smem4);
+  PosedSmem sm = stage_posed<P>(a, smem4);
   const int n = box.R * box.R * box.R;
   SampleStats st;
   // grid-stride over whole warps so every lane takes part in the warp-level search;
@@ -203,7 +233,7 @@ __global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS) occ_density_kernel(c
       Ms[q] = a.S.M;
       Ns[q] = sm.sNinv;
     }
-    posed_field_warp_n<kNS>(a.S, Ms, a.F, a.cfg, Ns, sm.sw, sm.roots, act, xn, o, st);
+    posed_field_warp_n<kNS, P>(a.S, Ms, a.F, a.cfg, Ns, sm.fs, sm.roots, act, xn, o, st);
 #pragma unroll
     for (int q = 0; q < kNS; ++q) {
       const int cell = base + q * blockDim.x + threadIdx.x;
@@ -218,15 +248,25 @@ __global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS) occ_density_kernel(c
   }
 }
 
+template <Prec P>
+static cudaError_t launch_occ_density_p(const PosedArgs& a, const BoxDev& box, float* sigma,
+                                        unsigned long long* stats, cudaStream_t s) {
+  const int n = box.R * box.R * box.R;
+  const int blocks = (n + 256 * kNS - 1) / (256 * kNS);
+  const size_t smem = posed_smem_bytes_p<P>(256);
+  cudaError_t e = set_smem(occ_density_kernel<P>, smem);
+  if (e != cudaSuccess) return e;
+  occ_density_kernel<P><<<blocks, 256, smem, s>>>(a, box, sigma, stats);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_occ_density(const PosedArgs& a, const BoxDev& box, float* sigma, unsigned long long* stats,
                                cudaStream_t s) {
-  const int n = box.R * box.R * box.R;
-  int blocks = (n + 256 * kNS - 1) / (256 * kNS);
-  size_t smem = posed_smem_bytes(256);
-  cudaError_t e = cudaFuncSetAttribute(occ_density_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  occ_density_kernel<<<blocks, 256, smem, s>>>(a, box, sigma, stats);
-  return cudaGetLastError();
+  switch (a.prec) {
+    case 1: return launch_occ_density_p<Prec::F16>(a, box, sigma, stats, s);
+    case 2: return launch_occ_density_p<Prec::BF16>(a, box, sigma, stats, s);
+    default: return launch_occ_density_p<Prec::F32>(a, box, sigma, stats, s);
+  }
 }
 
 // occupied = sigma > tau, dilated by a (2 dilate + 1)^3 cube clipped to the grid;
@@ -273,10 +313,12 @@ cudaError_t launch_occ_bits(const float* sigma, int R, int dilate, float tau, ui
 // Queries
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS) query_posed_kernel(const PosedArgs a, int n, const float* __restrict__ x,
-                                                          float* sigma, float* rgb, float* xc, int* start) {
+template <Prec P>
+__global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS)
+    query_posed_kernel(const PosedArgs a, int n, const float* __restrict__ x, float* sigma, float* rgb, float* xc,
+                       int* start) {
   extern __shared__ float4 smem4[];
-  PosedSmem sm = stage_posed(a, smem4);
+  PosedSmem sm = stage_posed<P>(a, smem4);
   SampleStats st;
   for (int base = blockIdx.x * blockDim.x * kNS; base < n; base += gridDim.x * blockDim.x * kNS) {
     bool act[kNS];
@@ -292,7 +334,7 @@ __global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS) query_posed_kernel(c
       Ms[q] = a.S.M;
       Ns[q] = sm.sNinv;
     }
-    posed_field_warp_n<kNS>(a.S, Ms, a.F, a.cfg, Ns, sm.sw, sm.roots, act, xn, o, st);
+    posed_field_warp_n<kNS, P>(a.S, Ms, a.F, a.cfg, Ns, sm.fs, sm.roots, act, xn, o, st);
 #pragma unroll
     for (int q = 0; q < kNS; ++q) {
       const int i = base + q * blockDim.x + threadIdx.x;
@@ -305,36 +347,66 @@ __global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS) query_posed_kernel(c
   }
 }
 
+template <Prec P>
+static cudaError_t launch_query_posed_p(const PosedArgs& a, int n, const float* x, float* sigma, float* rgb,
+                                        float* xc, int* start, cudaStream_t s) {
+  const size_t smem = posed_smem_bytes_p<P>(256);
+  cudaError_t e = set_smem(query_posed_kernel<P>, smem);
+  if (e != cudaSuccess) return e;
+  query_posed_kernel<P><<<(n + 256 * kNS - 1) / (256 * kNS), 256, smem, s>>>(a, n, x, sigma, rgb, xc, start);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_query_posed(const PosedArgs& a, int n, const float* x, float* sigma, float* rgb, float* xc,
                                int* start, cudaStream_t s) {
-  size_t smem = posed_smem_bytes(256);
-  cudaError_t e = cudaFuncSetAttribute(query_posed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  query_posed_kernel<<<(n + 256 * kNS - 1) / (256 * kNS), 256, smem, s>>>(a, n, x, sigma, rgb, xc, start);
-  return cudaGetLastError();
+  switch (a.prec) {
+    case 1: return launch_query_posed_p<Prec::F16>(a, n, x, sigma, rgb, xc, start, s);
+    case 2: return launch_query_posed_p<Prec::BF16>(a, n, x, sigma, rgb, xc, start, s);
+    default: return launch_query_posed_p<Prec::F32>(a, n, x, sigma, rgb, xc, start, s);
+  }
 }
 
-__global__ void __launch_bounds__(256) query_canonical_kernel(const FieldDev F, const float* __restrict__ mlp,
-                                                              int n_in, int n, const float* __restrict__ x,
+// canonical field at caller points; whole warps iterate so the tensor-core
+// path has all 32 lanes
+template <Prec P>
+__global__ void __launch_bounds__(256) query_canonical_kernel(const PosedArgs a, int n, const float* __restrict__ x,
                                                               float* sigma, float* rgb) {
-  __shared__ __align__(16) float sw[kMlpPad];
-  stage_mlp(mlp, n_in, sw);
-  __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  float s;
-  float3 c;
-  field_fp32(F, sw, make_float3(x[3 * i], x[3 * i + 1], x[3 * i + 2]), s, c);
-  sigma[i] = s;
-  rgb[3 * i] = c.x;
-  rgb[3 * i + 1] = c.y;
-  rgb[3 * i + 2] = c.z;
+  extern __shared__ float4 smem4[];
+  PosedSmem sm = stage_posed<P>(a, smem4);
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int i = base + threadIdx.x;
+    const bool act = i < n;
+    const float3 p = act ? make_float3(x[3 * i], x[3 * i + 1], x[3 * i + 2])
+                         : make_float3(a.F.cmin[0], a.F.cmin[1], a.F.cmin[2]);
+    float s;
+    float3 c;
+    field_eval_warp<P>(a.F, sm.fs, p, s, c);
+    if (act) {
+      sigma[i] = s;
+      rgb[3 * i] = c.x;
+      rgb[3 * i + 1] = c.y;
+      rgb[3 * i + 2] = c.z;
+    }
+  }
 }
 
-cudaError_t launch_query_canonical(const FieldDev& F, const float* mlp, int n_in, int n, const float* x, float* sigma,
-                                   float* rgb, cudaStream_t s) {
-  query_canonical_kernel<<<(n + 255) / 256, 256, 0, s>>>(F, mlp, n_in, n, x, sigma, rgb);
+template <Prec P>
+static cudaError_t launch_query_canonical_p(const PosedArgs& a, int n, const float* x, float* sigma, float* rgb,
+                                            cudaStream_t s) {
+  const size_t smem = posed_smem_bytes_p<P>(256);
+  cudaError_t e = set_smem(query_canonical_kernel<P>, smem);
+  if (e != cudaSuccess) return e;
+  query_canonical_kernel<P><<<(n + 255) / 256, 256, smem, s>>>(a, n, x, sigma, rgb);
   return cudaGetLastError();
+}
+
+cudaError_t launch_query_canonical(const PosedArgs& a, int n, const float* x, float* sigma, float* rgb,
+                                   cudaStream_t s) {
+  switch (a.prec) {
+    case 1: return launch_query_canonical_p<Prec::F16>(a, n, x, sigma, rgb, s);
+    case 2: return launch_query_canonical_p<Prec::BF16>(a, n, x, sigma, rgb, s);
+    default: return launch_query_canonical_p<Prec::F32>(a, n, x, sigma, rgb, s);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -353,10 +425,13 @@ cudaError_t launch_query_canonical(const FieldDev& F, const float* mlp, int n_in
 //     transmittance is below the threshold.
 // ---------------------------------------------------------------------------
 
-size_t render_smem_bytes(int K) {
-  return posed_smem_bytes(kRenderThreads) + sizeof(float4) * (2 * kRenderThreads + K * kRenderThreads) +
+template <Prec P>
+size_t render_smem_bytes_p(int K) {
+  return posed_smem_bytes_p<P>(kRenderThreads) + sizeof(float4) * (2 * kRenderThreads + K * kRenderThreads) +
          sizeof(int) * (2 * K * kRenderThreads);
 }
+
+size_t render_smem_bytes(int K) { return render_smem_bytes_p<Prec::F32>(K); }
 
 __device__ __forceinline__ void tile_pixel(int id, int tiles_x, int W, int H, int& u, int& v, bool& valid) {
   const int tile = id / (kTile * kTile), i = id % (kTile * kTile);
@@ -365,10 +440,10 @@ __device__ __forceinline__ void tile_pixel(int id, int tiles_x, int W, int H, in
   valid = u < W && v < H;
 }
 
-template <int K>
+template <int K, Prec P>
 __global__ void __launch_bounds__(kRenderThreads, IA_RENDER_MIN_BLOCKS) render_kernel(const RenderArgs a) {
   extern __shared__ float4 smem4[];
-  PosedSmem sm = stage_posed(a.P, smem4);
+  PosedSmem sm = stage_posed<P>(a.P, smem4);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // this warp's slices of the shared arrays
   float4* const after_roots = sm.roots + kMaxRoots * kNS * kRenderThreads;
@@ -496,7 +571,7 @@ __global__ void __launch_bounds__(kRenderThreads, IA_RENDER_MIN_BLOCKS) render_k
         Ms[q] = a.P.S.M;
         Ns[q] = sm.sNinv;
       }
-      posed_field_warp_n<kNS>(a.P.S, Ms, a.P.F, a.P.cfg, Ns, sm.sw, sm.roots, act, xn, r, st);
+      posed_field_warp_n<kNS, P>(a.P.S, Ms, a.P.F, a.P.cfg, Ns, sm.fs, sm.roots, act, xn, r, st);
 #pragma unroll
       for (int q = 0; q < kNS; ++q) {
         const int sidx = base + q * 32 + lane;
@@ -539,28 +614,48 @@ __global__ void __launch_bounds__(kRenderThreads, IA_RENDER_MIN_BLOCKS) render_k
   }
 }
 
-template <int K>
+template <int K, Prec P>
 static cudaError_t launch_render_k(const RenderArgs& a, int num_sms, cudaStream_t s) {
-  size_t smem = render_smem_bytes(K);
-  cudaError_t e = cudaFuncSetAttribute(render_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = render_smem_bytes_p<P>(K);
+  cudaError_t e = set_smem(render_kernel<K, P>, smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel<K>, kRenderThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel<K, P>, kRenderThreads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
-  int want = (a.n_ray_ids + kRenderThreads - 1) / kRenderThreads;
+  const int want = (a.n_ray_ids + kRenderThreads - 1) / kRenderThreads;
   int grid = num_sms * per_sm;
   if (grid > want) grid = want;
   if (grid < 1) grid = 1;
-  render_kernel<K><<<grid, kRenderThreads, smem, s>>>(a);
+  render_kernel<K, P><<<grid, kRenderThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_render(const RenderArgs& a, int num_sms, cudaStream_t s) {
+template <Prec P>
+static cudaError_t launch_render_p(const RenderArgs& a, int num_sms, cudaStream_t s) {
   // with early termination, few samples per ray per round bound the work done
   // past the stopping sample; without it, larger rounds amortise the scans
-  if (a.early_T > 0.f) return launch_render_k<2>(a, num_sms, s);
-  return launch_render_k<8>(a, num_sms, s);
+  if (a.early_T > 0.f) return launch_render_k<2, P>(a, num_sms, s);
+  return launch_render_k<8, P>(a, num_sms, s);
+}
+
+cudaError_t launch_render(const RenderArgs& a, int num_sms, cudaStream_t s) {
+  switch (a.P.prec) {
+    case 1: return launch_render_p<Prec::F16>(a, num_sms, s);
+    case 2: return launch_render_p<Prec::BF16>(a, num_sms, s);
+    default: return launch_render_p<Prec::F32>(a, num_sms, s);
+  }
+}
+
+// fp16 shadow of the fp32 master hash table (reduced-precision field)
+__global__ void table_to_half_kernel(const float2* __restrict__ t, __half2* __restrict__ th, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    th[i] = __float22half2_rn(t[i]);
+}
+
+cudaError_t launch_table_to_half(const float* table, __half2* th, int64_t entries, cudaStream_t s) {
+  table_to_half_kernel<<<1184, 256, 0, s>>>(reinterpret_cast<const float2*>(table), th, entries);
+  return cudaGetLastError();
 }
 
 // One thread per pixel: the slots the render kernel's march would keep.

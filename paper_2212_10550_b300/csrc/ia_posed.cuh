@@ -1,0 +1,223 @@
+// Precision-generic canonical field evaluation and the multi-start
+// correspondence search built on it (Sec. 3.1, Eq. 1-4 and 7).
+#pragma once
+
+#include "ia_device.cuh"
+#include "ia_mma.cuh"
+
+namespace ia {
+
+// Where a kernel keeps what the field evaluation reads.
+struct FieldSmem {
+  const float* sw;           // fp32 MLP in the layout of stage_mlp (Prec::F32)
+  const uint32_t* swh;       // reduced-precision MLP in the layout of stage_mlp_h
+  uint32_t* xstage;          // this warp's staging area (kWarpXWords words)
+  const float* gmlp;         // packed fp32 MLP in global memory
+  int n_in;
+  const __half2* table_h;    // fp16 shadow of the hash table (reduced precision)
+};
+
+// Field at one point per lane; all 32 lanes call (tensor cores need the warp).
+template <Prec P>
+__device__ __forceinline__ void field_eval_warp(const FieldDev& F, const FieldSmem& fs, float3 x, float& sigma,
+                                                float3& rgb) {
+  float feat[kIn], o[4];
+  if constexpr (P == Prec::F32) {
+    encode(F, x, feat);
+    mlp_fp32(fs.sw, feat, o);
+  } else {
+    encode_h(F, fs.table_h, x, feat);
+    mlp_mma_warp<P>(fs.swh, fs.xstage, feat, o);
+  }
+  activate(o, sigma, rgb);
+}
+
+// Field at one point for a single lane (numerically the same network).
+template <Prec P>
+__device__ __forceinline__ void field_eval_lane(const FieldDev& F, const FieldSmem& fs, float3 x, float& sigma,
+                                                float3& rgb) {
+  float feat[kIn], o[4];
+  if constexpr (P == Prec::F32) {
+    encode(F, x, feat);
+    mlp_fp32(fs.sw, feat, o);
+  } else {
+    encode_h(F, fs.table_h, x, feat);
+    mlp_lane_h<P>(fs.gmlp, fs.n_in, feat, o);
+  }
+  activate(o, sigma, rgb);
+}
+
+// Multi-start correspondence search and field evaluation for NS samples per
+// lane (NS independent Broyden chains interleaved, so that each loop step has
+// NS gathers of the blended grid in flight per lane).  All 32 lanes must call.
+//   M[s]: sample s's pose's blended grid; Ninv[s]: that pose's N_k^-1 ([nb][12]);
+//   roots: this CTA's float4 scratch of kMaxRoots * NS * blockDim.x entries
+//   (x, y, z, start bits).
+// The first kMaxRoots distinct roots of a sample are evaluated together by the
+// warp after the search; any further distinct root (rare) is evaluated on the
+// spot so that no root is ever dropped.
+template <int NS, Prec P>
+__device__ __forceinline__ void posed_field_warp_n(const SkinDev& S, const float4* const* M, const FieldDev& F,
+                                                   const SolveCfg& cfg, const float* const* Ninv, const FieldSmem& fs,
+                                                   float4* roots, const bool* active, const float3* xn,
+                                                   PosedOut* out, SampleStats& st) {
+  const int tid = threadIdx.x, stride = blockDim.x;
+  int k[NS], it[NS], nroots[NS], phase[NS];  // phase 0 = start k, 1 = iterate, 2 = done
+  float3 x[NS], r[NS], dx[NS];
+  float H[NS][9];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    out[s].sigma = 0.f;
+    out[s].rgb = make_float3(0.f, 0.f, 0.f);
+    out[s].xstar = out[s].rgb;
+    out[s].start = -1;
+    k[s] = 0; it[s] = 0; nroots[s] = 0;
+    phase[s] = active[s] ? 0 : 2;
+    x[s] = make_float3(0.f, 0.f, 0.f); r[s] = x[s]; dx[s] = x[s];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) H[s][q] = 0.f;
+  }
+  auto busy = [&]() {
+    bool b = false;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) b |= phase[s] != 2;
+    return b;
+  };
+  // ---- flattened multi-start Broyden: every loop step evaluates M once per chain
+  while (__any_sync(kFull, busy())) {
+    float3 q[NS];
+    float Mx[NS][12];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      q[s] = x[s];
+      if (phase[s] == 0) {
+        const float* A = Ninv[s] + 12 * k[s];
+        const float3 p = xn[s];
+        q[s] = make_float3(A[0] * p.x + A[1] * p.y + A[2] * p.z + A[3], A[4] * p.x + A[5] * p.y + A[6] * p.z + A[7],
+                           A[8] * p.x + A[9] * p.y + A[10] * p.z + A[11]);
+      } else if (phase[s] == 1) {
+        q[s] = make_float3(x[s].x + dx[s].x, x[s].y + dx[s].y, x[s].z + dx[s].z);
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+      if (phase[s] != 2) blend_value(S, M[s], q[s], Mx[s]);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      bool finish = false, conv = false;
+      if (phase[s] == 0) {
+        st.starts++;
+        const float3 y = apply34(Mx[s], q[s]);
+        x[s] = q[s];
+        r[s] = make_float3(y.x - xn[s].x, y.y - xn[s].y, y.z - xn[s].z);
+        // initial inverse Jacobian: LBS with the weights frozen at x0, (sum_i w_i R_i)^-1
+        const float J0[9] = {Mx[s][0], Mx[s][1], Mx[s][2], Mx[s][4], Mx[s][5], Mx[s][6], Mx[s][8], Mx[s][9], Mx[s][10]};
+        it[s] = 0;
+        if (!inv3(J0, H[s])) finish = true;
+      } else if (phase[s] == 1) {
+        const float3 y = apply34(Mx[s], q[s]);
+        const float3 rn = make_float3(y.x - xn[s].x, y.y - xn[s].y, y.z - xn[s].z);
+        const float3 dr = make_float3(rn.x - r[s].x, rn.y - r[s].y, rn.z - r[s].z);
+        x[s] = q[s];
+        r[s] = rn;
+        ++it[s];
+        st.iters++;
+        // good Broyden: H += (dx - H dr)(dx^T H) / (dx^T H dr)
+        float* h = H[s];
+        const float3 d = dx[s];
+        const float u0 = h[0] * dr.x + h[1] * dr.y + h[2] * dr.z;
+        const float u1 = h[3] * dr.x + h[4] * dr.y + h[5] * dr.z;
+        const float u2 = h[6] * dr.x + h[7] * dr.y + h[8] * dr.z;
+        const float den = d.x * u0 + d.y * u1 + d.z * u2;
+        if (fabsf(den) > 1e-12f) {
+          const float a0 = (d.x - u0) / den, a1 = (d.y - u1) / den, a2 = (d.z - u2) / den;
+          const float b0 = d.x * h[0] + d.y * h[3] + d.z * h[6];
+          const float b1 = d.x * h[1] + d.y * h[4] + d.z * h[7];
+          const float b2 = d.x * h[2] + d.y * h[5] + d.z * h[8];
+          h[0] += a0 * b0; h[1] += a0 * b1; h[2] += a0 * b2;
+          h[3] += a1 * b0; h[4] += a1 * b1; h[5] += a1 * b2;
+          h[6] += a2 * b0; h[7] += a2 * b1; h[8] += a2 * b2;
+        }
+      }
+      if (phase[s] != 2 && !finish) {
+        const float rr = r[s].x * r[s].x + r[s].y * r[s].y + r[s].z * r[s].z;
+        if (rr < cfg.tol2) {
+          conv = true;
+          finish = true;
+        } else if (it[s] >= cfg.max_iter) {
+          finish = true;
+        } else {
+          const float* h = H[s];
+          dx[s] = make_float3(-(h[0] * r[s].x + h[1] * r[s].y + h[2] * r[s].z),
+                              -(h[3] * r[s].x + h[4] * r[s].y + h[5] * r[s].z),
+                              -(h[6] * r[s].x + h[7] * r[s].y + h[8] * r[s].z));
+          phase[s] = 1;
+        }
+      }
+      if (finish) {
+        if (conv && in_box(S, x[s])) {
+          st.converged++;
+          bool dup = false;
+          for (int j = 0; j < min(nroots[s], kMaxRoots); ++j) {
+            const float4 o = roots[((s * kMaxRoots) + j) * stride + tid];
+            const float ddx = x[s].x - o.x, ddy = x[s].y - o.y, ddz = x[s].z - o.z;
+            if (ddx * ddx + ddy * ddy + ddz * ddz < 1e-8f) { dup = true; break; }
+          }
+          if (!dup) {
+            st.roots++;
+            if (nroots[s] < kMaxRoots) {
+              roots[((s * kMaxRoots) + nroots[s]) * stride + tid] = make_float4(x[s].x, x[s].y, x[s].z, __int_as_float(k[s]));
+            } else {
+              const float3 xs = polish_root(S, M[s], x[s], xn[s]);
+              float sig;
+              float3 rgb;
+              field_eval_lane<P>(F, fs, xs, sig, rgb);
+              take_best(out[s], sig, rgb, xs, k[s]);
+            }
+            nroots[s]++;
+          }
+        }
+        ++k[s];
+        phase[s] = (k[s] < cfg.nb) ? 0 : 2;
+      }
+    }
+  }
+  // ---- one Newton polish per stored root, field evaluation, max-density root;
+  //      the lane's (sample, root) pairs are evaluated one per warp step
+  int nr[NS], total = 0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    nr[s] = min(nroots[s], kMaxRoots);
+    total += nr[s];
+  }
+  const int nmax = __reduce_max_sync(kFull, total);
+  for (int e = 0; e < nmax; ++e) {
+    const bool has = e < total;
+    int si = 0, j = e;
+#pragma unroll
+    for (int s = 0; s + 1 < NS; ++s)
+      if (si == s && j >= nr[s]) { j -= nr[s]; si = s + 1; }
+    float3 xs = make_float3(S.cmin[0], S.cmin[1], S.cmin[2]);
+    int start = -1;
+    float3 xq = xn[0];
+    const float4* Mq = M[0];
+#pragma unroll
+    for (int s = 1; s < NS; ++s)
+      if (si == s) { xq = xn[s]; Mq = M[s]; }
+    if (has) {
+      const float4 o = roots[((si * kMaxRoots) + j) * stride + tid];
+      start = __float_as_int(o.w);
+      xs = polish_root(S, Mq, make_float3(o.x, o.y, o.z), xq);
+    }
+    float sig;
+    float3 rgb;
+    field_eval_warp<P>(F, fs, xs, sig, rgb);
+    if (has) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+        if (si == s) take_best(out[s], sig, rgb, xs, start);
+    }
+  }
+}
+
+}  // namespace ia

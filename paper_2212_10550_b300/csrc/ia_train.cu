@@ -66,6 +66,13 @@ __global__ void __launch_bounds__(256) train_sample_kernel(const TrainArgs a) {
   float4* roots = reinterpret_cast<float4*>(sw + kMlpPadT);
   stage_mlp(a.P.mlp, a.P.n_in, sw);
   __syncthreads();
+  FieldSmem fs;
+  fs.sw = sw;
+  fs.swh = nullptr;
+  fs.xstage = nullptr;
+  fs.gmlp = a.P.mlp;
+  fs.n_in = a.P.n_in;
+  fs.table_h = nullptr;
   const int n = *a.count;
   const int lane = threadIdx.x & 31;
   SampleStats st;
@@ -87,7 +94,7 @@ __global__ void __launch_bounds__(256) train_sample_kernel(const TrainArgs a) {
       Ms[q] = a.P.S.M + (size_t)pose * a.V * 3;
       Ns[q] = a.P.Ninv + (size_t)pose * a.P.cfg.nb * 12;
     }
-    posed_field_warp_n<kNS>(a.P.S, Ms, a.P.F, a.P.cfg, Ns, sw, roots, act, xn, o, st);
+    posed_field_warp_n<kNS, Prec::F32>(a.P.S, Ms, a.P.F, a.P.cfg, Ns, fs, roots, act, xn, o, st);
 #pragma unroll
     for (int q = 0; q < kNS; ++q) {
       const int s = base + q * 32 + lane;

@@ -24,12 +24,12 @@ import tempfile
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = [os.path.join(_HERE, f) for f in ("oracle.c", "oracle_grad.c")]
+_SRC = [os.path.join(_HERE, f) for f in ("oracle.c", "oracle_grad.c", "oracle_prop.c")]
 _HDR = os.path.join(_HERE, "oracle.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
 MAX_BONES = 32
 
-FLAG_CONV, FLAG_BOX, FLAG_DUP, FLAG_TIE, FLAG_SING, FLAG_TERM = 1, 2, 4, 8, 16, 32
+FLAG_CONV, FLAG_BOX, FLAG_DUP, FLAG_TIE, FLAG_SING, FLAG_TERM, FLAG_PROP = 1, 2, 4, 8, 16, 32, 64
 
 
 def build(force: bool = False) -> str:
@@ -131,6 +131,9 @@ def _declare(L):
         f.argtypes = args
     if hasattr(L, "or_train"):
         _declare_grad(L)
+    if hasattr(L, "or_prop_forward"):
+        from . import prop as _pp
+        _pp.declare(L)
 
 
 def _declare_grad(L):

@@ -289,27 +289,28 @@ static double box_margin(const or_model *m, const double x[3]) {
   return d;
 }
 
-/* All bone-wise starts x0 = N_k^-1 x'; valid = converged and inside the canonical
-   box; roots are polished and merged when closer than 1e-4 (lowest start kept).
-   A start whose convergence decision at the iteration cap is marginal (see
-   or_broyden) only raises OR_FLAG_CONV when its nearby root would be a root no
-   other start found, i.e. when an fp32 trajectory could change the root set. */
-static int roots_impl(const or_model *m, const or_pose *p, const double xn[3], double *roots,
-                      int *starts, int *flags, int *iters_sum, int *n_conv) {
+/* Roots reached from a list of starts x0s[j] (labelled labels[j]); valid =
+   converged and inside the canonical box; roots are polished and merged when
+   closer than 1e-4 (the earliest start kept).  A start whose convergence
+   decision at the iteration cap is marginal (see or_broyden) only raises
+   OR_FLAG_CONV when its nearby root would be a root no other start found, i.e.
+   when an fp32 trajectory could change the root set. */
+int or_roots_from_starts(const or_model *m, const or_pose *p, const double xn[3], int ns,
+                         const double *x0s, const int *labels, double *roots, int *starts, int *flags,
+                         int *iters_sum, int *n_conv) {
   int n = 0, fl = 0, its = 0, nc = 0;
-  double xs[OR_MAX_BONES][3];
-  int conv[OR_MAX_BONES], marg[OR_MAX_BONES];
-  for (int k = 0; k < m->nb; ++k) {
-    double x0[3], rn;
+  double xs[OR_MAX_STARTS][3];
+  int conv[OR_MAX_STARTS], marg[OR_MAX_STARTS];
+  for (int k = 0; k < ns; ++k) {
+    double rn;
     int it = 0, f = 0;
-    mat34_apply(p->Ninv[k], xn, x0);
-    conv[k] = or_broyden(m, p, xn, x0, xs[k], &it, &rn, &f);
+    conv[k] = or_broyden(m, p, xn, x0s + 3 * k, xs[k], &it, &rn, &f);
     marg[k] = (f & OR_FLAG_CONV) != 0;
     fl |= f & ~OR_FLAG_CONV;
     its += it;
     if (conv[k] || marg[k]) or_polish(m, p, xn, xs[k]);
   }
-  for (int k = 0; k < m->nb; ++k) {
+  for (int k = 0; k < ns; ++k) {
     if (!conv[k]) continue;
     double *x = xs[k];
     if (box_margin(m, x) < 1e-4) fl |= OR_FLAG_BOX;
@@ -326,13 +327,13 @@ static int roots_impl(const or_model *m, const or_pose *p, const double xn[3], d
     roots[3 * n] = x[0];
     roots[3 * n + 1] = x[1];
     roots[3 * n + 2] = x[2];
-    starts[n] = k;
+    starts[n] = labels[k];
     n++;
   }
-  for (int k = 0; k < m->nb; ++k) {
+  for (int k = 0; k < ns; ++k) {
     if (!marg[k] || !in_box(m, xs[k])) continue;
     int shared = 0;
-    for (int q = 0; q < m->nb; ++q) {
+    for (int q = 0; q < ns; ++q) {
       if (q == k || !conv[q] || marg[q]) continue;
       double d[3] = {xs[k][0] - xs[q][0], xs[k][1] - xs[q][1], xs[k][2] - xs[q][2]};
       if (norm3(d) < 1e-4) { shared = 1; break; }
@@ -343,6 +344,18 @@ static int roots_impl(const or_model *m, const or_pose *p, const double xn[3], d
   if (iters_sum) *iters_sum = its;
   if (n_conv) *n_conv = nc;
   return n;
+}
+
+/* All bone-wise starts x0 = N_k^-1 x', labelled by their bone. */
+static int roots_impl(const or_model *m, const or_pose *p, const double xn[3], double *roots,
+                      int *starts, int *flags, int *iters_sum, int *n_conv) {
+  double x0s[OR_MAX_BONES * 3];
+  int labels[OR_MAX_BONES];
+  for (int k = 0; k < m->nb; ++k) {
+    mat34_apply(p->Ninv[k], xn, x0s + 3 * k);
+    labels[k] = k;
+  }
+  return or_roots_from_starts(m, p, xn, m->nb, x0s, labels, roots, starts, flags, iters_sum, n_conv);
 }
 
 int or_roots(const or_model *m, const or_pose *p, const double xn[3], double *roots, int *starts,
@@ -434,11 +447,10 @@ void or_field(const or_model *m, const double x[3], double *sigma, double rgb[3]
 
 /* f'(x') = f(x*): the root with the highest density among the distinct valid
    roots (ties -> earliest start); no valid root -> density 0 */
-void or_posed_field(const or_model *m, const or_pose *p, const double xn[3], or_sample *s) {
-  double roots[OR_MAX_BONES * 3];
-  int starts[OR_MAX_BONES];
-  int fl = 0, its = 0, nc = 0;
-  int n = roots_impl(m, p, xn, roots, starts, &fl, &its, &nc);
+/* f'(x') = f(x*) over a root set: the root with the highest density (ties ->
+   the earlier root); no root -> density 0 */
+void or_select_root(const or_model *m, int n, const double *roots, const int *starts, int flags,
+                    int iters, int n_conv, or_sample *s) {
   memset(s, 0, sizeof(*s));
   s->start = -1;
   double best = -1.0, second = -1.0;
@@ -455,11 +467,21 @@ void or_posed_field(const or_model *m, const or_pose *p, const double xn[3], or_
       second = sig;
     }
   }
-  if (n >= 2 && best - second <= 1e-3 * best) fl |= OR_FLAG_TIE;
-  s->n_conv = nc;
+  if (n >= 2 && best - second <= 1e-3 * best) flags |= OR_FLAG_TIE;
+  s->n_conv = n_conv;
   s->n_unique = n;
-  s->flags = fl;
-  s->iters = its;
+  s->flags = flags;
+  s->iters = iters;
+}
+
+/* f'(x') = f(x*): the root with the highest density among the distinct valid
+   roots of all bone-wise starts */
+void or_posed_field(const or_model *m, const or_pose *p, const double xn[3], or_sample *s) {
+  double roots[OR_MAX_BONES * 3];
+  int starts[OR_MAX_BONES];
+  int fl = 0, its = 0, nc = 0;
+  int n = roots_impl(m, p, xn, roots, starts, &fl, &its, &nc);
+  or_select_root(m, n, roots, starts, fl, its, nc, s);
 }
 
 /* ------------------------------------------------------------------------- */

@@ -25,6 +25,7 @@
 
 #define OR_MAX_BONES 32
 #define OR_MAX_LEVELS 32
+#define OR_MAX_STARTS (OR_MAX_BONES + 4)
 
 #ifdef __cplusplus
 extern "C" {
@@ -77,6 +78,7 @@ enum {
   OR_FLAG_TIE = 8,    /* best and runner-up density within 1e-3 relative */
   OR_FLAG_SING = 16,  /* a start's Jacobian determinant near the 1e-6 cutoff */
   OR_FLAG_TERM = 32,  /* transmittance within 1e-3 relative of the stopping threshold */
+  OR_FLAG_PROP = 64,  /* the last proposed and the next logit within 0.05 */
 };
 
 typedef struct or_sample {
@@ -104,6 +106,13 @@ double or_polish(const or_model *m, const or_pose *p, const double xn[3], double
 /* Multi-start roots: distinct valid roots (polished), their starts; returns count. */
 int or_roots(const or_model *m, const or_pose *p, const double xn[3], double *roots,
              int *starts, int *flags);
+/* Roots from an explicit list of starts (x0s [ns][3], labels [ns]). */
+int or_roots_from_starts(const or_model *m, const or_pose *p, const double xn[3], int ns,
+                         const double *x0s, const int *labels, double *roots, int *starts, int *flags,
+                         int *iters_sum, int *n_conv);
+/* Max-density selection over a root set (fills s). */
+void or_select_root(const or_model *m, int n, const double *roots, const int *starts, int flags,
+                    int iters, int n_conv, or_sample *s);
 /* Eq. 1-2: hash-grid encoding, MLP, density and colour at canonical x. */
 void or_encode(const or_model *m, const double x[3], double *feat);
 void or_mlp(const or_model *m, const double *feat, double out[4]);
@@ -145,6 +154,28 @@ double or_train(const or_model *m, const or_pose *poses, int n_poses, const uint
                 const float *o, const float *d, const int32_t *pose_id, const double *target,
                 double *rgb_out, int *ray_flags, double *g_table, double *g_mlp, double *g_skin,
                 double *g_bones, int nthreads);
+/* Learned correspondence proposal (oracle_prop.c; not part of the paper). */
+typedef struct or_prop {
+  int L, log2_T;              /* hash grid over the normalised box */
+  const int32_t *res;         /* [L] */
+  const double *table;        /* [entries][2] */
+  int n_in, width, n_out;     /* n_in = 2L + 3 nb, n_out = nb + 3 */
+  const double *W1, *b1, *W2, *b2, *W3, *b3, *W4, *b4; /* row-major [out][in] */
+  int top_k;
+  double offset_weight;
+} or_prop;
+void or_prop_encode(const or_model *m, const or_prop *q, const double xn[3], double *feat, long *entry,
+                    double *weight);
+void or_prop_forward(const or_model *m, const or_prop *q, const double xn[3], const double *theta,
+                     double *out);
+int or_prop_label(const or_model *m, const or_pose *p, const double xs[3], const double xn[3],
+                  double offset[3]);
+long or_prop_mlp_count(const or_prop *q);
+double or_prop_loss_grad(const or_model *m, const or_prop *q, int n, const float *x, const int32_t *pose_id,
+                         const double *theta_all, const int32_t *label, const double *target,
+                         double *g_table, double *g_mlp);
+void or_posed_field_prop(const or_model *m, const or_pose *p, const or_prop *q, const double *theta,
+                         const double xn[3], or_sample *s, int *fallback);
 /* Brute-force root set: Newton from every point of an n^3 canonical lattice. */
 int or_bruteforce_roots(const or_model *m, const or_pose *p, const double xn[3], int n,
                         double seed_thresh, double *roots, int max_roots);

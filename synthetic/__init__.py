@@ -386,3 +386,32 @@ def random_points(scene: Scene, n: int, seed: int = 0, box: str = "norm") -> np.
     rng = np.random.default_rng(40_000 + seed)
     lo, hi = (scene.norm_min, scene.norm_max) if box == "norm" else (scene.canon_min, scene.canon_max)
     return rng.uniform(lo, hi, size=(n, 3)).astype(np.float32)
+
+
+def proposal_config(n_levels: int = 8, log2_table: int = 16, base: int = 8, growth: float = 1.5,
+                    top_k: int = 2, offset_weight: float = 100.0) -> dict:
+    """Sizes of the correspondence-proposal network (posed-space hash grid over
+    the normalised box, 64-wide MLP with three hidden layers)."""
+    return dict(n_levels=n_levels, log2_table=log2_table, level_res=level_resolutions(n_levels, base, growth=growth),
+                top_k=top_k, offset_weight=offset_weight)
+
+
+def proposal_init(scene: Scene, cfg: dict, seed: int = 0):
+    """Seeded initial proposal parameters: table U(-1e-4, 1e-4), He-normal weights, zero biases.
+    Returns the table [entries, 2] and the MLP dict (W1 [64, 2L+3nb], b1, W2, b2, W3, b3, W4 [nb+3, 64], b4)."""
+    rng = np.random.default_rng(50_000 + seed)
+    T = 1 << cfg["log2_table"]
+    entries = sum(min((int(r) + 1) ** 3, T) for r in cfg["level_res"])
+    table = rng.uniform(-1e-4, 1e-4, size=(entries, 2))
+    nin = 2 * cfg["n_levels"] + 3 * scene.n_bones
+    dims = [(64, nin), (64, 64), (64, 64), (scene.n_bones + 3, 64)]
+    mlp = {}
+    for i, (o, n) in enumerate(dims, start=1):
+        mlp[f"W{i}"] = rng.normal(0.0, np.sqrt(2.0 / n), size=(o, n))
+        mlp[f"b{i}"] = np.zeros(o)
+    return table.astype(np.float32), {k: v.astype(np.float32) for k, v in mlp.items()}
+
+
+def pack_proposal(mlp: dict) -> np.ndarray:
+    return np.concatenate([mlp[k].reshape(-1) for k in ("W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4")]
+                          ).astype(np.float32)

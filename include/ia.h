@@ -98,6 +98,8 @@ typedef struct ia_render_stats {
   int64_t converged;         /* starts that converged inside the canonical box */
   int64_t roots;             /* distinct roots kept (one field evaluation each) */
   int64_t early_stopped;     /* rays stopped by the transmittance threshold */
+  int64_t proposed;          /* samples whose first starts came from the proposal network */
+  int64_t fallbacks;         /* of those, samples that fell back to every bone-wise start */
 } ia_render_stats;
 
 /* Create a context on the current CUDA device.  cfg is copied. */
@@ -247,6 +249,58 @@ ia_status ia_train_step(ia_ctx *ctx, const ia_batch *batch, int occ_grid, float 
  *    device) race on it and must be serialised by the caller.
  *  bits_out [R^3 / 32] uint32 device or NULL; the render grid is replaced. */
 ia_status ia_update_occupancy_static(ia_ctx *ctx, int pose, uint32_t *bits_out, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned correspondence proposal.  The paper starts the search from every bone
+ * (Sec. 3.1); this optional network (not in the paper) proposes the first starts
+ * instead: input [hash features of x' over the normalised box (n_levels x 2) |
+ * the pose's axis-angles (n_bones x 3)], MLP 64-64-64 (ReLU), output n_bones
+ * logits and a 3-D start offset.  In IA_SEARCH_PROPOSAL mode every posed-field
+ * evaluation (render, occupancy, queries) starts from the top_k bones by logit
+ * (the first shifted by the offset) and falls back to every bone-wise start when
+ * those find no valid root.  Inference runs on tensor cores, so the mode needs
+ * precision IA_FP16 or IA_BF16.  Training pairs come from the plain search; the
+ * label is the bone with the largest skinning weight at the selected root x*,
+ * the offset target x* - N_label^-1 x'; loss per pair = cross-entropy +
+ * offset_weight |offset - target|^2, averaged over the batch; Adam (0.9, 0.999).
+ * ------------------------------------------------------------------------- */
+typedef struct ia_proposal_config {
+  int n_levels;                  /* 1..8 */
+  int log2_table;                /* 10..24 */
+  int level_res[IA_MAX_LEVELS];  /* grid resolution per level, >= 2 */
+  int top_k;                     /* proposed starts before the fallback: 1 or 2 */
+  float offset_weight;           /* weight of the offset term, >= 0 */
+} ia_proposal_config;
+
+typedef enum ia_search { IA_SEARCH_ALL_BONES = 0, IA_SEARCH_PROPOSAL = 1 } ia_search;
+
+/* Allocate the network (parameters zero until ia_proposal_set_params). */
+ia_status ia_proposal_init(ia_ctx *ctx, const ia_proposal_config *cfg);
+/* fp32 values of the table ([entries][2], same layout rules as the canonical
+ * grid over the normalised box) and of the packed MLP (W1 [64][2L + 3 n_b], b1,
+ * W2 [64][64], b2, W3 [64][64], b3, W4 [n_b + 3][64], b4). */
+ia_status ia_proposal_param_sizes(const ia_ctx *ctx, int64_t *table_floats, int64_t *mlp_floats);
+/* Load (host or device; resets the optimiser state) / read the parameters. */
+ia_status ia_proposal_set_params(ia_ctx *ctx, const float *table, const float *mlp, void *stream);
+ia_status ia_proposal_get_params(ia_ctx *ctx, float *table, float *mlp, void *stream);
+/* Training pairs for n normalised-space points x [n][3] of pose p from the
+ * plain search: label [n] int32 (-1 where no valid root), offset [n][3] (device). */
+ia_status ia_proposal_pairs(ia_ctx *ctx, int pose, int n, const float *x, int32_t *label, float *offset,
+                            void *stream);
+/* Loss and gradients over n pairs (device: x [n][3], pose [n], label [n] in
+ * [0, n_b), target [n][3]); *loss is overwritten; g_table and g_mlp are laid out
+ * like the parameters. */
+ia_status ia_proposal_grad(ia_ctx *ctx, int n, const float *x, const int32_t *pose, const int32_t *label,
+                           const float *target, float *loss, float *g_table, float *g_mlp, void *stream);
+/* `steps` Adam steps of `batch` pairs each, taking pairs in order and wrapping
+ * around (shuffle them beforehand); loss_out [steps] (device, may be NULL)
+ * receives each step's batch loss.  Workspace for `batch` pairs (~2.3 KB each)
+ * is allocated on first use. */
+ia_status ia_proposal_train(ia_ctx *ctx, int n, const float *x, const int32_t *pose, const int32_t *label,
+                            const float *target, int steps, int batch, float lr, float *loss_out,
+                            void *stream);
+/* IA_SEARCH_ALL_BONES (the paper's search) or IA_SEARCH_PROPOSAL. */
+ia_status ia_set_search(ia_ctx *ctx, int mode);
 
 /* The sample set of ia_render without evaluating it (the indexing contract):
  * bit i of slot_mask[(v * W + u) * ceil(N / 32) + i / 32] is set iff slot i of

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libia.so")
 IA_OK, IA_ERR_ARG, IA_ERR_STATE, IA_ERR_CUDA, IA_ERR_OOM, IA_ERR_LIMIT = range(6)
 IA_FP32, IA_FP16, IA_BF16 = 0, 1, 2
 IA_OCC_POSE, IA_OCC_UNION = 0, 1
+IA_SEARCH_ALL_BONES, IA_SEARCH_PROPOSAL = 0, 1
 MAX_LEVELS = 16
 
 
@@ -42,10 +43,17 @@ class Camera(C.Structure):
 
 class RenderStats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("rays", "hit_rays", "marched_slots", "occupied_samples", "starts",
-                                         "broyden_iters", "converged", "roots", "early_stopped")]
+                                         "broyden_iters", "converged", "roots", "early_stopped", "proposed",
+                                         "fallbacks")]
+
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+class ProposalConfig(C.Structure):
+    _fields_ = [("n_levels", C.c_int), ("log2_table", C.c_int), ("level_res", C.c_int * MAX_LEVELS),
+                ("top_k", C.c_int), ("offset_weight", C.c_float)]
 
 
 class Batch(C.Structure):
@@ -86,6 +94,14 @@ def lib():
             "ia_march_mask": [P, I, C.POINTER(Camera), P, V],
             "ia_train_step": [P, C.POINTER(Batch), I, P, P, C.POINTER(Grads), V],
             "ia_update_occupancy_static": [P, I, P, V],
+            "ia_proposal_init": [P, C.POINTER(ProposalConfig)],
+            "ia_proposal_param_sizes": [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
+            "ia_proposal_set_params": [P, P, P, V],
+            "ia_proposal_get_params": [P, P, P, V],
+            "ia_proposal_pairs": [P, I, I, P, P, P, V],
+            "ia_proposal_grad": [P, I, P, P, P, P, P, P, P, V],
+            "ia_proposal_train": [P, I, P, P, P, P, I, I, C.c_float, P, V],
+            "ia_set_search": [P, I],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -254,3 +270,48 @@ def ia_train_step(ctx, origin, direction, pose, target, loss, grads, occ_grid=IA
 def ia_update_occupancy_static(ctx, pose, bits_out=None, stream=None):
     """Occupancy refresh that allocates nothing (fixed 64^3-cell scratch in the library)."""
     _check(lib().ia_update_occupancy_static(ctx, pose, _ptr(bits_out), _stream(stream)), ctx)
+
+
+def make_proposal_config(n_levels, log2_table, level_res, top_k=2, offset_weight=100.0):
+    q = ProposalConfig()
+    q.n_levels, q.log2_table, q.top_k, q.offset_weight = n_levels, log2_table, top_k, offset_weight
+    for i, r in enumerate(level_res):
+        q.level_res[i] = int(r)
+    return q
+
+
+def ia_proposal_init(ctx, cfg: ProposalConfig):
+    _check(lib().ia_proposal_init(ctx, C.byref(cfg)), ctx)
+
+
+def ia_proposal_param_sizes(ctx):
+    a, b = C.c_int64(), C.c_int64()
+    _check(lib().ia_proposal_param_sizes(ctx, C.byref(a), C.byref(b)), ctx)
+    return a.value, b.value
+
+
+def ia_proposal_set_params(ctx, table, mlp, stream=None):
+    _check(lib().ia_proposal_set_params(ctx, _ptr(table), _ptr(mlp), _stream(stream)), ctx)
+
+
+def ia_proposal_get_params(ctx, table, mlp, stream=None):
+    _check(lib().ia_proposal_get_params(ctx, _ptr(table), _ptr(mlp), _stream(stream)), ctx)
+
+
+def ia_proposal_pairs(ctx, pose, x, label, offset, stream=None):
+    _check(lib().ia_proposal_pairs(ctx, pose, int(x.shape[0]), _ptr(x), _ptr(label), _ptr(offset),
+                                   _stream(stream)), ctx)
+
+
+def ia_proposal_grad(ctx, x, pose, label, target, loss, g_table, g_mlp, stream=None):
+    _check(lib().ia_proposal_grad(ctx, int(x.shape[0]), _ptr(x), _ptr(pose), _ptr(label), _ptr(target), _ptr(loss),
+                                  _ptr(g_table), _ptr(g_mlp), _stream(stream)), ctx)
+
+
+def ia_proposal_train(ctx, x, pose, label, target, steps, batch, lr, loss_out=None, stream=None):
+    _check(lib().ia_proposal_train(ctx, int(x.shape[0]), _ptr(x), _ptr(pose), _ptr(label), _ptr(target), int(steps),
+                                   int(batch), float(lr), _ptr(loss_out), _stream(stream)), ctx)
+
+
+def ia_set_search(ctx, mode):
+    _check(lib().ia_set_search(ctx, mode), ctx)

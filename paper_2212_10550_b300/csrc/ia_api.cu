@@ -67,6 +67,25 @@ struct ia_ctx {
   float4* d_s_x = nullptr;
   float4* d_s_grad = nullptr;
   float* d_act = nullptr;
+  // proposal network
+  bool prop_ready = false;
+  int search = IA_SEARCH_ALL_BONES;
+  ia_proposal_config pcfg{};
+  Level plv[kMaxLevels]{};
+  int64_t p_entries = 0, p_mlp = 0;
+  float* d_pp = nullptr;      // parameters: table then MLP (one allocation)
+  float* d_ptable = nullptr;  // views into d_pp
+  float* d_pmlp = nullptr;
+  float* d_ploss = nullptr;   // scratch loss of training steps
+  float* d_pg = nullptr;   // gradients: table then MLP
+  float* d_pm = nullptr;   // Adam first moments (same layout)
+  float* d_pv = nullptr;   // Adam second moments
+  int adam_step = 0;
+  int prow_cap = 0;
+  float* d_prows = nullptr;
+  int pair_cap = 0;
+  float* d_pxc = nullptr;
+  int* d_pstart = nullptr;
 };
 
 namespace {
@@ -131,6 +150,22 @@ FieldDev field_dev(const ia_ctx* c) {
   return F;
 }
 
+PropDev prop_dev(const ia_ctx* c) {
+  PropDev Q{};
+  if (!c->prop_ready) return Q;
+  Q.table = reinterpret_cast<const float2*>(c->d_ptable);
+  Q.L = c->pcfg.n_levels;
+  for (int l = 0; l < kMaxLevels; ++l) Q.lv[l] = c->plv[l];
+  for (int a = 0; a < 3; ++a) {
+    Q.nmin[a] = c->nmin[a];
+    Q.inv_ext[a] = 1.0f / (c->nmax[a] - c->nmin[a]);
+  }
+  Q.mlp = c->d_pmlp;
+  Q.n_in = 2 * c->pcfg.n_levels + 3 * c->nb;
+  Q.top_k = c->pcfg.top_k;
+  return Q;
+}
+
 PosedArgs posed_args(const ia_ctx* c, int pose) {
   PosedArgs a{};
   a.S.M = c->d_M + (size_t)pose * c->Rw * c->Rw * c->Rw * 3;
@@ -149,6 +184,9 @@ PosedArgs posed_args(const ia_ctx* c, int pose) {
   a.n_in = c->n_in;
   a.prec = c->cfg.precision;
   a.table_h = c->d_table_h;
+  a.search = (c->search == IA_SEARCH_PROPOSAL && c->prop_ready && c->cfg.precision != IA_FP32) ? 1 : 0;
+  a.prop = prop_dev(c);
+  a.theta = c->d_theta ? c->d_theta + (size_t)pose * c->nb * 3 : nullptr;
   return a;
 }
 
@@ -199,6 +237,8 @@ void read_stats(ia_ctx* c, ia_render_stats* out, cudaStream_t s) {
   out->converged = (int64_t)h[ST_CONV];
   out->roots = (int64_t)h[ST_ROOTS];
   out->early_stopped = (int64_t)h[ST_EARLY];
+  out->proposed = (int64_t)h[ST_PROP];
+  out->fallbacks = (int64_t)h[ST_FALLBACK];
 }
 
 }  // namespace
@@ -305,6 +345,14 @@ void ia_destroy(ia_ctx* c) {
   dfree(c->d_s_x);
   dfree(c->d_s_grad);
   dfree(c->d_act);
+  dfree(c->d_pp);
+  dfree(c->d_ploss);
+  dfree(c->d_pg);
+  dfree(c->d_pm);
+  dfree(c->d_pv);
+  dfree(c->d_prows);
+  dfree(c->d_pxc);
+  dfree(c->d_pstart);
   delete c;
 }
 
@@ -645,6 +693,214 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
   a.g_skin = g->skin;
   a.g_bones = g->bones;
   IA_CUDA(c, launch_train(a, c->num_sms, s), "ia_train_step: kernels");
+  return IA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Learned correspondence proposal
+// ---------------------------------------------------------------------------
+
+ia_status ia_proposal_init(ia_ctx* c, const ia_proposal_config* q) {
+  if (!c || !q) return fail(c, IA_ERR_ARG, "null argument");
+  if (c->nb == 0) return fail(c, IA_ERR_STATE, "ia_set_skeleton has not been called");
+  if (q->n_levels < 1 || q->n_levels > 8) return fail(c, IA_ERR_ARG, "proposal n_levels must be 1..8");
+  if (q->log2_table < 10 || q->log2_table > 24) return fail(c, IA_ERR_ARG, "proposal log2_table must be 10..24");
+  for (int l = 0; l < q->n_levels; ++l)
+    if (q->level_res[l] < 2 || q->level_res[l] > (1 << 16)) return fail(c, IA_ERR_ARG, "bad proposal level_res");
+  if (q->top_k < 1 || q->top_k > 2) return fail(c, IA_ERR_ARG, "top_k must be 1 or 2");
+  if (!(q->offset_weight >= 0.f) || !std::isfinite(q->offset_weight)) return fail(c, IA_ERR_ARG, "bad offset_weight");
+  if (c->nb + 3 > kPropMaxOut) return fail(c, IA_ERR_LIMIT, "the proposal supports at most %d bones", kPropMaxOut - 3);
+  const int64_t T = 1LL << q->log2_table;
+  int64_t off = 0;
+  for (int l = 0; l < q->n_levels; ++l) {
+    const int64_t r1 = (int64_t)q->level_res[l] + 1, dense = r1 * r1 * r1;
+    c->plv[l].res = q->level_res[l];
+    c->plv[l].dense = dense <= T ? 1 : 0;
+    c->plv[l].size = (uint32_t)(dense <= T ? dense : T);
+    c->plv[l].offset = (uint32_t)off;
+    off += c->plv[l].size;
+  }
+  c->pcfg = *q;
+  c->p_entries = off;
+  const int nin = 2 * q->n_levels + 3 * c->nb;
+  c->p_mlp = (int64_t)kWidth * nin + kWidth + 2 * ((int64_t)kWidth * kWidth + kWidth) + (int64_t)(c->nb + 3) * kWidth +
+             (c->nb + 3);
+  const size_t np = (size_t)(2 * off + c->p_mlp);
+  c->prop_ready = false;
+  IA_CUDA(c, dalloc(&c->d_pp, np), "ia_proposal_init");
+  c->d_ptable = c->d_pp;
+  c->d_pmlp = c->d_pp + 2 * off;
+  IA_CUDA(c, dalloc(&c->d_ploss, (size_t)1), "ia_proposal_init");
+  IA_CUDA(c, dalloc(&c->d_pg, np), "ia_proposal_init");
+  IA_CUDA(c, dalloc(&c->d_pm, np), "ia_proposal_init");
+  IA_CUDA(c, dalloc(&c->d_pv, np), "ia_proposal_init");
+  IA_CUDA(c, cudaMemset(c->d_ptable, 0, sizeof(float) * 2 * off), "ia_proposal_init");
+  IA_CUDA(c, cudaMemset(c->d_pmlp, 0, sizeof(float) * c->p_mlp), "ia_proposal_init");
+  IA_CUDA(c, cudaMemset(c->d_pm, 0, sizeof(float) * np), "ia_proposal_init");
+  IA_CUDA(c, cudaMemset(c->d_pv, 0, sizeof(float) * np), "ia_proposal_init");
+  c->adam_step = 0;
+  c->prop_ready = true;
+  return IA_OK;
+}
+
+ia_status ia_proposal_param_sizes(const ia_ctx* c, int64_t* table_floats, int64_t* mlp_floats) {
+  if (!c) return fail(nullptr, IA_ERR_ARG, "null context");
+  if (!c->prop_ready) return fail(const_cast<ia_ctx*>(c), IA_ERR_STATE, "ia_proposal_init has not been called");
+  if (table_floats) *table_floats = 2 * c->p_entries;
+  if (mlp_floats) *mlp_floats = c->p_mlp;
+  return IA_OK;
+}
+
+ia_status ia_proposal_set_params(ia_ctx* c, const float* table, const float* mlp, void* stream) {
+  if (!c) return fail(nullptr, IA_ERR_ARG, "null context");
+  if (!c->prop_ready) return fail(c, IA_ERR_STATE, "ia_proposal_init has not been called");
+  if (!table || !mlp) return fail(c, IA_ERR_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t np = (size_t)(2 * c->p_entries + c->p_mlp);
+  IA_CUDA(c, cudaMemcpyAsync(c->d_ptable, table, sizeof(float) * 2 * c->p_entries, cudaMemcpyDefault, s),
+          "ia_proposal_set_params");
+  IA_CUDA(c, cudaMemcpyAsync(c->d_pmlp, mlp, sizeof(float) * c->p_mlp, cudaMemcpyDefault, s), "ia_proposal_set_params");
+  IA_CUDA(c, cudaMemsetAsync(c->d_pm, 0, sizeof(float) * np, s), "ia_proposal_set_params");
+  IA_CUDA(c, cudaMemsetAsync(c->d_pv, 0, sizeof(float) * np, s), "ia_proposal_set_params");
+  c->adam_step = 0;
+  return IA_OK;
+}
+
+ia_status ia_proposal_get_params(ia_ctx* c, float* table, float* mlp, void* stream) {
+  if (!c) return fail(nullptr, IA_ERR_ARG, "null context");
+  if (!c->prop_ready) return fail(c, IA_ERR_STATE, "ia_proposal_init has not been called");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (table)
+    IA_CUDA(c, cudaMemcpyAsync(table, c->d_ptable, sizeof(float) * 2 * c->p_entries, cudaMemcpyDefault, s),
+            "ia_proposal_get_params");
+  if (mlp) IA_CUDA(c, cudaMemcpyAsync(mlp, c->d_pmlp, sizeof(float) * c->p_mlp, cudaMemcpyDefault, s), "ia_proposal_get_params");
+  IA_CUDA(c, cudaStreamSynchronize(s), "ia_proposal_get_params");
+  return IA_OK;
+}
+
+ia_status ia_proposal_pairs(ia_ctx* c, int pose, int n, const float* x, int32_t* label, float* offset,
+                            void* stream) {
+  ia_status st = need_ready(c, pose, false);
+  if (st != IA_OK) return st;
+  if (n < 0 || (n > 0 && (!x || !label || !offset))) return fail(c, IA_ERR_ARG, "bad arrays");
+  if (n == 0) return IA_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n > c->pair_cap) {
+    IA_CUDA(c, cudaStreamSynchronize(s), "ia_proposal_pairs");
+    c->pair_cap = 0;
+    IA_CUDA(c, dalloc(&c->d_pxc, (size_t)3 * n), "ia_proposal_pairs: workspace");
+    IA_CUDA(c, dalloc(&c->d_pstart, (size_t)n), "ia_proposal_pairs: workspace");
+    c->pair_cap = n;
+  }
+  PosedArgs a = posed_args(c, pose);
+  a.search = 0;  // labels come from the plain search over every bone
+  IA_CUDA(c, launch_query_posed(a, n, x, nullptr, nullptr, c->d_pxc, c->d_pstart, s), "ia_proposal_pairs: search");
+  PropLabelArgs la{};
+  la.S = a.S;
+  la.skin = c->d_skin;
+  la.nb = c->nb;
+  la.Ninv = a.Ninv;
+  la.n = n;
+  la.x = x;
+  la.xc = c->d_pxc;
+  la.start = c->d_pstart;
+  la.label = label;
+  la.offset = offset;
+  IA_CUDA(c, launch_prop_label(la, s), "ia_proposal_pairs: labels");
+  return IA_OK;
+}
+
+static ia_status prop_check(ia_ctx* c, int n, const float* x, const int32_t* pose, const int32_t* label,
+                            const float* target) {
+  if (!c) return fail(nullptr, IA_ERR_ARG, "null context");
+  if (!c->prop_ready) return fail(c, IA_ERR_STATE, "ia_proposal_init has not been called");
+  if (c->n_poses == 0) return fail(c, IA_ERR_STATE, "ia_set_pose has not been called");
+  if (n < 1 || !x || !pose || !label || !target) return fail(c, IA_ERR_ARG, "bad pair arrays");
+  return IA_OK;
+}
+
+static ia_status prop_workspace(ia_ctx* c, int batch, cudaStream_t s) {
+  if (batch > c->prow_cap) {
+    IA_CUDA(c, cudaStreamSynchronize(s), "proposal workspace");
+    c->prow_cap = 0;
+    IA_CUDA(c, dalloc(&c->d_prows, (size_t)batch * kPropRow), "proposal workspace");
+    c->prow_cap = batch;
+  }
+  return IA_OK;
+}
+
+static PropTrainArgs prop_train_args(ia_ctx* c, int n, const float* x, const int32_t* pose, const int32_t* label,
+                                     const float* target) {
+  PropTrainArgs a{};
+  a.Q = prop_dev(c);
+  a.nb = c->nb;
+  a.theta = c->d_theta;
+  a.n = n;
+  a.x = x;
+  a.pose = pose;
+  a.label = label;
+  a.target = target;
+  a.offset_weight = c->pcfg.offset_weight;
+  a.rows = c->d_prows;
+  a.g_table = c->d_pg;
+  a.g_mlp = c->d_pg + 2 * c->p_entries;
+  return a;
+}
+
+ia_status ia_proposal_grad(ia_ctx* c, int n, const float* x, const int32_t* pose, const int32_t* label,
+                           const float* target, float* loss, float* g_table, float* g_mlp, void* stream) {
+  ia_status st = prop_check(c, n, x, pose, label, target);
+  if (st != IA_OK) return st;
+  if (!loss) return fail(c, IA_ERR_ARG, "null loss");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = prop_workspace(c, n, s)) != IA_OK) return st;
+  const size_t np = (size_t)(2 * c->p_entries + c->p_mlp);
+  IA_CUDA(c, cudaMemsetAsync(c->d_pg, 0, sizeof(float) * np, s), "ia_proposal_grad");
+  IA_CUDA(c, cudaMemsetAsync(loss, 0, sizeof(float), s), "ia_proposal_grad");
+  PropTrainArgs a = prop_train_args(c, n, x, pose, label, target);
+  a.first = 0;
+  a.batch = n;
+  a.loss = loss;
+  IA_CUDA(c, launch_prop_grad(a, s), "ia_proposal_grad");
+  if (g_table)
+    IA_CUDA(c, cudaMemcpyAsync(g_table, c->d_pg, sizeof(float) * 2 * c->p_entries, cudaMemcpyDefault, s), "ia_proposal_grad");
+  if (g_mlp)
+    IA_CUDA(c, cudaMemcpyAsync(g_mlp, c->d_pg + 2 * c->p_entries, sizeof(float) * c->p_mlp, cudaMemcpyDefault, s),
+            "ia_proposal_grad");
+  return IA_OK;
+}
+
+ia_status ia_proposal_train(ia_ctx* c, int n, const float* x, const int32_t* pose, const int32_t* label,
+                            const float* target, int steps, int batch, float lr, float* loss_out, void* stream) {
+  ia_status st = prop_check(c, n, x, pose, label, target);
+  if (st != IA_OK) return st;
+  if (steps < 0 || batch < 1 || batch > (1 << 22) || !(lr > 0.f)) return fail(c, IA_ERR_ARG, "bad training settings");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = prop_workspace(c, batch, s)) != IA_OK) return st;
+  const size_t np = (size_t)(2 * c->p_entries + c->p_mlp);
+  PropTrainArgs a = prop_train_args(c, n, x, pose, label, target);
+  a.batch = batch;
+  for (int k = 0; k < steps; ++k) {
+    a.first = (int)(((int64_t)k * batch) % n);
+    a.loss = loss_out ? loss_out + k : c->d_ploss;
+    IA_CUDA(c, cudaMemsetAsync(c->d_pg, 0, sizeof(float) * np, s), "ia_proposal_train");
+    IA_CUDA(c, cudaMemsetAsync(a.loss, 0, sizeof(float), s), "ia_proposal_train");
+    IA_CUDA(c, launch_prop_grad(a, s), "ia_proposal_train: gradient");
+    ++c->adam_step;
+    IA_CUDA(c, launch_adam(c->d_pp, c->d_pg, c->d_pm, c->d_pv, (int64_t)np, lr, c->adam_step, s),
+            "ia_proposal_train: adam");
+  }
+  return IA_OK;
+}
+
+ia_status ia_set_search(ia_ctx* c, int mode) {
+  if (!c) return fail(nullptr, IA_ERR_ARG, "null context");
+  if (mode != IA_SEARCH_ALL_BONES && mode != IA_SEARCH_PROPOSAL) return fail(c, IA_ERR_ARG, "unknown search mode");
+  if (mode == IA_SEARCH_PROPOSAL) {
+    if (!c->prop_ready) return fail(c, IA_ERR_STATE, "ia_proposal_init has not been called");
+    if (c->cfg.precision == IA_FP32) return fail(c, IA_ERR_ARG, "the proposal search needs precision fp16 or bf16");
+  }
+  c->search = mode;
   return IA_OK;
 }
 

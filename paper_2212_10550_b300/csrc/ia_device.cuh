@@ -67,7 +67,7 @@ struct SolveCfg {
 };
 
 struct SampleStats {
-  long long starts = 0, iters = 0, converged = 0, roots = 0;
+  long long starts = 0, iters = 0, converged = 0, roots = 0, proposed = 0, fallbacks = 0;
 };
 
 // ---------------------------------------------------------------------------

@@ -11,7 +11,7 @@
 namespace ia {
 
 enum StatIdx {
-  ST_RAYS = 0, ST_HIT, ST_MARCHED, ST_OCC, ST_STARTS, ST_ITERS, ST_CONV, ST_ROOTS, ST_EARLY,
+  ST_RAYS = 0, ST_HIT, ST_MARCHED, ST_OCC, ST_STARTS, ST_ITERS, ST_CONV, ST_ROOTS, ST_EARLY, ST_PROP, ST_FALLBACK,
   ST_COUNT = 16
 };
 
@@ -27,6 +27,9 @@ struct PosedArgs {
   int n_in;
   int prec;            // ia_precision of the field evaluation
   const __half2* table_h;  // fp16 shadow of the hash table (prec != fp32)
+  int search;          // 1: proposal network picks the first starts (prec != fp32)
+  PropDev prop;
+  const double* theta; // [nb][3] axis-angles of the pose (proposal input)
 };
 
 struct RenderArgs {
@@ -84,6 +87,45 @@ struct TrainArgs {
 };
 
 cudaError_t launch_train(const TrainArgs& a, int num_sms, cudaStream_t s);
+
+// Proposal network (ia_prop.cu).
+constexpr int kPropMaxIn = 2 * 8 + 3 * kMaxBones;  // 8 levels x 2 features + 32 bones x 3
+constexpr int kPropRow = kPropMaxIn + 3 * kWidth + 2 * kPropMaxOut + 3 * kWidth;
+
+struct PropLabelArgs {
+  SkinDev S;
+  const float* skin;     // [V][nb]
+  int nb;
+  const float* Ninv;     // [nb][12] of the pose
+  int n;
+  const float* x;        // [n][3] normalised posed points
+  const float* xc;       // [n][3] selected roots
+  const int* start;      // [n] (-1: no root)
+  int* label;            // [n] (-1: no root)
+  float* offset;         // [n][3]
+};
+
+struct PropTrainArgs {
+  PropDev Q;             // fp32 master table and MLP
+  int nb;
+  const double* theta;   // [n_poses][nb][3]
+  int n;                 // pairs
+  int first, batch;      // this step's pairs: (first + i) % n, i < batch
+  const float* x;        // [n][3]
+  const int* pose;       // [n]
+  const int* label;      // [n]
+  const float* target;   // [n][3]
+  float offset_weight;
+  float* rows;           // [batch][kPropRow]
+  float* loss;           // device scalar (accumulated)
+  float* g_table;        // [entries][2]
+  float* g_mlp;          // packed
+};
+
+cudaError_t launch_prop_label(const PropLabelArgs& a, cudaStream_t s);
+cudaError_t launch_prop_grad(const PropTrainArgs& a, cudaStream_t s);
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, int step,
+                        cudaStream_t s);
 
 size_t posed_smem_bytes(int threads);
 size_t render_smem_bytes(int K);

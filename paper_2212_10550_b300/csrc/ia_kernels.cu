@@ -152,7 +152,8 @@ cudaError_t launch_blend(int P, int V, int nb, const float* W, const float* N, f
 constexpr int kMlpPad = (kMlpSmemFloats + 3) / 4 * 4;
 
 __host__ __device__ constexpr int mlp_smem_words(Prec P, int threads) {
-  return P == Prec::F32 ? kMlpPad : ((kMlpHWords + 3) / 4 * 4 + (threads / 32) * kWarpXWords);
+  return P == Prec::F32 ? kMlpPad
+                        : ((kMlpHWords + 3) / 4 * 4 + (kPropWords + 3) / 4 * 4 + (threads / 32) * kStageWords);
 }
 
 template <Prec P>
@@ -179,13 +180,17 @@ __device__ __forceinline__ PosedSmem stage_posed(const PosedArgs& a, float4* sme
     p.fs.sw = base;
     p.fs.swh = nullptr;
     p.fs.xstage = nullptr;
+    p.fs.pw = nullptr;
     stage_mlp(a.mlp, a.n_in, base);
   } else {
     uint32_t* w = reinterpret_cast<uint32_t*>(base);
+    uint32_t* pw = w + (kMlpHWords + 3) / 4 * 4;
     p.fs.sw = nullptr;
     p.fs.swh = w;
-    p.fs.xstage = w + (kMlpHWords + 3) / 4 * 4 + (threadIdx.x >> 5) * kWarpXWords;
+    p.fs.pw = pw;
+    p.fs.xstage = pw + (kPropWords + 3) / 4 * 4 + (threadIdx.x >> 5) * kStageWords;
     stage_mlp_h<P>(a.mlp, a.n_in, w);
+    if (a.search) stage_prop_h<P>(a.prop, a.cfg.nb, a.theta, pw);
   }
   p.sNinv = base + mlp_smem_words(P, blockDim.x);
   p.roots = reinterpret_cast<float4*>(p.sNinv + kMaxBones * 12);
@@ -233,7 +238,7 @@ __global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS)
       Ms[q] = a.S.M;
       Ns[q] = sm.sNinv;
     }
-    posed_field_warp_n<kNS, P>(a.S, Ms, a.F, a.cfg, Ns, sm.fs, sm.roots, act, xn, o, st);
+    posed_field_warp_n<kNS, P>(a.S, Ms, a.F, a.cfg, Ns, sm.fs, sm.roots, act, xn, o, st, a.prop, a.search != 0);
 #pragma unroll
     for (int q = 0; q < kNS; ++q) {
       const int cell = base + q * blockDim.x + threadIdx.x;
@@ -245,6 +250,8 @@ __global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS)
     flush_stats(stats, ST_ITERS, st.iters);
     flush_stats(stats, ST_CONV, st.converged);
     flush_stats(stats, ST_ROOTS, st.roots);
+    flush_stats(stats, ST_PROP, st.proposed);
+    flush_stats(stats, ST_FALLBACK, st.fallbacks);
   }
 }
 
@@ -334,7 +341,7 @@ __global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS)
       Ms[q] = a.S.M;
       Ns[q] = sm.sNinv;
     }
-    posed_field_warp_n<kNS, P>(a.S, Ms, a.F, a.cfg, Ns, sm.fs, sm.roots, act, xn, o, st);
+    posed_field_warp_n<kNS, P>(a.S, Ms, a.F, a.cfg, Ns, sm.fs, sm.roots, act, xn, o, st, a.prop, a.search != 0);
 #pragma unroll
     for (int q = 0; q < kNS; ++q) {
       const int i = base + q * blockDim.x + threadIdx.x;
@@ -571,7 +578,8 @@ __global__ void __launch_bounds__(kRenderThreads, IA_RENDER_MIN_BLOCKS) render_k
         Ms[q] = a.P.S.M;
         Ns[q] = sm.sNinv;
       }
-      posed_field_warp_n<kNS, P>(a.P.S, Ms, a.P.F, a.P.cfg, Ns, sm.fs, sm.roots, act, xn, r, st);
+      posed_field_warp_n<kNS, P>(a.P.S, Ms, a.P.F, a.P.cfg, Ns, sm.fs, sm.roots, act, xn, r, st, a.P.prop,
+                                 a.P.search != 0);
 #pragma unroll
       for (int q = 0; q < kNS; ++q) {
         const int sidx = base + q * 32 + lane;
@@ -611,6 +619,8 @@ __global__ void __launch_bounds__(kRenderThreads, IA_RENDER_MIN_BLOCKS) render_k
     flush_stats(a.stats, ST_CONV, st.converged);
     flush_stats(a.stats, ST_ROOTS, st.roots);
     flush_stats(a.stats, ST_EARLY, n_early);
+    flush_stats(a.stats, ST_PROP, st.proposed);
+    flush_stats(a.stats, ST_FALLBACK, st.fallbacks);
   }
 }
 

@@ -4,6 +4,7 @@
 
 #include "ia_device.cuh"
 #include "ia_mma.cuh"
+#include "ia_prop.cuh"
 
 namespace ia {
 
@@ -11,7 +12,8 @@ namespace ia {
 struct FieldSmem {
   const float* sw;           // fp32 MLP in the layout of stage_mlp (Prec::F32)
   const uint32_t* swh;       // reduced-precision MLP in the layout of stage_mlp_h
-  uint32_t* xstage;          // this warp's staging area (kWarpXWords words)
+  uint32_t* xstage;          // this warp's staging area (kStageWords words)
+  const uint32_t* pw;        // proposal network in the layout of stage_prop_h (or null)
   const float* gmlp;         // packed fp32 MLP in global memory
   int n_in;
   const __half2* table_h;    // fp16 shadow of the hash table (reduced precision)
@@ -56,13 +58,53 @@ __device__ __forceinline__ void field_eval_lane(const FieldDev& F, const FieldSm
 // The first kMaxRoots distinct roots of a sample are evaluated together by the
 // warp after the search; any further distinct root (rare) is evaluated on the
 // spot so that no root is ever dropped.
+// With use_prop (warp-uniform; reduced precision only) the proposal network
+// picks each sample's first starts: the top_k bones by logit (ties to the lower
+// bone), the first shifted by the predicted offset; when none of them yields a
+// valid root the search continues over every bone-wise start (the fallback).
 template <int NS, Prec P>
 __device__ __forceinline__ void posed_field_warp_n(const SkinDev& S, const float4* const* M, const FieldDev& F,
                                                    const SolveCfg& cfg, const float* const* Ninv, const FieldSmem& fs,
                                                    float4* roots, const bool* active, const float3* xn,
-                                                   PosedOut* out, SampleStats& st) {
+                                                   PosedOut* out, SampleStats& st, const PropDev& Q = PropDev{},
+                                                   bool use_prop = false) {
   const int tid = threadIdx.x, stride = blockDim.x;
+  // ---- proposed starts
+  int nprop[NS], pk[NS][2];
+  float3 poff[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    nprop[s] = 0;
+    pk[s][0] = pk[s][1] = 0;
+    poff[s] = make_float3(0.f, 0.f, 0.f);
+  }
+  if constexpr (P != Prec::F32) {
+    if (use_prop) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        float f16[16];
+        prop_encode(Q, active[s] ? xn[s] : make_float3(Q.nmin[0], Q.nmin[1], Q.nmin[2]), f16);
+        const float* O = prop_mma_warp<P>(fs.pw, fs.xstage, f16) + (threadIdx.x & 31) * (kPropMaxOut + 1);
+        if (active[s]) {
+          int b0 = 0, b1 = -1;
+          float v0 = O[0], v1 = -3.0e38f;
+          for (int i = 1; i < cfg.nb; ++i) {
+            const float v = O[i];
+            if (v > v0) { b1 = b0; v1 = v0; b0 = i; v0 = v; }
+            else if (v > v1) { b1 = i; v1 = v; }
+          }
+          pk[s][0] = b0;
+          pk[s][1] = b1 < 0 ? b0 : b1;
+          nprop[s] = min(Q.top_k, cfg.nb);
+          poff[s] = make_float3(O[cfg.nb], O[cfg.nb + 1], O[cfg.nb + 2]);
+          st.proposed++;
+        }
+        __syncwarp();  // every lane has read its row before the staging area is reused
+      }
+    }
+  }
   int k[NS], it[NS], nroots[NS], phase[NS];  // phase 0 = start k, 1 = iterate, 2 = done
+  int label[NS];
   float3 x[NS], r[NS], dx[NS];
   float H[NS][9];
 #pragma unroll
@@ -71,7 +113,7 @@ __device__ __forceinline__ void posed_field_warp_n(const SkinDev& S, const float
     out[s].rgb = make_float3(0.f, 0.f, 0.f);
     out[s].xstar = out[s].rgb;
     out[s].start = -1;
-    k[s] = 0; it[s] = 0; nroots[s] = 0;
+    k[s] = 0; it[s] = 0; nroots[s] = 0; label[s] = 0;
     phase[s] = active[s] ? 0 : 2;
     x[s] = make_float3(0.f, 0.f, 0.f); r[s] = x[s]; dx[s] = x[s];
 #pragma unroll
@@ -91,10 +133,14 @@ __device__ __forceinline__ void posed_field_warp_n(const SkinDev& S, const float
     for (int s = 0; s < NS; ++s) {
       q[s] = x[s];
       if (phase[s] == 0) {
-        const float* A = Ninv[s] + 12 * k[s];
+        // starts 0 .. nprop-1 are proposed bones, the rest every bone in order
+        const bool proposed = k[s] < nprop[s];
+        label[s] = proposed ? (k[s] == 0 ? pk[s][0] : pk[s][1]) : k[s] - nprop[s];
+        const float* A = Ninv[s] + 12 * label[s];
         const float3 p = xn[s];
         q[s] = make_float3(A[0] * p.x + A[1] * p.y + A[2] * p.z + A[3], A[4] * p.x + A[5] * p.y + A[6] * p.z + A[7],
                            A[8] * p.x + A[9] * p.y + A[10] * p.z + A[11]);
+        if (proposed && k[s] == 0) q[s] = make_float3(q[s].x + poff[s].x, q[s].y + poff[s].y, q[s].z + poff[s].z);
       } else if (phase[s] == 1) {
         q[s] = make_float3(x[s].x + dx[s].x, x[s].y + dx[s].y, x[s].z + dx[s].z);
       }
@@ -166,19 +212,24 @@ __device__ __forceinline__ void posed_field_warp_n(const SkinDev& S, const float
           if (!dup) {
             st.roots++;
             if (nroots[s] < kMaxRoots) {
-              roots[((s * kMaxRoots) + nroots[s]) * stride + tid] = make_float4(x[s].x, x[s].y, x[s].z, __int_as_float(k[s]));
+              roots[((s * kMaxRoots) + nroots[s]) * stride + tid] =
+                  make_float4(x[s].x, x[s].y, x[s].z, __int_as_float(label[s]));
             } else {
               const float3 xs = polish_root(S, M[s], x[s], xn[s]);
               float sig;
               float3 rgb;
               field_eval_lane<P>(F, fs, xs, sig, rgb);
-              take_best(out[s], sig, rgb, xs, k[s]);
+              take_best(out[s], sig, rgb, xs, label[s]);
             }
             nroots[s]++;
           }
         }
         ++k[s];
-        phase[s] = (k[s] < cfg.nb) ? 0 : 2;
+        if (nprop[s] > 0 && k[s] == nprop[s]) {
+          if (nroots[s] > 0) k[s] = nprop[s] + cfg.nb;  // a proposed start found a root: done
+          else st.fallbacks++;                            // none did: every bone-wise start follows
+        }
+        phase[s] = (k[s] < nprop[s] + cfg.nb) ? 0 : 2;
       }
     }
   }

@@ -73,6 +73,7 @@ __global__ void __launch_bounds__(256) train_sample_kernel(const TrainArgs a) {
   fs.gmlp = a.P.mlp;
   fs.n_in = a.P.n_in;
   fs.table_h = nullptr;
+  fs.pw = nullptr;
   const int n = *a.count;
   const int lane = threadIdx.x & 31;
   SampleStats st;

@@ -103,21 +103,140 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ our arm
 
-def setup_ours(torch, ia, rank):
-    sc = S.make_scene("full", 0)
-    table, mlp = S.make_field(sc, 0)
+def make_ctx(torch, ia, sc, table, mlp, precision, early_T):
     cfg = ia.make_config(n_levels=sc.n_levels, log2_table=sc.log2_table, level_res=sc.level_res,
                          max_samples=sc.max_samples, broyden_max_iter=sc.broyden_max_iter,
                          broyden_tol=sc.broyden_tol, occ_res=sc.occ_res, occ_tau=sc.occ_tau,
-                         occ_dilate=sc.occ_dilate, early_stop_T=EARLY_T)
+                         occ_dilate=sc.occ_dilate, early_stop_T=early_T, precision=precision)
     ctx = ia.ia_create(cfg)
     ia.ia_set_skeleton(ctx, sc.parents, sc.rest_joints, sc.skin_grid, sc.canon_min, sc.canon_max,
                        sc.norm_min, sc.norm_max)
     ia.ia_set_params(ctx, torch.from_numpy(table).cuda(), torch.from_numpy(S.pack_mlp(mlp)).cuda())
-    poses = [S.make_pose(sc, (rank * N_POSES + i) % 1024) for i in range(N_POSES)]
-    cam = S.make_camera(sc)
-    icam = ia.make_camera(cam["fx"], cam["fy"], cam["cx"], cam["cy"], cam["width"], cam["height"], cam["c2w"])
-    return sc, table, mlp, ctx, poses, cam, icam
+    return ctx
+
+
+def occupied_points(bits, sc, n, rng):
+    """Uniform points inside the occupied cells of a packed grid (training-pair sampling)."""
+    R = sc.occ_res
+    occ = np.unpackbits(np.asarray(bits).view(np.uint8), bitorder="little")[:R ** 3].astype(bool)
+    c = rng.choice(np.nonzero(occ)[0], n)
+    ijk = np.stack([c % R, (c // R) % R, c // (R * R)], -1)
+    cs = (sc.norm_max.astype(np.float64) - sc.norm_min) / R
+    return (sc.norm_min + (ijk + rng.uniform(size=(n, 3))) * cs).astype(np.float32)
+
+
+def train_proposal(torch, ia, ctx, sc, n_poses=256, per_pose=8192, steps=1000, batch=8192, lr=2e-3):
+    """Proposal pairs from the plain search over n_poses seed-drawn poses (not the
+    benchmark sequence), then training with the library's kernels."""
+    pc = S.proposal_config()
+    ia.ia_proposal_init(ctx, ia.make_proposal_config(pc["n_levels"], pc["log2_table"], pc["level_res"],
+                                                     pc["top_k"], pc["offset_weight"]))
+    pt, pm = S.proposal_init(sc, pc, 0)
+    ia.ia_proposal_set_params(ctx, torch.from_numpy(pt).cuda(), torch.from_numpy(S.pack_proposal(pm)).cuda())
+    poses = [S.make_pose(sc, 5000 + i) for i in range(n_poses)]
+    ia.ia_set_pose(ctx, np.stack([p[0] for p in poses]), np.stack([p[1] for p in poses]))
+    rng = np.random.default_rng(77)
+    R = sc.occ_res
+    bits = torch.zeros((R ** 3 + 31) // 32, dtype=torch.int32, device="cuda")
+    X, P, L, T = [], [], [], []
+    for i in range(n_poses):
+        ia.ia_update_occupancy(ctx, i, ia.IA_OCC_POSE, None, bits)
+        x = torch.from_numpy(occupied_points(bits.cpu().numpy().view(np.uint32), sc, per_pose, rng)).cuda()
+        lab = torch.zeros(per_pose, dtype=torch.int32, device="cuda")
+        off = torch.zeros(per_pose, 3, device="cuda")
+        ia.ia_proposal_pairs(ctx, i, x, lab, off)
+        X.append(x); P.append(torch.full((per_pose,), i, dtype=torch.int32, device="cuda"))
+        L.append(lab); T.append(off)
+    X, P, L, T = (torch.cat(a) for a in (X, P, L, T))
+    keep = torch.nonzero(L >= 0).squeeze(1)
+    perm = keep[torch.from_numpy(rng.permutation(len(keep))).cuda()]
+    X, P, L, T = (a[perm].contiguous() for a in (X, P, L, T))
+    losses = torch.zeros(steps, device="cuda")
+    t = time.perf_counter()
+    ia.ia_proposal_train(ctx, X, P, L, T, steps, batch, lr, losses)
+    torch.cuda.synchronize()
+    ls = losses.cpu().numpy()
+    return {"pairs": int(len(perm)), "poses": n_poses, "steps": steps, "batch": batch,
+            "train_s": round(time.perf_counter() - t, 3), "loss_first": round(float(ls[0]), 4),
+            "loss_last": round(float(ls[-50:].mean()), 4)}
+
+
+def time_frames(torch, ia, ctx, poses, icam, rgb, alpha, flush, steps, warmup, stream):
+    """Per step: pose + occupancy refresh + render; CUDA events on the stream,
+    L2 flushed before each step outside the events."""
+    def step(i):
+        th, tr = poses[i % len(poses)]
+        ia.ia_set_pose(ctx, th[None], tr[None], stream=stream)
+        ia.ia_update_occupancy(ctx, 0, ia.IA_OCC_POSE, stream=stream)
+        ia.ia_render(ctx, 0, icam, rgb, alpha, stream=stream)
+
+    for i in range(warmup):
+        step(i)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.zero_()
+        a, b, c = ev[i]
+        th, tr = poses[i % len(poses)]
+        a.record(stream)
+        ia.ia_set_pose(ctx, th[None], tr[None], stream=stream)
+        ia.ia_update_occupancy(ctx, 0, ia.IA_OCC_POSE, stream=stream)
+        b.record(stream)
+        ia.ia_render(ctx, 0, icam, rgb, alpha, stream=stream)
+        c.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(c) for a, b, c in ev], [b.elapsed_time(c) for a, b, c in ev]
+
+
+def frame_stats(ia, ctx, poses, icam, rgb, alpha):
+    tot, occ = {}, {}
+    for th, tr in poses:
+        ia.ia_set_pose(ctx, th[None], tr[None])
+        o = ia.ia_update_occupancy(ctx, 0, ia.IA_OCC_POSE, stats=True)
+        r = ia.ia_render(ctx, 0, icam, rgb, alpha, stats=True)
+        for k, v in r.items():
+            tot[k] = tot.get(k, 0) + v
+        for k, v in o.items():
+            occ[k] = occ.get(k, 0) + v
+    n = len(poses)
+    return {k: v / n for k, v in tot.items()}, {k: v / n for k, v in occ.items()}
+
+
+def time_train_step(torch, ia, sc, table, mlp, flush, steps, warmup, stream, n_rays=8192, n_poses=16):
+    """fwd+bwd training step: 8192 random rays over 16 poses, L2 loss, occupancy =
+    union of the 16 per-pose grids, no early termination; optimiser excluded."""
+    ctx = make_ctx(__import__("torch"), ia, sc, table, mlp, 0, 0.0)
+    poses = [S.make_pose(sc, 200 + i) for i in range(n_poses)]
+    ia.ia_set_pose(ctx, np.stack([p[0] for p in poses]), np.stack([p[1] for p in poses]))
+    for i in range(n_poses):
+        ia.ia_update_occupancy(ctx, i, ia.IA_OCC_UNION)
+    rb = S.make_ray_batch(sc, n_rays, n_poses, seed=3)
+    dev = {k: torch.from_numpy(np.ascontiguousarray(rb[k])).cuda() for k in ("origin", "direction", "pose", "target")}
+    nt, nm = ia.ia_param_sizes(ctx)
+    g = dict(table=torch.zeros(nt, device="cuda"), mlp=torch.zeros(nm, device="cuda"),
+             skin=torch.zeros(sc.skin_res ** 3 * sc.n_bones, device="cuda"),
+             bones=torch.zeros(n_poses * sc.n_bones * 12, device="cuda"))
+    loss = torch.zeros(1, device="cuda")
+
+    def step():
+        loss.zero_()
+        ia.ia_train_step(ctx, dev["origin"], dev["direction"], dev["pose"], dev["target"], loss, g,
+                         occ_grid=ia.IA_OCC_UNION, stream=stream)
+
+    for _ in range(warmup):
+        step()
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    ia.ia_destroy(ctx)
+    return ms
 
 
 def run_ours(args, rank, world, local_rank):
@@ -126,61 +245,36 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    sc, table, mlp, ctx, poses, cam, icam = setup_ours(torch, ia, rank)
+    stream = torch.cuda.current_stream()
+    sc = S.make_scene("full", 0)
+    table, mlp = S.make_field(sc, 0)
+    poses = [S.make_pose(sc, (rank * N_POSES + i) % 1024) for i in range(N_POSES)]
+    cam = S.make_camera(sc)
+    icam = ia.make_camera(cam["fx"], cam["fy"], cam["cx"], cam["cy"], cam["width"], cam["height"], cam["c2w"])
     W, H = cam["width"], cam["height"]
     rgb = torch.zeros(W * H, 3, device=dev)
     alpha = torch.zeros(W * H, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
 
-    def step(i):
-        th, tr = poses[i % N_POSES]
-        ia.ia_set_pose(ctx, th[None], tr[None], stream=stream)
-        ia.ia_update_occupancy(ctx, 0, ia.IA_OCC_POSE, stream=stream)
-        ia.ia_render(ctx, 0, icam, rgb, alpha, stream=stream)
-
-    # per-step work counters (one untimed pass over the whole sequence)
-    tot = {}
-    occ_tot = {}
-    for i in range(N_POSES):
-        th, tr = poses[i]
+    # ---- plain fp32 multi-start (the headline workload)
+    ctx = make_ctx(torch, ia, sc, table, mlp, 0, EARLY_T)
+    per_frame, occ_per_frame = frame_stats(ia, ctx, poses, icam, rgb, alpha)
+    ref_rgb = []
+    for th, tr in poses[:4]:
         ia.ia_set_pose(ctx, th[None], tr[None])
-        o = ia.ia_update_occupancy(ctx, 0, ia.IA_OCC_POSE, stats=True)
-        r = ia.ia_render(ctx, 0, icam, rgb, alpha, stats=True)
-        for k, v in r.items():
-            tot[k] = tot.get(k, 0) + v
-        for k, v in o.items():
-            occ_tot[k] = occ_tot.get(k, 0) + v
-    per_frame = {k: v / N_POSES for k, v in tot.items()}
-    occ_per_frame = {k: v / N_POSES for k, v in occ_tot.items()}
-
-    for i in range(args.warmup):
-        step(i)
-    torch.cuda.synchronize()
+        ia.ia_update_occupancy(ctx, 0)
+        ia.ia_render(ctx, 0, icam, rgb, alpha)
+        ref_rgb.append((rgb.clone(), alpha.clone()))
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     clocks = ClockSampler(local_rank)
     clocks.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for i in range(args.steps):
-        flush.zero_()  # L2 flush outside the timed events
-        a, b, c = ev[i]
-        th, tr = poses[i % N_POSES]
-        a.record(stream)
-        ia.ia_set_pose(ctx, th[None], tr[None], stream=stream)
-        ia.ia_update_occupancy(ctx, 0, ia.IA_OCC_POSE, stream=stream)
-        b.record(stream)
-        ia.ia_render(ctx, 0, icam, rgb, alpha, stream=stream)
-        c.record(stream)
-    torch.cuda.synchronize()
+    step_ms, render_ms = time_frames(torch, ia, ctx, poses, icam, rgb, alpha, flush, args.steps, args.warmup,
+                                     stream)
     wall = time.perf_counter() - t0
     clk = clocks.stop()
-    step_ms = [a.elapsed_time(c) for a, b, c in ev]
-    render_ms = [b.elapsed_time(c) for a, b, c in ev]
     local_total_s = sum(step_ms) / 1e3
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside
@@ -196,6 +290,37 @@ def run_ours(args, rank, world, local_rank):
         ia.ia_update_occupancy(ctx, 0, ia.IA_OCC_POSE, stream=stream)
         ia.ia_render(ctx, 0, icam, h_rgb, h_a, stream=stream)  # copies back and synchronises
         e2e_s.append(time.perf_counter() - t)
+    ia.ia_destroy(ctx)
+
+    if args.only == "plain":
+        total = sum(step_ms) / 1e3
+        if rank == 0:
+            return {"metric": METRIC, "value": round(args.steps / total, 3), "unit": "frames/s (plain fp32 only)",
+                    "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                    "ms_per_step": round(1e3 * total / args.steps, 4), "higher_is_better": True,
+                    "render_ms": round(statistics.mean(render_ms), 4), "partial": "plain fp32 frames only"}
+        return None
+
+    # ---- fp16 + learned proposal on the same sequence (proposal trained on other poses)
+    ctx16 = make_ctx(torch, ia, sc, table, mlp, 1, EARLY_T)
+    prop_train = train_proposal(torch, ia, ctx16, sc)
+    ia.ia_set_search(ctx16, ia.IA_SEARCH_PROPOSAL)
+    per_frame16, occ16 = frame_stats(ia, ctx16, poses, icam, rgb, alpha)
+    differ = hit = 0
+    for (th, tr), (r0, a0) in zip(poses[:4], ref_rgb):
+        ia.ia_set_pose(ctx16, th[None], tr[None])
+        ia.ia_update_occupancy(ctx16, 0)
+        ia.ia_render(ctx16, 0, icam, rgb, alpha)
+        torch.cuda.synchronize()
+        d = ((rgb - r0).abs() > 2e-3 * r0.abs() + 2e-4).any(dim=1) | ((alpha - a0).abs() > 2e-3 * a0.abs() + 2e-4)
+        differ += int(d.sum().item())
+        hit += int((a0 > 0).sum().item())
+    step16, render16 = time_frames(torch, ia, ctx16, poses, icam, rgb, alpha, flush, args.steps, args.warmup,
+                                   stream)
+    ia.ia_destroy(ctx16)
+
+    # ---- fwd+bwd training step (fp32)
+    train_ms = time_train_step(torch, ia, sc, table, mlp, flush, max(5, args.steps // 10), 3, stream)
 
     if world > 1:
         import torch.distributed as dist
@@ -204,7 +329,6 @@ def run_ours(args, rank, world, local_rank):
         total_s = float(tt.item())
     else:
         total_s = local_total_s
-    ia.ia_destroy(ctx)
     if rank != 0:
         return None
     frames = args.steps * world
@@ -217,10 +341,11 @@ def run_ours(args, rank, world, local_rank):
                    FLOP_ROOT * per_frame["roots"] + FLOP_SAMPLE * per_frame["occupied_samples"])
     r_ms = statistics.mean(render_ms)
     achieved = flop_render / (r_ms * 1e-3) / 1e12
+    m16 = statistics.mean(step16)
     line = {
         "metric": METRIC,
         "value": round(fps, 3),
-        "unit": "frames/s (540x540, pose + occupancy refresh + render)",
+        "unit": "frames/s (540x540, pose + occupancy refresh + render, plain fp32)",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms_per_step, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -229,12 +354,30 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": f"replicas x{world}", "precision": "fp32", "starts": "all 24 bones"},
         "samples_per_s": round(per_frame["occupied_samples"] * fps, 1),
         "render_only_fps": round(1e3 / r_ms, 3),
+        "mean_broyden_iters_per_sample": round(per_frame["broyden_iters"] / per_frame["occupied_samples"], 2),
         "per_frame": {k: round(v, 1) for k, v in per_frame.items()},
         "occupancy_per_frame": {k: round(v, 1) for k, v in occ_per_frame.items()},
         "step_ms": {"mean": round(statistics.mean(step_ms), 4), "min": round(min(step_ms), 4),
                     "max": round(max(step_ms), 4)},
         "render_ms": {"mean": round(r_ms, 4), "min": round(min(render_ms), 4)},
         "wall_s": round(wall, 3),
+        "fp16_proposal": {
+            "frames_per_s": round(1e3 / m16, 3), "ms_per_step": round(m16, 4),
+            "render_only_fps": round(1e3 / statistics.mean(render16), 3),
+            "samples_per_s": round(per_frame16["occupied_samples"] * 1e3 / m16, 1),
+            "mean_broyden_iters_per_sample": round(per_frame16["broyden_iters"] / per_frame16["occupied_samples"], 2),
+            "mean_starts_per_sample": round(per_frame16["starts"] / per_frame16["occupied_samples"], 2),
+            "fallback_rate": round(per_frame16["fallbacks"] / max(per_frame16["proposed"], 1), 4),
+            "miss_rate_rays": round(differ / max(hit, 1), 5),
+            "miss_definition": "hit rays of 4 frames whose colour or opacity differs from plain fp32 by more "
+                               "than 2e-3 relative + 2e-4",
+            "speedup_vs_plain_fp32": round(statistics.mean(step_ms) / m16, 3),
+            "proposal_training": prop_train,
+            "per_frame": {k: round(v, 1) for k, v in per_frame16.items()},
+        },
+        "train_step_fp32": {"ms": round(statistics.mean(train_ms), 4), "min_ms": round(min(train_ms), 4),
+                            "rays": 8192, "poses": 16, "what": "forward + hand-written backward (all gradients), "
+                            "no optimiser, L2 flushed before each step"},
         "roofline": {"kernel": "render_kernel", "bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                      "traffic": None,
@@ -333,6 +476,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", default="all", choices=["all", "plain"],
+                    help="plain: time only the plain fp32 frames (used for profiling captures)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -225,10 +225,30 @@ typedef struct ia_grads {
  * with lambda = J(x*)^-T dL/dx* (J the analytic Jacobian),
  *   dL/dN_k = -lambda w_k(x*) [x*;1]^T,  dL/dW(v, k) = -c_v(x*) lambda . N_k [x*;1].
  * The selected root is treated as constant.  rgb_out [n][3] (device) may be
- * NULL.  Workspace for n_rays * max_samples samples (about 1.2 KB each) is
- * allocated by the context on first use and grown when a larger batch comes. */
+ * NULL.  Workspace for n_rays * max_samples samples (about 1.2 KB each in fp32,
+ * 0.8 KB in fp16 / bf16) is allocated by the context on first use and grown
+ * when a larger batch comes.
+ *
+ * Precision (Sec. 3.4 trains in half precision): with IA_FP16 / IA_BF16 the
+ * forward uses the reduced-precision field (fp16 hash features, tensor-core MLP),
+ * the MLP backward runs on fp16 / bf16 operands with fp32 accumulation, the
+ * weight gradients are one tensor-core GEMM over the samples, and every
+ * gradient is delivered in fp32 against the fp32 master parameters.  fp16 uses
+ * a dynamic loss scale S (initially 2^14): the output gradient is multiplied by
+ * S before the MLP backward and divided out of every result.  If a scaled
+ * gradient leaves the fp16 range, the step is skipped: all four gradient
+ * buffers are zeroed and S halves; after 1000 clean steps S doubles (at most
+ * 2^24).  bf16 keeps S = 1.  ia_loss_scale reports S and whether the last step
+ * was skipped. */
 ia_status ia_train_step(ia_ctx *ctx, const ia_batch *batch, int occ_grid, float *loss, float *rgb_out,
                         const ia_grads *grads, void *stream);
+
+/* The loss scale S after the last ia_train_step (host float) and whether that
+ * step overflowed and was skipped (host int32, 1 = skipped); either may be NULL,
+ * not both.  Waits on `stream`.  fp32 contexts report S = 1, never skipped.
+ * Returns IA_ERR_CUDA if the tensor-core weight-gradient reduction of a step
+ * gave up waiting on its own copy pipeline (its gradients are then incomplete). */
+ia_status ia_loss_scale(ia_ctx *ctx, float *scale, int32_t *skipped, void *stream);
 
 /* Same result as ia_update_occupancy(ctx, pose, IA_OCC_POSE, NULL, bits_out,
  * NULL, stream), for callers that cannot allocate device memory while they run:

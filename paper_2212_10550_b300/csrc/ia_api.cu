@@ -66,7 +66,14 @@ struct ia_ctx {
   float4* d_s_out = nullptr;
   float4* d_s_x = nullptr;
   float4* d_s_grad = nullptr;
-  float* d_act = nullptr;
+  float* d_act = nullptr;           // fp32 step: per-sample activations
+  uint16_t* d_X = nullptr;          // fp16 / bf16 step: channel-major GEMM operands
+  int64_t x_ld = 0;
+  CUtensorMap x_map{};
+  float* d_scale = nullptr;         // loss scale, overflow flag, clean steps, GEMM wait flag
+  int* d_overflow = nullptr;
+  int* d_good = nullptr;
+  int* d_wg_err = nullptr;
   // proposal network
   bool prop_ready = false;
   int search = IA_SEARCH_ALL_BONES;
@@ -345,6 +352,11 @@ void ia_destroy(ia_ctx* c) {
   dfree(c->d_s_x);
   dfree(c->d_s_grad);
   dfree(c->d_act);
+  dfree(c->d_X);
+  dfree(c->d_scale);
+  dfree(c->d_overflow);
+  dfree(c->d_good);
+  dfree(c->d_wg_err);
   dfree(c->d_pp);
   dfree(c->d_ploss);
   dfree(c->d_pg);
@@ -629,7 +641,6 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
                         const ia_grads* g, void* stream) {
   ia_status st = need_ready(c, 0, false);
   if (st != IA_OK) return st;
-  if (c->cfg.precision != IA_FP32) return fail(c, IA_ERR_ARG, "the training step runs in fp32 only");
   if (!b || !loss || !g || !g->table || !g->mlp || !g->skin || !g->bones) return fail(c, IA_ERR_ARG, "null argument");
   if (b->n_rays < 1 || b->n_rays > (1 << 24)) return fail(c, IA_ERR_ARG, "n_rays must be 1..2^24");
   if (!b->origin || !b->direction || !b->pose || !b->target) return fail(c, IA_ERR_ARG, "null batch array");
@@ -650,14 +661,34 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
     IA_CUDA(c, dalloc(&c->d_s_out, cap), "ia_train_step: workspace");
     IA_CUDA(c, dalloc(&c->d_s_x, cap), "ia_train_step: workspace");
     IA_CUDA(c, dalloc(&c->d_s_grad, cap), "ia_train_step: workspace");
-    IA_CUDA(c, dalloc(&c->d_act, cap * kActStride), "ia_train_step: workspace");
+    if (c->cfg.precision == IA_FP32) {
+      IA_CUDA(c, dalloc(&c->d_act, cap * kActStride), "ia_train_step: workspace");
+    } else {
+      // rows that the backward never writes must stay zero: clear once here
+      const int64_t ld = ((int64_t)cap + kWgChunk - 1) / kWgChunk * kWgChunk;
+      IA_CUDA(c, dalloc(&c->d_X, (size_t)kWgRows * ld), "ia_train_step: workspace");
+      IA_CUDA(c, cudaMemset(c->d_X, 0, sizeof(uint16_t) * kWgRows * ld), "ia_train_step: workspace");
+      IA_CUDA(c, make_wgrad_map(&c->x_map, c->d_X, ld, c->cfg.precision == IA_BF16), "ia_train_step: tensor map");
+      c->x_ld = ld;
+    }
     c->ray_cap = n;
     c->s_cap = cap;
+  }
+  if (c->cfg.precision != IA_FP32 && !c->d_scale) {
+    IA_CUDA(c, dalloc(&c->d_scale, (size_t)1), "ia_train_step: loss scale");
+    IA_CUDA(c, dalloc(&c->d_overflow, (size_t)1), "ia_train_step: loss scale");
+    IA_CUDA(c, dalloc(&c->d_good, (size_t)1), "ia_train_step: loss scale");
+    IA_CUDA(c, dalloc(&c->d_wg_err, (size_t)1), "ia_train_step: loss scale");
+    const float s0 = c->cfg.precision == IA_FP16 ? kInitialLossScale : 1.f;
+    IA_CUDA(c, cudaMemcpy(c->d_scale, &s0, sizeof(float), cudaMemcpyHostToDevice), "ia_train_step: loss scale");
+    IA_CUDA(c, cudaMemset(c->d_good, 0, sizeof(int)), "ia_train_step: loss scale");
+    IA_CUDA(c, cudaMemset(c->d_wg_err, 0, sizeof(int)), "ia_train_step: loss scale");
   }
   int64_t nt = 0, nm = 0;
   ia_param_sizes(c, &nt, &nm);
   const size_t V = (size_t)c->Rw * c->Rw * c->Rw;
   IA_CUDA(c, cudaMemsetAsync(c->d_count, 0, sizeof(int), s), "ia_train_step");
+  if (c->d_overflow) IA_CUDA(c, cudaMemsetAsync(c->d_overflow, 0, sizeof(int), s), "ia_train_step");
   IA_CUDA(c, cudaMemsetAsync(g->table, 0, sizeof(float) * nt, s), "ia_train_step");
   IA_CUDA(c, cudaMemsetAsync(g->mlp, 0, sizeof(float) * nm, s), "ia_train_step");
   IA_CUDA(c, cudaMemsetAsync(g->skin, 0, sizeof(float) * V * c->nb, s), "ia_train_step");
@@ -692,7 +723,37 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
   a.g_mlp = g->mlp;
   a.g_skin = g->skin;
   a.g_bones = g->bones;
-  IA_CUDA(c, launch_train(a, c->num_sms, s), "ia_train_step: kernels");
+  a.prec = c->cfg.precision;
+  a.X = c->d_X;
+  a.ld = c->x_ld;
+  a.scale = c->d_scale;
+  a.overflow = c->d_overflow;
+  a.good_steps = c->d_good;
+  a.err = c->d_wg_err;
+  a.n_table_f = (size_t)nt;
+  a.n_mlp_f = (size_t)nm;
+  a.n_skin_f = V * c->nb;
+  a.n_bones_f = (size_t)c->n_poses * c->nb * 12;
+  IA_CUDA(c, launch_train(a, &c->x_map, c->num_sms, s), "ia_train_step: kernels");
+  return IA_OK;
+}
+
+ia_status ia_loss_scale(ia_ctx* c, float* scale, int32_t* skipped, void* stream) {
+  if (!c) return fail(nullptr, IA_ERR_ARG, "null context");
+  if (!scale && !skipped) return fail(c, IA_ERR_ARG, "null argument");
+  if (!c->d_scale) {  // fp32, or no reduced-precision step yet
+    if (scale) *scale = c->cfg.precision == IA_FP16 ? kInitialLossScale : 1.f;
+    if (skipped) *skipped = 0;
+    return IA_OK;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  int err = 0, ovf = 0;
+  IA_CUDA(c, cudaMemcpyAsync(&err, c->d_wg_err, sizeof(int), cudaMemcpyDeviceToHost, s), "ia_loss_scale");
+  IA_CUDA(c, cudaMemcpyAsync(&ovf, c->d_overflow, sizeof(int), cudaMemcpyDeviceToHost, s), "ia_loss_scale");
+  if (scale) IA_CUDA(c, cudaMemcpyAsync(scale, c->d_scale, sizeof(float), cudaMemcpyDeviceToHost, s), "ia_loss_scale");
+  IA_CUDA(c, cudaStreamSynchronize(s), "ia_loss_scale");
+  if (skipped) *skipped = ovf;
+  if (err) return fail(c, IA_ERR_CUDA, "the tensor-core weight-gradient reduction timed out waiting on its pipeline");
   return IA_OK;
 }
 

@@ -7,6 +7,7 @@
 #include "ia_device.cuh"
 #include "ia_index.cuh"
 #include "ia_posed.cuh"
+#include "ia_wgrad.h"
 
 namespace ia {
 
@@ -15,7 +16,10 @@ enum StatIdx {
   ST_COUNT = 16
 };
 
-constexpr int kRenderThreads = 256;
+#ifndef IA_RENDER_THREADS
+#define IA_RENDER_THREADS 256
+#endif
+constexpr int kRenderThreads = IA_RENDER_THREADS;
 constexpr int kTile = 16;  // rays are handed out in 16 x 16 pixel tiles
 
 struct PosedArgs {
@@ -31,6 +35,19 @@ struct PosedArgs {
   PropDev prop;
   const double* theta; // [nb][3] axis-angles of the pose (proposal input)
 };
+
+__device__ __forceinline__ PosedStage stage_of(const PosedArgs& a) {
+  PosedStage s;
+  s.mlp = a.mlp;
+  s.n_in = a.n_in;
+  s.table_h = a.table_h;
+  s.search = a.search;
+  s.prop = a.prop;
+  s.theta = a.theta;
+  s.Ninv = a.Ninv;
+  s.nb = a.cfg.nb;
+  return s;
+}
 
 struct RenderArgs {
   PosedArgs P;
@@ -84,9 +101,20 @@ struct TrainArgs {
   float* g_mlp;
   float* g_skin;
   float* g_bones;
+  // reduced precision (prec != fp32): channel-major operands of the weight-gradient GEMM
+  int prec;
+  uint16_t* X;           // [kWgRows][ld] fp16 / bf16
+  int64_t ld;            // multiple of 64
+  float* scale;          // dynamic loss scale (device scalar)
+  int* overflow;         // set when a scaled gradient left the fp16 range
+  int* good_steps;       // steps since the last overflow
+  int* err;              // tensor-core pipeline wait expired
+  size_t n_table_f, n_mlp_f, n_skin_f, n_bones_f;  // gradient sizes (floats)
 };
 
-cudaError_t launch_train(const TrainArgs& a, int num_sms, cudaStream_t s);
+constexpr float kInitialLossScale = 16384.f;  // 2^14
+
+cudaError_t launch_train(const TrainArgs& a, const CUtensorMap* map, int num_sms, cudaStream_t s);
 
 // Proposal network (ia_prop.cu).
 constexpr int kPropMaxIn = 2 * 8 + 3 * kMaxBones;  // 8 levels x 2 features + 32 bones x 3

@@ -44,22 +44,26 @@ __device__ void rigid_inv_d(const double* a, double* c) {
   }
 }
 
+// One block per pose, one thread per joint: every joint composes its ancestor
+// path from the root down, G_k = ((L_root L_a1) L_a2) ... L_k, the same
+// left-to-right product the sequential chain forms, so the fp64 results are
+// identical to composing parent-first.
 __global__ void pose_chain_kernel(int P, int nb, const int* __restrict__ parent, const double* __restrict__ rest,
                                   const double* __restrict__ theta, const double* __restrict__ trans,
                                   float* __restrict__ N, float* __restrict__ Ninv, float* __restrict__ B0inv) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double sL[kMaxBones][12];
+  __shared__ double sB0i[12];
+  const int p = blockIdx.x, k = threadIdx.x;
   if (p >= P) return;
-  double G[kMaxBones][12];
-  double B0i[12];
-  for (int k = 0; k < nb; ++k) {
+  if (k < nb) {
     const double* th = theta + ((size_t)p * nb + k) * 3;
     double R[9];
-    double a = __dsqrt_rn(DA(DA(DM(th[0], th[0]), DM(th[1], th[1])), DM(th[2], th[2])));
+    const double a = __dsqrt_rn(DA(DA(DM(th[0], th[0]), DM(th[1], th[1])), DM(th[2], th[2])));
     if (a == 0.0) {
       for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0) ? 1.0 : 0.0;
     } else {
-      double k0 = __ddiv_rn(th[0], a), k1 = __ddiv_rn(th[1], a), k2 = __ddiv_rn(th[2], a);
-      double c = cos(a), s = sin(a), C = DS(1.0, c);
+      const double k0 = __ddiv_rn(th[0], a), k1 = __ddiv_rn(th[1], a), k2 = __ddiv_rn(th[2], a);
+      const double c = cos(a), s = sin(a), C = DS(1.0, c);
       R[0] = DA(c, DM(DM(C, k0), k0));
       R[1] = DS(DM(DM(C, k0), k1), DM(s, k2));
       R[2] = DA(DM(DM(C, k0), k2), DM(s, k1));
@@ -71,27 +75,35 @@ __global__ void pose_chain_kernel(int P, int nb, const int* __restrict__ parent,
       R[8] = DA(c, DM(DM(C, k2), k2));
     }
     const int par = parent[k];
-    double L[12];
     for (int i = 0; i < 3; ++i) {
-      for (int j = 0; j < 3; ++j) L[i * 4 + j] = R[i * 3 + j];
-      L[i * 4 + 3] = (par < 0) ? rest[3 * k + i] : DS(rest[3 * k + i], rest[3 * par + i]);
+      for (int j = 0; j < 3; ++j) sL[k][i * 4 + j] = R[i * 3 + j];
+      sL[k][i * 4 + 3] = (par < 0) ? rest[3 * k + i] : DS(rest[3 * k + i], rest[3 * par + i]);
     }
-    if (par < 0) {
-      for (int q = 0; q < 12; ++q) G[k][q] = L[q];
-    } else {
-      mat34_mul_d(G[par], L, G[k]);
+  }
+  __syncthreads();
+  double B[12];
+  if (k < nb) {
+    int path[kMaxBones], depth = 0;
+    for (int j = k; j >= 0; j = parent[j]) path[depth++] = j;  // k, parent(k), ..., root
+    double G[12], T[12];
+    for (int q = 0; q < 12; ++q) G[q] = sL[path[depth - 1]][q];
+    for (int d = depth - 2; d >= 0; --d) {
+      mat34_mul_d(G, sL[path[d]], T);
+      for (int q = 0; q < 12; ++q) G[q] = T[q];
     }
     // rest-relative bone transform B_k = G_k [I | -j_k] + root translation
-    double B[12];
     for (int i = 0; i < 3; ++i) {
-      for (int j = 0; j < 3; ++j) B[i * 4 + j] = G[k][i * 4 + j];
-      double Rj = DA(DA(DM(G[k][i * 4 + 0], rest[3 * k + 0]), DM(G[k][i * 4 + 1], rest[3 * k + 1])),
-                     DM(G[k][i * 4 + 2], rest[3 * k + 2]));
-      B[i * 4 + 3] = DA(DS(G[k][i * 4 + 3], Rj), trans[(size_t)p * 3 + i]);
+      for (int j = 0; j < 3; ++j) B[i * 4 + j] = G[i * 4 + j];
+      const double Rj = DA(DA(DM(G[i * 4 + 0], rest[3 * k + 0]), DM(G[i * 4 + 1], rest[3 * k + 1])),
+                           DM(G[i * 4 + 2], rest[3 * k + 2]));
+      B[i * 4 + 3] = DA(DS(G[i * 4 + 3], Rj), trans[(size_t)p * 3 + i]);
     }
-    if (k == 0) rigid_inv_d(B, B0i);  // the root is bone 0 (parents precede children)
+    if (k == 0) rigid_inv_d(B, sB0i);  // the root is bone 0 (parents precede children)
+  }
+  __syncthreads();
+  if (k < nb) {
     double Nk[12], Ni[12];
-    mat34_mul_d(B0i, B, Nk);
+    mat34_mul_d(sB0i, B, Nk);
     rigid_inv_d(Nk, Ni);
     float* No = N + ((size_t)p * nb + k) * 12;
     float* Nio = Ninv + ((size_t)p * nb + k) * 12;
@@ -99,13 +111,14 @@ __global__ void pose_chain_kernel(int P, int nb, const int* __restrict__ parent,
       No[q] = (float)Nk[q];
       Nio[q] = (float)Ni[q];
     }
+    if (k == 0)
+      for (int q = 0; q < 12; ++q) B0inv[(size_t)p * 12 + q] = (float)sB0i[q];
   }
-  for (int q = 0; q < 12; ++q) B0inv[(size_t)p * 12 + q] = (float)B0i[q];
 }
 
 cudaError_t launch_pose_chain(int P, int nb, const int* parent, const double* rest, const double* theta,
                               const double* trans, float* N, float* Ninv, float* B0inv, cudaStream_t s) {
-  pose_chain_kernel<<<(P + 63) / 64, 64, 0, s>>>(P, nb, parent, rest, theta, trans, N, Ninv, B0inv);
+  pose_chain_kernel<<<P, 32, 0, s>>>(P, nb, parent, rest, theta, trans, N, Ninv, B0inv);
   return cudaGetLastError();
 }
 
@@ -149,55 +162,12 @@ cudaError_t launch_blend(int P, int V, int nb, const float* W, const float* N, f
 //   pose's N_k^-1, and the per-lane root lists.
 // ---------------------------------------------------------------------------
 
-constexpr int kMlpPad = (kMlpSmemFloats + 3) / 4 * 4;
-
-__host__ __device__ constexpr int mlp_smem_words(Prec P, int threads) {
-  return P == Prec::F32 ? kMlpPad
-                        : ((kMlpHWords + 3) / 4 * 4 + (kPropWords + 3) / 4 * 4 + (threads / 32) * kStageWords);
-}
-
 template <Prec P>
 size_t posed_smem_bytes_p(int threads) {
   return sizeof(float) * (mlp_smem_words(P, threads) + kMaxBones * 12) + sizeof(float4) * kMaxRoots * kNS * threads;
 }
 
 size_t posed_smem_bytes(int threads) { return posed_smem_bytes_p<Prec::F32>(threads); }
-
-struct PosedSmem {
-  FieldSmem fs;
-  float* sNinv;
-  float4* roots;
-};
-
-template <Prec P>
-__device__ __forceinline__ PosedSmem stage_posed(const PosedArgs& a, float4* smem4) {
-  PosedSmem p;
-  float* base = reinterpret_cast<float*>(smem4);
-  p.fs.gmlp = a.mlp;
-  p.fs.n_in = a.n_in;
-  p.fs.table_h = a.table_h;
-  if constexpr (P == Prec::F32) {
-    p.fs.sw = base;
-    p.fs.swh = nullptr;
-    p.fs.xstage = nullptr;
-    p.fs.pw = nullptr;
-    stage_mlp(a.mlp, a.n_in, base);
-  } else {
-    uint32_t* w = reinterpret_cast<uint32_t*>(base);
-    uint32_t* pw = w + (kMlpHWords + 3) / 4 * 4;
-    p.fs.sw = nullptr;
-    p.fs.swh = w;
-    p.fs.pw = pw;
-    p.fs.xstage = pw + (kPropWords + 3) / 4 * 4 + (threadIdx.x >> 5) * kStageWords;
-    stage_mlp_h<P>(a.mlp, a.n_in, w);
-    if (a.search) stage_prop_h<P>(a.prop, a.cfg.nb, a.theta, pw);
-  }
-  p.sNinv = base + mlp_smem_words(P, blockDim.x);
-  p.roots = reinterpret_cast<float4*>(p.sNinv + kMaxBones * 12);
-  for (int t = threadIdx.x; t < a.cfg.nb * 12; t += blockDim.x) p.sNinv[t] = a.Ninv[t];
-  __syncthreads();
-  return p;
-}
 
 __device__ __forceinline__ void flush_stats(unsigned long long* stats, int idx, long long v) {
   // warp-reduce then one atomic per warp
@@ -219,7 +189,7 @@ __global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS)
     occ_density_kernel(const PosedArgs a, const BoxDev box, float* __restrict__ sigma,
                        unsigned long long* __restrict__ stats) {
   extern __shared__ float4 smem4[];
-  PosedSmem sm = stage_posed<P>(a, smem4);
+  PosedSmem sm = stage_posed<P>(stage_of(a), smem4);
   const int n = box.R * box.R * box.R;
   SampleStats st;
   // grid-stride over whole warps so every lane takes part in the warp-level search;
@@ -325,7 +295,7 @@ __global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS)
     query_posed_kernel(const PosedArgs a, int n, const float* __restrict__ x, float* sigma, float* rgb, float* xc,
                        int* start) {
   extern __shared__ float4 smem4[];
-  PosedSmem sm = stage_posed<P>(a, smem4);
+  PosedSmem sm = stage_posed<P>(stage_of(a), smem4);
   SampleStats st;
   for (int base = blockIdx.x * blockDim.x * kNS; base < n; base += gridDim.x * blockDim.x * kNS) {
     bool act[kNS];
@@ -379,7 +349,7 @@ template <Prec P>
 __global__ void __launch_bounds__(256) query_canonical_kernel(const PosedArgs a, int n, const float* __restrict__ x,
                                                               float* sigma, float* rgb) {
   extern __shared__ float4 smem4[];
-  PosedSmem sm = stage_posed<P>(a, smem4);
+  PosedSmem sm = stage_posed<P>(stage_of(a), smem4);
   for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
     const int i = base + threadIdx.x;
     const bool act = i < n;
@@ -450,7 +420,7 @@ __device__ __forceinline__ void tile_pixel(int id, int tiles_x, int W, int H, in
 template <int K, Prec P>
 __global__ void __launch_bounds__(kRenderThreads, IA_RENDER_MIN_BLOCKS) render_kernel(const RenderArgs a) {
   extern __shared__ float4 smem4[];
-  PosedSmem sm = stage_posed<P>(a.P, smem4);
+  PosedSmem sm = stage_posed<P>(stage_of(a.P), smem4);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // this warp's slices of the shared arrays
   float4* const after_roots = sm.roots + kMaxRoots * kNS * kRenderThreads;

@@ -41,6 +41,8 @@ struct HalfOf<Prec::F16> {
     return *reinterpret_cast<uint32_t*>(&h);
   }
   __device__ static float round(float x) { return __half2float(__float2half_rn(x)); }
+  __device__ static uint16_t bits(float x) { return __half_as_ushort(__float2half_rn(x)); }
+  static constexpr float kMax = 65504.f;
 };
 template <>
 struct HalfOf<Prec::BF16> {
@@ -50,6 +52,8 @@ struct HalfOf<Prec::BF16> {
     return *reinterpret_cast<uint32_t*>(&h);
   }
   __device__ static float round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+  __device__ static uint16_t bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+  static constexpr float kMax = 3.38e38f;
 };
 
 // Stage the packed fp32 MLP into the reduced-precision shared layout.

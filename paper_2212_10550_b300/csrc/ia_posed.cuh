@@ -271,4 +271,64 @@ __device__ __forceinline__ void posed_field_warp_n(const SkinDev& S, const float
   }
 }
 
+// ---------------------------------------------------------------------------
+// Shared-memory layout of kernels that evaluate the posed field:
+//   MLP (fp32 layout, or reduced-precision layout + proposal + per-warp
+//   staging), a pose's N_k^-1, and the per-lane root lists.
+// ---------------------------------------------------------------------------
+
+struct PosedStage {
+  const float* mlp;      // packed fp32 MLP (global)
+  int n_in;
+  const __half2* table_h;
+  int search;            // stage the proposal network too
+  PropDev prop;
+  const double* theta;   // pose axis-angles (proposal input)
+  const float* Ninv;     // [nb][12]
+  int nb;
+};
+
+constexpr int kMlpPad = (kMlpSmemFloats + 3) / 4 * 4;
+
+__host__ __device__ constexpr int mlp_smem_words(Prec P, int threads) {
+  return P == Prec::F32 ? kMlpPad
+                        : ((kMlpHWords + 3) / 4 * 4 + (kPropWords + 3) / 4 * 4 + (threads / 32) * kStageWords);
+}
+
+struct PosedSmem {
+  FieldSmem fs;
+  float* sNinv;
+  float4* roots;
+};
+
+template <Prec P>
+__device__ __forceinline__ PosedSmem stage_posed(const PosedStage& a, float4* smem4) {
+  PosedSmem p;
+  float* base = reinterpret_cast<float*>(smem4);
+  p.fs.gmlp = a.mlp;
+  p.fs.n_in = a.n_in;
+  p.fs.table_h = a.table_h;
+  if constexpr (P == Prec::F32) {
+    p.fs.sw = base;
+    p.fs.swh = nullptr;
+    p.fs.xstage = nullptr;
+    p.fs.pw = nullptr;
+    stage_mlp(a.mlp, a.n_in, base);
+  } else {
+    uint32_t* w = reinterpret_cast<uint32_t*>(base);
+    uint32_t* pw = w + (kMlpHWords + 3) / 4 * 4;
+    p.fs.sw = nullptr;
+    p.fs.swh = w;
+    p.fs.pw = pw;
+    p.fs.xstage = pw + (kPropWords + 3) / 4 * 4 + (threadIdx.x >> 5) * kStageWords;
+    stage_mlp_h<P>(a.mlp, a.n_in, w);
+    if (a.search) stage_prop_h<P>(a.prop, a.nb, a.theta, pw);
+  }
+  p.sNinv = base + mlp_smem_words(P, blockDim.x);
+  p.roots = reinterpret_cast<float4*>(p.sNinv + kMaxBones * 12);
+  for (int t = threadIdx.x; t < a.nb * 12; t += blockDim.x) p.sNinv[t] = a.Ninv[t];
+  __syncthreads();
+  return p;
+}
+
 }  // namespace ia

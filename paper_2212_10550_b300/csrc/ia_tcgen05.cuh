@@ -1,0 +1,260 @@
+// Weight-gradient reduction of the reduced-precision training step on the
+// 5th-generation tensor cores (tcgen05 + TMA + TMEM), sm_103a.
+//
+// The per-sample backward writes its recomputed activations and (loss-scaled)
+// gradients channel-major into one fp16/bf16 array X [kWgRows][ld] (a row per
+// channel, a column per sample), so every operand is K-major with K = samples:
+//
+//   rows   0.. 63  dH2        rows 128..191  H1        rows 240..303  H2
+//   rows  64..127  dH1        rows 192..223  F         row  304       1
+//                             row  224       1         rows 305..367  0
+//                             rows 225..239  0         rows 368..371  dO
+//                                                      rows 372..383  0
+//
+//   GEMM 1: D1 [128 x 112] = X[0:128] X[128:240]^T  -> dW2 (rows 0..63, cols 0..63),
+//           db2 (rows 0..63, col 96), dW1 (rows 64..127, cols 64..95), db1 (col 96)
+//   GEMM 2: D2 [128 x 16]  = X[240:368] X[368:384]^T -> dW3^T (rows 0..63, cols 0..3),
+//           db3 (row 64, cols 0..3)
+//
+// Each CTA reduces a contiguous range of 64-sample chunks: one thread issues the
+// TMA loads (16-row boxes, 128-byte swizzle) into a two-stage ring and the MMAs
+// (M = 128, K = 16 per instruction, fp32 accumulation in 128 TMEM columns);
+// the four warps then read the accumulators with tcgen05.ld, unscale and add
+// them to the fp32 gradients.  Every mbarrier wait is bounded: on expiry the
+// kernel records an error, stops issuing, and still frees its TMEM.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "ia_wgrad.h"
+
+namespace ia {
+
+constexpr int kWgStageBytes = kWgRows * kWgChunk * 2; // 48 KiB
+constexpr int kWgStages = 2;
+constexpr int kWgThreads = 128;
+constexpr uint32_t kWgSpinLimit = 1u << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// bounded wait for the phase with the given parity; false when the limit expired
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (uint32_t i = 0; i < kWgSpinLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// K-major operand, 128-byte swizzle: 8-row atoms of 1024 B (stride-dimension
+// byte offset 1024), descriptor version 1, layout type 2 (SWIZZLE_128B).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);         // start address
+  d |= (uint64_t)1 << 16;                        // leading byte offset (unused within one atom)
+  d |= (uint64_t)(1024 >> 4) << 32;              // stride byte offset
+  d |= (uint64_t)1 << 46;                        // version
+  d |= (uint64_t)2 << 61;                        // SWIZZLE_128B
+  return d;
+}
+
+// kind::f16 instruction descriptor: fp32 accumulator, fp16 or bf16 operands,
+// both K-major, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, int bf16) {
+  return (1u << 4) | ((uint32_t)bf16 << 7) | ((uint32_t)bf16 << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(kWgThreads, 1) wgrad_tc_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                               const WgradArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kWgStages * kWgStageBytes);
+  uint64_t* done = full + kWgStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + kWgStages + 1);
+  __shared__ int s_abort;
+
+  const int n = *a.count;
+  const int chunks = (n + kWgChunk - 1) / kWgChunk;
+  const int per = (chunks + gridDim.x - 1) / gridDim.x;
+  const int c0 = blockIdx.x * per, c1 = min(chunks, c0 + per);
+  if (c0 >= c1) return;  // uniform over the CTA
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;\n" ::"r"(smem_u32(tmem_slot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kWgStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&done[s], 1);
+    }
+    mbar_init(&done[kWgStages], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    s_abort = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t tD1 = tmem, tD2 = tmem + 112;
+
+  if (threadIdx.x == 0) {
+    const uint32_t id1 = idesc_f16(128, 112, a.bf16), id2 = idesc_f16(128, 16, a.bf16);
+    bool ok = true;
+    for (int c = c0; c < c1 && ok; ++c) {
+      const int i = c - c0, st = i % kWgStages;
+      uint8_t* base = smem + st * kWgStageBytes;
+      if (i >= kWgStages) ok = mbar_wait(&done[st], ((i / kWgStages) - 1) & 1);  // stage free again
+      if (!ok) break;
+      mbar_expect_tx(&full[st], kWgStageBytes);
+      for (int r = 0; r < kWgRows; r += 16) tma_load_2d(base + r * 128, &tmap, c * kWgChunk, r, &full[st]);
+      ok = mbar_wait(&full[st], (i / kWgStages) & 1);
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t b = smem_u32(base);
+#pragma unroll
+      for (int kk = 0; kk < kWgChunk / 16; ++kk) {
+        const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
+        umma_f16(tD1, smem_desc_sw128(b + kk * 32), smem_desc_sw128(b + 128 * 128 + kk * 32), id1, acc);
+        umma_f16(tD2, smem_desc_sw128(b + 240 * 128 + kk * 32), smem_desc_sw128(b + 368 * 128 + kk * 32), id2, acc);
+      }
+      umma_commit(&done[st]);
+    }
+    if (ok) {
+      umma_commit(&done[kWgStages]);
+      ok = mbar_wait(&done[kWgStages], 0);
+    }
+    if (!ok) {
+      s_abort = 1;
+      atomicExch(a.err, 1);
+    }
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (!s_abort) {
+    const float inv = 1.f / *a.scale;
+    const int row = warp * 32 + lane;  // TMEM lane = accumulator row
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    float v[16];
+    // D1 columns in blocks of 16: 0..63 H1, 64..95 F, 96 ones
+#pragma unroll 1
+    for (int cb = 0; cb < 112; cb += 16) {
+      tmem_ld16(tD1 + lane_base + cb, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int col = cb + j;
+        const float g = v[j] * inv;
+        if (row < 64) {
+          if (col < 64) atomicAdd(a.gW2 + row * 64 + col, g);
+          else if (col == 96) atomicAdd(a.gb2 + row, g);
+        } else {
+          const int r = row - 64;
+          if (col >= 64 && col < 64 + a.n_in) atomicAdd(a.gW1 + r * a.n_in + (col - 64), g);
+          else if (col == 96) atomicAdd(a.gb1 + r, g);
+        }
+      }
+    }
+    tmem_ld16(tD2 + lane_base, v);
+    if (row < 64) {
+#pragma unroll
+      for (int o = 0; o < 4; ++o) atomicAdd(a.gW3 + o * 64 + row, v[o] * inv);
+    } else if (row == 64) {
+#pragma unroll
+      for (int o = 0; o < 4; ++o) atomicAdd(a.gb3 + o, v[o] * inv);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;\n" ::"r"(tmem));
+}
+
+static size_t wgrad_smem_bytes() { return (size_t)kWgStages * kWgStageBytes + 8 * (2 * kWgStages + 1) + 16 + 1024; }
+
+cudaError_t make_wgrad_map(CUtensorMap* map, void* X, int64_t ld, int bf16) {
+  using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static EncodeFn encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = reinterpret_cast<EncodeFn>(fn);
+  }
+  if (ld % kWgChunk != 0 || (reinterpret_cast<uintptr_t>(X) & 15) != 0) return cudaErrorInvalidValue;
+  const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)kWgRows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kWgChunk, 16};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, X, dims,
+                      strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_wgrad_tc(const CUtensorMap& map, const WgradArgs& a, int grid, cudaStream_t s) {
+  const size_t smem = wgrad_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  wgrad_tc_kernel<<<grid, kWgThreads, smem, s>>>(map, a);
+  return cudaGetLastError();
+}
+
+}  // namespace ia

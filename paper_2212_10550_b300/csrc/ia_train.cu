@@ -1,5 +1,6 @@
 // Training step of the articulated radiance-field path: L2 photometric loss and
-// its hand-written backward (sm_103a, fp32).
+// its hand-written backward (sm_103a; fp32, or fp16 / bf16 operands with fp32
+// accumulation and master gradients).
 //
 //   train_march_kernel      world rays -> normalised space of each ray's pose,
 //                           occupied slots, compacted sample list
@@ -16,10 +17,16 @@
 //   mlp_grad_kernel         weight gradients dW = sum_s dH_s^T A_s as split-K
 //                           reductions over the samples
 //
+// In fp16 / bf16 the forward runs the tensor-core field, train_backward_h_kernel
+// replaces the per-sample backward (loss-scaled, channel-major operands), and
+// the weight gradients come from the tcgen05 GEMM of wgrad_tc_kernel; a
+// loss-scale update closes the step.
+//
 // Per-sample activations are recomputed from x* in the backward (nothing of the
 // MLP is kept from the forward); the backward writes them once, next to their
 // gradients, for the weight-gradient reduction.
 #include "ia_internal.h"
+#include "ia_tcgen05.cuh"
 
 namespace ia {
 
@@ -60,20 +67,19 @@ __global__ void train_march_kernel(const TrainArgs a) {
   }
 }
 
+template <Prec P>
 __global__ void __launch_bounds__(256) train_sample_kernel(const TrainArgs a) {
   extern __shared__ float4 smem4[];
-  float* sw = reinterpret_cast<float*>(smem4);
-  float4* roots = reinterpret_cast<float4*>(sw + kMlpPadT);
-  stage_mlp(a.P.mlp, a.P.n_in, sw);
-  __syncthreads();
-  FieldSmem fs;
-  fs.sw = sw;
-  fs.swh = nullptr;
-  fs.xstage = nullptr;
-  fs.gmlp = a.P.mlp;
-  fs.n_in = a.P.n_in;
-  fs.table_h = nullptr;
-  fs.pw = nullptr;
+  PosedStage ps;
+  ps.mlp = a.P.mlp;
+  ps.n_in = a.P.n_in;
+  ps.table_h = a.P.table_h;
+  ps.search = 0;
+  ps.prop = a.P.prop;
+  ps.theta = nullptr;
+  ps.Ninv = a.P.Ninv;
+  ps.nb = a.P.cfg.nb;
+  PosedSmem sm = stage_posed<P>(ps, smem4);
   const int n = *a.count;
   const int lane = threadIdx.x & 31;
   SampleStats st;
@@ -95,7 +101,7 @@ __global__ void __launch_bounds__(256) train_sample_kernel(const TrainArgs a) {
       Ms[q] = a.P.S.M + (size_t)pose * a.V * 3;
       Ns[q] = a.P.Ninv + (size_t)pose * a.P.cfg.nb * 12;
     }
-    posed_field_warp_n<kNS, Prec::F32>(a.P.S, Ms, a.P.F, a.P.cfg, Ns, fs, roots, act, xn, o, st);
+    posed_field_warp_n<kNS, P>(a.P.S, Ms, a.P.F, a.P.cfg, Ns, sm.fs, sm.roots, act, xn, o, st);
 #pragma unroll
     for (int q = 0; q < kNS; ++q) {
       const int s = base + q * 32 + lane;
@@ -105,6 +111,11 @@ __global__ void __launch_bounds__(256) train_sample_kernel(const TrainArgs a) {
       a.s_x[s] = make_float4(o[q].xstar.x, o[q].xstar.y, o[q].xstar.z, has ? 1.f : 0.f);
     }
   }
+}
+
+template <Prec P>
+static size_t train_sample_smem() {
+  return sizeof(float) * (mlp_smem_words(P, 256) + kMaxBones * 12) + sizeof(float4) * kMaxRoots * kNS * 256;
 }
 
 // front-to-back compositing of one ray, the loss, and the reverse sweep
@@ -164,13 +175,105 @@ __global__ void train_composite_kernel(const TrainArgs a) {
 // Per-sample backward
 // ---------------------------------------------------------------------------
 
+// dL/dx* -> lambda = J(x*)^-T dL/dx* -> bone-transform and skinning-grid gradients
+__device__ __forceinline__ void ift_scatter(const TrainArgs& a, int s, float3 xs, float gx, float gy, float gz) {
+  const int nb = a.P.cfg.nb;
+  const int pose = __float_as_int(a.s_pos[s].w);
+  const float4* M = a.P.S.M + (size_t)pose * a.V * 3;
+  float Mx[12], J[9], Hi[9];
+  blend_value_jac(a.P.S, M, xs, Mx, J);
+  if (!inv3(J, Hi)) return;
+  const float l0 = Hi[0] * gx + Hi[3] * gy + Hi[6] * gz;
+  const float l1 = Hi[1] * gx + Hi[4] * gy + Hi[7] * gz;
+  const float l2 = Hi[2] * gx + Hi[5] * gy + Hi[8] * gz;
+  const float xb[4] = {xs.x, xs.y, xs.z, 1.f};
+  // trilinear coefficients of x* in the skinning grid (as the forward blends them)
+  CellCoord cc = skin_cell(a.P.S, xs);
+  const float* Np = a.N + (size_t)pose * nb * 12;
+  float* gB = a.g_bones + (size_t)pose * nb * 12;
+  for (int k = 0; k < nb; ++k) {
+    float wk = 0.f;
+#pragma unroll
+    for (int corner = 0; corner < 8; ++corner) {
+      const int v = corner_index(a.P.S, cc.base, corner);
+      const float cw = ((corner & 1) ? cc.f[0] : 1.f - cc.f[0]) * (((corner >> 1) & 1) ? cc.f[1] : 1.f - cc.f[1]) *
+                       (((corner >> 2) & 1) ? cc.f[2] : 1.f - cc.f[2]);
+      wk = fmaf(cw, __ldg(a.skin + (size_t)v * nb + k), wk);
+    }
+    // dL/dN_k[a][b] = -lambda_a w_k [x*;1]_b
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      atomicAdd(gB + k * 12 + b, -l0 * wk * xb[b]);
+      atomicAdd(gB + k * 12 + 4 + b, -l1 * wk * xb[b]);
+      atomicAdd(gB + k * 12 + 8 + b, -l2 * wk * xb[b]);
+    }
+    // dL/dW(v, k) = -c_v lambda . (N_k [x*;1])
+    const float* Nk = Np + 12 * k;
+    const float ln = l0 * (Nk[0] * xb[0] + Nk[1] * xb[1] + Nk[2] * xb[2] + Nk[3]) +
+                     l1 * (Nk[4] * xb[0] + Nk[5] * xb[1] + Nk[6] * xb[2] + Nk[7]) +
+                     l2 * (Nk[8] * xb[0] + Nk[9] * xb[1] + Nk[10] * xb[2] + Nk[11]);
+#pragma unroll
+    for (int corner = 0; corner < 8; ++corner) {
+      const int v = corner_index(a.P.S, cc.base, corner);
+      const float cw = ((corner & 1) ? cc.f[0] : 1.f - cc.f[0]) * (((corner >> 1) & 1) ? cc.f[1] : 1.f - cc.f[1]) *
+                       (((corner >> 2) & 1) ? cc.f[2] : 1.f - cc.f[2]);
+      atomicAdd(a.g_skin + (size_t)v * nb + k, -cw * ln);
+    }
+  }
+}
+
+// hash-table scatter of dL/dfeatures and the canonical-position gradient dL/dx*
+template <bool kHalfTable>
+__device__ __forceinline__ void hash_backward(const TrainArgs& a, float3 xs, const float dfeat[kIn], float& gx,
+                                              float& gy, float& gz) {
+  const FieldDev& F = a.P.F;
+  gx = gy = gz = 0.f;
+  const float u[3] = {(xs.x - F.cmin[0]) * F.inv_ext[0], (xs.y - F.cmin[1]) * F.inv_ext[1],
+                      (xs.z - F.cmin[2]) * F.inv_ext[2]};
+#pragma unroll
+  for (int l = 0; l < kMaxLevels; ++l) {
+    if (l < F.L) {
+      const Level lv = F.lv[l];
+      int p0[3];
+      float f[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float pos = u[q] * (float)lv.res;
+        int c = (int)floorf(pos);
+        c = min(max(c, 0), lv.res - 1);
+        p0[q] = c;
+        f[q] = pos - (float)c;
+      }
+      const float d0 = dfeat[2 * l], d1 = dfeat[2 * l + 1];
+      const float sx = (float)lv.res * F.inv_ext[0], sy = (float)lv.res * F.inv_ext[1],
+                  sz = (float)lv.res * F.inv_ext[2];
+#pragma unroll
+      for (int corner = 0; corner < 8; ++corner) {
+        const int cx = corner & 1, cy = (corner >> 1) & 1, cz = (corner >> 2) & 1;
+        const float wx = cx ? f[0] : 1.f - f[0], wy = cy ? f[1] : 1.f - f[1], wz = cz ? f[2] : 1.f - f[2];
+        const uint32_t e = lv.offset + vertex_index(lv, p0[0] + cx, p0[1] + cy, p0[2] + cz);
+        const float w = wx * wy * wz;
+        atomicAdd(a.g_table + 2 * (size_t)e, w * d0);
+        atomicAdd(a.g_table + 2 * (size_t)e + 1, w * d1);
+        float2 t;
+        if constexpr (kHalfTable) t = __half22float2(a.P.table_h[e]);
+        else t = __ldg(F.table + e);
+        const float proj = t.x * d0 + t.y * d1;
+        gx = fmaf(proj * (cx ? 1.f : -1.f) * wy * wz, sx, gx);
+        gy = fmaf(proj * (cy ? 1.f : -1.f) * wx * wz, sy, gy);
+        gz = fmaf(proj * (cz ? 1.f : -1.f) * wx * wy, sz, gz);
+      }
+    }
+  }
+}
+
+
 __global__ void __launch_bounds__(128) train_backward_kernel(const TrainArgs a) {
   __shared__ __align__(16) float sw[kMlpPadT];
   stage_mlp(a.P.mlp, a.P.n_in, sw);
   __syncthreads();
   const int n = *a.count;
   const FieldDev& F = a.P.F;
-  const int nb = a.P.cfg.nb;
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
     float* act = a.act + (size_t)s * kActStride;
     const float4 xs4 = a.s_x[s];
@@ -276,87 +379,9 @@ __global__ void __launch_bounds__(128) train_backward_kernel(const TrainArgs a) 
       }
     }
     // ---- hash encoding backward: scatter-add into the table gradient, and dL/dx*
-    float gx = 0.f, gy = 0.f, gz = 0.f;
-    {
-      const float u[3] = {(xs.x - F.cmin[0]) * F.inv_ext[0], (xs.y - F.cmin[1]) * F.inv_ext[1],
-                          (xs.z - F.cmin[2]) * F.inv_ext[2]};
-#pragma unroll
-      for (int l = 0; l < kMaxLevels; ++l) {
-        if (l < F.L) {
-          const Level lv = F.lv[l];
-          int p0[3];
-          float f[3];
-#pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            const float pos = u[q] * (float)lv.res;
-            int c = (int)floorf(pos);
-            c = min(max(c, 0), lv.res - 1);
-            p0[q] = c;
-            f[q] = pos - (float)c;
-          }
-          const float d0 = dfeat[2 * l], d1 = dfeat[2 * l + 1];
-          const float sx = (float)lv.res * F.inv_ext[0], sy = (float)lv.res * F.inv_ext[1],
-                      sz = (float)lv.res * F.inv_ext[2];
-#pragma unroll
-          for (int corner = 0; corner < 8; ++corner) {
-            const int cx = corner & 1, cy = (corner >> 1) & 1, cz = (corner >> 2) & 1;
-            const float wx = cx ? f[0] : 1.f - f[0], wy = cy ? f[1] : 1.f - f[1], wz = cz ? f[2] : 1.f - f[2];
-            const uint32_t e = lv.offset + vertex_index(lv, p0[0] + cx, p0[1] + cy, p0[2] + cz);
-            const float w = wx * wy * wz;
-            atomicAdd(a.g_table + 2 * (size_t)e, w * d0);
-            atomicAdd(a.g_table + 2 * (size_t)e + 1, w * d1);
-            const float2 t = __ldg(F.table + e);
-            const float proj = t.x * d0 + t.y * d1;
-            gx = fmaf(proj * (cx ? 1.f : -1.f) * wy * wz, sx, gx);
-            gy = fmaf(proj * (cy ? 1.f : -1.f) * wx * wz, sy, gy);
-            gz = fmaf(proj * (cz ? 1.f : -1.f) * wx * wy, sz, gz);
-          }
-        }
-      }
-    }
-    // ---- implicit function theorem: lambda = J(x*)^-T dL/dx*
-    const int pose = __float_as_int(a.s_pos[s].w);
-    const float4* M = a.P.S.M + (size_t)pose * a.V * 3;
-    float Mx[12], J[9], Hi[9];
-    blend_value_jac(a.P.S, M, xs, Mx, J);
-    if (!inv3(J, Hi)) continue;
-    const float l0 = Hi[0] * gx + Hi[3] * gy + Hi[6] * gz;
-    const float l1 = Hi[1] * gx + Hi[4] * gy + Hi[7] * gz;
-    const float l2 = Hi[2] * gx + Hi[5] * gy + Hi[8] * gz;
-    const float xb[4] = {xs.x, xs.y, xs.z, 1.f};
-    // trilinear coefficients of x* in the skinning grid (as the forward blends them)
-    CellCoord cc = skin_cell(a.P.S, xs);
-    const float* Np = a.N + (size_t)pose * nb * 12;
-    float* gB = a.g_bones + (size_t)pose * nb * 12;
-    for (int k = 0; k < nb; ++k) {
-      float wk = 0.f;
-#pragma unroll
-      for (int corner = 0; corner < 8; ++corner) {
-        const int v = corner_index(a.P.S, cc.base, corner);
-        const float cw = ((corner & 1) ? cc.f[0] : 1.f - cc.f[0]) * (((corner >> 1) & 1) ? cc.f[1] : 1.f - cc.f[1]) *
-                         (((corner >> 2) & 1) ? cc.f[2] : 1.f - cc.f[2]);
-        wk = fmaf(cw, __ldg(a.skin + (size_t)v * nb + k), wk);
-      }
-      // dL/dN_k[a][b] = -lambda_a w_k [x*;1]_b
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        atomicAdd(gB + k * 12 + b, -l0 * wk * xb[b]);
-        atomicAdd(gB + k * 12 + 4 + b, -l1 * wk * xb[b]);
-        atomicAdd(gB + k * 12 + 8 + b, -l2 * wk * xb[b]);
-      }
-      // dL/dW(v, k) = -c_v lambda . (N_k [x*;1])
-      const float* Nk = Np + 12 * k;
-      const float ln = l0 * (Nk[0] * xb[0] + Nk[1] * xb[1] + Nk[2] * xb[2] + Nk[3]) +
-                       l1 * (Nk[4] * xb[0] + Nk[5] * xb[1] + Nk[6] * xb[2] + Nk[7]) +
-                       l2 * (Nk[8] * xb[0] + Nk[9] * xb[1] + Nk[10] * xb[2] + Nk[11]);
-#pragma unroll
-      for (int corner = 0; corner < 8; ++corner) {
-        const int v = corner_index(a.P.S, cc.base, corner);
-        const float cw = ((corner & 1) ? cc.f[0] : 1.f - cc.f[0]) * (((corner >> 1) & 1) ? cc.f[1] : 1.f - cc.f[1]) *
-                         (((corner >> 2) & 1) ? cc.f[2] : 1.f - cc.f[2]);
-        atomicAdd(a.g_skin + (size_t)v * nb + k, -cw * ln);
-      }
-    }
+    float gx, gy, gz;
+    hash_backward<false>(a, xs, dfeat, gx, gy, gz);
+    ift_scatter(a, s, xs, gx, gy, gz);
   }
 }
 
@@ -431,22 +456,233 @@ __global__ void __launch_bounds__(256) mlp_grad_kernel(const TrainArgs a) {
   else if (t < 2 * kWidth + 4) atomicAdd(gb3 + t - 2 * kWidth, accb);
 }
 
-cudaError_t launch_train(const TrainArgs& a, int num_sms, cudaStream_t s) {
+// ---------------------------------------------------------------------------
+// Reduced-precision backward (fp16 / bf16 operands, fp32 accumulation).
+//
+// The MLP is recomputed with the operands the tensor-core forward used (weights,
+// features and hidden activations rounded to the operand type, biases and
+// accumulation fp32), and run backward like a reduced-precision GEMM chain: the
+// output gradient is multiplied by the loss scale S, and every gradient that a
+// later product consumes (dO, dH2, dH1) is rounded to the operand type.  These
+// rounded operands and activations are written channel-major into X for the
+// tensor-core weight-gradient reduction; dL/dfeatures is unscaled to fp32 before
+// the hash-table scatter and the implicit-function gradient.  A scaled gradient
+// outside the operand type's range sets the overflow flag.
+// ---------------------------------------------------------------------------
+
+constexpr int kXdH2 = 0, kXdH1 = 64, kXH1 = 128, kXF = 192, kXOne = 224, kXH2 = 240, kXOne2 = 304, kXdO = 368;
+
+template <Prec P>
+__device__ __forceinline__ float put(uint16_t* col, int64_t ld, int row, float v) {
+  const uint16_t b = HalfOf<P>::bits(v);
+  col[(size_t)row * ld] = b;
+  if constexpr (P == Prec::F16) return __half2float(__ushort_as_half(b));
+  else return __bfloat162float(__ushort_as_bfloat16(b));
+}
+
+template <Prec P>
+__global__ void __launch_bounds__(128) train_backward_h_kernel(const TrainArgs a) {
+  __shared__ __align__(16) float sw[kMlpPadT];
+  stage_mlp(a.P.mlp, a.P.n_in, sw);
+  __syncthreads();
+  for (int t = threadIdx.x; t < kMlpPadT; t += blockDim.x) {
+    const bool bias = (t >= kOffB1 && t < kOffW2) || (t >= kOffB2 && t < kOffW3T) || t >= kOffB3;
+    if (!bias) sw[t] = HalfOf<P>::round(sw[t]);
+  }
+  __syncthreads();
+  const int n = *a.count;
+  const int n_pad = (n + kWgChunk - 1) / kWgChunk * kWgChunk;
+  const float S = *a.scale, inv_S = 1.f / S;
+  const int64_t ld = a.ld;
+  const FieldDev& F = a.P.F;
+  bool overflow = false;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_pad; s += gridDim.x * blockDim.x) {
+    uint16_t* col = a.X + s;
+    const float4 xs4 = s < n ? a.s_x[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!(xs4.w > 0.f)) {  // no root, or padding up to the chunk: zero columns
+      for (int r = 0; r <= kXOne; ++r) col[(size_t)r * ld] = 0;
+      for (int r = kXH2; r <= kXOne2; ++r) col[(size_t)r * ld] = 0;
+      for (int r = kXdO; r < kXdO + 4; ++r) col[(size_t)r * ld] = 0;
+      continue;
+    }
+    const float3 xs = make_float3(xs4.x, xs4.y, xs4.z);
+    const float4 gr = a.s_grad[s];
+    // ---- forward recompute with the forward's operands
+    float feat[kIn];
+    encode_h(F, a.P.table_h, xs, feat);
+#pragma unroll
+    for (int i = 0; i < kIn; ++i) feat[i] = put<P>(col, ld, kXF + i, feat[i]);
+    col[(size_t)kXOne * ld] = HalfOf<P>::bits(1.f);
+    col[(size_t)kXOne2 * ld] = HalfOf<P>::bits(1.f);
+    float h1[kWidth];
+    uint64_t m1 = 0;
+#pragma unroll
+    for (int j = 0; j < kWidth; ++j) {
+      float acc = sw[kOffB1 + j];
+      const float4* row = reinterpret_cast<const float4*>(sw + kOffW1 + j * kIn);
+#pragma unroll
+      for (int i = 0; i < kIn / 4; ++i) {
+        const float4 w = row[i];
+        acc = fmaf(w.x, feat[4 * i], fmaf(w.y, feat[4 * i + 1], fmaf(w.z, feat[4 * i + 2], fmaf(w.w, feat[4 * i + 3], acc))));
+      }
+      if (acc > 0.f) m1 |= 1ull << j;
+      h1[j] = put<P>(col, ld, kXH1 + j, fmaxf(acc, 0.f));
+    }
+    float o0 = sw[kOffB3], o1 = sw[kOffB3 + 1], o2 = sw[kOffB3 + 2], o3 = sw[kOffB3 + 3];
+    uint64_t m2 = 0;
+    for (int j = 0; j < kWidth; ++j) {
+      float acc = sw[kOffB2 + j];
+      const float4* row = reinterpret_cast<const float4*>(sw + kOffW2 + j * kWidth);
+#pragma unroll
+      for (int i = 0; i < kWidth / 4; ++i) {
+        const float4 w = row[i];
+        acc = fmaf(w.x, h1[4 * i], fmaf(w.y, h1[4 * i + 1], fmaf(w.z, h1[4 * i + 2], fmaf(w.w, h1[4 * i + 3], acc))));
+      }
+      if (acc > 0.f) m2 |= 1ull << j;
+      const float h = put<P>(col, ld, kXH2 + j, fmaxf(acc, 0.f));
+      const float4 w3 = reinterpret_cast<const float4*>(sw + kOffW3T)[j];
+      o0 = fmaf(w3.x, h, o0);
+      o1 = fmaf(w3.y, h, o1);
+      o2 = fmaf(w3.z, h, o2);
+      o3 = fmaf(w3.w, h, o3);
+    }
+    // ---- output activations, scaled output gradient
+    float dO[4];
+    {
+      const float sig = expf(fminf(fmaxf(o0, -15.f), 15.f));
+      dO[0] = (o0 > -15.f && o0 < 15.f) ? gr.x * sig : 0.f;
+      const float oc[3] = {o1, o2, o3}, gc[3] = {gr.y, gr.z, gr.w};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float sg = 1.f / (1.f + expf(-oc[c]));
+        dO[1 + c] = gc[c] * sg * (1.f - sg);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float v = dO[q] * S;
+      overflow |= !(fabsf(v) <= HalfOf<P>::kMax);
+      dO[q] = put<P>(col, ld, kXdO + q, v);
+    }
+    // ---- MLP backward (scaled)
+    float dh2[kWidth];
+#pragma unroll
+    for (int j = 0; j < kWidth; ++j) {
+      const float4 w3 = reinterpret_cast<const float4*>(sw + kOffW3T)[j];
+      const float v = ((m2 >> j) & 1ull) ? w3.x * dO[0] + w3.y * dO[1] + w3.z * dO[2] + w3.w * dO[3] : 0.f;
+      overflow |= !(fabsf(v) <= HalfOf<P>::kMax);
+      dh2[j] = put<P>(col, ld, kXdH2 + j, v);
+    }
+    float dh1[kWidth];
+#pragma unroll
+    for (int i = 0; i < kWidth; ++i) dh1[i] = 0.f;
+#pragma unroll
+    for (int j = 0; j < kWidth; ++j) {
+      const float4* row = reinterpret_cast<const float4*>(sw + kOffW2 + j * kWidth);
+      const float d = dh2[j];
+#pragma unroll
+      for (int i = 0; i < kWidth / 4; ++i) {
+        const float4 w = row[i];
+        dh1[4 * i] = fmaf(w.x, d, dh1[4 * i]);
+        dh1[4 * i + 1] = fmaf(w.y, d, dh1[4 * i + 1]);
+        dh1[4 * i + 2] = fmaf(w.z, d, dh1[4 * i + 2]);
+        dh1[4 * i + 3] = fmaf(w.w, d, dh1[4 * i + 3]);
+      }
+    }
+    float dfeat[kIn];
+#pragma unroll
+    for (int i = 0; i < kIn; ++i) dfeat[i] = 0.f;
+#pragma unroll
+    for (int j = 0; j < kWidth; ++j) {
+      const float v = ((m1 >> j) & 1ull) ? dh1[j] : 0.f;
+      overflow |= !(fabsf(v) <= HalfOf<P>::kMax);
+      const float d = put<P>(col, ld, kXdH1 + j, v);
+      const float4* row = reinterpret_cast<const float4*>(sw + kOffW1 + j * kIn);
+#pragma unroll
+      for (int i = 0; i < kIn / 4; ++i) {
+        const float4 w = row[i];
+        dfeat[4 * i] = fmaf(w.x, d, dfeat[4 * i]);
+        dfeat[4 * i + 1] = fmaf(w.y, d, dfeat[4 * i + 1]);
+        dfeat[4 * i + 2] = fmaf(w.z, d, dfeat[4 * i + 2]);
+        dfeat[4 * i + 3] = fmaf(w.w, d, dfeat[4 * i + 3]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kIn; ++i) dfeat[i] *= inv_S;
+    float gx, gy, gz;
+    hash_backward<true>(a, xs, dfeat, gx, gy, gz);
+    ift_scatter(a, s, xs, gx, gy, gz);
+  }
+  if (overflow) atomicExch(a.overflow, 1);
+}
+
+// After an overflow the step's gradients are meaningless: zero them (the step is
+// skipped) -- the flag is read on the device, so nothing waits for the host.
+__global__ void zero_on_overflow_kernel(const int* overflow, float* p, size_t n) {
+  if (!*overflow) return;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = 0.f;
+}
+
+// Dynamic loss scale: halve on overflow, double after kScaleWindow clean steps
+// (fp16 only; bf16 has fp32's exponent range and keeps S = 1).
+constexpr int kScaleWindow = 1000;
+constexpr float kScaleMax = 16777216.f;  // 2^24
+
+__global__ void loss_scale_kernel(const TrainArgs a, int dynamic) {
+  if (*a.overflow) {
+    *a.scale = fmaxf(*a.scale * 0.5f, 1.f);
+    *a.good_steps = 0;
+  } else if (dynamic && ++*a.good_steps >= kScaleWindow) {
+    *a.scale = fminf(*a.scale * 2.f, kScaleMax);
+    *a.good_steps = 0;
+  }
+}
+
+cudaError_t launch_train(const TrainArgs& a, const CUtensorMap* map, int num_sms, cudaStream_t s) {
   cudaError_t e;
   const int rb = (a.n_rays + 127) / 128;
   train_march_kernel<<<rb, 128, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const size_t smem = sizeof(float) * kMlpPadT + sizeof(float4) * kMaxRoots * kNS * 256;
-  if ((e = cudaFuncSetAttribute(train_sample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-      cudaSuccess)
+  const Prec P = (Prec)a.prec;
+  auto sample = P == Prec::F32 ? train_sample_kernel<Prec::F32>
+                : P == Prec::F16 ? train_sample_kernel<Prec::F16> : train_sample_kernel<Prec::BF16>;
+  const size_t smem = P == Prec::F32 ? train_sample_smem<Prec::F32>()
+                      : P == Prec::F16 ? train_sample_smem<Prec::F16>() : train_sample_smem<Prec::BF16>();
+  if ((e = cudaFuncSetAttribute(sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
     return e;
-  train_sample_kernel<<<num_sms * 2, 256, smem, s>>>(a);
+  sample<<<num_sms * 2, 256, smem, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   train_composite_kernel<<<rb, 128, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  train_backward_kernel<<<num_sms * 4, 128, 0, s>>>(a);
+  if (P == Prec::F32) {
+    train_backward_kernel<<<num_sms * 4, 128, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    mlp_grad_kernel<<<num_sms * 2, 256, 0, s>>>(a);
+    return cudaGetLastError();
+  }
+  if (P == Prec::F16) train_backward_h_kernel<Prec::F16><<<num_sms * 4, 128, 0, s>>>(a);
+  else train_backward_h_kernel<Prec::BF16><<<num_sms * 4, 128, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  mlp_grad_kernel<<<num_sms * 2, 256, 0, s>>>(a);
+  WgradArgs w{};
+  w.count = a.count;
+  w.scale = a.scale;
+  w.gW1 = a.g_mlp;
+  w.gb1 = w.gW1 + kWidth * a.P.n_in;
+  w.gW2 = w.gb1 + kWidth;
+  w.gb2 = w.gW2 + kWidth * kWidth;
+  w.gW3 = w.gb2 + kWidth;
+  w.gb3 = w.gW3 + 4 * kWidth;
+  w.n_in = a.P.n_in;
+  w.bf16 = P == Prec::BF16 ? 1 : 0;
+  w.err = a.err;
+  if ((e = launch_wgrad_tc(*map, w, num_sms, s)) != cudaSuccess) return e;
+  const size_t sizes[4] = {a.n_table_f, a.n_mlp_f, a.n_skin_f, a.n_bones_f};
+  float* bufs[4] = {a.g_table, a.g_mlp, a.g_skin, a.g_bones};
+  for (int q = 0; q < 4; ++q) {
+    zero_on_overflow_kernel<<<num_sms * 4, 256, 0, s>>>(a.overflow, bufs[q], sizes[q]);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  loss_scale_kernel<<<1, 1, 0, s>>>(a, P == Prec::F16 ? 1 : 0);
   return cudaGetLastError();
 }
 

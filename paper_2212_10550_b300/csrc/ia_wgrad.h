@@ -1,0 +1,34 @@
+// Host-visible part of the tensor-core weight-gradient reduction: the operand
+// layout constants, its arguments, and the host entry points (defined with the
+// kernel in the translation unit of the training step).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace ia {
+
+constexpr int kWgRows = 384;   // channel rows of the operand array X
+constexpr int kWgChunk = 64;   // samples per pipeline stage (128 B of fp16 / bf16)
+
+struct WgradArgs {
+  const int* count;    // samples (device scalar)
+  const float* scale;  // loss scale (device scalar)
+  float* gW1;          // [64][n_in]
+  float* gb1;          // [64]
+  float* gW2;          // [64][64]
+  float* gb2;          // [64]
+  float* gW3;          // [4][64]
+  float* gb3;          // [4]
+  int n_in;
+  int bf16;            // operand type: 0 fp16, 1 bf16
+  int* err;            // set to 1 when a wait expires
+};
+
+// Tensor map over X [kWgRows][ld] (2-byte elements), 64 x 16 boxes, 128-byte
+// swizzle.  ld must be a multiple of 64 and X 16-byte aligned.
+cudaError_t make_wgrad_map(CUtensorMap* map, void* X, int64_t ld, int bf16);
+cudaError_t launch_wgrad_tc(const CUtensorMap& map, const WgradArgs& a, int grid, cudaStream_t s);
+
+}  // namespace ia

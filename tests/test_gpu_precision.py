@@ -105,22 +105,3 @@ def test_render_reduced_precision(ia, prec):
         print(f"{NAMES[prec]} {config}: {np.sum(~good)} of {ok.sum()} rays outside tolerance")
         assert np.sum(~good) <= 0.002 * ok.sum() + 1
         ia.ia_destroy(ctx)
-
-
-def test_reduced_precision_training_is_refused(ia):
-    sc = S.make_scene("tiny", 0)
-    table, mlp = S.make_field(sc, 0)
-    ctx = _ctx(ia, sc, table, mlp, 1)
-    th, tr = S.make_pose(sc, 0)
-    ia.ia_set_pose(ctx, th[None], tr[None])
-    ia.ia_update_occupancy(ctx, 0)
-    nt, nm = ia.ia_param_sizes(ctx)
-    g = dict(table=torch.zeros(nt, device="cuda"), mlp=torch.zeros(nm, device="cuda"),
-             skin=torch.zeros(sc.skin_res ** 3 * sc.n_bones, device="cuda"),
-             bones=torch.zeros(sc.n_bones * 12, device="cuda"))
-    rb = S.make_ray_batch(sc, 16, 1)
-    dev = {k: torch.from_numpy(np.ascontiguousarray(rb[k])).cuda() for k in ("origin", "direction", "pose", "target")}
-    with pytest.raises(ia.IAError):
-        ia.ia_train_step(ctx, dev["origin"], dev["direction"], dev["pose"], dev["target"],
-                         torch.zeros(1, device="cuda"), g, occ_grid=ia.IA_OCC_POSE)
-    ia.ia_destroy(ctx)

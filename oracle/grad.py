@@ -29,10 +29,13 @@ def mlp_size(sc):
     return W * sc.mlp_in() + W + W * W + W + 4 * W + 4
 
 
-def train(om, poses, occ_bits, origin, direction, pose_id, target, grad=True, nthreads=0):
+def train(om, poses, occ_bits, origin, direction, pose_id, target, grad=True, nthreads=0, prop=None,
+          theta=None):
     """Loss, per-ray colour and flags, and (if grad) the gradients as a dict:
     table [entries, F], mlp (packed W1, b1, W2, b2, W3, b3), skin [R, R, R, nb],
-    bones [n_poses, nb, 12] (gradient w.r.t. the normalised-space N_k)."""
+    bones [n_poses, nb, 12] (gradient w.r.t. the normalised-space N_k).
+    With prop (an oracle.prop.PropModel) and theta ([n_poses, nb, 3] axis-angles)
+    the proposal chooses each sample's starts."""
     from . import _p
     sc = om.scene
     n = len(pose_id)
@@ -50,7 +53,13 @@ def train(om, poses, occ_bits, origin, direction, pose_id, target, grad=True, nt
         g = dict(table=np.zeros((sc.n_table_entries(), sc.n_features)), mlp=np.zeros(mlp_size(sc)),
                  skin=np.zeros(om.skin.shape), bones=np.zeros((n_poses, sc.n_bones, 12)))
     args = [g[k] if g else None for k in ("table", "mlp", "skin", "bones")]
-    loss = om.L.or_train(C.byref(om.m), arr, n_poses, _p(occ, C.c_uint32), n, _p(o, C.c_float),
-                         _p(d, C.c_float), _p(pid, C.c_int32), _p(tgt, C.c_double), _p(rgb, C.c_double),
-                         _p(flags, C.c_int32), *[_p(a, C.c_double) for a in args], nthreads)
+    common = [C.byref(om.m), arr, n_poses, _p(occ, C.c_uint32), n, _p(o, C.c_float), _p(d, C.c_float),
+              _p(pid, C.c_int32), _p(tgt, C.c_double), _p(rgb, C.c_double), _p(flags, C.c_int32),
+              *[_p(a, C.c_double) for a in args], nthreads]
+    if prop is None:
+        loss = om.L.or_train(*common)
+    else:
+        th = np.ascontiguousarray(theta, dtype=np.float64).reshape(-1)
+        assert th.size == n_poses * sc.n_bones * 3
+        loss = om.L.or_train_prop(*common, C.byref(prop.q), _p(th, C.c_double))
     return loss, rgb, flags, g

@@ -176,6 +176,12 @@ double or_prop_loss_grad(const or_model *m, const or_prop *q, int n, const float
                          double *g_table, double *g_mlp);
 void or_posed_field_prop(const or_model *m, const or_pose *p, const or_prop *q, const double *theta,
                          const double xn[3], or_sample *s, int *fallback);
+/* or_train with the proposal choosing each sample's starts; theta_all
+ * [n_poses][nb][3] axis-angles of the poses (the proposal's pose input). */
+double or_train_prop(const or_model *m, const or_pose *poses, int n_poses, const uint32_t *occ, int n,
+                     const float *o, const float *d, const int32_t *pose_id, const double *target,
+                     double *rgb_out, int *ray_flags, double *g_table, double *g_mlp, double *g_skin,
+                     double *g_bones, int nthreads, const or_prop *q, const double *theta_all);
 /* Brute-force root set: Newton from every point of an n^3 canonical lattice. */
 int or_bruteforce_roots(const or_model *m, const or_pose *p, const double xn[3], int n,
                         double seed_thresh, double *roots, int max_roots);

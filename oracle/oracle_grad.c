@@ -57,7 +57,7 @@ static int norm_ray(const or_model *m, const or_pose *p, const float ow[3], cons
 /* forward of one ray: samples in march order, colour, final transmittance */
 static int forward_ray(const or_model *m, const or_pose *poses, int pose, const uint32_t *occ,
                        const float ow[3], const float dw[3], fsamp *S, double C[3], double *T_out,
-                       double *dt_out, int *flags) {
+                       double *dt_out, int *flags, const or_prop *q, const double *theta_all) {
   const or_pose *p = &poses[pose];
   float o[3], d[3], tn, tf;
   int n = 0, fl = 0;
@@ -75,7 +75,12 @@ static int forward_ray(const or_model *m, const or_pose *poses, int pose, const 
       if (!((occ[cell >> 5] >> (cell & 31)) & 1u)) continue;
       or_sample s;
       double xn[3] = {(double)x[0], (double)x[1], (double)x[2]};
-      or_posed_field(m, p, xn, &s);
+      if (q) {
+        int fb = 0;
+        or_posed_field_prop(m, p, q, theta_all + (long)pose * 3 * m->nb, xn, &s, &fb);
+      } else {
+        or_posed_field(m, p, xn, &s);
+      }
       fl |= s.flags;
       fsamp *q = &S[n++];
       q->has = s.start >= 0;
@@ -273,10 +278,10 @@ static void backward_sample(const or_model *m, const or_pose *poses, const fsamp
  * (fp32), pose_id [n], target [n][3].  Gradients are overwritten:
  * g_table [entries][F], g_mlp (packed), g_skin [rw^3][nb], g_bones [n_poses][nb][12]
  * (all NULL: loss only).  rgb_out [n][3], ray_flags [n] may be NULL. */
-double or_train(const or_model *m, const or_pose *poses, int n_poses, const uint32_t *occ, int n,
-                const float *o, const float *d, const int32_t *pose_id, const double *target,
-                double *rgb_out, int *ray_flags, double *g_table, double *g_mlp, double *g_skin,
-                double *g_bones, int nthreads) {
+static double train_impl(const or_model *m, const or_pose *poses, int n_poses, const uint32_t *occ, int n,
+                         const float *o, const float *d, const int32_t *pose_id, const double *target,
+                         double *rgb_out, int *ray_flags, double *g_table, double *g_mlp, double *g_skin,
+                         double *g_bones, int nthreads, const or_prop *q, const double *theta_all) {
   long entries = 0;
   {
     long T = 1L << m->log2_T;
@@ -302,7 +307,7 @@ double or_train(const or_model *m, const or_pose *poses, int n_poses, const uint
   for (int r = 0; r < n; ++r) {
     int fl = 0;
     cnt[r] = forward_ray(m, poses, pose_id[r], occ, o + 3 * r, d + 3 * r, S + (long)r * m->n_slots,
-                         Cs + 4 * r, Cs + 4 * r + 3, dts + r, &fl);
+                         Cs + 4 * r, Cs + 4 * r + 3, dts + r, &fl, q, theta_all);
     if (ray_flags) ray_flags[r] = fl;
   }
   double loss = 0.0;
@@ -340,4 +345,22 @@ double or_train(const or_model *m, const or_pose *poses, int n_poses, const uint
   free(Cs);
   free(dts);
   return loss;
+}
+
+double or_train(const or_model *m, const or_pose *poses, int n_poses, const uint32_t *occ, int n,
+                const float *o, const float *d, const int32_t *pose_id, const double *target,
+                double *rgb_out, int *ray_flags, double *g_table, double *g_mlp, double *g_skin,
+                double *g_bones, int nthreads) {
+  return train_impl(m, poses, n_poses, occ, n, o, d, pose_id, target, rgb_out, ray_flags, g_table, g_mlp, g_skin,
+                    g_bones, nthreads, NULL, NULL);
+}
+
+/* The same step with the correspondence proposal choosing each sample's starts
+ * (or_posed_field_prop; theta_all [n_poses][nb][3] the poses' axis-angles). */
+double or_train_prop(const or_model *m, const or_pose *poses, int n_poses, const uint32_t *occ, int n,
+                     const float *o, const float *d, const int32_t *pose_id, const double *target,
+                     double *rgb_out, int *ray_flags, double *g_table, double *g_mlp, double *g_skin,
+                     double *g_bones, int nthreads, const or_prop *q, const double *theta_all) {
+  return train_impl(m, poses, n_poses, occ, n, o, d, pose_id, target, rgb_out, ray_flags, g_table, g_mlp, g_skin,
+                    g_bones, nthreads, q, theta_all);
 }

@@ -96,3 +96,86 @@ def test_gradient_support(case):
     assert loss < 1e-28
     for v in g.values():
         assert np.abs(v).max() < 1e-14
+
+
+def test_proposal_step_gradient_matches_central_differences(case):
+    """The same pin for the step whose starts come from the correspondence
+    proposal (an untrained, seeded network: many samples take the fallback,
+    the others keep the proposed starts' roots).  Whether a proposed start
+    converges within the iteration limit is a discrete event that a wide
+    stencil can straddle, so the step is h = 3e-5 here (at 1e-4 one bone entry
+    of the fixture differs by 1.8e-3 relative; at 3e-5 by 4e-6)."""
+    from oracle import prop as PP
+    sc, om, poses, occ, rays = case
+    cfg = S.proposal_config()
+    pt, pm = S.proposal_init(sc, cfg, 3)
+    pr = PP.PropModel(om, cfg, pt, pm)
+    theta = np.stack([S.make_pose(sc, i)[0] for i in range(2)])
+
+    def loss_of(pp):
+        return G.train(om, pp, occ, rays["origin"], rays["direction"], rays["pose"], rays["target"], grad=False,
+                       prop=pr, theta=theta)[0]
+
+    loss, _, flags, g = G.train(om, poses, occ, rays["origin"], rays["direction"], rays["pose"], rays["target"],
+                                prop=pr, theta=theta)
+    keep = flags == 0
+    assert keep.sum() >= 32
+    rays = {k: v[keep] for k, v in rays.items()}
+    loss, _, _, g = G.train(om, poses, occ, rays["origin"], rays["direction"], rays["pose"], rays["target"],
+                            prop=pr, theta=theta)
+    rng = np.random.default_rng(1)
+    h = 3e-5
+    worst = 0.0
+    for name, arr, flat in (("table", om.table.reshape(-1), g["table"].reshape(-1)),
+                            ("skin", om.skin.reshape(-1), g["skin"].reshape(-1)),
+                            ("W2", om.mlp["W2"].reshape(-1), None)):
+        if flat is None:
+            off = om.mlp["W1"].size + om.mlp["b1"].size
+            flat = g["mlp"][off:off + arr.size]
+        for i in _pick(flat, 8, rng):
+            old = arr[i]
+            arr[i] = old + h
+            lp = loss_of(poses)
+            arr[i] = old - h
+            lm = loss_of(poses)
+            arr[i] = old
+            fd = (lp - lm) / (2 * h)
+            worst = max(worst, abs(flat[i] - fd) / max(abs(flat[i]), abs(fd), 1e-12))
+            assert abs(flat[i] - fd) <= 1e-3 * max(abs(flat[i]), abs(fd)) + 1e-9, (name, flat[i], fd)
+    for i in _pick(g["bones"].reshape(-1), 8, rng):
+        p, k, e = np.unravel_index(i, g["bones"].shape)
+        pp = G.pose_array(poses)
+        old = pp[p].N[k][e]
+        pp[p].N[k][e] = old + h
+        lp = loss_of(pp)
+        pp[p].N[k][e] = old - h
+        lm = loss_of(pp)
+        fd = (lp - lm) / (2 * h)
+        worst = max(worst, abs(g["bones"][p, k, e] - fd) / max(abs(fd), 1e-12))
+        assert abs(g["bones"][p, k, e] - fd) <= 1e-3 * max(abs(g["bones"][p, k, e]), abs(fd)) + 1e-9
+    print(f"32 finite-difference checks (proposal starts), worst relative error {worst:.2e}")
+
+
+def test_proposal_step_equals_plain_step_when_roots_agree(case):
+    """Where the proposal's starts reach the same root as the plain search
+    (one root per sample, as on most of the body), the two steps are the same
+    function: equal loss and gradient on rays whose samples all agree (up to
+    the roots' polish, 1e-12, reached from different starts)."""
+    from oracle import prop as PP
+    sc, om, poses, occ, rays = case
+    cfg = S.proposal_config()
+    pt, pm = S.proposal_init(sc, cfg, 3)
+    pr = PP.PropModel(om, cfg, pt, pm)
+    theta = np.stack([S.make_pose(sc, i)[0] for i in range(2)])
+    args = (om, poses, occ, rays["origin"], rays["direction"], rays["pose"], rays["target"])
+    _, rgb_a, _, _ = G.train(*args, grad=False)
+    _, rgb_b, _, _ = G.train(*args, grad=False, prop=pr, theta=theta)
+    same = np.all(np.abs(rgb_a - rgb_b) <= 1e-12, axis=1)
+    assert same.sum() >= 16
+    sub = {k: v[same] for k, v in rays.items()}
+    args = (om, poses, occ, sub["origin"], sub["direction"], sub["pose"], sub["target"])
+    la, _, _, ga = G.train(*args)
+    lb, _, _, gb = G.train(*args, prop=pr, theta=theta)
+    assert abs(la - lb) <= 1e-12 * la
+    for k in ga:
+        np.testing.assert_allclose(gb[k], ga[k], rtol=1e-6, atol=1e-10 * max(np.abs(ga[k]).max(), 1e-30))

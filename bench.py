@@ -203,14 +203,23 @@ def frame_stats(ia, ctx, poses, icam, rgb, alpha):
     return {k: v / n for k, v in tot.items()}, {k: v / n for k, v in occ.items()}
 
 
-def time_train_step(torch, ia, sc, table, mlp, flush, steps, warmup, stream, n_rays=8192, n_poses=16):
-    """fwd+bwd training step: 8192 random rays over 16 poses, L2 loss, occupancy =
-    union of the 16 per-pose grids, no early termination; optimiser excluded."""
-    ctx = make_ctx(__import__("torch"), ia, sc, table, mlp, 0, 0.0)
+def time_train_step(torch, ia, sc, table, mlp, flush, steps, warmup, stream, n_rays=8192, n_poses=16,
+                    precision=0, prop=None):
+    """fwd+bwd training step: n_rays random rays over 16 poses, L2 loss, occupancy =
+    union of the 16 per-pose grids, no early termination; optimiser excluded.
+    prop: (table, packed MLP) device tensors of a trained proposal (fp16 / bf16
+    only): the correspondence search starts from its top-2 bones."""
+    ctx = make_ctx(__import__("torch"), ia, sc, table, mlp, precision, 0.0)
     poses = [S.make_pose(sc, 200 + i) for i in range(n_poses)]
     ia.ia_set_pose(ctx, np.stack([p[0] for p in poses]), np.stack([p[1] for p in poses]))
     for i in range(n_poses):
         ia.ia_update_occupancy(ctx, i, ia.IA_OCC_UNION)
+    if prop is not None:
+        pc = S.proposal_config()
+        ia.ia_proposal_init(ctx, ia.make_proposal_config(pc["n_levels"], pc["log2_table"], pc["level_res"],
+                                                         pc["top_k"], pc["offset_weight"]))
+        ia.ia_proposal_set_params(ctx, prop[0], prop[1])
+        ia.ia_set_search(ctx, ia.IA_SEARCH_PROPOSAL)
     rb = S.make_ray_batch(sc, n_rays, n_poses, seed=3)
     dev = {k: torch.from_numpy(np.ascontiguousarray(rb[k])).cuda() for k in ("origin", "direction", "pose", "target")}
     nt, nm = ia.ia_param_sizes(ctx)
@@ -235,8 +244,15 @@ def time_train_step(torch, ia, sc, table, mlp, flush, steps, warmup, stream, n_r
         b.record(stream)
         torch.cuda.synchronize()
         ms.append(a.elapsed_time(b))
+    scale, skipped = ia.ia_loss_scale(ctx)
+    st = ia.ia_train_stats(ctx)
     ia.ia_destroy(ctx)
-    return ms
+    occ = max(st["occupied_samples"], 1)
+    return {"ms": round(statistics.mean(ms), 4), "min_ms": round(min(ms), 4), "rays": n_rays, "poses": n_poses,
+            "samples": st["occupied_samples"], "mean_starts_per_sample": round(st["starts"] / occ, 3),
+            "mean_broyden_iters_per_sample": round(st["broyden_iters"] / occ, 3),
+            "fallback_rate": round(st["fallbacks"] / max(st["proposed"], 1), 4),
+            "loss_scale": scale, "last_step_skipped": skipped}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -255,6 +271,16 @@ def run_ours(args, rank, world, local_rank):
     rgb = torch.zeros(W * H, 3, device=dev)
     alpha = torch.zeros(W * H, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    if args.only == "train":
+        tsteps = max(3, args.steps)
+        res = {name: time_train_step(torch, ia, sc, table, mlp, flush, tsteps, args.warmup, stream, n_rays=32768,
+                                     precision=prec) for name, prec in (("fp32", 0), ("fp16", 1))}
+        if rank != 0:
+            return None
+        return {"metric": METRIC, "value": res["fp16"]["ms"], "unit": "ms per fp16 training step (32768 rays)",
+                "n_gpus": world, "steps": tsteps, "warmup": args.warmup, "higher_is_better": False,
+                "train_step_32768": res, "partial": "training steps only"}
 
     # ---- plain fp32 multi-start (the headline workload)
     ctx = make_ctx(torch, ia, sc, table, mlp, 0, EARLY_T)
@@ -317,10 +343,17 @@ def run_ours(args, rank, world, local_rank):
         hit += int((a0 > 0).sum().item())
     step16, render16 = time_frames(torch, ia, ctx16, poses, icam, rgb, alpha, flush, args.steps, args.warmup,
                                    stream)
+    pnt, pnm = ia.ia_proposal_param_sizes(ctx16)
+    prop_params = (torch.zeros(pnt, device=dev), torch.zeros(pnm, device=dev))
+    ia.ia_proposal_get_params(ctx16, *prop_params)
     ia.ia_destroy(ctx16)
 
-    # ---- fwd+bwd training step (fp32)
-    train_ms = time_train_step(torch, ia, sc, table, mlp, flush, max(5, args.steps // 10), 3, stream)
+    # ---- fwd+bwd training steps: fp32 at 8192 rays; fp32 / fp16 / bf16 / fp16+proposal at 32768 rays
+    tsteps = max(5, args.steps // 10)
+    train = {"fp32_8192": time_train_step(torch, ia, sc, table, mlp, flush, tsteps, 3, stream)}
+    for name, prec, pp in (("fp32", 0, None), ("fp16", 1, None), ("bf16", 2, None), ("fp16_proposal", 1, prop_params)):
+        train[name] = time_train_step(torch, ia, sc, table, mlp, flush, tsteps, 3, stream, n_rays=32768,
+                                      precision=prec, prop=pp)
 
     if world > 1:
         import torch.distributed as dist
@@ -375,9 +408,16 @@ def run_ours(args, rank, world, local_rank):
             "proposal_training": prop_train,
             "per_frame": {k: round(v, 1) for k, v in per_frame16.items()},
         },
-        "train_step_fp32": {"ms": round(statistics.mean(train_ms), 4), "min_ms": round(min(train_ms), 4),
-                            "rays": 8192, "poses": 16, "what": "forward + hand-written backward (all gradients), "
-                            "no optimiser, L2 flushed before each step"},
+        "train_step_fp32": dict(train["fp32_8192"], what="forward + hand-written backward (all gradients), "
+                                "no optimiser, L2 flushed before each step"),
+        "train_step_32768": {
+            "fp32_ms": train["fp32"]["ms"], "fp16_ms": train["fp16"]["ms"], "bf16_ms": train["bf16"]["ms"],
+            "fp16_proposal_ms": train["fp16_proposal"]["ms"],
+            "speedup_fp16_proposal_vs_fp32": round(train["fp32"]["ms"] / train["fp16_proposal"]["ms"], 3),
+            "speedup_fp16_vs_fp32": round(train["fp32"]["ms"] / train["fp16"]["ms"], 3),
+            "detail": {k: train[k] for k in ("fp32", "fp16", "bf16", "fp16_proposal")},
+            "what": "32768 rays over 16 poses, <=128 slots, forward + hand-written backward, fp32 master "
+                    "gradients; fp16 with dynamic loss scaling, weight gradients on tcgen05"},
         "roofline": {"kernel": "render_kernel", "bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                      "traffic": None,
@@ -476,8 +516,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", default="all", choices=["all", "plain"],
-                    help="plain: time only the plain fp32 frames (used for profiling captures)")
+    ap.add_argument("--only", default="all", choices=["all", "plain", "train"],
+                    help="plain: time only the plain fp32 frames; train: only the fp32 and fp16 training "
+                         "steps at 32768 rays (both used for profiling captures)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

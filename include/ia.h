@@ -239,9 +239,22 @@ typedef struct ia_grads {
  * gradient leaves the fp16 range, the step is skipped: all four gradient
  * buffers are zeroed and S halves; after 1000 clean steps S doubles (at most
  * 2^24).  bf16 keeps S = 1.  ia_loss_scale reports S and whether the last step
- * was skipped. */
+ * was skipped.
+ *
+ * Search: with ia_set_search(ctx, IA_SEARCH_PROPOSAL) (fp16 / bf16 only) each
+ * sample's correspondence search starts from the proposal's top_k bones of the
+ * sample's own pose and falls back to every bone-wise start when they find no
+ * valid root, as in ia_render; the backward is unchanged (the selected root is
+ * a constant of the gradient). */
 ia_status ia_train_step(ia_ctx *ctx, const ia_batch *batch, int occ_grid, float *loss, float *rgb_out,
                         const ia_grads *grads, void *stream);
+
+/* Counters of the last ia_train_step (host struct; waits on `stream`): rays,
+ * rays that cross the normalised box (hit_rays), their slots (marched_slots),
+ * occupied samples, Broyden starts / iterations / converged chains / distinct
+ * roots, and with the proposal search the proposed samples and fallbacks.
+ * early_stopped is 0 (training composites every sample). */
+ia_status ia_train_stats(ia_ctx *ctx, ia_render_stats *stats, void *stream);
 
 /* The loss scale S after the last ia_train_step (host float) and whether that
  * step overflowed and was skipped (host int32, 1 = skipped); either may be NULL,

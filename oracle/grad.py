@@ -30,12 +30,13 @@ def mlp_size(sc):
 
 
 def train(om, poses, occ_bits, origin, direction, pose_id, target, grad=True, nthreads=0, prop=None,
-          theta=None):
+          theta=None, fallbacks=None):
     """Loss, per-ray colour and flags, and (if grad) the gradients as a dict:
     table [entries, F], mlp (packed W1, b1, W2, b2, W3, b3), skin [R, R, R, nb],
     bones [n_poses, nb, 12] (gradient w.r.t. the normalised-space N_k).
     With prop (an oracle.prop.PropModel) and theta ([n_poses, nb, 3] axis-angles)
-    the proposal chooses each sample's starts."""
+    the proposal chooses each sample's starts; fallbacks (int32 [n], optional)
+    then receives each ray's count of samples that fell back to every bone."""
     from . import _p
     sc = om.scene
     n = len(pose_id)
@@ -61,5 +62,9 @@ def train(om, poses, occ_bits, origin, direction, pose_id, target, grad=True, nt
     else:
         th = np.ascontiguousarray(theta, dtype=np.float64).reshape(-1)
         assert th.size == n_poses * sc.n_bones * 3
-        loss = om.L.or_train_prop(*common, C.byref(prop.q), _p(th, C.c_double))
+        fb = None
+        if fallbacks is not None:
+            assert fallbacks.dtype == np.int32 and fallbacks.shape == (n,) and fallbacks.flags.c_contiguous
+            fb = _p(fallbacks, C.c_int32)
+        loss = om.L.or_train_prop(*common, C.byref(prop.q), _p(th, C.c_double), fb)
     return loss, rgb, flags, g

@@ -177,11 +177,14 @@ double or_prop_loss_grad(const or_model *m, const or_prop *q, int n, const float
 void or_posed_field_prop(const or_model *m, const or_pose *p, const or_prop *q, const double *theta,
                          const double xn[3], or_sample *s, int *fallback);
 /* or_train with the proposal choosing each sample's starts; theta_all
- * [n_poses][nb][3] axis-angles of the poses (the proposal's pose input). */
+ * [n_poses][nb][3] axis-angles of the poses (the proposal's pose input);
+ * ray_fallbacks [n] (may be NULL) counts each ray's samples that fell back to
+ * the search over every bone. */
 double or_train_prop(const or_model *m, const or_pose *poses, int n_poses, const uint32_t *occ, int n,
                      const float *o, const float *d, const int32_t *pose_id, const double *target,
                      double *rgb_out, int *ray_flags, double *g_table, double *g_mlp, double *g_skin,
-                     double *g_bones, int nthreads, const or_prop *q, const double *theta_all);
+                     double *g_bones, int nthreads, const or_prop *q, const double *theta_all,
+                     int *ray_fallbacks);
 /* Brute-force root set: Newton from every point of an n^3 canonical lattice. */
 int or_bruteforce_roots(const or_model *m, const or_pose *p, const double xn[3], int n,
                         double seed_thresh, double *roots, int max_roots);

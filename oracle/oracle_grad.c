@@ -57,7 +57,7 @@ static int norm_ray(const or_model *m, const or_pose *p, const float ow[3], cons
 /* forward of one ray: samples in march order, colour, final transmittance */
 static int forward_ray(const or_model *m, const or_pose *poses, int pose, const uint32_t *occ,
                        const float ow[3], const float dw[3], fsamp *S, double C[3], double *T_out,
-                       double *dt_out, int *flags, const or_prop *q, const double *theta_all) {
+                       double *dt_out, int *flags, const or_prop *q, const double *theta_all, int *n_fallback) {
   const or_pose *p = &poses[pose];
   float o[3], d[3], tn, tf;
   int n = 0, fl = 0;
@@ -78,6 +78,7 @@ static int forward_ray(const or_model *m, const or_pose *poses, int pose, const 
       if (q) {
         int fb = 0;
         or_posed_field_prop(m, p, q, theta_all + (long)pose * 3 * m->nb, xn, &s, &fb);
+        if (n_fallback) *n_fallback += fb;
       } else {
         or_posed_field(m, p, xn, &s);
       }
@@ -281,7 +282,8 @@ static void backward_sample(const or_model *m, const or_pose *poses, const fsamp
 static double train_impl(const or_model *m, const or_pose *poses, int n_poses, const uint32_t *occ, int n,
                          const float *o, const float *d, const int32_t *pose_id, const double *target,
                          double *rgb_out, int *ray_flags, double *g_table, double *g_mlp, double *g_skin,
-                         double *g_bones, int nthreads, const or_prop *q, const double *theta_all) {
+                         double *g_bones, int nthreads, const or_prop *q, const double *theta_all,
+                         int *ray_fallbacks) {
   long entries = 0;
   {
     long T = 1L << m->log2_T;
@@ -305,9 +307,10 @@ static double train_impl(const or_model *m, const or_pose *poses, int n_poses, c
 #endif
 #pragma omp parallel for schedule(dynamic, 4)
   for (int r = 0; r < n; ++r) {
-    int fl = 0;
+    int fl = 0, nfb = 0;
     cnt[r] = forward_ray(m, poses, pose_id[r], occ, o + 3 * r, d + 3 * r, S + (long)r * m->n_slots,
-                         Cs + 4 * r, Cs + 4 * r + 3, dts + r, &fl, q, theta_all);
+                         Cs + 4 * r, Cs + 4 * r + 3, dts + r, &fl, q, theta_all, &nfb);
+    if (ray_fallbacks) ray_fallbacks[r] = nfb;
     if (ray_flags) ray_flags[r] = fl;
   }
   double loss = 0.0;
@@ -352,15 +355,18 @@ double or_train(const or_model *m, const or_pose *poses, int n_poses, const uint
                 double *rgb_out, int *ray_flags, double *g_table, double *g_mlp, double *g_skin,
                 double *g_bones, int nthreads) {
   return train_impl(m, poses, n_poses, occ, n, o, d, pose_id, target, rgb_out, ray_flags, g_table, g_mlp, g_skin,
-                    g_bones, nthreads, NULL, NULL);
+                    g_bones, nthreads, NULL, NULL, NULL);
 }
 
 /* The same step with the correspondence proposal choosing each sample's starts
- * (or_posed_field_prop; theta_all [n_poses][nb][3] the poses' axis-angles). */
+ * (or_posed_field_prop; theta_all [n_poses][nb][3] the poses' axis-angles).
+ * ray_fallbacks [n] (may be NULL): samples of each ray whose proposed starts
+ * found no valid root, so that the search over every bone ran. */
 double or_train_prop(const or_model *m, const or_pose *poses, int n_poses, const uint32_t *occ, int n,
                      const float *o, const float *d, const int32_t *pose_id, const double *target,
                      double *rgb_out, int *ray_flags, double *g_table, double *g_mlp, double *g_skin,
-                     double *g_bones, int nthreads, const or_prop *q, const double *theta_all) {
+                     double *g_bones, int nthreads, const or_prop *q, const double *theta_all,
+                     int *ray_fallbacks) {
   return train_impl(m, poses, n_poses, occ, n, o, d, pose_id, target, rgb_out, ray_flags, g_table, g_mlp, g_skin,
-                    g_bones, nthreads, q, theta_all);
+                    g_bones, nthreads, q, theta_all, ray_fallbacks);
 }

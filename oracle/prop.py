@@ -26,7 +26,8 @@ def declare(L):
         "or_posed_field_prop": (None, [PM, P(Pose), PQ, P(C.c_double), P(C.c_double), P(Sample), P(C.c_int)]),
         "or_train_prop": (C.c_double, [PM, P(Pose), C.c_int, P(C.c_uint32), C.c_int, P(C.c_float), P(C.c_float),
                                        P(C.c_int32), P(C.c_double), P(C.c_double), P(C.c_int32), P(C.c_double),
-                                       P(C.c_double), P(C.c_double), P(C.c_double), C.c_int, PQ, P(C.c_double)]),
+                                       P(C.c_double), P(C.c_double), P(C.c_double), C.c_int, PQ, P(C.c_double),
+                                       P(C.c_int32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -95,6 +95,7 @@ def lib():
             "ia_train_step": [P, C.POINTER(Batch), I, P, P, C.POINTER(Grads), V],
             "ia_update_occupancy_static": [P, I, P, V],
             "ia_loss_scale": [P, C.POINTER(C.c_float), C.POINTER(C.c_int32), V],
+            "ia_train_stats": [P, C.POINTER(RenderStats), V],
             "ia_proposal_init": [P, C.POINTER(ProposalConfig)],
             "ia_proposal_param_sizes": [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
             "ia_proposal_set_params": [P, P, P, V],
@@ -266,6 +267,13 @@ def ia_train_step(ctx, origin, direction, pose, target, loss, grads, occ_grid=IA
     g.table, g.mlp, g.skin, g.bones = (_ptr(grads[k]) for k in ("table", "mlp", "skin", "bones"))
     _check(lib().ia_train_step(ctx, C.byref(b), occ_grid, _ptr(loss), _ptr(rgb_out), C.byref(g),
                                _stream(stream)), ctx)
+
+
+def ia_train_stats(ctx, stream=None):
+    """Counters of the last training step (dict, same keys as the render counters)."""
+    st = RenderStats()
+    _check(lib().ia_train_stats(ctx, C.byref(st), _stream(stream)), ctx)
+    return st.as_dict()
 
 
 def ia_loss_scale(ctx, stream=None):

@@ -52,6 +52,7 @@ struct ia_ctx {
   // counters
   unsigned long long* d_stats = nullptr;
   unsigned int* d_counter = nullptr;
+  unsigned long long* d_tstats = nullptr;  // counters of the last training step
   // scratch for host-memory outputs of ia_render
   float* d_out = nullptr;
   size_t out_cap = 0;
@@ -91,6 +92,8 @@ struct ia_ctx {
   int prow_cap = 0;
   float* d_prows = nullptr;
   int pair_cap = 0;
+  int pb1_cap = 0;
+  float* d_pb1 = nullptr;     // per-pose layer-1 bias of the training step's proposal
   float* d_pxc = nullptr;
   int* d_pstart = nullptr;
 };
@@ -231,9 +234,9 @@ ia_status need_ready(ia_ctx* c, int pose, bool need_occ) {
   return IA_OK;
 }
 
-void read_stats(ia_ctx* c, ia_render_stats* out, cudaStream_t s) {
+void read_stats(ia_ctx* c, ia_render_stats* out, cudaStream_t s, const unsigned long long* src = nullptr) {
   unsigned long long h[ST_COUNT];
-  cudaMemcpyAsync(h, c->d_stats, sizeof(h), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(h, src ? src : c->d_stats, sizeof(h), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
   out->rays = (int64_t)h[ST_RAYS];
   out->hit_rays = (int64_t)h[ST_HIT];
@@ -312,6 +315,8 @@ ia_status ia_create(const ia_config* cfg, ia_ctx** out) {
   if (e == cudaSuccess) e = dalloc(&c->d_sigma, (size_t)R * R * R);
   if (e == cudaSuccess) e = dalloc(&c->d_stats, (size_t)ST_COUNT);
   if (e == cudaSuccess) e = dalloc(&c->d_counter, (size_t)1);
+  if (e == cudaSuccess) e = dalloc(&c->d_tstats, (size_t)ST_COUNT);
+  if (e == cudaSuccess) e = cudaMemset(c->d_tstats, 0, sizeof(unsigned long long) * ST_COUNT);
   if (e == cudaSuccess) e = cudaMemset(c->d_occ_train, 0, words * sizeof(uint32_t));
   if (e != cudaSuccess) {
     ia_status st = cuda_fail(nullptr, e, "ia_create");
@@ -342,6 +347,7 @@ void ia_destroy(ia_ctx* c) {
   dfree(c->d_sigma);
   dfree(c->d_stats);
   dfree(c->d_counter);
+  dfree(c->d_tstats);
   dfree(c->d_out);
   dfree(c->d_ray_n);
   dfree(c->d_ray_dt);
@@ -364,6 +370,7 @@ void ia_destroy(ia_ctx* c) {
   dfree(c->d_pv);
   dfree(c->d_prows);
   dfree(c->d_pxc);
+  dfree(c->d_pb1);
   dfree(c->d_pstart);
   delete c;
 }
@@ -689,6 +696,7 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
   const size_t V = (size_t)c->Rw * c->Rw * c->Rw;
   IA_CUDA(c, cudaMemsetAsync(c->d_count, 0, sizeof(int), s), "ia_train_step");
   if (c->d_overflow) IA_CUDA(c, cudaMemsetAsync(c->d_overflow, 0, sizeof(int), s), "ia_train_step");
+  IA_CUDA(c, cudaMemsetAsync(c->d_tstats, 0, sizeof(unsigned long long) * ST_COUNT, s), "ia_train_step");
   IA_CUDA(c, cudaMemsetAsync(g->table, 0, sizeof(float) * nt, s), "ia_train_step");
   IA_CUDA(c, cudaMemsetAsync(g->mlp, 0, sizeof(float) * nm, s), "ia_train_step");
   IA_CUDA(c, cudaMemsetAsync(g->skin, 0, sizeof(float) * V * c->nb, s), "ia_train_step");
@@ -734,7 +742,25 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
   a.n_mlp_f = (size_t)nm;
   a.n_skin_f = V * c->nb;
   a.n_bones_f = (size_t)c->n_poses * c->nb * 12;
+  a.theta_all = c->d_theta;
+  a.stats = c->d_tstats;
+  if (a.P.search) {
+    if (c->n_poses > c->pb1_cap) {
+      IA_CUDA(c, cudaStreamSynchronize(s), "ia_train_step");
+      c->pb1_cap = 0;
+      IA_CUDA(c, dalloc(&c->d_pb1, (size_t)c->n_poses * kWidth), "ia_train_step: workspace");
+      c->pb1_cap = c->n_poses;
+    }
+    a.P.prop.b1p = c->d_pb1;
+  }
   IA_CUDA(c, launch_train(a, &c->x_map, c->num_sms, s), "ia_train_step: kernels");
+  return IA_OK;
+}
+
+ia_status ia_train_stats(ia_ctx* c, ia_render_stats* stats, void* stream) {
+  if (!c || !stats) return fail(c, IA_ERR_ARG, "null argument");
+  read_stats(c, stats, (cudaStream_t)stream, c->d_tstats);
+  stats->early_stopped = 0;
   return IA_OK;
 }
 

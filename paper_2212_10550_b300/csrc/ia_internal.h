@@ -11,6 +11,12 @@
 
 namespace ia {
 
+// warp-reduce a per-lane count, one atomic per warp; all 32 lanes call
+__device__ __forceinline__ void flush_stats(unsigned long long* stats, int idx, long long v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+  if ((threadIdx.x & 31) == 0 && v != 0) atomicAdd(stats + idx, (unsigned long long)v);
+}
+
 enum StatIdx {
   ST_RAYS = 0, ST_HIT, ST_MARCHED, ST_OCC, ST_STARTS, ST_ITERS, ST_CONV, ST_ROOTS, ST_EARLY, ST_PROP, ST_FALLBACK,
   ST_COUNT = 16
@@ -110,7 +116,13 @@ struct TrainArgs {
   int* good_steps;       // steps since the last overflow
   int* err;              // tensor-core pipeline wait expired
   size_t n_table_f, n_mlp_f, n_skin_f, n_bones_f;  // gradient sizes (floats)
+  const double* theta_all;  // [n_poses][nb][3] (proposal search: per-pose layer-1 bias)
+  unsigned long long* stats;  // [ST_COUNT] counters of this step
 };
+
+// b1p[pose][j] = b1[j] + W1[j, pose columns] . theta_pose for every pose
+cudaError_t launch_prop_bias(const PropDev& Q, int nb, const double* theta_all, int n_poses, float* b1p,
+                             cudaStream_t s);
 
 constexpr float kInitialLossScale = 16384.f;  // 2^14
 

@@ -169,12 +169,6 @@ size_t posed_smem_bytes_p(int threads) {
 
 size_t posed_smem_bytes(int threads) { return posed_smem_bytes_p<Prec::F32>(threads); }
 
-__device__ __forceinline__ void flush_stats(unsigned long long* stats, int idx, long long v) {
-  // warp-reduce then one atomic per warp
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
-  if ((threadIdx.x & 31) == 0 && v != 0) atomicAdd(stats + idx, (unsigned long long)v);
-}
-
 template <typename Kern>
 static cudaError_t set_smem(Kern k, size_t smem) {
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

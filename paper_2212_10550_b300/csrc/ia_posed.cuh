@@ -62,12 +62,13 @@ __device__ __forceinline__ void field_eval_lane(const FieldDev& F, const FieldSm
 // picks each sample's first starts: the top_k bones by logit (ties to the lower
 // bone), the first shifted by the predicted offset; when none of them yields a
 // valid root the search continues over every bone-wise start (the fallback).
+// With Q.b1p set, lane_pose[s] names sample s's pose (its layer-1 bias row).
 template <int NS, Prec P>
 __device__ __forceinline__ void posed_field_warp_n(const SkinDev& S, const float4* const* M, const FieldDev& F,
                                                    const SolveCfg& cfg, const float* const* Ninv, const FieldSmem& fs,
                                                    float4* roots, const bool* active, const float3* xn,
                                                    PosedOut* out, SampleStats& st, const PropDev& Q = PropDev{},
-                                                   bool use_prop = false) {
+                                                   bool use_prop = false, const int* lane_pose = nullptr) {
   const int tid = threadIdx.x, stride = blockDim.x;
   // ---- proposed starts
   int nprop[NS], pk[NS][2];
@@ -84,7 +85,8 @@ __device__ __forceinline__ void posed_field_warp_n(const SkinDev& S, const float
       for (int s = 0; s < NS; ++s) {
         float f16[16];
         prop_encode(Q, active[s] ? xn[s] : make_float3(Q.nmin[0], Q.nmin[1], Q.nmin[2]), f16);
-        const float* O = prop_mma_warp<P>(fs.pw, fs.xstage, f16) + (threadIdx.x & 31) * (kPropMaxOut + 1);
+        const float* O = prop_mma_warp<P>(fs.pw, fs.xstage, f16, Q.b1p, lane_pose ? lane_pose[s] : 0) +
+                         (threadIdx.x & 31) * (kPropMaxOut + 1);
         if (active[s]) {
           int b0 = 0, b1 = -1;
           float v0 = O[0], v1 = -3.0e38f;

@@ -278,4 +278,26 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n,
   return cudaGetLastError();
 }
 
+// per-pose layer-1 bias of the proposal: one thread per (pose, hidden unit),
+// fp32 accumulation in the order of the per-block fold (stage_prop_h)
+__global__ void prop_bias_kernel(const PropDev Q, int nb, const double* __restrict__ theta_all, int n_poses,
+                                 float* __restrict__ b1p) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_poses * kWidth) return;
+  const int pose = i / kWidth, q = i % kWidth;
+  const int nin = Q.n_in, nf = 2 * Q.L;
+  const float* g = Q.mlp;
+  const double* th = theta_all + (size_t)pose * 3 * nb;
+  float f = g[kWidth * nin + q];
+  for (int j = 0; j < 3 * nb; ++j) f = fmaf(g[q * nin + nf + j], (float)th[j], f);
+  b1p[i] = f;
+}
+
+cudaError_t launch_prop_bias(const PropDev& Q, int nb, const double* theta_all, int n_poses, float* b1p,
+                             cudaStream_t s) {
+  const int n = n_poses * kWidth;
+  prop_bias_kernel<<<(n + 255) / 256, 256, 0, s>>>(Q, nb, theta_all, n_poses, b1p);
+  return cudaGetLastError();
+}
+
 }  // namespace ia

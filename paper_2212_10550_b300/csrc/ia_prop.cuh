@@ -33,6 +33,8 @@ struct PropDev {
   const float* mlp;        // packed fp32: W1 [64][n_in], b1, W2, b2, W3, b3, W4 [nb+3][64], b4
   int n_in;                // 2L + 3 nb
   int top_k;               // 1 or 2
+  const float* b1p;        // [n_poses][64] per-pose layer-1 bias b1' (kernels whose
+                           // lanes hold different poses), or null: b1' staged per block
 };
 
 // hash features of x' over the normalised box (2L values, zero-padded to 16)
@@ -107,7 +109,8 @@ __device__ __forceinline__ void stage_prop_h(const PropDev& Q, int nb, const dou
       float f = 0.f;
       if (q < kWidth) {  // b1' = b1 + W1[:, pose part] theta (fp32)
         f = b1[q];
-        for (int i = 0; i < 3 * nb; ++i) f = fmaf(g[q * nin + nf + i], (float)theta[i], f);
+        if (theta)
+          for (int i = 0; i < 3 * nb; ++i) f = fmaf(g[q * nin + nf + i], (float)theta[i], f);
       } else if (q < 2 * kWidth) {
         f = b2[q - kWidth];
       } else if (q < 3 * kWidth) {
@@ -144,10 +147,12 @@ __device__ __forceinline__ void prop_hidden(const uint32_t* __restrict__ W, cons
 }
 
 // The warp's 32 feature rows -> 32 output rows (logits, offset) in the staging
-// area O [32][kPropMaxOut + 1]; all 32 lanes call.  Returns O.
+// area O [32][kPropMaxOut + 1]; all 32 lanes call.  Returns O.  With b1p, each
+// row takes the layer-1 bias of its own lane's pose (b1p + 64 * pose).
 template <Prec P>
 __device__ __forceinline__ const float* prop_mma_warp(const uint32_t* __restrict__ sw, uint32_t* xs,
-                                                      const float feat[16]) {
+                                                      const float feat[16], const float* __restrict__ b1p = nullptr,
+                                                      int pose = 0) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   uint32_t* X = xs;
   float* O = reinterpret_cast<float*>(xs + 32 * kPW1Stride);
@@ -160,11 +165,18 @@ __device__ __forceinline__ const float* prop_mma_warp(const uint32_t* __restrict
     const int r0 = 16 * mt + g, r1 = r0 + 8;
     uint32_t A1[4] = {X[r0 * kPW1Stride + t], X[r1 * kPW1Stride + t], X[r0 * kPW1Stride + 4 + t],
                       X[r1 * kPW1Stride + 4 + t]};
+    const float* bias0 = bias;  // layer-1 bias of rows r0 and r1
+    const float* bias1 = bias;
+    if (b1p) {
+      bias0 = b1p + kWidth * __shfl_sync(kFull, pose, r0);
+      bias1 = b1p + kWidth * __shfl_sync(kFull, pose, r1);
+    }
     float acc[8][4];
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
-      const float b0 = bias[8 * nt + 2 * t], b1 = bias[8 * nt + 2 * t + 1];
-      acc[nt][0] = b0; acc[nt][1] = b1; acc[nt][2] = b0; acc[nt][3] = b1;
+      const float2 c0 = *reinterpret_cast<const float2*>(bias0 + 8 * nt + 2 * t);
+      const float2 c1 = *reinterpret_cast<const float2*>(bias1 + 8 * nt + 2 * t);
+      acc[nt][0] = c0.x; acc[nt][1] = c0.y; acc[nt][2] = c1.x; acc[nt][3] = c1.y;
       const uint32_t* Wr = sw + kPOffW1 + (8 * nt + g) * kPW1Stride;
       mma16816<P>(acc[nt], A1, Wr[t], Wr[4 + t]);
     }

@@ -37,34 +37,42 @@ constexpr int kActF = 0, kActH1 = kIn, kActH2 = kActH1 + kWidth, kActD1 = kActH2
 
 __global__ void train_march_kernel(const TrainArgs a) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= a.n_rays) return;
-  const int pose = a.pose[r];
-  a.ray_n[r] = 0;
-  a.ray_dt[r] = 0.f;
-  if (pose < 0 || pose >= a.n_poses) return;
-  const float ow[3] = {a.origin[3 * r], a.origin[3 * r + 1], a.origin[3 * r + 2]};
-  const float dw[3] = {a.direction[3 * r], a.direction[3 * r + 1], a.direction[3 * r + 2]};
-  float o[3], d[3], tn, tf;
-  if (!normalise_and_clip(a.B0inv + 12 * (size_t)pose, a.box, ow, dw, o, d, tn, tf)) return;
-  const float dt = slot_delta(tn, tf, a.n_slots);
-  int n = 0;
-  for (int i = 0; i < a.n_slots; ++i) {
-    const int cell = cell_of(a.box, slot_position(o, d, tn, dt, i));
-    n += (__ldg(a.occ + (cell >> 5)) >> (cell & 31)) & 1u;
-  }
-  a.ray_n[r] = n;
-  a.ray_dt[r] = dt;
-  if (n == 0) return;
-  int base = atomicAdd(a.count, n), j = 0;
-  for (int i = 0; i < a.n_slots; ++i) {
-    const float3 x = slot_position(o, d, tn, dt, i);
-    const int cell = cell_of(a.box, x);
-    if ((__ldg(a.occ + (cell >> 5)) >> (cell & 31)) & 1u) {
-      a.s_pos[base + j] = make_float4(x.x, x.y, x.z, __int_as_float(pose));
-      a.ray_idx[(size_t)r * a.n_slots + j] = base + j;
-      ++j;
+  int n = 0, hit = 0;
+  if (r < a.n_rays) {
+    const int pose = a.pose[r];
+    float dt = 0.f;
+    float o[3], d[3], tn, tf;
+    if (pose >= 0 && pose < a.n_poses) {
+      const float ow[3] = {a.origin[3 * r], a.origin[3 * r + 1], a.origin[3 * r + 2]};
+      const float dw[3] = {a.direction[3 * r], a.direction[3 * r + 1], a.direction[3 * r + 2]};
+      hit = normalise_and_clip(a.B0inv + 12 * (size_t)pose, a.box, ow, dw, o, d, tn, tf) ? 1 : 0;
+    }
+    if (hit) {
+      dt = slot_delta(tn, tf, a.n_slots);
+      for (int i = 0; i < a.n_slots; ++i) {
+        const int cell = cell_of(a.box, slot_position(o, d, tn, dt, i));
+        n += (__ldg(a.occ + (cell >> 5)) >> (cell & 31)) & 1u;
+      }
+    }
+    a.ray_n[r] = n;
+    a.ray_dt[r] = dt;
+    if (n > 0) {
+      int base = atomicAdd(a.count, n), j = 0;
+      for (int i = 0; i < a.n_slots; ++i) {
+        const float3 x = slot_position(o, d, tn, dt, i);
+        const int cell = cell_of(a.box, x);
+        if ((__ldg(a.occ + (cell >> 5)) >> (cell & 31)) & 1u) {
+          a.s_pos[base + j] = make_float4(x.x, x.y, x.z, __int_as_float(pose));
+          a.ray_idx[(size_t)r * a.n_slots + j] = base + j;
+          ++j;
+        }
+      }
     }
   }
+  flush_stats(a.stats, ST_RAYS, r < a.n_rays ? 1 : 0);
+  flush_stats(a.stats, ST_HIT, hit);
+  flush_stats(a.stats, ST_MARCHED, hit ? a.n_slots : 0);
+  flush_stats(a.stats, ST_OCC, n);
 }
 
 template <Prec P>
@@ -74,7 +82,7 @@ __global__ void __launch_bounds__(256) train_sample_kernel(const TrainArgs a) {
   ps.mlp = a.P.mlp;
   ps.n_in = a.P.n_in;
   ps.table_h = a.P.table_h;
-  ps.search = 0;
+  ps.search = a.P.search;  // proposal: layer-1 bias per lane from P.prop.b1p
   ps.prop = a.P.prop;
   ps.theta = nullptr;
   ps.Ninv = a.P.Ninv;
@@ -90,6 +98,7 @@ __global__ void __launch_bounds__(256) train_sample_kernel(const TrainArgs a) {
     float3 xn[kNS];
     const float4* Ms[kNS];
     const float* Ns[kNS];
+    int poses[kNS];
     PosedOut o[kNS];
 #pragma unroll
     for (int q = 0; q < kNS; ++q) {
@@ -97,11 +106,13 @@ __global__ void __launch_bounds__(256) train_sample_kernel(const TrainArgs a) {
       act[q] = s < n;
       const float4 p = act[q] ? a.s_pos[s] : make_float4(0.f, 0.f, 0.f, 0.f);
       const int pose = act[q] ? __float_as_int(p.w) : 0;
+      poses[q] = pose;
       xn[q] = make_float3(p.x, p.y, p.z);
       Ms[q] = a.P.S.M + (size_t)pose * a.V * 3;
       Ns[q] = a.P.Ninv + (size_t)pose * a.P.cfg.nb * 12;
     }
-    posed_field_warp_n<kNS, P>(a.P.S, Ms, a.P.F, a.P.cfg, Ns, sm.fs, sm.roots, act, xn, o, st);
+    posed_field_warp_n<kNS, P>(a.P.S, Ms, a.P.F, a.P.cfg, Ns, sm.fs, sm.roots, act, xn, o, st, a.P.prop,
+                               a.P.search != 0, poses);
 #pragma unroll
     for (int q = 0; q < kNS; ++q) {
       const int s = base + q * 32 + lane;
@@ -111,6 +122,12 @@ __global__ void __launch_bounds__(256) train_sample_kernel(const TrainArgs a) {
       a.s_x[s] = make_float4(o[q].xstar.x, o[q].xstar.y, o[q].xstar.z, has ? 1.f : 0.f);
     }
   }
+  flush_stats(a.stats, ST_STARTS, st.starts);
+  flush_stats(a.stats, ST_ITERS, st.iters);
+  flush_stats(a.stats, ST_CONV, st.converged);
+  flush_stats(a.stats, ST_ROOTS, st.roots);
+  flush_stats(a.stats, ST_PROP, st.proposed);
+  flush_stats(a.stats, ST_FALLBACK, st.fallbacks);
 }
 
 template <Prec P>
@@ -644,6 +661,11 @@ cudaError_t launch_train(const TrainArgs& a, const CUtensorMap* map, int num_sms
   train_march_kernel<<<rb, 128, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const Prec P = (Prec)a.prec;
+  if (a.P.search) {
+    if ((e = launch_prop_bias(a.P.prop, a.P.cfg.nb, a.theta_all, a.n_poses, const_cast<float*>(a.P.prop.b1p), s)) !=
+        cudaSuccess)
+      return e;
+  }
   auto sample = P == Prec::F32 ? train_sample_kernel<Prec::F32>
                 : P == Prec::F16 ? train_sample_kernel<Prec::F16> : train_sample_kernel<Prec::BF16>;
   const size_t smem = P == Prec::F32 ? train_sample_smem<Prec::F32>()

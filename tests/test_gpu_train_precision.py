@@ -105,9 +105,14 @@ def test_train_step_reduced_precision(ia, prec, config, n_poses, n_rays):
     ia.ia_train_step(ctx, dev["origin"], dev["direction"], dev["pose"], dev["target"], loss, g,
                      occ_grid=ia.IA_OCC_POSE)
     scale, skipped = ia.ia_loss_scale(ctx)
+    st = ia.ia_train_stats(ctx)
     torch.cuda.synchronize()
     ia.ia_destroy(ctx)
     assert not skipped
+    # plain search: every occupied sample runs every bone-wise start
+    assert st["rays"] == keep.sum() and st["occupied_samples"] > 0
+    assert st["starts"] == sc.n_bones * st["occupied_samples"]
+    assert st["proposed"] == 0 and st["fallbacks"] == 0
     assert scale == (16384.0 if prec == 1 else 1.0)
 
     ref_loss, _, _, ref = G.train(om, op, occ, rays["origin"], rays["direction"], rays["pose"], rays["target"])
@@ -195,3 +200,76 @@ def test_overflow_skips_the_step_and_halves_the_scale(ia):
     assert not skipped and scale == 8192.0
     assert torch.count_nonzero(g["mlp"]).item() > 0
     ia.ia_destroy(ctx)
+
+
+def test_train_step_with_proposal_starts(ia):
+    """fp16 step whose correspondence search starts from the proposal's top-2
+    bones of each sample's own pose (the batch mixes 4 poses, so every warp
+    holds several poses) against the oracle's proposal-start step.  The
+    proposal is the seeded initial network with its pose columns amplified, so
+    the chosen bones depend strongly on the pose; the oracle reads the same
+    fp16-rounded weights (the pose columns are folded in fp32 on both sides).
+    Rays the oracle flags (near-tied logits, marginal roots) are dropped."""
+    from oracle import prop as PP
+    sc = S.make_scene("full", 0)
+    table, mlp = S.make_field(sc, 0)
+    t_op, m_op = _operands(table, mlp, 1)
+    om = O.OracleModel(sc, t_op, m_op)
+    n_poses = 4
+    poses = [S.make_pose(sc, 20 + i) for i in range(n_poses)]
+    theta = np.stack([p[0] for p in poses])
+    op = [om.pose(*p) for p in poses]
+    occ = np.zeros((sc.occ_res ** 3 + 31) // 32, np.uint32)
+    for p in op:
+        occ |= om.occupancy(p)[1]
+    cfg = S.proposal_config()
+    pt, pm = S.proposal_init(sc, cfg, 3)
+    nf = 2 * cfg["n_levels"]
+    pm["W1"][:, nf:] *= 4.0
+    pm_op = {k: (v.copy() if not k.startswith("W") else _round_fp16(v)) for k, v in pm.items()}
+    pm_op["W1"][:, nf:] = pm["W1"][:, nf:]  # folded into the fp32 bias, not rounded
+    pr = PP.PropModel(om, cfg, pt, pm_op)
+    rb = S.make_ray_batch(sc, 2048, n_poses, seed=7)
+    args = (om, op, occ, rb["origin"], rb["direction"], rb["pose"], rb["target"])
+    _, _, flags, _ = G.train(*args, grad=False, prop=pr, theta=theta)
+    keep = flags == 0
+    rays = {k: rb[k][keep] for k in ("origin", "direction", "pose", "target")}
+
+    ctx = _ctx(ia, sc, table, mlp, 1)
+    ia.ia_set_pose(ctx, theta, np.stack([p[1] for p in poses]))
+    ia.ia_set_occupancy(ctx, occ)
+    ia.ia_proposal_init(ctx, ia.make_proposal_config(cfg["n_levels"], cfg["log2_table"], cfg["level_res"],
+                                                     cfg["top_k"], cfg["offset_weight"]))
+    ia.ia_proposal_set_params(ctx, torch.from_numpy(np.ascontiguousarray(pt)).cuda(),
+                              torch.from_numpy(S.pack_proposal(pm)).cuda())
+    ia.ia_set_search(ctx, ia.IA_SEARCH_PROPOSAL)
+    g = _grads(ia, ctx, sc, n_poses)
+    dev = _dev(rays)
+    loss = torch.zeros(1, device="cuda")
+    ia.ia_train_step(ctx, dev["origin"], dev["direction"], dev["pose"], dev["target"], loss, g,
+                     occ_grid=ia.IA_OCC_POSE)
+    st = ia.ia_train_stats(ctx)
+    torch.cuda.synchronize()
+    ia.ia_destroy(ctx)
+
+    args = (om, op, occ, rays["origin"], rays["direction"], rays["pose"], rays["target"])
+    fb = np.zeros(len(rays["pose"]), np.int32)
+    ref_loss, _, _, ref = G.train(*args, prop=pr, theta=theta, fallbacks=fb)
+    # which samples needed the fallback depends on the bones proposed for each
+    # sample's own pose: the counts must agree (a few marginal samples aside)
+    print(f"fallbacks gpu {st['fallbacks']} oracle {int(fb.sum())} of {st['proposed']} proposed samples "
+          f"({st['occupied_samples']} samples)")
+    assert st["proposed"] == st["occupied_samples"] > 0
+    assert abs(st["fallbacks"] - int(fb.sum())) <= max(3, 0.005 * fb.sum())
+    assert 0 < fb.sum() < st["proposed"]
+    plain_loss, _, _, plain = G.train(*args)
+    lg = float(loss.item())
+    print(f"proposal fp16: {keep.sum()} rays, loss gpu {lg:.6e} oracle {ref_loss:.6e} (plain search {plain_loss:.6e})")
+    assert abs(lg - ref_loss) <= TOL[1]["loss"] * ref_loss
+    for k in ("table", "mlp", "skin", "bones"):
+        a = g[k].cpu().numpy().astype(np.float64)
+        b = ref[k].reshape(-1)
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        rel_plain = np.linalg.norm(plain[k].reshape(-1) - b) / max(np.linalg.norm(b), 1e-30)
+        print(f"  grad {k}: rel L2 {rel:.2e} (oracle proposal vs oracle plain search: {rel_plain:.2e})")
+        assert rel <= TOL[1]["grad"], k

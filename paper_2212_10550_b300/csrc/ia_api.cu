@@ -67,6 +67,7 @@ struct ia_ctx {
   float4* d_s_out = nullptr;
   float4* d_s_x = nullptr;
   float4* d_s_grad = nullptr;
+  float4* d_s_dfeat = nullptr;
   float* d_act = nullptr;           // fp32 step: per-sample activations
   uint16_t* d_X = nullptr;          // fp16 / bf16 step: channel-major GEMM operands
   int64_t x_ld = 0;
@@ -92,6 +93,8 @@ struct ia_ctx {
   int prow_cap = 0;
   float* d_prows = nullptr;
   int pair_cap = 0;
+  int pose_ws_cap = 0;
+  int* d_pose_ws = nullptr;   // training step: per-pose sample totals / offsets and fill counters
   int pb1_cap = 0;
   float* d_pb1 = nullptr;     // per-pose layer-1 bias of the training step's proposal
   float* d_pxc = nullptr;
@@ -357,6 +360,7 @@ void ia_destroy(ia_ctx* c) {
   dfree(c->d_s_out);
   dfree(c->d_s_x);
   dfree(c->d_s_grad);
+  dfree(c->d_s_dfeat);
   dfree(c->d_act);
   dfree(c->d_X);
   dfree(c->d_scale);
@@ -371,6 +375,7 @@ void ia_destroy(ia_ctx* c) {
   dfree(c->d_prows);
   dfree(c->d_pxc);
   dfree(c->d_pb1);
+  dfree(c->d_pose_ws);
   dfree(c->d_pstart);
   delete c;
 }
@@ -668,6 +673,7 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
     IA_CUDA(c, dalloc(&c->d_s_out, cap), "ia_train_step: workspace");
     IA_CUDA(c, dalloc(&c->d_s_x, cap), "ia_train_step: workspace");
     IA_CUDA(c, dalloc(&c->d_s_grad, cap), "ia_train_step: workspace");
+    IA_CUDA(c, dalloc(&c->d_s_dfeat, cap * (kIn / 4)), "ia_train_step: workspace");
     if (c->cfg.precision == IA_FP32) {
       IA_CUDA(c, dalloc(&c->d_act, cap * kActStride), "ia_train_step: workspace");
     } else {
@@ -697,6 +703,13 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
   IA_CUDA(c, cudaMemsetAsync(c->d_count, 0, sizeof(int), s), "ia_train_step");
   if (c->d_overflow) IA_CUDA(c, cudaMemsetAsync(c->d_overflow, 0, sizeof(int), s), "ia_train_step");
   IA_CUDA(c, cudaMemsetAsync(c->d_tstats, 0, sizeof(unsigned long long) * ST_COUNT, s), "ia_train_step");
+  if (c->n_poses > c->pose_ws_cap) {
+    IA_CUDA(c, cudaStreamSynchronize(s), "ia_train_step");
+    c->pose_ws_cap = 0;
+    IA_CUDA(c, dalloc(&c->d_pose_ws, (size_t)2 * c->n_poses), "ia_train_step: workspace");
+    c->pose_ws_cap = c->n_poses;
+  }
+  IA_CUDA(c, cudaMemsetAsync(c->d_pose_ws, 0, sizeof(int) * 2 * c->n_poses, s), "ia_train_step");
   IA_CUDA(c, cudaMemsetAsync(g->table, 0, sizeof(float) * nt, s), "ia_train_step");
   IA_CUDA(c, cudaMemsetAsync(g->mlp, 0, sizeof(float) * nm, s), "ia_train_step");
   IA_CUDA(c, cudaMemsetAsync(g->skin, 0, sizeof(float) * V * c->nb, s), "ia_train_step");
@@ -724,6 +737,7 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
   a.s_out = c->d_s_out;
   a.s_x = c->d_s_x;
   a.s_grad = c->d_s_grad;
+  a.s_dfeat = c->d_s_dfeat;
   a.act = c->d_act;
   a.loss = loss;
   a.rgb_out = rgb_out;
@@ -744,6 +758,8 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
   a.n_bones_f = (size_t)c->n_poses * c->nb * 12;
   a.theta_all = c->d_theta;
   a.stats = c->d_tstats;
+  a.pose_tot = c->d_pose_ws;
+  a.pose_fill = c->d_pose_ws + c->n_poses;
   if (a.P.search) {
     if (c->n_poses > c->pb1_cap) {
       IA_CUDA(c, cudaStreamSynchronize(s), "ia_train_step");

@@ -118,6 +118,9 @@ struct TrainArgs {
   size_t n_table_f, n_mlp_f, n_skin_f, n_bones_f;  // gradient sizes (floats)
   const double* theta_all;  // [n_poses][nb][3] (proposal search: per-pose layer-1 bias)
   unsigned long long* stats;  // [ST_COUNT] counters of this step
+  int* pose_tot;         // [n_poses] samples per pose, then the first index of each pose (zeroed by the host)
+  int* pose_fill;        // [n_poses] fill counters (zeroed by the host)
+  float4* s_dfeat;       // [samples][kIn / 4] dL/dfeatures (fp32, unscaled)
 };
 
 // b1p[pose][j] = b1[j] + W1[j, pose columns] . theta_pose for every pose

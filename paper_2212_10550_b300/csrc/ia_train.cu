@@ -2,8 +2,9 @@
 // its hand-written backward (sm_103a; fp32, or fp16 / bf16 operands with fp32
 // accumulation and master gradients).
 //
-//   train_march_kernel      world rays -> normalised space of each ray's pose,
-//                           occupied slots, compacted sample list
+//   train_count_kernel,     world rays -> normalised space of each ray's pose,
+//   pose_scan_kernel,       occupied slots; samples compacted and grouped by
+//   train_emit_kernel       pose (count, per-pose offsets, emit)
 //   train_sample_kernel     posed field f'(x') at every sample (same warp-level
 //                           correspondence search as rendering, per-lane pose)
 //   train_composite_kernel  per ray: front-to-back compositing, loss, and its
@@ -35,44 +36,76 @@ constexpr int kActF = 0, kActH1 = kIn, kActH2 = kActH1 + kWidth, kActD1 = kActH2
 
 // ---------------------------------------------------------------------------
 
-__global__ void train_march_kernel(const TrainArgs a) {
+// March of one training ray in the normalised space of its pose: the occupied
+// slots in march order.  Returns the count; emit(i, x) is called for each.
+template <typename Emit>
+__device__ __forceinline__ int march_train_ray(const TrainArgs& a, int r, int& pose, int& hit, float& dt, Emit emit) {
+  pose = a.pose[r];
+  hit = 0;
+  dt = 0.f;
+  if (pose < 0 || pose >= a.n_poses) return 0;
+  const float ow[3] = {a.origin[3 * r], a.origin[3 * r + 1], a.origin[3 * r + 2]};
+  const float dw[3] = {a.direction[3 * r], a.direction[3 * r + 1], a.direction[3 * r + 2]};
+  float o[3], d[3], tn, tf;
+  if (!normalise_and_clip(a.B0inv + 12 * (size_t)pose, a.box, ow, dw, o, d, tn, tf)) return 0;
+  hit = 1;
+  dt = slot_delta(tn, tf, a.n_slots);
+  int n = 0;
+  for (int i = 0; i < a.n_slots; ++i) {
+    const float3 x = slot_position(o, d, tn, dt, i);
+    const int cell = cell_of(a.box, x);
+    if ((__ldg(a.occ + (cell >> 5)) >> (cell & 31)) & 1u) emit(n++, x);
+  }
+  return n;
+}
+
+// pass 1: per-ray sample counts and per-pose totals
+__global__ void train_count_kernel(const TrainArgs a) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   int n = 0, hit = 0;
   if (r < a.n_rays) {
-    const int pose = a.pose[r];
-    float dt = 0.f;
-    float o[3], d[3], tn, tf;
-    if (pose >= 0 && pose < a.n_poses) {
-      const float ow[3] = {a.origin[3 * r], a.origin[3 * r + 1], a.origin[3 * r + 2]};
-      const float dw[3] = {a.direction[3 * r], a.direction[3 * r + 1], a.direction[3 * r + 2]};
-      hit = normalise_and_clip(a.B0inv + 12 * (size_t)pose, a.box, ow, dw, o, d, tn, tf) ? 1 : 0;
-    }
-    if (hit) {
-      dt = slot_delta(tn, tf, a.n_slots);
-      for (int i = 0; i < a.n_slots; ++i) {
-        const int cell = cell_of(a.box, slot_position(o, d, tn, dt, i));
-        n += (__ldg(a.occ + (cell >> 5)) >> (cell & 31)) & 1u;
-      }
-    }
+    int pose;
+    float dt;
+    n = march_train_ray(a, r, pose, hit, dt, [](int, float3) {});
     a.ray_n[r] = n;
     a.ray_dt[r] = dt;
-    if (n > 0) {
-      int base = atomicAdd(a.count, n), j = 0;
-      for (int i = 0; i < a.n_slots; ++i) {
-        const float3 x = slot_position(o, d, tn, dt, i);
-        const int cell = cell_of(a.box, x);
-        if ((__ldg(a.occ + (cell >> 5)) >> (cell & 31)) & 1u) {
-          a.s_pos[base + j] = make_float4(x.x, x.y, x.z, __int_as_float(pose));
-          a.ray_idx[(size_t)r * a.n_slots + j] = base + j;
-          ++j;
-        }
-      }
-    }
+    if (n > 0) atomicAdd(a.pose_tot + pose, n);
   }
   flush_stats(a.stats, ST_RAYS, r < a.n_rays ? 1 : 0);
   flush_stats(a.stats, ST_HIT, hit);
   flush_stats(a.stats, ST_MARCHED, hit ? a.n_slots : 0);
   flush_stats(a.stats, ST_OCC, n);
+}
+
+// pass 2: per-pose totals -> first sample index of each pose; total count
+__global__ void pose_scan_kernel(const TrainArgs a) {
+  if (threadIdx.x != 0) return;
+  int run = 0;
+  for (int p = 0; p < a.n_poses; ++p) {
+    const int t = a.pose_tot[p];
+    a.pose_tot[p] = run;
+    run += t;
+  }
+  *a.count = run;
+}
+
+// pass 3: samples written grouped by pose (so that concurrent warps of the
+// sample kernels share one pose's blended grid in L2), each ray's list of its
+// sample indices in march order
+__global__ void train_emit_kernel(const TrainArgs a) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= a.n_rays) return;
+  const int n = a.ray_n[r];
+  if (n == 0) return;
+  const int pose = a.pose[r];
+  const int base = a.pose_tot[pose] + atomicAdd(a.pose_fill + pose, n);
+  int p, hit;
+  float dt;
+  int* idx = a.ray_idx + (size_t)r * a.n_slots;
+  march_train_ray(a, r, p, hit, dt, [&](int j, float3 x) {
+    a.s_pos[base + j] = make_float4(x.x, x.y, x.z, __int_as_float(pose));
+    idx[j] = base + j;
+  });
 }
 
 template <Prec P>
@@ -192,49 +225,99 @@ __global__ void train_composite_kernel(const TrainArgs a) {
 // Per-sample backward
 // ---------------------------------------------------------------------------
 
-// dL/dx* -> lambda = J(x*)^-T dL/dx* -> bone-transform and skinning-grid gradients
-__device__ __forceinline__ void ift_scatter(const TrainArgs& a, int s, float3 xs, float gx, float gy, float gz) {
-  const int nb = a.P.cfg.nb;
-  const int pose = __float_as_int(a.s_pos[s].w);
-  const float4* M = a.P.S.M + (size_t)pose * a.V * 3;
-  float Mx[12], J[9], Hi[9];
-  blend_value_jac(a.P.S, M, xs, Mx, J);
-  if (!inv3(J, Hi)) return;
-  const float l0 = Hi[0] * gx + Hi[3] * gy + Hi[6] * gz;
-  const float l1 = Hi[1] * gx + Hi[4] * gy + Hi[7] * gz;
-  const float l2 = Hi[2] * gx + Hi[5] * gy + Hi[8] * gz;
+// Warp-wide sums of 16 per-lane values, scattered: lane l returns the sum over
+// all 32 lanes of v[(l >> 1) & 15] (reduce-scatter by recursive halving, 16
+// shuffles instead of 80).  All 32 lanes call; v is clobbered.
+__device__ __forceinline__ float warp_reduce_scatter16(float v[16], int lane) {
+#pragma unroll
+  for (int step = 0; step < 4; ++step) {
+    const int half = 8 >> step, off = 16 >> step;
+    const bool upper = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const float send = upper ? v[i] : v[half + i];
+      const float keep = upper ? v[half + i] : v[i];
+      v[i] = keep + __shfl_xor_sync(kFull, send, off);
+    }
+  }
+  return v[0] + __shfl_xor_sync(kFull, v[0], 1);
+}
+
+// dL/dx* -> lambda = J(x*)^-T dL/dx* -> bone-transform and skinning-grid
+// gradients.  All 32 lanes call (has = this lane carries a sample with a root).
+// When every contributing lane of the warp holds the same pose (the usual case:
+// samples are grouped by pose), the bone-transform gradient is summed over the
+// warp first and added with one atomic per entry.
+__device__ __forceinline__ void ift_scatter_warp(const TrainArgs& a, bool has, int pose, float3 xs, float gx,
+                                                 float gy, float gz) {
+  const int nb = a.P.cfg.nb, lane = threadIdx.x & 31;
+  float l0 = 0.f, l1 = 0.f, l2 = 0.f;
+  bool ok = false;
+  if (has) {
+    const float4* M = a.P.S.M + (size_t)pose * a.V * 3;
+    float Mx[12], J[9], Hi[9];
+    blend_value_jac(a.P.S, M, xs, Mx, J);
+    ok = inv3(J, Hi);
+    if (ok) {
+      l0 = Hi[0] * gx + Hi[3] * gy + Hi[6] * gz;
+      l1 = Hi[1] * gx + Hi[4] * gy + Hi[7] * gz;
+      l2 = Hi[2] * gx + Hi[5] * gy + Hi[8] * gz;
+    }
+  }
+  const unsigned okm = __ballot_sync(kFull, ok);
+  if (okm == 0) return;
+  const int p0 = __shfl_sync(kFull, pose, __ffs(okm) - 1);
+  const bool uniform = __all_sync(kFull, !ok || pose == p0);
   const float xb[4] = {xs.x, xs.y, xs.z, 1.f};
   // trilinear coefficients of x* in the skinning grid (as the forward blends them)
-  CellCoord cc = skin_cell(a.P.S, xs);
-  const float* Np = a.N + (size_t)pose * nb * 12;
-  float* gB = a.g_bones + (size_t)pose * nb * 12;
+  CellCoord cc = skin_cell(a.P.S, ok ? xs : make_float3(a.P.S.cmin[0], a.P.S.cmin[1], a.P.S.cmin[2]));
+  const float* Np = a.N + (size_t)(ok ? pose : p0) * nb * 12;
   for (int k = 0; k < nb; ++k) {
     float wk = 0.f;
+    if (ok) {
 #pragma unroll
-    for (int corner = 0; corner < 8; ++corner) {
-      const int v = corner_index(a.P.S, cc.base, corner);
-      const float cw = ((corner & 1) ? cc.f[0] : 1.f - cc.f[0]) * (((corner >> 1) & 1) ? cc.f[1] : 1.f - cc.f[1]) *
-                       (((corner >> 2) & 1) ? cc.f[2] : 1.f - cc.f[2]);
-      wk = fmaf(cw, __ldg(a.skin + (size_t)v * nb + k), wk);
+      for (int corner = 0; corner < 8; ++corner) {
+        const int v = corner_index(a.P.S, cc.base, corner);
+        const float cw = ((corner & 1) ? cc.f[0] : 1.f - cc.f[0]) * (((corner >> 1) & 1) ? cc.f[1] : 1.f - cc.f[1]) *
+                         (((corner >> 2) & 1) ? cc.f[2] : 1.f - cc.f[2]);
+        wk = fmaf(cw, __ldg(a.skin + (size_t)v * nb + k), wk);
+      }
     }
     // dL/dN_k[a][b] = -lambda_a w_k [x*;1]_b
+    if (uniform) {
+      float v[16];
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      atomicAdd(gB + k * 12 + b, -l0 * wk * xb[b]);
-      atomicAdd(gB + k * 12 + 4 + b, -l1 * wk * xb[b]);
-      atomicAdd(gB + k * 12 + 8 + b, -l2 * wk * xb[b]);
+      for (int b = 0; b < 4; ++b) {
+        v[b] = -l0 * wk * xb[b];
+        v[4 + b] = -l1 * wk * xb[b];
+        v[8 + b] = -l2 * wk * xb[b];
+        v[12 + b] = 0.f;
+      }
+      const float sum = warp_reduce_scatter16(v, lane);
+      const int idx = (lane >> 1) & 15;
+      if ((lane & 1) == 0 && idx < 12) atomicAdd(a.g_bones + ((size_t)p0 * nb + k) * 12 + idx, sum);
+    } else if (ok) {
+      float* gB = a.g_bones + ((size_t)pose * nb + k) * 12;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        atomicAdd(gB + b, -l0 * wk * xb[b]);
+        atomicAdd(gB + 4 + b, -l1 * wk * xb[b]);
+        atomicAdd(gB + 8 + b, -l2 * wk * xb[b]);
+      }
     }
     // dL/dW(v, k) = -c_v lambda . (N_k [x*;1])
-    const float* Nk = Np + 12 * k;
-    const float ln = l0 * (Nk[0] * xb[0] + Nk[1] * xb[1] + Nk[2] * xb[2] + Nk[3]) +
-                     l1 * (Nk[4] * xb[0] + Nk[5] * xb[1] + Nk[6] * xb[2] + Nk[7]) +
-                     l2 * (Nk[8] * xb[0] + Nk[9] * xb[1] + Nk[10] * xb[2] + Nk[11]);
+    if (ok) {
+      const float* Nk = Np + 12 * k;
+      const float ln = l0 * (Nk[0] * xb[0] + Nk[1] * xb[1] + Nk[2] * xb[2] + Nk[3]) +
+                       l1 * (Nk[4] * xb[0] + Nk[5] * xb[1] + Nk[6] * xb[2] + Nk[7]) +
+                       l2 * (Nk[8] * xb[0] + Nk[9] * xb[1] + Nk[10] * xb[2] + Nk[11]);
 #pragma unroll
-    for (int corner = 0; corner < 8; ++corner) {
-      const int v = corner_index(a.P.S, cc.base, corner);
-      const float cw = ((corner & 1) ? cc.f[0] : 1.f - cc.f[0]) * (((corner >> 1) & 1) ? cc.f[1] : 1.f - cc.f[1]) *
-                       (((corner >> 2) & 1) ? cc.f[2] : 1.f - cc.f[2]);
-      atomicAdd(a.g_skin + (size_t)v * nb + k, -cw * ln);
+      for (int corner = 0; corner < 8; ++corner) {
+        const int v = corner_index(a.P.S, cc.base, corner);
+        const float cw = ((corner & 1) ? cc.f[0] : 1.f - cc.f[0]) * (((corner >> 1) & 1) ? cc.f[1] : 1.f - cc.f[1]) *
+                         (((corner >> 2) & 1) ? cc.f[2] : 1.f - cc.f[2]);
+        atomicAdd(a.g_skin + (size_t)v * nb + k, -cw * ln);
+      }
     }
   }
 }
@@ -284,6 +367,44 @@ __device__ __forceinline__ void hash_backward(const TrainArgs& a, float3 xs, con
   }
 }
 
+
+// Per-sample scatter of the backward: hash-table gradient (trilinear weights of
+// dL/dfeatures), dL/dx*, and the implicit-function gradient to the bone
+// transforms and the skinning grid.  Few registers, so many warps hide the
+// gathers and atomics.  Warps walk the samples in order (grouped by pose).
+template <bool kHalfTable>
+__global__ void __launch_bounds__(256) train_scatter_kernel(const TrainArgs a) {
+  const int n = *a.count;
+  const int lane = threadIdx.x & 31;
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+    const int s = base + lane;
+    bool has = false;
+    float3 xs = make_float3(0.f, 0.f, 0.f);
+    int pose = 0;
+    if (s < n) {
+      const float4 x4 = a.s_x[s];
+      has = x4.w > 0.f;
+      xs = make_float3(x4.x, x4.y, x4.z);
+      pose = __float_as_int(a.s_pos[s].w);
+    }
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    if (has) {
+      float dfeat[kIn];
+      const float4* src = a.s_dfeat + (size_t)s * (kIn / 4);
+#pragma unroll
+      for (int i = 0; i < kIn / 4; ++i) {
+        const float4 v = src[i];
+        dfeat[4 * i] = v.x;
+        dfeat[4 * i + 1] = v.y;
+        dfeat[4 * i + 2] = v.z;
+        dfeat[4 * i + 3] = v.w;
+      }
+      hash_backward<kHalfTable>(a, xs, dfeat, gx, gy, gz);
+    }
+    ift_scatter_warp(a, has, pose, xs, gx, gy, gz);
+  }
+}
 
 __global__ void __launch_bounds__(128) train_backward_kernel(const TrainArgs a) {
   __shared__ __align__(16) float sw[kMlpPadT];
@@ -395,10 +516,10 @@ __global__ void __launch_bounds__(128) train_backward_kernel(const TrainArgs a) 
         dfeat[4 * i + 3] = fmaf(w.w, d, dfeat[4 * i + 3]);
       }
     }
-    // ---- hash encoding backward: scatter-add into the table gradient, and dL/dx*
-    float gx, gy, gz;
-    hash_backward<false>(a, xs, dfeat, gx, gy, gz);
-    ift_scatter(a, s, xs, gx, gy, gz);
+    // ---- dL/dfeatures for the scatter kernel
+    float4* dst = a.s_dfeat + (size_t)s * (kIn / 4);
+#pragma unroll
+    for (int i = 0; i < kIn / 4; ++i) dst[i] = make_float4(dfeat[4 * i], dfeat[4 * i + 1], dfeat[4 * i + 2], dfeat[4 * i + 3]);
   }
 }
 
@@ -624,11 +745,11 @@ __global__ void __launch_bounds__(128) train_backward_h_kernel(const TrainArgs a
         dfeat[4 * i + 3] = fmaf(w.w, d, dfeat[4 * i + 3]);
       }
     }
+    float4* dst = a.s_dfeat + (size_t)s * (kIn / 4);
 #pragma unroll
-    for (int i = 0; i < kIn; ++i) dfeat[i] *= inv_S;
-    float gx, gy, gz;
-    hash_backward<true>(a, xs, dfeat, gx, gy, gz);
-    ift_scatter(a, s, xs, gx, gy, gz);
+    for (int i = 0; i < kIn / 4; ++i)
+      dst[i] = make_float4(dfeat[4 * i] * inv_S, dfeat[4 * i + 1] * inv_S, dfeat[4 * i + 2] * inv_S,
+                           dfeat[4 * i + 3] * inv_S);
   }
   if (overflow) atomicExch(a.overflow, 1);
 }
@@ -658,7 +779,11 @@ __global__ void loss_scale_kernel(const TrainArgs a, int dynamic) {
 cudaError_t launch_train(const TrainArgs& a, const CUtensorMap* map, int num_sms, cudaStream_t s) {
   cudaError_t e;
   const int rb = (a.n_rays + 127) / 128;
-  train_march_kernel<<<rb, 128, 0, s>>>(a);
+  train_count_kernel<<<rb, 128, 0, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  pose_scan_kernel<<<1, 32, 0, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  train_emit_kernel<<<rb, 128, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const Prec P = (Prec)a.prec;
   if (a.P.search) {
@@ -679,11 +804,15 @@ cudaError_t launch_train(const TrainArgs& a, const CUtensorMap* map, int num_sms
   if (P == Prec::F32) {
     train_backward_kernel<<<num_sms * 4, 128, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    train_scatter_kernel<false><<<num_sms * 8, 256, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     mlp_grad_kernel<<<num_sms * 2, 256, 0, s>>>(a);
     return cudaGetLastError();
   }
   if (P == Prec::F16) train_backward_h_kernel<Prec::F16><<<num_sms * 4, 128, 0, s>>>(a);
   else train_backward_h_kernel<Prec::BF16><<<num_sms * 4, 128, 0, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  train_scatter_kernel<true><<<num_sms * 8, 256, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   WgradArgs w{};
   w.count = a.count;

@@ -66,8 +66,9 @@ struct SolveCfg {
   float tol2;           // tol^2
 };
 
+// per-lane counters (32-bit: a lane's share of one launch stays far below 2^32)
 struct SampleStats {
-  long long starts = 0, iters = 0, converged = 0, roots = 0, proposed = 0, fallbacks = 0;
+  unsigned starts = 0, iters = 0, converged = 0, roots = 0, proposed = 0, fallbacks = 0;
 };
 
 // ---------------------------------------------------------------------------

@@ -127,6 +127,29 @@ struct TrainArgs {
 cudaError_t launch_prop_bias(const PropDev& Q, int nb, const double* theta_all, int n_poses, float* b1p,
                              cudaStream_t s);
 
+// Opt a kernel into `smem` bytes of dynamic shared memory and ask for the
+// smallest shared-memory carveout that still fits as many blocks per SM as its
+// registers allow, so that the rest of the SM's unified memory serves as L1
+// (the correspondence search gathers the blended grid through L1).
+template <typename Kern>
+cudaError_t set_smem(Kern k, size_t smem, int threads) {
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  if ((e = cudaFuncGetAttributes(&fa, k)) != cudaSuccess) return e;
+  int dev = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
+    return e;
+  const int regs = fa.numRegs > 0 ? fa.numRegs : 1;
+  int blocks = 65536 / (regs * threads);
+  blocks = blocks < 1 ? 1 : (blocks > 32 ? 32 : blocks);
+  const size_t need = (size_t)blocks * (smem + fa.sharedSizeBytes + 1024);  // + per-block reserve
+  int pct = (int)((100 * need + per_sm - 1) / per_sm);
+  pct = pct > 100 ? 100 : pct;
+  return cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+}
+
 constexpr float kInitialLossScale = 16384.f;  // 2^14
 
 cudaError_t launch_train(const TrainArgs& a, const CUtensorMap* map, int num_sms, cudaStream_t s);

@@ -163,16 +163,12 @@ cudaError_t launch_blend(int P, int V, int nb, const float* W, const float* N, f
 // ---------------------------------------------------------------------------
 
 template <Prec P>
-size_t posed_smem_bytes_p(int threads) {
-  return sizeof(float) * (mlp_smem_words(P, threads) + kMaxBones * 12) + sizeof(float4) * kMaxRoots * kNS * threads;
+size_t posed_smem_bytes_p(int threads, bool prop) {
+  return sizeof(float) * (mlp_smem_words(P, threads, prop) + kMaxBones * 12) +
+         sizeof(float4) * kMaxRoots * kNS * threads;
 }
 
-size_t posed_smem_bytes(int threads) { return posed_smem_bytes_p<Prec::F32>(threads); }
-
-template <typename Kern>
-static cudaError_t set_smem(Kern k, size_t smem) {
-  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
+size_t posed_smem_bytes(int threads) { return posed_smem_bytes_p<Prec::F32>(threads, false); }
 
 // ---------------------------------------------------------------------------
 // Occupancy grid (Sec. 3.3, inference mode)
@@ -224,8 +220,8 @@ static cudaError_t launch_occ_density_p(const PosedArgs& a, const BoxDev& box, f
                                         unsigned long long* stats, cudaStream_t s) {
   const int n = box.R * box.R * box.R;
   const int blocks = (n + 256 * kNS - 1) / (256 * kNS);
-  const size_t smem = posed_smem_bytes_p<P>(256);
-  cudaError_t e = set_smem(occ_density_kernel<P>, smem);
+  const size_t smem = posed_smem_bytes_p<P>(256, a.search != 0);
+  cudaError_t e = set_smem(occ_density_kernel<P>, smem, 256);
   if (e != cudaSuccess) return e;
   occ_density_kernel<P><<<blocks, 256, smem, s>>>(a, box, sigma, stats);
   return cudaGetLastError();
@@ -321,8 +317,8 @@ __global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS)
 template <Prec P>
 static cudaError_t launch_query_posed_p(const PosedArgs& a, int n, const float* x, float* sigma, float* rgb,
                                         float* xc, int* start, cudaStream_t s) {
-  const size_t smem = posed_smem_bytes_p<P>(256);
-  cudaError_t e = set_smem(query_posed_kernel<P>, smem);
+  const size_t smem = posed_smem_bytes_p<P>(256, a.search != 0);
+  cudaError_t e = set_smem(query_posed_kernel<P>, smem, 256);
   if (e != cudaSuccess) return e;
   query_posed_kernel<P><<<(n + 256 * kNS - 1) / (256 * kNS), 256, smem, s>>>(a, n, x, sigma, rgb, xc, start);
   return cudaGetLastError();
@@ -364,8 +360,8 @@ __global__ void __launch_bounds__(256) query_canonical_kernel(const PosedArgs a,
 template <Prec P>
 static cudaError_t launch_query_canonical_p(const PosedArgs& a, int n, const float* x, float* sigma, float* rgb,
                                             cudaStream_t s) {
-  const size_t smem = posed_smem_bytes_p<P>(256);
-  cudaError_t e = set_smem(query_canonical_kernel<P>, smem);
+  const size_t smem = posed_smem_bytes_p<P>(256, a.search != 0);
+  cudaError_t e = set_smem(query_canonical_kernel<P>, smem, 256);
   if (e != cudaSuccess) return e;
   query_canonical_kernel<P><<<(n + 255) / 256, 256, smem, s>>>(a, n, x, sigma, rgb);
   return cudaGetLastError();
@@ -397,12 +393,12 @@ cudaError_t launch_query_canonical(const PosedArgs& a, int n, const float* x, fl
 // ---------------------------------------------------------------------------
 
 template <Prec P>
-size_t render_smem_bytes_p(int K) {
-  return posed_smem_bytes_p<P>(kRenderThreads) + sizeof(float4) * (2 * kRenderThreads + K * kRenderThreads) +
-         sizeof(int) * (2 * K * kRenderThreads);
+size_t render_smem_bytes_p(int K, bool prop) {
+  return posed_smem_bytes_p<P>(kRenderThreads, prop) + sizeof(float4) * (2 * kRenderThreads + K * kRenderThreads) +
+         (sizeof(uint8_t) + sizeof(uint16_t)) * K * kRenderThreads;
 }
 
-size_t render_smem_bytes(int K) { return render_smem_bytes_p<Prec::F32>(K); }
+size_t render_smem_bytes(int K) { return render_smem_bytes_p<Prec::F32>(K, false); }
 
 __device__ __forceinline__ void tile_pixel(int id, int tiles_x, int W, int H, int& u, int& v, bool& valid) {
   const int tile = id / (kTile * kTile), i = id % (kTile * kTile);
@@ -411,7 +407,7 @@ __device__ __forceinline__ void tile_pixel(int id, int tiles_x, int W, int H, in
   valid = u < W && v < H;
 }
 
-template <int K, Prec P>
+template <int K, Prec P, bool kProp>
 __global__ void __launch_bounds__(kRenderThreads, IA_RENDER_MIN_BLOCKS) render_kernel(const RenderArgs a) {
   extern __shared__ float4 smem4[];
   PosedSmem sm = stage_posed<P>(stage_of(a.P), smem4);
@@ -421,8 +417,9 @@ __global__ void __launch_bounds__(kRenderThreads, IA_RENDER_MIN_BLOCKS) render_k
   float4* ray_o = after_roots + warp * 32;                             // (o.xyz, delta)
   float4* ray_d = ray_o + kRenderThreads;                              // (d.xyz, t_near)
   float4* s_res = after_roots + 2 * kRenderThreads + warp * 32 * K;    // (sigma, r, g, b)
-  int* s_ray = reinterpret_cast<int*>(after_roots + (2 + K) * kRenderThreads) + warp * 32 * K;
-  int* s_slot = s_ray + K * kRenderThreads;
+  uint8_t* const idx_area = reinterpret_cast<uint8_t*>(after_roots + (2 + K) * kRenderThreads);
+  uint16_t* s_slot = reinterpret_cast<uint16_t*>(idx_area) + warp * 32 * K;              // [K * threads]
+  uint8_t* s_ray = idx_area + sizeof(uint16_t) * K * kRenderThreads + warp * 32 * K;     // [K * threads]
   __shared__ float sB0inv[12];
   if (tid < 12) sB0inv[tid] = a.B0inv[tid];
   __syncthreads();
@@ -435,7 +432,7 @@ __global__ void __launch_bounds__(kRenderThreads, IA_RENDER_MIN_BLOCKS) render_k
   int pix = 0, cursor = 0;
   float depth = 0.f;  // optical depth sum sigma_i delta
   float cr = 0.f, cg = 0.f, cb = 0.f;
-  long long n_rays = 0, n_hit = 0, n_marched = 0, n_occ = 0, n_early = 0;
+  unsigned n_rays = 0, n_hit = 0, n_marched = 0, n_occ = 0, n_early = 0;
   SampleStats st;
 
   while (true) {
@@ -516,8 +513,8 @@ __global__ void __launch_bounds__(kRenderThreads, IA_RENDER_MIN_BLOCKS) render_k
 #pragma unroll
     for (int j = 0; j < K; ++j)
       if (j < nfound) {
-        s_ray[offset + j] = lane;
-        s_slot[offset + j] = slots[j];
+        s_ray[offset + j] = (uint8_t)lane;
+        s_slot[offset + j] = (uint16_t)slots[j];  // n_slots <= 1024
       }
     n_occ += nfound;
     __syncwarp();
@@ -543,7 +540,7 @@ __global__ void __launch_bounds__(kRenderThreads, IA_RENDER_MIN_BLOCKS) render_k
         Ns[q] = sm.sNinv;
       }
       posed_field_warp_n<kNS, P>(a.P.S, Ms, a.P.F, a.P.cfg, Ns, sm.fs, sm.roots, act, xn, r, st, a.P.prop,
-                                 a.P.search != 0);
+                                 kProp);  // the proposal code is compiled only into kProp variants
 #pragma unroll
       for (int q = 0; q < kNS; ++q) {
         const int sidx = base + q * 32 + lane;
@@ -588,29 +585,39 @@ __global__ void __launch_bounds__(kRenderThreads, IA_RENDER_MIN_BLOCKS) render_k
   }
 }
 
-template <int K, Prec P>
+template <int K, Prec P, bool kProp>
 static cudaError_t launch_render_k(const RenderArgs& a, int num_sms, cudaStream_t s) {
-  const size_t smem = render_smem_bytes_p<P>(K);
-  cudaError_t e = set_smem(render_kernel<K, P>, smem);
+  const size_t smem = render_smem_bytes_p<P>(K, kProp);
+  cudaError_t e = set_smem(render_kernel<K, P, kProp>, smem, kRenderThreads);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel<K, P>, kRenderThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel<K, P, kProp>, kRenderThreads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   const int want = (a.n_ray_ids + kRenderThreads - 1) / kRenderThreads;
   int grid = num_sms * per_sm;
   if (grid > want) grid = want;
   if (grid < 1) grid = 1;
-  render_kernel<K, P><<<grid, kRenderThreads, smem, s>>>(a);
+  render_kernel<K, P, kProp><<<grid, kRenderThreads, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <Prec P, bool kProp>
+static cudaError_t launch_render_pp(const RenderArgs& a, int num_sms, cudaStream_t s) {
+  // with early termination, few samples per ray per round bound the work done
+  // past the stopping sample; without it, larger rounds amortise the scans
+  if (a.early_T > 0.f) return launch_render_k<2, P, kProp>(a, num_sms, s);
+  return launch_render_k<8, P, kProp>(a, num_sms, s);
 }
 
 template <Prec P>
 static cudaError_t launch_render_p(const RenderArgs& a, int num_sms, cudaStream_t s) {
-  // with early termination, few samples per ray per round bound the work done
-  // past the stopping sample; without it, larger rounds amortise the scans
-  if (a.early_T > 0.f) return launch_render_k<2, P>(a, num_sms, s);
-  return launch_render_k<8, P>(a, num_sms, s);
+  if constexpr (P == Prec::F32) {
+    return launch_render_pp<P, false>(a, num_sms, s);  // the proposal search needs fp16 / bf16
+  } else {
+    if (a.P.search) return launch_render_pp<P, true>(a, num_sms, s);
+    return launch_render_pp<P, false>(a, num_sms, s);
+  }
 }
 
 cudaError_t launch_render(const RenderArgs& a, int num_sms, cudaStream_t s) {

@@ -178,7 +178,8 @@ __device__ __forceinline__ void posed_field_warp_n(const SkinDev& S, const float
         const float u2 = h[6] * dr.x + h[7] * dr.y + h[8] * dr.z;
         const float den = d.x * u0 + d.y * u1 + d.z * u2;
         if (fabsf(den) > 1e-12f) {
-          const float a0 = (d.x - u0) / den, a1 = (d.y - u1) / den, a2 = (d.z - u2) / den;
+          const float rden = 1.f / den;  // one reciprocal for the three quotients
+          const float a0 = (d.x - u0) * rden, a1 = (d.y - u1) * rden, a2 = (d.z - u2) * rden;
           const float b0 = d.x * h[0] + d.y * h[3] + d.z * h[6];
           const float b1 = d.x * h[1] + d.y * h[4] + d.z * h[7];
           const float b2 = d.x * h[2] + d.y * h[5] + d.z * h[8];
@@ -283,7 +284,8 @@ struct PosedStage {
   const float* mlp;      // packed fp32 MLP (global)
   int n_in;
   const __half2* table_h;
-  int search;            // stage the proposal network too
+  int search;            // stage the proposal network too (the host sizes the
+                         // shared memory with the same flag: mlp_smem_words)
   PropDev prop;
   const double* theta;   // pose axis-angles (proposal input)
   const float* Ninv;     // [nb][12]
@@ -292,9 +294,13 @@ struct PosedStage {
 
 constexpr int kMlpPad = (kMlpSmemFloats + 3) / 4 * 4;
 
-__host__ __device__ constexpr int mlp_smem_words(Prec P, int threads) {
+// 32-bit words of the MLP area; the proposal's weights and its larger per-warp
+// staging are reserved only when the proposal is staged (prop), so that kernels
+// without it leave more of the SM's unified memory to L1
+__host__ __device__ constexpr int mlp_smem_words(Prec P, int threads, bool prop) {
   return P == Prec::F32 ? kMlpPad
-                        : ((kMlpHWords + 3) / 4 * 4 + (kPropWords + 3) / 4 * 4 + (threads / 32) * kStageWords);
+                        : ((kMlpHWords + 3) / 4 * 4 + (prop ? (kPropWords + 3) / 4 * 4 : 0) +
+                           (threads / 32) * (prop ? kStageWords : kWarpXWords));
 }
 
 struct PosedSmem {
@@ -321,12 +327,13 @@ __device__ __forceinline__ PosedSmem stage_posed(const PosedStage& a, float4* sm
     uint32_t* pw = w + (kMlpHWords + 3) / 4 * 4;
     p.fs.sw = nullptr;
     p.fs.swh = w;
-    p.fs.pw = pw;
-    p.fs.xstage = pw + (kPropWords + 3) / 4 * 4 + (threadIdx.x >> 5) * kStageWords;
+    p.fs.pw = a.search ? pw : nullptr;
+    p.fs.xstage = a.search ? pw + (kPropWords + 3) / 4 * 4 + (threadIdx.x >> 5) * kStageWords
+                           : pw + (threadIdx.x >> 5) * kWarpXWords;
     stage_mlp_h<P>(a.mlp, a.n_in, w);
     if (a.search) stage_prop_h<P>(a.prop, a.nb, a.theta, pw);
   }
-  p.sNinv = base + mlp_smem_words(P, blockDim.x);
+  p.sNinv = base + mlp_smem_words(P, blockDim.x, a.search != 0);
   p.roots = reinterpret_cast<float4*>(p.sNinv + kMaxBones * 12);
   for (int t = threadIdx.x; t < a.nb * 12; t += blockDim.x) p.sNinv[t] = a.Ninv[t];
   __syncthreads();

@@ -108,14 +108,14 @@ __global__ void train_emit_kernel(const TrainArgs a) {
   });
 }
 
-template <Prec P>
+template <Prec P, bool kProp>
 __global__ void __launch_bounds__(256) train_sample_kernel(const TrainArgs a) {
   extern __shared__ float4 smem4[];
   PosedStage ps;
   ps.mlp = a.P.mlp;
   ps.n_in = a.P.n_in;
   ps.table_h = a.P.table_h;
-  ps.search = a.P.search;  // proposal: layer-1 bias per lane from P.prop.b1p
+  ps.search = kProp ? 1 : 0;  // proposal: layer-1 bias per lane from P.prop.b1p
   ps.prop = a.P.prop;
   ps.theta = nullptr;
   ps.Ninv = a.P.Ninv;
@@ -144,8 +144,8 @@ __global__ void __launch_bounds__(256) train_sample_kernel(const TrainArgs a) {
       Ms[q] = a.P.S.M + (size_t)pose * a.V * 3;
       Ns[q] = a.P.Ninv + (size_t)pose * a.P.cfg.nb * 12;
     }
-    posed_field_warp_n<kNS, P>(a.P.S, Ms, a.P.F, a.P.cfg, Ns, sm.fs, sm.roots, act, xn, o, st, a.P.prop,
-                               a.P.search != 0, poses);
+    posed_field_warp_n<kNS, P>(a.P.S, Ms, a.P.F, a.P.cfg, Ns, sm.fs, sm.roots, act, xn, o, st, a.P.prop, kProp,
+                               poses);
 #pragma unroll
     for (int q = 0; q < kNS; ++q) {
       const int s = base + q * 32 + lane;
@@ -164,8 +164,8 @@ __global__ void __launch_bounds__(256) train_sample_kernel(const TrainArgs a) {
 }
 
 template <Prec P>
-static size_t train_sample_smem() {
-  return sizeof(float) * (mlp_smem_words(P, 256) + kMaxBones * 12) + sizeof(float4) * kMaxRoots * kNS * 256;
+static size_t train_sample_smem(bool prop) {
+  return sizeof(float) * (mlp_smem_words(P, 256, prop) + kMaxBones * 12) + sizeof(float4) * kMaxRoots * kNS * 256;
 }
 
 // front-to-back compositing of one ray, the loss, and the reverse sweep
@@ -791,12 +791,13 @@ cudaError_t launch_train(const TrainArgs& a, const CUtensorMap* map, int num_sms
         cudaSuccess)
       return e;
   }
-  auto sample = P == Prec::F32 ? train_sample_kernel<Prec::F32>
-                : P == Prec::F16 ? train_sample_kernel<Prec::F16> : train_sample_kernel<Prec::BF16>;
-  const size_t smem = P == Prec::F32 ? train_sample_smem<Prec::F32>()
-                      : P == Prec::F16 ? train_sample_smem<Prec::F16>() : train_sample_smem<Prec::BF16>();
-  if ((e = cudaFuncSetAttribute(sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-    return e;
+  const bool prop = a.P.search != 0 && P != Prec::F32;
+  auto sample = P == Prec::F32   ? train_sample_kernel<Prec::F32, false>
+                : P == Prec::F16 ? (prop ? train_sample_kernel<Prec::F16, true> : train_sample_kernel<Prec::F16, false>)
+                                 : (prop ? train_sample_kernel<Prec::BF16, true> : train_sample_kernel<Prec::BF16, false>);
+  const size_t smem = P == Prec::F32   ? train_sample_smem<Prec::F32>(false)
+                      : P == Prec::F16 ? train_sample_smem<Prec::F16>(prop) : train_sample_smem<Prec::BF16>(prop);
+  if ((e = set_smem(sample, smem, 256)) != cudaSuccess) return e;
   sample<<<num_sms * 2, 256, smem, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   train_composite_kernel<<<rb, 128, 0, s>>>(a);

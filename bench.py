@@ -44,6 +44,13 @@ FLOP_START = 306       # x0 = N_k^-1 x', LBS value (8-corner trilinear blend of 
 FLOP_ITER = 320        # Broyden step: H r, LBS value, residual difference, rank-one update of H
 FLOP_ROOT = 620 + 960 + 12800 + 40  # Newton polish with the analytic Jacobian, hash encoding, MLP, activations
 FLOP_SAMPLE = 20       # alpha, transmittance, colour accumulation
+# DRAM bytes (read + write) of one render_kernel<2, fp32> launch on this workload,
+# from the ncu capture summarised in profiles/render_kernel_540x540_fp32.md; the
+# ncu-measured busiest unit of that launch is reported beside the roofline
+RENDER_DRAM_BYTES = 51.92e6 + 2.99e6
+RENDER_LIMITER = {"unit": "L1 (blended-grid gathers)", "l1tex_throughput_pct": 64.2, "issue_active_pct": 31.3,
+                  "fma_pipe_pct": 17.6, "l1_hit_pct": 91.0, "l2_hit_pct": 97.8,
+                  "source": "profiles/render_kernel_540x540_fp32.md"}
 
 
 def fp32_peak_tflops(sm_mhz: float) -> float:
@@ -420,9 +427,9 @@ def run_ours(args, rank, world, local_rank):
                     "gradients; fp16 with dynamic loss scaling, weight gradients on tcgen05"},
         "roofline": {"kernel": "render_kernel", "bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                     "traffic": None,
+                     "traffic": RENDER_DRAM_BYTES,
                      "peak_source": f"fp32 FMA: 148 SM x 128 lanes x 2 x {sm_mhz:.0f} MHz ({peak_kind} max clock)",
-                     "flop_per_frame": round(flop_render)},
+                     "flop_per_frame": round(flop_render), "limiter": RENDER_LIMITER},
         "e2e": {"value": round(1.0 / statistics.mean(e2e_s), 3), "unit": "frames/s",
                 "h2d_bytes_per_step": int(sc.n_bones * 3 * 8 + 3 * 8),
                 "d2h_bytes_per_step": int(W * H * 4 * 4)},

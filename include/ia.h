@@ -205,6 +205,11 @@ typedef struct ia_batch {
   const float *target;       /* [n][3] target colours */
 } ia_batch;
 
+/* Floats of the skinning-grid and bone-transform gradients of ia_train_step
+ * for the current skeleton and poses: skin_res^3 * n_bones and
+ * n_poses * n_bones * 12 (either pointer may be NULL). */
+ia_status ia_grad_sizes(const ia_ctx *ctx, int64_t *skin_floats, int64_t *bone_floats);
+
 /* Gradient buffers (device, caller-owned, overwritten by each step). */
 typedef struct ia_grads {
   float *table;   /* [entries][F], same layout as the hash table */

@@ -96,6 +96,7 @@ def lib():
             "ia_update_occupancy_static": [P, I, P, V],
             "ia_loss_scale": [P, C.POINTER(C.c_float), C.POINTER(C.c_int32), V],
             "ia_train_stats": [P, C.POINTER(RenderStats), V],
+            "ia_grad_sizes": [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
             "ia_proposal_init": [P, C.POINTER(ProposalConfig)],
             "ia_proposal_param_sizes": [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
             "ia_proposal_set_params": [P, P, P, V],
@@ -267,6 +268,13 @@ def ia_train_step(ctx, origin, direction, pose, target, loss, grads, occ_grid=IA
     g.table, g.mlp, g.skin, g.bones = (_ptr(grads[k]) for k in ("table", "mlp", "skin", "bones"))
     _check(lib().ia_train_step(ctx, C.byref(b), occ_grid, _ptr(loss), _ptr(rgb_out), C.byref(g),
                                _stream(stream)), ctx)
+
+
+def ia_grad_sizes(ctx):
+    """(skinning-grid floats, bone-transform floats) of the training step's gradients."""
+    a, b = C.c_int64(), C.c_int64()
+    _check(lib().ia_grad_sizes(ctx, C.byref(a), C.byref(b)), ctx)
+    return a.value, b.value
 
 
 def ia_train_stats(ctx, stream=None):

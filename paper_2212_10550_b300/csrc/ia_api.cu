@@ -773,6 +773,14 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
   return IA_OK;
 }
 
+ia_status ia_grad_sizes(const ia_ctx* c, int64_t* skin_floats, int64_t* bone_floats) {
+  if (!c) return fail(nullptr, IA_ERR_ARG, "null context");
+  if (c->nb == 0) return fail(const_cast<ia_ctx*>(c), IA_ERR_STATE, "ia_set_skeleton has not been called");
+  if (skin_floats) *skin_floats = (int64_t)c->Rw * c->Rw * c->Rw * c->nb;
+  if (bone_floats) *bone_floats = (int64_t)c->n_poses * c->nb * 12;
+  return IA_OK;
+}
+
 ia_status ia_train_stats(ia_ctx* c, ia_render_stats* stats, void* stream) {
   if (!c || !stats) return fail(c, IA_ERR_ARG, "null argument");
   read_stats(c, stats, (cudaStream_t)stream, c->d_tstats);

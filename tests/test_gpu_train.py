@@ -111,3 +111,34 @@ def test_train_step_bad_pose_index_is_an_empty_ray(ia):
     rays["pose"][:10] = 7  # only poses 0 and 1 exist
     _, _, rgb, _, _ = _run_gpu(ia, sc, table, mlp, poses, occ, rays)
     assert np.all(rgb[:10] == 0)
+
+
+def test_autograd_function_matches_the_step(ia):
+    """loss.backward() through the torch.autograd front gives the step's own
+    table and MLP gradients (scaled by the incoming gradient), and the loss of
+    the oracle."""
+    from paper_2212_10550_b300.autograd import train_loss
+    sc, table, mlp, om, poses, op, occ, rays, _ = _case("tiny", 2, 1500)
+    ctx = make_ctx(ia, torch, sc, table, mlp)
+    ia.ia_set_pose(ctx, np.stack([p[0] for p in poses]), np.stack([p[1] for p in poses]))
+    ia.ia_set_occupancy(ctx, occ)
+    dev = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in rays.items()}
+    t = torch.from_numpy(np.ascontiguousarray(table).reshape(-1)).cuda().requires_grad_()
+    m = torch.from_numpy(S.pack_mlp(mlp)).cuda().requires_grad_()
+    loss, rgb, g_skin, g_bones = train_loss(t, m, ctx, dev["origin"], dev["direction"], dev["pose"], dev["target"],
+                                            ia.IA_OCC_POSE)
+    (3.0 * loss).backward()
+    nt, nm = ia.ia_param_sizes(ctx)
+    g = dict(table=torch.zeros(nt, device="cuda"), mlp=torch.zeros(nm, device="cuda"),
+             skin=torch.zeros_like(g_skin), bones=torch.zeros_like(g_bones))
+    ref = torch.zeros(1, device="cuda")
+    ia.ia_train_step(ctx, dev["origin"], dev["direction"], dev["pose"], dev["target"], ref, g, occ_grid=ia.IA_OCC_POSE)
+    torch.cuda.synchronize()
+    ia.ia_destroy(ctx)
+    assert not rgb.requires_grad and not g_skin.requires_grad
+    assert abs(loss.item() - ref.item()) <= 1e-6 * ref.item()
+    for name, a, b in (("table", t.grad, g["table"]), ("mlp", m.grad, g["mlp"])):
+        torch.testing.assert_close(a, 3.0 * b, rtol=1e-4, atol=1e-6 * b.abs().max().item(), msg=name)
+    torch.testing.assert_close(g_skin, g["skin"], rtol=1e-4, atol=1e-6 * g["skin"].abs().max().item())
+    ref_loss = G.train(om, op, occ, rays["origin"], rays["direction"], rays["pose"], rays["target"], grad=False)[0]
+    assert abs(loss.item() - ref_loss) <= 1e-5 * ref_loss

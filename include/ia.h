@@ -159,7 +159,10 @@ ia_status ia_get_transforms(ia_ctx *ctx, int pose, float *N, float *Ninv, float 
  * centre norm_min + (c + 1/2) * (norm_max - norm_min) / R (fp32, fixed order),
  * then occupied = density > occ_tau, dilated by occ_dilate cells, packed so that
  * cell b = x + R (y + R z) is bit b % 32 of word b / 32.  IA_OCC_POSE replaces
- * the render grid; IA_OCC_UNION ORs the result into the training grid.
+ * the render grid; IA_OCC_UNION ORs the result into the training grid.  The
+ * cells take the plain search over every bone even when ia_set_search selected
+ * the proposal (most cells are empty space, where the proposal would fall back
+ * to that search anyway).
  *  sigma_out [R^3] fp32 device or NULL; bits_out [R^3 / 32] uint32 device or NULL. */
 ia_status ia_update_occupancy(ia_ctx *ctx, int pose, int mode, float *sigma_out,
                               uint32_t *bits_out, ia_render_stats *stats, void *stream);

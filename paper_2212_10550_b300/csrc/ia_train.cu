@@ -618,75 +618,210 @@ __device__ __forceinline__ float put(uint16_t* col, int64_t ld, int row, float v
   else return __bfloat162float(__ushort_as_bfloat16(b));
 }
 
+// Shared memory of the reduced-precision backward: the forward's MLP layout
+// (stage_mlp_h), the transposed weights the backward products need
+// (W2T[i][j] = W2[j][i], W1T[f][i] = W1[i][f], rows padded like the forward's),
+// W3 rounded to the operand type in fp32, then per warp: staged features and
+// outputs, the scaled output gradients, and a [64 channel][32 sample] buffer
+// that turns fragment-ordered values into coalesced rows of X.
+constexpr int kBwThreads = 256;
+constexpr int kBwOffW2T = (kMlpHWords + 3) / 4 * 4;
+constexpr int kBwOffW1T = kBwOffW2T + kWidth * kW2Stride;
+constexpr int kBwOffW3F = kBwOffW1T + kIn * kW2Stride;
+constexpr int kBwShared = kBwOffW3F + 4 * kWidth;
+constexpr int kTrStride = 20;  // words per channel row of the transposition buffer (32 samples + pad)
+constexpr int kBwWarpWords = kWarpXWords + 32 * 4 + kWidth * kTrStride;
+constexpr size_t kBwSmemBytes = sizeof(uint32_t) * (kBwShared + (kBwThreads / 32) * kBwWarpWords);
+
 template <Prec P>
-__global__ void __launch_bounds__(128) train_backward_h_kernel(const TrainArgs a) {
-  __shared__ __align__(16) float sw[kMlpPadT];
-  stage_mlp(a.P.mlp, a.P.n_in, sw);
-  __syncthreads();
-  for (int t = threadIdx.x; t < kMlpPadT; t += blockDim.x) {
-    const bool bias = (t >= kOffB1 && t < kOffW2) || (t >= kOffB2 && t < kOffW3T) || t >= kOffB3;
-    if (!bias) sw[t] = HalfOf<P>::round(sw[t]);
+__device__ __forceinline__ void stage_backward_h(const float* __restrict__ g, int n_in, uint32_t* sw) {
+  stage_mlp_h<P>(g, n_in, sw);
+  const float* W2 = g + kWidth * n_in + kWidth;
+  const float* W3 = W2 + kWidth * kWidth + kWidth;
+  for (int t = threadIdx.x; t < kBwShared - kBwOffW2T; t += blockDim.x) {
+    if (t < kWidth * kW2Stride) {  // W2T
+      const int i = t / kW2Stride, c = t % kW2Stride;
+      sw[kBwOffW2T + t] = c < kWidth / 2 ? HalfOf<P>::pack(W2[(2 * c) * kWidth + i], W2[(2 * c + 1) * kWidth + i]) : 0u;
+    } else if (t < (kWidth + kIn) * kW2Stride) {  // W1T (feature rows past n_in are zero)
+      const int q = t - kWidth * kW2Stride, f = q / kW2Stride, c = q % kW2Stride;
+      sw[kBwOffW2T + t] =
+          (c < kWidth / 2 && f < n_in) ? HalfOf<P>::pack(g[(2 * c) * n_in + f], g[(2 * c + 1) * n_in + f]) : 0u;
+    } else {  // W3 [4][64], rounded as the forward's operand
+      const int q = t - (kWidth + kIn) * kW2Stride;
+      reinterpret_cast<float*>(sw)[kBwOffW2T + t] = HalfOf<P>::round(W3[q]);
+    }
   }
+}
+
+// fragment (rows r0 / r0 + 8, columns 8 nt + 2t, + 1) -> transposition buffer
+__device__ __forceinline__ void tr_put(uint16_t* tr16, int ch, int r, uint16_t v) { tr16[ch * 2 * kTrStride + r] = v; }
+
+// transposition buffer (64 channels x 32 samples) -> rows row0 .. row0 + 63 of X
+// at columns s0 .. s0 + 31 (two samples per 32-bit store, 64 B per row)
+__device__ __forceinline__ void tr_flush(const uint32_t* tr32, uint16_t* X, int64_t ld, int row0, int s0, int lane) {
+  __syncwarp();
+  uint32_t* X32 = reinterpret_cast<uint32_t*>(X);
+#pragma unroll 4
+  for (int c2 = 0; c2 < kWidth / 2; ++c2) {
+    const int ch = 2 * c2 + (lane >> 4);
+    X32[(((size_t)(row0 + ch)) * ld + s0) / 2 + (lane & 15)] = tr32[ch * kTrStride + (lane & 15)];
+  }
+  __syncwarp();
+}
+
+template <Prec P>
+__device__ __forceinline__ float rnd_bits(float v, uint16_t& b) {
+  b = HalfOf<P>::bits(v);
+  if constexpr (P == Prec::F16) return __half2float(__ushort_as_half(b));
+  else return __bfloat162float(__ushort_as_bfloat16(b));
+}
+
+// One warp, 32 samples (one per lane): the forward recomputed with tensor-core
+// MMAs (m16n8k16, fp32 accumulation, operands as the forward rounded them), the
+// backward as two more MMA chains: dH1 = (dH2 W2) o [h1 > 0], dF = dH1 W1, with
+// dH2 = (dO W3) o [h2 > 0] done in fp32 (K = 4).  Operands and gradients are
+// written channel-major into X for the weight-gradient GEMM, dL/dfeatures
+// (unscaled, fp32) into s_dfeat for the scatter kernel.
+template <Prec P>
+__global__ void __launch_bounds__(kBwThreads) train_backward_h_kernel(const TrainArgs a) {
+  extern __shared__ uint32_t bw_smem[];
+  uint32_t* sw = bw_smem;
+  stage_backward_h<P>(a.P.mlp, a.P.n_in, sw);
   __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  uint32_t* wbase = bw_smem + kBwShared + warp * kBwWarpWords;
+  uint32_t* Xs = wbase;                                                   // [32][kXStride] features
+  float* Os = reinterpret_cast<float*>(wbase + 32 * kXStride);            // [32][4] outputs
+  float* Ds = reinterpret_cast<float*>(wbase + kWarpXWords);              // [32][4] scaled dO (rounded)
+  uint32_t* tr32 = wbase + kWarpXWords + 32 * 4;                          // [64][kTrStride]
+  uint16_t* tr16 = reinterpret_cast<uint16_t*>(tr32);
+  const float* bias = reinterpret_cast<const float*>(sw + kOffHB);
+  const float* W3f = reinterpret_cast<const float*>(sw + kBwOffW3F);
+  const uint32_t* W2T = sw + kBwOffW2T;
+  const uint32_t* W1T = sw + kBwOffW1T;
+
   const int n = *a.count;
   const int n_pad = (n + kWgChunk - 1) / kWgChunk * kWgChunk;
   const float S = *a.scale, inv_S = 1.f / S;
   const int64_t ld = a.ld;
-  const FieldDev& F = a.P.F;
   bool overflow = false;
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_pad; s += gridDim.x * blockDim.x) {
-    uint16_t* col = a.X + s;
-    const float4 xs4 = s < n ? a.s_x[s] : make_float4(0.f, 0.f, 0.f, 0.f);
-    if (!(xs4.w > 0.f)) {  // no root, or padding up to the chunk: zero columns
-      for (int r = 0; r <= kXOne; ++r) col[(size_t)r * ld] = 0;
-      for (int r = kXH2; r <= kXOne2; ++r) col[(size_t)r * ld] = 0;
-      for (int r = kXdO; r < kXdO + 4; ++r) col[(size_t)r * ld] = 0;
-      continue;
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  for (int s0 = (blockIdx.x * (blockDim.x >> 5) + warp) * 32; s0 < n_pad; s0 += warps * 32) {
+    const int s = s0 + lane;
+    // ---- this lane's sample: features (zero without a root), compositing gradient
+    bool valid = false;
+    float3 xs = make_float3(0.f, 0.f, 0.f);
+    float4 gr = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (s < n) {
+      const float4 x4 = a.s_x[s];
+      valid = x4.w > 0.f;
+      xs = make_float3(x4.x, x4.y, x4.z);
+      if (valid) gr = a.s_grad[s];
     }
-    const float3 xs = make_float3(xs4.x, xs4.y, xs4.z);
-    const float4 gr = a.s_grad[s];
-    // ---- forward recompute with the forward's operands
-    float feat[kIn];
-    encode_h(F, a.P.table_h, xs, feat);
-#pragma unroll
-    for (int i = 0; i < kIn; ++i) feat[i] = put<P>(col, ld, kXF + i, feat[i]);
-    col[(size_t)kXOne * ld] = HalfOf<P>::bits(1.f);
-    col[(size_t)kXOne2 * ld] = HalfOf<P>::bits(1.f);
-    float h1[kWidth];
-    uint64_t m1 = 0;
-#pragma unroll
-    for (int j = 0; j < kWidth; ++j) {
-      float acc = sw[kOffB1 + j];
-      const float4* row = reinterpret_cast<const float4*>(sw + kOffW1 + j * kIn);
-#pragma unroll
-      for (int i = 0; i < kIn / 4; ++i) {
-        const float4 w = row[i];
-        acc = fmaf(w.x, feat[4 * i], fmaf(w.y, feat[4 * i + 1], fmaf(w.z, feat[4 * i + 2], fmaf(w.w, feat[4 * i + 3], acc))));
-      }
-      if (acc > 0.f) m1 |= 1ull << j;
-      h1[j] = put<P>(col, ld, kXH1 + j, fmaxf(acc, 0.f));
-    }
-    float o0 = sw[kOffB3], o1 = sw[kOffB3 + 1], o2 = sw[kOffB3 + 2], o3 = sw[kOffB3 + 3];
-    uint64_t m2 = 0;
-    for (int j = 0; j < kWidth; ++j) {
-      float acc = sw[kOffB2 + j];
-      const float4* row = reinterpret_cast<const float4*>(sw + kOffW2 + j * kWidth);
-#pragma unroll
-      for (int i = 0; i < kWidth / 4; ++i) {
-        const float4 w = row[i];
-        acc = fmaf(w.x, h1[4 * i], fmaf(w.y, h1[4 * i + 1], fmaf(w.z, h1[4 * i + 2], fmaf(w.w, h1[4 * i + 3], acc))));
-      }
-      if (acc > 0.f) m2 |= 1ull << j;
-      const float h = put<P>(col, ld, kXH2 + j, fmaxf(acc, 0.f));
-      const float4 w3 = reinterpret_cast<const float4*>(sw + kOffW3T)[j];
-      o0 = fmaf(w3.x, h, o0);
-      o1 = fmaf(w3.y, h, o1);
-      o2 = fmaf(w3.z, h, o2);
-      o3 = fmaf(w3.w, h, o3);
-    }
-    // ---- output activations, scaled output gradient
-    float dO[4];
     {
+      float feat[kIn];
+      if (valid) encode_h(a.P.F, a.P.table_h, xs, feat);
+      uint16_t* col = a.X + s;
+#pragma unroll
+      for (int c = 0; c < kIn / 2; ++c) {
+        uint16_t b0 = 0, b1 = 0;
+        if (valid) {
+          rnd_bits<P>(feat[2 * c], b0);
+          rnd_bits<P>(feat[2 * c + 1], b1);
+        }
+        Xs[lane * kXStride + c] = (uint32_t)b0 | ((uint32_t)b1 << 16);
+        col[(size_t)(kXF + 2 * c) * ld] = b0;
+        col[(size_t)(kXF + 2 * c + 1) * ld] = b1;
+      }
+      const uint16_t one = HalfOf<P>::bits(1.f);
+      col[(size_t)kXOne * ld] = one;
+      col[(size_t)kXOne2 * ld] = one;
+    }
+    __syncwarp();
+    // ---- layer 1: h1 = relu(W1 f + b1); masks and rounded A fragments of layer 2
+    uint32_t A2[2][4][4], m1[2];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      const int r0 = 16 * mt + g, r1 = r0 + 8;
+      uint32_t A[2][4];
+#pragma unroll
+      for (int kt = 0; kt < 2; ++kt) {
+        A[kt][0] = Xs[r0 * kXStride + 8 * kt + t];
+        A[kt][1] = Xs[r1 * kXStride + 8 * kt + t];
+        A[kt][2] = Xs[r0 * kXStride + 8 * kt + 4 + t];
+        A[kt][3] = Xs[r1 * kXStride + 8 * kt + 4 + t];
+      }
+      m1[mt] = 0;
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        const float b0 = bias[8 * nt + 2 * t], b1 = bias[8 * nt + 2 * t + 1];
+        float acc[4] = {b0, b1, b0, b1};
+        const uint32_t* Wr = sw + kOffHW1 + (8 * nt + g) * kW1Stride;
+#pragma unroll
+        for (int kt = 0; kt < 2; ++kt) mma16816<P>(acc, A[kt], Wr[8 * kt + t], Wr[8 * kt + 4 + t]);
+        uint16_t hb[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (acc[q] > 0.f) m1[mt] |= 1u << (4 * nt + q);
+          rnd_bits<P>(fmaxf(acc[q], 0.f), hb[q]);
+        }
+        const int ch = 8 * nt + 2 * t;
+        tr_put(tr16, ch, r0, hb[0]);
+        tr_put(tr16, ch + 1, r0, hb[1]);
+        tr_put(tr16, ch, r1, hb[2]);
+        tr_put(tr16, ch + 1, r1, hb[3]);
+        // accumulator (cols 8nt..8nt+7) -> A fragment of k-tile nt / 2
+        const uint32_t lo = (uint32_t)hb[0] | ((uint32_t)hb[1] << 16), hi = (uint32_t)hb[2] | ((uint32_t)hb[3] << 16);
+        A2[mt][nt >> 1][(nt & 1) * 2] = lo;
+        A2[mt][nt >> 1][(nt & 1) * 2 + 1] = hi;
+      }
+    }
+    tr_flush(tr32, a.X, ld, kXH1, s0, lane);
+    // ---- layer 2: h2 = relu(W2 h1 + b2); layer 3: o = W3 h2 + b3
+    uint32_t m2[2];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      const int r0 = 16 * mt + g, r1 = r0 + 8;
+      uint32_t A3[4][4];
+      m2[mt] = 0;
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        const float b0 = bias[kWidth + 8 * nt + 2 * t], b1 = bias[kWidth + 8 * nt + 2 * t + 1];
+        float acc[4] = {b0, b1, b0, b1};
+        const uint32_t* Wr = sw + kOffHW2 + (8 * nt + g) * kW2Stride;
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt) mma16816<P>(acc, A2[mt][kt], Wr[8 * kt + t], Wr[8 * kt + 4 + t]);
+        uint16_t hb[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (acc[q] > 0.f) m2[mt] |= 1u << (4 * nt + q);
+          rnd_bits<P>(fmaxf(acc[q], 0.f), hb[q]);
+        }
+        const int ch = 8 * nt + 2 * t;
+        tr_put(tr16, ch, r0, hb[0]);
+        tr_put(tr16, ch + 1, r0, hb[1]);
+        tr_put(tr16, ch, r1, hb[2]);
+        tr_put(tr16, ch + 1, r1, hb[3]);
+        A3[nt >> 1][(nt & 1) * 2] = (uint32_t)hb[0] | ((uint32_t)hb[1] << 16);
+        A3[nt >> 1][(nt & 1) * 2 + 1] = (uint32_t)hb[2] | ((uint32_t)hb[3] << 16);
+      }
+      const float b0 = bias[2 * kWidth + 2 * t], b1 = bias[2 * kWidth + 2 * t + 1];
+      float o[4] = {b0, b1, b0, b1};
+      const uint32_t* Wr = sw + kOffHW3 + g * kW2Stride;
+#pragma unroll
+      for (int kt = 0; kt < 4; ++kt) mma16816<P>(o, A3[kt], Wr[8 * kt + t], Wr[8 * kt + 4 + t]);
+      if (t < 2) {
+        Os[r0 * 4 + 2 * t] = o[0];
+        Os[r0 * 4 + 2 * t + 1] = o[1];
+        Os[r1 * 4 + 2 * t] = o[2];
+        Os[r1 * 4 + 2 * t + 1] = o[3];
+      }
+    }
+    tr_flush(tr32, a.X, ld, kXH2, s0, lane);  // (also orders the Os writes before the reads below)
+    // ---- scaled output gradient of this lane's sample (zero without a root)
+    {
+      const float o0 = Os[lane * 4], o1 = Os[lane * 4 + 1], o2 = Os[lane * 4 + 2], o3 = Os[lane * 4 + 3];
+      float dO[4];
       const float sig = expf(fminf(fmaxf(o0, -15.f), 15.f));
       dO[0] = (o0 > -15.f && o0 < 15.f) ? gr.x * sig : 0.f;
       const float oc[3] = {o1, o2, o3}, gc[3] = {gr.y, gr.z, gr.w};
@@ -695,61 +830,91 @@ __global__ void __launch_bounds__(128) train_backward_h_kernel(const TrainArgs a
         const float sg = 1.f / (1.f + expf(-oc[c]));
         dO[1 + c] = gc[c] * sg * (1.f - sg);
       }
-    }
+      uint16_t* col = a.X + s;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float v = dO[q] * S;
-      overflow |= !(fabsf(v) <= HalfOf<P>::kMax);
-      dO[q] = put<P>(col, ld, kXdO + q, v);
-    }
-    // ---- MLP backward (scaled)
-    float dh2[kWidth];
-#pragma unroll
-    for (int j = 0; j < kWidth; ++j) {
-      const float4 w3 = reinterpret_cast<const float4*>(sw + kOffW3T)[j];
-      const float v = ((m2 >> j) & 1ull) ? w3.x * dO[0] + w3.y * dO[1] + w3.z * dO[2] + w3.w * dO[3] : 0.f;
-      overflow |= !(fabsf(v) <= HalfOf<P>::kMax);
-      dh2[j] = put<P>(col, ld, kXdH2 + j, v);
-    }
-    float dh1[kWidth];
-#pragma unroll
-    for (int i = 0; i < kWidth; ++i) dh1[i] = 0.f;
-#pragma unroll
-    for (int j = 0; j < kWidth; ++j) {
-      const float4* row = reinterpret_cast<const float4*>(sw + kOffW2 + j * kWidth);
-      const float d = dh2[j];
-#pragma unroll
-      for (int i = 0; i < kWidth / 4; ++i) {
-        const float4 w = row[i];
-        dh1[4 * i] = fmaf(w.x, d, dh1[4 * i]);
-        dh1[4 * i + 1] = fmaf(w.y, d, dh1[4 * i + 1]);
-        dh1[4 * i + 2] = fmaf(w.z, d, dh1[4 * i + 2]);
-        dh1[4 * i + 3] = fmaf(w.w, d, dh1[4 * i + 3]);
+      for (int q = 0; q < 4; ++q) {
+        const float v = dO[q] * S;
+        overflow |= !(fabsf(v) <= HalfOf<P>::kMax);
+        uint16_t b;
+        Ds[lane * 4 + q] = rnd_bits<P>(v, b);
+        col[(size_t)(kXdO + q) * ld] = b;
       }
     }
-    float dfeat[kIn];
+    __syncwarp();
+    // ---- dH2 = (dO W3) o [h2 > 0], fp32 (K = 4), rounded: A fragments of the next product
+    uint32_t B2[2][4][4];
 #pragma unroll
-    for (int i = 0; i < kIn; ++i) dfeat[i] = 0.f;
+    for (int mt = 0; mt < 2; ++mt) {
+      const int r0 = 16 * mt + g, r1 = r0 + 8;
+      const float4 d0 = reinterpret_cast<const float4*>(Ds)[r0], d1 = reinterpret_cast<const float4*>(Ds)[r1];
 #pragma unroll
-    for (int j = 0; j < kWidth; ++j) {
-      const float v = ((m1 >> j) & 1ull) ? dh1[j] : 0.f;
-      overflow |= !(fabsf(v) <= HalfOf<P>::kMax);
-      const float d = put<P>(col, ld, kXdH1 + j, v);
-      const float4* row = reinterpret_cast<const float4*>(sw + kOffW1 + j * kIn);
+      for (int nt = 0; nt < 8; ++nt) {
+        uint16_t hb[4];
 #pragma unroll
-      for (int i = 0; i < kIn / 4; ++i) {
-        const float4 w = row[i];
-        dfeat[4 * i] = fmaf(w.x, d, dfeat[4 * i]);
-        dfeat[4 * i + 1] = fmaf(w.y, d, dfeat[4 * i + 1]);
-        dfeat[4 * i + 2] = fmaf(w.z, d, dfeat[4 * i + 2]);
-        dfeat[4 * i + 3] = fmaf(w.w, d, dfeat[4 * i + 3]);
+        for (int q = 0; q < 4; ++q) {
+          const int j = 8 * nt + 2 * t + (q & 1);
+          const float4 d = (q < 2) ? d0 : d1;
+          float v = W3f[j] * d.x + W3f[kWidth + j] * d.y + W3f[2 * kWidth + j] * d.z + W3f[3 * kWidth + j] * d.w;
+          v = ((m2[mt] >> (4 * nt + q)) & 1u) ? v : 0.f;
+          overflow |= !(fabsf(v) <= HalfOf<P>::kMax);
+          rnd_bits<P>(v, hb[q]);
+        }
+        const int ch = 8 * nt + 2 * t;
+        tr_put(tr16, ch, r0, hb[0]);
+        tr_put(tr16, ch + 1, r0, hb[1]);
+        tr_put(tr16, ch, r1, hb[2]);
+        tr_put(tr16, ch + 1, r1, hb[3]);
+        B2[mt][nt >> 1][(nt & 1) * 2] = (uint32_t)hb[0] | ((uint32_t)hb[1] << 16);
+        B2[mt][nt >> 1][(nt & 1) * 2 + 1] = (uint32_t)hb[2] | ((uint32_t)hb[3] << 16);
       }
     }
-    float4* dst = a.s_dfeat + (size_t)s * (kIn / 4);
+    tr_flush(tr32, a.X, ld, kXdH2, s0, lane);
+    // ---- dH1 = (dH2 W2) o [h1 > 0] on tensor cores, rounded
 #pragma unroll
-    for (int i = 0; i < kIn / 4; ++i)
-      dst[i] = make_float4(dfeat[4 * i] * inv_S, dfeat[4 * i + 1] * inv_S, dfeat[4 * i + 2] * inv_S,
-                           dfeat[4 * i + 3] * inv_S);
+    for (int mt = 0; mt < 2; ++mt) {
+      const int r0 = 16 * mt + g, r1 = r0 + 8;
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        const uint32_t* Wr = W2T + (8 * nt + g) * kW2Stride;
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt) mma16816<P>(acc, B2[mt][kt], Wr[8 * kt + t], Wr[8 * kt + 4 + t]);
+        uint16_t hb[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float v = ((m1[mt] >> (4 * nt + q)) & 1u) ? acc[q] : 0.f;
+          overflow |= !(fabsf(v) <= HalfOf<P>::kMax);
+          rnd_bits<P>(v, hb[q]);
+        }
+        const int ch = 8 * nt + 2 * t;
+        tr_put(tr16, ch, r0, hb[0]);
+        tr_put(tr16, ch + 1, r0, hb[1]);
+        tr_put(tr16, ch, r1, hb[2]);
+        tr_put(tr16, ch + 1, r1, hb[3]);
+        // reuse A2 for the dH1 fragments (layer 1's are no longer needed)
+        A2[mt][nt >> 1][(nt & 1) * 2] = (uint32_t)hb[0] | ((uint32_t)hb[1] << 16);
+        A2[mt][nt >> 1][(nt & 1) * 2 + 1] = (uint32_t)hb[2] | ((uint32_t)hb[3] << 16);
+      }
+    }
+    tr_flush(tr32, a.X, ld, kXdH1, s0, lane);
+    // ---- dF = dH1 W1 on tensor cores, unscaled to fp32
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      const int r0 = 16 * mt + g, r1 = r0 + 8;
+#pragma unroll
+      for (int nt = 0; nt < kIn / 8; ++nt) {
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        const uint32_t* Wr = W1T + (8 * nt + g) * kW2Stride;
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt) mma16816<P>(acc, A2[mt][kt], Wr[8 * kt + t], Wr[8 * kt + 4 + t]);
+        const int c = 8 * nt + 2 * t;
+        float* df = reinterpret_cast<float*>(a.s_dfeat);
+        if (s0 + r0 < n)
+          *reinterpret_cast<float2*>(df + (size_t)(s0 + r0) * kIn + c) = make_float2(acc[0] * inv_S, acc[1] * inv_S);
+        if (s0 + r1 < n)
+          *reinterpret_cast<float2*>(df + (size_t)(s0 + r1) * kIn + c) = make_float2(acc[2] * inv_S, acc[3] * inv_S);
+      }
+    }
   }
   if (overflow) atomicExch(a.overflow, 1);
 }
@@ -810,8 +975,13 @@ cudaError_t launch_train(const TrainArgs& a, const CUtensorMap* map, int num_sms
     mlp_grad_kernel<<<num_sms * 2, 256, 0, s>>>(a);
     return cudaGetLastError();
   }
-  if (P == Prec::F16) train_backward_h_kernel<Prec::F16><<<num_sms * 4, 128, 0, s>>>(a);
-  else train_backward_h_kernel<Prec::BF16><<<num_sms * 4, 128, 0, s>>>(a);
+  if (P == Prec::F16) {
+    if ((e = set_smem(train_backward_h_kernel<Prec::F16>, kBwSmemBytes, kBwThreads)) != cudaSuccess) return e;
+    train_backward_h_kernel<Prec::F16><<<num_sms * 2, kBwThreads, kBwSmemBytes, s>>>(a);
+  } else {
+    if ((e = set_smem(train_backward_h_kernel<Prec::BF16>, kBwSmemBytes, kBwThreads)) != cudaSuccess) return e;
+    train_backward_h_kernel<Prec::BF16><<<num_sms * 2, kBwThreads, kBwSmemBytes, s>>>(a);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   train_scatter_kernel<true><<<num_sms * 8, 256, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

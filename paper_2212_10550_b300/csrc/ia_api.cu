@@ -52,6 +52,7 @@ struct ia_ctx {
   // counters
   unsigned long long* d_stats = nullptr;
   unsigned int* d_counter = nullptr;
+  unsigned int* d_work = nullptr;   // list counters: [0] occupancy, [1] training sample kernel
   unsigned long long* d_tstats = nullptr;  // counters of the last training step
   // scratch for host-memory outputs of ia_render
   float* d_out = nullptr;
@@ -328,6 +329,7 @@ ia_status ia_create(const ia_config* cfg, ia_ctx** out) {
   if (e == cudaSuccess) e = dalloc(&c->d_sigma, (size_t)R * R * R);
   if (e == cudaSuccess) e = dalloc(&c->d_stats, (size_t)ST_COUNT);
   if (e == cudaSuccess) e = dalloc(&c->d_counter, (size_t)1);
+  if (e == cudaSuccess) e = dalloc(&c->d_work, (size_t)2);
   if (e == cudaSuccess) e = dalloc(&c->d_tstats, (size_t)ST_COUNT);
   if (e == cudaSuccess) e = cudaMemset(c->d_tstats, 0, sizeof(unsigned long long) * ST_COUNT);
   if (e == cudaSuccess) e = cudaMemset(c->d_occ_train, 0, words * sizeof(uint32_t));
@@ -360,6 +362,7 @@ void ia_destroy(ia_ctx* c) {
   dfree(c->d_sigma);
   dfree(c->d_stats);
   dfree(c->d_counter);
+  dfree(c->d_work);
   dfree(c->d_tstats);
   dfree(c->d_out);
   dfree(c->d_ray_n);
@@ -520,7 +523,8 @@ ia_status ia_update_occupancy(ia_ctx* c, int pose, int mode, float* sigma_out, u
   const size_t words = ((size_t)R * R * R + 31) / 32;
   float* sig = sigma_out ? sigma_out : c->d_sigma;
   IA_CUDA(c, cudaMemsetAsync(c->d_stats, 0, sizeof(unsigned long long) * ST_COUNT, s), "ia_update_occupancy");
-  IA_CUDA(c, launch_occ_density(occ_args(c, pose), box_dev(c), sig, c->d_stats, s), "ia_update_occupancy: density");
+  IA_CUDA(c, launch_occ_density(occ_args(c, pose), box_dev(c), sig, c->d_stats, c->d_work, c->num_sms, s),
+          "ia_update_occupancy: density");
   if (mode == IA_OCC_POSE) {
     IA_CUDA(c, launch_occ_bits(sig, R, c->cfg.occ_dilate, c->cfg.occ_tau, c->d_occ, nullptr, s),
             "ia_update_occupancy: bits");
@@ -713,6 +717,7 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
   IA_CUDA(c, cudaMemsetAsync(c->d_count, 0, sizeof(int), s), "ia_train_step");
   if (c->d_overflow) IA_CUDA(c, cudaMemsetAsync(c->d_overflow, 0, sizeof(int), s), "ia_train_step");
   IA_CUDA(c, cudaMemsetAsync(c->d_tstats, 0, sizeof(unsigned long long) * ST_COUNT, s), "ia_train_step");
+  IA_CUDA(c, cudaMemsetAsync(c->d_work + 1, 0, sizeof(unsigned), s), "ia_train_step");
   if (c->n_poses > c->pose_ws_cap) {
     IA_CUDA(c, cudaStreamSynchronize(s), "ia_train_step");
     c->pose_ws_cap = 0;
@@ -748,6 +753,7 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
   a.s_x = c->d_s_x;
   a.s_grad = c->d_s_grad;
   a.s_dfeat = c->d_s_dfeat;
+  a.work = c->d_work + 1;
   a.act = c->d_act;
   a.loss = loss;
   a.rgb_out = rgb_out;
@@ -1073,7 +1079,7 @@ ia_status ia_update_occupancy_static(ia_ctx* c, int pose, uint32_t* bits_out, vo
   cudaStream_t s = (cudaStream_t)stream;
   // the density kernel writes all R^3 cells before the bits kernel reads them, so
   // the scratch needs no clearing; cells past R^3 are never read
-  IA_CUDA(c, launch_occ_density(occ_args(c, pose), box_dev(c), sigma, nullptr, s),
+  IA_CUDA(c, launch_occ_density(occ_args(c, pose), box_dev(c), sigma, nullptr, c->d_work, c->num_sms, s),
           "ia_update_occupancy_static: density");
   IA_CUDA(c, launch_occ_bits(sigma, R, c->cfg.occ_dilate, c->cfg.occ_tau, c->d_occ, nullptr, s),
           "ia_update_occupancy_static: bits");

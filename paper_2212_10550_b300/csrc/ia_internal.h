@@ -17,6 +17,14 @@ __device__ __forceinline__ void flush_stats(unsigned long long* stats, int idx, 
   if ((threadIdx.x & 31) == 0 && v != 0) atomicAdd(stats + idx, (unsigned long long)v);
 }
 
+// the next list index of a warp from a counter shared by the grid (zeroed by
+// the host before the launch); all 32 lanes call
+__device__ __forceinline__ int next_list(unsigned* work) {
+  int w = 0;
+  if ((threadIdx.x & 31) == 0) w = (int)atomicAdd(work, 1u);
+  return __shfl_sync(kFull, w, 0);
+}
+
 enum StatIdx {
   ST_RAYS = 0, ST_HIT, ST_MARCHED, ST_OCC, ST_STARTS, ST_ITERS, ST_CONV, ST_ROOTS, ST_EARLY, ST_PROP, ST_FALLBACK,
   ST_COUNT = 16
@@ -121,6 +129,7 @@ struct TrainArgs {
   int* pose_tot;         // [n_poses] samples per pose, then the first index of each pose (zeroed by the host)
   int* pose_fill;        // [n_poses] fill counters (zeroed by the host)
   float4* s_dfeat;       // [samples][kIn / 4] dL/dfeatures (fp32, unscaled)
+  unsigned* work;        // list counter of the sample kernel (zeroed by the host)
 };
 
 // b1p[pose][j] = b1[j] + W1[j, pose columns] . theta_pose for every pose
@@ -200,7 +209,7 @@ cudaError_t launch_pose_chain(int P, int nb, const int* parent, const double* re
                               const double* trans, float* N, float* Ninv, float* B0inv, cudaStream_t s);
 cudaError_t launch_blend(int P, int V, int nb, const float* W, const float* N, float4* M, cudaStream_t s);
 cudaError_t launch_occ_density(const PosedArgs& a, const BoxDev& box, float* sigma,
-                               unsigned long long* stats, cudaStream_t s);
+                               unsigned long long* stats, unsigned* work, int num_sms, cudaStream_t s);
 cudaError_t launch_occ_bits(const float* sigma, int R, int dilate, float tau, uint32_t* bits,
                             uint32_t* union_bits, cudaStream_t s);
 cudaError_t launch_query_posed(const PosedArgs& a, int n, const float* x, float* sigma, float* rgb,

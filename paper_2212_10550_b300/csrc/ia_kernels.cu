@@ -165,7 +165,7 @@ cudaError_t launch_blend(int P, int V, int nb, const float* W, const float* N, f
 template <Prec P>
 size_t posed_smem_bytes_p(int threads, bool prop) {
   return sizeof(float) * (mlp_smem_words(P, threads, prop) + kMaxBones * 12) +
-         sizeof(float4) * kMaxRoots * kNS * threads;
+         sizeof(uint32_t) * (threads / 32) * list_smem_words(prop);
 }
 
 size_t posed_smem_bytes(int threads) { return posed_smem_bytes_p<Prec::F32>(threads, false); }
@@ -174,36 +174,29 @@ size_t posed_smem_bytes(int threads) { return posed_smem_bytes_p<Prec::F32>(thre
 // Occupancy grid (Sec. 3.3, inference mode)
 // ---------------------------------------------------------------------------
 
+// Per warp: a list of kList consecutive cells taken from a shared counter
+// (lists differ a lot in cost: a cell without a root runs every start to the
+// iteration cap), searched with lane refill.
 template <Prec P>
 __global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS)
     occ_density_kernel(const PosedArgs a, const BoxDev box, float* __restrict__ sigma,
-                       unsigned long long* __restrict__ stats) {
+                       unsigned long long* __restrict__ stats, unsigned* __restrict__ work) {
   extern __shared__ float4 smem4[];
   PosedSmem sm = stage_posed<P>(stage_of(a), smem4);
   const int n = box.R * box.R * box.R;
   SampleStats st;
-  // grid-stride over whole warps so every lane takes part in the warp-level search;
-  // each lane carries kNS cells through the search
-  for (int base = blockIdx.x * blockDim.x * kNS; base < n; base += gridDim.x * blockDim.x * kNS) {
-    bool act[kNS];
-    float3 xn[kNS];
-    const float4* Ms[kNS];
-    const float* Ns[kNS];
-    PosedOut o[kNS];
-#pragma unroll
-    for (int q = 0; q < kNS; ++q) {
-      const int cell = base + q * blockDim.x + threadIdx.x;
-      act[q] = cell < n;
-      xn[q] = act[q] ? cell_center(box, cell) : make_float3(0.f, 0.f, 0.f);
-      Ms[q] = a.S.M;
-      Ns[q] = sm.sNinv;
-    }
-    posed_field_warp_n<kNS, P>(a.S, Ms, a.F, a.cfg, Ns, sm.fs, sm.roots, act, xn, o, st, a.prop, a.search != 0);
-#pragma unroll
-    for (int q = 0; q < kNS; ++q) {
-      const int cell = base + q * blockDim.x + threadIdx.x;
-      if (act[q]) sigma[cell] = o[q].start >= 0 ? o[q].sigma : 0.f;
-    }
+  for (int list = next_list(work); list * kList < n; list = next_list(work)) {
+    const int base = list * kList;
+    posed_field_list<P>(
+        a.S, a.F, a.cfg, sm.fs, sm.list, min(kList, n - base),
+        [&](int i, float3& xn, const float4*& M, const float*& Ni, int& pose) {
+          xn = cell_center(box, base + i);
+          M = a.S.M;
+          Ni = sm.sNinv;
+          pose = 0;
+        },
+        [&](int i, const PosedOut& o) { sigma[base + i] = o.start >= 0 ? o.sigma : 0.f; }, st, a.prop,
+        false);  // occupancy cells take the plain search (the host never sets a.search here)
   }
   if (stats) {
     flush_stats(stats, ST_STARTS, st.starts);
@@ -217,22 +210,28 @@ __global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS)
 
 template <Prec P>
 static cudaError_t launch_occ_density_p(const PosedArgs& a, const BoxDev& box, float* sigma,
-                                        unsigned long long* stats, cudaStream_t s) {
+                                        unsigned long long* stats, unsigned* work, int num_sms, cudaStream_t s) {
   const int n = box.R * box.R * box.R;
-  const int blocks = (n + 256 * kNS - 1) / (256 * kNS);
   const size_t smem = posed_smem_bytes_p<P>(256, a.search != 0);
   cudaError_t e = set_smem(occ_density_kernel<P>, smem, 256);
   if (e != cudaSuccess) return e;
-  occ_density_kernel<P><<<blocks, 256, smem, s>>>(a, box, sigma, stats);
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, occ_density_kernel<P>, 256, smem);
+  if (e != cudaSuccess) return e;
+  const int lists = (n + kList - 1) / kList;
+  int blocks = num_sms * (per_sm < 1 ? 1 : per_sm);
+  if (blocks > (lists + 7) / 8) blocks = (lists + 7) / 8;
+  if ((e = cudaMemsetAsync(work, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
+  occ_density_kernel<P><<<blocks, 256, smem, s>>>(a, box, sigma, stats, work);
   return cudaGetLastError();
 }
 
 cudaError_t launch_occ_density(const PosedArgs& a, const BoxDev& box, float* sigma, unsigned long long* stats,
-                               cudaStream_t s) {
+                               unsigned* work, int num_sms, cudaStream_t s) {
   switch (a.prec) {
-    case 1: return launch_occ_density_p<Prec::F16>(a, box, sigma, stats, s);
-    case 2: return launch_occ_density_p<Prec::BF16>(a, box, sigma, stats, s);
-    default: return launch_occ_density_p<Prec::F32>(a, box, sigma, stats, s);
+    case 1: return launch_occ_density_p<Prec::F16>(a, box, sigma, stats, work, num_sms, s);
+    case 2: return launch_occ_density_p<Prec::BF16>(a, box, sigma, stats, work, num_sms, s);
+    default: return launch_occ_density_p<Prec::F32>(a, box, sigma, stats, work, num_sms, s);
   }
 }
 
@@ -287,30 +286,26 @@ __global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS)
   extern __shared__ float4 smem4[];
   PosedSmem sm = stage_posed<P>(stage_of(a), smem4);
   SampleStats st;
-  for (int base = blockIdx.x * blockDim.x * kNS; base < n; base += gridDim.x * blockDim.x * kNS) {
-    bool act[kNS];
-    float3 xn[kNS];
-    const float4* Ms[kNS];
-    const float* Ns[kNS];
-    PosedOut o[kNS];
-#pragma unroll
-    for (int q = 0; q < kNS; ++q) {
-      const int i = base + q * blockDim.x + threadIdx.x;
-      act[q] = i < n;
-      xn[q] = act[q] ? make_float3(x[3 * i], x[3 * i + 1], x[3 * i + 2]) : make_float3(0.f, 0.f, 0.f);
-      Ms[q] = a.S.M;
-      Ns[q] = sm.sNinv;
-    }
-    posed_field_warp_n<kNS, P>(a.S, Ms, a.F, a.cfg, Ns, sm.fs, sm.roots, act, xn, o, st, a.prop, a.search != 0);
-#pragma unroll
-    for (int q = 0; q < kNS; ++q) {
-      const int i = base + q * blockDim.x + threadIdx.x;
-      if (!act[q]) continue;
-      if (sigma) sigma[i] = o[q].start >= 0 ? o[q].sigma : 0.f;
-      if (rgb) { rgb[3 * i] = o[q].rgb.x; rgb[3 * i + 1] = o[q].rgb.y; rgb[3 * i + 2] = o[q].rgb.z; }
-      if (xc) { xc[3 * i] = o[q].xstar.x; xc[3 * i + 1] = o[q].xstar.y; xc[3 * i + 2] = o[q].xstar.z; }
-      if (start) start[i] = o[q].start;
-    }
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  for (int base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kList; base < n;
+       base += warps * kList) {
+    posed_field_list<P>(
+        a.S, a.F, a.cfg, sm.fs, sm.list, min(kList, n - base),
+        [&](int i, float3& xn, const float4*& M, const float*& Ni, int& pose) {
+          const int j = base + i;
+          xn = make_float3(x[3 * j], x[3 * j + 1], x[3 * j + 2]);
+          M = a.S.M;
+          Ni = sm.sNinv;
+          pose = 0;
+        },
+        [&](int i, const PosedOut& o) {
+          const int j = base + i;
+          if (sigma) sigma[j] = o.start >= 0 ? o.sigma : 0.f;
+          if (rgb) { rgb[3 * j] = o.rgb.x; rgb[3 * j + 1] = o.rgb.y; rgb[3 * j + 2] = o.rgb.z; }
+          if (xc) { xc[3 * j] = o.xstar.x; xc[3 * j + 1] = o.xstar.y; xc[3 * j + 2] = o.xstar.z; }
+          if (start) start[j] = o.start;
+        },
+        st, a.prop, a.search != 0);
   }
 }
 
@@ -320,7 +315,7 @@ static cudaError_t launch_query_posed_p(const PosedArgs& a, int n, const float* 
   const size_t smem = posed_smem_bytes_p<P>(256, a.search != 0);
   cudaError_t e = set_smem(query_posed_kernel<P>, smem, 256);
   if (e != cudaSuccess) return e;
-  query_posed_kernel<P><<<(n + 256 * kNS - 1) / (256 * kNS), 256, smem, s>>>(a, n, x, sigma, rgb, xc, start);
+  query_posed_kernel<P><<<(n + 8 * kList - 1) / (8 * kList), 256, smem, s>>>(a, n, x, sigma, rgb, xc, start);
   return cudaGetLastError();
 }
 
@@ -413,7 +408,8 @@ __global__ void __launch_bounds__(kRenderThreads, IA_RENDER_MIN_BLOCKS) render_k
   PosedSmem sm = stage_posed<P>(stage_of(a.P), smem4);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // this warp's slices of the shared arrays
-  float4* const after_roots = sm.roots + kMaxRoots * kNS * kRenderThreads;
+  float4* const after_roots = reinterpret_cast<float4*>(sm.sNinv + kMaxBones * 12) +
+                              (kRenderThreads / 32) * list_smem_words(kProp) / 4;
   float4* ray_o = after_roots + warp * 32;                             // (o.xyz, delta)
   float4* ray_d = ray_o + kRenderThreads;                              // (d.xyz, t_near)
   float4* s_res = after_roots + 2 * kRenderThreads + warp * 32 * K;    // (sigma, r, g, b)
@@ -518,34 +514,24 @@ __global__ void __launch_bounds__(kRenderThreads, IA_RENDER_MIN_BLOCKS) render_k
       }
     n_occ += nfound;
     __syncwarp();
-    // ---- 3. evaluate samples, 32 * kNS per step (kNS per lane)
-    for (int base = 0; base < total; base += 32 * kNS) {
-      bool act[kNS];
-      float3 xn[kNS];
-      const float4* Ms[kNS];
-      const float* Ns[kNS];
-      PosedOut r[kNS];
-#pragma unroll
-      for (int q = 0; q < kNS; ++q) {
-        const int sidx = base + q * 32 + lane;
-        act[q] = sidx < total;
-        xn[q] = make_float3(0.f, 0.f, 0.f);
-        if (act[q]) {
-          const int owner = s_ray[sidx];
-          const float4 ro = ray_o[owner], rd = ray_d[owner];
-          const float o[3] = {ro.x, ro.y, ro.z}, d[3] = {rd.x, rd.y, rd.z};
-          xn[q] = slot_position(o, d, rd.w, ro.w, s_slot[sidx]);
-        }
-        Ms[q] = a.P.S.M;
-        Ns[q] = sm.sNinv;
-      }
-      posed_field_warp_n<kNS, P>(a.P.S, Ms, a.P.F, a.P.cfg, Ns, sm.fs, sm.roots, act, xn, r, st, a.P.prop,
-                                 kProp);  // the proposal code is compiled only into kProp variants
-#pragma unroll
-      for (int q = 0; q < kNS; ++q) {
-        const int sidx = base + q * 32 + lane;
-        if (act[q]) s_res[sidx] = make_float4(r[q].start >= 0 ? r[q].sigma : 0.f, r[q].rgb.x, r[q].rgb.y, r[q].rgb.z);
-      }
+    // ---- 3. correspondence search and field at the round's samples (lists of kList)
+    for (int base = 0; base < total; base += kList) {
+      posed_field_list<P>(
+          a.P.S, a.P.F, a.P.cfg, sm.fs, sm.list, min(kList, total - base),
+          [&](int i, float3& xn, const float4*& M, const float*& Ni, int& pose) {
+            const int sidx = base + i;
+            const int owner = s_ray[sidx];
+            const float4 ro = ray_o[owner], rd = ray_d[owner];
+            const float o[3] = {ro.x, ro.y, ro.z}, d[3] = {rd.x, rd.y, rd.z};
+            xn = slot_position(o, d, rd.w, ro.w, s_slot[sidx]);
+            M = a.P.S.M;
+            Ni = sm.sNinv;
+            pose = 0;
+          },
+          [&](int i, const PosedOut& o) {
+            s_res[base + i] = make_float4(o.start >= 0 ? o.sigma : 0.f, o.rgb.x, o.rgb.y, o.rgb.z);
+          },
+          st, a.P.prop, kProp);  // the proposal code is compiled only into kProp variants
     }
     __syncwarp();
     // ---- 4. composite this ray's samples, alpha_i = 1 - exp(-sigma_i delta)

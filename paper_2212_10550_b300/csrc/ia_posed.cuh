@@ -49,235 +49,262 @@ __device__ __forceinline__ void field_eval_lane(const FieldDev& F, const FieldSm
   activate(o, sigma, rgb);
 }
 
-// Multi-start correspondence search and field evaluation for NS samples per
-// lane (NS independent Broyden chains interleaved, so that each loop step has
-// NS gathers of the blended grid in flight per lane).  All 32 lanes must call.
-//   M[s]: sample s's pose's blended grid; Ninv[s]: that pose's N_k^-1 ([nb][12]);
-//   roots: this CTA's float4 scratch of kMaxRoots * NS * blockDim.x entries
-//   (x, y, z, start bits).
-// The first kMaxRoots distinct roots of a sample are evaluated together by the
-// warp after the search; any further distinct root (rare) is evaluated on the
-// spot so that no root is ever dropped.
-// With use_prop (warp-uniform; reduced precision only) the proposal network
-// picks each sample's first starts: the top_k bones by logit (ties to the lower
-// bone), the first shifted by the predicted offset; when none of them yields a
-// valid root the search continues over every bone-wise start (the fallback).
-// With Q.b1p set, lane_pose[s] names sample s's pose (its layer-1 bias row).
-template <int NS, Prec P>
-__device__ __forceinline__ void posed_field_warp_n(const SkinDev& S, const float4* const* M, const FieldDev& F,
-                                                   const SolveCfg& cfg, const float* const* Ninv, const FieldSmem& fs,
-                                                   float4* roots, const bool* active, const float3* xn,
-                                                   PosedOut* out, SampleStats& st, const PropDev& Q = PropDev{},
-                                                   bool use_prop = false, const int* lane_pose = nullptr) {
-  const int tid = threadIdx.x, stride = blockDim.x;
-  // ---- proposed starts
-  int nprop[NS], pk[NS][2];
-  float3 poff[NS];
-#pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    nprop[s] = 0;
-    pk[s][0] = pk[s][1] = 0;
-    poff[s] = make_float3(0.f, 0.f, 0.f);
-  }
-  if constexpr (P != Prec::F32) {
-    if (use_prop) {
-#pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        float f16[16];
-        prop_encode(Q, active[s] ? xn[s] : make_float3(Q.nmin[0], Q.nmin[1], Q.nmin[2]), f16);
-        const float* O = prop_mma_warp<P>(fs.pw, fs.xstage, f16, Q.b1p, lane_pose ? lane_pose[s] : 0) +
-                         (threadIdx.x & 31) * (kPropMaxOut + 1);
-        if (active[s]) {
-          int b0 = 0, b1 = -1;
-          float v0 = O[0], v1 = -3.0e38f;
-          for (int i = 1; i < cfg.nb; ++i) {
-            const float v = O[i];
-            if (v > v0) { b1 = b0; v1 = v0; b0 = i; v0 = v; }
-            else if (v > v1) { b1 = i; v1 = v; }
-          }
-          pk[s][0] = b0;
-          pk[s][1] = b1 < 0 ? b0 : b1;
-          nprop[s] = min(Q.top_k, cfg.nb);
-          poff[s] = make_float3(O[cfg.nb], O[cfg.nb + 1], O[cfg.nb + 2]);
-          st.proposed++;
-        }
-        __syncwarp();  // every lane has read its row before the staging area is reused
-      }
-    }
-  }
-  int k[NS], it[NS], nroots[NS], phase[NS];  // phase 0 = start k, 1 = iterate, 2 = done
-  int label[NS];
-  float3 x[NS], r[NS], dx[NS];
-  float H[NS][9];
-#pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    out[s].sigma = 0.f;
-    out[s].rgb = make_float3(0.f, 0.f, 0.f);
-    out[s].xstar = out[s].rgb;
-    out[s].start = -1;
-    k[s] = 0; it[s] = 0; nroots[s] = 0; label[s] = 0;
-    phase[s] = active[s] ? 0 : 2;
-    x[s] = make_float3(0.f, 0.f, 0.f); r[s] = x[s]; dx[s] = x[s];
-#pragma unroll
-    for (int q = 0; q < 9; ++q) H[s][q] = 0.f;
-  }
-  auto busy = [&]() {
-    bool b = false;
-#pragma unroll
-    for (int s = 0; s < NS; ++s) b |= phase[s] != 2;
-    return b;
-  };
-  // ---- flattened multi-start Broyden: every loop step evaluates M once per chain
-  while (__any_sync(kFull, busy())) {
-    float3 q[NS];
-    float Mx[NS][12];
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      q[s] = x[s];
-      if (phase[s] == 0) {
-        // starts 0 .. nprop-1 are proposed bones, the rest every bone in order
-        const bool proposed = k[s] < nprop[s];
-        label[s] = proposed ? (k[s] == 0 ? pk[s][0] : pk[s][1]) : k[s] - nprop[s];
-        const float* A = Ninv[s] + 12 * label[s];
-        const float3 p = xn[s];
-        q[s] = make_float3(A[0] * p.x + A[1] * p.y + A[2] * p.z + A[3], A[4] * p.x + A[5] * p.y + A[6] * p.z + A[7],
-                           A[8] * p.x + A[9] * p.y + A[10] * p.z + A[11]);
-        if (proposed && k[s] == 0) q[s] = make_float3(q[s].x + poff[s].x, q[s].y + poff[s].y, q[s].z + poff[s].z);
-      } else if (phase[s] == 1) {
-        q[s] = make_float3(x[s].x + dx[s].x, x[s].y + dx[s].y, x[s].z + dx[s].z);
-      }
-    }
-#pragma unroll
-    for (int s = 0; s < NS; ++s)
-      if (phase[s] != 2) blend_value(S, M[s], q[s], Mx[s]);
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      bool finish = false, conv = false;
-      if (phase[s] == 0) {
-        st.starts++;
-        const float3 y = apply34(Mx[s], q[s]);
-        x[s] = q[s];
-        r[s] = make_float3(y.x - xn[s].x, y.y - xn[s].y, y.z - xn[s].z);
-        // initial inverse Jacobian: LBS with the weights frozen at x0, (sum_i w_i R_i)^-1
-        const float J0[9] = {Mx[s][0], Mx[s][1], Mx[s][2], Mx[s][4], Mx[s][5], Mx[s][6], Mx[s][8], Mx[s][9], Mx[s][10]};
-        it[s] = 0;
-        if (!inv3(J0, H[s])) finish = true;
-      } else if (phase[s] == 1) {
-        const float3 y = apply34(Mx[s], q[s]);
-        const float3 rn = make_float3(y.x - xn[s].x, y.y - xn[s].y, y.z - xn[s].z);
-        const float3 dr = make_float3(rn.x - r[s].x, rn.y - r[s].y, rn.z - r[s].z);
-        x[s] = q[s];
-        r[s] = rn;
-        ++it[s];
-        st.iters++;
-        // good Broyden: H += (dx - H dr)(dx^T H) / (dx^T H dr)
-        float* h = H[s];
-        const float3 d = dx[s];
-        const float u0 = h[0] * dr.x + h[1] * dr.y + h[2] * dr.z;
-        const float u1 = h[3] * dr.x + h[4] * dr.y + h[5] * dr.z;
-        const float u2 = h[6] * dr.x + h[7] * dr.y + h[8] * dr.z;
-        const float den = d.x * u0 + d.y * u1 + d.z * u2;
-        if (fabsf(den) > 1e-12f) {
-          const float rden = 1.f / den;  // one reciprocal for the three quotients
-          const float a0 = (d.x - u0) * rden, a1 = (d.y - u1) * rden, a2 = (d.z - u2) * rden;
-          const float b0 = d.x * h[0] + d.y * h[3] + d.z * h[6];
-          const float b1 = d.x * h[1] + d.y * h[4] + d.z * h[7];
-          const float b2 = d.x * h[2] + d.y * h[5] + d.z * h[8];
-          h[0] += a0 * b0; h[1] += a0 * b1; h[2] += a0 * b2;
-          h[3] += a1 * b0; h[4] += a1 * b1; h[5] += a1 * b2;
-          h[6] += a2 * b0; h[7] += a2 * b1; h[8] += a2 * b2;
-        }
-      }
-      if (phase[s] != 2 && !finish) {
-        const float rr = r[s].x * r[s].x + r[s].y * r[s].y + r[s].z * r[s].z;
-        if (rr < cfg.tol2) {
-          conv = true;
-          finish = true;
-        } else if (it[s] >= cfg.max_iter) {
-          finish = true;
-        } else {
-          const float* h = H[s];
-          dx[s] = make_float3(-(h[0] * r[s].x + h[1] * r[s].y + h[2] * r[s].z),
-                              -(h[3] * r[s].x + h[4] * r[s].y + h[5] * r[s].z),
-                              -(h[6] * r[s].x + h[7] * r[s].y + h[8] * r[s].z));
-          phase[s] = 1;
-        }
-      }
-      if (finish) {
-        if (conv && in_box(S, x[s])) {
-          st.converged++;
-          bool dup = false;
-          for (int j = 0; j < min(nroots[s], kMaxRoots); ++j) {
-            const float4 o = roots[((s * kMaxRoots) + j) * stride + tid];
-            const float ddx = x[s].x - o.x, ddy = x[s].y - o.y, ddz = x[s].z - o.z;
-            if (ddx * ddx + ddy * ddy + ddz * ddz < 1e-8f) { dup = true; break; }
-          }
-          if (!dup) {
-            st.roots++;
-            if (nroots[s] < kMaxRoots) {
-              roots[((s * kMaxRoots) + nroots[s]) * stride + tid] =
-                  make_float4(x[s].x, x[s].y, x[s].z, __int_as_float(label[s]));
-            } else {
-              const float3 xs = polish_root(S, M[s], x[s], xn[s]);
-              float sig;
-              float3 rgb;
-              field_eval_lane<P>(F, fs, xs, sig, rgb);
-              take_best(out[s], sig, rgb, xs, label[s]);
-            }
-            nroots[s]++;
-          }
-        }
-        ++k[s];
-        if (nprop[s] > 0 && k[s] == nprop[s]) {
-          if (nroots[s] > 0) k[s] = nprop[s] + cfg.nb;  // a proposed start found a root: done
-          else st.fallbacks++;                            // none did: every bone-wise start follows
-        }
-        phase[s] = (k[s] < nprop[s] + cfg.nb) ? 0 : 2;
-      }
-    }
-  }
-  // ---- one Newton polish per stored root, field evaluation, max-density root;
-  //      the lane's (sample, root) pairs are evaluated one per warp step
-  int nr[NS], total = 0;
-#pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    nr[s] = min(nroots[s], kMaxRoots);
-    total += nr[s];
-  }
-  const int nmax = __reduce_max_sync(kFull, total);
-  for (int e = 0; e < nmax; ++e) {
-    const bool has = e < total;
-    int si = 0, j = e;
-#pragma unroll
-    for (int s = 0; s + 1 < NS; ++s)
-      if (si == s && j >= nr[s]) { j -= nr[s]; si = s + 1; }
-    float3 xs = make_float3(S.cmin[0], S.cmin[1], S.cmin[2]);
-    int start = -1;
-    float3 xq = xn[0];
-    const float4* Mq = M[0];
-#pragma unroll
-    for (int s = 1; s < NS; ++s)
-      if (si == s) { xq = xn[s]; Mq = M[s]; }
-    if (has) {
-      const float4 o = roots[((si * kMaxRoots) + j) * stride + tid];
-      start = __float_as_int(o.w);
-      xs = polish_root(S, Mq, make_float3(o.x, o.y, o.z), xq);
-    }
+// ---------------------------------------------------------------------------
+// Multi-start correspondence search and field evaluation (Sec. 3.1, Eq. 3-4, 7)
+// for a warp's list of m <= 32 samples, one per lane.  The bone-wise Broyden
+// chains are flattened: every loop step evaluates the blended grid once per
+// lane, whatever start or iteration the lane is on.  Each sample's distinct
+// roots go to the warp's shared-memory list; once the search is done the warp
+// evaluates the field at the roots (the tensor-core MLP needs the whole warp)
+// and keeps each sample's max-density root.
+//   src(i, xn, M, Ninv, pose): sample i's normalised point, blended grid, N^-1
+//   rows and pose index;  dst(i, out): its result.
+// With use_prop (reduced precision only) the proposal network picks each
+// sample's first starts: the top_k bones by logit (ties to the lower bone), the
+// first shifted by the predicted offset; when none of them yields a valid root
+// the search continues over every bone-wise start (the fallback).
+// Kernels hand their warps lists from a counter shared by the grid, since lists
+// differ a lot in cost (a sample without a root runs every start to the cap).
+// (Longer lists with lanes refilled from them were measured: no faster, and
+// their root lists cost L1 capacity.)
+// ---------------------------------------------------------------------------
+
+constexpr int kList = 32;
+
+struct ListSmem {
+  float4* roots;     // [kMaxRoots][kList]  (x, y, z, start bone), slot-major: conflict-free rows
+  uint8_t* nroots;   // [kList]
+  float4* prop;      // [kList]  (bones b0 | b1 << 8, offset xyz), or null
+};
+
+__host__ __device__ constexpr int list_smem_words(bool prop) {
+  return kList * kMaxRoots * 4 + kList / 4 + (prop ? kList * 4 : 0);
+}
+
+__device__ __forceinline__ ListSmem list_smem(uint32_t* base, bool prop) {
+  ListSmem q;
+  q.roots = reinterpret_cast<float4*>(base);
+  q.prop = prop ? reinterpret_cast<float4*>(base + kList * kMaxRoots * 4) : nullptr;
+  q.nroots = reinterpret_cast<uint8_t*>(base + kList * kMaxRoots * 4 + (prop ? kList * 4 : 0));
+  return q;
+}
+
+// A sample found more distinct roots than its list holds: evaluate the list and
+// the new root now and keep only the max-density one (ties to the earlier
+// start), so that no root is ever dropped from the selection.
+template <Prec P>
+__device__ __noinline__ void compress_roots(const SkinDev& S, const float4* M, const FieldDev& F, const FieldSmem& fs,
+                                            float4* list, float3 xn, float3 xnew, int label_new) {
+  // list[j * kList]: root j of this sample
+  PosedOut best;
+  best.sigma = 0.f;
+  best.rgb = best.xstar = make_float3(0.f, 0.f, 0.f);
+  best.start = -1;
+  for (int j = 0; j <= kMaxRoots; ++j) {
+    const float4 o =
+        j < kMaxRoots ? list[j * kList] : make_float4(xnew.x, xnew.y, xnew.z, __int_as_float(label_new));
+    const float3 xs = polish_root(S, M, make_float3(o.x, o.y, o.z), xn);
     float sig;
     float3 rgb;
-    field_eval_warp<P>(F, fs, xs, sig, rgb);
-    if (has) {
-#pragma unroll
-      for (int s = 0; s < NS; ++s)
-        if (si == s) take_best(out[s], sig, rgb, xs, start);
+    field_eval_lane<P>(F, fs, xs, sig, rgb);
+    take_best(best, sig, rgb, xs, __float_as_int(o.w));
+  }
+  list[0] = make_float4(best.xstar.x, best.xstar.y, best.xstar.z, __int_as_float(best.start));
+}
+
+template <Prec P, class Src, class Dst>
+__device__ __forceinline__ void posed_field_list(const SkinDev& S, const FieldDev& F, const SolveCfg& cfg,
+                                                  const FieldSmem& fs, const ListSmem& qs, int m, Src src, Dst dst,
+                                                  SampleStats& st, const PropDev& Q = PropDev{},
+                                                  bool use_prop = false) {
+  const int lane = threadIdx.x & 31;
+  // ---- proposed starts of every sample of the list (warp MMA)
+  if constexpr (P != Prec::F32) {
+    if (use_prop) {
+      const bool act = lane < m;
+      float3 xn = make_float3(Q.nmin[0], Q.nmin[1], Q.nmin[2]);
+      const float4* Mi;
+      const float* Ni;
+      int pose = 0;
+      if (act) src(lane, xn, Mi, Ni, pose);
+      float f16[16];
+      prop_encode(Q, xn, f16);
+      const float* O = prop_mma_warp<P>(fs.pw, fs.xstage, f16, Q.b1p, pose) + lane * (kPropMaxOut + 1);
+      if (act) {
+        int b0 = 0, b1 = -1;
+        float v0 = O[0], v1 = -3.0e38f;
+        for (int k = 1; k < cfg.nb; ++k) {
+          const float v = O[k];
+          if (v > v0) { b1 = b0; v1 = v0; b0 = k; v0 = v; }
+          else if (v > v1) { b1 = k; v1 = v; }
+        }
+        if (b1 < 0) b1 = b0;
+        qs.prop[lane] = make_float4(__int_as_float(b0 | (b1 << 8)), O[cfg.nb], O[cfg.nb + 1], O[cfg.nb + 2]);
+        st.proposed++;
+      }
+      __syncwarp();  // every lane has read its row before the staging area is reused
     }
   }
+  // ---- search: lane i takes sample i
+  int k = 0, it = 0, nr = 0, label = 0, phase = 2, nprop = 0, pk0 = 0, pk1 = 0;
+  const int cur = lane;
+  float3 xn = make_float3(0.f, 0.f, 0.f), x = xn, r = xn, dx = xn, poff = xn;
+  const float4* M = nullptr;
+  const float* Ninv = nullptr;
+  float H[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) H[q] = 0.f;
+  if (lane < m) {
+    int pose;
+    src(lane, xn, M, Ninv, pose);
+    phase = 0;
+    if (use_prop) {
+      nprop = min(Q.top_k, cfg.nb);
+      const float4 pp = qs.prop[lane];
+      const int bb = __float_as_int(pp.x);
+      pk0 = bb & 0xff;
+      pk1 = (bb >> 8) & 0xff;
+      poff = make_float3(pp.y, pp.z, pp.w);
+    }
+  }
+  while (__any_sync(kFull, phase != 2)) {
+    float3 q = x;
+    if (phase == 0) {
+      // starts 0 .. nprop-1 are proposed bones, the rest every bone in order
+      const bool proposed = k < nprop;
+      label = proposed ? (k == 0 ? pk0 : pk1) : k - nprop;
+      const float* A = Ninv + 12 * label;
+      q = make_float3(A[0] * xn.x + A[1] * xn.y + A[2] * xn.z + A[3], A[4] * xn.x + A[5] * xn.y + A[6] * xn.z + A[7],
+                      A[8] * xn.x + A[9] * xn.y + A[10] * xn.z + A[11]);
+      if (proposed && k == 0) q = make_float3(q.x + poff.x, q.y + poff.y, q.z + poff.z);
+    } else if (phase == 1) {
+      q = make_float3(x.x + dx.x, x.y + dx.y, x.z + dx.z);
+    }
+    float Mx[12];
+    if (phase != 2) blend_value(S, M, q, Mx);
+    bool finish = false, conv = false;
+    if (phase == 0) {
+      st.starts++;
+      const float3 y = apply34(Mx, q);
+      x = q;
+      r = make_float3(y.x - xn.x, y.y - xn.y, y.z - xn.z);
+      // initial inverse Jacobian: LBS with the weights frozen at x0, (sum_i w_i R_i)^-1
+      const float J0[9] = {Mx[0], Mx[1], Mx[2], Mx[4], Mx[5], Mx[6], Mx[8], Mx[9], Mx[10]};
+      it = 0;
+      if (!inv3(J0, H)) finish = true;
+    } else if (phase == 1) {
+      const float3 y = apply34(Mx, q);
+      const float3 rn = make_float3(y.x - xn.x, y.y - xn.y, y.z - xn.z);
+      const float3 dr = make_float3(rn.x - r.x, rn.y - r.y, rn.z - r.z);
+      x = q;
+      r = rn;
+      ++it;
+      st.iters++;
+      // good Broyden: H += (dx - H dr)(dx^T H) / (dx^T H dr)
+      const float3 d = dx;
+      const float u0 = H[0] * dr.x + H[1] * dr.y + H[2] * dr.z;
+      const float u1 = H[3] * dr.x + H[4] * dr.y + H[5] * dr.z;
+      const float u2 = H[6] * dr.x + H[7] * dr.y + H[8] * dr.z;
+      const float den = d.x * u0 + d.y * u1 + d.z * u2;
+      if (fabsf(den) > 1e-12f) {
+        const float rden = 1.f / den;  // one reciprocal for the three quotients
+        const float a0 = (d.x - u0) * rden, a1 = (d.y - u1) * rden, a2 = (d.z - u2) * rden;
+        const float b0 = d.x * H[0] + d.y * H[3] + d.z * H[6];
+        const float b1 = d.x * H[1] + d.y * H[4] + d.z * H[7];
+        const float b2 = d.x * H[2] + d.y * H[5] + d.z * H[8];
+        H[0] += a0 * b0; H[1] += a0 * b1; H[2] += a0 * b2;
+        H[3] += a1 * b0; H[4] += a1 * b1; H[5] += a1 * b2;
+        H[6] += a2 * b0; H[7] += a2 * b1; H[8] += a2 * b2;
+      }
+    }
+    if (phase != 2 && !finish) {
+      const float rr = r.x * r.x + r.y * r.y + r.z * r.z;
+      if (rr < cfg.tol2) {
+        conv = true;
+        finish = true;
+      } else if (it >= cfg.max_iter) {
+        finish = true;
+      } else {
+        dx = make_float3(-(H[0] * r.x + H[1] * r.y + H[2] * r.z), -(H[3] * r.x + H[4] * r.y + H[5] * r.z),
+                         -(H[6] * r.x + H[7] * r.y + H[8] * r.z));
+        phase = 1;
+      }
+    }
+    if (finish) {
+      float4* list = qs.roots + cur;
+      if (conv && in_box(S, x)) {
+        st.converged++;
+        bool dup = false;
+        for (int j = 0; j < nr; ++j) {
+          const float4 o = list[j * kList];
+          const float ddx = x.x - o.x, ddy = x.y - o.y, ddz = x.z - o.z;
+          if (ddx * ddx + ddy * ddy + ddz * ddz < 1e-8f) { dup = true; break; }
+        }
+        if (!dup) {
+          st.roots++;
+          if (nr < kMaxRoots) {
+            list[kList * nr++] = make_float4(x.x, x.y, x.z, __int_as_float(label));
+          } else {
+            compress_roots<P>(S, M, F, fs, list, xn, x, label);
+            nr = 1;
+          }
+        }
+      }
+      ++k;
+      if (nprop > 0 && k == nprop) {
+        if (nr > 0) k = nprop + cfg.nb;  // a proposed start found a root: done
+        else st.fallbacks++;             // none did: every bone-wise start follows
+      }
+      if (k < nprop + cfg.nb) {
+        phase = 0;
+      } else {
+        qs.nroots[cur] = (uint8_t)nr;
+        phase = 2;
+      }
+    }
+  }
+  __syncwarp();
+  // ---- one Newton polish per stored root, field at the roots, max-density root
+  {
+    const int i = lane;  // the lane evaluates its own sample's roots
+    const bool act = i < m;
+    PosedOut out;
+    out.sigma = 0.f;
+    out.rgb = out.xstar = make_float3(0.f, 0.f, 0.f);
+    out.start = -1;
+    int n_r = 0;
+    float3 xq = make_float3(0.f, 0.f, 0.f);
+    const float4* Mq = nullptr;
+    if (act) {
+      const float* Nq;
+      int pose;
+      src(i, xq, Mq, Nq, pose);
+      n_r = qs.nroots[i];
+    }
+    const int nmax = __reduce_max_sync(kFull, n_r);
+    for (int e = 0; e < nmax; ++e) {
+      const bool has = e < n_r;
+      float3 xs = make_float3(S.cmin[0], S.cmin[1], S.cmin[2]);
+      int start = -1;
+      if (has) {
+        const float4 o = qs.roots[e * kList + i];
+        start = __float_as_int(o.w);
+        xs = polish_root(S, Mq, make_float3(o.x, o.y, o.z), xq);
+      }
+      float sig;
+      float3 rgb;
+      field_eval_warp<P>(F, fs, xs, sig, rgb);
+      if (has) take_best(out, sig, rgb, xs, start);
+    }
+    if (act) dst(i, out);
+  }
+  __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
 // Shared-memory layout of kernels that evaluate the posed field:
 //   MLP (fp32 layout, or reduced-precision layout + proposal + per-warp
-//   staging), a pose's N_k^-1, and the per-lane root lists.
+//   staging), a pose's N_k^-1, and each warp's search lists.
 // ---------------------------------------------------------------------------
 
 struct PosedStage {
@@ -306,7 +333,7 @@ __host__ __device__ constexpr int mlp_smem_words(Prec P, int threads, bool prop)
 struct PosedSmem {
   FieldSmem fs;
   float* sNinv;
-  float4* roots;
+  ListSmem list;  // this warp's search list
 };
 
 template <Prec P>
@@ -334,7 +361,9 @@ __device__ __forceinline__ PosedSmem stage_posed(const PosedStage& a, float4* sm
     if (a.search) stage_prop_h<P>(a.prop, a.nb, a.theta, pw);
   }
   p.sNinv = base + mlp_smem_words(P, blockDim.x, a.search != 0);
-  p.roots = reinterpret_cast<float4*>(p.sNinv + kMaxBones * 12);
+  p.list = list_smem(reinterpret_cast<uint32_t*>(p.sNinv + kMaxBones * 12) +
+                           (threadIdx.x >> 5) * list_smem_words(a.search != 0),
+                       a.search != 0);
   for (int t = threadIdx.x; t < a.nb * 12; t += blockDim.x) p.sNinv[t] = a.Ninv[t];
   __syncthreads();
   return p;

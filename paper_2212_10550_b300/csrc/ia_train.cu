@@ -122,38 +122,26 @@ __global__ void __launch_bounds__(256) train_sample_kernel(const TrainArgs a) {
   ps.nb = a.P.cfg.nb;
   PosedSmem sm = stage_posed<P>(ps, smem4);
   const int n = *a.count;
-  const int lane = threadIdx.x & 31;
   SampleStats st;
-  const int warp_id = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int n_warps = gridDim.x * (blockDim.x >> 5);
-  for (int base = warp_id * 32 * kNS; base < n; base += n_warps * 32 * kNS) {
-    bool act[kNS];
-    float3 xn[kNS];
-    const float4* Ms[kNS];
-    const float* Ns[kNS];
-    int poses[kNS];
-    PosedOut o[kNS];
-#pragma unroll
-    for (int q = 0; q < kNS; ++q) {
-      const int s = base + q * 32 + lane;
-      act[q] = s < n;
-      const float4 p = act[q] ? a.s_pos[s] : make_float4(0.f, 0.f, 0.f, 0.f);
-      const int pose = act[q] ? __float_as_int(p.w) : 0;
-      poses[q] = pose;
-      xn[q] = make_float3(p.x, p.y, p.z);
-      Ms[q] = a.P.S.M + (size_t)pose * a.V * 3;
-      Ns[q] = a.P.Ninv + (size_t)pose * a.P.cfg.nb * 12;
-    }
-    posed_field_warp_n<kNS, P>(a.P.S, Ms, a.P.F, a.P.cfg, Ns, sm.fs, sm.roots, act, xn, o, st, a.P.prop, kProp,
-                               poses);
-#pragma unroll
-    for (int q = 0; q < kNS; ++q) {
-      const int s = base + q * 32 + lane;
-      if (!act[q]) continue;
-      const bool has = o[q].start >= 0;
-      a.s_out[s] = make_float4(has ? o[q].sigma : 0.f, o[q].rgb.x, o[q].rgb.y, o[q].rgb.z);
-      a.s_x[s] = make_float4(o[q].xstar.x, o[q].xstar.y, o[q].xstar.z, has ? 1.f : 0.f);
-    }
+  // per warp: lists of kList consecutive samples (one or two poses, since the
+  // samples are grouped by pose) from a shared counter, searched with lane refill
+  for (int list = next_list(a.work); list * kList < n; list = next_list(a.work)) {
+    const int base = list * kList;
+    posed_field_list<P>(
+        a.P.S, a.P.F, a.P.cfg, sm.fs, sm.list, min(kList, n - base),
+        [&](int i, float3& xn, const float4*& M, const float*& Ni, int& pose) {
+          const float4 p = a.s_pos[base + i];
+          pose = __float_as_int(p.w);
+          xn = make_float3(p.x, p.y, p.z);
+          M = a.P.S.M + (size_t)pose * a.V * 3;
+          Ni = a.P.Ninv + (size_t)pose * a.P.cfg.nb * 12;
+        },
+        [&](int i, const PosedOut& o) {
+          const bool has = o.start >= 0;
+          a.s_out[base + i] = make_float4(has ? o.sigma : 0.f, o.rgb.x, o.rgb.y, o.rgb.z);
+          a.s_x[base + i] = make_float4(o.xstar.x, o.xstar.y, o.xstar.z, has ? 1.f : 0.f);
+        },
+        st, a.P.prop, kProp);
   }
   flush_stats(a.stats, ST_STARTS, st.starts);
   flush_stats(a.stats, ST_ITERS, st.iters);
@@ -165,7 +153,8 @@ __global__ void __launch_bounds__(256) train_sample_kernel(const TrainArgs a) {
 
 template <Prec P>
 static size_t train_sample_smem(bool prop) {
-  return sizeof(float) * (mlp_smem_words(P, 256, prop) + kMaxBones * 12) + sizeof(float4) * kMaxRoots * kNS * 256;
+  return sizeof(float) * (mlp_smem_words(P, 256, prop) + kMaxBones * 12) +
+         sizeof(uint32_t) * (256 / 32) * list_smem_words(prop);
 }
 
 // front-to-back compositing of one ray, the loss, and the reverse sweep
@@ -963,7 +952,9 @@ cudaError_t launch_train(const TrainArgs& a, const CUtensorMap* map, int num_sms
   const size_t smem = P == Prec::F32   ? train_sample_smem<Prec::F32>(false)
                       : P == Prec::F16 ? train_sample_smem<Prec::F16>(prop) : train_sample_smem<Prec::BF16>(prop);
   if ((e = set_smem(sample, smem, 256)) != cudaSuccess) return e;
-  sample<<<num_sms * 2, 256, smem, s>>>(a);
+  int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sample, 256, smem)) != cudaSuccess) return e;
+  sample<<<num_sms * (per_sm < 1 ? 1 : per_sm), 256, smem, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   train_composite_kernel<<<rb, 128, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -47,9 +47,9 @@ FLOP_SAMPLE = 20       # alpha, transmittance, colour accumulation
 # DRAM bytes (read + write) of one render_kernel<2, fp32> launch on this workload,
 # from the ncu capture summarised in profiles/render_kernel_540x540_fp32.md; the
 # ncu-measured busiest unit of that launch is reported beside the roofline
-RENDER_DRAM_BYTES = 51.92e6 + 2.99e6
-RENDER_LIMITER = {"unit": "L1 (blended-grid gathers)", "l1tex_throughput_pct": 64.2, "issue_active_pct": 31.3,
-                  "fma_pipe_pct": 17.6, "l1_hit_pct": 91.0, "l2_hit_pct": 97.8,
+RENDER_DRAM_BYTES = 51.91e6 + 2.60e6
+RENDER_LIMITER = {"unit": "L1 (blended-grid gathers)", "l1tex_throughput_pct": 63.8, "issue_active_pct": 29.8,
+                  "fma_pipe_pct": 17.5, "l1_hit_pct": 91.0, "l2_hit_pct": 97.1, "simt_lanes_per_inst": 20.4,
                   "source": "profiles/render_kernel_540x540_fp32.md"}
 
 

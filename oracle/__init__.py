@@ -119,6 +119,7 @@ def _declare(L):
         "or_render": (None, [PM, PP, PC, PU32, PD, PD, PI32, PI32, PI64, C.c_int]),
         "or_render_pixels": (None, [PM, PP, PC, PU32, C.c_int, PI32, PD, PD, PI32, PI32, C.c_int]),
         "or_occupancy": (None, [PM, PP, PD, PU32, C.c_int]),
+        "or_occupancy_ema": (None, [PM, PP, PF, C.c_double, PD, PU32, C.c_int]),
         "or_march_mask": (None, [PM, PP, PC, PU32, PU32]),
         "or_occupancy_cells": (None, [PM, PP, C.c_int, PI32, PD, C.c_int]),
         "or_occ_bits": (None, [C.c_int, C.c_int, C.c_double, PD, PU32]),
@@ -366,6 +367,17 @@ class OracleModel:
         self.L.or_occupancy_cells(C.byref(self.m), C.byref(p), len(cells), _p(cells, C.c_int32),
                                   _p(sigma, C.c_double), nthreads)
         return sigma
+
+    def occupancy_ema(self, p, d, jitter=None, decay=0.95, nthreads=0):
+        """Training-mode update: d <- max(decay d, sigma at the (jittered) cell
+        points of pose p), in place; returns the bits of the updated d."""
+        R = self.scene.occ_res
+        assert d.dtype == np.float64 and d.shape == (R ** 3,) and d.flags.c_contiguous
+        bits = np.zeros((R ** 3 + 31) // 32, dtype=np.uint32)
+        jit = None if jitter is None else np.ascontiguousarray(jitter, dtype=np.float32).reshape(-1)
+        self.L.or_occupancy_ema(C.byref(self.m), C.byref(p), _p(jit, C.c_float), float(decay), _p(d, C.c_double),
+                                _p(bits, C.c_uint32), nthreads)
+        return bits
 
     def occupancy(self, p, nthreads=0):
         R = self.scene.occ_res

@@ -14,6 +14,10 @@ def declare(L):
     L.or_train.argtypes = [P(Model), P(Pose), C.c_int, P(C.c_uint32), C.c_int, P(C.c_float), P(C.c_float),
                            P(C.c_int32), P(C.c_double), P(C.c_double), P(C.c_int32), P(C.c_double),
                            P(C.c_double), P(C.c_double), P(C.c_double), C.c_int]
+    L.or_density_reg.restype = C.c_double
+    L.or_density_reg.argtypes = [P(Model), P(Pose), C.c_int, P(C.c_uint32), C.c_int, P(C.c_float), P(C.c_int32),
+                                 C.c_double, P(C.c_int32), P(C.c_double), P(C.c_double), P(C.c_double),
+                                 P(C.c_double)]
 
 
 def pose_array(poses):
@@ -68,3 +72,22 @@ def train(om, poses, occ_bits, origin, direction, pose_id, target, grad=True, nt
             fb = _p(fallbacks, C.c_int32)
         loss = om.L.or_train_prop(*common, C.byref(prop.q), _p(th, C.c_double), fb)
     return loss, rgb, flags, g
+
+
+def density_reg(om, poses, occ_bits, x, pose_id, weight, grads=None):
+    """Occupancy-based density regulariser (Eq. 12) at normalised-space points:
+    (loss, per-point flags).  grads: the dict train() returned, to which the
+    regulariser's gradient is added in place (None: loss only)."""
+    from . import _p
+    arr = pose_array(poses) if isinstance(poses, (list, tuple)) else poses
+    xs = np.ascontiguousarray(x, dtype=np.float32)
+    pid = np.ascontiguousarray(pose_id, dtype=np.int32)
+    occ = np.ascontiguousarray(occ_bits, dtype=np.uint32)
+    flags = np.zeros(len(pid), dtype=np.int32)
+    args = [None] * 4 if grads is None else [grads[k] for k in ("table", "mlp", "skin", "bones")]
+    for a in args:
+        assert a is None or (a.dtype == np.float64 and a.flags.c_contiguous)
+    loss = om.L.or_density_reg(C.byref(om.m), arr, len(arr), _p(occ, C.c_uint32), len(pid), _p(xs, C.c_float),
+                               _p(pid, C.c_int32), float(weight), _p(flags, C.c_int32),
+                               *[_p(a, C.c_double) for a in args])
+    return loss, flags

@@ -689,6 +689,36 @@ void or_occupancy(const or_model *m, const or_pose *p, double *sigma, uint32_t *
   if (bits) or_occ_bits(R, m->dilate, m->tau, sigma, bits);
 }
 
+/* Training-mode occupancy (Sec. 3.3, training stage): one grid for the whole
+ * sequence.  Each update queries the posed field of one frame at one point per
+ * cell, x = norm_min + (c + u) * (norm_max - norm_min) / R (fp32, fixed order;
+ * u = jitter[cell][3] in [0, 1), NULL = the cell centre), and folds it into the
+ * running density d <- max(decay * d, sigma); the bits are d thresholded and
+ * dilated as in or_occ_bits. */
+void or_occupancy_ema(const or_model *m, const or_pose *p, const float *jitter, double decay, double *d,
+                      uint32_t *bits, int nthreads) {
+  set_threads(nthreads);
+  int R = m->occ_res;
+  long n = (long)R * R * R;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (long cell = 0; cell < n; ++cell) {
+    int c[3] = {(int)(cell % R), (int)((cell / R) % R), (int)(cell / ((long)R * R))};
+    float x[3];
+    for (int a = 0; a < 3; ++a) {
+      float cs = (m->nmax[a] - m->nmin[a]) / (float)R;
+      float u = jitter ? jitter[3 * cell + a] : 0.5f;
+      x[a] = m->nmin[a] + (((float)c[a] + u) * cs);
+    }
+    double xn[3] = {(double)x[0], (double)x[1], (double)x[2]};
+    or_sample s;
+    or_posed_field(m, p, xn, &s);
+    double sig = s.start >= 0 ? s.sigma : 0.0;
+    double old = decay * d[cell];
+    d[cell] = sig > old ? sig : old;
+  }
+  if (bits) or_occ_bits(R, m->dilate, m->tau, d, bits);
+}
+
 void or_occupancy_cells(const or_model *m, const or_pose *p, int n, const int32_t *cells,
                         double *sigma, int nthreads) {
   set_threads(nthreads);

@@ -143,6 +143,10 @@ void or_march_mask(const or_model *m, const or_pose *p, const or_camera *c, cons
 void or_occupancy(const or_model *m, const or_pose *p, double *sigma, uint32_t *bits,
                   int nthreads);
 /* Density at the centres of n given cells (a bounded part of the grid). */
+/* Training-mode occupancy update (Sec. 3.3): d <- max(decay d, sigma(x_c)) with
+ * x_c = norm_min + (c + jitter[c]) * cell size (jitter NULL = centres); bits of d. */
+void or_occupancy_ema(const or_model *m, const or_pose *p, const float *jitter, double decay, double *d,
+                      uint32_t *bits, int nthreads);
 void or_occupancy_cells(const or_model *m, const or_pose *p, int n, const int32_t *cells,
                         double *sigma, int nthreads);
 void or_occ_bits(int R, int dilate, double tau, const double *sigma, uint32_t *bits);
@@ -185,6 +189,14 @@ double or_train_prop(const or_model *m, const or_pose *poses, int n_poses, const
                      double *rgb_out, int *ray_flags, double *g_table, double *g_mlp, double *g_skin,
                      double *g_bones, int nthreads, const or_prop *q, const double *theta_all,
                      int *ray_fallbacks);
+/* Occupancy-based density regulariser (Eq. 12) at n normalised-space points x
+ * [n][3] fp32 of poses pose_id [n]: L = weight / n * sum of sigma(x) over the
+ * points whose cell (or_cell) is empty in occ.  Its gradient is ADDED to the
+ * four buffers (dL/dsigma = weight / n, dL/dc = 0 through the same backward as
+ * the photometric loss).  point_flags [n] may be NULL. */
+double or_density_reg(const or_model *m, const or_pose *poses, int n_poses, const uint32_t *occ, int n,
+                      const float *x, const int32_t *pose_id, double weight, int *point_flags, double *g_table,
+                      double *g_mlp, double *g_skin, double *g_bones);
 /* Brute-force root set: Newton from every point of an n^3 canonical lattice. */
 int or_bruteforce_roots(const or_model *m, const or_pose *p, const double xn[3], int n,
                         double seed_thresh, double *roots, int max_roots);

@@ -370,3 +370,36 @@ double or_train_prop(const or_model *m, const or_pose *poses, int n_poses, const
   return train_impl(m, poses, n_poses, occ, n, o, d, pose_id, target, rgb_out, ray_flags, g_table, g_mlp, g_skin,
                     g_bones, nthreads, q, theta_all, ray_fallbacks);
 }
+
+double or_density_reg(const or_model *m, const or_pose *poses, int n_poses, const uint32_t *occ, int n,
+                      const float *x, const int32_t *pose_id, double weight, int *point_flags, double *g_table,
+                      double *g_mlp, double *g_skin, double *g_bones) {
+  double loss = 0.0;
+  const double w = n > 0 ? weight / (double)n : 0.0;
+  const double dc[3] = {0.0, 0.0, 0.0};
+  for (int i = 0; i < n; ++i) {
+    if (point_flags) point_flags[i] = 0;
+    const int pose = pose_id[i];
+    if (pose < 0 || pose >= n_poses) continue;
+    const int cell = or_cell(m, x + 3 * i);
+    if ((occ[cell >> 5] >> (cell & 31)) & 1u) continue; /* occupied: no penalty */
+    const double xn[3] = {(double)x[3 * i], (double)x[3 * i + 1], (double)x[3 * i + 2]};
+    or_sample s;
+    or_posed_field(m, &poses[pose], xn, &s);
+    if (point_flags) point_flags[i] = s.flags;
+    if (s.start < 0) continue; /* no root: density 0, nothing to differentiate */
+    loss += w * s.sigma;
+    if (g_table && g_mlp && g_skin && g_bones) {
+      fsamp q;
+      q.has = 1;
+      q.pose = pose;
+      q.sigma = s.sigma;
+      for (int k = 0; k < 3; ++k) {
+        q.xs[k] = s.xstar[k];
+        q.rgb[k] = s.rgb[k];
+      }
+      backward_sample(m, poses, &q, w, dc, g_table, g_mlp, g_skin, g_bones);
+    }
+  }
+  return loss;
+}

@@ -381,6 +381,13 @@ def pack_mlp(mlp: dict) -> np.ndarray:
                           ).astype(np.float32)
 
 
+def occupancy_jitter(scene: Scene, seed: int = 0) -> np.ndarray:
+    """Per-cell offsets u in [0, 1)^3 (fp32 [R^3][3]) of the points a training-mode
+    occupancy update queries inside each cell (the random draw is an input)."""
+    rng = np.random.default_rng(60_000 + seed)
+    return rng.uniform(0.0, 1.0, size=(scene.occ_res ** 3, 3)).astype(np.float32)
+
+
 def random_points(scene: Scene, n: int, seed: int = 0, box: str = "norm") -> np.ndarray:
     """Uniform fp32 points in the normalised (or canonical) box."""
     rng = np.random.default_rng(40_000 + seed)

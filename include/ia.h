@@ -166,6 +166,20 @@ ia_status ia_get_transforms(ia_ctx *ctx, int pose, float *N, float *Ninv, float 
  *  sigma_out [R^3] fp32 device or NULL; bits_out [R^3 / 32] uint32 device or NULL. */
 ia_status ia_update_occupancy(ia_ctx *ctx, int pose, int mode, float *sigma_out,
                               uint32_t *bits_out, ia_render_stats *stats, void *stream);
+/* Training-mode occupancy (Sec. 3.3, training stage): one grid for the whole
+ * sequence, kept in the normalised space.  Each call queries the posed field of
+ * frame `pose` at one point per cell, x = norm_min + (c + u) * (norm_max -
+ * norm_min) / R (fp32, fixed order; u = jitter[c] in [0, 1)^3 from the caller's
+ * random draw, or the cell centre when jitter is NULL), folds it into the
+ * context's running density d <- max(decay * d, sigma) (the paper's "moving
+ * average" read as a decaying maximum; d starts at 0 when the context is
+ * created, and decay 0 restarts it), and replaces the training grid (the one
+ * ia_train_step uses with IA_OCC_UNION) by d thresholded at occ_tau and dilated.
+ *  jitter [R^3][3] fp32 device or NULL; decay in [0, 1]; density_out [R^3] fp32
+ *  device (the updated d) or NULL; bits_out [R^3 / 32] uint32 device or NULL. */
+ia_status ia_update_occupancy_ema(ia_ctx *ctx, int pose, const float *jitter, float decay, float *density_out,
+                                  uint32_t *bits_out, ia_render_stats *stats, void *stream);
+
 /* Threshold + dilation + packing alone, from a caller density array.
  *  sigma [R^3] fp32 device; bits_out [R^3 / 32] uint32 device.  Also installs
  *  the result as the render grid. */
@@ -199,13 +213,18 @@ ia_status ia_query_canonical(ia_ctx *ctx, int n, const float *x, float *sigma, f
 ia_status ia_render(ia_ctx *ctx, int pose, const ia_camera *cam, float *rgb, float *alpha,
                     ia_render_stats *stats, void *stream);
 
-/* A batch of training rays (all device pointers). */
+/* A batch of training rays (all device pointers), and optionally the points of
+ * the occupancy-based density regulariser (Eq. 12). */
 typedef struct ia_batch {
   int n_rays;                /* 1..2^24 */
   const float *origin;       /* [n][3] world-space ray origins */
   const float *direction;    /* [n][3] world-space unit directions */
   const int32_t *pose;       /* [n] index of a pose set by ia_set_pose */
   const float *target;       /* [n][3] target colours */
+  int n_reg;                 /* 0..2^24 regulariser points (0: no regulariser) */
+  const float *reg_x;        /* [n_reg][3] points in the normalised space of their pose */
+  const int32_t *reg_pose;   /* [n_reg] pose of each point */
+  float reg_weight;          /* weight of the regulariser term */
 } ia_batch;
 
 /* Floats of the skinning-grid and bone-transform gradients of ia_train_step
@@ -248,6 +267,13 @@ typedef struct ia_grads {
  * buffers are zeroed and S halves; after 1000 clean steps S doubles (at most
  * 2^24).  bf16 keeps S = 1.  ia_loss_scale reports S and whether the last step
  * was skipped.
+ *
+ * Regulariser (Eq. 12): with n_reg > 0 the loss gains
+ *   reg_weight / n_reg * sum of sigma(x) over the points x whose cell is empty
+ * in the occupancy grid the step uses (density is non-negative, so |sigma| =
+ * sigma); those points are evaluated with the posed field like the ray samples
+ * and their gradient (dL/dsigma = reg_weight / n_reg) goes through the same
+ * backward.  Points with an invalid pose or in occupied cells contribute nothing.
  *
  * Search: with ia_set_search(ctx, IA_SEARCH_PROPOSAL) (fp16 / bf16 only) each
  * sample's correspondence search starts from the proposal's top_k bones of the

@@ -58,7 +58,8 @@ class ProposalConfig(C.Structure):
 
 class Batch(C.Structure):
     _fields_ = [("n_rays", C.c_int), ("origin", C.c_void_p), ("direction", C.c_void_p), ("pose", C.c_void_p),
-                ("target", C.c_void_p)]
+                ("target", C.c_void_p), ("n_reg", C.c_int), ("reg_x", C.c_void_p), ("reg_pose", C.c_void_p),
+                ("reg_weight", C.c_float)]
 
 
 class Grads(C.Structure):
@@ -94,6 +95,7 @@ def lib():
             "ia_march_mask": [P, I, C.POINTER(Camera), P, V],
             "ia_train_step": [P, C.POINTER(Batch), I, P, P, C.POINTER(Grads), V],
             "ia_update_occupancy_static": [P, I, P, V],
+            "ia_update_occupancy_ema": [P, I, P, C.c_float, P, P, C.POINTER(RenderStats), V],
             "ia_loss_scale": [P, C.POINTER(C.c_float), C.POINTER(C.c_int32), V],
             "ia_train_stats": [P, C.POINTER(RenderStats), V],
             "ia_grad_sizes": [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
@@ -259,11 +261,15 @@ def ia_march_mask(ctx, pose, cam: Camera, slot_mask, stream=None):
 
 
 def ia_train_step(ctx, origin, direction, pose, target, loss, grads, occ_grid=IA_OCC_UNION, rgb_out=None,
-                  stream=None):
-    """grads: dict of device tensors table, mlp, skin, bones (overwritten); loss: device scalar (added to)."""
+                  stream=None, reg_x=None, reg_pose=None, reg_weight=0.0):
+    """grads: dict of device tensors table, mlp, skin, bones (overwritten); loss: device scalar (added to).
+    reg_x [n][3] / reg_pose [n]: points of the density regulariser (optional)."""
     b = Batch()
     b.n_rays = int(pose.shape[0])
     b.origin, b.direction, b.pose, b.target = _ptr(origin), _ptr(direction), _ptr(pose), _ptr(target)
+    if reg_x is not None:
+        b.n_reg = int(reg_pose.shape[0])
+        b.reg_x, b.reg_pose, b.reg_weight = _ptr(reg_x), _ptr(reg_pose), float(reg_weight)
     g = Grads()
     g.table, g.mlp, g.skin, g.bones = (_ptr(grads[k]) for k in ("table", "mlp", "skin", "bones"))
     _check(lib().ia_train_step(ctx, C.byref(b), occ_grid, _ptr(loss), _ptr(rgb_out), C.byref(g),
@@ -289,6 +295,15 @@ def ia_loss_scale(ctx, stream=None):
     sc, sk = C.c_float(), C.c_int32()
     _check(lib().ia_loss_scale(ctx, C.byref(sc), C.byref(sk), _stream(stream)), ctx)
     return sc.value, bool(sk.value)
+
+
+def ia_update_occupancy_ema(ctx, pose, jitter=None, decay=0.95, density_out=None, bits_out=None, stats=False,
+                            stream=None):
+    """Training-mode occupancy update (running density max(decay d, sigma), training grid replaced)."""
+    st = RenderStats() if stats else None
+    _check(lib().ia_update_occupancy_ema(ctx, pose, _ptr(jitter), float(decay), _ptr(density_out), _ptr(bits_out),
+                                         C.byref(st) if st is not None else None, _stream(stream)), ctx)
+    return st.as_dict() if st is not None else None
 
 
 def ia_update_occupancy_static(ctx, pose, bits_out=None, stream=None):

@@ -48,6 +48,7 @@ struct ia_ctx {
   uint32_t* d_occ = nullptr;
   uint32_t* d_occ_train = nullptr;
   float* d_sigma = nullptr;
+  float* d_occ_ema = nullptr;  // training-mode running density [R^3] (zero at creation)
   bool have_occ = false;
   // counters
   unsigned long long* d_stats = nullptr;
@@ -59,6 +60,8 @@ struct ia_ctx {
   size_t out_cap = 0;
   // training-step workspace
   int ray_cap = 0;
+  int reg_cap = 0;
+  int* d_reg_idx = nullptr;
   int* d_ray_n = nullptr;
   float* d_ray_dt = nullptr;
   int* d_ray_idx = nullptr;
@@ -327,6 +330,8 @@ ia_status ia_create(const ia_config* cfg, ia_ctx** out) {
   if (e == cudaSuccess) e = dalloc(&c->d_occ, words);
   if (e == cudaSuccess) e = dalloc(&c->d_occ_train, words);
   if (e == cudaSuccess) e = dalloc(&c->d_sigma, (size_t)R * R * R);
+  if (e == cudaSuccess) e = dalloc(&c->d_occ_ema, (size_t)R * R * R);
+  if (e == cudaSuccess) e = cudaMemset(c->d_occ_ema, 0, sizeof(float) * R * R * R);
   if (e == cudaSuccess) e = dalloc(&c->d_stats, (size_t)ST_COUNT);
   if (e == cudaSuccess) e = dalloc(&c->d_counter, (size_t)1);
   if (e == cudaSuccess) e = dalloc(&c->d_work, (size_t)2);
@@ -360,6 +365,7 @@ void ia_destroy(ia_ctx* c) {
   dfree(c->d_occ);
   dfree(c->d_occ_train);
   dfree(c->d_sigma);
+  dfree(c->d_occ_ema);
   dfree(c->d_stats);
   dfree(c->d_counter);
   dfree(c->d_work);
@@ -368,6 +374,7 @@ void ia_destroy(ia_ctx* c) {
   dfree(c->d_ray_n);
   dfree(c->d_ray_dt);
   dfree(c->d_ray_idx);
+  dfree(c->d_reg_idx);
   dfree(c->d_count);
   dfree(c->d_s_pos);
   dfree(c->d_s_out);
@@ -523,7 +530,7 @@ ia_status ia_update_occupancy(ia_ctx* c, int pose, int mode, float* sigma_out, u
   const size_t words = ((size_t)R * R * R + 31) / 32;
   float* sig = sigma_out ? sigma_out : c->d_sigma;
   IA_CUDA(c, cudaMemsetAsync(c->d_stats, 0, sizeof(unsigned long long) * ST_COUNT, s), "ia_update_occupancy");
-  IA_CUDA(c, launch_occ_density(occ_args(c, pose), box_dev(c), sig, c->d_stats, c->d_work, c->num_sms, s),
+  IA_CUDA(c, launch_occ_density(occ_args(c, pose), box_dev(c), nullptr, sig, c->d_stats, c->d_work, c->num_sms, s),
           "ia_update_occupancy: density");
   if (mode == IA_OCC_POSE) {
     IA_CUDA(c, launch_occ_bits(sig, R, c->cfg.occ_dilate, c->cfg.occ_tau, c->d_occ, nullptr, s),
@@ -535,6 +542,32 @@ ia_status ia_update_occupancy(ia_ctx* c, int pose, int mode, float* sigma_out, u
     IA_CUDA(c, launch_occ_bits(sig, R, c->cfg.occ_dilate, c->cfg.occ_tau, bits_out, c->d_occ_train, s),
             "ia_update_occupancy: union");
   }
+  if (stats) read_stats(c, stats, s);
+  return IA_OK;
+}
+
+ia_status ia_update_occupancy_ema(ia_ctx* c, int pose, const float* jitter, float decay, float* density_out,
+                                  uint32_t* bits_out, ia_render_stats* stats, void* stream) {
+  ia_status st = need_ready(c, pose, false);
+  if (st != IA_OK) return st;
+  if (!(decay >= 0.f && decay <= 1.f)) return fail(c, IA_ERR_ARG, "decay must be in [0, 1]");
+  if (jitter && !is_device_ptr(jitter)) return fail(c, IA_ERR_ARG, "jitter must be device memory");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int R = c->cfg.occ_res, n = R * R * R;
+  const size_t words = ((size_t)n + 31) / 32;
+  IA_CUDA(c, cudaMemsetAsync(c->d_stats, 0, sizeof(unsigned long long) * ST_COUNT, s), "ia_update_occupancy_ema");
+  IA_CUDA(c, launch_occ_density(occ_args(c, pose), box_dev(c), jitter, c->d_sigma, c->d_stats, c->d_work,
+                                c->num_sms, s),
+          "ia_update_occupancy_ema: density");
+  IA_CUDA(c, launch_occ_ema(c->d_sigma, c->d_occ_ema, n, decay, s), "ia_update_occupancy_ema: running density");
+  IA_CUDA(c, launch_occ_bits(c->d_occ_ema, R, c->cfg.occ_dilate, c->cfg.occ_tau, c->d_occ_train, nullptr, s),
+          "ia_update_occupancy_ema: bits");
+  if (bits_out)
+    IA_CUDA(c, cudaMemcpyAsync(bits_out, c->d_occ_train, words * 4, cudaMemcpyDeviceToDevice, s),
+            "ia_update_occupancy_ema");
+  if (density_out)
+    IA_CUDA(c, cudaMemcpyAsync(density_out, c->d_occ_ema, sizeof(float) * n, cudaMemcpyDeviceToDevice, s),
+            "ia_update_occupancy_ema");
   if (stats) read_stats(c, stats, s);
   return IA_OK;
 }
@@ -672,16 +705,19 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
   if (!b->origin || !b->direction || !b->pose || !b->target) return fail(c, IA_ERR_ARG, "null batch array");
   if (occ_grid != IA_OCC_POSE && occ_grid != IA_OCC_UNION) return fail(c, IA_ERR_ARG, "unknown occupancy grid");
   if (occ_grid == IA_OCC_POSE && !c->have_occ) return fail(c, IA_ERR_STATE, "no render grid (ia_update_occupancy)");
+  if (b->n_reg < 0 || b->n_reg > (1 << 24)) return fail(c, IA_ERR_ARG, "n_reg must be 0..2^24");
+  if (b->n_reg > 0 && (!b->reg_x || !b->reg_pose)) return fail(c, IA_ERR_ARG, "null regulariser array");
+  if (b->n_reg > 0 && !(std::isfinite(b->reg_weight))) return fail(c, IA_ERR_ARG, "reg_weight must be finite");
   cudaStream_t s = (cudaStream_t)stream;
   const int n = b->n_rays, N = c->cfg.max_samples;
-  const size_t cap = (size_t)n * N;
+  const size_t cap = (size_t)n * N + (size_t)b->n_reg;
   if (n > c->ray_cap || cap > c->s_cap) {
     IA_CUDA(c, cudaStreamSynchronize(s), "ia_train_step");
     c->ray_cap = 0;
     c->s_cap = 0;
     IA_CUDA(c, dalloc(&c->d_ray_n, (size_t)n), "ia_train_step: workspace");
     IA_CUDA(c, dalloc(&c->d_ray_dt, (size_t)n), "ia_train_step: workspace");
-    IA_CUDA(c, dalloc(&c->d_ray_idx, cap), "ia_train_step: workspace");
+    IA_CUDA(c, dalloc(&c->d_ray_idx, (size_t)n * N), "ia_train_step: workspace");
     IA_CUDA(c, dalloc(&c->d_count, (size_t)1), "ia_train_step: workspace");
     IA_CUDA(c, dalloc(&c->d_s_pos, cap), "ia_train_step: workspace");
     IA_CUDA(c, dalloc(&c->d_s_out, cap), "ia_train_step: workspace");
@@ -700,6 +736,12 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
     }
     c->ray_cap = n;
     c->s_cap = cap;
+  }
+  if (b->n_reg > c->reg_cap) {
+    IA_CUDA(c, cudaStreamSynchronize(s), "ia_train_step");
+    c->reg_cap = 0;
+    IA_CUDA(c, dalloc(&c->d_reg_idx, (size_t)b->n_reg), "ia_train_step: workspace");
+    c->reg_cap = b->n_reg;
   }
   if (c->cfg.precision != IA_FP32 && !c->d_scale) {
     IA_CUDA(c, dalloc(&c->d_scale, (size_t)1), "ia_train_step: loss scale");
@@ -754,6 +796,11 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
   a.s_grad = c->d_s_grad;
   a.s_dfeat = c->d_s_dfeat;
   a.work = c->d_work + 1;
+  a.n_reg = b->n_reg;
+  a.reg_x = b->reg_x;
+  a.reg_pose = b->reg_pose;
+  a.reg_weight = b->reg_weight;
+  a.reg_idx = c->d_reg_idx;
   a.act = c->d_act;
   a.loss = loss;
   a.rgb_out = rgb_out;
@@ -1079,7 +1126,7 @@ ia_status ia_update_occupancy_static(ia_ctx* c, int pose, uint32_t* bits_out, vo
   cudaStream_t s = (cudaStream_t)stream;
   // the density kernel writes all R^3 cells before the bits kernel reads them, so
   // the scratch needs no clearing; cells past R^3 are never read
-  IA_CUDA(c, launch_occ_density(occ_args(c, pose), box_dev(c), sigma, nullptr, c->d_work, c->num_sms, s),
+  IA_CUDA(c, launch_occ_density(occ_args(c, pose), box_dev(c), nullptr, sigma, nullptr, c->d_work, c->num_sms, s),
           "ia_update_occupancy_static: density");
   IA_CUDA(c, launch_occ_bits(sigma, R, c->cfg.occ_dilate, c->cfg.occ_tau, c->d_occ, nullptr, s),
           "ia_update_occupancy_static: bits");

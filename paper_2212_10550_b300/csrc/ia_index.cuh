@@ -107,4 +107,14 @@ __device__ __forceinline__ float3 cell_center(const BoxDev& bx, int cell) {
   return make_float3(x[0], x[1], x[2]);
 }
 
+// a point inside the cell: norm_min + (c + u) * cell size, u in [0, 1)^3 (fp32,
+// the operation order of cell_center, which is u = 1/2)
+__device__ __forceinline__ float3 cell_point(const BoxDev& bx, int cell, const float* __restrict__ u) {
+  const int c[3] = {cell % bx.R, (cell / bx.R) % bx.R, cell / (bx.R * bx.R)};
+  float x[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) x[a] = __fadd_rn(bx.nmin[a], __fmul_rn(__fadd_rn((float)c[a], u[a]), bx.cell_size[a]));
+  return make_float3(x[0], x[1], x[2]);
+}
+
 }  // namespace ia

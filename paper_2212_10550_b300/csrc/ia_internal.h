@@ -130,6 +130,12 @@ struct TrainArgs {
   int* pose_fill;        // [n_poses] fill counters (zeroed by the host)
   float4* s_dfeat;       // [samples][kIn / 4] dL/dfeatures (fp32, unscaled)
   unsigned* work;        // list counter of the sample kernel (zeroed by the host)
+  // occupancy-based density regulariser (Eq. 12)
+  int n_reg;
+  const float* reg_x;    // [n_reg][3] normalised space
+  const int32_t* reg_pose;
+  float reg_weight;
+  int* reg_idx;          // [n_reg] sample index of each point in an empty cell, else -1
 };
 
 // b1p[pose][j] = b1[j] + W1[j, pose columns] . theta_pose for every pose
@@ -208,8 +214,9 @@ size_t render_smem_bytes(int K);
 cudaError_t launch_pose_chain(int P, int nb, const int* parent, const double* rest, const double* theta,
                               const double* trans, float* N, float* Ninv, float* B0inv, cudaStream_t s);
 cudaError_t launch_blend(int P, int V, int nb, const float* W, const float* N, float4* M, cudaStream_t s);
-cudaError_t launch_occ_density(const PosedArgs& a, const BoxDev& box, float* sigma,
+cudaError_t launch_occ_density(const PosedArgs& a, const BoxDev& box, const float* jitter, float* sigma,
                                unsigned long long* stats, unsigned* work, int num_sms, cudaStream_t s);
+cudaError_t launch_occ_ema(const float* sigma, float* d, int n, float decay, cudaStream_t s);
 cudaError_t launch_occ_bits(const float* sigma, int R, int dilate, float tau, uint32_t* bits,
                             uint32_t* union_bits, cudaStream_t s);
 cudaError_t launch_query_posed(const PosedArgs& a, int n, const float* x, float* sigma, float* rgb,

@@ -179,8 +179,9 @@ size_t posed_smem_bytes(int threads) { return posed_smem_bytes_p<Prec::F32>(thre
 // iteration cap), searched with lane refill.
 template <Prec P>
 __global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS)
-    occ_density_kernel(const PosedArgs a, const BoxDev box, float* __restrict__ sigma,
-                       unsigned long long* __restrict__ stats, unsigned* __restrict__ work) {
+    occ_density_kernel(const PosedArgs a, const BoxDev box, const float* __restrict__ jitter,
+                       float* __restrict__ sigma, unsigned long long* __restrict__ stats,
+                       unsigned* __restrict__ work) {
   extern __shared__ float4 smem4[];
   PosedSmem sm = stage_posed<P>(stage_of(a), smem4);
   const int n = box.R * box.R * box.R;
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS)
     posed_field_list<P>(
         a.S, a.F, a.cfg, sm.fs, sm.list, min(kList, n - base),
         [&](int i, float3& xn, const float4*& M, const float*& Ni, int& pose) {
-          xn = cell_center(box, base + i);
+          xn = jitter ? cell_point(box, base + i, jitter + 3 * (size_t)(base + i)) : cell_center(box, base + i);
           M = a.S.M;
           Ni = sm.sNinv;
           pose = 0;
@@ -209,7 +210,7 @@ __global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS)
 }
 
 template <Prec P>
-static cudaError_t launch_occ_density_p(const PosedArgs& a, const BoxDev& box, float* sigma,
+static cudaError_t launch_occ_density_p(const PosedArgs& a, const BoxDev& box, const float* jitter, float* sigma,
                                         unsigned long long* stats, unsigned* work, int num_sms, cudaStream_t s) {
   const int n = box.R * box.R * box.R;
   const size_t smem = posed_smem_bytes_p<P>(256, a.search != 0);
@@ -222,17 +223,29 @@ static cudaError_t launch_occ_density_p(const PosedArgs& a, const BoxDev& box, f
   int blocks = num_sms * (per_sm < 1 ? 1 : per_sm);
   if (blocks > (lists + 7) / 8) blocks = (lists + 7) / 8;
   if ((e = cudaMemsetAsync(work, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
-  occ_density_kernel<P><<<blocks, 256, smem, s>>>(a, box, sigma, stats, work);
+  occ_density_kernel<P><<<blocks, 256, smem, s>>>(a, box, jitter, sigma, stats, work);
   return cudaGetLastError();
 }
 
-cudaError_t launch_occ_density(const PosedArgs& a, const BoxDev& box, float* sigma, unsigned long long* stats,
-                               unsigned* work, int num_sms, cudaStream_t s) {
+cudaError_t launch_occ_density(const PosedArgs& a, const BoxDev& box, const float* jitter, float* sigma,
+                               unsigned long long* stats, unsigned* work, int num_sms, cudaStream_t s) {
   switch (a.prec) {
-    case 1: return launch_occ_density_p<Prec::F16>(a, box, sigma, stats, work, num_sms, s);
-    case 2: return launch_occ_density_p<Prec::BF16>(a, box, sigma, stats, work, num_sms, s);
-    default: return launch_occ_density_p<Prec::F32>(a, box, sigma, stats, work, num_sms, s);
+    case 1: return launch_occ_density_p<Prec::F16>(a, box, jitter, sigma, stats, work, num_sms, s);
+    case 2: return launch_occ_density_p<Prec::BF16>(a, box, jitter, sigma, stats, work, num_sms, s);
+    default: return launch_occ_density_p<Prec::F32>(a, box, jitter, sigma, stats, work, num_sms, s);
   }
+}
+
+// training-mode occupancy (Sec. 3.3): the sequence's running density
+// d <- max(decay d, sigma) of one frame's query
+__global__ void occ_ema_kernel(const float* __restrict__ sigma, float* __restrict__ d, int n, float decay) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = fmaxf(__fmul_rn(decay, d[i]), sigma[i]);
+}
+
+cudaError_t launch_occ_ema(const float* sigma, float* d, int n, float decay, cudaStream_t s) {
+  occ_ema_kernel<<<(n + 255) / 256, 256, 0, s>>>(sigma, d, n, decay);
+  return cudaGetLastError();
 }
 
 // occupied = sigma > tau, dilated by a (2 dilate + 1)^3 cube clipped to the grid;

@@ -4,7 +4,8 @@
 //
 //   train_count_kernel,     world rays -> normalised space of each ray's pose,
 //   pose_scan_kernel,       occupied slots; samples compacted and grouped by
-//   train_emit_kernel       pose (count, per-pose offsets, emit)
+//   train_emit_kernel       pose (count, per-pose offsets, emit); the density
+//   (reg_*_kernel)          regulariser's points in empty cells join them
 //   train_sample_kernel     posed field f'(x') at every sample (same warp-level
 //                           correspondence search as rendering, per-lane pose)
 //   train_composite_kernel  per ray: front-to-back compositing, loss, and its
@@ -106,6 +107,48 @@ __global__ void train_emit_kernel(const TrainArgs a) {
     a.s_pos[base + j] = make_float4(x.x, x.y, x.z, __int_as_float(pose));
     idx[j] = base + j;
   });
+}
+
+// Regulariser points (Eq. 12): only points in empty cells of the step's grid
+// are samples.  Pass 1 counts them per pose (with the rays' counts) ...
+__global__ void reg_count_kernel(const TrainArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n_reg) return;
+  const int pose = a.reg_pose[i];
+  bool keep = false;
+  if (pose >= 0 && pose < a.n_poses) {
+    const float3 x = make_float3(a.reg_x[3 * i], a.reg_x[3 * i + 1], a.reg_x[3 * i + 2]);
+    const int cell = cell_of(a.box, x);
+    keep = !((__ldg(a.occ + (cell >> 5)) >> (cell & 31)) & 1u);
+  }
+  a.reg_idx[i] = keep ? 0 : -1;
+  if (keep) atomicAdd(a.pose_tot + pose, 1);
+}
+
+// ... pass 3 places them among their pose's samples
+__global__ void reg_emit_kernel(const TrainArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n_reg || a.reg_idx[i] < 0) return;
+  const int pose = a.reg_pose[i];
+  const int j = a.pose_tot[pose] + atomicAdd(a.pose_fill + pose, 1);
+  a.s_pos[j] = make_float4(a.reg_x[3 * i], a.reg_x[3 * i + 1], a.reg_x[3 * i + 2], __int_as_float(pose));
+  a.reg_idx[i] = j;
+}
+
+// after the forward: the regulariser's loss, weight / n_reg * sum sigma, and the
+// density gradient of its samples (sigma >= 0, so d|sigma| / d sigma = 1)
+__global__ void reg_grad_kernel(const TrainArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = i < a.n_reg ? a.reg_idx[i] : -1;
+  const float w = a.reg_weight / (float)a.n_reg;
+  float l = 0.f;
+  if (j >= 0) {
+    const float4 o = a.s_out[j];
+    l = w * o.x;
+    a.s_grad[j] = make_float4(o.x > 0.f ? w : 0.f, 0.f, 0.f, 0.f);
+  }
+  for (int d = 16; d > 0; d >>= 1) l += __shfl_down_sync(kFull, l, d);
+  if ((threadIdx.x & 31) == 0 && l != 0.f) atomicAdd(a.loss, l);
 }
 
 template <Prec P, bool kProp>
@@ -933,12 +976,21 @@ __global__ void loss_scale_kernel(const TrainArgs a, int dynamic) {
 cudaError_t launch_train(const TrainArgs& a, const CUtensorMap* map, int num_sms, cudaStream_t s) {
   cudaError_t e;
   const int rb = (a.n_rays + 127) / 128;
+  const int gb = (a.n_reg + 127) / 128;
   train_count_kernel<<<rb, 128, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (a.n_reg > 0) {
+    reg_count_kernel<<<gb, 128, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   pose_scan_kernel<<<1, 32, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   train_emit_kernel<<<rb, 128, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (a.n_reg > 0) {
+    reg_emit_kernel<<<gb, 128, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   const Prec P = (Prec)a.prec;
   if (a.P.search) {
     if ((e = launch_prop_bias(a.P.prop, a.P.cfg.nb, a.theta_all, a.n_poses, const_cast<float*>(a.P.prop.b1p), s)) !=
@@ -958,6 +1010,10 @@ cudaError_t launch_train(const TrainArgs& a, const CUtensorMap* map, int num_sms
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   train_composite_kernel<<<rb, 128, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (a.n_reg > 0) {
+    reg_grad_kernel<<<gb, 128, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   if (P == Prec::F32) {
     train_backward_kernel<<<num_sms * 4, 128, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -14,10 +14,17 @@ def declare(L):
     L.or_train.argtypes = [P(Model), P(Pose), C.c_int, P(C.c_uint32), C.c_int, P(C.c_float), P(C.c_float),
                            P(C.c_int32), P(C.c_double), P(C.c_double), P(C.c_int32), P(C.c_double),
                            P(C.c_double), P(C.c_double), P(C.c_double), C.c_int]
+    L.or_train_loss.restype = C.c_double
+    L.or_train_loss.argtypes = L.or_train.argtypes + [P(Loss)]
     L.or_density_reg.restype = C.c_double
     L.or_density_reg.argtypes = [P(Model), P(Pose), C.c_int, P(C.c_uint32), C.c_int, P(C.c_float), P(C.c_int32),
                                  C.c_double, P(C.c_int32), P(C.c_double), P(C.c_double), P(C.c_double),
                                  P(C.c_double)]
+
+
+class Loss(C.Structure):
+    _fields_ = [("huber", C.c_int), ("delta", C.c_double), ("w_rgb", C.c_double), ("w_alpha", C.c_double),
+                ("w_hard", C.c_double), ("alpha_target", C.POINTER(C.c_double))]
 
 
 def pose_array(poses):
@@ -34,13 +41,15 @@ def mlp_size(sc):
 
 
 def train(om, poses, occ_bits, origin, direction, pose_id, target, grad=True, nthreads=0, prop=None,
-          theta=None, fallbacks=None):
+          theta=None, fallbacks=None, loss=None):
     """Loss, per-ray colour and flags, and (if grad) the gradients as a dict:
     table [entries, F], mlp (packed W1, b1, W2, b2, W3, b3), skin [R, R, R, nb],
     bones [n_poses, nb, 12] (gradient w.r.t. the normalised-space N_k).
     With prop (an oracle.prop.PropModel) and theta ([n_poses, nb, 3] axis-angles)
     the proposal chooses each sample's starts; fallbacks (int32 [n], optional)
-    then receives each ray's count of samples that fell back to every bone."""
+    then receives each ray's count of samples that fell back to every bone.
+    loss: dict(huber, delta, w_rgb, w_alpha, w_hard, alpha_target) for the loss
+    set of Sec. 3.4 (default: L2 over the colour channels)."""
     from . import _p
     sc = om.scene
     n = len(pose_id)
@@ -61,7 +70,17 @@ def train(om, poses, occ_bits, origin, direction, pose_id, target, grad=True, nt
     common = [C.byref(om.m), arr, n_poses, _p(occ, C.c_uint32), n, _p(o, C.c_float), _p(d, C.c_float),
               _p(pid, C.c_int32), _p(tgt, C.c_double), _p(rgb, C.c_double), _p(flags, C.c_int32),
               *[_p(a, C.c_double) for a in args], nthreads]
-    if prop is None:
+    if loss is not None:
+        assert prop is None
+        lc = Loss()
+        lc.huber, lc.delta = int(loss.get("huber", 0)), float(loss.get("delta", 0.1))
+        lc.w_rgb, lc.w_alpha, lc.w_hard = (float(loss.get(k, d)) for k, d in
+                                           (("w_rgb", 1.0), ("w_alpha", 0.0), ("w_hard", 0.0)))
+        at = np.ascontiguousarray(loss.get("alpha_target", np.zeros(n)), dtype=np.float64)
+        assert at.shape == (n,)
+        lc.alpha_target = _p(at, C.c_double)
+        loss = om.L.or_train_loss(*common, C.byref(lc))
+    elif prop is None:
         loss = om.L.or_train(*common)
     else:
         th = np.ascontiguousarray(theta, dtype=np.float64).reshape(-1)

@@ -154,6 +154,19 @@ void or_occ_bits_f32(int R, int dilate, float tau, const float *sigma, uint32_t 
 /* Training step (oracle_grad.c): L2 loss over world rays of several poses and
  * its fp64 reverse-mode gradient, including the implicit-function gradient
  * through the root to the skinning grid and the bone transforms N. */
+/* Loss set of Sec. 3.4 per ray, averaged over the rays:
+ *   w_rgb * (huber ? rho_delta(|C - C_gt|_2) : sum_channels (C - C_gt)^2)     (Eq. 9)
+ * + w_alpha * |alpha - alpha_gt|                                              (Eq. 10)
+ * + w_hard * (-log(exp(-|alpha|) + exp(-|alpha - 1|)) + log(1 + exp(-1)))    (Eq. 11)
+ * with alpha = 1 - final transmittance and rho_delta the Huber function
+ * (r^2 / 2 below delta, delta (r - delta / 2) above). */
+typedef struct or_loss {
+  int huber;
+  double delta;
+  double w_rgb, w_alpha, w_hard;
+  const double *alpha_target; /* [n], read when w_alpha != 0 */
+} or_loss;
+
 double or_train(const or_model *m, const or_pose *poses, int n_poses, const uint32_t *occ, int n,
                 const float *o, const float *d, const int32_t *pose_id, const double *target,
                 double *rgb_out, int *ray_flags, double *g_table, double *g_mlp, double *g_skin,
@@ -189,6 +202,13 @@ double or_train_prop(const or_model *m, const or_pose *poses, int n_poses, const
                      double *rgb_out, int *ray_flags, double *g_table, double *g_mlp, double *g_skin,
                      double *g_bones, int nthreads, const or_prop *q, const double *theta_all,
                      int *ray_fallbacks);
+
+/* or_train with the loss set lc (NULL = or_train's L2). */
+double or_train_loss(const or_model *m, const or_pose *poses, int n_poses, const uint32_t *occ, int n,
+                     const float *o, const float *d, const int32_t *pose_id, const double *target,
+                     double *rgb_out, int *ray_flags, double *g_table, double *g_mlp, double *g_skin,
+                     double *g_bones, int nthreads, const or_loss *lc);
+
 /* Occupancy-based density regulariser (Eq. 12) at n normalised-space points x
  * [n][3] fp32 of poses pose_id [n]: L = weight / n * sum of sigma(x) over the
  * points whose cell (or_cell) is empty in occ.  Its gradient is ADDED to the

@@ -283,7 +283,9 @@ static double train_impl(const or_model *m, const or_pose *poses, int n_poses, c
                          const float *o, const float *d, const int32_t *pose_id, const double *target,
                          double *rgb_out, int *ray_flags, double *g_table, double *g_mlp, double *g_skin,
                          double *g_bones, int nthreads, const or_prop *q, const double *theta_all,
-                         int *ray_fallbacks) {
+                         int *ray_fallbacks, const or_loss *lc) {
+  static const or_loss l2 = {0, 0.0, 1.0, 0.0, 0.0, NULL};
+  if (!lc) lc = &l2;
   long entries = 0;
   {
     long T = 1L << m->log2_T;
@@ -316,13 +318,46 @@ static double train_impl(const or_model *m, const or_pose *poses, int n_poses, c
   double loss = 0.0;
   for (int r = 0; r < n; ++r) {
     const double *C = Cs + 4 * r;
-    double g[3];
+    double g[3], e[3], ee = 0.0;
     for (int k = 0; k < 3; ++k) {
-      double e = C[k] - target[3 * r + k];
-      loss += e * e / (double)n;
-      g[k] = 2.0 * e / (double)n;
+      e[k] = C[k] - target[3 * r + k];
+      ee += e[k] * e[k];
       if (rgb_out) rgb_out[3 * r + k] = C[k];
     }
+    /* colour term (Eq. 9): L2 over channels, or Huber of the colour error's norm */
+    double lr;
+    if (!lc->huber) {
+      lr = ee;
+      for (int k = 0; k < 3; ++k) g[k] = 2.0 * e[k];
+    } else {
+      const double rn = sqrt(ee);
+      if (rn <= lc->delta) {
+        lr = 0.5 * ee;
+        for (int k = 0; k < 3; ++k) g[k] = e[k];
+      } else {
+        lr = lc->delta * (rn - 0.5 * lc->delta);
+        for (int k = 0; k < 3; ++k) g[k] = lc->delta * e[k] / rn;
+      }
+    }
+    for (int k = 0; k < 3; ++k) g[k] *= lc->w_rgb / (double)n;
+    /* opacity terms of alpha = 1 - T: L1 to the mask (Eq. 10), hard surface (Eq. 11) */
+    const double alpha = 1.0 - Cs[4 * r + 3];
+    double la = 0.0, ga = 0.0;
+    if (lc->w_alpha != 0.0) {
+      const double da = alpha - lc->alpha_target[r];
+      la += lc->w_alpha * fabs(da);
+      ga += lc->w_alpha * (da > 0.0 ? 1.0 : (da < 0.0 ? -1.0 : 0.0));
+    }
+    if (lc->w_hard != 0.0) {
+      const double e0 = exp(-fabs(alpha)), e1 = exp(-fabs(alpha - 1.0));
+      la += lc->w_hard * (-log(e0 + e1) + log(1.0 + exp(-1.0)));
+      const double s0 = alpha > 0.0 ? 1.0 : (alpha < 0.0 ? -1.0 : 0.0);
+      const double s1 = alpha > 1.0 ? 1.0 : (alpha < 1.0 ? -1.0 : 0.0);
+      ga += lc->w_hard * (s0 * e0 + s1 * e1) / (e0 + e1);
+    }
+    ga /= (double)n;
+    loss += (lc->w_rgb * lr + la) / (double)n;
+    const double TN = Cs[4 * r + 3];
     if (!g_table || !g_mlp || !g_skin || !g_bones) continue;
     /* compositing backward, front to back */
     double T = 1.0, Cle[3] = {0.0, 0.0, 0.0};
@@ -338,7 +373,8 @@ static double train_impl(const or_model *m, const or_pose *poses, int n_poses, c
         cg += q->rgb[k] * g[k];
         rest += g[k] * (C[k] - Cle[k]);
       }
-      double dsig = dts[r] * (Tn * cg - rest);
+      /* d alpha / d sigma_i = delta T_N */
+      double dsig = dts[r] * (Tn * cg - rest) + ga * dts[r] * TN;
       backward_sample(m, poses, q, dsig, dc, g_table, g_mlp, g_skin, g_bones);
       T = Tn;
     }
@@ -355,7 +391,7 @@ double or_train(const or_model *m, const or_pose *poses, int n_poses, const uint
                 double *rgb_out, int *ray_flags, double *g_table, double *g_mlp, double *g_skin,
                 double *g_bones, int nthreads) {
   return train_impl(m, poses, n_poses, occ, n, o, d, pose_id, target, rgb_out, ray_flags, g_table, g_mlp, g_skin,
-                    g_bones, nthreads, NULL, NULL, NULL);
+                    g_bones, nthreads, NULL, NULL, NULL, NULL);
 }
 
 /* The same step with the correspondence proposal choosing each sample's starts
@@ -368,7 +404,17 @@ double or_train_prop(const or_model *m, const or_pose *poses, int n_poses, const
                      double *g_bones, int nthreads, const or_prop *q, const double *theta_all,
                      int *ray_fallbacks) {
   return train_impl(m, poses, n_poses, occ, n, o, d, pose_id, target, rgb_out, ray_flags, g_table, g_mlp, g_skin,
-                    g_bones, nthreads, q, theta_all, ray_fallbacks);
+                    g_bones, nthreads, q, theta_all, ray_fallbacks, NULL);
+}
+
+/* or_train with the paper's loss set (config lc; alpha of a ray = 1 - its final
+ * transmittance). */
+double or_train_loss(const or_model *m, const or_pose *poses, int n_poses, const uint32_t *occ, int n,
+                     const float *o, const float *d, const int32_t *pose_id, const double *target,
+                     double *rgb_out, int *ray_flags, double *g_table, double *g_mlp, double *g_skin,
+                     double *g_bones, int nthreads, const or_loss *lc) {
+  return train_impl(m, poses, n_poses, occ, n, o, d, pose_id, target, rgb_out, ray_flags, g_table, g_mlp, g_skin,
+                    g_bones, nthreads, NULL, NULL, NULL, lc);
 }
 
 double or_density_reg(const or_model *m, const or_pose *poses, int n_poses, const uint32_t *occ, int n,

@@ -225,7 +225,24 @@ typedef struct ia_batch {
   const float *reg_x;        /* [n_reg][3] points in the normalised space of their pose */
   const int32_t *reg_pose;   /* [n_reg] pose of each point */
   float reg_weight;          /* weight of the regulariser term */
+  const float *alpha_target; /* [n] mask values (Eq. 10); read when the loss has w_alpha != 0 */
 } ia_batch;
+
+/* The per-ray loss of ia_train_step (Sec. 3.4), averaged over the rays:
+ *   w_rgb * (rgb_loss == IA_LOSS_HUBER ? rho(|C - C_gt|_2) : sum_channels (C - C_gt)^2)   (Eq. 9)
+ * + w_alpha * |alpha - alpha_gt|                                                       (Eq. 10)
+ * + w_hard * (-log(exp(-|alpha|) + exp(-|alpha - 1|)) + log(1 + exp(-1)))              (Eq. 11)
+ * with alpha = 1 - the ray's final transmittance and rho the Huber function with
+ * threshold huber_delta (r^2 / 2 below, huber_delta (r - huber_delta / 2)
+ * above).  The paper prints no weights or threshold; a new context uses
+ * {IA_LOSS_L2, 0, 1, 0, 0}. */
+typedef enum ia_rgb_loss { IA_LOSS_L2 = 0, IA_LOSS_HUBER = 1 } ia_rgb_loss;
+typedef struct ia_loss {
+  int rgb_loss;       /* ia_rgb_loss */
+  float huber_delta;  /* > 0 for IA_LOSS_HUBER */
+  float w_rgb, w_alpha, w_hard;
+} ia_loss;
+ia_status ia_set_loss(ia_ctx *ctx, const ia_loss *loss);
 
 /* Floats of the skinning-grid and bone-transform gradients of ia_train_step
  * for the current skeleton and poses: skin_res^3 * n_bones and
@@ -244,8 +261,8 @@ typedef struct ia_grads {
  * loss): every ray is mapped into the normalised space of its pose, its slots
  * in occupied cells (occ_grid: IA_OCC_POSE = the render grid, IA_OCC_UNION = the
  * training grid) are evaluated with the posed field and composited front to
- * back (no early termination), and
- *   loss = (1 / n) sum_rays sum_channels (C - target)^2
+ * back (no early termination), and the loss set by ia_set_loss (by default
+ *   loss = (1 / n) sum_rays sum_channels (C - target)^2)
  * is added to *loss (device scalar; the caller zeroes it).  The backward is
  * exact reverse mode: compositing, activations, MLP, hash-table scatter-add, and
  * the implicit-function gradient through the root x* of LBS(x*) = x' (Eq. 7):
@@ -289,6 +306,15 @@ ia_status ia_train_step(ia_ctx *ctx, const ia_batch *batch, int occ_grid, float 
  * roots, and with the proposal search the proposed samples and fallbacks.
  * early_stopped is 0 (training composites every sample). */
 ia_status ia_train_stats(ia_ctx *ctx, ia_render_stats *stats, void *stream);
+
+/* One Adam step (beta1, beta2, eps; bias-corrected) on the context's canonical
+ * field, hash table and MLP (the fp32 masters; the fp16 shadow table is
+ * refreshed), from gradients laid out as ia_grads' table and mlp (device).  The
+ * moments live in the context and restart with ia_set_params.  In an fp16
+ * context a step that ia_train_step skipped on overflow changes nothing.  The
+ * skinning grid and the poses are inputs of the method here, not optimised. */
+ia_status ia_adam_step(ia_ctx *ctx, const float *g_table, const float *g_mlp, float lr, float beta1, float beta2,
+                       float eps, void *stream);
 
 /* The loss scale S after the last ia_train_step (host float) and whether that
  * step overflowed and was skipped (host int32, 1 = skipped); either may be NULL,

@@ -19,6 +19,7 @@ IA_OK, IA_ERR_ARG, IA_ERR_STATE, IA_ERR_CUDA, IA_ERR_OOM, IA_ERR_LIMIT = range(6
 IA_FP32, IA_FP16, IA_BF16 = 0, 1, 2
 IA_OCC_POSE, IA_OCC_UNION = 0, 1
 IA_SEARCH_ALL_BONES, IA_SEARCH_PROPOSAL = 0, 1
+IA_LOSS_L2, IA_LOSS_HUBER = 0, 1
 MAX_LEVELS = 16
 
 
@@ -59,7 +60,12 @@ class ProposalConfig(C.Structure):
 class Batch(C.Structure):
     _fields_ = [("n_rays", C.c_int), ("origin", C.c_void_p), ("direction", C.c_void_p), ("pose", C.c_void_p),
                 ("target", C.c_void_p), ("n_reg", C.c_int), ("reg_x", C.c_void_p), ("reg_pose", C.c_void_p),
-                ("reg_weight", C.c_float)]
+                ("reg_weight", C.c_float), ("alpha_target", C.c_void_p)]
+
+
+class Loss(C.Structure):
+    _fields_ = [("rgb_loss", C.c_int), ("huber_delta", C.c_float), ("w_rgb", C.c_float), ("w_alpha", C.c_float),
+                ("w_hard", C.c_float)]
 
 
 class Grads(C.Structure):
@@ -99,6 +105,8 @@ def lib():
             "ia_loss_scale": [P, C.POINTER(C.c_float), C.POINTER(C.c_int32), V],
             "ia_train_stats": [P, C.POINTER(RenderStats), V],
             "ia_grad_sizes": [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
+            "ia_set_loss": [P, C.POINTER(Loss)],
+            "ia_adam_step": [P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, V],
             "ia_proposal_init": [P, C.POINTER(ProposalConfig)],
             "ia_proposal_param_sizes": [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
             "ia_proposal_set_params": [P, P, P, V],
@@ -261,12 +269,13 @@ def ia_march_mask(ctx, pose, cam: Camera, slot_mask, stream=None):
 
 
 def ia_train_step(ctx, origin, direction, pose, target, loss, grads, occ_grid=IA_OCC_UNION, rgb_out=None,
-                  stream=None, reg_x=None, reg_pose=None, reg_weight=0.0):
+                  stream=None, reg_x=None, reg_pose=None, reg_weight=0.0, alpha_target=None):
     """grads: dict of device tensors table, mlp, skin, bones (overwritten); loss: device scalar (added to).
     reg_x [n][3] / reg_pose [n]: points of the density regulariser (optional)."""
     b = Batch()
     b.n_rays = int(pose.shape[0])
     b.origin, b.direction, b.pose, b.target = _ptr(origin), _ptr(direction), _ptr(pose), _ptr(target)
+    b.alpha_target = _ptr(alpha_target)
     if reg_x is not None:
         b.n_reg = int(reg_pose.shape[0])
         b.reg_x, b.reg_pose, b.reg_weight = _ptr(reg_x), _ptr(reg_pose), float(reg_weight)
@@ -274,6 +283,19 @@ def ia_train_step(ctx, origin, direction, pose, target, loss, grads, occ_grid=IA
     g.table, g.mlp, g.skin, g.bones = (_ptr(grads[k]) for k in ("table", "mlp", "skin", "bones"))
     _check(lib().ia_train_step(ctx, C.byref(b), occ_grid, _ptr(loss), _ptr(rgb_out), C.byref(g),
                                _stream(stream)), ctx)
+
+
+def ia_set_loss(ctx, rgb_loss=IA_LOSS_L2, huber_delta=0.0, w_rgb=1.0, w_alpha=0.0, w_hard=0.0):
+    """Loss of the training step (Sec. 3.4, Eq. 9-11)."""
+    l = Loss()
+    l.rgb_loss, l.huber_delta, l.w_rgb, l.w_alpha, l.w_hard = rgb_loss, huber_delta, w_rgb, w_alpha, w_hard
+    _check(lib().ia_set_loss(ctx, C.byref(l)), ctx)
+
+
+def ia_adam_step(ctx, g_table, g_mlp, lr, beta1=0.9, beta2=0.99, eps=1e-15, stream=None):
+    """Adam on the context's hash table and MLP from the step's gradients."""
+    _check(lib().ia_adam_step(ctx, _ptr(g_table), _ptr(g_mlp), float(lr), float(beta1), float(beta2), float(eps),
+                              _stream(stream)), ctx)
 
 
 def ia_grad_sizes(ctx):

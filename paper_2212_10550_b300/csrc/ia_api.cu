@@ -61,6 +61,11 @@ struct ia_ctx {
   // training-step workspace
   int ray_cap = 0;
   int reg_cap = 0;
+  ia_loss loss{IA_LOSS_L2, 0.f, 1.f, 0.f, 0.f};
+  // Adam state of the canonical field (table then MLP, one allocation each)
+  float* d_fm = nullptr;
+  float* d_fv = nullptr;
+  int field_step = 0;
   int* d_reg_idx = nullptr;
   int* d_ray_n = nullptr;
   float* d_ray_dt = nullptr;
@@ -375,6 +380,8 @@ void ia_destroy(ia_ctx* c) {
   dfree(c->d_ray_dt);
   dfree(c->d_ray_idx);
   dfree(c->d_reg_idx);
+  dfree(c->d_fm);
+  dfree(c->d_fv);
   dfree(c->d_count);
   dfree(c->d_s_pos);
   dfree(c->d_s_out);
@@ -456,6 +463,11 @@ ia_status ia_set_params(ia_ctx* c, const float* table, const float* mlp, void* s
   IA_CUDA(c, cudaMemcpyAsync(c->d_table, table, sizeof(float) * nt, cudaMemcpyDefault, s), "ia_set_params");
   IA_CUDA(c, cudaMemcpyAsync(c->d_mlp, mlp, sizeof(float) * nm, cudaMemcpyDefault, s), "ia_set_params");
   if (c->d_table_h) IA_CUDA(c, launch_table_to_half(c->d_table, c->d_table_h, c->n_entries, s), "ia_set_params");
+  if (c->d_fm) {  // new parameters: the Adam state restarts
+    dfree(c->d_fm);
+    dfree(c->d_fv);
+    c->field_step = 0;
+  }
   c->have_params = true;
   return IA_OK;
 }
@@ -708,6 +720,8 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
   if (b->n_reg < 0 || b->n_reg > (1 << 24)) return fail(c, IA_ERR_ARG, "n_reg must be 0..2^24");
   if (b->n_reg > 0 && (!b->reg_x || !b->reg_pose)) return fail(c, IA_ERR_ARG, "null regulariser array");
   if (b->n_reg > 0 && !(std::isfinite(b->reg_weight))) return fail(c, IA_ERR_ARG, "reg_weight must be finite");
+  if (c->loss.w_alpha != 0.f && !b->alpha_target)
+    return fail(c, IA_ERR_ARG, "the loss has an alpha term: batch->alpha_target is needed");
   cudaStream_t s = (cudaStream_t)stream;
   const int n = b->n_rays, N = c->cfg.max_samples;
   const size_t cap = (size_t)n * N + (size_t)b->n_reg;
@@ -801,6 +815,12 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
   a.reg_pose = b->reg_pose;
   a.reg_weight = b->reg_weight;
   a.reg_idx = c->d_reg_idx;
+  a.huber = c->loss.rgb_loss == IA_LOSS_HUBER ? 1 : 0;
+  a.huber_delta = c->loss.huber_delta;
+  a.w_rgb = c->loss.w_rgb;
+  a.w_alpha = c->loss.w_alpha;
+  a.w_hard = c->loss.w_hard;
+  a.alpha_target = b->alpha_target;
   a.act = c->d_act;
   a.loss = loss;
   a.rgb_out = rgb_out;
@@ -833,6 +853,46 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
     a.P.prop.b1p = c->d_pb1;
   }
   IA_CUDA(c, launch_train(a, &c->x_map, c->num_sms, s), "ia_train_step: kernels");
+  return IA_OK;
+}
+
+ia_status ia_adam_step(ia_ctx* c, const float* g_table, const float* g_mlp, float lr, float beta1, float beta2,
+                       float eps, void* stream) {
+  if (!c || !g_table || !g_mlp) return fail(c, IA_ERR_ARG, "null argument");
+  if (!c->have_params) return fail(c, IA_ERR_STATE, "ia_set_params has not been called");
+  if (!(lr >= 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+    return fail(c, IA_ERR_ARG, "bad Adam hyper-parameters");
+  if (!is_device_ptr(g_table) || !is_device_ptr(g_mlp)) return fail(c, IA_ERR_ARG, "gradients must be device memory");
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t nt = 0, nm = 0;
+  ia_param_sizes(c, &nt, &nm);
+  if (!c->d_fm) {
+    IA_CUDA(c, dalloc(&c->d_fm, (size_t)(nt + nm)), "ia_adam_step: moments");
+    IA_CUDA(c, dalloc(&c->d_fv, (size_t)(nt + nm)), "ia_adam_step: moments");
+    IA_CUDA(c, cudaMemsetAsync(c->d_fm, 0, sizeof(float) * (nt + nm), s), "ia_adam_step");
+    IA_CUDA(c, cudaMemsetAsync(c->d_fv, 0, sizeof(float) * (nt + nm), s), "ia_adam_step");
+    c->field_step = 0;
+  }
+  ++c->field_step;
+  // an overflowed reduced-precision step (zeroed gradients) leaves the state alone
+  const int* skip = c->cfg.precision == IA_FP16 ? c->d_overflow : nullptr;
+  IA_CUDA(c, launch_adam(c->d_table, g_table, c->d_fm, c->d_fv, nt, lr, c->field_step, beta1, beta2, eps, skip, s),
+          "ia_adam_step: table");
+  IA_CUDA(c, launch_adam(c->d_mlp, g_mlp, c->d_fm + nt, c->d_fv + nt, nm, lr, c->field_step, beta1, beta2, eps, skip,
+                         s),
+          "ia_adam_step: mlp");
+  if (c->d_table_h) IA_CUDA(c, launch_table_to_half(c->d_table, c->d_table_h, c->n_entries, s), "ia_adam_step");
+  return IA_OK;
+}
+
+ia_status ia_set_loss(ia_ctx* c, const ia_loss* l) {
+  if (!c || !l) return fail(c, IA_ERR_ARG, "null argument");
+  if (l->rgb_loss != IA_LOSS_L2 && l->rgb_loss != IA_LOSS_HUBER) return fail(c, IA_ERR_ARG, "unknown rgb_loss");
+  if (l->rgb_loss == IA_LOSS_HUBER && !(l->huber_delta > 0.f && std::isfinite(l->huber_delta)))
+    return fail(c, IA_ERR_ARG, "huber_delta must be positive");
+  if (!std::isfinite(l->w_rgb) || !std::isfinite(l->w_alpha) || !std::isfinite(l->w_hard))
+    return fail(c, IA_ERR_ARG, "loss weights must be finite");
+  c->loss = *l;
   return IA_OK;
 }
 
@@ -1061,7 +1121,8 @@ ia_status ia_proposal_train(ia_ctx* c, int n, const float* x, const int32_t* pos
     IA_CUDA(c, cudaMemsetAsync(a.loss, 0, sizeof(float), s), "ia_proposal_train");
     IA_CUDA(c, launch_prop_grad(a, s), "ia_proposal_train: gradient");
     ++c->adam_step;
-    IA_CUDA(c, launch_adam(c->d_pp, c->d_pg, c->d_pm, c->d_pv, (int64_t)np, lr, c->adam_step, s),
+    IA_CUDA(c, launch_adam(c->d_pp, c->d_pg, c->d_pm, c->d_pv, (int64_t)np, lr, c->adam_step, 0.9f, 0.999f, 1e-8f,
+                           nullptr, s),
             "ia_proposal_train: adam");
   }
   return IA_OK;

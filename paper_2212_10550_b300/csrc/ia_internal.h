@@ -136,6 +136,10 @@ struct TrainArgs {
   const int32_t* reg_pose;
   float reg_weight;
   int* reg_idx;          // [n_reg] sample index of each point in an empty cell, else -1
+  // loss set (Sec. 3.4)
+  int huber;
+  float huber_delta, w_rgb, w_alpha, w_hard;
+  const float* alpha_target;  // [n_rays] (w_alpha != 0)
 };
 
 // b1p[pose][j] = b1[j] + W1[j, pose columns] . theta_pose for every pose
@@ -205,8 +209,8 @@ struct PropTrainArgs {
 
 cudaError_t launch_prop_label(const PropLabelArgs& a, cudaStream_t s);
 cudaError_t launch_prop_grad(const PropTrainArgs& a, cudaStream_t s);
-cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, int step,
-                        cudaStream_t s);
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, int step, float b1,
+                        float b2, float eps, const int* skip, cudaStream_t s);
 
 size_t posed_smem_bytes(int threads);
 size_t render_smem_bytes(int K);

@@ -235,8 +235,9 @@ __global__ void __launch_bounds__(256) dense_grad_kernel(const float* __restrict
 }
 
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
-                            float* __restrict__ v, int64_t n, float lr, float c1, float c2) {
-  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+                            float* __restrict__ v, int64_t n, float lr, float c1, float c2, float b1, float b2,
+                            float eps, const int* __restrict__ skip) {
+  if (skip && *skip) return;  // a skipped (overflowed) step leaves parameters and moments alone
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float gi = g[i];
     const float mi = b1 * m[i] + (1.f - b1) * gi;
@@ -271,10 +272,11 @@ cudaError_t launch_prop_grad(const PropTrainArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, int step,
-                        cudaStream_t s) {
-  const float c1 = 1.f / (1.f - powf(0.9f, (float)step)), c2 = 1.f / (1.f - powf(0.999f, (float)step));
-  adam_kernel<<<592, 256, 0, s>>>(p, g, m, v, n, lr, c1, c2);
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, int step, float b1,
+                        float b2, float eps, const int* skip, cudaStream_t s) {
+  // bias corrections of step t (1-based): 1 / (1 - b^t)
+  const float c1 = 1.f / (1.f - powf(b1, (float)step)), c2 = 1.f / (1.f - powf(b2, (float)step));
+  adam_kernel<<<592, 256, 0, s>>>(p, g, m, v, n, lr, c1, c2, b1, b2, eps, skip);
   return cudaGetLastError();
 }
 

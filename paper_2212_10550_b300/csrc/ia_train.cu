@@ -200,8 +200,11 @@ static size_t train_sample_smem(bool prop) {
          sizeof(uint32_t) * (256 / 32) * list_smem_words(prop);
 }
 
-// front-to-back compositing of one ray, the loss, and the reverse sweep
-//   dL/dc_i = T_i alpha_i g,  dL/dsigma_i = delta (T_{i+1} c_i.g - g.(C - C_{<=i}))
+// Front-to-back compositing of one ray, the loss, and the reverse sweep
+//   dL/dc_i = T_i alpha_i g,
+//   dL/dsigma_i = delta (T_{i+1} c_i.g - g.(C - C_{<=i})) + g_alpha delta T_N
+// with g = dL/dC and g_alpha = dL/dalpha for the ray's alpha = 1 - T_N
+// (Sec. 3.2, Eq. 8; loss terms of Sec. 3.4, Eq. 9-11).
 __global__ void train_composite_kernel(const TrainArgs a) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = r < a.n_rays;
@@ -221,14 +224,45 @@ __global__ void train_composite_kernel(const TrainArgs a) {
     }
   }
   const float inv_n = 1.f / (float)a.n_rays;
-  float g[3], l = 0.f;
+  float e[3], ee = 0.f;
   for (int k = 0; k < 3; ++k) {
-    const float e = active ? C[k] - a.target[3 * r + k] : 0.f;
-    l = fmaf(e, e, l);
-    g[k] = 2.f * e * inv_n;
+    e[k] = active ? C[k] - a.target[3 * r + k] : 0.f;
+    ee = fmaf(e[k], e[k], ee);
     if (active && a.rgb_out) a.rgb_out[3 * r + k] = C[k];
   }
-  float lw = l * inv_n;  // loss = (1/n) sum_rays sum_channels (C - C_target)^2
+  // colour term (Eq. 9): L2 over channels, or Huber of the colour error's norm
+  float g[3], lr;
+  if (!a.huber) {
+    lr = ee;
+    for (int k = 0; k < 3; ++k) g[k] = 2.f * e[k];
+  } else {
+    const float rn = sqrtf(ee);
+    if (rn <= a.huber_delta) {
+      lr = 0.5f * ee;
+      for (int k = 0; k < 3; ++k) g[k] = e[k];
+    } else {
+      lr = a.huber_delta * (rn - 0.5f * a.huber_delta);
+      for (int k = 0; k < 3; ++k) g[k] = a.huber_delta * e[k] / rn;
+    }
+  }
+  for (int k = 0; k < 3; ++k) g[k] *= a.w_rgb * inv_n;
+  // opacity terms of alpha = 1 - T_N: L1 to the mask (Eq. 10), hard surface (Eq. 11)
+  const float alpha = -expm1f(-depth), TN = expf(-depth);
+  float la = 0.f, ga = 0.f;
+  if (active && a.w_alpha != 0.f) {
+    const float da = alpha - a.alpha_target[r];
+    la += a.w_alpha * fabsf(da);
+    ga += a.w_alpha * (da > 0.f ? 1.f : (da < 0.f ? -1.f : 0.f));
+  }
+  if (active && a.w_hard != 0.f) {
+    const float e0 = expf(-fabsf(alpha)), e1 = expf(-fabsf(alpha - 1.f));
+    la += a.w_hard * (-logf(e0 + e1) + 0.31326169f);  // log(1 + e^-1): zero at alpha in {0, 1}
+    const float s0 = alpha > 0.f ? 1.f : (alpha < 0.f ? -1.f : 0.f);
+    const float s1 = alpha > 1.f ? 1.f : (alpha < 1.f ? -1.f : 0.f);
+    ga += a.w_hard * (s0 * e0 + s1 * e1) / (e0 + e1);
+  }
+  ga *= inv_n;
+  float lw = active ? (a.w_rgb * lr + la) * inv_n : 0.f;
   for (int o = 16; o > 0; o >>= 1) lw += __shfl_down_sync(kFull, lw, o);
   if ((threadIdx.x & 31) == 0) atomicAdd(a.loss, lw);
   if (!active) return;
@@ -248,7 +282,7 @@ __global__ void train_composite_kernel(const TrainArgs a) {
     Cle[2] = fmaf(w, o.w, Cle[2]);
     const float cg = o.y * g[0] + o.z * g[1] + o.w * g[2];
     const float rest = g[0] * (C[0] - Cle[0]) + g[1] * (C[1] - Cle[1]) + g[2] * (C[2] - Cle[2]);
-    a.s_grad[s] = make_float4(dt * (Tn * cg - rest), w * g[0], w * g[1], w * g[2]);
+    a.s_grad[s] = make_float4(dt * (Tn * cg - rest) + ga * dt * TN, w * g[0], w * g[1], w * g[2]);
     depth += sd;
   }
 }

@@ -142,3 +142,70 @@ def test_autograd_function_matches_the_step(ia):
     torch.testing.assert_close(g_skin, g["skin"], rtol=1e-4, atol=1e-6 * g["skin"].abs().max().item())
     ref_loss = G.train(om, op, occ, rays["origin"], rays["direction"], rays["pose"], rays["target"], grad=False)[0]
     assert abs(loss.item() - ref_loss) <= 1e-5 * ref_loss
+
+
+def test_loss_set_matches_oracle(ia):
+    """Huber colour loss (Eq. 9), alpha L1 to a mask (Eq. 10) and the hard-surface
+    term (Eq. 11) together, against the oracle's loss set."""
+    sc, table, mlp, om, poses, op, occ, rays, _ = _case("tiny", 2, 3000)
+    alpha_gt = np.random.default_rng(12).uniform(0, 1, len(rays["pose"]))
+    cfg = dict(huber=1, delta=0.8, w_rgb=1.0, w_alpha=0.7, w_hard=0.3, alpha_target=alpha_gt)
+    ref_loss, _, _, ref = G.train(om, op, occ, rays["origin"], rays["direction"], rays["pose"], rays["target"],
+                                  loss=cfg)
+    ctx = make_ctx(ia, torch, sc, table, mlp)
+    ia.ia_set_pose(ctx, np.stack([p[0] for p in poses]), np.stack([p[1] for p in poses]))
+    ia.ia_set_occupancy(ctx, occ)
+    ia.ia_set_loss(ctx, ia.IA_LOSS_HUBER, 0.8, 1.0, 0.7, 0.3)
+    nt, nm = ia.ia_param_sizes(ctx)
+    g = dict(table=torch.zeros(nt, device="cuda"), mlp=torch.zeros(nm, device="cuda"),
+             skin=torch.zeros(sc.skin_res ** 3 * sc.n_bones, device="cuda"),
+             bones=torch.zeros(len(poses) * sc.n_bones * 12, device="cuda"))
+    dev = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in rays.items()}
+    loss = torch.zeros(1, device="cuda")
+    ia.ia_train_step(ctx, dev["origin"], dev["direction"], dev["pose"], dev["target"], loss, g,
+                     occ_grid=ia.IA_OCC_POSE, alpha_target=torch.from_numpy(alpha_gt.astype(np.float32)).cuda())
+    torch.cuda.synchronize()
+    ia.ia_destroy(ctx)
+    print(f"loss set: gpu {loss.item():.8e} oracle {ref_loss:.8e}")
+    assert abs(loss.item() - ref_loss) <= 1e-5 * ref_loss
+    for k in ("table", "mlp", "skin", "bones"):
+        a, b = g[k].cpu().numpy().astype(np.float64), ref[k].reshape(-1)
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        worst = np.abs(a - b).max() / max(np.abs(b).max(), 1e-30)
+        print(f"grad {k}: rel L2 {rel:.2e}, worst element / scale {worst:.2e}")
+        assert rel <= GRAD_REL_L2 and worst <= GRAD_ELEM, k
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_adam_step_matches_its_definition(ia, prec):
+    """Two Adam steps on the context's table and MLP against the update rule
+    written out in numpy (fp64)."""
+    sc = S.make_scene("tiny", 0)
+    table, mlp = S.make_field(sc, 0)
+    cfg = ia.make_config(n_levels=sc.n_levels, log2_table=sc.log2_table, level_res=sc.level_res,
+                         max_samples=sc.max_samples, precision=prec)
+    ctx = ia.ia_create(cfg)
+    ia.ia_set_skeleton(ctx, sc.parents, sc.rest_joints, sc.skin_grid, sc.canon_min, sc.canon_max,
+                       sc.norm_min, sc.norm_max)
+    p0 = [np.ascontiguousarray(table).reshape(-1).astype(np.float64), S.pack_mlp(mlp).astype(np.float64)]
+    ia.ia_set_params(ctx, torch.from_numpy(np.ascontiguousarray(table)).cuda(), torch.from_numpy(S.pack_mlp(mlp)).cuda())
+    rng = np.random.default_rng(7)
+    grads = [[rng.normal(0, s, p.shape) for p, s in zip(p0, (1e-3, 1e-2))] for _ in range(2)]
+    lr, b1, b2, eps = 1e-2, 0.9, 0.99, 1e-15
+    for gt, gm in grads:
+        ia.ia_adam_step(ctx, torch.from_numpy(gt.astype(np.float32)).cuda(), torch.from_numpy(gm.astype(np.float32)).cuda(),
+                        lr, b1, b2, eps)
+    nt, nm = ia.ia_param_sizes(ctx)
+    t_out, m_out = np.zeros(nt, np.float32), np.zeros(nm, np.float32)
+    ia.ia_get_params(ctx, t_out, m_out)
+    ia.ia_destroy(ctx)
+    for p, out, gs in ((p0[0], t_out, [g[0] for g in grads]), (p0[1], m_out, [g[1] for g in grads])):
+        m = np.zeros_like(p)
+        v = np.zeros_like(p)
+        x = p.copy()
+        for t, gg in enumerate(gs, start=1):
+            gg = gg.astype(np.float32).astype(np.float64)
+            m = b1 * m + (1 - b1) * gg
+            v = b2 * v + (1 - b2) * gg * gg
+            x = x - lr * (m / (1 - b1 ** t)) / (np.sqrt(v / (1 - b2 ** t)) + eps)
+        np.testing.assert_allclose(out, x, rtol=1e-5, atol=1e-6 * lr)

@@ -262,6 +262,104 @@ def time_train_step(torch, ia, sc, table, mlp, flush, steps, warmup, stream, n_r
             "loss_scale": scale, "last_step_skipped": skipped}
 
 
+def train_quality(torch, ia, sc, table, mlp, prop=None, iters=2000, batch=8192, n_frames=16, eval_every=250,
+                  lr=1e-2, start=("scratch",)):
+    """Time to quality of the whole training loop (Sec. 3.3-3.4) on a synthetic
+    video: 16 frames of 540x540 rendered by the library from the fixture field
+    (targets: colour and alpha mask), a learner that starts from an untrained
+    field (or a seeded perturbation of the fixture), and per iteration: 8192 random pixels of random
+    frames, the fp16 step with the loss set (Huber colour, alpha L1, hard
+    surface) and the density regulariser on 8192 random points, an Adam step;
+    every 16 iterations a training-mode occupancy update from a random frame.
+    PSNR of a held-out frame is taken every eval_every iterations (outside the
+    timed total)."""
+    dev = "cuda"
+    poses = [S.make_pose(sc, 300 + i) for i in range(n_frames + 1)]  # the last one is held out
+    th = np.stack([p[0] for p in poses])
+    tr = np.stack([p[1] for p in poses])
+    cam = S.make_camera(sc)
+    icam = ia.make_camera(cam["fx"], cam["fy"], cam["cx"], cam["cy"], cam["width"], cam["height"], cam["c2w"])
+    HW = cam["width"] * cam["height"]
+    gt = make_ctx(torch, ia, sc, table, mlp, 0, EARLY_T)
+    ia.ia_set_pose(gt, th, tr)
+    T_rgb = torch.zeros(n_frames + 1, HW, 3, device=dev)
+    T_a = torch.zeros(n_frames + 1, HW, device=dev)
+    for i in range(n_frames + 1):
+        ia.ia_update_occupancy(gt, i)
+        ia.ia_render(gt, i, icam, T_rgb[i], T_a[i])
+    ia.ia_destroy(gt)
+    o_np, d_np = S.pixel_rays(sc)
+    O = torch.from_numpy(o_np).to(dev)
+    D = torch.from_numpy(d_np).to(dev)
+    t0, m0 = S.init_field(sc, 0) if start[0] == "scratch" else S.perturb_field(table, mlp, 0, start[1], start[2])
+    ctx = make_ctx(torch, ia, sc, t0, m0, 1, EARLY_T)
+    ia.ia_set_pose(ctx, th, tr)
+    if prop is not None:
+        pc = S.proposal_config()
+        ia.ia_proposal_init(ctx, ia.make_proposal_config(pc["n_levels"], pc["log2_table"], pc["level_res"],
+                                                         pc["top_k"], pc["offset_weight"]))
+        ia.ia_proposal_set_params(ctx, prop[0], prop[1])
+        ia.ia_set_search(ctx, ia.IA_SEARCH_PROPOSAL)
+    ia.ia_set_loss(ctx, ia.IA_LOSS_HUBER, 0.1, 1.0, 1.0, 0.1)
+    R = sc.occ_res
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(123)
+    frame_rng = np.random.default_rng(124)
+    for i in range(n_frames):  # the sequence grid from every frame once
+        ia.ia_update_occupancy_ema(ctx, i, None, 1.0 if i else 0.0)
+    nt, nm = ia.ia_param_sizes(ctx)
+    ns, nbn = ia.ia_grad_sizes(ctx)
+    g = dict(table=torch.zeros(nt, device=dev), mlp=torch.zeros(nm, device=dev), skin=torch.zeros(ns, device=dev),
+             bones=torch.zeros(nbn, device=dev))
+    loss = torch.zeros(1, device=dev)
+    eval_rgb = torch.zeros(HW, 3, device=dev)
+    eval_a = torch.zeros(HW, device=dev)
+    nmin = torch.from_numpy(sc.norm_min.astype(np.float32)).to(dev)
+    ext = torch.from_numpy((sc.norm_max - sc.norm_min).astype(np.float32)).to(dev)
+
+    def psnr():
+        ia.ia_update_occupancy(ctx, n_frames)
+        ia.ia_render(ctx, n_frames, icam, eval_rgb, eval_a)
+        mse = torch.mean((eval_rgb - T_rgb[n_frames]) ** 2).item()
+        return float(10 * np.log10(1.0 / max(mse, 1e-12)))
+
+    curve = [(0, 0.0, round(psnr(), 3))]
+    timed = 0.0
+    losses = []
+    for it in range(1, iters + 1):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        f = torch.randint(0, n_frames, (batch,), device=dev, generator=gen, dtype=torch.int32)
+        px = torch.randint(0, HW, (batch,), device=dev, generator=gen)
+        rx = nmin + ext * torch.rand(batch, 3, device=dev, generator=gen)
+        rp = torch.randint(0, n_frames, (batch,), device=dev, generator=gen, dtype=torch.int32)
+        loss.zero_()
+        ia.ia_train_step(ctx, O[px].contiguous(), D[px].contiguous(), f, T_rgb[f.long(), px].contiguous(), loss, g,
+                         occ_grid=ia.IA_OCC_UNION, alpha_target=T_a[f.long(), px].contiguous(), reg_x=rx.contiguous(),
+                         reg_pose=rp, reg_weight=0.1)
+        ia.ia_adam_step(ctx, g["table"], g["mlp"], lr, 0.9, 0.99, 1e-15)
+        if it % 16 == 0:
+            jit = torch.rand(R ** 3, 3, device=dev, generator=gen)
+            ia.ia_update_occupancy_ema(ctx, int(frame_rng.integers(0, n_frames)), jit, 0.95)
+        torch.cuda.synchronize()
+        timed += time.perf_counter() - t
+        if it % 50 == 0:
+            losses.append(round(loss.item(), 5))
+        if it % eval_every == 0 or it == iters:
+            curve.append((it, round(timed, 3), round(psnr(), 3)))
+    ia.ia_destroy(ctx)
+    reach = {}
+    for db in (30, 40, 50):
+        hit = [c for c in curve if c[2] >= db]
+        reach[f"{db}dB"] = {"iteration": hit[0][0], "seconds": hit[0][1]} if hit else None
+    return {"iterations": iters, "batch_rays": batch, "frames": n_frames, "seconds": round(timed, 3),
+            "time_to_psnr": reach,
+            "iters_per_s": round(iters / timed, 1), "psnr_curve": curve, "loss_every_50": losses[:8] + losses[-4:],
+            "psnr_start": curve[0][2], "psnr_end": curve[-1][2], "start": list(start),
+            "what": "fp16 step (+proposal) with Huber/alpha/hard losses and the density regulariser, Adam, "
+                    "training-mode occupancy every 16 iterations; PSNR on a held-out frame"}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2212_10550_b300 as ia
@@ -278,6 +376,10 @@ def run_ours(args, rank, world, local_rank):
     rgb = torch.zeros(W * H, 3, device=dev)
     alpha = torch.zeros(W * H, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    if args.only == "quality":
+        q = train_quality(torch, ia, sc, table, mlp, None, iters=max(50, args.steps), eval_every=100)
+        return {"metric": METRIC, "partial": "training quality only", "train_quality": q} if rank == 0 else None
 
     if args.only == "train":
         tsteps = max(3, args.steps)
@@ -358,6 +460,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- fwd+bwd training steps: fp32 at 8192 rays; fp32 / fp16 / bf16 / fp16+proposal at 32768 rays
     tsteps = max(5, args.steps // 10)
     train = {"fp32_8192": time_train_step(torch, ia, sc, table, mlp, flush, tsteps, 3, stream)}
+    quality = train_quality(torch, ia, sc, table, mlp, prop_params, iters=2000, eval_every=100)
     for name, prec, pp in (("fp32", 0, None), ("fp16", 1, None), ("bf16", 2, None), ("fp16_proposal", 1, prop_params)):
         train[name] = time_train_step(torch, ia, sc, table, mlp, flush, tsteps, 3, stream, n_rays=32768,
                                       precision=prec, prop=pp)
@@ -425,6 +528,7 @@ def run_ours(args, rank, world, local_rank):
             "detail": {k: train[k] for k in ("fp32", "fp16", "bf16", "fp16_proposal")},
             "what": "32768 rays over 16 poses, <=128 slots, forward + hand-written backward, fp32 master "
                     "gradients; fp16 with dynamic loss scaling, weight gradients on tcgen05"},
+        "train_quality": quality,
         "roofline": {"kernel": "render_kernel", "bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                      "traffic": RENDER_DRAM_BYTES,
@@ -523,7 +627,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", default="all", choices=["all", "plain", "train"],
+    ap.add_argument("--only", default="all", choices=["all", "plain", "train", "quality"],
                     help="plain: time only the plain fp32 frames; train: only the fp32 and fp16 training "
                          "steps at 32768 rays (both used for profiling captures)")
     args = ap.parse_args()

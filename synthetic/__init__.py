@@ -351,6 +351,42 @@ def make_camera(scene: Scene, width: int | None = None, height: int | None = Non
                 cy=np.float32(0.5 * H), width=int(W), height=int(H), c2w=c2w)
 
 
+def pixel_rays(scene: Scene) -> tuple:
+    """World origin and unit direction (fp32 [H*W][3] each) of every pixel centre
+    of the default camera, pixel v * W + u, as make_ray_batch draws them."""
+    cam = make_camera(scene)
+    v, u = np.meshgrid(np.arange(cam["height"]), np.arange(cam["width"]), indexing="ij")
+    u, v = u.reshape(-1), v.reshape(-1)
+    dc = np.stack([(u + 0.5 - cam["cx"]) / cam["fx"], (v + 0.5 - cam["cy"]) / cam["fy"], np.ones(u.size)], axis=-1)
+    d = dc @ cam["c2w"][:, :3].astype(np.float64).T
+    d /= np.linalg.norm(d, axis=-1, keepdims=True)
+    o = np.broadcast_to(cam["c2w"][:, 3].astype(np.float64), d.shape)
+    return np.ascontiguousarray(o, dtype=np.float32), d.astype(np.float32)
+
+
+def init_field(scene: Scene, seed: int = 0):
+    """A seeded untrained field (the start of a training run from scratch): table
+    U(-1e-4, 1e-4), He-normal MLP weights, zero biases."""
+    rng = np.random.default_rng(80_000 + seed)
+    table = rng.uniform(-1e-4, 1e-4, size=(scene.n_table_entries(), scene.n_features)).astype(np.float32)
+    W, nin = scene.mlp_width, scene.mlp_in()
+    mlp = {}
+    for name, (o, n) in (("1", (W, nin)), ("2", (W, W)), ("3", (4, W))):
+        mlp["W" + name] = rng.normal(0.0, np.sqrt(2.0 / n), size=(o, n)).astype(np.float32)
+        mlp["b" + name] = np.zeros(o, np.float32)
+    return table, mlp
+
+
+def perturb_field(table: np.ndarray, mlp: dict, seed: int, table_std: float, weight_std: float):
+    """A seeded perturbation of a field (the start of a training run): Gaussian
+    noise on every table entry and on the MLP weights."""
+    rng = np.random.default_rng(70_000 + seed)
+    t = (table + rng.normal(0.0, table_std, table.shape)).astype(np.float32)
+    m = {k: (v + rng.normal(0.0, weight_std, v.shape)).astype(np.float32) if k.startswith("W") else v.copy()
+         for k, v in mlp.items()}
+    return t, m
+
+
 def make_ray_batch(scene: Scene, n_rays: int, n_poses: int, seed: int = 0) -> dict:
     """Random training rays: pose index, pixel, world origin/direction, target rgb.
 

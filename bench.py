@@ -360,6 +360,65 @@ def train_quality(torch, ia, sc, table, mlp, prop=None, iters=2000, batch=8192, 
                     "training-mode occupancy every 16 iterations; PSNR on a held-out frame"}
 
 
+def skip_ablation(torch, ia, sc, table, mlp, icam, rgb, alpha, stream, poses, frames=2):
+    """Empty-space skipping on and off (the Table 3 analogue): plain fp32 render
+    of a frame with the pose's occupancy grid against an all-occupied grid, and a
+    fp32 training step (8192 rays, 16 poses) on the union grid against an
+    all-occupied grid."""
+    ctx = make_ctx(torch, ia, sc, table, mlp, 0, EARLY_T)
+    R = sc.occ_res
+    full = np.full((R ** 3 + 31) // 32, 0xFFFFFFFF, dtype=np.uint32)
+    if R ** 3 % 32:
+        full[-1] = (1 << (R ** 3 % 32)) - 1
+    out = {}
+    for name, skip in (("skip", True), ("no_skip", False)):
+        ms = []
+        for th, tr in poses[:frames]:
+            ia.ia_set_pose(ctx, th[None], tr[None])
+            if skip:
+                ia.ia_update_occupancy(ctx, 0)
+            else:
+                ia.ia_set_occupancy(ctx, full)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ia.ia_render(ctx, 0, icam, rgb, alpha, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        out[f"render_ms_{name}"] = round(statistics.mean(ms), 3)
+    ia.ia_destroy(ctx)
+    # training step: union grid vs all occupied (IA_OCC_POSE carrying the full grid)
+    ctx = make_ctx(torch, ia, sc, table, mlp, 0, 0.0)
+    tposes = [S.make_pose(sc, 200 + i) for i in range(16)]
+    ia.ia_set_pose(ctx, np.stack([p[0] for p in tposes]), np.stack([p[1] for p in tposes]))
+    for i in range(16):
+        ia.ia_update_occupancy(ctx, i, ia.IA_OCC_UNION)
+    ia.ia_set_occupancy(ctx, full)
+    rb = S.make_ray_batch(sc, 8192, 16, seed=3)
+    dev = {k: torch.from_numpy(np.ascontiguousarray(rb[k])).cuda() for k in ("origin", "direction", "pose", "target")}
+    nt, nm = ia.ia_param_sizes(ctx)
+    ns, nbn = ia.ia_grad_sizes(ctx)
+    g = dict(table=torch.zeros(nt, device="cuda"), mlp=torch.zeros(nm, device="cuda"),
+             skin=torch.zeros(ns, device="cuda"), bones=torch.zeros(nbn, device="cuda"))
+    loss = torch.zeros(1, device="cuda")
+    for name, grid in (("skip", ia.IA_OCC_UNION), ("no_skip", ia.IA_OCC_POSE)):
+        ms = []
+        for it in range(4):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ia.ia_train_step(ctx, dev["origin"], dev["direction"], dev["pose"], dev["target"], loss, g, occ_grid=grid,
+                             stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if it:
+                ms.append(a.elapsed_time(b))
+        out[f"train_step_ms_{name}"] = round(statistics.mean(ms), 3)
+    ia.ia_destroy(ctx)
+    out["render_speedup"] = round(out["render_ms_no_skip"] / out["render_ms_skip"], 2)
+    out["train_speedup"] = round(out["train_step_ms_no_skip"] / out["train_step_ms_skip"], 2)
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2212_10550_b300 as ia
@@ -376,6 +435,10 @@ def run_ours(args, rank, world, local_rank):
     rgb = torch.zeros(W * H, 3, device=dev)
     alpha = torch.zeros(W * H, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    if args.only == "ablation":
+        ab = skip_ablation(torch, ia, sc, table, mlp, icam, rgb, alpha, stream, poses)
+        return {"metric": METRIC, "partial": "skip ablation only", "skip_ablation": ab} if rank == 0 else None
 
     if args.only == "quality":
         q = train_quality(torch, ia, sc, table, mlp, None, iters=max(50, args.steps), eval_every=100)
@@ -461,6 +524,7 @@ def run_ours(args, rank, world, local_rank):
     tsteps = max(5, args.steps // 10)
     train = {"fp32_8192": time_train_step(torch, ia, sc, table, mlp, flush, tsteps, 3, stream)}
     quality = train_quality(torch, ia, sc, table, mlp, prop_params, iters=2000, eval_every=100)
+    ablation = skip_ablation(torch, ia, sc, table, mlp, icam, rgb, alpha, stream, poses)
     for name, prec, pp in (("fp32", 0, None), ("fp16", 1, None), ("bf16", 2, None), ("fp16_proposal", 1, prop_params)):
         train[name] = time_train_step(torch, ia, sc, table, mlp, flush, tsteps, 3, stream, n_rays=32768,
                                       precision=prec, prop=pp)
@@ -529,6 +593,7 @@ def run_ours(args, rank, world, local_rank):
             "what": "32768 rays over 16 poses, <=128 slots, forward + hand-written backward, fp32 master "
                     "gradients; fp16 with dynamic loss scaling, weight gradients on tcgen05"},
         "train_quality": quality,
+        "skip_ablation": ablation,
         "roofline": {"kernel": "render_kernel", "bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                      "traffic": RENDER_DRAM_BYTES,
@@ -627,7 +692,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", default="all", choices=["all", "plain", "train", "quality"],
+    ap.add_argument("--only", default="all", choices=["all", "plain", "train", "quality", "ablation"],
                     help="plain: time only the plain fp32 frames; train: only the fp32 and fp16 training "
                          "steps at 32768 rays (both used for profiling captures)")
     args = ap.parse_args()

@@ -309,12 +309,15 @@ ia_status ia_train_stats(ia_ctx *ctx, ia_render_stats *stats, void *stream);
 
 /* One Adam step (beta1, beta2, eps; bias-corrected) on the context's canonical
  * field, hash table and MLP (the fp32 masters; the fp16 shadow table is
- * refreshed), from gradients laid out as ia_grads' table and mlp (device).  The
- * moments live in the context and restart with ia_set_params.  In an fp16
- * context a step that ia_train_step skipped on overflow changes nothing.  The
- * skinning grid and the poses are inputs of the method here, not optimised. */
-ia_status ia_adam_step(ia_ctx *ctx, const float *g_table, const float *g_mlp, float lr, float beta1, float beta2,
-                       float eps, void *stream);
+ * refreshed), from gradients laid out as ia_grads' table and mlp (device).
+ * With g_skin (ia_grads' skin layout, device; NULL keeps the grid fixed) the
+ * skinning-weight grid is a learnable parameter too (unconstrained: its rows
+ * are not renormalised), and every pose's blended transform grid is rebuilt
+ * from it.  The moments live in the context and restart with ia_set_params /
+ * ia_set_skeleton.  In an fp16 context a step that ia_train_step skipped on
+ * overflow changes nothing.  The bone transforms (poses) are inputs. */
+ia_status ia_adam_step(ia_ctx *ctx, const float *g_table, const float *g_mlp, const float *g_skin, float lr,
+                       float beta1, float beta2, float eps, void *stream);
 
 /* The loss scale S after the last ia_train_step (host float) and whether that
  * step overflowed and was skipped (host int32, 1 = skipped); either may be NULL,

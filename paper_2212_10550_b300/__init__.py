@@ -106,7 +106,7 @@ def lib():
             "ia_train_stats": [P, C.POINTER(RenderStats), V],
             "ia_grad_sizes": [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
             "ia_set_loss": [P, C.POINTER(Loss)],
-            "ia_adam_step": [P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, V],
+            "ia_adam_step": [P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, V],
             "ia_proposal_init": [P, C.POINTER(ProposalConfig)],
             "ia_proposal_param_sizes": [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
             "ia_proposal_set_params": [P, P, P, V],
@@ -292,10 +292,10 @@ def ia_set_loss(ctx, rgb_loss=IA_LOSS_L2, huber_delta=0.0, w_rgb=1.0, w_alpha=0.
     _check(lib().ia_set_loss(ctx, C.byref(l)), ctx)
 
 
-def ia_adam_step(ctx, g_table, g_mlp, lr, beta1=0.9, beta2=0.99, eps=1e-15, stream=None):
-    """Adam on the context's hash table and MLP from the step's gradients."""
-    _check(lib().ia_adam_step(ctx, _ptr(g_table), _ptr(g_mlp), float(lr), float(beta1), float(beta2), float(eps),
-                              _stream(stream)), ctx)
+def ia_adam_step(ctx, g_table, g_mlp, lr, beta1=0.9, beta2=0.99, eps=1e-15, g_skin=None, stream=None):
+    """Adam on the context's hash table and MLP (and the skinning grid with g_skin)."""
+    _check(lib().ia_adam_step(ctx, _ptr(g_table), _ptr(g_mlp), _ptr(g_skin), float(lr), float(beta1), float(beta2),
+                              float(eps), _stream(stream)), ctx)
 
 
 def ia_grad_sizes(ctx):

@@ -66,6 +66,9 @@ struct ia_ctx {
   float* d_fm = nullptr;
   float* d_fv = nullptr;
   int field_step = 0;
+  float* d_sm = nullptr;  // Adam state of the skinning-weight grid
+  float* d_sv = nullptr;
+  int skin_step = 0;
   int* d_reg_idx = nullptr;
   int* d_ray_n = nullptr;
   float* d_ray_dt = nullptr;
@@ -382,6 +385,8 @@ void ia_destroy(ia_ctx* c) {
   dfree(c->d_reg_idx);
   dfree(c->d_fm);
   dfree(c->d_fv);
+  dfree(c->d_sm);
+  dfree(c->d_sv);
   dfree(c->d_count);
   dfree(c->d_s_pos);
   dfree(c->d_s_out);
@@ -434,6 +439,11 @@ ia_status ia_set_skeleton(ia_ctx* c, int n_bones, const int32_t* parent, const d
   IA_CUDA(c, cudaMemcpy(c->d_rest, rest_joints, sizeof(double) * 3 * n_bones, cudaMemcpyHostToDevice),
           "ia_set_skeleton");
   IA_CUDA(c, cudaMemcpy(c->d_skin, skin_grid, sizeof(float) * V * n_bones, cudaMemcpyDefault), "ia_set_skeleton");
+  if (c->d_sm) {  // a new grid: its Adam state restarts
+    dfree(c->d_sm);
+    dfree(c->d_sv);
+    c->skin_step = 0;
+  }
   c->nb = n_bones;
   c->Rw = skin_res;
   for (int a = 0; a < 3; ++a) {
@@ -856,13 +866,15 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
   return IA_OK;
 }
 
-ia_status ia_adam_step(ia_ctx* c, const float* g_table, const float* g_mlp, float lr, float beta1, float beta2,
-                       float eps, void* stream) {
+ia_status ia_adam_step(ia_ctx* c, const float* g_table, const float* g_mlp, const float* g_skin, float lr,
+                       float beta1, float beta2, float eps, void* stream) {
   if (!c || !g_table || !g_mlp) return fail(c, IA_ERR_ARG, "null argument");
   if (!c->have_params) return fail(c, IA_ERR_STATE, "ia_set_params has not been called");
   if (!(lr >= 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
     return fail(c, IA_ERR_ARG, "bad Adam hyper-parameters");
-  if (!is_device_ptr(g_table) || !is_device_ptr(g_mlp)) return fail(c, IA_ERR_ARG, "gradients must be device memory");
+  if (!is_device_ptr(g_table) || !is_device_ptr(g_mlp) || (g_skin && !is_device_ptr(g_skin)))
+    return fail(c, IA_ERR_ARG, "gradients must be device memory");
+  if (g_skin && c->nb == 0) return fail(c, IA_ERR_STATE, "ia_set_skeleton has not been called");
   cudaStream_t s = (cudaStream_t)stream;
   int64_t nt = 0, nm = 0;
   ia_param_sizes(c, &nt, &nm);
@@ -882,6 +894,23 @@ ia_status ia_adam_step(ia_ctx* c, const float* g_table, const float* g_mlp, floa
                          s),
           "ia_adam_step: mlp");
   if (c->d_table_h) IA_CUDA(c, launch_table_to_half(c->d_table, c->d_table_h, c->n_entries, s), "ia_adam_step");
+  if (g_skin) {
+    // the learnable skinning-weight grid: its own moments, then every pose's blended grid again
+    const size_t V = (size_t)c->Rw * c->Rw * c->Rw, ns = V * c->nb;
+    if (!c->d_sm) {
+      IA_CUDA(c, dalloc(&c->d_sm, ns), "ia_adam_step: moments");
+      IA_CUDA(c, dalloc(&c->d_sv, ns), "ia_adam_step: moments");
+      IA_CUDA(c, cudaMemsetAsync(c->d_sm, 0, sizeof(float) * ns, s), "ia_adam_step");
+      IA_CUDA(c, cudaMemsetAsync(c->d_sv, 0, sizeof(float) * ns, s), "ia_adam_step");
+      c->skin_step = 0;
+    }
+    ++c->skin_step;
+    IA_CUDA(c, launch_adam(c->d_skin, g_skin, c->d_sm, c->d_sv, (int64_t)ns, lr, c->skin_step, beta1, beta2, eps, skip,
+                           s),
+            "ia_adam_step: skinning grid");
+    if (c->n_poses > 0)
+      IA_CUDA(c, launch_blend(c->n_poses, (int)V, c->nb, c->d_skin, c->d_N, c->d_M, s), "ia_adam_step: blend grid");
+  }
   return IA_OK;
 }
 

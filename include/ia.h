@@ -171,8 +171,8 @@ ia_status ia_update_occupancy(ia_ctx *ctx, int pose, int mode, float *sigma_out,
  * frame `pose` at one point per cell, x = norm_min + (c + u) * (norm_max -
  * norm_min) / R (fp32, fixed order; u = jitter[c] in [0, 1)^3 from the caller's
  * random draw, or the cell centre when jitter is NULL), folds it into the
- * context's running density d <- max(decay * d, sigma) (the paper's "moving
- * average" read as a decaying maximum; d starts at 0 when the context is
+ * context's running density d <- max(decay * d, sigma) (the paper's averaging
+ * of old and new values read as a decaying maximum; d starts at 0 when the context is
  * created, and decay 0 restarts it), and replaces the training grid (the one
  * ia_train_step uses with IA_OCC_UNION) by d thresholded at occ_tau and dilated.
  *  jitter [R^3][3] fp32 device or NULL; decay in [0, 1]; density_out [R^3] fp32

@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS)
   SampleStats st;
   for (int list = next_list(work); list * kList < n; list = next_list(work)) {
     const int base = list * kList;
-    posed_field_list<P>(
+    posed_field_list<P, ItemOrder::kPerLane>(
         a.S, a.F, a.cfg, sm.fs, sm.list, min(kList, n - base),
         [&](int i, float3& xn, const float4*& M, const float*& Ni, int& pose) {
           xn = jitter ? cell_point(box, base + i, jitter + 3 * (size_t)(base + i)) : cell_center(box, base + i);
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS)
   const int warps = gridDim.x * (blockDim.x >> 5);
   for (int base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kList; base < n;
        base += warps * kList) {
-    posed_field_list<P>(
+    posed_field_list<P, ItemOrder::kSampleMajor>(
         a.S, a.F, a.cfg, sm.fs, sm.list, min(kList, n - base),
         [&](int i, float3& xn, const float4*& M, const float*& Ni, int& pose) {
           const int j = base + i;
@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(kRenderThreads, IA_RENDER_MIN_BLOCKS) render_k
     __syncwarp();
     // ---- 3. correspondence search and field at the round's samples (lists of kList)
     for (int base = 0; base < total; base += kList) {
-      posed_field_list<P>(
+      posed_field_list<P, kProp ? ItemOrder::kStartMajor : ItemOrder::kPerLane>(
           a.P.S, a.P.F, a.P.cfg, sm.fs, sm.list, min(kList, total - base),
           [&](int i, float3& xn, const float4*& M, const float*& Ni, int& pose) {
             const int sidx = base + i;

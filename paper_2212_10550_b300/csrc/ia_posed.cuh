@@ -51,34 +51,42 @@ __device__ __forceinline__ void field_eval_lane(const FieldDev& F, const FieldSm
 
 // ---------------------------------------------------------------------------
 // Multi-start correspondence search and field evaluation (Sec. 3.1, Eq. 3-4, 7)
-// for a warp's list of m <= 32 samples, one per lane.  The bone-wise Broyden
-// chains are flattened: every loop step evaluates the blended grid once per
-// lane, whatever start or iteration the lane is on.  Each sample's distinct
-// roots go to the warp's shared-memory list; once the search is done the warp
-// evaluates the field at the roots (the tensor-core MLP needs the whole warp)
-// and keeps each sample's max-density root.
+// for a warp's list of m <= 32 samples.
+//
+// The work items are (sample, start) pairs (ItemOrder below): with a shared
+// queue a lane that finishes an item takes the next one, so a sample without a
+// root (every start runs to the iteration cap) no longer holds a whole warp
+// while the other lanes idle.  Every loop step evaluates the blended grid once per busy lane, whatever
+// start or iteration the lane is on.  Converged roots inside the canonical box
+// are merged into their sample's shared-memory list: a root within 1e-4 of a
+// listed one is the same root, and the list keeps the earlier start's (code and
+// position; found by each lane in parallel); new roots are appended one at a
+// time by the whole warp.  Once the items are
+// done the warp evaluates the field at the roots (the tensor-core MLP needs the
+// whole warp), lane i for sample i, and keeps each sample's max-density root
+// (ties to the lower start bone).
 //   src(i, xn, M, Ninv, pose): sample i's normalised point, blended grid, N^-1
 //   rows and pose index;  dst(i, out): its result.
 // With use_prop (reduced precision only) the proposal network picks each
 // sample's first starts: the top_k bones by logit (ties to the lower bone), the
-// first shifted by the predicted offset; when none of them yields a valid root
-// the search continues over every bone-wise start (the fallback).
+// first shifted by the predicted offset.  Those items run first; the samples
+// none of whose proposed starts yields a valid root then take every bone-wise
+// start (the fallback).
 // Kernels hand their warps lists from a counter shared by the grid, since lists
-// differ a lot in cost (a sample without a root runs every start to the cap).
-// (Longer lists with lanes refilled from them were measured: no faster, and
-// their root lists cost L1 capacity.)
+// differ a lot in cost.
 // ---------------------------------------------------------------------------
 
 constexpr int kList = 32;
 
 struct ListSmem {
-  float4* roots;     // [kMaxRoots][kList]  (x, y, z, start bone), slot-major: conflict-free rows
+  float4* roots;     // [kMaxRoots][kList]  (x, y, z, order << 8 | start bone), slot-major rows
   uint8_t* nroots;   // [kList]
+  uint8_t* fb;       // [kList] samples that fall back to every start
   float4* prop;      // [kList]  (bones b0 | b1 << 8, offset xyz), or null
 };
 
 __host__ __device__ constexpr int list_smem_words(bool prop) {
-  return kList * kMaxRoots * 4 + kList / 4 + (prop ? kList * 4 : 0);
+  return kList * kMaxRoots * 4 + kList / 4 + kList / 4 + (prop ? kList * 4 : 0);
 }
 
 __device__ __forceinline__ ListSmem list_smem(uint32_t* base, bool prop) {
@@ -86,38 +94,58 @@ __device__ __forceinline__ ListSmem list_smem(uint32_t* base, bool prop) {
   q.roots = reinterpret_cast<float4*>(base);
   q.prop = prop ? reinterpret_cast<float4*>(base + kList * kMaxRoots * 4) : nullptr;
   q.nroots = reinterpret_cast<uint8_t*>(base + kList * kMaxRoots * 4 + (prop ? kList * 4 : 0));
+  q.fb = q.nroots + kList;
   return q;
 }
 
 // A sample found more distinct roots than its list holds: evaluate the list and
-// the new root now and keep only the max-density one (ties to the earlier
-// start), so that no root is ever dropped from the selection.
+// the new root now and keep only the max-density one (ties to the lower start
+// bone), so that no root is ever dropped from the selection.
 template <Prec P>
 __device__ __noinline__ void compress_roots(const SkinDev& S, const float4* M, const FieldDev& F, const FieldSmem& fs,
-                                            float4* list, float3 xn, float3 xnew, int label_new) {
+                                            float4* list, float3 xn, float3 xnew, int code_new) {
   // list[j * kList]: root j of this sample
   PosedOut best;
   best.sigma = 0.f;
   best.rgb = best.xstar = make_float3(0.f, 0.f, 0.f);
   best.start = -1;
+  int best_code = code_new;
   for (int j = 0; j <= kMaxRoots; ++j) {
     const float4 o =
-        j < kMaxRoots ? list[j * kList] : make_float4(xnew.x, xnew.y, xnew.z, __int_as_float(label_new));
+        j < kMaxRoots ? list[j * kList] : make_float4(xnew.x, xnew.y, xnew.z, __int_as_float(code_new));
+    const int code = __float_as_int(o.w), bone = code & 0xff;
     const float3 xs = polish_root(S, M, make_float3(o.x, o.y, o.z), xn);
     float sig;
     float3 rgb;
     field_eval_lane<P>(F, fs, xs, sig, rgb);
-    take_best(best, sig, rgb, xs, __float_as_int(o.w));
+    // take_best's rule, with the list code kept alongside
+    if (sig > best.sigma || (sig == best.sigma && best.start >= 0 && bone < best.start) || best.start < 0) {
+      best.sigma = sig;
+      best.rgb = rgb;
+      best.xstar = xs;
+      best.start = bone;
+      best_code = code;
+    }
   }
-  list[0] = make_float4(best.xstar.x, best.xstar.y, best.xstar.z, __int_as_float(best.start));
+  list[0] = make_float4(best.xstar.x, best.xstar.y, best.xstar.z, __int_as_float(best_code));
 }
 
-template <Prec P, class Src, class Dst>
+// How a list's (sample, start) items meet the lanes:
+//   kPerLane      lane i runs sample i's starts in order (no sharing)
+//   kSampleMajor  a shared queue, every start of sample 0, then of sample 1, ...
+//   kStartMajor   a shared queue, start 0 of every sample, then start 1, ...
+// (measured: the plain 24-start render keeps its L1 locality best per lane; the
+// proposal's render, whose fallbacks are few but long, and the training forward
+// gain from the shared queue, start-major and sample-major respectively)
+enum class ItemOrder { kPerLane, kSampleMajor, kStartMajor };
+
+template <Prec P, ItemOrder kOrder, class Src, class Dst>
 __device__ __forceinline__ void posed_field_list(const SkinDev& S, const FieldDev& F, const SolveCfg& cfg,
-                                                  const FieldSmem& fs, const ListSmem& qs, int m, Src src, Dst dst,
-                                                  SampleStats& st, const PropDev& Q = PropDev{},
-                                                  bool use_prop = false) {
+                                                 const FieldSmem& fs, const ListSmem& qs, int m, Src src, Dst dst,
+                                                 SampleStats& st, const PropDev& Q = PropDev{},
+                                                 bool use_prop = false) {
   const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
   // ---- proposed starts of every sample of the list (warp MMA)
   if constexpr (P != Prec::F32) {
     if (use_prop) {
@@ -145,125 +173,259 @@ __device__ __forceinline__ void posed_field_list(const SkinDev& S, const FieldDe
       __syncwarp();  // every lane has read its row before the staging area is reused
     }
   }
-  // ---- search: lane i takes sample i
-  int k = 0, it = 0, nr = 0, label = 0, phase = 2, nprop = 0, pk0 = 0, pk1 = 0;
-  const int cur = lane;
-  float3 xn = make_float3(0.f, 0.f, 0.f), x = xn, r = xn, dx = xn, poff = xn;
-  const float4* M = nullptr;
-  const float* Ninv = nullptr;
-  float H[9];
+  if (lane < m) qs.nroots[lane] = 0;
+  __syncwarp();
+  const int nprop = use_prop ? min(Q.top_k, cfg.nb) : 0;
+  // ---- stage 0: the proposed starts (or every start without the proposal);
+  //      stage 1: every start of the samples whose proposed starts found no root
+  for (int stage = 0; stage < (use_prop ? 2 : 1); ++stage) {
+    int per, n_items, ns;  // starts per sample, items, samples of the stage
+    if (stage == 0) {
+      per = use_prop ? nprop : cfg.nb;
+      ns = m;
+      n_items = m * per;
+    } else {
+      const bool fall = lane < m && qs.nroots[lane] == 0;
+      const unsigned fm = __ballot_sync(kFull, fall);
+      if (fall) {
+        qs.fb[__popc(fm & lt)] = (uint8_t)lane;
+        st.fallbacks++;
+      }
+      __syncwarp();
+      per = cfg.nb;
+      ns = __popc(fm);
+      n_items = ns * per;
+    }
+    // shared queue: idx -> (sample, start) by a multiply-high division (exact
+    // for idx < 2^16; ns == 1 and per == 1 need none: 2^32 does not fit)
+    const int dv = kOrder == ItemOrder::kStartMajor ? ns : per;
+    const unsigned magic = dv > 1 ? 0xFFFFFFFFu / (unsigned)dv + 1u : 0u;
+    const bool mine = stage == 0 ? lane < m : (lane < m && qs.nroots[lane] == 0);  // kPerLane
+    int next = 0;  // warp-uniform: items handed out so far
+    int jl = -1;   // kPerLane: this lane's last start
+    int loaded = -1;
+    bool need = true;
+    int phase = 2, cur = 0, label = 0, order = 0, it = 0;
+    bool shift = false;
+    float3 xn = make_float3(0.f, 0.f, 0.f), x = xn, r = xn, dx = xn, poff = xn;
+    const float4* M = nullptr;
+    const float* Ninv = nullptr;
+    float H[9];
 #pragma unroll
-  for (int q = 0; q < 9; ++q) H[q] = 0.f;
-  if (lane < m) {
-    int pose;
-    src(lane, xn, M, Ninv, pose);
-    phase = 0;
-    if (use_prop) {
-      nprop = min(Q.top_k, cfg.nb);
-      const float4 pp = qs.prop[lane];
-      const int bb = __float_as_int(pp.x);
-      pk0 = bb & 0xff;
-      pk1 = (bb >> 8) & 0xff;
-      poff = make_float3(pp.y, pp.z, pp.w);
-    }
-  }
-  while (__any_sync(kFull, phase != 2)) {
-    float3 q = x;
-    if (phase == 0) {
-      // starts 0 .. nprop-1 are proposed bones, the rest every bone in order
-      const bool proposed = k < nprop;
-      label = proposed ? (k == 0 ? pk0 : pk1) : k - nprop;
-      const float* A = Ninv + 12 * label;
-      q = make_float3(A[0] * xn.x + A[1] * xn.y + A[2] * xn.z + A[3], A[4] * xn.x + A[5] * xn.y + A[6] * xn.z + A[7],
-                      A[8] * xn.x + A[9] * xn.y + A[10] * xn.z + A[11]);
-      if (proposed && k == 0) q = make_float3(q.x + poff.x, q.y + poff.y, q.z + poff.z);
-    } else if (phase == 1) {
-      q = make_float3(x.x + dx.x, x.y + dx.y, x.z + dx.z);
-    }
-    float Mx[12];
-    if (phase != 2) blend_value(S, M, q, Mx);
-    bool finish = false, conv = false;
-    if (phase == 0) {
-      st.starts++;
-      const float3 y = apply34(Mx, q);
-      x = q;
-      r = make_float3(y.x - xn.x, y.y - xn.y, y.z - xn.z);
-      // initial inverse Jacobian: LBS with the weights frozen at x0, (sum_i w_i R_i)^-1
-      const float J0[9] = {Mx[0], Mx[1], Mx[2], Mx[4], Mx[5], Mx[6], Mx[8], Mx[9], Mx[10]};
-      it = 0;
-      if (!inv3(J0, H)) finish = true;
-    } else if (phase == 1) {
-      const float3 y = apply34(Mx, q);
-      const float3 rn = make_float3(y.x - xn.x, y.y - xn.y, y.z - xn.z);
-      const float3 dr = make_float3(rn.x - r.x, rn.y - r.y, rn.z - r.z);
-      x = q;
-      r = rn;
-      ++it;
-      st.iters++;
-      // good Broyden: H += (dx - H dr)(dx^T H) / (dx^T H dr)
-      const float3 d = dx;
-      const float u0 = H[0] * dr.x + H[1] * dr.y + H[2] * dr.z;
-      const float u1 = H[3] * dr.x + H[4] * dr.y + H[5] * dr.z;
-      const float u2 = H[6] * dr.x + H[7] * dr.y + H[8] * dr.z;
-      const float den = d.x * u0 + d.y * u1 + d.z * u2;
-      if (fabsf(den) > 1e-12f) {
-        const float rden = 1.f / den;  // one reciprocal for the three quotients
-        const float a0 = (d.x - u0) * rden, a1 = (d.y - u1) * rden, a2 = (d.z - u2) * rden;
-        const float b0 = d.x * H[0] + d.y * H[3] + d.z * H[6];
-        const float b1 = d.x * H[1] + d.y * H[4] + d.z * H[7];
-        const float b2 = d.x * H[2] + d.y * H[5] + d.z * H[8];
-        H[0] += a0 * b0; H[1] += a0 * b1; H[2] += a0 * b2;
-        H[3] += a1 * b0; H[4] += a1 * b1; H[5] += a1 * b2;
-        H[6] += a2 * b0; H[7] += a2 * b1; H[8] += a2 * b2;
-      }
-    }
-    if (phase != 2 && !finish) {
-      const float rr = r.x * r.x + r.y * r.y + r.z * r.z;
-      if (rr < cfg.tol2) {
-        conv = true;
-        finish = true;
-      } else if (it >= cfg.max_iter) {
-        finish = true;
-      } else {
-        dx = make_float3(-(H[0] * r.x + H[1] * r.y + H[2] * r.z), -(H[3] * r.x + H[4] * r.y + H[5] * r.z),
-                         -(H[6] * r.x + H[7] * r.y + H[8] * r.z));
-        phase = 1;
-      }
-    }
-    if (finish) {
-      float4* list = qs.roots + cur;
-      if (conv && in_box(S, x)) {
-        st.converged++;
-        bool dup = false;
-        for (int j = 0; j < nr; ++j) {
-          const float4 o = list[j * kList];
-          const float ddx = x.x - o.x, ddy = x.y - o.y, ddz = x.z - o.z;
-          if (ddx * ddx + ddy * ddy + ddz * ddz < 1e-8f) { dup = true; break; }
+    for (int q = 0; q < 9; ++q) H[q] = 0.f;
+    while (true) {
+      // lanes without an item take the next one
+      bool got = false;
+      int i = 0, j = 0;
+      if constexpr (kOrder == ItemOrder::kPerLane) {
+        if (need) {
+          need = false;
+          phase = 2;
+          if (mine && jl + 1 < per) {
+            got = true;
+            i = lane;
+            j = ++jl;
+          }
         }
-        if (!dup) {
-          st.roots++;
-          if (nr < kMaxRoots) {
-            list[kList * nr++] = make_float4(x.x, x.y, x.z, __int_as_float(label));
-          } else {
-            compress_roots<P>(S, M, F, fs, list, xn, x, label);
-            nr = 1;
+      } else {
+        const unsigned needm = __ballot_sync(kFull, need);
+        if (needm) {
+          const int idx = next + __popc(needm & lt);
+          next += __popc(needm);
+          if (need) {
+            need = false;
+            phase = 2;
+            if (idx < n_items) {
+              got = true;
+              const int q = dv > 1 ? (int)__umulhi((unsigned)idx, magic) : idx, rm = idx - q * dv;
+              if (kOrder == ItemOrder::kStartMajor) { j = q; i = rm; }
+              else { i = q; j = rm; }
+            }
           }
         }
       }
-      ++k;
-      if (nprop > 0 && k == nprop) {
-        if (nr > 0) k = nprop + cfg.nb;  // a proposed start found a root: done
-        else st.fallbacks++;             // none did: every bone-wise start follows
-      }
-      if (k < nprop + cfg.nb) {
+      if (got) {
+        cur = (stage == 0 || kOrder == ItemOrder::kPerLane) ? i : qs.fb[i];
+        if (cur != loaded) {  // consecutive items of one sample reuse its point and grids
+          int pose;
+          src(cur, xn, M, Ninv, pose);
+          loaded = cur;
+        }
+        if (stage == 0 && use_prop) {
+          const float4 pp = qs.prop[cur];
+          const int bb = __float_as_int(pp.x);
+          label = j == 0 ? (bb & 0xff) : ((bb >> 8) & 0xff);
+          shift = j == 0;
+          poff = make_float3(pp.y, pp.z, pp.w);
+          order = j;
+        } else {
+          label = j;
+          shift = false;
+          order = (stage == 0 ? 0 : nprop) + j;
+        }
         phase = 0;
+      }
+      if (!__any_sync(kFull, phase != 2)) break;
+      float3 q = x;
+      if (phase == 0) {
+        const float* A = Ninv + 12 * label;
+        q = make_float3(A[0] * xn.x + A[1] * xn.y + A[2] * xn.z + A[3], A[4] * xn.x + A[5] * xn.y + A[6] * xn.z + A[7],
+                        A[8] * xn.x + A[9] * xn.y + A[10] * xn.z + A[11]);
+        if (shift) q = make_float3(q.x + poff.x, q.y + poff.y, q.z + poff.z);
+      } else if (phase == 1) {
+        q = make_float3(x.x + dx.x, x.y + dx.y, x.z + dx.z);
+      }
+      float Mx[12];
+      if (phase != 2) blend_value(S, M, q, Mx);
+      bool finish = false, conv = false;
+      if (phase == 0) {
+        st.starts++;
+        const float3 y = apply34(Mx, q);
+        x = q;
+        r = make_float3(y.x - xn.x, y.y - xn.y, y.z - xn.z);
+        // initial inverse Jacobian: LBS with the weights frozen at x0, (sum_i w_i R_i)^-1
+        const float J0[9] = {Mx[0], Mx[1], Mx[2], Mx[4], Mx[5], Mx[6], Mx[8], Mx[9], Mx[10]};
+        it = 0;
+        if (!inv3(J0, H)) finish = true;
+      } else if (phase == 1) {
+        const float3 y = apply34(Mx, q);
+        const float3 rn = make_float3(y.x - xn.x, y.y - xn.y, y.z - xn.z);
+        const float3 dr = make_float3(rn.x - r.x, rn.y - r.y, rn.z - r.z);
+        x = q;
+        r = rn;
+        ++it;
+        st.iters++;
+        // good Broyden: H += (dx - H dr)(dx^T H) / (dx^T H dr)
+        const float3 d = dx;
+        const float u0 = H[0] * dr.x + H[1] * dr.y + H[2] * dr.z;
+        const float u1 = H[3] * dr.x + H[4] * dr.y + H[5] * dr.z;
+        const float u2 = H[6] * dr.x + H[7] * dr.y + H[8] * dr.z;
+        const float den = d.x * u0 + d.y * u1 + d.z * u2;
+        if (fabsf(den) > 1e-12f) {
+          const float rden = 1.f / den;  // one reciprocal for the three quotients
+          const float a0 = (d.x - u0) * rden, a1 = (d.y - u1) * rden, a2 = (d.z - u2) * rden;
+          const float b0 = d.x * H[0] + d.y * H[3] + d.z * H[6];
+          const float b1 = d.x * H[1] + d.y * H[4] + d.z * H[7];
+          const float b2 = d.x * H[2] + d.y * H[5] + d.z * H[8];
+          H[0] += a0 * b0; H[1] += a0 * b1; H[2] += a0 * b2;
+          H[3] += a1 * b0; H[4] += a1 * b1; H[5] += a1 * b2;
+          H[6] += a2 * b0; H[7] += a2 * b1; H[8] += a2 * b2;
+        }
+      }
+      if (phase != 2 && !finish) {
+        const float rr = r.x * r.x + r.y * r.y + r.z * r.z;
+        if (rr < cfg.tol2) {
+          conv = true;
+          finish = true;
+        } else if (it >= cfg.max_iter) {
+          finish = true;
+        } else {
+          dx = make_float3(-(H[0] * r.x + H[1] * r.y + H[2] * r.z), -(H[3] * r.x + H[4] * r.y + H[5] * r.z),
+                           -(H[6] * r.x + H[7] * r.y + H[8] * r.z));
+          phase = 1;
+        }
+      }
+      if constexpr (kOrder == ItemOrder::kPerLane) {
+        // the lane owns its sample and runs its starts in order: the first of
+        // equal roots is the earlier start's
+        if (finish) {
+          if (conv && in_box(S, x)) {
+            st.converged++;
+            const int nr = qs.nroots[cur];
+            bool dup = false;
+            for (int j2 = 0; j2 < nr; ++j2) {
+              const float4 o = qs.roots[j2 * kList + cur];
+              const float ddx = x.x - o.x, ddy = x.y - o.y, ddz = x.z - o.z;
+              if (ddx * ddx + ddy * ddy + ddz * ddz < 1e-8f) { dup = true; break; }
+            }
+            if (!dup) {
+              st.roots++;
+              const int code = (order << 8) | label;
+              if (nr < kMaxRoots) {
+                qs.roots[nr * kList + cur] = make_float4(x.x, x.y, x.z, __int_as_float(code));
+                qs.nroots[cur] = (uint8_t)(nr + 1);
+              } else {
+                compress_roots<P>(S, M, F, fs, qs.roots + cur, xn, x, code);
+                qs.nroots[cur] = 1;
+              }
+            }
+          }
+          phase = 2;
+          need = true;
+        }
       } else {
-        qs.nroots[cur] = (uint8_t)nr;
-        phase = 2;
+        bool fresh = false;
+        int dupj = -1;
+        const int code = (order << 8) | label;
+        if (finish) {
+          if (conv && in_box(S, x)) {
+            st.converged++;
+            // most converged starts find a root already listed: those only lower
+            // the listed root's start code, in parallel
+            const int nr = qs.nroots[cur];
+            fresh = true;
+            for (int j = 0; j < nr; ++j) {
+              float4* o = qs.roots + j * kList + cur;
+              const float ddx = x.x - o->x, ddy = x.y - o->y, ddz = x.z - o->z;
+              if (ddx * ddx + ddy * ddy + ddz * ddz < 1e-8f) {
+                atomicMin(reinterpret_cast<int*>(&o->w), code);
+                fresh = false;
+                dupj = j;
+                break;
+              }
+            }
+          }
+          phase = 2;
+          need = true;
+        }
+        __syncwarp();
+        // the earliest start's position stays with the root (codes of a sample are distinct)
+        if (dupj >= 0 && __float_as_int(qs.roots[dupj * kList + cur].w) == code) {
+          float4* o = qs.roots + dupj * kList + cur;
+          o->x = x.x;
+          o->y = x.y;
+          o->z = x.z;
+        }
+        __syncwarp();
+        // the others are merged into their samples' lists one at a time (two of
+        // this step's roots may be the same)
+        unsigned ins = __ballot_sync(kFull, fresh);
+        while (ins) {
+          const int ld = __ffs(ins) - 1;
+          ins &= ins - 1u;
+          const int s_l = __shfl_sync(kFull, cur, ld);
+          const float px = __shfl_sync(kFull, x.x, ld), py = __shfl_sync(kFull, x.y, ld),
+                      pz = __shfl_sync(kFull, x.z, ld);
+          const int code_l = (__shfl_sync(kFull, order, ld) << 8) | __shfl_sync(kFull, label, ld);
+          const int nr = qs.nroots[s_l];
+          bool dup = false;
+          float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (lane < nr) {
+            o = qs.roots[lane * kList + s_l];
+            const float ddx = px - o.x, ddy = py - o.y, ddz = pz - o.z;
+            dup = ddx * ddx + ddy * ddy + ddz * ddz < 1e-8f;
+          }
+          const unsigned dupm = __ballot_sync(kFull, dup);
+          if (dupm) {
+            // the same root: the list keeps the earlier start's (its position too)
+            if (lane == __ffs(dupm) - 1 && code_l < __float_as_int(o.w))
+              qs.roots[lane * kList + s_l] = make_float4(px, py, pz, __int_as_float(code_l));
+          } else if (lane == ld) {
+            st.roots++;
+            if (nr < kMaxRoots) {
+              qs.roots[nr * kList + s_l] = make_float4(px, py, pz, __int_as_float(code_l));
+              qs.nroots[s_l] = (uint8_t)(nr + 1);
+            } else {
+              compress_roots<P>(S, M, F, fs, qs.roots + s_l, xn, x, code_l);
+              qs.nroots[s_l] = 1;
+            }
+          }
+          __syncwarp();
+        }
       }
     }
+    __syncwarp();
   }
-  __syncwarp();
   // ---- one Newton polish per stored root, field at the roots, max-density root
   {
     const int i = lane;  // the lane evaluates its own sample's roots
@@ -288,7 +450,7 @@ __device__ __forceinline__ void posed_field_list(const SkinDev& S, const FieldDe
       int start = -1;
       if (has) {
         const float4 o = qs.roots[e * kList + i];
-        start = __float_as_int(o.w);
+        start = __float_as_int(o.w) & 0xff;
         xs = polish_root(S, Mq, make_float3(o.x, o.y, o.z), xq);
       }
       float sig;

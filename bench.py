@@ -44,6 +44,8 @@ FLOP_START = 306       # x0 = N_k^-1 x', LBS value (8-corner trilinear blend of 
 FLOP_ITER = 320        # Broyden step: H r, LBS value, residual difference, rank-one update of H
 FLOP_ROOT = 620 + 960 + 12800 + 40  # Newton polish with the analytic Jacobian, hash encoding, MLP, activations
 FLOP_SAMPLE = 20       # alpha, transmittance, colour accumulation
+GATHER_LBS = 8 * 48    # bytes of the blended grid one LBS evaluation reads
+GATHER_HASH = 16 * 8 * 8  # bytes of the fp32 hash table one field evaluation reads
 # DRAM bytes (read + write) of one render_kernel<2, fp32> launch on this workload,
 # from the ncu capture summarised in profiles/render_kernel_540x540_fp32.md; the
 # ncu-measured busiest unit of that launch is reported beside the roofline
@@ -324,7 +326,15 @@ def train_quality(torch, ia, sc, table, mlp, prop=None, iters=2000, batch=8192, 
         return float(10 * np.log10(1.0 / max(mse, 1e-12)))
 
     curve = [(0, 0.0, round(psnr(), 3))]
+    # one untimed step first: the workspaces are allocated on the first call
+    f = torch.randint(0, n_frames, (batch,), device=dev, dtype=torch.int32)
+    px = torch.randint(0, HW, (batch,), device=dev)
+    ia.ia_train_step(ctx, O[px].contiguous(), D[px].contiguous(), f, T_rgb[f.long(), px].contiguous(), loss, g,
+                     occ_grid=ia.IA_OCC_UNION, alpha_target=T_a[f.long(), px].contiguous(),
+                     reg_x=(nmin + ext * torch.rand(batch, 3, device=dev)).contiguous(), reg_pose=f, reg_weight=0.1)
+    torch.cuda.synchronize()
     timed = 0.0
+    skips = 0
     losses = []
     for it in range(1, iters + 1):
         torch.cuda.synchronize()
@@ -345,6 +355,8 @@ def train_quality(torch, ia, sc, table, mlp, prop=None, iters=2000, batch=8192, 
         timed += time.perf_counter() - t
         if it % 50 == 0:
             losses.append(round(loss.item(), 5))
+            scale, skipped = ia.ia_loss_scale(ctx)
+            skips += int(skipped)
         if it % eval_every == 0 or it == iters:
             curve.append((it, round(timed, 3), round(psnr(), 3)))
     ia.ia_destroy(ctx)
@@ -356,6 +368,7 @@ def train_quality(torch, ia, sc, table, mlp, prop=None, iters=2000, batch=8192, 
             "time_to_psnr": reach,
             "iters_per_s": round(iters / timed, 1), "psnr_curve": curve, "loss_every_50": losses[:8] + losses[-4:],
             "psnr_start": curve[0][2], "psnr_end": curve[-1][2], "start": list(start),
+            "skipped_steps_seen": skips,
             "what": "fp16 step (+proposal) with Huber/alpha/hard losses and the density regulariser, Adam, "
                     "training-mode occupancy every 16 iterations; PSNR on a held-out frame"}
 
@@ -416,6 +429,28 @@ def skip_ablation(torch, ia, sc, table, mlp, icam, rgb, alpha, stream, poses, fr
     ia.ia_destroy(ctx)
     out["render_speedup"] = round(out["render_ms_no_skip"] / out["render_ms_skip"], 2)
     out["train_speedup"] = round(out["train_step_ms_no_skip"] / out["train_step_ms_skip"], 2)
+    return out
+
+
+def gather_peaks(torch, ia, stream, num_sms):
+    """Random 48-byte record gathers (ia_gather_probe) from a 64 KiB table (L1
+    resident) and from a table the size of one blended grid, 64^3 vertices
+    (12.6 MB, L2 resident): useful GB/s, best of 5 launches."""
+    out = {}
+    sink = torch.zeros(1, device="cuda")
+    for name, n_rec in (("l1", 65536 // 48), ("l2", 64 ** 3)):
+        table = torch.rand(n_rec * 12, device="cuda")
+        blocks, iters = num_sms * 8, 640
+        ia.ia_gather_probe(table, n_rec, 64, blocks, sink, stream=stream)  # warm-up
+        best = 0.0
+        for _ in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ia.ia_gather_probe(table, n_rec, iters, blocks, sink, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            best = max(best, blocks * 256 * iters * 48 / (a.elapsed_time(b) * 1e-3) / 1e9)
+        out[name] = round(best, 1)
     return out
 
 
@@ -548,6 +583,18 @@ def run_ours(args, rank, world, local_rank):
                    FLOP_ROOT * per_frame["roots"] + FLOP_SAMPLE * per_frame["occupied_samples"])
     r_ms = statistics.mean(render_ms)
     achieved = flop_render / (r_ms * 1e-3) / 1e12
+    # the gathers of the search and the field: 8 corners x 48 B of the blended grid per
+    # LBS evaluation (start or Broyden step), and per distinct root its polish (one
+    # more LBS with the Jacobian) and the hash encoding (16 levels x 8 corners x 8 B)
+    gather_bytes = (GATHER_LBS * (per_frame["starts"] + per_frame["broyden_iters"]) +
+                    (GATHER_LBS + GATHER_HASH) * per_frame["roots"])
+    g_achieved = gather_bytes / (r_ms * 1e-3) / 1e9
+    peaks_g = gather_peaks(torch, ia, stream, torch.cuda.get_device_properties(0).multi_processor_count)
+    roofline_gather = {"kernel": "render_kernel", "bound": "l1-gather", "achieved": round(g_achieved, 1),
+                       "peak": peaks_g["l1"], "unit": "GB/s", "frac": round(g_achieved / peaks_g["l1"], 4),
+                       "peak_l2_random": peaks_g["l2"], "bytes_per_frame": round(gather_bytes),
+                       "peak_source": "ia_gather_probe, random 48-byte records, 64 KiB table (L1) / 12.6 MB (L2), "
+                                      "measured in this run"}
     m16 = statistics.mean(step16)
     line = {
         "metric": METRIC,
@@ -594,6 +641,7 @@ def run_ours(args, rank, world, local_rank):
                     "gradients; fp16 with dynamic loss scaling, weight gradients on tcgen05"},
         "train_quality": quality,
         "skip_ablation": ablation,
+        "roofline_gather": roofline_gather,
         "roofline": {"kernel": "render_kernel", "bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                      "traffic": RENDER_DRAM_BYTES,

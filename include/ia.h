@@ -319,6 +319,14 @@ ia_status ia_train_stats(ia_ctx *ctx, ia_render_stats *stats, void *stream);
 ia_status ia_adam_step(ia_ctx *ctx, const float *g_table, const float *g_mlp, const float *g_skin, float lr,
                        float beta1, float beta2, float eps, void *stream);
 
+/* Measurement helper, not part of the method: every one of blocks x 256 threads
+ * reads `iters` records of 48 bytes (three float4, one vertex of the blended
+ * transform grid) at xorshift-random indices of table [n_records][12] fp32
+ * (device, 16-byte aligned), and writes nothing that matters to sink (device,
+ * one float).  Timing it on a table that fits L1 or L2 gives the random-gather
+ * peak that the correspondence search's gathers are measured against. */
+ia_status ia_gather_probe(const float *table, int64_t n_records, int iters, int blocks, float *sink, void *stream);
+
 /* The loss scale S after the last ia_train_step (host float) and whether that
  * step overflowed and was skipped (host int32, 1 = skipped); either may be NULL,
  * not both.  Waits on `stream`.  fp32 contexts report S = 1, never skipped.

@@ -106,6 +106,7 @@ def lib():
             "ia_train_stats": [P, C.POINTER(RenderStats), V],
             "ia_grad_sizes": [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
             "ia_set_loss": [P, C.POINTER(Loss)],
+            "ia_gather_probe": [P, C.c_int64, I, I, P, V],
             "ia_adam_step": [P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, V],
             "ia_proposal_init": [P, C.POINTER(ProposalConfig)],
             "ia_proposal_param_sizes": [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
@@ -283,6 +284,12 @@ def ia_train_step(ctx, origin, direction, pose, target, loss, grads, occ_grid=IA
     g.table, g.mlp, g.skin, g.bones = (_ptr(grads[k]) for k in ("table", "mlp", "skin", "bones"))
     _check(lib().ia_train_step(ctx, C.byref(b), occ_grid, _ptr(loss), _ptr(rgb_out), C.byref(g),
                                _stream(stream)), ctx)
+
+
+def ia_gather_probe(table, n_records, iters, blocks, sink, stream=None):
+    """Random 48-byte record gathers (a measurement helper)."""
+    _check(lib().ia_gather_probe(_ptr(table), int(n_records), int(iters), int(blocks), _ptr(sink), _stream(stream)),
+           None)
 
 
 def ia_set_loss(ctx, rgb_loss=IA_LOSS_L2, huber_delta=0.0, w_rgb=1.0, w_alpha=0.0, w_hard=0.0):

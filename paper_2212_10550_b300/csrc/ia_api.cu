@@ -914,6 +914,16 @@ ia_status ia_adam_step(ia_ctx* c, const float* g_table, const float* g_mlp, cons
   return IA_OK;
 }
 
+ia_status ia_gather_probe(const float* table, int64_t n_records, int iters, int blocks, float* sink, void* stream) {
+  if (!table || !sink || n_records < 1 || n_records > (1LL << 31) || iters < 1 || blocks < 1)
+    return fail(nullptr, IA_ERR_ARG, "bad gather probe arguments");
+  if ((reinterpret_cast<uintptr_t>(table) & 15) != 0) return fail(nullptr, IA_ERR_ARG, "table must be 16-byte aligned");
+  cudaError_t e = launch_gather_probe(reinterpret_cast<const float4*>(table), n_records, iters, blocks, sink,
+                                      (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "ia_gather_probe");
+  return IA_OK;
+}
+
 ia_status ia_set_loss(ia_ctx* c, const ia_loss* l) {
   if (!c || !l) return fail(c, IA_ERR_ARG, "null argument");
   if (l->rgb_loss != IA_LOSS_L2 && l->rgb_loss != IA_LOSS_HUBER) return fail(c, IA_ERR_ARG, "unknown rgb_loss");

@@ -220,6 +220,8 @@ cudaError_t launch_pose_chain(int P, int nb, const int* parent, const double* re
 cudaError_t launch_blend(int P, int V, int nb, const float* W, const float* N, float4* M, cudaStream_t s);
 cudaError_t launch_occ_density(const PosedArgs& a, const BoxDev& box, const float* jitter, float* sigma,
                                unsigned long long* stats, unsigned* work, int num_sms, cudaStream_t s);
+cudaError_t launch_gather_probe(const float4* table, int64_t n_records, int iters, int blocks, float* sink,
+                                cudaStream_t s);
 cudaError_t launch_occ_ema(const float* sigma, float* d, int n, float decay, cudaStream_t s);
 cudaError_t launch_occ_bits(const float* sigma, int R, int dilate, float tau, uint32_t* bits,
                             uint32_t* union_bits, cudaStream_t s);

@@ -661,4 +661,32 @@ cudaError_t launch_march_mask(const RenderArgs& a, uint32_t* mask, cudaStream_t 
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Gather probe (a measurement helper, not part of the method): random 48-byte
+// records (three float4, the blended grid's vertex) read by every thread, the
+// access pattern of one corner of the LBS gather.  Its rate on a table that fits
+// L1, or L2, is the peak the search kernels' gathers are compared against.
+// ---------------------------------------------------------------------------
+
+__global__ void gather_probe_kernel(const float4* __restrict__ table, unsigned n_records, int iters,
+                                    float* __restrict__ sink) {
+  unsigned h = (blockIdx.x * blockDim.x + threadIdx.x) * 2654435761u + 12345u;
+  float acc = 0.f;
+  for (int i = 0; i < iters; ++i) {
+    h ^= h << 13;  // xorshift32 (Marsaglia): the record index
+    h ^= h >> 17;
+    h ^= h << 5;
+    const float4* p = table + 3 * (size_t)(h % n_records);
+    const float4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+    acc += a.x + b.y + c.z;
+  }
+  if (acc == 1.2345f) sink[0] = acc;  // keeps the loads; practically never taken
+}
+
+cudaError_t launch_gather_probe(const float4* table, int64_t n_records, int iters, int blocks, float* sink,
+                                cudaStream_t s) {
+  gather_probe_kernel<<<blocks, 256, 0, s>>>(table, (unsigned)n_records, iters, sink);
+  return cudaGetLastError();
+}
+
 }  // namespace ia

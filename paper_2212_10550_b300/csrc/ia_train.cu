@@ -671,7 +671,8 @@ __global__ void __launch_bounds__(256) mlp_grad_kernel(const TrainArgs a) {
 // rounded operands and activations are written channel-major into X for the
 // tensor-core weight-gradient reduction; dL/dfeatures is unscaled to fp32 before
 // the hash-table scatter and the implicit-function gradient.  A scaled gradient
-// outside the operand type's range sets the overflow flag.
+// or a hidden activation outside the operand type's range, or a non-finite
+// dL/dfeatures, sets the overflow flag (the step is then skipped).
 // ---------------------------------------------------------------------------
 
 constexpr int kXdH2 = 0, kXdH1 = 64, kXH1 = 128, kXF = 192, kXOne = 224, kXH2 = 240, kXOne2 = 304, kXdO = 368;
@@ -829,6 +830,7 @@ __global__ void __launch_bounds__(kBwThreads) train_backward_h_kernel(const Trai
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           if (acc[q] > 0.f) m1[mt] |= 1u << (4 * nt + q);
+          overflow |= !(acc[q] <= HalfOf<P>::kMax);  // an operand out of range (or NaN) spoils the GEMM
           rnd_bits<P>(fmaxf(acc[q], 0.f), hb[q]);
         }
         const int ch = 8 * nt + 2 * t;
@@ -861,6 +863,7 @@ __global__ void __launch_bounds__(kBwThreads) train_backward_h_kernel(const Trai
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           if (acc[q] > 0.f) m2[mt] |= 1u << (4 * nt + q);
+          overflow |= !(acc[q] <= HalfOf<P>::kMax);
           rnd_bits<P>(fmaxf(acc[q], 0.f), hb[q]);
         }
         const int ch = 8 * nt + 2 * t;
@@ -974,6 +977,7 @@ __global__ void __launch_bounds__(kBwThreads) train_backward_h_kernel(const Trai
 #pragma unroll
         for (int kt = 0; kt < 4; ++kt) mma16816<P>(acc, A2[mt][kt], Wr[8 * kt + t], Wr[8 * kt + 4 + t]);
         const int c = 8 * nt + 2 * t;
+        overflow |= !(isfinite(acc[0]) && isfinite(acc[1]) && isfinite(acc[2]) && isfinite(acc[3]));
         float* df = reinterpret_cast<float*>(a.s_dfeat);
         if (s0 + r0 < n)
           *reinterpret_cast<float2*>(df + (size_t)(s0 + r0) * kIn + c) = make_float2(acc[0] * inv_S, acc[1] * inv_S);

@@ -49,9 +49,9 @@ GATHER_HASH = 16 * 8 * 8  # bytes of the fp32 hash table one field evaluation re
 # DRAM bytes (read + write) of one render_kernel<2, fp32> launch on this workload,
 # from the ncu capture summarised in profiles/render_kernel_540x540_fp32.md; the
 # ncu-measured busiest unit of that launch is reported beside the roofline
-RENDER_DRAM_BYTES = 51.91e6 + 2.60e6
-RENDER_LIMITER = {"unit": "L1 (blended-grid gathers)", "l1tex_throughput_pct": 63.8, "issue_active_pct": 29.8,
-                  "fma_pipe_pct": 17.5, "l1_hit_pct": 91.0, "l2_hit_pct": 97.1, "simt_lanes_per_inst": 20.4,
+RENDER_DRAM_BYTES = 51.88e6 + 2.28e6
+RENDER_LIMITER = {"unit": "L1 (blended-grid gathers)", "l1tex_throughput_pct": 62.8, "issue_active_pct": 30.5,
+                  "fma_pipe_pct": 17.4, "l1_hit_pct": 91.0, "l2_hit_pct": 97.6, "simt_lanes_per_inst": 20.1,
                   "source": "profiles/render_kernel_540x540_fp32.md"}
 
 

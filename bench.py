@@ -471,6 +471,19 @@ def run_ours(args, rank, world, local_rank):
     alpha = torch.zeros(W * H, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
+    if args.only == "proposal":
+        ctx16 = make_ctx(torch, ia, sc, table, mlp, 1, EARLY_T)
+        pt = train_proposal(torch, ia, ctx16, sc, n_poses=64, steps=400)
+        ia.ia_set_search(ctx16, ia.IA_SEARCH_PROPOSAL)
+        step16, render16 = time_frames(torch, ia, ctx16, poses, icam, rgb, alpha, flush, args.steps, args.warmup,
+                                       stream)
+        ia.ia_destroy(ctx16)
+        if rank != 0:
+            return None
+        return {"metric": METRIC, "partial": "fp16 + proposal frames only (proposal trained on 64 poses)",
+                "ms_per_step": round(statistics.mean(step16), 4), "render_ms": round(statistics.mean(render16), 4),
+                "proposal_training": pt}
+
     if args.only == "ablation":
         ab = skip_ablation(torch, ia, sc, table, mlp, icam, rgb, alpha, stream, poses)
         return {"metric": METRIC, "partial": "skip ablation only", "skip_ablation": ab} if rank == 0 else None
@@ -745,7 +758,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", default="all", choices=["all", "plain", "train", "quality", "ablation"],
+    ap.add_argument("--only", default="all", choices=["all", "plain", "train", "quality", "ablation", "proposal"],
                     help="plain: time only the plain fp32 frames; train: only the fp32 and fp16 training "
                          "steps at 32768 rays (both used for profiling captures)")
     args = ap.parse_args()

@@ -25,7 +25,6 @@ constexpr int kMaxLevels = 16;
 constexpr int kWidth = 64;
 constexpr int kIn = 32;          // MLP input, zero-padded to 16 levels x 2 features
 constexpr int kMaxRoots = 4;     // distinct roots remembered per sample for merging
-constexpr int kNS = 1;           // samples per lane in the correspondence search (2 measured slower)
 constexpr unsigned kFull = 0xffffffffu;
 
 // MLP weights staged in shared memory (fp32): W1 [64][32] (zero-padded

@@ -212,9 +212,6 @@ cudaError_t launch_prop_grad(const PropTrainArgs& a, cudaStream_t s);
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, int step, float b1,
                         float b2, float eps, const int* skip, cudaStream_t s);
 
-size_t posed_smem_bytes(int threads);
-size_t render_smem_bytes(int K);
-
 cudaError_t launch_pose_chain(int P, int nb, const int* parent, const double* rest, const double* theta,
                               const double* trans, float* N, float* Ninv, float* B0inv, cudaStream_t s);
 cudaError_t launch_blend(int P, int V, int nb, const float* W, const float* N, float4* M, cudaStream_t s);

@@ -17,7 +17,6 @@
 #define IA_POSED_MIN_BLOCKS 1
 #endif
 
-
 namespace ia {
 
 // ---------------------------------------------------------------------------
@@ -167,8 +166,6 @@ size_t posed_smem_bytes_p(int threads, bool prop) {
   return sizeof(float) * (mlp_smem_words(P, threads, prop) + kMaxBones * 12) +
          sizeof(uint32_t) * (threads / 32) * list_smem_words(prop);
 }
-
-size_t posed_smem_bytes(int threads) { return posed_smem_bytes_p<Prec::F32>(threads, false); }
 
 // ---------------------------------------------------------------------------
 // Occupancy grid (Sec. 3.3, inference mode)
@@ -405,8 +402,6 @@ size_t render_smem_bytes_p(int K, bool prop) {
   return posed_smem_bytes_p<P>(kRenderThreads, prop) + sizeof(float4) * (2 * kRenderThreads + K * kRenderThreads) +
          (sizeof(uint8_t) + sizeof(uint16_t)) * K * kRenderThreads;
 }
-
-size_t render_smem_bytes(int K) { return render_smem_bytes_p<Prec::F32>(K, false); }
 
 __device__ __forceinline__ void tile_pixel(int id, int tiles_x, int W, int H, int& u, int& v, bool& valid) {
   const int tile = id / (kTile * kTile), i = id % (kTile * kTile);

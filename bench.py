@@ -198,6 +198,26 @@ def time_frames(torch, ia, ctx, poses, icam, rgb, alpha, flush, steps, warmup, s
     return [a.elapsed_time(c) for a, b, c in ev], [b.elapsed_time(c) for a, b, c in ev]
 
 
+def time_occupancy(torch, ia, ctx, poses, flush, steps, stream, cull):
+    """ia_update_occupancy alone (with culling on or off): mean ms per pose, CUDA
+    events on the stream, L2 flushed before each call outside the events."""
+    ia.ia_set_occupancy_culling(ctx, cull)
+    ms = []
+    for i in range(3 + steps):
+        th, tr = poses[i % len(poses)]
+        ia.ia_set_pose(ctx, th[None], tr[None], stream=stream)
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ia.ia_update_occupancy(ctx, 0, ia.IA_OCC_POSE, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i >= 3:
+            ms.append(a.elapsed_time(b))
+    ia.ia_set_occupancy_culling(ctx, True)
+    return statistics.mean(ms)
+
+
 def frame_stats(ia, ctx, poses, icam, rgb, alpha):
     tot, occ = {}, {}
     for th, tr in poses:
@@ -536,6 +556,8 @@ def run_ours(args, rank, world, local_rank):
         ia.ia_update_occupancy(ctx, 0, ia.IA_OCC_POSE, stream=stream)
         ia.ia_render(ctx, 0, icam, h_rgb, h_a, stream=stream)  # copies back and synchronises
         e2e_s.append(time.perf_counter() - t)
+    occ_cull_ms = time_occupancy(torch, ia, ctx, poses, flush, 16, stream, True)
+    occ_full_ms = time_occupancy(torch, ia, ctx, poses, flush, 16, stream, False)
     ia.ia_destroy(ctx)
 
     if args.only == "plain":
@@ -544,7 +566,9 @@ def run_ours(args, rank, world, local_rank):
             return {"metric": METRIC, "value": round(args.steps / total, 3), "unit": "frames/s (plain fp32 only)",
                     "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                     "ms_per_step": round(1e3 * total / args.steps, 4), "higher_is_better": True,
-                    "render_ms": round(statistics.mean(render_ms), 4), "partial": "plain fp32 frames only"}
+                    "render_ms": round(statistics.mean(render_ms), 4),
+                    "occupancy_refresh": {"culled_ms": round(occ_cull_ms, 4), "full_search_ms": round(occ_full_ms, 4)},
+                    "partial": "plain fp32 frames only"}
         return None
 
     # ---- fp16 + learned proposal on the same sequence (proposal trained on other poses)
@@ -624,6 +648,11 @@ def run_ours(args, rank, world, local_rank):
         "mean_broyden_iters_per_sample": round(per_frame["broyden_iters"] / per_frame["occupied_samples"], 2),
         "per_frame": {k: round(v, 1) for k, v in per_frame.items()},
         "occupancy_per_frame": {k: round(v, 1) for k, v in occ_per_frame.items()},
+        "occupancy_refresh": {
+            "culled_ms": round(occ_cull_ms, 4), "full_search_ms": round(occ_full_ms, 4),
+            "speedup": round(occ_full_ms / occ_cull_ms, 2),
+            "searched_cells": round(occ_per_frame["starts"] / (sc.n_bones * sc.occ_res ** 3), 4),
+            "what": "ia_update_occupancy of one 64^3 grid, plain fp32, culling on vs off (same densities)"},
         "step_ms": {"mean": round(statistics.mean(step_ms), 4), "min": round(min(step_ms), 4),
                     "max": round(max(step_ms), 4)},
         "render_ms": {"mean": round(r_ms, 4), "min": round(min(render_ms), 4)},

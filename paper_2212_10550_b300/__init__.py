@@ -116,6 +116,7 @@ def lib():
             "ia_proposal_grad": [P, I, P, P, P, P, P, P, P, V],
             "ia_proposal_train": [P, I, P, P, P, P, I, I, C.c_float, P, V],
             "ia_set_search": [P, I],
+            "ia_set_occupancy_culling": [P, I],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -383,3 +384,7 @@ def ia_proposal_train(ctx, x, pose, label, target, steps, batch, lr, loss_out=No
 
 def ia_set_search(ctx, mode):
     _check(lib().ia_set_search(ctx, mode), ctx)
+
+
+def ia_set_occupancy_culling(ctx, on):
+    _check(lib().ia_set_occupancy_culling(ctx, 1 if on else 0), ctx)

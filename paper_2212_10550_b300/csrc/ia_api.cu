@@ -49,6 +49,9 @@ struct ia_ctx {
   uint32_t* d_occ_train = nullptr;
   float* d_sigma = nullptr;
   float* d_occ_ema = nullptr;  // training-mode running density [R^3] (zero at creation)
+  uint32_t* d_cull = nullptr;  // cells that can hold a root: [R^3 / 32] bits + candidate count
+  int* d_cand = nullptr;       // their indices [R^3]
+  bool occ_cull = true;
   bool have_occ = false;
   // counters
   unsigned long long* d_stats = nullptr;
@@ -249,6 +252,22 @@ BoxDev box_dev(const ia_ctx* c) {
   return b;
 }
 
+// Density of the posed field at every occupancy cell's query point (centre, or
+// norm_min + (c + jitter) * cell size) into sigma [R^3]: with culling on, only
+// the cells whose point can have a root are searched, the rest get 0 (the same
+// values the full search gives).
+cudaError_t occ_density(const ia_ctx* c, int pose, const float* jitter, float* sigma, unsigned long long* stats,
+                        cudaStream_t s) {
+  const PosedArgs a = occ_args(c, pose);
+  const BoxDev box = box_dev(c);
+  if (!c->occ_cull) return launch_occ_density(a, box, jitter, nullptr, nullptr, sigma, stats, c->d_work, c->num_sms, s);
+  const int R = c->cfg.occ_res;
+  const unsigned* count = c->d_cull + ((size_t)R * R * R + 31) / 32;
+  cudaError_t e = launch_occ_cull(a, box, jitter, c->d_cull, c->d_cand, sigma, s);
+  if (e != cudaSuccess) return e;
+  return launch_occ_density(a, box, jitter, c->d_cand, count, sigma, stats, c->d_work, c->num_sms, s);
+}
+
 ia_status need_ready(ia_ctx* c, int pose, bool need_occ) {
   if (!c) return fail(nullptr, IA_ERR_ARG, "null context");
   if (c->nb == 0) return fail(c, IA_ERR_STATE, "ia_set_skeleton has not been called");
@@ -339,6 +358,8 @@ ia_status ia_create(const ia_config* cfg, ia_ctx** out) {
   if (e == cudaSuccess) e = dalloc(&c->d_occ_train, words);
   if (e == cudaSuccess) e = dalloc(&c->d_sigma, (size_t)R * R * R);
   if (e == cudaSuccess) e = dalloc(&c->d_occ_ema, (size_t)R * R * R);
+  if (e == cudaSuccess) e = dalloc(&c->d_cull, words + 1);
+  if (e == cudaSuccess) e = dalloc(&c->d_cand, (size_t)R * R * R);
   if (e == cudaSuccess) e = cudaMemset(c->d_occ_ema, 0, sizeof(float) * R * R * R);
   if (e == cudaSuccess) e = dalloc(&c->d_stats, (size_t)ST_COUNT);
   if (e == cudaSuccess) e = dalloc(&c->d_counter, (size_t)1);
@@ -374,6 +395,8 @@ void ia_destroy(ia_ctx* c) {
   dfree(c->d_occ_train);
   dfree(c->d_sigma);
   dfree(c->d_occ_ema);
+  dfree(c->d_cull);
+  dfree(c->d_cand);
   dfree(c->d_stats);
   dfree(c->d_counter);
   dfree(c->d_work);
@@ -552,8 +575,7 @@ ia_status ia_update_occupancy(ia_ctx* c, int pose, int mode, float* sigma_out, u
   const size_t words = ((size_t)R * R * R + 31) / 32;
   float* sig = sigma_out ? sigma_out : c->d_sigma;
   IA_CUDA(c, cudaMemsetAsync(c->d_stats, 0, sizeof(unsigned long long) * ST_COUNT, s), "ia_update_occupancy");
-  IA_CUDA(c, launch_occ_density(occ_args(c, pose), box_dev(c), nullptr, sig, c->d_stats, c->d_work, c->num_sms, s),
-          "ia_update_occupancy: density");
+  IA_CUDA(c, occ_density(c, pose, nullptr, sig, c->d_stats, s), "ia_update_occupancy: density");
   if (mode == IA_OCC_POSE) {
     IA_CUDA(c, launch_occ_bits(sig, R, c->cfg.occ_dilate, c->cfg.occ_tau, c->d_occ, nullptr, s),
             "ia_update_occupancy: bits");
@@ -578,9 +600,7 @@ ia_status ia_update_occupancy_ema(ia_ctx* c, int pose, const float* jitter, floa
   const int R = c->cfg.occ_res, n = R * R * R;
   const size_t words = ((size_t)n + 31) / 32;
   IA_CUDA(c, cudaMemsetAsync(c->d_stats, 0, sizeof(unsigned long long) * ST_COUNT, s), "ia_update_occupancy_ema");
-  IA_CUDA(c, launch_occ_density(occ_args(c, pose), box_dev(c), jitter, c->d_sigma, c->d_stats, c->d_work,
-                                c->num_sms, s),
-          "ia_update_occupancy_ema: density");
+  IA_CUDA(c, occ_density(c, pose, jitter, c->d_sigma, c->d_stats, s), "ia_update_occupancy_ema: density");
   IA_CUDA(c, launch_occ_ema(c->d_sigma, c->d_occ_ema, n, decay, s), "ia_update_occupancy_ema: running density");
   IA_CUDA(c, launch_occ_bits(c->d_occ_ema, R, c->cfg.occ_dilate, c->cfg.occ_tau, c->d_occ_train, nullptr, s),
           "ia_update_occupancy_ema: bits");
@@ -1167,6 +1187,13 @@ ia_status ia_proposal_train(ia_ctx* c, int n, const float* x, const int32_t* pos
   return IA_OK;
 }
 
+ia_status ia_set_occupancy_culling(ia_ctx* c, int on) {
+  if (!c) return fail(nullptr, IA_ERR_ARG, "null context");
+  if (on != 0 && on != 1) return fail(c, IA_ERR_ARG, "culling must be 0 or 1");
+  c->occ_cull = on == 1;
+  return IA_OK;
+}
+
 ia_status ia_set_search(ia_ctx* c, int mode) {
   if (!c) return fail(nullptr, IA_ERR_ARG, "null context");
   if (mode != IA_SEARCH_ALL_BONES && mode != IA_SEARCH_PROPOSAL) return fail(c, IA_ERR_ARG, "unknown search mode");
@@ -1224,10 +1251,10 @@ ia_status ia_update_occupancy_static(ia_ctx* c, int pose, uint32_t* bits_out, vo
   float* sigma = nullptr;
   IA_CUDA(c, static_scratch(dev, &sigma), "ia_update_occupancy_static: cudaGetSymbolAddress");
   cudaStream_t s = (cudaStream_t)stream;
-  // the density kernel writes all R^3 cells before the bits kernel reads them, so
-  // the scratch needs no clearing; cells past R^3 are never read
-  IA_CUDA(c, launch_occ_density(occ_args(c, pose), box_dev(c), nullptr, sigma, nullptr, c->d_work, c->num_sms, s),
-          "ia_update_occupancy_static: density");
+  // every one of the R^3 cells is written (searched, or set to 0 when culled)
+  // before the bits kernel reads them, so the scratch needs no clearing; cells
+  // past R^3 are never read
+  IA_CUDA(c, occ_density(c, pose, nullptr, sigma, nullptr, s), "ia_update_occupancy_static: density");
   IA_CUDA(c, launch_occ_bits(sigma, R, c->cfg.occ_dilate, c->cfg.occ_tau, c->d_occ, nullptr, s),
           "ia_update_occupancy_static: bits");
   c->have_occ = true;

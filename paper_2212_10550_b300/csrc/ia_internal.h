@@ -215,8 +215,11 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n,
 cudaError_t launch_pose_chain(int P, int nb, const int* parent, const double* rest, const double* theta,
                               const double* trans, float* N, float* Ninv, float* B0inv, cudaStream_t s);
 cudaError_t launch_blend(int P, int V, int nb, const float* W, const float* N, float4* M, cudaStream_t s);
-cudaError_t launch_occ_density(const PosedArgs& a, const BoxDev& box, const float* jitter, float* sigma,
-                               unsigned long long* stats, unsigned* work, int num_sms, cudaStream_t s);
+cudaError_t launch_occ_density(const PosedArgs& a, const BoxDev& box, const float* jitter, const int* cells,
+                               const unsigned* count, float* sigma, unsigned long long* stats, unsigned* work,
+                               int num_sms, cudaStream_t s);
+cudaError_t launch_occ_cull(const PosedArgs& a, const BoxDev& box, const float* jitter, uint32_t* mask,
+                            int* cells, float* sigma, cudaStream_t s);
 cudaError_t launch_gather_probe(const float4* table, int64_t n_records, int iters, int blocks, float* sink,
                                 cudaStream_t s);
 cudaError_t launch_occ_ema(const float* sigma, float* d, int n, float decay, cudaStream_t s);

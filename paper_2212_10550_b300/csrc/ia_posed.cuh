@@ -100,7 +100,10 @@ __device__ __forceinline__ ListSmem list_smem(uint32_t* base, bool prop) {
 
 // A sample found more distinct roots than its list holds: evaluate the list and
 // the new root now and keep only the max-density one (ties to the lower start
-// bone), so that no root is ever dropped from the selection.
+// bone), so that no root is ever dropped from the selection.  The kept entry
+// is the root as found (position and start code), not its polished position:
+// the final selection polishes it once like every other root, so the result
+// does not depend on when (or whether) the list was compressed.
 template <Prec P>
 __device__ __noinline__ void compress_roots(const SkinDev& S, const float4* M, const FieldDev& F, const FieldSmem& fs,
                                             float4* list, float3 xn, float3 xnew, int code_new) {
@@ -110,6 +113,7 @@ __device__ __noinline__ void compress_roots(const SkinDev& S, const float4* M, c
   best.rgb = best.xstar = make_float3(0.f, 0.f, 0.f);
   best.start = -1;
   int best_code = code_new;
+  float3 best_raw = xnew;
   for (int j = 0; j <= kMaxRoots; ++j) {
     const float4 o =
         j < kMaxRoots ? list[j * kList] : make_float4(xnew.x, xnew.y, xnew.z, __int_as_float(code_new));
@@ -125,9 +129,10 @@ __device__ __noinline__ void compress_roots(const SkinDev& S, const float4* M, c
       best.xstar = xs;
       best.start = bone;
       best_code = code;
+      best_raw = make_float3(o.x, o.y, o.z);
     }
   }
-  list[0] = make_float4(best.xstar.x, best.xstar.y, best.xstar.z, __int_as_float(best_code));
+  list[0] = make_float4(best_raw.x, best_raw.y, best_raw.z, __int_as_float(best_code));
 }
 
 // How a list's (sample, start) items meet the lanes:
@@ -135,8 +140,13 @@ __device__ __noinline__ void compress_roots(const SkinDev& S, const float4* M, c
 //   kSampleMajor  a shared queue, every start of sample 0, then of sample 1, ...
 //   kStartMajor   a shared queue, start 0 of every sample, then start 1, ...
 // (measured: the plain 24-start render keeps its L1 locality best per lane; the
-// proposal's render, whose fallbacks are few but long, and the training forward
-// gain from the shared queue, start-major and sample-major respectively)
+// proposal's render, whose fallbacks are few but long, the culled occupancy
+// grid, whose short lists leave few per warp, and the training forward gain from
+// the shared queue, start-major, start-major and sample-major respectively).
+// The queues run a sample's starts concurrently and in an order that depends on
+// the other samples of the list; the selected root does not depend on it (the
+// earliest start keeps a root's code and position, compressed lists keep roots
+// as found), barring roots within the merge distance of two listed ones.
 enum class ItemOrder { kPerLane, kSampleMajor, kStartMajor };
 
 template <Prec P, ItemOrder kOrder, class Src, class Dst>

@@ -1,0 +1,128 @@
+"""Exact culling of the occupancy queries (Sec. 3.3 grid, searched only where a
+root can exist): with culling on, the densities of every cell are bit-identical
+to those of the full search (fp32 and fp16, cell centres and jittered points),
+the culled cells are the ones without a root (same root and convergence counts),
+and the search work drops.  The full search itself is checked against the
+oracle in test_gpu_parity.py; this file checks that culling changes nothing."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic as S
+from gpu_helpers import make_ctx
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ia():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2212_10550_b300 as ia
+    ia.lib()
+    return ia
+
+
+def _ctx(ia, sc, table, mlp, precision):
+    if precision == "fp32":
+        return make_ctx(ia, torch, sc, table, mlp)
+    cfg = ia.make_config(n_levels=sc.n_levels, log2_table=sc.log2_table, level_res=sc.level_res,
+                         max_samples=sc.max_samples, broyden_max_iter=sc.broyden_max_iter,
+                         broyden_tol=sc.broyden_tol, occ_res=sc.occ_res, occ_tau=sc.occ_tau,
+                         occ_dilate=sc.occ_dilate, early_stop_T=0.0, precision=ia.IA_FP16)
+    ctx = ia.ia_create(cfg)
+    ia.ia_set_skeleton(ctx, sc.parents, sc.rest_joints, sc.skin_grid, sc.canon_min, sc.canon_max,
+                       sc.norm_min, sc.norm_max)
+    ia.ia_set_params(ctx, torch.from_numpy(np.ascontiguousarray(table)).cuda(),
+                     torch.from_numpy(S.pack_mlp(mlp)).cuda())
+    torch.cuda.synchronize()
+    return ctx
+
+
+def _densities(ia, ctx, pose, R, cull):
+    ia.ia_set_occupancy_culling(ctx, cull)
+    sig = torch.full((R ** 3,), -1.0, device="cuda")
+    bits = torch.zeros((R ** 3 + 31) // 32, dtype=torch.int32, device="cuda")
+    st = ia.ia_update_occupancy(ctx, pose, ia.IA_OCC_POSE, sig, bits, stats=True)
+    torch.cuda.synchronize()
+    return sig.cpu().numpy(), bits.cpu().numpy(), st
+
+
+@pytest.mark.parametrize("config", ["tiny", "full"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_culling_keeps_every_density(ia, config, precision):
+    sc = S.make_scene(config, 0)
+    table, mlp = S.make_field(sc, 0)
+    ctx = _ctx(ia, sc, table, mlp, precision)
+    seeds = [1, 2, 5]
+    poses = [S.make_pose(sc, s) for s in seeds]
+    ia.ia_set_pose(ctx, np.stack([p[0] for p in poses]), np.stack([p[1] for p in poses]))
+    R = sc.occ_res
+    for i in range(len(seeds)):
+        s_off, b_off, st_off = _densities(ia, ctx, i, R, False)
+        s_on, b_on, st_on = _densities(ia, ctx, i, R, True)
+        print(f"{config} {precision} pose {i}: starts {st_on['starts']} of {st_off['starts']}, "
+              f"roots {st_on['roots']}, rooted cells {(s_off > 0).sum()} of {R ** 3}")
+        assert (s_on >= 0).all()  # every cell written
+        np.testing.assert_array_equal(s_on, s_off)
+        np.testing.assert_array_equal(b_on, b_off)
+        assert st_on["roots"] == st_off["roots"]
+        assert st_on["converged"] == st_off["converged"]
+        assert st_on["starts"] <= st_off["starts"]
+        if config == "full":
+            assert st_on["starts"] < 0.5 * st_off["starts"]  # most of the grid is culled
+    ia.ia_destroy(ctx)
+
+
+def test_culling_with_jitter_and_static_entry(ia):
+    sc = S.make_scene("full", 0)
+    table, mlp = S.make_field(sc, 0)
+    ctx = make_ctx(ia, torch, sc, table, mlp)
+    poses = [S.make_pose(sc, s) for s in (3, 4)]
+    ia.ia_set_pose(ctx, np.stack([p[0] for p in poses]), np.stack([p[1] for p in poses]))
+    R = sc.occ_res
+    out = {}
+    for cull in (False, True):
+        ia.ia_set_occupancy_culling(ctx, cull)
+        dens = torch.zeros(R ** 3, device="cuda")
+        for i in range(2):
+            jit = torch.from_numpy(S.occupancy_jitter(sc, 10 + i)).cuda()
+            # decay 0 on the first frame restarts the running density
+            ia.ia_update_occupancy_ema(ctx, i, jit, 0.0 if i == 0 else 0.9, dens, None)
+        # points outside their cells (u outside [0, 1)) are searched as well
+        u = np.random.default_rng(7).uniform(-0.5, 1.5, size=(R ** 3, 3)).astype(np.float32)
+        ia.ia_update_occupancy_ema(ctx, 1, torch.from_numpy(u).cuda(), 0.5, dens, None)
+        static_bits = torch.zeros((R ** 3 + 31) // 32, dtype=torch.int32, device="cuda")
+        ia.ia_update_occupancy_static(ctx, 0, static_bits)
+        torch.cuda.synchronize()
+        out[cull] = (dens.cpu().numpy(), static_bits.cpu().numpy())
+    np.testing.assert_array_equal(out[True][0], out[False][0])
+    np.testing.assert_array_equal(out[True][1], out[False][1])
+    assert (out[True][0] > 0).any()
+    ia.ia_destroy(ctx)
+
+
+def test_culled_search_against_oracle(ia):
+    """Against the fp64 oracle at every cell of one full-size pose, the culled
+    search differs only where the full search does: a cell where one side finds
+    a marginal root and the other none (at most 0.1 % of the cells, as in the
+    occupancy parity tests).  The bound itself is pinned against the oracle's
+    roots on the CPU (test_occ_cull_bound.py)."""
+    sc = S.make_scene("full", 0)
+    table, mlp = S.make_field(sc, 0)
+    ctx = make_ctx(ia, torch, sc, table, mlp)
+    th, tr = S.make_pose(sc, 6)
+    ia.ia_set_pose(ctx, th[None], tr[None])
+    R = sc.occ_res
+    s_off, _, _ = _densities(ia, ctx, 0, R, False)
+    s_on, _, st = _densities(ia, ctx, 0, R, True)
+    om = O.OracleModel(sc, table, mlp)
+    ref, _ = om.occupancy(om.pose(th, tr))
+    diff_on = (s_on > 0) != (ref > 0)
+    diff_off = (s_off > 0) != (ref > 0)
+    print(f"oracle rooted cells {(ref > 0).sum()}, searched {st['starts'] / sc.n_bones:.0f} of {R ** 3}, "
+          f"rooted on one side only {diff_on.sum()}")
+    np.testing.assert_array_equal(diff_on, diff_off)
+    assert diff_on.sum() <= 1e-3 * R ** 3
+    ia.ia_destroy(ctx)

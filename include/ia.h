@@ -92,7 +92,7 @@ typedef struct ia_render_stats {
   int64_t rays;              /* rays launched */
   int64_t hit_rays;          /* rays whose clipped interval is non-empty */
   int64_t marched_slots;     /* slots tested against the occupancy grid */
-  int64_t occupied_samples;  /* slots in occupied cells that were evaluated */
+  int64_t occupied_samples;  /* slots in occupied cells reached (evaluated or culled) */
   int64_t starts;            /* Broyden starts run */
   int64_t broyden_iters;     /* Broyden updates run (summed over starts) */
   int64_t converged;         /* starts that converged inside the canonical box */
@@ -100,6 +100,9 @@ typedef struct ia_render_stats {
   int64_t early_stopped;     /* rays stopped by the transmittance threshold */
   int64_t proposed;          /* samples whose first starts came from the proposal network */
   int64_t fallbacks;         /* of those, samples that fell back to every bone-wise start */
+  int64_t culled;            /* render: occupied samples, occupancy: cells, whose point can
+                                have no root (density 0 without a search; see
+                                ia_update_occupancy) */
 } ia_render_stats;
 
 /* Create a context on the current CUDA device.  cfg is copied. */

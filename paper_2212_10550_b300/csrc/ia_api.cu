@@ -49,8 +49,13 @@ struct ia_ctx {
   uint32_t* d_occ_train = nullptr;
   float* d_sigma = nullptr;
   float* d_occ_ema = nullptr;  // training-mode running density [R^3] (zero at creation)
-  uint32_t* d_cull = nullptr;  // cells that can hold a root: [R^3 / 32] bits + candidate count
-  int* d_cand = nullptr;       // their indices [R^3]
+  // root culling: per occupancy cell a 64-bit mask of the sub-cells where a root
+  // is possible, for pose sub_pose (-1: none; any change of the blended grid
+  // clears it), and the occupancy cells to search
+  unsigned long long* d_sub = nullptr;  // [R^3]
+  unsigned* d_cand_count = nullptr;
+  int* d_cand = nullptr;                // [R^3]
+  int sub_pose = -1;
   bool occ_cull = true;
   bool have_occ = false;
   // counters
@@ -248,6 +253,7 @@ BoxDev box_dev(const ia_ctx* c) {
     const float ext = c->nmax[a] - c->nmin[a];  // fp32, as the documented indexing
     b.cell_scale[a] = (float)b.R / ext;
     b.cell_size[a] = ext / (float)b.R;
+    b.sub_scale[a] = (float)(kSub * b.R) / ext;
   }
   return b;
 }
@@ -256,16 +262,17 @@ BoxDev box_dev(const ia_ctx* c) {
 // norm_min + (c + jitter) * cell size) into sigma [R^3]: with culling on, only
 // the cells whose point can have a root are searched, the rest get 0 (the same
 // values the full search gives).
-cudaError_t occ_density(const ia_ctx* c, int pose, const float* jitter, float* sigma, unsigned long long* stats,
+// The culling masks built here stay valid for the render of the same pose.
+cudaError_t occ_density(ia_ctx* c, int pose, const float* jitter, float* sigma, unsigned long long* stats,
                         cudaStream_t s) {
   const PosedArgs a = occ_args(c, pose);
   const BoxDev box = box_dev(c);
   if (!c->occ_cull) return launch_occ_density(a, box, jitter, nullptr, nullptr, sigma, stats, c->d_work, c->num_sms, s);
-  const int R = c->cfg.occ_res;
-  const unsigned* count = c->d_cull + ((size_t)R * R * R + 31) / 32;
-  cudaError_t e = launch_occ_cull(a, box, jitter, c->d_cull, c->d_cand, sigma, s);
+  c->sub_pose = -1;
+  cudaError_t e = launch_occ_cull(a, box, jitter, c->d_sub, c->d_cand_count, c->d_cand, sigma, stats, s);
   if (e != cudaSuccess) return e;
-  return launch_occ_density(a, box, jitter, c->d_cand, count, sigma, stats, c->d_work, c->num_sms, s);
+  c->sub_pose = pose;
+  return launch_occ_density(a, box, jitter, c->d_cand, c->d_cand_count, sigma, stats, c->d_work, c->num_sms, s);
 }
 
 ia_status need_ready(ia_ctx* c, int pose, bool need_occ) {
@@ -293,6 +300,7 @@ void read_stats(ia_ctx* c, ia_render_stats* out, cudaStream_t s, const unsigned 
   out->early_stopped = (int64_t)h[ST_EARLY];
   out->proposed = (int64_t)h[ST_PROP];
   out->fallbacks = (int64_t)h[ST_FALLBACK];
+  out->culled = (int64_t)h[ST_CULLED];
 }
 
 }  // namespace
@@ -358,7 +366,8 @@ ia_status ia_create(const ia_config* cfg, ia_ctx** out) {
   if (e == cudaSuccess) e = dalloc(&c->d_occ_train, words);
   if (e == cudaSuccess) e = dalloc(&c->d_sigma, (size_t)R * R * R);
   if (e == cudaSuccess) e = dalloc(&c->d_occ_ema, (size_t)R * R * R);
-  if (e == cudaSuccess) e = dalloc(&c->d_cull, words + 1);
+  if (e == cudaSuccess) e = dalloc(&c->d_sub, (size_t)R * R * R);
+  if (e == cudaSuccess) e = dalloc(&c->d_cand_count, (size_t)1);
   if (e == cudaSuccess) e = dalloc(&c->d_cand, (size_t)R * R * R);
   if (e == cudaSuccess) e = cudaMemset(c->d_occ_ema, 0, sizeof(float) * R * R * R);
   if (e == cudaSuccess) e = dalloc(&c->d_stats, (size_t)ST_COUNT);
@@ -395,7 +404,8 @@ void ia_destroy(ia_ctx* c) {
   dfree(c->d_occ_train);
   dfree(c->d_sigma);
   dfree(c->d_occ_ema);
-  dfree(c->d_cull);
+  dfree(c->d_sub);
+  dfree(c->d_cand_count);
   dfree(c->d_cand);
   dfree(c->d_stats);
   dfree(c->d_counter);
@@ -476,6 +486,7 @@ ia_status ia_set_skeleton(ia_ctx* c, int n_bones, const int32_t* parent, const d
     c->nmax[a] = norm_max[a];
   }
   c->n_poses = 0;  // per-pose state depends on the skeleton
+  c->sub_pose = -1;
   c->have_occ = false;
   return IA_OK;
 }
@@ -546,6 +557,7 @@ ia_status ia_set_pose(ia_ctx* c, int n_poses, const double* axis_angle, const do
   IA_CUDA(c, launch_pose_chain(n_poses, c->nb, c->d_parent, c->d_rest, c->d_theta, c->d_trans, c->d_N, c->d_Ninv,
                                c->d_B0inv, s),
           "ia_set_pose: pose chain");
+  c->sub_pose = -1;  // the culling masks belong to the previous grids
   IA_CUDA(c, launch_blend(n_poses, (int)V, c->nb, c->d_skin, c->d_N, c->d_M, s), "ia_set_pose: blend grid");
   c->n_poses = n_poses;
   return IA_OK;
@@ -677,6 +689,7 @@ static RenderArgs render_args(ia_ctx* c, int pose, const ia_camera* cam) {
   a.P = posed_args(c, pose);
   a.B0inv = c->d_B0inv + (size_t)pose * 12;
   a.occ = c->d_occ;
+  a.sub = (c->occ_cull && c->sub_pose == pose) ? c->d_sub : nullptr;
   a.box = box_dev(c);
   a.cam.fx = cam->fx;
   a.cam.fy = cam->fy;
@@ -929,6 +942,7 @@ ia_status ia_adam_step(ia_ctx* c, const float* g_table, const float* g_mlp, cons
                            s),
             "ia_adam_step: skinning grid");
     if (c->n_poses > 0)
+      c->sub_pose = -1;
       IA_CUDA(c, launch_blend(c->n_poses, (int)V, c->nb, c->d_skin, c->d_N, c->d_M, s), "ia_adam_step: blend grid");
   }
   return IA_OK;

@@ -28,8 +28,32 @@ struct BoxDev {
   float nmin[3], nmax[3];
   float cell_scale[3];  // R / (nmax - nmin)
   float cell_size[3];   // (nmax - nmin) / R
+  float sub_scale[3];   // kSub R / (nmax - nmin)
   int R;
 };
+
+// Sub-cells of the occupancy grid, kSub^3 per cell, for the root-culling masks:
+// the global sub-cell index of x along axis a is floor((x_a - nmin_a) *
+// sub_scale_a) in fp32 (monotone in x), and bit sx + kSub (sy + kSub sz) of
+// sub[c] stands for sub-cell (kSub c + s) of cell c.
+constexpr int kSub = 4;
+
+// False only when the sub-cell holding x meets none of the boxes the culling
+// kernel marked, i.e. when no root is possible at x; points outside the grid
+// are never excluded.
+__device__ __forceinline__ bool sub_marked(const unsigned long long* __restrict__ sub, const BoxDev& bx, float3 x) {
+  const float xs[3] = {x.x, x.y, x.z};
+  int g[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float f = floorf(__fmul_rn(__fsub_rn(xs[a], bx.nmin[a]), bx.sub_scale[a]));
+    if (!(f >= 0.f && f <= (float)(kSub * bx.R - 1))) return true;
+    g[a] = (int)f;
+  }
+  const int cell = g[0] / kSub + bx.R * (g[1] / kSub + bx.R * (g[2] / kSub));
+  const int bit = g[0] % kSub + kSub * (g[1] % kSub + kSub * (g[2] % kSub));
+  return (__ldg(sub + cell) >> bit) & 1ull;
+}
 
 __device__ __forceinline__ float dot3_rn(float a0, float a1, float a2, float b0, float b1, float b2) {
   return __fadd_rn(__fadd_rn(__fmul_rn(a0, b0), __fmul_rn(a1, b1)), __fmul_rn(a2, b2));

@@ -27,6 +27,7 @@ __device__ __forceinline__ int next_list(unsigned* work) {
 
 enum StatIdx {
   ST_RAYS = 0, ST_HIT, ST_MARCHED, ST_OCC, ST_STARTS, ST_ITERS, ST_CONV, ST_ROOTS, ST_EARLY, ST_PROP, ST_FALLBACK,
+  ST_CULLED,
   ST_COUNT = 16
 };
 
@@ -67,6 +68,7 @@ struct RenderArgs {
   PosedArgs P;
   const float* B0inv;  // [12]
   const uint32_t* occ;
+  const unsigned long long* sub;  // root-culling masks of this pose, or null
   BoxDev box;
   CamDev cam;
   int n_slots;
@@ -218,8 +220,8 @@ cudaError_t launch_blend(int P, int V, int nb, const float* W, const float* N, f
 cudaError_t launch_occ_density(const PosedArgs& a, const BoxDev& box, const float* jitter, const int* cells,
                                const unsigned* count, float* sigma, unsigned long long* stats, unsigned* work,
                                int num_sms, cudaStream_t s);
-cudaError_t launch_occ_cull(const PosedArgs& a, const BoxDev& box, const float* jitter, uint32_t* mask,
-                            int* cells, float* sigma, cudaStream_t s);
+cudaError_t launch_occ_cull(const PosedArgs& a, const BoxDev& box, const float* jitter, unsigned long long* sub,
+                            unsigned* count, int* cells, float* sigma, unsigned long long* stats, cudaStream_t s);
 cudaError_t launch_gather_probe(const float4* table, int64_t n_records, int iters, int blocks, float* sink,
                                 cudaStream_t s);
 cudaError_t launch_occ_ema(const float* sigma, float* d, int n, float decay, cudaStream_t s);

@@ -264,14 +264,19 @@ cudaError_t launch_occ_density(const PosedArgs& a, const BoxDev& box, const floa
 // over one cell, mostly far below a cell).  A query point with a root is within
 // the Broyden tolerance of f(cell) for some cell, so a point outside all these
 // boxes, grown by `slack` (the tolerance plus a margin far above fp32
-// rounding), has no root and density 0: the search would end with none.
+// rounding), has no root and density 0: the search would end with none.  The
+// boxes are recorded at the resolution of kSub^3 sub-cells per occupancy cell
+// (a 64-bit mask per cell), which the occupancy queries and the render's
+// samples test.
 // ---------------------------------------------------------------------------
 
 // One lane per skinning-grid cell, a warp per 4 x 4 x 2 block of cells: marks
-// the occupancy cells meeting the cell's image box (the index of a point is
-// floor((x - norm_min) * R / extent) in fp32, monotone in x, so the range of
-// the box's two corners holds the index of every point inside).
-__global__ void occ_cover_kernel(const SkinDev S, const BoxDev box, float slack, uint32_t* __restrict__ mask) {
+// the occupancy sub-cells meeting the cell's image box (sub_marked's index of a
+// point is monotone in x, so the range of the box's two corners holds the index
+// of every point inside), one 64-bit OR per occupancy cell the box meets.
+__global__ void occ_cover_kernel(const SkinDev S, const BoxDev box, float slack,
+                                 unsigned long long* __restrict__ sub) {
+  static_assert(kSub * kSub * kSub == 64, "one 64-bit word per occupancy cell");
   const int nc = S.Rw - 1;  // cells per axis
   const int tx = (nc + 3) / 4, ty = (nc + 3) / 4, tz = (nc + 1) / 2;
   const int tile = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
@@ -312,7 +317,8 @@ __global__ void occ_cover_kernel(const SkinDev S, const BoxDev box, float slack,
 #pragma unroll
     for (int q = 0; q < 9; ++q) mean[q] += 0.125f * A[corner][q];
   }
-  int i0[3], i1[3];
+  const int ns = kSub * box.R;  // sub-cells per axis
+  int s0[3], s1[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     float m = 0.f;
@@ -320,50 +326,44 @@ __global__ void occ_cover_kernel(const SkinDev S, const BoxDev box, float slack,
     for (int corner = 0; corner < 8; ++corner)
       m = fmaxf(m, fabsf(A[corner][3 * a] - mean[3 * a]) * h[0] + fabsf(A[corner][3 * a + 1] - mean[3 * a + 1]) * h[1] +
                        fabsf(A[corner][3 * a + 2] - mean[3 * a + 2]) * h[2]);
-    // the density kernel's index arithmetic (fp32), clamped before the conversion
+    // sub_marked's index arithmetic (fp32), clamped before the conversion
     const float g = m + slack;
-    const float f0 = floorf(__fmul_rn(__fsub_rn(lo[a] - g, box.nmin[a]), box.cell_scale[a]));
-    const float f1 = floorf(__fmul_rn(__fsub_rn(hi[a] + g, box.nmin[a]), box.cell_scale[a]));
-    if (!(f1 >= 0.f) || !(f0 <= (float)(box.R - 1))) return;  // the box misses the grid
-    i0[a] = (int)fmaxf(f0, 0.f);
-    i1[a] = (int)fminf(f1, (float)(box.R - 1));
+    const float f0 = floorf(__fmul_rn(__fsub_rn(lo[a] - g, box.nmin[a]), box.sub_scale[a]));
+    const float f1 = floorf(__fmul_rn(__fsub_rn(hi[a] + g, box.nmin[a]), box.sub_scale[a]));
+    if (!(f1 >= 0.f) || !(f0 <= (float)(ns - 1))) return;  // the box misses the grid
+    s0[a] = (int)fmaxf(f0, 0.f);
+    s1[a] = (int)fminf(f1, (float)(ns - 1));
   }
-  for (int z = i0[2]; z <= i1[2]; ++z)
-    for (int y = i0[1]; y <= i1[1]; ++y)
-      for (int x = i0[0]; x <= i1[0]; ++x) {
-        const int c = x + box.R * (y + box.R * z);
-        atomicOr(mask + (c >> 5), 1u << (c & 31));
+  for (int z = s0[2] / kSub; z <= s1[2] / kSub; ++z) {
+    const int z0 = max(s0[2] - kSub * z, 0), z1 = min(s1[2] - kSub * z, kSub - 1);
+    for (int y = s0[1] / kSub; y <= s1[1] / kSub; ++y) {
+      const int y0 = max(s0[1] - kSub * y, 0), y1 = min(s1[1] - kSub * y, kSub - 1);
+      for (int x = s0[0] / kSub; x <= s1[0] / kSub; ++x) {
+        const int x0 = max(s0[0] - kSub * x, 0), x1 = min(s1[0] - kSub * x, kSub - 1);
+        const unsigned long long row = ((1ull << (x1 + 1)) - 1ull) & ~((1ull << x0) - 1ull);
+        unsigned long long m = 0ull;
+        for (int sz = z0; sz <= z1; ++sz)
+          for (int sy = y0; sy <= y1; ++sy) m |= row << (kSub * (sy + kSub * sz));
+        atomicOr(sub + (x + box.R * (y + box.R * z)), m);
       }
+    }
+  }
 }
 
-// One thread per occupancy cell: its query point (the density kernel's), the
-// cell that point falls in, and that cell's mark.  Points that can have a root
-// go to `cells` (one atomic per warp; order across warps is free, since each
-// cell's search is independent of the others); the others get density 0.
-// Points outside the grid (a jitter outside [0, 1)) are always searched.
+// One thread per occupancy cell: its query point (the density kernel's) and
+// that point's sub-cell mark.  Points that can have a root go to `cells` (one
+// atomic per warp; order across warps is free, since each cell's search is
+// independent of the others); the others get density 0.
 __global__ void occ_cand_kernel(const BoxDev box, const float* __restrict__ jitter,
-                                const uint32_t* __restrict__ mask, int* __restrict__ cells,
-                                unsigned* __restrict__ count, float* __restrict__ sigma) {
+                                const unsigned long long* __restrict__ sub, int* __restrict__ cells,
+                                unsigned* __restrict__ count, float* __restrict__ sigma,
+                                unsigned long long* __restrict__ stats) {
   const int n = box.R * box.R * box.R;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   bool cand = false;
   if (c < n) {
     const float3 x = jitter ? cell_point(box, c, jitter + 3 * (size_t)c) : cell_center(box, c);
-    const float xs[3] = {x.x, x.y, x.z};
-    int q[3];
-    bool inside = true;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float f = floorf(__fmul_rn(__fsub_rn(xs[a], box.nmin[a]), box.cell_scale[a]));
-      inside = inside && f >= 0.f && f <= (float)(box.R - 1);
-      q[a] = inside ? (int)f : 0;
-    }
-    if (inside) {
-      const int b = q[0] + box.R * (q[1] + box.R * q[2]);
-      cand = (__ldg(mask + (b >> 5)) >> (b & 31)) & 1u;
-    } else {
-      cand = true;
-    }
+    cand = sub_marked(sub, box, x);
     if (!cand) sigma[c] = 0.f;
   }
   const unsigned m = __ballot_sync(kFull, cand);
@@ -372,16 +372,17 @@ __global__ void occ_cand_kernel(const BoxDev box, const float* __restrict__ jitt
   if (lane == 0 && m) base = atomicAdd(count, (unsigned)__popc(m));
   base = __shfl_sync(kFull, base, 0);
   if (cand) cells[base + __popc(m & ((1u << lane) - 1u))] = c;
+  const unsigned culled = __ballot_sync(kFull, c < n && !cand);
+  if (stats && lane == 0 && culled) atomicAdd(stats + ST_CULLED, (unsigned long long)__popc(culled));
 }
 
-// mask: (R^3 + 31) / 32 words followed by the candidate count (cleared here)
-cudaError_t launch_occ_cull(const PosedArgs& a, const BoxDev& box, const float* jitter, uint32_t* mask,
-                            int* cells, float* sigma, cudaStream_t s) {
+// sub: [R^3] masks (rebuilt here); count: the candidate count (cleared here)
+cudaError_t launch_occ_cull(const PosedArgs& a, const BoxDev& box, const float* jitter, unsigned long long* sub,
+                            unsigned* count, int* cells, float* sigma, unsigned long long* stats, cudaStream_t s) {
   const int n = box.R * box.R * box.R;
-  const size_t words = ((size_t)n + 31) / 32;
-  unsigned* count = mask + words;
-  cudaError_t e = cudaMemsetAsync(mask, 0, (words + 1) * sizeof(uint32_t), s);
+  cudaError_t e = cudaMemsetAsync(sub, 0, (size_t)n * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(count, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
   // slack: the Broyden tolerance plus 1e-4 of the scene's largest coordinate
   // (fp32 rounding of the LBS map and of these bounds is below 1e-6 of it)
   float L = 0.f;
@@ -390,9 +391,9 @@ cudaError_t launch_occ_cull(const PosedArgs& a, const BoxDev& box, const float* 
   const float slack = std::sqrt(a.cfg.tol2) + 1e-4f * L;
   const int nc = a.S.Rw - 1;
   const int tiles = ((nc + 3) / 4) * ((nc + 3) / 4) * ((nc + 1) / 2);
-  occ_cover_kernel<<<(tiles + 7) / 8, 256, 0, s>>>(a.S, box, slack, mask);
+  occ_cover_kernel<<<(tiles + 7) / 8, 256, 0, s>>>(a.S, box, slack, sub);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  occ_cand_kernel<<<(n + 255) / 256, 256, 0, s>>>(box, jitter, mask, cells, count, sigma);
+  occ_cand_kernel<<<(n + 255) / 256, 256, 0, s>>>(box, jitter, sub, cells, count, sigma, stats);
   return cudaGetLastError();
 }
 
@@ -550,9 +551,10 @@ cudaError_t launch_query_canonical(const PosedArgs& a, int n, const float* x, fl
 // Every warp runs on its own: it keeps a pool of 32 rays, one per lane, and
 // loops over rounds with warp-level synchronisation only.  A round:
 //  1. march: every ray advances its slot cursor until it has found up to K
-//     slots in occupied cells (empty-space skipping); exhausted rays write
-//     their pixel and take the next ray from a global counter (one atomic per
-//     warp);
+//     slots in occupied cells (empty-space skipping) whose point can have a
+//     root (the pose's root-culling masks, when present: the others have
+//     density 0); exhausted rays write their pixel and take the next ray from
+//     a global counter (one atomic per warp);
 //  2. a warp scan packs the found (ray, slot) samples into shared memory;
 //  3. the warp evaluates them 32 at a time: bone-wise Broyden search, polish,
 //     hash encoding, MLP, max-density root;
@@ -599,7 +601,7 @@ __global__ void __launch_bounds__(kRenderThreads, IA_RENDER_MIN_BLOCKS) render_k
   int pix = 0, cursor = 0;
   float depth = 0.f;  // optical depth sum sigma_i delta
   float cr = 0.f, cg = 0.f, cb = 0.f;
-  unsigned n_rays = 0, n_hit = 0, n_marched = 0, n_occ = 0, n_early = 0;
+  unsigned n_rays = 0, n_hit = 0, n_marched = 0, n_occ = 0, n_early = 0, n_culled = 0;
   SampleStats st;
 
   while (true) {
@@ -615,10 +617,14 @@ __global__ void __launch_bounds__(kRenderThreads, IA_RENDER_MIN_BLOCKS) render_k
           const int cell = cell_of(a.box, x);
           ++n_marched;
           if ((__ldg(a.occ + (cell >> 5)) >> (cell & 31)) & 1u) {
+            if (a.sub && !sub_marked(a.sub, a.box, x)) {
+              ++n_culled;  // no root possible: density 0, nothing to composite
+            } else {
 #pragma unroll
-            for (int q = 0; q < K; ++q)
-              if (q == nfound) slots[q] = cursor;
-            ++nfound;
+              for (int q = 0; q < K; ++q)
+                if (q == nfound) slots[q] = cursor;
+              ++nfound;
+            }
           }
           ++cursor;
         }
@@ -731,7 +737,8 @@ __global__ void __launch_bounds__(kRenderThreads, IA_RENDER_MIN_BLOCKS) render_k
     flush_stats(a.stats, ST_RAYS, n_rays);
     flush_stats(a.stats, ST_HIT, n_hit);
     flush_stats(a.stats, ST_MARCHED, n_marched);
-    flush_stats(a.stats, ST_OCC, n_occ);
+    flush_stats(a.stats, ST_OCC, n_occ + n_culled);
+    flush_stats(a.stats, ST_CULLED, n_culled);
     flush_stats(a.stats, ST_STARTS, st.starts);
     flush_stats(a.stats, ST_ITERS, st.iters);
     flush_stats(a.stats, ST_CONV, st.converged);

@@ -126,3 +126,68 @@ def test_culled_search_against_oracle(ia):
     np.testing.assert_array_equal(diff_on, diff_off)
     assert diff_on.sum() <= 1e-3 * R ** 3
     ia.ia_destroy(ctx)
+
+
+def _render(ia, ctx, pose, icam, n, cull):
+    ia.ia_set_occupancy_culling(ctx, cull)
+    ia.ia_update_occupancy(ctx, pose)
+    rgb = torch.zeros(n, 3, device="cuda")
+    alpha = torch.zeros(n, device="cuda")
+    st = ia.ia_render(ctx, pose, icam, rgb, alpha, stats=True)
+    torch.cuda.synchronize()
+    return rgb.cpu().numpy(), alpha.cpu().numpy(), st
+
+
+@pytest.mark.parametrize("mode", ["fp32", "fp16_proposal"])
+def test_render_culling_keeps_every_pixel(ia, mode):
+    """Samples whose point can have no root are not searched; the frame is
+    bit-identical to the one that searches them (with early termination on, as
+    in the frame benchmark).  The proposal mode uses an untrained network, so
+    most proposals fail and the fallback search runs often."""
+    from gpu_helpers import camera
+    sc = S.make_scene("full", 0)
+    table, mlp = S.make_field(sc, 0)
+    prec = ia.IA_FP32 if mode == "fp32" else ia.IA_FP16
+    cfg = ia.make_config(n_levels=sc.n_levels, log2_table=sc.log2_table, level_res=sc.level_res,
+                         max_samples=sc.max_samples, occ_res=sc.occ_res, occ_tau=sc.occ_tau,
+                         occ_dilate=sc.occ_dilate, early_stop_T=1e-4, precision=prec)
+    ctx = ia.ia_create(cfg)
+    ia.ia_set_skeleton(ctx, sc.parents, sc.rest_joints, sc.skin_grid, sc.canon_min, sc.canon_max,
+                       sc.norm_min, sc.norm_max)
+    ia.ia_set_params(ctx, torch.from_numpy(table).cuda(), torch.from_numpy(S.pack_mlp(mlp)).cuda())
+    poses = [S.make_pose(sc, s) for s in (2, 9)]
+    ia.ia_set_pose(ctx, np.stack([p[0] for p in poses]), np.stack([p[1] for p in poses]))
+    if mode == "fp16_proposal":
+        pc = S.proposal_config()
+        ia.ia_proposal_init(ctx, ia.make_proposal_config(pc["n_levels"], pc["log2_table"], pc["level_res"],
+                                                         pc["top_k"], pc["offset_weight"]))
+        pt, pm = S.proposal_init(sc, pc, 3)
+        ia.ia_proposal_set_params(ctx, torch.from_numpy(pt).cuda(), torch.from_numpy(S.pack_proposal(pm)).cuda())
+        ia.ia_set_search(ctx, ia.IA_SEARCH_PROPOSAL)
+    cam = S.make_camera(sc)
+    icam = camera(ia, cam)
+    n = cam["width"] * cam["height"]
+    for pose in range(2):
+        r0, a0, st0 = _render(ia, ctx, pose, icam, n, False)
+        r1, a1, st1 = _render(ia, ctx, pose, icam, n, True)
+        print(f"{mode} pose {pose}: culled {st1['culled']} of {st1['occupied_samples']} samples, "
+              f"starts {st1['starts']} vs {st0['starts']}, fallbacks {st1['fallbacks']} vs {st0['fallbacks']}")
+        np.testing.assert_array_equal(r1, r0)
+        np.testing.assert_array_equal(a1, a0)
+        assert st0["culled"] == 0 and st1["culled"] > 0
+        assert st1["starts"] < st0["starts"]
+        if mode == "fp32":  # the queues' root count depends on the list composition
+            assert st1["roots"] == st0["roots"]
+        assert (a1 > 0).sum() > 0.05 * n
+    # the masks belong to the pose of the last occupancy update: rendering another
+    # pose (here with that pose's grid) culls nothing
+    ia.ia_update_occupancy(ctx, 0)
+    rgb = torch.zeros(n, 3, device="cuda")
+    alpha = torch.zeros(n, device="cuda")
+    st = ia.ia_render(ctx, 1, icam, rgb, alpha, stats=True)
+    assert st["culled"] == 0
+    # so does a grid whose pose's blended grid has changed since
+    ia.ia_set_pose(ctx, np.stack([p[0] for p in poses]), np.stack([p[1] for p in poses]))
+    st = ia.ia_render(ctx, 0, icam, rgb, alpha, stats=True)
+    assert st["culled"] == 0
+    ia.ia_destroy(ctx)

@@ -181,7 +181,9 @@ def test_trained_proposal_gains_over_plain_search(ia, trained):
         hit = a0 > 0
         print(f"pose {i}: search work plain {work0} -> proposal {work1} ({work0 / work1:.1f}x), "
               f"fallbacks {sp['fallbacks']}/{sp['proposed']}, rays differing {diff.sum()}/{hit.sum()}")
-        assert sp["proposed"] == s0["occupied_samples"]
+        # every searched sample takes the proposal (culled ones have no root and are not searched)
+        assert sp["proposed"] == s0["occupied_samples"] - s0["culled"]
+        assert sp["culled"] == s0["culled"]
         assert work0 >= 4 * work1
         miss_tot += diff.sum()
         has_tot += hit.sum()

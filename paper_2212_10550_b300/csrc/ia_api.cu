@@ -57,6 +57,10 @@ struct ia_ctx {
   int* d_cand = nullptr;                // [R^3]
   int sub_pose = -1;
   bool occ_cull = true;
+  // the same masks for every pose, for the training step: [sub_all_cap][R^3]
+  unsigned long long* d_sub_all = nullptr;
+  int sub_all_cap = 0;
+  bool sub_all_valid = false;
   bool have_occ = false;
   // counters
   unsigned long long* d_stats = nullptr;
@@ -405,6 +409,7 @@ void ia_destroy(ia_ctx* c) {
   dfree(c->d_sigma);
   dfree(c->d_occ_ema);
   dfree(c->d_sub);
+  dfree(c->d_sub_all);
   dfree(c->d_cand_count);
   dfree(c->d_cand);
   dfree(c->d_stats);
@@ -487,6 +492,7 @@ ia_status ia_set_skeleton(ia_ctx* c, int n_bones, const int32_t* parent, const d
   }
   c->n_poses = 0;  // per-pose state depends on the skeleton
   c->sub_pose = -1;
+  c->sub_all_valid = false;
   c->have_occ = false;
   return IA_OK;
 }
@@ -558,6 +564,7 @@ ia_status ia_set_pose(ia_ctx* c, int n_poses, const double* axis_angle, const do
                                c->d_B0inv, s),
           "ia_set_pose: pose chain");
   c->sub_pose = -1;  // the culling masks belong to the previous grids
+  c->sub_all_valid = false;
   IA_CUDA(c, launch_blend(n_poses, (int)V, c->nb, c->d_skin, c->d_N, c->d_M, s), "ia_set_pose: blend grid");
   c->n_poses = n_poses;
   return IA_OK;
@@ -831,11 +838,32 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
   TrainArgs a{};
   a.P = posed_args(c, 0);
   a.V = (int)V;
+  a.box = box_dev(c);
+  // root-culling masks of every pose, built on the first step after the blended
+  // grids changed (one launch over all poses; skipped above 4 GiB)
+  a.sub = nullptr;
+  if (c->occ_cull) {
+    const size_t per = (size_t)c->cfg.occ_res * c->cfg.occ_res * c->cfg.occ_res;
+    if ((size_t)c->n_poses * per * sizeof(unsigned long long) <= (size_t(4) << 30)) {
+      if (c->n_poses > c->sub_all_cap) {
+        IA_CUDA(c, cudaStreamSynchronize(s), "ia_train_step");
+        c->sub_all_cap = 0;
+        c->sub_all_valid = false;
+        IA_CUDA(c, dalloc(&c->d_sub_all, (size_t)c->n_poses * per), "ia_train_step: culling masks");
+        c->sub_all_cap = c->n_poses;
+      }
+      if (!c->sub_all_valid) {
+        IA_CUDA(c, launch_occ_cover(a.P.S, (int)V, c->n_poses, a.P.cfg, a.box, c->d_sub_all, s),
+                "ia_train_step: culling masks");
+        c->sub_all_valid = true;
+      }
+      a.sub = c->d_sub_all;
+    }
+  }
   a.B0inv = c->d_B0inv;
   a.N = c->d_N;
   a.skin = c->d_skin;
   a.occ = occ_grid == IA_OCC_POSE ? c->d_occ : c->d_occ_train;
-  a.box = box_dev(c);
   a.n_slots = N;
   a.n_rays = n;
   a.origin = b->origin;
@@ -943,6 +971,7 @@ ia_status ia_adam_step(ia_ctx* c, const float* g_table, const float* g_mlp, cons
             "ia_adam_step: skinning grid");
     if (c->n_poses > 0)
       c->sub_pose = -1;
+      c->sub_all_valid = false;
       IA_CUDA(c, launch_blend(c->n_poses, (int)V, c->nb, c->d_skin, c->d_N, c->d_M, s), "ia_adam_step: blend grid");
   }
   return IA_OK;

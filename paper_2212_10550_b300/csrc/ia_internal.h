@@ -94,6 +94,7 @@ struct TrainArgs {
   const float* N;        // [n_poses][nb][12]
   const float* skin;     // [V][nb]
   const uint32_t* occ;
+  const unsigned long long* sub;  // root-culling masks [n_poses][R^3], or null
   BoxDev box;
   int n_slots;
   int n_rays;
@@ -220,6 +221,8 @@ cudaError_t launch_blend(int P, int V, int nb, const float* W, const float* N, f
 cudaError_t launch_occ_density(const PosedArgs& a, const BoxDev& box, const float* jitter, const int* cells,
                                const unsigned* count, float* sigma, unsigned long long* stats, unsigned* work,
                                int num_sms, cudaStream_t s);
+cudaError_t launch_occ_cover(const SkinDev& S, int V, int n_poses, const SolveCfg& cfg, const BoxDev& box,
+                             unsigned long long* sub, cudaStream_t s);
 cudaError_t launch_occ_cull(const PosedArgs& a, const BoxDev& box, const float* jitter, unsigned long long* sub,
                             unsigned* count, int* cells, float* sigma, unsigned long long* stats, cudaStream_t s);
 cudaError_t launch_gather_probe(const float4* table, int64_t n_records, int iters, int blocks, float* sink,

@@ -274,9 +274,12 @@ cudaError_t launch_occ_density(const PosedArgs& a, const BoxDev& box, const floa
 // the occupancy sub-cells meeting the cell's image box (sub_marked's index of a
 // point is monotone in x, so the range of the box's two corners holds the index
 // of every point inside), one 64-bit OR per occupancy cell the box meets.
-__global__ void occ_cover_kernel(const SkinDev S, const BoxDev box, float slack,
+// blockIdx.y: the pose (blended grid S.M + pose * V * 3, masks sub + pose * R^3).
+__global__ void occ_cover_kernel(SkinDev S, int V, const BoxDev box, float slack,
                                  unsigned long long* __restrict__ sub) {
   static_assert(kSub * kSub * kSub == 64, "one 64-bit word per occupancy cell");
+  S.M += (size_t)blockIdx.y * V * 3;
+  sub += (size_t)blockIdx.y * box.R * box.R * box.R;
   const int nc = S.Rw - 1;  // cells per axis
   const int tx = (nc + 3) / 4, ty = (nc + 3) / 4, tz = (nc + 1) / 2;
   const int tile = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
@@ -376,23 +379,32 @@ __global__ void occ_cand_kernel(const BoxDev box, const float* __restrict__ jitt
   if (stats && lane == 0 && culled) atomicAdd(stats + ST_CULLED, (unsigned long long)__popc(culled));
 }
 
-// sub: [R^3] masks (rebuilt here); count: the candidate count (cleared here)
-cudaError_t launch_occ_cull(const PosedArgs& a, const BoxDev& box, const float* jitter, unsigned long long* sub,
-                            unsigned* count, int* cells, float* sigma, unsigned long long* stats, cudaStream_t s) {
-  const int n = box.R * box.R * box.R;
-  cudaError_t e = cudaMemsetAsync(sub, 0, (size_t)n * sizeof(unsigned long long), s);
+// The root-culling masks of n_poses consecutive blended grids (S.M = the
+// first, V vertices each) into sub [n_poses][R^3] (cleared here).
+cudaError_t launch_occ_cover(const SkinDev& S, int V, int n_poses, const SolveCfg& cfg, const BoxDev& box,
+                             unsigned long long* sub, cudaStream_t s) {
+  const size_t n = (size_t)box.R * box.R * box.R;
+  cudaError_t e = cudaMemsetAsync(sub, 0, n * n_poses * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(count, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
   // slack: the Broyden tolerance plus 1e-4 of the scene's largest coordinate
   // (fp32 rounding of the LBS map and of these bounds is below 1e-6 of it)
   float L = 0.f;
   for (int k = 0; k < 3; ++k)
-    L = std::max({L, std::fabs(a.S.cmin[k]), std::fabs(a.S.cmax[k]), std::fabs(box.nmin[k]), std::fabs(box.nmax[k])});
-  const float slack = std::sqrt(a.cfg.tol2) + 1e-4f * L;
-  const int nc = a.S.Rw - 1;
+    L = std::max({L, std::fabs(S.cmin[k]), std::fabs(S.cmax[k]), std::fabs(box.nmin[k]), std::fabs(box.nmax[k])});
+  const float slack = std::sqrt(cfg.tol2) + 1e-4f * L;
+  const int nc = S.Rw - 1;
   const int tiles = ((nc + 3) / 4) * ((nc + 3) / 4) * ((nc + 1) / 2);
-  occ_cover_kernel<<<(tiles + 7) / 8, 256, 0, s>>>(a.S, box, slack, sub);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  occ_cover_kernel<<<dim3((tiles + 7) / 8, n_poses), 256, 0, s>>>(S, V, box, slack, sub);
+  return cudaGetLastError();
+}
+
+// sub: [R^3] masks (rebuilt here); count: the candidate count (cleared here)
+cudaError_t launch_occ_cull(const PosedArgs& a, const BoxDev& box, const float* jitter, unsigned long long* sub,
+                            unsigned* count, int* cells, float* sigma, unsigned long long* stats, cudaStream_t s) {
+  const int n = box.R * box.R * box.R;
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  if ((e = launch_occ_cover(a.S, a.S.Rw * a.S.Rw * a.S.Rw, 1, a.cfg, box, sub, s)) != cudaSuccess) return e;
   occ_cand_kernel<<<(n + 255) / 256, 256, 0, s>>>(box, jitter, sub, cells, count, sigma, stats);
   return cudaGetLastError();
 }

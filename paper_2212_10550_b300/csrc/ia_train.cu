@@ -38,9 +38,13 @@ constexpr int kActF = 0, kActH1 = kIn, kActH2 = kActH1 + kWidth, kActD1 = kActH2
 // ---------------------------------------------------------------------------
 
 // March of one training ray in the normalised space of its pose: the occupied
-// slots in march order.  Returns the count; emit(i, x) is called for each.
+// slots in march order, except those whose point can have no root in that pose
+// (the pose's root-culling masks, when present: density 0 and no gradient, so
+// they change neither the ray's colour nor any gradient; counted in *culled).
+// Returns the count; emit(i, x) is called for each.
 template <typename Emit>
-__device__ __forceinline__ int march_train_ray(const TrainArgs& a, int r, int& pose, int& hit, float& dt, Emit emit) {
+__device__ __forceinline__ int march_train_ray(const TrainArgs& a, int r, int& pose, int& hit, float& dt, Emit emit,
+                                               int* culled = nullptr) {
   pose = a.pose[r];
   hit = 0;
   dt = 0.f;
@@ -51,23 +55,29 @@ __device__ __forceinline__ int march_train_ray(const TrainArgs& a, int r, int& p
   if (!normalise_and_clip(a.B0inv + 12 * (size_t)pose, a.box, ow, dw, o, d, tn, tf)) return 0;
   hit = 1;
   dt = slot_delta(tn, tf, a.n_slots);
-  int n = 0;
+  const unsigned long long* sub =
+      a.sub ? a.sub + (size_t)pose * a.box.R * a.box.R * a.box.R : nullptr;
+  int n = 0, nc = 0;
   for (int i = 0; i < a.n_slots; ++i) {
     const float3 x = slot_position(o, d, tn, dt, i);
     const int cell = cell_of(a.box, x);
-    if ((__ldg(a.occ + (cell >> 5)) >> (cell & 31)) & 1u) emit(n++, x);
+    if ((__ldg(a.occ + (cell >> 5)) >> (cell & 31)) & 1u) {
+      if (sub && !sub_marked(sub, a.box, x)) ++nc;
+      else emit(n++, x);
+    }
   }
+  if (culled) *culled = nc;
   return n;
 }
 
 // pass 1: per-ray sample counts and per-pose totals
 __global__ void train_count_kernel(const TrainArgs a) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  int n = 0, hit = 0;
+  int n = 0, hit = 0, culled = 0;
   if (r < a.n_rays) {
     int pose;
     float dt;
-    n = march_train_ray(a, r, pose, hit, dt, [](int, float3) {});
+    n = march_train_ray(a, r, pose, hit, dt, [](int, float3) {}, &culled);
     a.ray_n[r] = n;
     a.ray_dt[r] = dt;
     if (n > 0) atomicAdd(a.pose_tot + pose, n);
@@ -75,7 +85,8 @@ __global__ void train_count_kernel(const TrainArgs a) {
   flush_stats(a.stats, ST_RAYS, r < a.n_rays ? 1 : 0);
   flush_stats(a.stats, ST_HIT, hit);
   flush_stats(a.stats, ST_MARCHED, hit ? a.n_slots : 0);
-  flush_stats(a.stats, ST_OCC, n);
+  flush_stats(a.stats, ST_OCC, n + culled);
+  flush_stats(a.stats, ST_CULLED, culled);
 }
 
 // pass 2: per-pose totals -> first sample index of each pose; total count
@@ -120,6 +131,8 @@ __global__ void reg_count_kernel(const TrainArgs a) {
     const float3 x = make_float3(a.reg_x[3 * i], a.reg_x[3 * i + 1], a.reg_x[3 * i + 2]);
     const int cell = cell_of(a.box, x);
     keep = !((__ldg(a.occ + (cell >> 5)) >> (cell & 31)) & 1u);
+    // a point that can have no root has density 0: no loss, no gradient
+    if (keep && a.sub) keep = sub_marked(a.sub + (size_t)pose * a.box.R * a.box.R * a.box.R, a.box, x);
   }
   a.reg_idx[i] = keep ? 0 : -1;
   if (keep) atomicAdd(a.pose_tot + pose, 1);

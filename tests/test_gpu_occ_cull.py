@@ -191,3 +191,59 @@ def test_render_culling_keeps_every_pixel(ia, mode):
     st = ia.ia_render(ctx, 0, icam, rgb, alpha, stats=True)
     assert st["culled"] == 0
     ia.ia_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_training_culling_keeps_the_step(ia, prec):
+    """The training step skips samples (and regulariser points) whose point can
+    have no root in their own pose: per-ray colours are bit-identical, loss and
+    gradients equal up to the order of their fp32 atomic sums."""
+    sc = S.make_scene("full", 0)
+    table, mlp = S.make_field(sc, 0)
+    cfg = ia.make_config(n_levels=sc.n_levels, log2_table=sc.log2_table, level_res=sc.level_res,
+                         max_samples=sc.max_samples, occ_res=sc.occ_res, occ_tau=sc.occ_tau,
+                         occ_dilate=sc.occ_dilate, early_stop_T=0.0,
+                         precision=ia.IA_FP32 if prec == "fp32" else ia.IA_FP16)
+    ctx = ia.ia_create(cfg)
+    ia.ia_set_skeleton(ctx, sc.parents, sc.rest_joints, sc.skin_grid, sc.canon_min, sc.canon_max,
+                       sc.norm_min, sc.norm_max)
+    ia.ia_set_params(ctx, torch.from_numpy(table).cuda(), torch.from_numpy(S.pack_mlp(mlp)).cuda())
+    n_poses = 8
+    poses = [S.make_pose(sc, i) for i in range(n_poses)]
+    ia.ia_set_pose(ctx, np.stack([p[0] for p in poses]), np.stack([p[1] for p in poses]))
+    for i in range(n_poses):
+        ia.ia_update_occupancy(ctx, i, ia.IA_OCC_UNION)
+    rb = S.make_ray_batch(sc, 8192, n_poses, seed=4)
+    dev = {k: torch.from_numpy(np.ascontiguousarray(rb[k])).cuda() for k in ("origin", "direction", "pose", "target")}
+    rng = np.random.default_rng(5)
+    reg_x = torch.from_numpy(S.random_points(sc, 8192, seed=6)).cuda()
+    reg_pose = torch.from_numpy(rng.integers(0, n_poses, 8192).astype(np.int32)).cuda()
+    nt, nm = ia.ia_param_sizes(ctx)
+    out = {}
+    for cull in (False, True):
+        ia.ia_set_occupancy_culling(ctx, cull)
+        g = dict(table=torch.zeros(nt, device="cuda"), mlp=torch.zeros(nm, device="cuda"),
+                 skin=torch.zeros(sc.skin_res ** 3 * sc.n_bones, device="cuda"),
+                 bones=torch.zeros(n_poses * sc.n_bones * 12, device="cuda"))
+        loss = torch.zeros(1, device="cuda")
+        rgb = torch.zeros(8192, 3, device="cuda")
+        ia.ia_train_step(ctx, dev["origin"], dev["direction"], dev["pose"], dev["target"], loss, g,
+                         occ_grid=ia.IA_OCC_UNION, rgb_out=rgb, reg_x=reg_x, reg_pose=reg_pose, reg_weight=0.1)
+        st = ia.ia_train_stats(ctx)
+        torch.cuda.synchronize()
+        out[cull] = (float(loss.item()), rgb.cpu().numpy(), {k: v.cpu().numpy().astype(np.float64) for k, v in g.items()},
+                     st)
+    (l0, r0, g0, s0), (l1, r1, g1, s1) = out[False], out[True]
+    print(f"{prec}: culled {s1['culled']} of {s1['occupied_samples']} samples, starts {s1['starts']} vs {s0['starts']}, "
+          f"loss {l1:.8e} vs {l0:.8e}")
+    assert s0["culled"] == 0 and s1["culled"] > 0
+    assert s1["occupied_samples"] == s0["occupied_samples"]
+    assert s1["starts"] < s0["starts"]
+    np.testing.assert_array_equal(r1, r0)
+    assert abs(l1 - l0) <= 1e-6 * abs(l0)
+    for k in ("table", "mlp", "skin", "bones"):
+        rel = np.linalg.norm(g1[k] - g0[k]) / max(np.linalg.norm(g0[k]), 1e-30)
+        print(f"grad {k}: rel L2 {rel:.2e}")
+        assert np.count_nonzero(g0[k]) > 0
+        assert rel <= 1e-5, k
+    ia.ia_destroy(ctx)

@@ -163,16 +163,18 @@ ia_status ia_get_transforms(ia_ctx *ctx, int pose, float *N, float *Ninv, float 
  * then occupied = density > occ_tau, dilated by occ_dilate cells, packed so that
  * cell b = x + R (y + R z) is bit b % 32 of word b / 32.  IA_OCC_POSE replaces
  * the render grid; IA_OCC_UNION ORs the result into the training grid.  The
- * cells take the plain search over every bone even when ia_set_search selected
- * the proposal (most cells are empty space, where the proposal would fall back
- * to that search anyway).  Culling (on by default, ia_set_occupancy_culling)
- * searches only the cells whose query point can have a root: a root lies in the
- * canonical box, and the LBS image of each skinning-grid cell lies in the
- * bounding box of its corner images grown by the variation of the blended
- * rotation over the cell (times the cell's edges), the Broyden tolerance and a
- * rounding margin; a point outside every such box gets density 0 without a
- * search, which is what the search would return.  The densities are the same
- * with culling on or off.
+ * cells take the context's search (ia_set_search).  Culling (on by default,
+ * ia_set_occupancy_culling) searches only the cells whose query point can have
+ * a root: a root lies in the canonical box, and the LBS image of each
+ * skinning-grid cell lies in the bounding box of its corner images grown by the
+ * variation of the blended rotation over the cell (times the cell's edges), the
+ * Broyden tolerance and a rounding margin.  The boxes are recorded per 4x4x4
+ * sub-cells of each occupancy cell; a point whose sub-cell meets no box gets
+ * density 0 without a search, which is what the search would return.  The
+ * masks also serve ia_render of the same pose (until ia_set_pose or a skinning
+ * update changes its blended grid), whose samples in such sub-cells are not
+ * searched.  Densities are the same with culling on or off (up to the root
+ * merge order of the shared work queue: within rounding).
  *  sigma_out [R^3] fp32 device or NULL; bits_out [R^3 / 32] uint32 device or NULL. */
 ia_status ia_update_occupancy(ia_ctx *ctx, int pose, int mode, float *sigma_out,
                               uint32_t *bits_out, ia_render_stats *stats, void *stream);
@@ -415,9 +417,12 @@ ia_status ia_proposal_train(ia_ctx *ctx, int n, const float *x, const int32_t *p
                             void *stream);
 /* IA_SEARCH_ALL_BONES (the paper's search) or IA_SEARCH_PROPOSAL. */
 ia_status ia_set_search(ia_ctx *ctx, int mode);
-/* Occupancy culling of ia_update_occupancy, ia_update_occupancy_ema and
- * ia_update_occupancy_static: 1 (default) searches only the cells whose query
- * point can have a root, 0 searches every cell.  Same densities either way. */
+/* Root culling (see ia_update_occupancy): 1 (default) skips the search of
+ * occupancy cells, render samples (pose of the last occupancy update) and
+ * training samples and regulariser points (masks of every pose, built on the
+ * first training step after the blended grids change; skipped when they would
+ * exceed 4 GiB) whose point can have no root; 0 searches them all.  Results
+ * are the same either way. */
 ia_status ia_set_occupancy_culling(ia_ctx *ctx, int on);
 
 /* The sample set of ia_render without evaluating it (the indexing contract):

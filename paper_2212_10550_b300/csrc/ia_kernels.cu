@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS)
           const int c = cells ? cells[base + i] : base + i;
           sigma[c] = o.start >= 0 ? o.sigma : 0.f;
         },
-        st, a.prop, false);  // occupancy cells take the plain search (the host never sets a.search here)
+        st, a.prop, a.search != 0);
   }
   if (stats) {
     flush_stats(stats, ST_STARTS, st.starts);
@@ -270,87 +270,129 @@ cudaError_t launch_occ_density(const PosedArgs& a, const BoxDev& box, const floa
 // samples test.
 // ---------------------------------------------------------------------------
 
-// One lane per skinning-grid cell, a warp per 4 x 4 x 2 block of cells: marks
-// the occupancy sub-cells meeting the cell's image box (sub_marked's index of a
+// One thread per skinning-grid cell, a block per 8 x 8 x 4 of them: marks the
+// occupancy sub-cells meeting the cell's image box (sub_marked's index of a
 // point is monotone in x, so the range of the box's two corners holds the index
-// of every point inside), one 64-bit OR per occupancy cell the box meets.
+// of every point inside).  The block first ORs its masks into a shared window
+// over the occupancy cells its boxes meet and then adds each touched word to
+// the grid with one global OR; a block whose window would not fit writes
+// straight to the grid.
+constexpr int kCoverWin = 4096;  // 64-bit words of the shared window (32 KB)
+
 // blockIdx.y: the pose (blended grid S.M + pose * V * 3, masks sub + pose * R^3).
-__global__ void occ_cover_kernel(SkinDev S, int V, const BoxDev box, float slack,
-                                 unsigned long long* __restrict__ sub) {
+__global__ void __launch_bounds__(256) occ_cover_kernel(SkinDev S, int V, const BoxDev box, float slack,
+                                                        unsigned long long* __restrict__ sub) {
   static_assert(kSub * kSub * kSub == 64, "one 64-bit word per occupancy cell");
+  __shared__ unsigned long long win[kCoverWin];
+  __shared__ int wlo[3], whi[3];
   S.M += (size_t)blockIdx.y * V * 3;
   sub += (size_t)blockIdx.y * box.R * box.R * box.R;
   const int nc = S.Rw - 1;  // cells per axis
-  const int tx = (nc + 3) / 4, ty = (nc + 3) / 4, tz = (nc + 1) / 2;
-  const int tile = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-  if (tile >= tx * ty * tz) return;
-  const int cx = (tile % tx) * 4 + (lane & 3), cy = ((tile / tx) % ty) * 4 + ((lane >> 2) & 3),
-            cz = (tile / (tx * ty)) * 2 + (lane >> 4);
-  if (cx >= nc || cy >= nc || cz >= nc) return;
-  float h[3], v0[3];
-  const int ci[3] = {cx, cy, cz};
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    h[a] = (S.cmax[a] - S.cmin[a]) / (float)nc;
-    v0[a] = S.cmin[a] + (float)ci[a] * h[a];
+  const int bx = (nc + 7) / 8, by = (nc + 7) / 8;
+  const int tid = threadIdx.x;
+  const int cx = (blockIdx.x % bx) * 8 + (tid & 7), cy = ((blockIdx.x / bx) % by) * 8 + ((tid >> 3) & 7),
+            cz = (blockIdx.x / (bx * by)) * 4 + (tid >> 6);
+  if (tid < 3) {
+    wlo[tid] = 0x7fffffff;
+    whi[tid] = -1;
   }
-  float A[8][9];
-  float lo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, hi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
-  float mean[9];
-#pragma unroll
-  for (int q = 0; q < 9; ++q) mean[q] = 0.f;
-#pragma unroll
-  for (int corner = 0; corner < 8; ++corner) {
-    const int ox = corner & 1, oy = (corner >> 1) & 1, oz = (corner >> 2) & 1;
-    const int v = (cz + oz) * S.Rw * S.Rw + (cy + oy) * S.Rw + (cx + ox);
-    const float4* p = S.M + 3 * (size_t)v;
-    const float4 r[3] = {__ldg(p), __ldg(p + 1), __ldg(p + 2)};
-    const float x = ox ? v0[0] + h[0] : v0[0], y = oy ? v0[1] + h[1] : v0[1], z = oz ? v0[2] + h[2] : v0[2];
-    const float img[3] = {fmaf(r[0].x, x, fmaf(r[0].y, y, fmaf(r[0].z, z, r[0].w))),
-                          fmaf(r[1].x, x, fmaf(r[1].y, y, fmaf(r[1].z, z, r[1].w))),
-                          fmaf(r[2].x, x, fmaf(r[2].y, y, fmaf(r[2].z, z, r[2].w)))};
+  __syncthreads();
+  const int ns = kSub * box.R;  // sub-cells per axis
+  int s0[3] = {0, 0, 0}, s1[3] = {-1, -1, -1};
+  bool live = cx < nc && cy < nc && cz < nc;
+  if (live) {
+    float h[3], v0[3];
+    const int ci[3] = {cx, cy, cz};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      lo[a] = fminf(lo[a], img[a]);
-      hi[a] = fmaxf(hi[a], img[a]);
-      A[corner][3 * a + 0] = a == 0 ? r[0].x : a == 1 ? r[1].x : r[2].x;
-      A[corner][3 * a + 1] = a == 0 ? r[0].y : a == 1 ? r[1].y : r[2].y;
-      A[corner][3 * a + 2] = a == 0 ? r[0].z : a == 1 ? r[1].z : r[2].z;
+      h[a] = (S.cmax[a] - S.cmin[a]) / (float)nc;
+      v0[a] = S.cmin[a] + (float)ci[a] * h[a];
+    }
+    float A[8][9];
+    float lo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, hi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
+    float mean[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) mean[q] = 0.f;
+#pragma unroll
+    for (int corner = 0; corner < 8; ++corner) {
+      const int ox = corner & 1, oy = (corner >> 1) & 1, oz = (corner >> 2) & 1;
+      const int v = (cz + oz) * S.Rw * S.Rw + (cy + oy) * S.Rw + (cx + ox);
+      const float4* p = S.M + 3 * (size_t)v;
+      const float4 r[3] = {__ldg(p), __ldg(p + 1), __ldg(p + 2)};
+      const float x = ox ? v0[0] + h[0] : v0[0], y = oy ? v0[1] + h[1] : v0[1], z = oz ? v0[2] + h[2] : v0[2];
+      const float img[3] = {fmaf(r[0].x, x, fmaf(r[0].y, y, fmaf(r[0].z, z, r[0].w))),
+                            fmaf(r[1].x, x, fmaf(r[1].y, y, fmaf(r[1].z, z, r[1].w))),
+                            fmaf(r[2].x, x, fmaf(r[2].y, y, fmaf(r[2].z, z, r[2].w)))};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = fminf(lo[a], img[a]);
+        hi[a] = fmaxf(hi[a], img[a]);
+        A[corner][3 * a + 0] = a == 0 ? r[0].x : a == 1 ? r[1].x : r[2].x;
+        A[corner][3 * a + 1] = a == 0 ? r[0].y : a == 1 ? r[1].y : r[2].y;
+        A[corner][3 * a + 2] = a == 0 ? r[0].z : a == 1 ? r[1].z : r[2].z;
+      }
+#pragma unroll
+      for (int q = 0; q < 9; ++q) mean[q] += 0.125f * A[corner][q];
     }
 #pragma unroll
-    for (int q = 0; q < 9; ++q) mean[q] += 0.125f * A[corner][q];
-  }
-  const int ns = kSub * box.R;  // sub-cells per axis
-  int s0[3], s1[3];
+    for (int a = 0; a < 3; ++a) {
+      float m = 0.f;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    float m = 0.f;
-#pragma unroll
-    for (int corner = 0; corner < 8; ++corner)
-      m = fmaxf(m, fabsf(A[corner][3 * a] - mean[3 * a]) * h[0] + fabsf(A[corner][3 * a + 1] - mean[3 * a + 1]) * h[1] +
-                       fabsf(A[corner][3 * a + 2] - mean[3 * a + 2]) * h[2]);
-    // sub_marked's index arithmetic (fp32), clamped before the conversion
-    const float g = m + slack;
-    const float f0 = floorf(__fmul_rn(__fsub_rn(lo[a] - g, box.nmin[a]), box.sub_scale[a]));
-    const float f1 = floorf(__fmul_rn(__fsub_rn(hi[a] + g, box.nmin[a]), box.sub_scale[a]));
-    if (!(f1 >= 0.f) || !(f0 <= (float)(ns - 1))) return;  // the box misses the grid
-    s0[a] = (int)fmaxf(f0, 0.f);
-    s1[a] = (int)fminf(f1, (float)(ns - 1));
+      for (int corner = 0; corner < 8; ++corner)
+        m = fmaxf(m, fabsf(A[corner][3 * a] - mean[3 * a]) * h[0] +
+                         fabsf(A[corner][3 * a + 1] - mean[3 * a + 1]) * h[1] +
+                         fabsf(A[corner][3 * a + 2] - mean[3 * a + 2]) * h[2]);
+      // sub_marked's index arithmetic (fp32), clamped before the conversion
+      const float g = m + slack;
+      const float f0 = floorf(__fmul_rn(__fsub_rn(lo[a] - g, box.nmin[a]), box.sub_scale[a]));
+      const float f1 = floorf(__fmul_rn(__fsub_rn(hi[a] + g, box.nmin[a]), box.sub_scale[a]));
+      if (!(f1 >= 0.f) || !(f0 <= (float)(ns - 1))) live = false;  // the box misses the grid
+      s0[a] = (int)fminf(fmaxf(f0, 0.f), (float)(ns - 1));
+      s1[a] = (int)fmaxf(fminf(f1, (float)(ns - 1)), 0.f);
+    }
   }
-  for (int z = s0[2] / kSub; z <= s1[2] / kSub; ++z) {
-    const int z0 = max(s0[2] - kSub * z, 0), z1 = min(s1[2] - kSub * z, kSub - 1);
-    for (int y = s0[1] / kSub; y <= s1[1] / kSub; ++y) {
-      const int y0 = max(s0[1] - kSub * y, 0), y1 = min(s1[1] - kSub * y, kSub - 1);
-      for (int x = s0[0] / kSub; x <= s1[0] / kSub; ++x) {
-        const int x0 = max(s0[0] - kSub * x, 0), x1 = min(s1[0] - kSub * x, kSub - 1);
-        const unsigned long long row = ((1ull << (x1 + 1)) - 1ull) & ~((1ull << x0) - 1ull);
-        unsigned long long m = 0ull;
-        for (int sz = z0; sz <= z1; ++sz)
-          for (int sy = y0; sy <= y1; ++sy) m |= row << (kSub * (sy + kSub * sz));
-        atomicOr(sub + (x + box.R * (y + box.R * z)), m);
+  if (live) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      atomicMin(&wlo[a], s0[a] / kSub);
+      atomicMax(&whi[a], s1[a] / kSub);
+    }
+  }
+  __syncthreads();
+  const int ex = whi[0] - wlo[0] + 1, ey = whi[1] - wlo[1] + 1, ez = whi[2] - wlo[2] + 1;
+  const bool any = whi[0] >= 0;
+  const bool shared = any && ex * ey * ez <= kCoverWin;
+  if (shared)
+    for (int t = tid; t < ex * ey * ez; t += blockDim.x) win[t] = 0ull;
+  __syncthreads();
+  if (live) {
+    for (int z = s0[2] / kSub; z <= s1[2] / kSub; ++z) {
+      const int z0 = max(s0[2] - kSub * z, 0), z1 = min(s1[2] - kSub * z, kSub - 1);
+      for (int y = s0[1] / kSub; y <= s1[1] / kSub; ++y) {
+        const int y0 = max(s0[1] - kSub * y, 0), y1 = min(s1[1] - kSub * y, kSub - 1);
+        for (int x = s0[0] / kSub; x <= s1[0] / kSub; ++x) {
+          const int x0 = max(s0[0] - kSub * x, 0), x1 = min(s1[0] - kSub * x, kSub - 1);
+          const unsigned long long row = ((1ull << (x1 + 1)) - 1ull) & ~((1ull << x0) - 1ull);
+          unsigned long long m = 0ull;
+          for (int sz = z0; sz <= z1; ++sz)
+            for (int sy = y0; sy <= y1; ++sy) m |= row << (kSub * (sy + kSub * sz));
+          if (shared)
+            atomicOr(win + ((x - wlo[0]) + ex * ((y - wlo[1]) + ey * (z - wlo[2]))), m);
+          else
+            atomicOr(sub + (x + box.R * (y + box.R * z)), m);
+        }
       }
     }
   }
+  __syncthreads();
+  if (shared)
+    for (int t = tid; t < ex * ey * ez; t += blockDim.x) {
+      const unsigned long long m = win[t];
+      if (m) {
+        const int x = wlo[0] + t % ex, y = wlo[1] + (t / ex) % ey, z = wlo[2] + t / (ex * ey);
+        atomicOr(sub + (x + box.R * (y + box.R * z)), m);
+      }
+    }
 }
 
 // One thread per occupancy cell: its query point (the density kernel's) and
@@ -393,8 +435,8 @@ cudaError_t launch_occ_cover(const SkinDev& S, int V, int n_poses, const SolveCf
     L = std::max({L, std::fabs(S.cmin[k]), std::fabs(S.cmax[k]), std::fabs(box.nmin[k]), std::fabs(box.nmax[k])});
   const float slack = std::sqrt(cfg.tol2) + 1e-4f * L;
   const int nc = S.Rw - 1;
-  const int tiles = ((nc + 3) / 4) * ((nc + 3) / 4) * ((nc + 1) / 2);
-  occ_cover_kernel<<<dim3((tiles + 7) / 8, n_poses), 256, 0, s>>>(S, V, box, slack, sub);
+  const int blocks = ((nc + 7) / 8) * ((nc + 7) / 8) * ((nc + 3) / 4);
+  occ_cover_kernel<<<dim3(blocks, n_poses), 256, 0, s>>>(S, V, box, slack, sub);
   return cudaGetLastError();
 }
 
@@ -422,42 +464,40 @@ cudaError_t launch_occ_ema(const float* sigma, float* d, int n, float decay, cud
 }
 
 // occupied = sigma > tau, dilated by a (2 dilate + 1)^3 cube clipped to the grid;
-// cell b = x + R (y + R z) is bit b % 32 of word b / 32
+// cell b = x + R (y + R z) is bit b % 32 of word b / 32.  One thread per cell, a
+// warp per word (blocks of whole warps, so warp w holds cells 32 w .. 32 w + 31).
 __global__ void occ_bits_kernel(const float* __restrict__ sigma, int R, int dilate, float tau,
                                 uint32_t* __restrict__ bits, uint32_t* __restrict__ union_bits) {
   const int n = R * R * R;
-  const int words = (n + 31) / 32;
-  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < words; w += gridDim.x * blockDim.x) {
-    uint32_t word = 0;
-    for (int b = 0; b < 32; ++b) {
-      const int cell = w * 32 + b;
-      if (cell >= n) break;
-      const int x = cell % R, y = (cell / R) % R, z = cell / (R * R);
-      bool on = false;
-      for (int dz = -dilate; dz <= dilate && !on; ++dz) {
-        const int zz = z + dz;
-        if (zz < 0 || zz >= R) continue;
-        for (int dy = -dilate; dy <= dilate && !on; ++dy) {
-          const int yy = y + dy;
-          if (yy < 0 || yy >= R) continue;
-          for (int dx = -dilate; dx <= dilate && !on; ++dx) {
-            const int xx = x + dx;
-            if (xx < 0 || xx >= R) continue;
-            if (sigma[xx + R * (yy + R * zz)] > tau) on = true;
-          }
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  bool on = false;
+  if (cell < n) {
+    const int x = cell % R, y = (cell / R) % R, z = cell / (R * R);
+    for (int dz = -dilate; dz <= dilate && !on; ++dz) {
+      const int zz = z + dz;
+      if (zz < 0 || zz >= R) continue;
+      for (int dy = -dilate; dy <= dilate && !on; ++dy) {
+        const int yy = y + dy;
+        if (yy < 0 || yy >= R) continue;
+        for (int dx = -dilate; dx <= dilate && !on; ++dx) {
+          const int xx = x + dx;
+          if (xx < 0 || xx >= R) continue;
+          if (__ldg(sigma + xx + R * (yy + R * zz)) > tau) on = true;
         }
       }
-      if (on) word |= 1u << b;
     }
-    if (bits) bits[w] = word;
-    if (union_bits) union_bits[w] |= word;
+  }
+  const unsigned word = __ballot_sync(kFull, on);
+  if ((threadIdx.x & 31) == 0 && cell < n) {
+    if (bits) bits[cell >> 5] = word;
+    if (union_bits) union_bits[cell >> 5] |= word;
   }
 }
 
 cudaError_t launch_occ_bits(const float* sigma, int R, int dilate, float tau, uint32_t* bits, uint32_t* union_bits,
                             cudaStream_t s) {
-  const int words = (R * R * R + 31) / 32;
-  occ_bits_kernel<<<(words + 127) / 128, 128, 0, s>>>(sigma, R, dilate, tau, bits, union_bits);
+  const int n = R * R * R;
+  occ_bits_kernel<<<(n + 255) / 256, 256, 0, s>>>(sigma, R, dilate, tau, bits, union_bits);
   return cudaGetLastError();
 }
 

@@ -49,9 +49,9 @@ GATHER_HASH = 16 * 8 * 8  # bytes of the fp32 hash table one field evaluation re
 # DRAM bytes (read + write) of one render_kernel<2, fp32> launch on this workload,
 # from the ncu capture summarised in profiles/render_kernel_540x540_fp32.md; the
 # ncu-measured busiest unit of that launch is reported beside the roofline
-RENDER_DRAM_BYTES = 51.88e6 + 2.28e6
-RENDER_LIMITER = {"unit": "L1 (blended-grid gathers)", "l1tex_throughput_pct": 62.8, "issue_active_pct": 30.5,
-                  "fma_pipe_pct": 17.4, "l1_hit_pct": 91.0, "l2_hit_pct": 97.6, "simt_lanes_per_inst": 20.1,
+RENDER_DRAM_BYTES = 52.256e6 + 2.020e6
+RENDER_LIMITER = {"unit": "L1 (blended-grid gathers)", "l1tex_throughput_pct": 62.7, "issue_active_pct": 30.1,
+                  "fma_pipe_pct": 17.2, "l1_hit_pct": 90.9, "l2_hit_pct": 97.3, "simt_lanes_per_inst": 20.65,
                   "source": "profiles/render_kernel_540x540_fp32.md"}
 
 

@@ -395,9 +395,10 @@ def train_quality(torch, ia, sc, table, mlp, prop=None, iters=2000, batch=8192, 
 
 def skip_ablation(torch, ia, sc, table, mlp, icam, rgb, alpha, stream, poses, frames=2):
     """Empty-space skipping on and off (the Table 3 analogue): plain fp32 render
-    of a frame with the pose's occupancy grid against an all-occupied grid, and a
-    fp32 training step (8192 rays, 16 poses) on the union grid against an
-    all-occupied grid."""
+    of a frame with the pose's occupancy grid (and root culling) against an
+    all-occupied grid with root culling off, and a fp32 training step (8192 rays,
+    16 poses) on the union grid (and root culling) against an all-occupied grid
+    with root culling off: 'off' searches every sample."""
     ctx = make_ctx(torch, ia, sc, table, mlp, 0, EARLY_T)
     R = sc.occ_res
     full = np.full((R ** 3 + 31) // 32, 0xFFFFFFFF, dtype=np.uint32)
@@ -405,6 +406,7 @@ def skip_ablation(torch, ia, sc, table, mlp, icam, rgb, alpha, stream, poses, fr
         full[-1] = (1 << (R ** 3 % 32)) - 1
     out = {}
     for name, skip in (("skip", True), ("no_skip", False)):
+        ia.ia_set_occupancy_culling(ctx, skip)
         ms = []
         for th, tr in poses[:frames]:
             ia.ia_set_pose(ctx, th[None], tr[None])
@@ -435,6 +437,7 @@ def skip_ablation(torch, ia, sc, table, mlp, icam, rgb, alpha, stream, poses, fr
              skin=torch.zeros(ns, device="cuda"), bones=torch.zeros(nbn, device="cuda"))
     loss = torch.zeros(1, device="cuda")
     for name, grid in (("skip", ia.IA_OCC_UNION), ("no_skip", ia.IA_OCC_POSE)):
+        ia.ia_set_occupancy_culling(ctx, grid == ia.IA_OCC_UNION)
         ms = []
         for it in range(4):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -697,7 +700,8 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": round(1.0 / statistics.mean(e2e_s), 3), "unit": "frames/s",
                 "h2d_bytes_per_step": int(sc.n_bones * 3 * 8 + 3 * 8),
                 "d2h_bytes_per_step": int(W * H * 4 * 4)},
-        "gpu_launches": 5 * args.steps,
+        # per step: pose chain, blend, culling masks, candidates, density, bits, render
+        "gpu_launches": 7 * args.steps,
         "clocks": clk,
     }
     if not args.no_cpu_baseline and world == 1:

@@ -261,7 +261,9 @@ ia_status ia_set_loss(ia_ctx *ctx, const ia_loss *loss);
  * n_poses * n_bones * 12 (either pointer may be NULL). */
 ia_status ia_grad_sizes(const ia_ctx *ctx, int64_t *skin_floats, int64_t *bone_floats);
 
-/* Gradient buffers (device, caller-owned, overwritten by each step). */
+/* Gradient buffers (device, caller-owned, overwritten by each step).  table must
+ * be 8-byte aligned (IA_ERR_ARG otherwise); a 16-byte aligned skin with n_bones
+ * a multiple of 4 takes the skinning-grid gradient four bones per atomic. */
 typedef struct ia_grads {
   float *table;   /* [entries][F], same layout as the hash table */
   float *mlp;     /* packed like the MLP of ia_set_params */

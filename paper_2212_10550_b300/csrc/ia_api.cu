@@ -767,6 +767,8 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
   if (b->n_reg > 0 && !(std::isfinite(b->reg_weight))) return fail(c, IA_ERR_ARG, "reg_weight must be finite");
   if (c->loss.w_alpha != 0.f && !b->alpha_target)
     return fail(c, IA_ERR_ARG, "the loss has an alpha term: batch->alpha_target is needed");
+  if ((reinterpret_cast<uintptr_t>(g->table) & 7) != 0)
+    return fail(c, IA_ERR_ARG, "grads->table must be 8-byte aligned (one float pair per entry)");
   cudaStream_t s = (cudaStream_t)stream;
   const int n = b->n_rays, N = c->cfg.max_samples;
   const size_t cap = (size_t)n * N + (size_t)b->n_reg;
@@ -887,6 +889,8 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
   a.w_alpha = c->loss.w_alpha;
   a.w_hard = c->loss.w_hard;
   a.alpha_target = b->alpha_target;
+  a.skin_vec = (c->nb % 4 == 0 && (reinterpret_cast<uintptr_t>(g->skin) & 15) == 0 &&
+                (reinterpret_cast<uintptr_t>(c->d_skin) & 15) == 0) ? 1 : 0;
   a.act = c->d_act;
   a.loss = loss;
   a.rgb_out = rgb_out;

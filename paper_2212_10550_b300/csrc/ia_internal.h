@@ -143,6 +143,7 @@ struct TrainArgs {
   int huber;
   float huber_delta, w_rgb, w_alpha, w_hard;
   const float* alpha_target;  // [n_rays] (w_alpha != 0)
+  int skin_vec;          // skin / g_skin as float4 groups of bones (nb % 4 == 0, 16-byte aligned)
 };
 
 // b1p[pose][j] = b1[j] + W1[j, pose columns] . theta_pose for every pose

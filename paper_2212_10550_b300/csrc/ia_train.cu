@@ -351,51 +351,82 @@ __device__ __forceinline__ void ift_scatter_warp(const TrainArgs& a, bool has, i
   // trilinear coefficients of x* in the skinning grid (as the forward blends them)
   CellCoord cc = skin_cell(a.P.S, ok ? xs : make_float3(a.P.S.cmin[0], a.P.S.cmin[1], a.P.S.cmin[2]));
   const float* Np = a.N + (size_t)(ok ? pose : p0) * nb * 12;
-  for (int k = 0; k < nb; ++k) {
-    float wk = 0.f;
+  float cwc[8];
+  int vc[8];
+#pragma unroll
+  for (int corner = 0; corner < 8; ++corner) {
+    vc[corner] = corner_index(a.P.S, cc.base, corner);
+    cwc[corner] = ((corner & 1) ? cc.f[0] : 1.f - cc.f[0]) * (((corner >> 1) & 1) ? cc.f[1] : 1.f - cc.f[1]) *
+                  (((corner >> 2) & 1) ? cc.f[2] : 1.f - cc.f[2]);
+  }
+  // bones in groups of four: with a.skin_vec (nb % 4 == 0 and 16-byte aligned
+  // grids, checked by the host) one float4 load and one float4 atomic per corner
+  // serve four bones of the [v][nb] layout; otherwise one bone at a time
+  for (int k0 = 0; k0 < nb; k0 += 4) {
+    float wk4[4] = {0.f, 0.f, 0.f, 0.f};
     if (ok) {
 #pragma unroll
       for (int corner = 0; corner < 8; ++corner) {
-        const int v = corner_index(a.P.S, cc.base, corner);
-        const float cw = ((corner & 1) ? cc.f[0] : 1.f - cc.f[0]) * (((corner >> 1) & 1) ? cc.f[1] : 1.f - cc.f[1]) *
-                         (((corner >> 2) & 1) ? cc.f[2] : 1.f - cc.f[2]);
-        wk = fmaf(cw, __ldg(a.skin + (size_t)v * nb + k), wk);
+        const float* src = a.skin + (size_t)vc[corner] * nb + k0;
+        float4 w4;
+        if (a.skin_vec) {
+          w4 = __ldg(reinterpret_cast<const float4*>(src));
+        } else {
+          w4.x = __ldg(src);
+          w4.y = k0 + 1 < nb ? __ldg(src + 1) : 0.f;
+          w4.z = k0 + 2 < nb ? __ldg(src + 2) : 0.f;
+          w4.w = k0 + 3 < nb ? __ldg(src + 3) : 0.f;
+        }
+        wk4[0] = fmaf(cwc[corner], w4.x, wk4[0]);
+        wk4[1] = fmaf(cwc[corner], w4.y, wk4[1]);
+        wk4[2] = fmaf(cwc[corner], w4.z, wk4[2]);
+        wk4[3] = fmaf(cwc[corner], w4.w, wk4[3]);
       }
     }
-    // dL/dN_k[a][b] = -lambda_a w_k [x*;1]_b
-    if (uniform) {
-      float v[16];
+    float ln4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        v[b] = -l0 * wk * xb[b];
-        v[4 + b] = -l1 * wk * xb[b];
-        v[8 + b] = -l2 * wk * xb[b];
-        v[12 + b] = 0.f;
-      }
-      const float sum = warp_reduce_scatter16(v, lane);
-      const int idx = (lane >> 1) & 15;
-      if ((lane & 1) == 0 && idx < 12) atomicAdd(a.g_bones + ((size_t)p0 * nb + k) * 12 + idx, sum);
-    } else if (ok) {
-      float* gB = a.g_bones + ((size_t)pose * nb + k) * 12;
+    for (int kk = 0; kk < 4; ++kk) {
+      const int k = k0 + kk;
+      if (k >= nb) break;  // uniform across the warp
+      const float wk = wk4[kk];
+      // dL/dN_k[a][b] = -lambda_a w_k [x*;1]_b
+      if (uniform) {
+        float v[16];
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        atomicAdd(gB + b, -l0 * wk * xb[b]);
-        atomicAdd(gB + 4 + b, -l1 * wk * xb[b]);
-        atomicAdd(gB + 8 + b, -l2 * wk * xb[b]);
+        for (int b = 0; b < 4; ++b) {
+          v[b] = -l0 * wk * xb[b];
+          v[4 + b] = -l1 * wk * xb[b];
+          v[8 + b] = -l2 * wk * xb[b];
+          v[12 + b] = 0.f;
+        }
+        const float sum = warp_reduce_scatter16(v, lane);
+        const int idx = (lane >> 1) & 15;
+        if ((lane & 1) == 0 && idx < 12) atomicAdd(a.g_bones + ((size_t)p0 * nb + k) * 12 + idx, sum);
+      } else if (ok) {
+        float* gB = a.g_bones + ((size_t)pose * nb + k) * 12;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          atomicAdd(gB + b, -l0 * wk * xb[b]);
+          atomicAdd(gB + 4 + b, -l1 * wk * xb[b]);
+          atomicAdd(gB + 8 + b, -l2 * wk * xb[b]);
+        }
       }
-    }
-    // dL/dW(v, k) = -c_v lambda . (N_k [x*;1])
-    if (ok) {
+      // dL/dW(v, k) = -c_v lambda . (N_k [x*;1])
       const float* Nk = Np + 12 * k;
-      const float ln = l0 * (Nk[0] * xb[0] + Nk[1] * xb[1] + Nk[2] * xb[2] + Nk[3]) +
-                       l1 * (Nk[4] * xb[0] + Nk[5] * xb[1] + Nk[6] * xb[2] + Nk[7]) +
-                       l2 * (Nk[8] * xb[0] + Nk[9] * xb[1] + Nk[10] * xb[2] + Nk[11]);
+      ln4[kk] = l0 * (Nk[0] * xb[0] + Nk[1] * xb[1] + Nk[2] * xb[2] + Nk[3]) +
+                l1 * (Nk[4] * xb[0] + Nk[5] * xb[1] + Nk[6] * xb[2] + Nk[7]) +
+                l2 * (Nk[8] * xb[0] + Nk[9] * xb[1] + Nk[10] * xb[2] + Nk[11]);
+    }
+    if (ok) {
 #pragma unroll
       for (int corner = 0; corner < 8; ++corner) {
-        const int v = corner_index(a.P.S, cc.base, corner);
-        const float cw = ((corner & 1) ? cc.f[0] : 1.f - cc.f[0]) * (((corner >> 1) & 1) ? cc.f[1] : 1.f - cc.f[1]) *
-                         (((corner >> 2) & 1) ? cc.f[2] : 1.f - cc.f[2]);
-        atomicAdd(a.g_skin + (size_t)v * nb + k, -cw * ln);
+        const float c = -cwc[corner];
+        float* dst = a.g_skin + (size_t)vc[corner] * nb + k0;
+        if (a.skin_vec) {
+          atomicAdd(reinterpret_cast<float4*>(dst), make_float4(c * ln4[0], c * ln4[1], c * ln4[2], c * ln4[3]));
+        } else {
+          for (int kk = 0; kk < 4 && k0 + kk < nb; ++kk) atomicAdd(dst + kk, c * ln4[kk]);
+        }
       }
     }
   }
@@ -432,8 +463,8 @@ __device__ __forceinline__ void hash_backward(const TrainArgs& a, float3 xs, con
         const float wx = cx ? f[0] : 1.f - f[0], wy = cy ? f[1] : 1.f - f[1], wz = cz ? f[2] : 1.f - f[2];
         const uint32_t e = lv.offset + vertex_index(lv, p0[0] + cx, p0[1] + cy, p0[2] + cz);
         const float w = wx * wy * wz;
-        atomicAdd(a.g_table + 2 * (size_t)e, w * d0);
-        atomicAdd(a.g_table + 2 * (size_t)e + 1, w * d1);
+        // one 8-byte vector atomic per entry (the host checks the alignment)
+        atomicAdd(reinterpret_cast<float2*>(a.g_table) + e, make_float2(w * d0, w * d1));
         float2 t;
         if constexpr (kHalfTable) t = __half22float2(a.P.table_h[e]);
         else t = __ldg(F.table + e);

@@ -249,3 +249,40 @@ def test_learnable_skinning_grid(ia):
         n_ok += 1
     print(f"{n_ok} posed queries on the updated skinning grid match the oracle")
     assert n_ok > 100
+
+
+def test_gradient_buffer_alignment(ia):
+    """A skinning-grid gradient buffer 4 bytes off a 16-byte boundary takes the
+    one-bone-at-a-time scatter: same gradients as the four-bone vector atomics
+    up to summation order.  A hash-table gradient buffer that is not 8-byte
+    aligned is refused before any launch."""
+    sc, table, mlp, om, poses, op, occ, rays, _ = _case("full", 2, 1024)
+    ctx = make_ctx(ia, torch, sc, table, mlp)
+    ia.ia_set_pose(ctx, np.stack([p[0] for p in poses]), np.stack([p[1] for p in poses]))
+    ia.ia_set_occupancy(ctx, occ)
+    nt, nm = ia.ia_param_sizes(ctx)
+    ns, nbn = ia.ia_grad_sizes(ctx)
+    dev = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in rays.items()}
+    out = []
+    for shift in (0, 1):
+        skin_buf = torch.zeros(ns + 4, device="cuda")
+        g = dict(table=torch.zeros(nt, device="cuda"), mlp=torch.zeros(nm, device="cuda"),
+                 skin=skin_buf[shift:shift + ns], bones=torch.zeros(nbn, device="cuda"))
+        loss = torch.zeros(1, device="cuda")
+        ia.ia_train_step(ctx, dev["origin"], dev["direction"], dev["pose"], dev["target"], loss, g,
+                         occ_grid=ia.IA_OCC_POSE)
+        torch.cuda.synchronize()
+        out.append({k: v.cpu().numpy().astype(np.float64) for k, v in g.items()})
+    for k in ("table", "mlp", "skin", "bones"):
+        a, b = out[1][k], out[0][k]
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        print(f"{k}: rel L2 {rel:.2e}")
+        assert np.count_nonzero(b) > 0 and rel <= 1e-5, k
+    bad = torch.zeros(nt + 1, device="cuda")
+    g = dict(table=bad[1:], mlp=torch.zeros(nm, device="cuda"), skin=torch.zeros(ns, device="cuda"),
+             bones=torch.zeros(nbn, device="cuda"))
+    with pytest.raises(ia.IAError) as e:
+        ia.ia_train_step(ctx, dev["origin"], dev["direction"], dev["pose"], dev["target"], torch.zeros(1, device="cuda"),
+                         g, occ_grid=ia.IA_OCC_POSE)
+    assert e.value.status == ia.IA_ERR_ARG
+    ia.ia_destroy(ctx)

@@ -892,6 +892,7 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
   a.skin_vec = (c->nb % 4 == 0 && (reinterpret_cast<uintptr_t>(g->skin) & 15) == 0 &&
                 (reinterpret_cast<uintptr_t>(c->d_skin) & 15) == 0) ? 1 : 0;
   a.act = c->d_act;
+  a.act_ld = (int64_t)c->s_cap;
   a.loss = loss;
   a.rgb_out = rgb_out;
   a.g_table = g->table;

@@ -81,7 +81,7 @@ struct RenderArgs {
   unsigned long long* stats;
 };
 
-// Training step (ia_train.cu).  Per-sample workspace: one row of kActStride
+// Training step (ia_train.cu).  Per-sample workspace: one column of kActStride
 // floats holds the recomputed features, hidden activations and their gradients
 // (F [32], H1 [64], H2 [64], dH1 [64], dH2 [64], dO [4]).
 constexpr int kActStride = kIn + 4 * kWidth + 4;
@@ -111,7 +111,8 @@ struct TrainArgs {
   float4* s_out;         // [cap] sigma (0 without a root), rgb
   float4* s_x;           // [cap] x*, has-root
   float4* s_grad;        // [cap] dL/dsigma, dL/dc
-  float* act;            // [cap][kActStride]
+  float* act;            // [kActStride][act_ld], channel-major (a warp's samples are contiguous)
+  int64_t act_ld;
   float* loss;           // device scalar (accumulated)
   float* rgb_out;        // [n][3] or null
   float* g_table;

@@ -516,17 +516,27 @@ __global__ void __launch_bounds__(256) train_scatter_kernel(const TrainArgs a) {
   }
 }
 
+// The 64-wide loops run rolled (a fully unrolled body does not fit the
+// instruction cache); a vector that a rolled loop indexes by its counter lives
+// in this thread's column of a shared array (vec[j * 128 + thread]: lanes hit
+// consecutive banks), which each thread reuses for h1, then dH2, then dH1.
+// Sums keep the order of the plain definition (inputs ascending).
 __global__ void __launch_bounds__(128) train_backward_kernel(const TrainArgs a) {
   __shared__ __align__(16) float sw[kMlpPadT];
+  extern __shared__ float vec[];  // [kWidth * 128], dynamic (static shared memory stops at 48 KB)
   stage_mlp(a.P.mlp, a.P.n_in, sw);
   __syncthreads();
   const int n = *a.count;
   const FieldDev& F = a.P.F;
+  float* my = vec + threadIdx.x;  // my[j * 128]: entry j of this thread's vector
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-    float* act = a.act + (size_t)s * kActStride;
+    // this sample's column of the channel-major activations: act[c * ld] is
+    // channel c (consecutive lanes write consecutive addresses)
+    float* act = a.act + s;
+    const int64_t ld = a.act_ld;
     const float4 xs4 = a.s_x[s];
-    if (!(xs4.w > 0.f)) {  // no root: no gradient; zero rows keep the reduction exact
-      for (int q = 0; q < kActStride; ++q) act[q] = 0.f;
+    if (!(xs4.w > 0.f)) {  // no root: no gradient; zero columns keep the reduction exact
+      for (int q = 0; q < kActStride; ++q) act[q * ld] = 0.f;
       continue;
     }
     const float3 xs = make_float3(xs4.x, xs4.y, xs4.z);
@@ -535,10 +545,9 @@ __global__ void __launch_bounds__(128) train_backward_kernel(const TrainArgs a) 
     float feat[kIn];
     encode(F, xs, feat);
 #pragma unroll
-    for (int i = 0; i < kIn; ++i) act[kActF + i] = feat[i];
-    float h1[kWidth];
+    for (int i = 0; i < kIn; ++i) act[(kActF + i) * ld] = feat[i];
     uint64_t m1 = 0;  // h1 > 0 mask
-#pragma unroll
+#pragma unroll 1
     for (int j = 0; j < kWidth; ++j) {
       float acc = sw[kOffB1 + j];
       const float4* row = reinterpret_cast<const float4*>(sw + kOffW1 + j * kIn);
@@ -547,12 +556,17 @@ __global__ void __launch_bounds__(128) train_backward_kernel(const TrainArgs a) 
         float4 w = row[i];
         acc = fmaf(w.x, feat[4 * i], fmaf(w.y, feat[4 * i + 1], fmaf(w.z, feat[4 * i + 2], fmaf(w.w, feat[4 * i + 3], acc))));
       }
-      h1[j] = fmaxf(acc, 0.f);
+      const float h = fmaxf(acc, 0.f);
       if (acc > 0.f) m1 |= 1ull << j;
-      act[kActH1 + j] = h1[j];
+      my[j * 128] = h;
+      act[(kActH1 + j) * ld] = h;
     }
+    float h1[kWidth];
+#pragma unroll
+    for (int i = 0; i < kWidth; ++i) h1[i] = my[i * 128];
     float o0 = sw[kOffB3], o1 = sw[kOffB3 + 1], o2 = sw[kOffB3 + 2], o3 = sw[kOffB3 + 3];
     uint64_t m2 = 0;  // h2 > 0 mask
+#pragma unroll 1
     for (int j = 0; j < kWidth; ++j) {
       float acc = sw[kOffB2 + j];
       const float4* row = reinterpret_cast<const float4*>(sw + kOffW2 + j * kWidth);
@@ -562,7 +576,7 @@ __global__ void __launch_bounds__(128) train_backward_kernel(const TrainArgs a) 
         acc = fmaf(w.x, h1[4 * i], fmaf(w.y, h1[4 * i + 1], fmaf(w.z, h1[4 * i + 2], fmaf(w.w, h1[4 * i + 3], acc))));
       }
       const float h = fmaxf(acc, 0.f);
-      act[kActH2 + j] = h;
+      act[(kActH2 + j) * ld] = h;
       if (acc > 0.f) m2 |= 1ull << j;
       const float4 w3 = reinterpret_cast<const float4*>(sw + kOffW3T)[j];
       o0 = fmaf(w3.x, h, o0);
@@ -583,23 +597,23 @@ __global__ void __launch_bounds__(128) train_backward_kernel(const TrainArgs a) 
       }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) act[kActDO + q] = dO[q];
+    for (int q = 0; q < 4; ++q) act[(kActDO + q) * ld] = dO[q];
     // ---- MLP backward to the features
-    float dh2[kWidth];
-#pragma unroll
+#pragma unroll 1
     for (int j = 0; j < kWidth; ++j) {
       const float4 w3 = reinterpret_cast<const float4*>(sw + kOffW3T)[j];
       const float v = w3.x * dO[0] + w3.y * dO[1] + w3.z * dO[2] + w3.w * dO[3];
-      dh2[j] = ((m2 >> j) & 1ull) ? v : 0.f;
-      act[kActD2 + j] = dh2[j];
+      const float d = ((m2 >> j) & 1ull) ? v : 0.f;
+      my[j * 128] = d;  // dH2 (h1 is in registers now)
+      act[(kActD2 + j) * ld] = d;
     }
     float dh1[kWidth];
 #pragma unroll
     for (int i = 0; i < kWidth; ++i) dh1[i] = 0.f;
-#pragma unroll
+#pragma unroll 1
     for (int j = 0; j < kWidth; ++j) {
       const float4* row = reinterpret_cast<const float4*>(sw + kOffW2 + j * kWidth);
-      const float d = dh2[j];
+      const float d = my[j * 128];
 #pragma unroll
       for (int i = 0; i < kWidth / 4; ++i) {
         float4 w = row[i];
@@ -609,13 +623,15 @@ __global__ void __launch_bounds__(128) train_backward_kernel(const TrainArgs a) 
         dh1[4 * i + 3] = fmaf(w.w, d, dh1[4 * i + 3]);
       }
     }
+#pragma unroll
+    for (int i = 0; i < kWidth; ++i) my[i * 128] = dh1[i];
     float dfeat[kIn];
 #pragma unroll
     for (int i = 0; i < kIn; ++i) dfeat[i] = 0.f;
-#pragma unroll
+#pragma unroll 1
     for (int j = 0; j < kWidth; ++j) {
-      const float d = ((m1 >> j) & 1ull) ? dh1[j] : 0.f;
-      act[kActD1 + j] = d;
+      const float d = ((m1 >> j) & 1ull) ? my[j * 128] : 0.f;
+      act[(kActD1 + j) * ld] = d;
       const float4* row = reinterpret_cast<const float4*>(sw + kOffW1 + j * kIn);
 #pragma unroll
       for (int i = 0; i < kIn / 4; ++i) {
@@ -661,9 +677,12 @@ __global__ void __launch_bounds__(256) mlp_grad_kernel(const TrainArgs a) {
   for (int base = s0; base < s1; base += kTileS) {
     const int m = min(kTileS, s1 - base);
     __syncthreads();
-    for (int q = t; q < m * kActStride; q += blockDim.x) {
-      const int r = q / kActStride, c = q % kActStride;
-      tile[r][c] = a.act[(size_t)(base + r) * kActStride + c];
+    // channel-major source: warp w stages channels w, w + 8, ...; lane r reads
+    // sample base + r (128-byte rows; the tile's odd row pitch spreads banks)
+    {
+      const int lane = t & 31;
+      for (int c = t >> 5; c < kActStride; c += blockDim.x >> 5)
+        if (lane < m) tile[lane][c] = __ldg(a.act + (size_t)c * a.act_ld + base + lane);
     }
     __syncthreads();
     for (int r = 0; r < m; ++r) {
@@ -1097,11 +1116,13 @@ cudaError_t launch_train(const TrainArgs& a, const CUtensorMap* map, int num_sms
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (P == Prec::F32) {
-    train_backward_kernel<<<num_sms * 4, 128, 0, s>>>(a);
+    const size_t vec_bytes = sizeof(float) * kWidth * 128;
+    if ((e = set_smem(train_backward_kernel, vec_bytes, 128)) != cudaSuccess) return e;
+    train_backward_kernel<<<num_sms * 4, 128, vec_bytes, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     train_scatter_kernel<false><<<num_sms * 8, 256, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    mlp_grad_kernel<<<num_sms * 2, 256, 0, s>>>(a);
+    mlp_grad_kernel<<<num_sms * 4, 256, 0, s>>>(a);
     return cudaGetLastError();
   }
   if (P == Prec::F16) {

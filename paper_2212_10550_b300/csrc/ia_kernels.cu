@@ -745,7 +745,7 @@ __global__ void __launch_bounds__(kRenderThreads, IA_RENDER_MIN_BLOCKS) render_k
     __syncwarp();
     // ---- 3. correspondence search and field at the round's samples (lists of kList)
     for (int base = 0; base < total; base += kList) {
-      posed_field_list<P, kProp ? ItemOrder::kStartMajor : ItemOrder::kPerLane>(
+      posed_field_list<P, kProp ? ItemOrder::kStartMajor : ItemOrder::kPerLane, kProp>(
           a.P.S, a.P.F, a.P.cfg, sm.fs, sm.list, min(kList, total - base),
           [&](int i, float3& xn, const float4*& M, const float*& Ni, int& pose) {
             const int sidx = base + i;

@@ -110,17 +110,30 @@ __device__ __forceinline__ void mma16816(float* d, const uint32_t* a, uint32_t b
 
 // The warp's 32 feature rows (one per lane) -> 32 output rows of 4, one per lane.
 // All 32 lanes must call; xs: this warp's staging area (kWarpXWords words).
+template <Prec P, bool kRolled = false>
+__device__ __forceinline__ void mlp_mma_warp_staged(const uint32_t* __restrict__ sw, uint32_t* xs, float out[4]);
+
 template <Prec P>
 __device__ __forceinline__ void mlp_mma_warp(const uint32_t* __restrict__ sw, uint32_t* xs, const float feat[kIn],
                                              float out[4]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int c = 0; c < kIn / 2; ++c) xs[lane * kXStride + c] = HalfOf<P>::pack(feat[2 * c], feat[2 * c + 1]);
+  mlp_mma_warp_staged<P>(sw, xs, out);
+}
+
+// The same chain with the feature rows already staged in xs (row = lane, word c
+// = the operand pair of inputs 2c, 2c + 1).  kRolled runs the two 16-row halves
+// rolled: the chain runs once per list, and in the proposal kernels, whose code
+// is largest, the search loop beside it must stay in the instruction cache.
+template <Prec P, bool kRolled>
+__device__ __forceinline__ void mlp_mma_warp_staged(const uint32_t* __restrict__ sw, uint32_t* xs, float out[4]) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   uint32_t* X = xs;
   float* O = reinterpret_cast<float*>(xs + 32 * kXStride);
-#pragma unroll
-  for (int c = 0; c < kIn / 2; ++c) X[lane * kXStride + c] = HalfOf<P>::pack(feat[2 * c], feat[2 * c + 1]);
   __syncwarp();
   const float* bias = reinterpret_cast<const float*>(sw + kOffHB);
-#pragma unroll
+#pragma unroll(kRolled ? 1 : 2)
   for (int mt = 0; mt < 2; ++mt) {
     const int r0 = 16 * mt + g, r1 = r0 + 8;
     // ---- layer 1: [16 x 32] x W1^T -> [16 x 64]
@@ -218,6 +231,45 @@ __device__ __forceinline__ void mlp_lane_h(const float* __restrict__ gm, int n_i
 }
 
 // fp16 hash features: the same encoding as encode(), reading the fp16 shadow table
+// Hash encoding from the fp16 shadow table, written as the MLP chain's operand
+// pairs straight into the staging row (word l = level l's two features), with
+// the level loop rolled (small code; encode_h keeps every level's gathers in
+// flight at once).  Same values as encode_h followed by the packing of
+// mlp_mma_warp.
+template <Prec P>
+__device__ __forceinline__ void encode_h_staged(const FieldDev& F, const __half2* __restrict__ th, float3 x,
+                                                uint32_t* row) {
+  const float u[3] = {(x.x - F.cmin[0]) * F.inv_ext[0], (x.y - F.cmin[1]) * F.inv_ext[1],
+                      (x.z - F.cmin[2]) * F.inv_ext[2]};
+#pragma unroll 1
+  for (int l = 0; l < kMaxLevels; ++l) {
+    float a0 = 0.f, a1 = 0.f;
+    if (l < F.L) {
+      const Level lv = F.lv[l];
+      int p0[3];
+      float f[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        float pos = u[a] * (float)lv.res;
+        int c = (int)floorf(pos);
+        c = min(max(c, 0), lv.res - 1);
+        p0[a] = c;
+        f[a] = pos - (float)c;
+      }
+#pragma unroll
+      for (int corner = 0; corner < 8; ++corner) {
+        const int cx = corner & 1, cy = (corner >> 1) & 1, cz = (corner >> 2) & 1;
+        const float w = (cx ? f[0] : 1.f - f[0]) * (cy ? f[1] : 1.f - f[1]) * (cz ? f[2] : 1.f - f[2]);
+        const uint32_t e = lv.offset + vertex_index(lv, p0[0] + cx, p0[1] + cy, p0[2] + cz);
+        const float2 t = __half22float2(th[e]);
+        a0 = fmaf(w, t.x, a0);
+        a1 = fmaf(w, t.y, a1);
+      }
+    }
+    row[l] = HalfOf<P>::pack(a0, a1);
+  }
+}
+
 __device__ __forceinline__ void encode_h(const FieldDev& F, const __half2* __restrict__ th, float3 x,
                                          float feat[kIn]) {
   const float u[3] = {(x.x - F.cmin[0]) * F.inv_ext[0], (x.y - F.cmin[1]) * F.inv_ext[1],

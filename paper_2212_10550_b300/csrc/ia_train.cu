@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(256) train_sample_kernel(const TrainArgs a) {
   // samples are grouped by pose) from a shared counter, searched with lane refill
   for (int list = next_list(a.work); list * kList < n; list = next_list(a.work)) {
     const int base = list * kList;
-    posed_field_list<P, ItemOrder::kSampleMajor>(
+    posed_field_list<P, ItemOrder::kSampleMajor, kProp>(
         a.P.S, a.P.F, a.P.cfg, sm.fs, sm.list, min(kList, n - base),
         [&](int i, float3& xn, const float4*& M, const float*& Ni, int& pose) {
           const float4 p = a.s_pos[base + i];

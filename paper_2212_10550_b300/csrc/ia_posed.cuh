@@ -171,9 +171,15 @@ __device__ __forceinline__ void posed_field_list(const SkinDev& S, const FieldDe
       const float* Ni;
       int pose = 0;
       if (act) src(lane, xn, Mi, Ni, pose);
-      float f16[16];
-      prop_encode(Q, xn, f16);
-      const float* O = prop_mma_warp<P>(fs.pw, fs.xstage, f16, Q.b1p, pose) + lane * (kPropMaxOut + 1);
+      const float* O;
+      if constexpr (kCompact) {
+        prop_encode_staged<P>(Q, xn, fs.xstage + lane * kPW1Stride);
+        O = prop_mma_warp<P, true>(fs.pw, fs.xstage, nullptr, Q.b1p, pose) + lane * (kPropMaxOut + 1);
+      } else {
+        float f16[16];
+        prop_encode(Q, xn, f16);
+        O = prop_mma_warp<P>(fs.pw, fs.xstage, f16, Q.b1p, pose) + lane * (kPropMaxOut + 1);
+      }
       if (act) {
         int b0 = 0, b1 = -1;
         float v0 = O[0], v1 = -3.0e38f;

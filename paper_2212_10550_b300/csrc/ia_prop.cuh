@@ -73,6 +73,41 @@ __device__ __forceinline__ void prop_encode(const PropDev& Q, float3 x, float fe
   }
 }
 
+// prop_encode written as the network's operand pairs straight into the staging
+// row (word l = level l's two features), with the level loop rolled.
+template <Prec P>
+__device__ __forceinline__ void prop_encode_staged(const PropDev& Q, float3 x, uint32_t* row) {
+  const float u[3] = {(x.x - Q.nmin[0]) * Q.inv_ext[0], (x.y - Q.nmin[1]) * Q.inv_ext[1],
+                      (x.z - Q.nmin[2]) * Q.inv_ext[2]};
+#pragma unroll 1
+  for (int l = 0; l < 8; ++l) {
+    float a0 = 0.f, a1 = 0.f;
+    if (l < Q.L) {
+      const Level lv = Q.lv[l];
+      int p0[3];
+      float f[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float pos = u[a] * (float)lv.res;
+        int c = (int)floorf(pos);
+        c = min(max(c, 0), lv.res - 1);
+        p0[a] = c;
+        f[a] = pos - (float)c;
+      }
+#pragma unroll
+      for (int corner = 0; corner < 8; ++corner) {
+        const int cx = corner & 1, cy = (corner >> 1) & 1, cz = (corner >> 2) & 1;
+        const float w = (cx ? f[0] : 1.f - f[0]) * (cy ? f[1] : 1.f - f[1]) * (cz ? f[2] : 1.f - f[2]);
+        const uint32_t e = lv.offset + vertex_index(lv, p0[0] + cx, p0[1] + cy, p0[2] + cz);
+        const float2 t = __ldg(Q.table + e);
+        a0 = fmaf(w, t.x, a0);
+        a1 = fmaf(w, t.y, a1);
+      }
+    }
+    row[l] = HalfOf<P>::pack(a0, a1);
+  }
+}
+
 // Stage the proposal weights (reduced precision) and the per-pose bias
 // b1' = b1 + W1[:, 2L:] theta into shared memory.  theta: [nb * 3] fp64.
 template <Prec P>
@@ -149,18 +184,23 @@ __device__ __forceinline__ void prop_hidden(const uint32_t* __restrict__ W, cons
 // The warp's 32 feature rows -> 32 output rows (logits, offset) in the staging
 // area O [32][kPropMaxOut + 1]; all 32 lanes call.  Returns O.  With b1p, each
 // row takes the layer-1 bias of its own lane's pose (b1p + 64 * pose).
-template <Prec P>
+// (kRolled: the feature rows are already staged in xs, row = lane, word c = the
+// operand pair of inputs 2c, 2c + 1, and the two 16-row halves run rolled, for
+// the kernels whose code overflows the instruction cache.)
+template <Prec P, bool kRolled = false>
 __device__ __forceinline__ const float* prop_mma_warp(const uint32_t* __restrict__ sw, uint32_t* xs,
                                                       const float feat[16], const float* __restrict__ b1p = nullptr,
                                                       int pose = 0) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   uint32_t* X = xs;
   float* O = reinterpret_cast<float*>(xs + 32 * kPW1Stride);
+  if constexpr (!kRolled) {
 #pragma unroll
-  for (int c = 0; c < 8; ++c) X[lane * kPW1Stride + c] = HalfOf<P>::pack(feat[2 * c], feat[2 * c + 1]);
+    for (int c = 0; c < 8; ++c) X[lane * kPW1Stride + c] = HalfOf<P>::pack(feat[2 * c], feat[2 * c + 1]);
+  }
   __syncwarp();
   const float* bias = reinterpret_cast<const float*>(sw + kPOffB);
-#pragma unroll
+#pragma unroll(kRolled ? 1 : 2)
   for (int mt = 0; mt < 2; ++mt) {
     const int r0 = 16 * mt + g, r1 = r0 + 8;
     uint32_t A1[4] = {X[r0 * kPW1Stride + t], X[r1 * kPW1Stride + t], X[r0 * kPW1Stride + 4 + t],

@@ -184,7 +184,7 @@ size_t posed_smem_bytes_p(int threads, bool prop) {
 // cells: the cells to search (occ_cand_kernel's list, *count of them), or null
 // for every cell of the grid.
 constexpr int kOccList = 16;
-template <Prec P>
+template <Prec P, bool kProp>
 __global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS)
     occ_density_kernel(const PosedArgs a, const BoxDev box, const float* __restrict__ jitter,
                        const int* __restrict__ cells, const unsigned* __restrict__ count,
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS)
   SampleStats st;
   for (int list = next_list(work); list * kOccList < n; list = next_list(work)) {
     const int base = list * kOccList;
-    posed_field_list<P, ItemOrder::kStartMajor>(
+    posed_field_list<P, ItemOrder::kStartMajor, kProp>(
         a.S, a.F, a.cfg, sm.fs, sm.list, min(kOccList, n - base),
         [&](int i, float3& xn, const float4*& M, const float*& Ni, int& pose) {
           const int c = cells ? cells[base + i] : base + i;
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS)
           const int c = cells ? cells[base + i] : base + i;
           sigma[c] = o.start >= 0 ? o.sigma : 0.f;
         },
-        st, a.prop, a.search != 0);
+        st, a.prop, kProp);  // the proposal code is compiled only into kProp variants
   }
   if (stats) {
     flush_stats(stats, ST_STARTS, st.starts);
@@ -221,23 +221,33 @@ __global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS)
   }
 }
 
-template <Prec P>
-static cudaError_t launch_occ_density_p(const PosedArgs& a, const BoxDev& box, const float* jitter, const int* cells,
+template <Prec P, bool kProp>
+static cudaError_t launch_occ_density_k(const PosedArgs& a, const BoxDev& box, const float* jitter, const int* cells,
                                         const unsigned* count, float* sigma, unsigned long long* stats,
                                         unsigned* work, int num_sms, cudaStream_t s) {
   const int n = box.R * box.R * box.R;
-  const size_t smem = posed_smem_bytes_p<P>(256, a.search != 0);
-  cudaError_t e = set_smem(occ_density_kernel<P>, smem, 256);
+  const size_t smem = posed_smem_bytes_p<P>(256, kProp);
+  cudaError_t e = set_smem(occ_density_kernel<P, kProp>, smem, 256);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, occ_density_kernel<P>, 256, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, occ_density_kernel<P, kProp>, 256, smem);
   if (e != cudaSuccess) return e;
   const int lists = (n + kOccList - 1) / kOccList;
   int blocks = num_sms * (per_sm < 1 ? 1 : per_sm);
   if (blocks > (lists + 7) / 8) blocks = (lists + 7) / 8;
   if ((e = cudaMemsetAsync(work, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
-  occ_density_kernel<P><<<blocks, 256, smem, s>>>(a, box, jitter, cells, count, sigma, stats, work);
+  occ_density_kernel<P, kProp><<<blocks, 256, smem, s>>>(a, box, jitter, cells, count, sigma, stats, work);
   return cudaGetLastError();
+}
+
+template <Prec P>
+static cudaError_t launch_occ_density_p(const PosedArgs& a, const BoxDev& box, const float* jitter, const int* cells,
+                                        const unsigned* count, float* sigma, unsigned long long* stats,
+                                        unsigned* work, int num_sms, cudaStream_t s) {
+  if constexpr (P != Prec::F32) {
+    if (a.search) return launch_occ_density_k<P, true>(a, box, jitter, cells, count, sigma, stats, work, num_sms, s);
+  }
+  return launch_occ_density_k<P, false>(a, box, jitter, cells, count, sigma, stats, work, num_sms, s);
 }
 
 cudaError_t launch_occ_density(const PosedArgs& a, const BoxDev& box, const float* jitter, const int* cells,

@@ -30,97 +30,127 @@ __device__ __forceinline__ double DM(double a, double b) { return __dmul_rn(a, b
 __device__ __forceinline__ double DA(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double DS(double a, double b) { return __dsub_rn(a, b); }
 
-__device__ void mat34_mul_d(const double* a, const double* b, double* c) {
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 4; ++j) {
-      double s = DA(DA(DM(a[i * 4 + 0], b[0 * 4 + j]), DM(a[i * 4 + 1], b[1 * 4 + j])), DM(a[i * 4 + 2], b[2 * 4 + j]));
-      if (j == 3) s = DA(s, a[i * 4 + 3]);
-      c[i * 4 + j] = s;
-    }
+// One block per pose, twelve threads per joint, thread (k, e) owning element e
+// of joint k's 3 x 4 matrices.  The chain is composed level by level down the
+// tree, G_k = G_p(k) L_k, which is the same left-to-right product
+// ((L_root L_a1) L_a2) ... L_k as composing parent-first; every element is
+// formed with the same rounded operations in the same order as a sequential
+// 3 x 4 product, so the fp64 results do not depend on the thread layout.
+// (fp64 runs at a small fraction of the fp32 rate here: spreading the products
+// over the elements shortens the chain of dependent fp64 instructions.)
+__device__ __forceinline__ double mat34_elem_d(const double* a, const double* b, int e) {
+  const int i = e >> 2, j = e & 3;
+  double s = DA(DA(DM(a[i * 4 + 0], b[0 * 4 + j]), DM(a[i * 4 + 1], b[1 * 4 + j])), DM(a[i * 4 + 2], b[2 * 4 + j]));
+  if (j == 3) s = DA(s, a[i * 4 + 3]);
+  return s;
 }
 
-__device__ void rigid_inv_d(const double* a, double* c) {
-  for (int i = 0; i < 3; ++i) {
-    for (int j = 0; j < 3; ++j) c[i * 4 + j] = a[j * 4 + i];
-    c[i * 4 + 3] = -DA(DA(DM(a[0 * 4 + i], a[3]), DM(a[1 * 4 + i], a[7])), DM(a[2 * 4 + i], a[11]));
-  }
+// element e of the inverse of the rigid transform a = [R | t]: [R^T | -R^T t]
+__device__ __forceinline__ double rigid_inv_elem_d(const double* a, int e) {
+  const int i = e >> 2, j = e & 3;
+  if (j < 3) return a[j * 4 + i];
+  return -DA(DA(DM(a[0 * 4 + i], a[3]), DM(a[1 * 4 + i], a[7])), DM(a[2 * 4 + i], a[11]));
 }
 
-// One block per pose, one thread per joint: every joint composes its ancestor
-// path from the root down, G_k = ((L_root L_a1) L_a2) ... L_k, the same
-// left-to-right product the sequential chain forms, so the fp64 results are
-// identical to composing parent-first.
 __global__ void pose_chain_kernel(int P, int nb, const int* __restrict__ parent, const double* __restrict__ rest,
                                   const double* __restrict__ theta, const double* __restrict__ trans,
                                   float* __restrict__ N, float* __restrict__ Ninv, float* __restrict__ B0inv) {
-  __shared__ double sL[kMaxBones][12];
+  __shared__ double sL[kMaxBones][12];   // local transforms [R_k | j_k - j_p(k)]
+  __shared__ double sG[kMaxBones][12];   // chain G_k, then rest-relative B_k
+  __shared__ double sN[kMaxBones][12];   // B_0^-1 B_k
+  __shared__ double sRod[kMaxBones][6];  // c, s, 1 - c, unit axis
   __shared__ double sB0i[12];
-  const int p = blockIdx.x, k = threadIdx.x;
+  __shared__ int sDepth[kMaxBones];
+  __shared__ int sMaxDepth;
+  const int p = blockIdx.x;
   if (p >= P) return;
-  if (k < nb) {
+  const int t = threadIdx.x, k = t / 12, e = t % 12;
+  const bool own = k < nb;
+  if (t == 0) sMaxDepth = 0;
+  __syncthreads();
+  if (own && e == 0) {
     const double* th = theta + ((size_t)p * nb + k) * 3;
-    double R[9];
     const double a = __dsqrt_rn(DA(DA(DM(th[0], th[0]), DM(th[1], th[1])), DM(th[2], th[2])));
     if (a == 0.0) {
-      for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0) ? 1.0 : 0.0;
+      sRod[k][0] = 1.0;  // identity rotation
     } else {
-      const double k0 = __ddiv_rn(th[0], a), k1 = __ddiv_rn(th[1], a), k2 = __ddiv_rn(th[2], a);
-      const double c = cos(a), s = sin(a), C = DS(1.0, c);
-      R[0] = DA(c, DM(DM(C, k0), k0));
-      R[1] = DS(DM(DM(C, k0), k1), DM(s, k2));
-      R[2] = DA(DM(DM(C, k0), k2), DM(s, k1));
-      R[3] = DA(DM(DM(C, k1), k0), DM(s, k2));
-      R[4] = DA(c, DM(DM(C, k1), k1));
-      R[5] = DS(DM(DM(C, k1), k2), DM(s, k0));
-      R[6] = DS(DM(DM(C, k2), k0), DM(s, k1));
-      R[7] = DA(DM(DM(C, k2), k1), DM(s, k0));
-      R[8] = DA(c, DM(DM(C, k2), k2));
+      const double c = cos(a), sn = sin(a);
+      sRod[k][0] = c;
+      sRod[k][1] = sn;
+      sRod[k][2] = DS(1.0, c);
+      sRod[k][3] = __ddiv_rn(th[0], a);
+      sRod[k][4] = __ddiv_rn(th[1], a);
+      sRod[k][5] = __ddiv_rn(th[2], a);
     }
-    const int par = parent[k];
-    for (int i = 0; i < 3; ++i) {
-      for (int j = 0; j < 3; ++j) sL[k][i * 4 + j] = R[i * 3 + j];
-      sL[k][i * 4 + 3] = (par < 0) ? rest[3 * k + i] : DS(rest[3 * k + i], rest[3 * par + i]);
-    }
+    int d = 0;
+    for (int j = parent[k]; j >= 0; j = parent[j]) ++d;
+    sDepth[k] = d;
+    atomicMax(&sMaxDepth, d);
   }
   __syncthreads();
-  double B[12];
-  if (k < nb) {
-    int path[kMaxBones], depth = 0;
-    for (int j = k; j >= 0; j = parent[j]) path[depth++] = j;  // k, parent(k), ..., root
-    double G[12], T[12];
-    for (int q = 0; q < 12; ++q) G[q] = sL[path[depth - 1]][q];
-    for (int d = depth - 2; d >= 0; --d) {
-      mat34_mul_d(G, sL[path[d]], T);
-      for (int q = 0; q < 12; ++q) G[q] = T[q];
+  const int i = e >> 2, j = e & 3;
+  if (own) {
+    // Rodrigues: R = c I + (1 - c) k k^T + s [k]_x
+    const double* th = theta + ((size_t)p * nb + k) * 3;
+    const bool zero = DA(DA(DM(th[0], th[0]), DM(th[1], th[1])), DM(th[2], th[2])) == 0.0;
+    const int par = parent[k];
+    double v;
+    if (j == 3) {
+      v = (par < 0) ? rest[3 * k + i] : DS(rest[3 * k + i], rest[3 * par + i]);
+    } else if (zero) {
+      v = i == j ? 1.0 : 0.0;
+    } else {
+      const double c = sRod[k][0], sn = sRod[k][1], C = sRod[k][2];
+      const double ki = sRod[k][3 + i], kj = sRod[k][3 + j];
+      const double Ck = DM(DM(C, ki), kj);
+      if (i == j) {
+        v = DA(c, Ck);
+      } else {
+        // the cross-product term s k_m, m the third axis; its sign as in [k]_x
+        const int m = 3 - i - j;
+        const double sk = DM(sn, sRod[k][3 + m]);
+        const bool plus = (i == 0 && j == 2) || (i == 1 && j == 0) || (i == 2 && j == 1);
+        v = plus ? DA(Ck, sk) : DS(Ck, sk);
+      }
     }
-    // rest-relative bone transform B_k = G_k [I | -j_k] + root translation
-    for (int i = 0; i < 3; ++i) {
-      for (int j = 0; j < 3; ++j) B[i * 4 + j] = G[i * 4 + j];
+    sL[k][e] = v;
+  }
+  __syncthreads();
+  const int depth = own ? sDepth[k] : -1;
+  const int maxd = sMaxDepth;
+  for (int d = 0; d <= maxd; ++d) {  // parents are final before their children read them
+    if (depth == d) sG[k][e] = d == 0 ? sL[k][e] : mat34_elem_d(sG[parent[k]], sL[k], e);
+    __syncthreads();
+  }
+  // rest-relative bone transform B_k = G_k [I | -j_k] + root translation
+  double b = 0.0;
+  if (own) {
+    const double* G = sG[k];
+    if (j < 3) {
+      b = G[e];
+    } else {
       const double Rj = DA(DA(DM(G[i * 4 + 0], rest[3 * k + 0]), DM(G[i * 4 + 1], rest[3 * k + 1])),
                            DM(G[i * 4 + 2], rest[3 * k + 2]));
-      B[i * 4 + 3] = DA(DS(G[i * 4 + 3], Rj), trans[(size_t)p * 3 + i]);
+      b = DA(DS(G[i * 4 + 3], Rj), trans[(size_t)p * 3 + i]);
     }
-    if (k == 0) rigid_inv_d(B, sB0i);  // the root is bone 0 (parents precede children)
   }
+  __syncthreads();  // every thread has read its G before B overwrites it
+  if (own) sG[k][e] = b;
   __syncthreads();
-  if (k < nb) {
-    double Nk[12], Ni[12];
-    mat34_mul_d(sB0i, B, Nk);
-    rigid_inv_d(Nk, Ni);
-    float* No = N + ((size_t)p * nb + k) * 12;
-    float* Nio = Ninv + ((size_t)p * nb + k) * 12;
-    for (int q = 0; q < 12; ++q) {
-      No[q] = (float)Nk[q];
-      Nio[q] = (float)Ni[q];
-    }
-    if (k == 0)
-      for (int q = 0; q < 12; ++q) B0inv[(size_t)p * 12 + q] = (float)sB0i[q];
+  if (k == 0) sB0i[e] = rigid_inv_elem_d(sG[0], e);  // the root is bone 0 (parents precede children)
+  __syncthreads();
+  if (own) sN[k][e] = mat34_elem_d(sB0i, sG[k], e);
+  __syncthreads();
+  if (own) {
+    N[((size_t)p * nb + k) * 12 + e] = (float)sN[k][e];
+    Ninv[((size_t)p * nb + k) * 12 + e] = (float)rigid_inv_elem_d(sN[k], e);
+    if (k == 0) B0inv[(size_t)p * 12 + e] = (float)sB0i[e];
   }
 }
 
 cudaError_t launch_pose_chain(int P, int nb, const int* parent, const double* rest, const double* theta,
                               const double* trans, float* N, float* Ninv, float* B0inv, cudaStream_t s) {
-  pose_chain_kernel<<<P, 32, 0, s>>>(P, nb, parent, rest, theta, trans, N, Ninv, B0inv);
+  pose_chain_kernel<<<P, (nb * 12 + 31) / 32 * 32, 0, s>>>(P, nb, parent, rest, theta, trans, N, Ninv, B0inv);
   return cudaGetLastError();
 }
 
@@ -378,14 +408,19 @@ __global__ void __launch_bounds__(256) occ_cover_kernel(SkinDev S, int V, const 
   if (live) {
     for (int z = s0[2] / kSub; z <= s1[2] / kSub; ++z) {
       const int z0 = max(s0[2] - kSub * z, 0), z1 = min(s1[2] - kSub * z, kSub - 1);
+      // one bit (kSub sy + kSub^2 sz) per z-layer of the box: 0x0001000100010001 masked
+      const unsigned long long zs = (z1 == kSub - 1 ? ~0ull : (1ull << (16 * (z1 + 1))) - 1ull) &
+                                    ~((1ull << (16 * z0)) - 1ull) & 0x0001000100010001ull;
       for (int y = s0[1] / kSub; y <= s1[1] / kSub; ++y) {
         const int y0 = max(s0[1] - kSub * y, 0), y1 = min(s1[1] - kSub * y, kSub - 1);
+        // one bit per row of the box within a layer (nibble sy), then per layer:
+        // the products place disjoint copies of the x-row, so they add without carries
+        const unsigned long long ys = ((1ull << (4 * (y1 + 1))) - 1ull) & ~((1ull << (4 * y0)) - 1ull) & 0x1111ull;
+        const unsigned long long yz = ys * zs;
         for (int x = s0[0] / kSub; x <= s1[0] / kSub; ++x) {
           const int x0 = max(s0[0] - kSub * x, 0), x1 = min(s1[0] - kSub * x, kSub - 1);
           const unsigned long long row = ((1ull << (x1 + 1)) - 1ull) & ~((1ull << x0) - 1ull);
-          unsigned long long m = 0ull;
-          for (int sz = z0; sz <= z1; ++sz)
-            for (int sy = y0; sy <= y1; ++sy) m |= row << (kSub * (sy + kSub * sz));
+          const unsigned long long m = row * yz;  // bits x + kSub (sy + kSub sz) of the box
           if (shared)
             atomicOr(win + ((x - wlo[0]) + ex * ((y - wlo[1]) + ey * (z - wlo[2]))), m);
           else

@@ -53,6 +53,7 @@ struct ia_ctx {
   // is possible, for pose sub_pose (-1: none; any change of the blended grid
   // clears it), and the occupancy cells to search
   unsigned long long* d_sub = nullptr;  // [R^3]
+  unsigned* d_cen = nullptr;             // [ceil(R^3 / 32)] centre flags of the culling
   unsigned* d_cand_count = nullptr;
   int* d_cand = nullptr;                // [R^3]
   int sub_pose = -1;
@@ -268,7 +269,8 @@ cudaError_t occ_density(ia_ctx* c, int pose, const float* jitter, float* sigma, 
   const BoxDev box = box_dev(c);
   if (!c->occ_cull) return launch_occ_density(a, box, jitter, nullptr, nullptr, sigma, stats, c->d_work, c->num_sms, s);
   c->sub_pose = -1;
-  cudaError_t e = launch_occ_cull(a, box, jitter, c->d_sub, c->d_cand_count, c->d_cand, sigma, stats, s);
+  cudaError_t e =
+      launch_occ_cull(a, box, jitter, c->d_sub, c->d_cen, c->d_cand_count, c->d_cand, sigma, stats, s);
   if (e != cudaSuccess) return e;
   c->sub_pose = pose;
   return launch_occ_density(a, box, jitter, c->d_cand, c->d_cand_count, sigma, stats, c->d_work, c->num_sms, s);
@@ -366,6 +368,7 @@ ia_status ia_create(const ia_config* cfg, ia_ctx** out) {
   if (e == cudaSuccess) e = dalloc(&c->d_sigma, (size_t)R * R * R);
   if (e == cudaSuccess) e = dalloc(&c->d_occ_ema, (size_t)R * R * R);
   if (e == cudaSuccess) e = dalloc(&c->d_sub, (size_t)R * R * R);
+  if (e == cudaSuccess) e = dalloc(&c->d_cen, ((size_t)R * R * R + 31) / 32);
   if (e == cudaSuccess) e = dalloc(&c->d_cand_count, (size_t)1);
   if (e == cudaSuccess) e = dalloc(&c->d_cand, (size_t)R * R * R);
   if (e == cudaSuccess) e = cudaMemset(c->d_occ_ema, 0, sizeof(float) * R * R * R);
@@ -404,6 +407,7 @@ void ia_destroy(ia_ctx* c) {
   dfree(c->d_sigma);
   dfree(c->d_occ_ema);
   dfree(c->d_sub);
+  dfree(c->d_cen);
   dfree(c->d_sub_all);
   dfree(c->d_cand_count);
   dfree(c->d_cand);
@@ -850,7 +854,7 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
         c->sub_all_cap = c->n_poses;
       }
       if (!c->sub_all_valid) {
-        IA_CUDA(c, launch_occ_cover(a.P.S, (int)V, c->n_poses, a.P.cfg, a.box, c->d_sub_all, s),
+        IA_CUDA(c, launch_occ_cover(a.P.S, (int)V, c->n_poses, a.P.cfg, a.box, c->d_sub_all, nullptr, s),
                 "ia_train_step: culling masks");
         c->sub_all_valid = true;
       }

@@ -224,9 +224,10 @@ cudaError_t launch_occ_density(const PosedArgs& a, const BoxDev& box, const floa
                                const unsigned* count, float* sigma, unsigned long long* stats, unsigned* work,
                                int num_sms, cudaStream_t s);
 cudaError_t launch_occ_cover(const SkinDev& S, int V, int n_poses, const SolveCfg& cfg, const BoxDev& box,
-                             unsigned long long* sub, cudaStream_t s);
+                             unsigned long long* sub, unsigned* cen, cudaStream_t s);
 cudaError_t launch_occ_cull(const PosedArgs& a, const BoxDev& box, const float* jitter, unsigned long long* sub,
-                            unsigned* count, int* cells, float* sigma, unsigned long long* stats, cudaStream_t s);
+                            unsigned* cen, unsigned* count, int* cells, float* sigma, unsigned long long* stats,
+                            cudaStream_t s);
 cudaError_t launch_gather_probe(const float4* table, int64_t n_records, int iters, int blocks, float* sink,
                                 cudaStream_t s);
 cudaError_t launch_occ_ema(const float* sigma, float* d, int n, float decay, cudaStream_t s);

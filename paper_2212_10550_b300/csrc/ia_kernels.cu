@@ -317,13 +317,21 @@ cudaError_t launch_occ_density(const PosedArgs& a, const BoxDev& box, const floa
 // over the occupancy cells its boxes meet and then adds each touched word to
 // the grid with one global OR; a block whose window would not fit writes
 // straight to the grid.
+// With cen (one pose only) it also marks, one bit per occupancy cell, the cells
+// whose centre (cell_center's fp32 value) lies inside a grown box: the point
+// test that the centre queries of the per-pose occupancy refresh use, finer
+// than the sub-cell masks (a rootless centre in a marked sub-cell is dropped
+// when no box holds the point itself).  The box's sub-cell range holds every
+// such cell (the index arithmetic is monotone), so the loop below visits them.
 constexpr int kCoverWin = 4096;  // 64-bit words of the shared window (32 KB)
 
 // blockIdx.y: the pose (blended grid S.M + pose * V * 3, masks sub + pose * R^3).
 __global__ void __launch_bounds__(256) occ_cover_kernel(SkinDev S, int V, const BoxDev box, float slack,
-                                                        unsigned long long* __restrict__ sub) {
+                                                        unsigned long long* __restrict__ sub,
+                                                        unsigned* __restrict__ cen) {
   static_assert(kSub * kSub * kSub == 64, "one 64-bit word per occupancy cell");
   __shared__ unsigned long long win[kCoverWin];
+  __shared__ unsigned char wcen[kCoverWin];  // centre flags of the window's cells
   __shared__ int wlo[3], whi[3];
   S.M += (size_t)blockIdx.y * V * 3;
   sub += (size_t)blockIdx.y * box.R * box.R * box.R;
@@ -339,6 +347,7 @@ __global__ void __launch_bounds__(256) occ_cover_kernel(SkinDev S, int V, const 
   __syncthreads();
   const int ns = kSub * box.R;  // sub-cells per axis
   int s0[3] = {0, 0, 0}, s1[3] = {-1, -1, -1};
+  float blo[3] = {0.f, 0.f, 0.f}, bhi[3] = {-1.f, -1.f, -1.f};  // the grown box
   bool live = cx < nc && cy < nc && cz < nc;
   if (live) {
     float h[3], v0[3];
@@ -384,8 +393,10 @@ __global__ void __launch_bounds__(256) occ_cover_kernel(SkinDev S, int V, const 
                          fabsf(A[corner][3 * a + 2] - mean[3 * a + 2]) * h[2]);
       // sub_marked's index arithmetic (fp32), clamped before the conversion
       const float g = m + slack;
-      const float f0 = floorf(__fmul_rn(__fsub_rn(lo[a] - g, box.nmin[a]), box.sub_scale[a]));
-      const float f1 = floorf(__fmul_rn(__fsub_rn(hi[a] + g, box.nmin[a]), box.sub_scale[a]));
+      blo[a] = lo[a] - g;
+      bhi[a] = hi[a] + g;
+      const float f0 = floorf(__fmul_rn(__fsub_rn(blo[a], box.nmin[a]), box.sub_scale[a]));
+      const float f1 = floorf(__fmul_rn(__fsub_rn(bhi[a], box.nmin[a]), box.sub_scale[a]));
       if (!(f1 >= 0.f) || !(f0 <= (float)(ns - 1))) live = false;  // the box misses the grid
       s0[a] = (int)fminf(fmaxf(f0, 0.f), (float)(ns - 1));
       s1[a] = (int)fmaxf(fminf(f1, (float)(ns - 1)), 0.f);
@@ -403,11 +414,20 @@ __global__ void __launch_bounds__(256) occ_cover_kernel(SkinDev S, int V, const 
   const bool any = whi[0] >= 0;
   const bool shared = any && ex * ey * ez <= kCoverWin;
   if (shared)
-    for (int t = tid; t < ex * ey * ez; t += blockDim.x) win[t] = 0ull;
+    for (int t = tid; t < ex * ey * ez; t += blockDim.x) {
+      win[t] = 0ull;
+      wcen[t] = 0;
+    }
   __syncthreads();
+  // cell_center's fp32 coordinate of cell index i on axis a, and the box test
+  auto centre_in = [&](int a, int i) {
+    const float xc = __fadd_rn(box.nmin[a], __fmul_rn(__fadd_rn((float)i, 0.5f), box.cell_size[a]));
+    return xc >= blo[a] && xc <= bhi[a];
+  };
   if (live) {
     for (int z = s0[2] / kSub; z <= s1[2] / kSub; ++z) {
       const int z0 = max(s0[2] - kSub * z, 0), z1 = min(s1[2] - kSub * z, kSub - 1);
+      const bool in_z = cen && centre_in(2, z);
       // one bit (kSub sy + kSub^2 sz) per z-layer of the box: 0x0001000100010001 masked
       const unsigned long long zs = (z1 == kSub - 1 ? ~0ull : (1ull << (16 * (z1 + 1))) - 1ull) &
                                     ~((1ull << (16 * z0)) - 1ull) & 0x0001000100010001ull;
@@ -417,14 +437,21 @@ __global__ void __launch_bounds__(256) occ_cover_kernel(SkinDev S, int V, const 
         // the products place disjoint copies of the x-row, so they add without carries
         const unsigned long long ys = ((1ull << (4 * (y1 + 1))) - 1ull) & ~((1ull << (4 * y0)) - 1ull) & 0x1111ull;
         const unsigned long long yz = ys * zs;
+        const bool in_yz = in_z && centre_in(1, y);
         for (int x = s0[0] / kSub; x <= s1[0] / kSub; ++x) {
           const int x0 = max(s0[0] - kSub * x, 0), x1 = min(s1[0] - kSub * x, kSub - 1);
           const unsigned long long row = ((1ull << (x1 + 1)) - 1ull) & ~((1ull << x0) - 1ull);
           const unsigned long long m = row * yz;  // bits x + kSub (sy + kSub sz) of the box
-          if (shared)
-            atomicOr(win + ((x - wlo[0]) + ex * ((y - wlo[1]) + ey * (z - wlo[2]))), m);
-          else
-            atomicOr(sub + (x + box.R * (y + box.R * z)), m);
+          const bool in_c = in_yz && centre_in(0, x);
+          if (shared) {
+            const int w = (x - wlo[0]) + ex * ((y - wlo[1]) + ey * (z - wlo[2]));
+            atomicOr(win + w, m);
+            if (in_c) wcen[w] = 1;  // every writer stores the same value
+          } else {
+            const int cell = x + box.R * (y + box.R * z);
+            atomicOr(sub + cell, m);
+            if (in_c) atomicOr(cen + (cell >> 5), 1u << (cell & 31));
+          }
         }
       }
     }
@@ -435,25 +462,28 @@ __global__ void __launch_bounds__(256) occ_cover_kernel(SkinDev S, int V, const 
       const unsigned long long m = win[t];
       if (m) {
         const int x = wlo[0] + t % ex, y = wlo[1] + (t / ex) % ey, z = wlo[2] + t / (ex * ey);
-        atomicOr(sub + (x + box.R * (y + box.R * z)), m);
+        const int cell = x + box.R * (y + box.R * z);
+        atomicOr(sub + cell, m);
+        if (wcen[t]) atomicOr(cen + (cell >> 5), 1u << (cell & 31));
       }
     }
 }
 
-// One thread per occupancy cell: its query point (the density kernel's) and
-// that point's sub-cell mark.  Points that can have a root go to `cells` (one
-// atomic per warp; order across warps is free, since each cell's search is
-// independent of the others); the others get density 0.
+// One thread per occupancy cell: its query point (the density kernel's), that
+// point's sub-cell mark and, for centre queries (cen), its centre flag.  Points
+// that can have a root go to `cells` (one atomic per warp; order across warps
+// is free, since each cell's search is independent of the others); the others
+// get density 0.
 __global__ void occ_cand_kernel(const BoxDev box, const float* __restrict__ jitter,
-                                const unsigned long long* __restrict__ sub, int* __restrict__ cells,
-                                unsigned* __restrict__ count, float* __restrict__ sigma,
+                                const unsigned long long* __restrict__ sub, const unsigned* __restrict__ cen,
+                                int* __restrict__ cells, unsigned* __restrict__ count, float* __restrict__ sigma,
                                 unsigned long long* __restrict__ stats) {
   const int n = box.R * box.R * box.R;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   bool cand = false;
   if (c < n) {
     const float3 x = jitter ? cell_point(box, c, jitter + 3 * (size_t)c) : cell_center(box, c);
-    cand = sub_marked(sub, box, x);
+    cand = sub_marked(sub, box, x) && (!cen || ((__ldg(cen + (c >> 5)) >> (c & 31)) & 1u));
     if (!cand) sigma[c] = 0.f;
   }
   const unsigned m = __ballot_sync(kFull, cand);
@@ -467,12 +497,15 @@ __global__ void occ_cand_kernel(const BoxDev box, const float* __restrict__ jitt
 }
 
 // The root-culling masks of n_poses consecutive blended grids (S.M = the
-// first, V vertices each) into sub [n_poses][R^3] (cleared here).
+// first, V vertices each) into sub [n_poses][R^3] (cleared here); with cen
+// (n_poses == 1) also the centre flags [ceil(R^3 / 32)] (cleared here).
 cudaError_t launch_occ_cover(const SkinDev& S, int V, int n_poses, const SolveCfg& cfg, const BoxDev& box,
-                             unsigned long long* sub, cudaStream_t s) {
+                             unsigned long long* sub, unsigned* cen, cudaStream_t s) {
   const size_t n = (size_t)box.R * box.R * box.R;
+  if (cen && n_poses != 1) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(sub, 0, n * n_poses * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
+  if (cen && (e = cudaMemsetAsync(cen, 0, (n + 31) / 32 * sizeof(unsigned), s)) != cudaSuccess) return e;
   // slack: the Broyden tolerance plus 1e-4 of the scene's largest coordinate
   // (fp32 rounding of the LBS map and of these bounds is below 1e-6 of it)
   float L = 0.f;
@@ -481,18 +514,22 @@ cudaError_t launch_occ_cover(const SkinDev& S, int V, int n_poses, const SolveCf
   const float slack = std::sqrt(cfg.tol2) + 1e-4f * L;
   const int nc = S.Rw - 1;
   const int blocks = ((nc + 7) / 8) * ((nc + 7) / 8) * ((nc + 3) / 4);
-  occ_cover_kernel<<<dim3(blocks, n_poses), 256, 0, s>>>(S, V, box, slack, sub);
+  occ_cover_kernel<<<dim3(blocks, n_poses), 256, 0, s>>>(S, V, box, slack, sub, cen);
   return cudaGetLastError();
 }
 
-// sub: [R^3] masks (rebuilt here); count: the candidate count (cleared here)
+// sub: [R^3] masks, cen: [ceil(R^3 / 32)] centre flags (both rebuilt here; the
+// flags only serve centre queries, jitter == null); count: the candidate count
+// (cleared here)
 cudaError_t launch_occ_cull(const PosedArgs& a, const BoxDev& box, const float* jitter, unsigned long long* sub,
-                            unsigned* count, int* cells, float* sigma, unsigned long long* stats, cudaStream_t s) {
+                            unsigned* cen, unsigned* count, int* cells, float* sigma, unsigned long long* stats,
+                            cudaStream_t s) {
   const int n = box.R * box.R * box.R;
   cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  if ((e = launch_occ_cover(a.S, a.S.Rw * a.S.Rw * a.S.Rw, 1, a.cfg, box, sub, s)) != cudaSuccess) return e;
-  occ_cand_kernel<<<(n + 255) / 256, 256, 0, s>>>(box, jitter, sub, cells, count, sigma, stats);
+  unsigned* c = jitter ? nullptr : cen;
+  if ((e = launch_occ_cover(a.S, a.S.Rw * a.S.Rw * a.S.Rw, 1, a.cfg, box, sub, c, s)) != cudaSuccess) return e;
+  occ_cand_kernel<<<(n + 255) / 256, 256, 0, s>>>(box, jitter, sub, c, cells, count, sigma, stats);
   return cudaGetLastError();
 }
 

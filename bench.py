@@ -46,12 +46,12 @@ FLOP_ROOT = 620 + 960 + 12800 + 40  # Newton polish with the analytic Jacobian, 
 FLOP_SAMPLE = 20       # alpha, transmittance, colour accumulation
 GATHER_LBS = 8 * 48    # bytes of the blended grid one LBS evaluation reads
 GATHER_HASH = 16 * 8 * 8  # bytes of the fp32 hash table one field evaluation reads
-# DRAM bytes (read + write) of one render_kernel<2, fp32> launch on this workload,
+# DRAM bytes (read + write) of one render_kernel<1, fp32> launch on this workload,
 # from the ncu capture summarised in profiles/render_kernel_540x540_fp32.md; the
 # ncu-measured busiest unit of that launch is reported beside the roofline
-RENDER_DRAM_BYTES = 52.256e6 + 2.020e6
-RENDER_LIMITER = {"unit": "L1 (blended-grid gathers)", "l1tex_throughput_pct": 62.7, "issue_active_pct": 30.1,
-                  "fma_pipe_pct": 17.2, "l1_hit_pct": 90.9, "l2_hit_pct": 97.3, "simt_lanes_per_inst": 20.65,
+RENDER_DRAM_BYTES = 51.910e6 + 2.344e6
+RENDER_LIMITER = {"unit": "L1 (blended-grid gathers)", "l1tex_throughput_pct": 53.6, "issue_active_pct": 34.0,
+                  "fma_pipe_pct": 19.6, "l1_hit_pct": 90.1, "l2_hit_pct": 97.0, "simt_lanes_per_inst": 18.0,
                   "source": "profiles/render_kernel_540x540_fp32.md"}
 
 

@@ -112,6 +112,25 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ our arm
 
+def job_seconds(local_s, world, device):
+    """The job's time under torchrun: the slowest rank's (all-reduce MAX over
+    the process group); with one process, the local time."""
+    if world <= 1:
+        return local_s
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local_s], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, local_s, world, device):
+    """Whole-job throughput of independent replicas: every rank's units over
+    the slowest rank's time; returns (rate, job seconds)."""
+    total_s = job_seconds(local_s, world, device)
+    return units_per_rank * world / total_s, total_s
+
+
 def make_ctx(torch, ia, sc, table, mlp, precision, early_T):
     cfg = ia.make_config(n_levels=sc.n_levels, log2_table=sc.log2_table, level_res=sc.level_res,
                          max_samples=sc.max_samples, broyden_max_iter=sc.broyden_max_iter,
@@ -604,18 +623,10 @@ def run_ours(args, rank, world, local_rank):
         train[name] = time_train_step(torch, ia, sc, table, mlp, flush, tsteps, 3, stream, n_rays=32768,
                                       precision=prec, prop=pp)
 
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([local_total_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_s = float(tt.item())
-    else:
-        total_s = local_total_s
+    fps, total_s = job_rate(args.steps, local_total_s, world, dev)
     if rank != 0:
         return None
-    frames = args.steps * world
     ms_per_step = 1e3 * total_s / args.steps
-    fps = frames / total_s
     peaks, peak_kind = load_peaks()
     sm_mhz = peaks.get("sm_max_mhz", 2032.0)
     peak = fp32_peak_tflops(sm_mhz)

@@ -314,6 +314,42 @@ typedef struct ia_grads {
 ia_status ia_train_step(ia_ctx *ctx, const ia_batch *batch, int occ_grid, float *loss, float *rgb_out,
                         const ia_grads *grads, void *stream);
 
+/* The training step split in two, for a loss computed by the caller (Sec. 3.2:
+ * the rendering is differentiable, so any loss on the rendered colour and
+ * opacity can be trained; Sec. 3.4 uses Eq. 9-12).
+ *
+ * ia_train_forward renders the batch's rays as ia_train_step does (normalised
+ * space of each ray's pose, occupied slots of occ_grid, posed field, front-to-
+ * back compositing of every sample, no early termination) and writes
+ *  rgb_out [n][3] (device) and alpha_out [n] (device or NULL; alpha = 1 - the
+ *  ray's final transmittance).
+ * table / mlp (device, fp32, laid out as in ia_set_params; NULL = the
+ * context's own) are the canonical field's parameters for this forward and its
+ * backward; they are read in place and must stay unchanged until the
+ * backward has run (a reduced-precision context converts a caller table into
+ * a context-owned fp16 copy).  The batch's target, alpha_target and
+ * regulariser are not used (n_reg must be 0).  The per-sample state (sample
+ * positions, selected roots, density and colour) stays in the context's
+ * training workspace; per-sample activations are not kept.
+ *
+ * ia_train_backward differentiates that forward: given the caller's
+ *  grad_rgb [n][3] = dL/dC and grad_alpha [n] = dL/dalpha (device; grad_alpha
+ *  may be NULL for zero)
+ * it runs the reverse compositing sweep and the same hand-written backward as
+ * ia_train_step (activations recomputed from the roots, MLP, hash-table
+ * scatter-add, implicit-function gradient through the root to the skinning
+ * grid and the bone transforms N_k; fp16 / bf16 with the dynamic loss scale),
+ * overwriting the four buffers of g (layouts as ia_grads).  It may be called
+ * more than once for one forward.  IA_ERR_STATE when there is no forward to
+ * differentiate: none ran, or ia_train_step, ia_set_pose, ia_set_skeleton, a
+ * skinning-grid ia_adam_step, or (when the forward read the context's own
+ * parameters) ia_set_params / ia_adam_step ran since.  One forward is kept per
+ * context: forwards for two batches need two contexts. */
+ia_status ia_train_forward(ia_ctx *ctx, const ia_batch *batch, int occ_grid, const float *table, const float *mlp,
+                           float *rgb_out, float *alpha_out, void *stream);
+ia_status ia_train_backward(ia_ctx *ctx, const float *grad_rgb, const float *grad_alpha, const ia_grads *grads,
+                            void *stream);
+
 /* Counters of the last ia_train_step (host struct; waits on `stream`): rays,
  * rays that cross the normalised box (hit_rays), their slots (marched_slots),
  * occupied samples, Broyden starts / iterations / converged chains / distinct
@@ -333,20 +369,35 @@ ia_status ia_train_stats(ia_ctx *ctx, ia_render_stats *stats, void *stream);
 ia_status ia_adam_step(ia_ctx *ctx, const float *g_table, const float *g_mlp, const float *g_skin, float lr,
                        float beta1, float beta2, float eps, void *stream);
 
-/* Measurement helper, not part of the method: every one of blocks x 256 threads
- * reads `iters` records of 48 bytes (three float4, one vertex of the blended
- * transform grid) at xorshift-random indices of table [n_records][12] fp32
- * (device, 16-byte aligned), and writes nothing that matters to sink (device,
- * one float).  Timing it on a table that fits L1 or L2 gives the random-gather
- * peak that the correspondence search's gathers are measured against. */
-ia_status ia_gather_probe(const float *table, int64_t n_records, int iters, int blocks, float *sink, void *stream);
-
 /* The loss scale S after the last ia_train_step (host float) and whether that
- * step overflowed and was skipped (host int32, 1 = skipped); either may be NULL,
- * not both.  Waits on `stream`.  fp32 contexts report S = 1, never skipped.
- * Returns IA_ERR_CUDA if the tensor-core weight-gradient reduction of a step
- * gave up waiting on its own copy pipeline (its gradients are then incomplete). */
+ * step was skipped (host int32, 1 = skipped: a scaled gradient or activation
+ * overflowed, or the tensor-core weight-gradient reduction gave up; every
+ * gradient buffer of a skipped step is zeroed and ia_adam_step leaves the
+ * parameters alone); either may be NULL, not both.  Waits on `stream`.  fp32
+ * contexts report S = 1, never skipped.  Returns IA_ERR_CUDA (after filling
+ * both outputs) if the last step's weight-gradient reduction gave up waiting
+ * on its copy / MMA pipeline (see ia_set_wait_limit); ia_train_stats reports
+ * the same. */
 ia_status ia_loss_scale(ia_ctx *ctx, float *scale, int32_t *skipped, void *stream);
+
+/* Bound, in nanoseconds, on every wait of the reduced-precision training step's
+ * tensor-core pipeline (TMA loads and MMAs on shared-memory barriers; a wait
+ * past it makes the kernel stop issuing, wait with a 1 s bound for the copies
+ * and MMAs it already started, free its tensor memory and skip the step,
+ * reported by ia_loss_scale / ia_train_stats as IA_ERR_CUDA).  0 restores the
+ * default (200 ms, far above the reduction's normal time); 1..1e10 otherwise.
+ * Not a method parameter: a diagnostics setting, also used to exercise the
+ * failure path. */
+ia_status ia_set_wait_limit(ia_ctx *ctx, int64_t limit_ns);
+
+/* Failure injection for tests of the bounded-wait path (no fault, no hang):
+ * with IA_INJECT_WITHHOLD_COPY the weight-gradient pipeline of the following
+ * reduced-precision training steps never issues the TMA copy of each CTA's last
+ * operand chunk, so the MMA thread's wait for it runs out after the wait limit
+ * (ia_set_wait_limit) and the step is skipped and reported as IA_ERR_CUDA.
+ * 0 turns injection off.  Not a method parameter. */
+#define IA_INJECT_WITHHOLD_COPY 1
+ia_status ia_set_fault_injection(ia_ctx *ctx, int flags);
 
 /* Same result as ia_update_occupancy(ctx, pose, IA_OCC_POSE, NULL, bits_out,
  * NULL, stream), for callers that cannot allocate device memory while they run:

@@ -80,7 +80,7 @@ class Model(C.Structure):
         ("W1", PD), ("b1", PD), ("W2", PD), ("b2", PD), ("W3", PD), ("b3", PD),
         ("max_iter", C.c_int), ("tol", C.c_double), ("n_slots", C.c_int),
         ("early_T", C.c_double), ("tau", C.c_double), ("dilate", C.c_int),
-        ("quantize_fp32", C.c_int),
+        ("quantize_fp32", C.c_int), ("h0_analytic", C.c_int),
     ]
 
 
@@ -104,6 +104,7 @@ def _declare(L):
     PM, PP, PC = C.POINTER(Model), C.POINTER(Pose), C.POINTER(Camera)
     sig = {
         "or_pose_chain": (None, [PM, PD, PD, PP]),
+        "or_cos_sin": (None, [C.c_double, PD, PD]),
         "or_skin": (None, [PM, PD, PD, PD]),
         "or_lbs": (None, [PM, PP, PD, PD, PD]),
         "or_broyden": (C.c_int, [PM, PP, PD, PD, PD, PI32, PD, PI32]),
@@ -154,7 +155,7 @@ class OracleModel:
     """Keeps the fp64 arrays alive and exposes the oracle entry points."""
 
     def __init__(self, scene, table, mlp, *, early_T: float = 0.0, quantize_fp32: bool = True,
-                 skin=None, n_slots=None, tol=None, max_iter=None):
+                 skin=None, n_slots=None, tol=None, max_iter=None, h0_analytic=False):
         L_ = lib()
         self.scene = scene
         self.parent = np.ascontiguousarray(scene.parents, dtype=np.int32)
@@ -190,6 +191,7 @@ class OracleModel:
         m.tau = scene.occ_tau
         m.dilate = scene.occ_dilate
         m.quantize_fp32 = 1 if quantize_fp32 else 0
+        m.h0_analytic = 1 if h0_analytic else 0
         self.m = m
         self.L = L_
 
@@ -386,6 +388,13 @@ class OracleModel:
         self.L.or_occupancy(C.byref(self.m), C.byref(p), _p(sigma, C.c_double),
                             _p(bits, C.c_uint32), nthreads)
         return sigma, bits
+
+
+def cos_sin(a):
+    """(cos a, sin a) as the pose chain evaluates them (fixed-order power series)."""
+    c, s = C.c_double(), C.c_double()
+    lib().or_cos_sin(float(a), C.byref(c), C.byref(s))
+    return c.value, s.value
 
 
 def occ_bits(R, dilate, tau, sigma):

@@ -16,6 +16,11 @@ def declare(L):
                            P(C.c_double), P(C.c_double), P(C.c_double), C.c_int]
     L.or_train_loss.restype = C.c_double
     L.or_train_loss.argtypes = L.or_train.argtypes + [P(Loss)]
+    L.or_train_upstream.restype = None
+    L.or_train_upstream.argtypes = [P(Model), P(Pose), C.c_int, P(C.c_uint32), C.c_int, P(C.c_float), P(C.c_float),
+                                    P(C.c_int32), P(C.c_double), P(C.c_double), P(C.c_double), P(C.c_double),
+                                    P(C.c_int32), P(C.c_double), P(C.c_double), P(C.c_double), P(C.c_double),
+                                    C.c_int]
     L.or_density_reg.restype = C.c_double
     L.or_density_reg.argtypes = [P(Model), P(Pose), C.c_int, P(C.c_uint32), C.c_int, P(C.c_float), P(C.c_int32),
                                  C.c_double, P(C.c_int32), P(C.c_double), P(C.c_double), P(C.c_double),
@@ -91,6 +96,33 @@ def train(om, poses, occ_bits, origin, direction, pose_id, target, grad=True, nt
             fb = _p(fallbacks, C.c_int32)
         loss = om.L.or_train_prop(*common, C.byref(prop.q), _p(th, C.c_double), fb)
     return loss, rgb, flags, g
+
+
+def train_upstream(om, poses, occ_bits, origin, direction, pose_id, up_rgb=None, up_alpha=None, nthreads=0):
+    """Forward colour and alpha of the rays and, with up_rgb ([n, 3] dL/dC) and
+    up_alpha ([n] dL/dalpha, optional), the backward of a loss built on them:
+    (rgb [n, 3], alpha [n], flags [n], grads dict as train() or None)."""
+    from . import _p
+    sc = om.scene
+    n = len(pose_id)
+    arr = pose_array(poses) if isinstance(poses, (list, tuple)) else poses
+    o = np.ascontiguousarray(origin, dtype=np.float32)
+    d = np.ascontiguousarray(direction, dtype=np.float32)
+    pid = np.ascontiguousarray(pose_id, dtype=np.int32)
+    occ = np.ascontiguousarray(occ_bits, dtype=np.uint32)
+    ur = None if up_rgb is None else np.ascontiguousarray(up_rgb, dtype=np.float64).reshape(n, 3)
+    ua = None if up_alpha is None else np.ascontiguousarray(up_alpha, dtype=np.float64).reshape(n)
+    rgb, alpha = np.zeros((n, 3)), np.zeros(n)
+    flags = np.zeros(n, dtype=np.int32)
+    g = None
+    if ur is not None:
+        g = dict(table=np.zeros((sc.n_table_entries(), sc.n_features)), mlp=np.zeros(mlp_size(sc)),
+                 skin=np.zeros(om.skin.shape), bones=np.zeros((len(arr), sc.n_bones, 12)))
+    args = [g[k] if g else None for k in ("table", "mlp", "skin", "bones")]
+    om.L.or_train_upstream(C.byref(om.m), arr, len(arr), _p(occ, C.c_uint32), n, _p(o, C.c_float), _p(d, C.c_float),
+                           _p(pid, C.c_int32), _p(ur, C.c_double), _p(ua, C.c_double), _p(rgb, C.c_double),
+                           _p(alpha, C.c_double), _p(flags, C.c_int32), *[_p(a, C.c_double) for a in args], nthreads)
+    return rgb, alpha, flags, g
 
 
 def density_reg(om, poses, occ_bits, x, pose_id, weight, grads=None):

@@ -71,6 +71,31 @@ static double norm3(const double v[3]) { return sqrt(v[0] * v[0] + v[1] * v[1] +
 /* Pose chain (Sec. 3.1 bone transforms B; Sec. 3.3 normalised space)         */
 /* ------------------------------------------------------------------------- */
 
+/* cos a and sin a from their Maclaurin series
+     sin x = sum_k (-1)^k x^(2k+1) / (2k+1)!,   cos x = sum_k (-1)^k x^(2k) / (2k)!,
+   after one reduction of a by the nearest multiple of 2 pi (fp64 constant),
+   each term from the previous one, t_{k+1} = t_k (-x^2) / ((2k+2)(2k+3)) for
+   sin and t_k (-x^2) / ((2k+1)(2k+2)) for cos, added in order; 22 terms (the
+   first omitted one is below pi^46 / 46! < 1e-32).  Every step is one
+   correctly rounded fp64 operation in a fixed order, so the values are the
+   same on any IEEE machine (the library's pose chain takes the same steps,
+   which keeps the fp32 bone transforms bit-identical); they agree with the C
+   library's cos / sin to a few 1e-16. */
+void or_cos_sin(double a, double *c, double *s) {
+  const double two_pi = 6.283185307179586;
+  const double x = a - rint(a / two_pi) * two_pi;
+  const double mx2 = -(x * x);
+  double ts = x, tc = 1.0, sn = x, cs = 1.0;
+  for (int k = 0; k < 22; ++k) {
+    ts = ts * mx2 / (double)((2 * k + 2) * (2 * k + 3));
+    tc = tc * mx2 / (double)((2 * k + 1) * (2 * k + 2));
+    sn = sn + ts;
+    cs = cs + tc;
+  }
+  *c = cs;
+  *s = sn;
+}
+
 /* Rodrigues: rotation by |th| about th/|th|. */
 static void rodrigues(const double th[3], double R[9]) {
   double a = sqrt(th[0] * th[0] + th[1] * th[1] + th[2] * th[2]);
@@ -79,7 +104,9 @@ static void rodrigues(const double th[3], double R[9]) {
     return;
   }
   double k0 = th[0] / a, k1 = th[1] / a, k2 = th[2] / a;
-  double c = cos(a), s = sin(a), C = 1.0 - c;
+  double c, s;
+  or_cos_sin(a, &c, &s);
+  double C = 1.0 - c;
   R[0] = c + C * k0 * k0;
   R[1] = C * k0 * k1 - s * k2;
   R[2] = C * k0 * k2 + s * k1;
@@ -202,18 +229,23 @@ void or_lbs(const or_model *m, const or_pose *p, const double x[3], double y[3],
 
 /* Broyden's method on g(x) = LBS(x) - x' from x0.  The initial inverse Jacobian
    is that of LBS with the skinning weights held at their value at x0, i.e.
-   (sum_i w_i(x0) R_i)^-1; the good-Broyden rank-one updates then correct it. */
+   (sum_i w_i(x0) R_i)^-1 (with m->h0_analytic: the full analytic J(x0)^-1);
+   the good-Broyden rank-one updates then correct it. */
 int or_broyden(const or_model *m, const or_pose *p, const double xn[3], const double x0[3],
                double x[3], int *iters, double *res_norm, int *flags) {
   double y[3], J[9], H[9], r[3], det, w[OR_MAX_BONES];
   int fl = 0;
   for (int a = 0; a < 3; ++a) x[a] = x0[a];
-  or_lbs(m, p, x, y, NULL);
-  or_skin(m, x, w, NULL);
-  for (int i = 0; i < 9; ++i) J[i] = 0.0;
-  for (int i = 0; i < m->nb; ++i)
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b) J[a * 3 + b] += w[i] * p->N[i][a * 4 + b];
+  if (m->h0_analytic) {
+    or_lbs(m, p, x, y, J);
+  } else {
+    or_lbs(m, p, x, y, NULL);
+    or_skin(m, x, w, NULL);
+    for (int i = 0; i < 9; ++i) J[i] = 0.0;
+    for (int i = 0; i < m->nb; ++i)
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) J[a * 3 + b] += w[i] * p->N[i][a * 4 + b];
+  }
   for (int a = 0; a < 3; ++a) r[a] = y[a] - xn[a];
   int ok = inv3(J, H, &det);
   if (fabs(det) > 0.5e-6 && fabs(det) < 2e-6) fl |= OR_FLAG_SING;
@@ -548,9 +580,13 @@ static void slot_position(const float o[3], const float d[3], float tn, float dt
 /* Volume rendering (Eq. 8, with alpha = 1 - exp(-sigma delta))               */
 /* ------------------------------------------------------------------------- */
 
+/* One pixel's ray.  With q (a correspondence proposal and the pose's
+   axis-angles theta) every sample's search starts from the proposal's bones
+   and falls back to every bone-wise start when they find no valid root
+   (or_posed_field_prop); *nfb counts those fallbacks (may be NULL). */
 static void render_ray(const or_model *m, const or_pose *p, const or_camera *c, const uint32_t *occ,
                        int u, int v, double rgb[3], double *alpha, int *flags, int *nsamp,
-                       int64_t *iters) {
+                       int64_t *iters, const or_prop *q, const double *theta, int *nfb) {
   float o[3], d[3], tn, tf;
   double C[3] = {0.0, 0.0, 0.0}, T = 1.0;
   int fl = 0, ns = 0;
@@ -565,7 +601,13 @@ static void render_ray(const or_model *m, const or_pose *p, const or_camera *c, 
       ns++;
       or_sample s;
       double xn[3] = {(double)x[0], (double)x[1], (double)x[2]};
-      or_posed_field(m, p, xn, &s);
+      if (q) {
+        int fb = 0;
+        or_posed_field_prop(m, p, q, theta, xn, &s, &fb);
+        if (nfb) *nfb += fb;
+      } else {
+        or_posed_field(m, p, xn, &s);
+      }
       fl |= s.flags;
       its += s.iters;
       if (s.start >= 0) {
@@ -601,7 +643,7 @@ void or_render(const or_model *m, const or_pose *p, const or_camera *c, const ui
   for (int r = 0; r < W * H; ++r) {
     int fl, ns;
     int64_t it;
-    render_ray(m, p, c, occ, r % W, r / W, rgb + 3 * r, alpha + r, &fl, &ns, &it);
+    render_ray(m, p, c, occ, r % W, r / W, rgb + 3 * r, alpha + r, &fl, &ns, &it, NULL, NULL, NULL);
     if (ray_flags) ray_flags[r] = fl;
     if (ray_nsamp) ray_nsamp[r] = ns;
     if (ray_iters) ray_iters[r] = it;
@@ -617,9 +659,25 @@ void or_render_pixels(const or_model *m, const or_pose *p, const or_camera *c,
   for (int r = 0; r < n; ++r) {
     int fl, ns;
     int64_t it;
-    render_ray(m, p, c, occ, pix[r] % W, pix[r] / W, rgb + 3 * r, alpha + r, &fl, &ns, &it);
+    render_ray(m, p, c, occ, pix[r] % W, pix[r] / W, rgb + 3 * r, alpha + r, &fl, &ns, &it, NULL, NULL, NULL);
     if (ray_flags) ray_flags[r] = fl;
     if (ray_nsamp) ray_nsamp[r] = ns;
+  }
+}
+
+void or_render_pixels_prop(const or_model *m, const or_pose *p, const or_prop *q, const double *theta,
+                           const or_camera *c, const uint32_t *occ, int n, const int32_t *pix, double *rgb,
+                           double *alpha, int *ray_flags, int *ray_nsamp, int *ray_fallbacks, int nthreads) {
+  set_threads(nthreads);
+  int W = c->width;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int r = 0; r < n; ++r) {
+    int fl, ns, fb = 0;
+    int64_t it;
+    render_ray(m, p, c, occ, pix[r] % W, pix[r] / W, rgb + 3 * r, alpha + r, &fl, &ns, &it, q, theta, &fb);
+    if (ray_flags) ray_flags[r] = fl;
+    if (ray_nsamp) ray_nsamp[r] = ns;
+    if (ray_fallbacks) ray_fallbacks[r] = fb;
   }
 }
 

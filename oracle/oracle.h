@@ -55,6 +55,9 @@ typedef struct or_model {
   double tau;                /* occupancy density threshold */
   int dilate;                /* occupancy dilation radius (cells, Chebyshev) */
   int quantize_fp32;         /* round bone transforms to fp32 (library storage) */
+  int h0_analytic;           /* Broyden's initial inverse Jacobian: 0 = LBS with the weights
+                                frozen at x0, (sum_i w_i(x0) R_i)^-1; 1 = the full analytic
+                                J(x0)^-1 (weight gradients included) */
 } or_model;
 
 typedef struct or_pose {
@@ -92,6 +95,9 @@ typedef struct or_sample {
   int iters;           /* Broyden updates summed over starts */
 } or_sample;
 
+/* cos a and sin a by their power series in fixed-order fp64 steps (reproducible
+ * on any IEEE machine; used by the pose chain's Rodrigues rotations). */
+void or_cos_sin(double a, double *c, double *s);
 /* Sec. 3.1 / Sec. 3.3: bone transforms from axis-angle pose and root translation. */
 void or_pose_chain(const or_model *m, const double *theta, const double *trans, or_pose *out);
 /* Eq. 5-6: trilinear skinning weights at canonical x (and d w / d x, [nb][3]). */
@@ -193,6 +199,14 @@ double or_prop_loss_grad(const or_model *m, const or_prop *q, int n, const float
                          double *g_table, double *g_mlp);
 void or_posed_field_prop(const or_model *m, const or_pose *p, const or_prop *q, const double *theta,
                          const double xn[3], or_sample *s, int *fallback);
+/* or_render_pixels with the proposal choosing every sample's starts (Sec. 3.2
+ * compositing, each sample's field from or_posed_field_prop; theta [nb][3] the
+ * pose's axis-angles); ray_fallbacks [n] (may be NULL) counts each ray's
+ * samples whose proposed starts found no valid root, so that the search over
+ * every bone ran. */
+void or_render_pixels_prop(const or_model *m, const or_pose *p, const or_prop *q, const double *theta,
+                           const or_camera *c, const uint32_t *occ, int n, const int32_t *pix, double *rgb,
+                           double *alpha, int *ray_flags, int *ray_nsamp, int *ray_fallbacks, int nthreads);
 /* or_train with the proposal choosing each sample's starts; theta_all
  * [n_poses][nb][3] axis-angles of the poses (the proposal's pose input);
  * ray_fallbacks [n] (may be NULL) counts each ray's samples that fell back to
@@ -208,6 +222,15 @@ double or_train_loss(const or_model *m, const or_pose *poses, int n_poses, const
                      const float *o, const float *d, const int32_t *pose_id, const double *target,
                      double *rgb_out, int *ray_flags, double *g_table, double *g_mlp, double *g_skin,
                      double *g_bones, int nthreads, const or_loss *lc);
+
+/* The same backward for dL/dC [n][3] and dL/dalpha [n] (NULL: zero) given by
+ * the caller (a loss built elsewhere on the rendered colour and opacity);
+ * rgb_out [n][3], alpha_out [n] (alpha = 1 - final transmittance), ray_flags
+ * and the gradients (overwritten) as or_train; any output may be NULL. */
+void or_train_upstream(const or_model *m, const or_pose *poses, int n_poses, const uint32_t *occ, int n,
+                       const float *o, const float *d, const int32_t *pose_id, const double *up_rgb,
+                       const double *up_alpha, double *rgb_out, double *alpha_out, int *ray_flags, double *g_table,
+                       double *g_mlp, double *g_skin, double *g_bones, int nthreads);
 
 /* Occupancy-based density regulariser (Eq. 12) at n normalised-space points x
  * [n][3] fp32 of poses pose_id [n]: L = weight / n * sum of sigma(x) over the

@@ -279,11 +279,57 @@ static void backward_sample(const or_model *m, const or_pose *poses, const fsamp
  * (fp32), pose_id [n], target [n][3].  Gradients are overwritten:
  * g_table [entries][F], g_mlp (packed), g_skin [rw^3][nb], g_bones [n_poses][nb][12]
  * (all NULL: loss only).  rgb_out [n][3], ray_flags [n] may be NULL. */
+/* Loss of ray r (Sec. 3.4) divided by the batch size n, and its gradients
+   g = dL/dC, *ga = dL/dalpha (alpha = 1 - the ray's final transmittance). */
+static double ray_loss(const or_loss *lc, int n, const double C[3], const double target[3], double alpha, int r,
+                       double g[3], double *ga) {
+  double e[3], ee = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    e[k] = C[k] - target[k];
+    ee += e[k] * e[k];
+  }
+  /* colour term (Eq. 9): L2 over channels, or Huber of the colour error's norm */
+  double lr;
+  if (!lc->huber) {
+    lr = ee;
+    for (int k = 0; k < 3; ++k) g[k] = 2.0 * e[k];
+  } else {
+    const double rn = sqrt(ee);
+    if (rn <= lc->delta) {
+      lr = 0.5 * ee;
+      for (int k = 0; k < 3; ++k) g[k] = e[k];
+    } else {
+      lr = lc->delta * (rn - 0.5 * lc->delta);
+      for (int k = 0; k < 3; ++k) g[k] = lc->delta * e[k] / rn;
+    }
+  }
+  for (int k = 0; k < 3; ++k) g[k] *= lc->w_rgb / (double)n;
+  /* opacity terms: L1 to the mask (Eq. 10), hard surface (Eq. 11) */
+  double la = 0.0, gal = 0.0;
+  if (lc->w_alpha != 0.0) {
+    const double da = alpha - lc->alpha_target[r];
+    la += lc->w_alpha * fabs(da);
+    gal += lc->w_alpha * (da > 0.0 ? 1.0 : (da < 0.0 ? -1.0 : 0.0));
+  }
+  if (lc->w_hard != 0.0) {
+    const double e0 = exp(-fabs(alpha)), e1 = exp(-fabs(alpha - 1.0));
+    la += lc->w_hard * (-log(e0 + e1) + log(1.0 + exp(-1.0)));
+    const double s0 = alpha > 0.0 ? 1.0 : (alpha < 0.0 ? -1.0 : 0.0);
+    const double s1 = alpha > 1.0 ? 1.0 : (alpha < 1.0 ? -1.0 : 0.0);
+    gal += lc->w_hard * (s0 * e0 + s1 * e1) / (e0 + e1);
+  }
+  *ga = gal / (double)n;
+  return (lc->w_rgb * lr + la) / (double)n;
+}
+
+/* up_rgb [n][3] / up_alpha [n] (optional): dL/dC and dL/dalpha given by the
+   caller instead of a loss (the loss returned is then 0); alpha_out [n] may be NULL. */
 static double train_impl(const or_model *m, const or_pose *poses, int n_poses, const uint32_t *occ, int n,
                          const float *o, const float *d, const int32_t *pose_id, const double *target,
                          double *rgb_out, int *ray_flags, double *g_table, double *g_mlp, double *g_skin,
                          double *g_bones, int nthreads, const or_prop *q, const double *theta_all,
-                         int *ray_fallbacks, const or_loss *lc) {
+                         int *ray_fallbacks, const or_loss *lc, const double *up_rgb, const double *up_alpha,
+                         double *alpha_out) {
   static const or_loss l2 = {0, 0.0, 1.0, 0.0, 0.0, NULL};
   if (!lc) lc = &l2;
   long entries = 0;
@@ -318,45 +364,19 @@ static double train_impl(const or_model *m, const or_pose *poses, int n_poses, c
   double loss = 0.0;
   for (int r = 0; r < n; ++r) {
     const double *C = Cs + 4 * r;
-    double g[3], e[3], ee = 0.0;
-    for (int k = 0; k < 3; ++k) {
-      e[k] = C[k] - target[3 * r + k];
-      ee += e[k] * e[k];
+    for (int k = 0; k < 3; ++k)
       if (rgb_out) rgb_out[3 * r + k] = C[k];
-    }
-    /* colour term (Eq. 9): L2 over channels, or Huber of the colour error's norm */
-    double lr;
-    if (!lc->huber) {
-      lr = ee;
-      for (int k = 0; k < 3; ++k) g[k] = 2.0 * e[k];
+    if (alpha_out) alpha_out[r] = 1.0 - Cs[4 * r + 3];
+    double g[3], ga;
+    if (up_rgb) {
+      /* the caller's dL/dC and dL/dalpha: no loss of ours */
+      for (int k = 0; k < 3; ++k) g[k] = up_rgb[3 * r + k];
+      ga = up_alpha ? up_alpha[r] : 0.0;
+    } else if (target) {
+      loss += ray_loss(lc, n, C, target + 3 * r, 1.0 - Cs[4 * r + 3], r, g, &ga);
     } else {
-      const double rn = sqrt(ee);
-      if (rn <= lc->delta) {
-        lr = 0.5 * ee;
-        for (int k = 0; k < 3; ++k) g[k] = e[k];
-      } else {
-        lr = lc->delta * (rn - 0.5 * lc->delta);
-        for (int k = 0; k < 3; ++k) g[k] = lc->delta * e[k] / rn;
-      }
+      continue; /* forward only */
     }
-    for (int k = 0; k < 3; ++k) g[k] *= lc->w_rgb / (double)n;
-    /* opacity terms of alpha = 1 - T: L1 to the mask (Eq. 10), hard surface (Eq. 11) */
-    const double alpha = 1.0 - Cs[4 * r + 3];
-    double la = 0.0, ga = 0.0;
-    if (lc->w_alpha != 0.0) {
-      const double da = alpha - lc->alpha_target[r];
-      la += lc->w_alpha * fabs(da);
-      ga += lc->w_alpha * (da > 0.0 ? 1.0 : (da < 0.0 ? -1.0 : 0.0));
-    }
-    if (lc->w_hard != 0.0) {
-      const double e0 = exp(-fabs(alpha)), e1 = exp(-fabs(alpha - 1.0));
-      la += lc->w_hard * (-log(e0 + e1) + log(1.0 + exp(-1.0)));
-      const double s0 = alpha > 0.0 ? 1.0 : (alpha < 0.0 ? -1.0 : 0.0);
-      const double s1 = alpha > 1.0 ? 1.0 : (alpha < 1.0 ? -1.0 : 0.0);
-      ga += lc->w_hard * (s0 * e0 + s1 * e1) / (e0 + e1);
-    }
-    ga /= (double)n;
-    loss += (lc->w_rgb * lr + la) / (double)n;
     const double TN = Cs[4 * r + 3];
     if (!g_table || !g_mlp || !g_skin || !g_bones) continue;
     /* compositing backward, front to back */
@@ -391,7 +411,7 @@ double or_train(const or_model *m, const or_pose *poses, int n_poses, const uint
                 double *rgb_out, int *ray_flags, double *g_table, double *g_mlp, double *g_skin,
                 double *g_bones, int nthreads) {
   return train_impl(m, poses, n_poses, occ, n, o, d, pose_id, target, rgb_out, ray_flags, g_table, g_mlp, g_skin,
-                    g_bones, nthreads, NULL, NULL, NULL, NULL);
+                    g_bones, nthreads, NULL, NULL, NULL, NULL, NULL, NULL, NULL);
 }
 
 /* The same step with the correspondence proposal choosing each sample's starts
@@ -404,7 +424,7 @@ double or_train_prop(const or_model *m, const or_pose *poses, int n_poses, const
                      double *g_bones, int nthreads, const or_prop *q, const double *theta_all,
                      int *ray_fallbacks) {
   return train_impl(m, poses, n_poses, occ, n, o, d, pose_id, target, rgb_out, ray_flags, g_table, g_mlp, g_skin,
-                    g_bones, nthreads, q, theta_all, ray_fallbacks, NULL);
+                    g_bones, nthreads, q, theta_all, ray_fallbacks, NULL, NULL, NULL, NULL);
 }
 
 /* or_train with the paper's loss set (config lc; alpha of a ray = 1 - its final
@@ -414,7 +434,19 @@ double or_train_loss(const or_model *m, const or_pose *poses, int n_poses, const
                      double *rgb_out, int *ray_flags, double *g_table, double *g_mlp, double *g_skin,
                      double *g_bones, int nthreads, const or_loss *lc) {
   return train_impl(m, poses, n_poses, occ, n, o, d, pose_id, target, rgb_out, ray_flags, g_table, g_mlp, g_skin,
-                    g_bones, nthreads, NULL, NULL, NULL, lc);
+                    g_bones, nthreads, NULL, NULL, NULL, lc, NULL, NULL, NULL);
+}
+
+/* The backward of the same forward for a loss computed elsewhere: the caller
+   gives dL/dC [n][3] and dL/dalpha [n] (NULL: zero) of every ray; the reverse
+   sweep and everything after it are those of or_train.  rgb_out, alpha_out
+   receive the forward's colour and alpha = 1 - final transmittance. */
+void or_train_upstream(const or_model *m, const or_pose *poses, int n_poses, const uint32_t *occ, int n,
+                       const float *o, const float *d, const int32_t *pose_id, const double *up_rgb,
+                       const double *up_alpha, double *rgb_out, double *alpha_out, int *ray_flags, double *g_table,
+                       double *g_mlp, double *g_skin, double *g_bones, int nthreads) {
+  train_impl(m, poses, n_poses, occ, n, o, d, pose_id, NULL, rgb_out, ray_flags, g_table, g_mlp, g_skin, g_bones,
+             nthreads, NULL, NULL, NULL, NULL, up_rgb, up_alpha, alpha_out);
 }
 
 double or_density_reg(const or_model *m, const or_pose *poses, int n_poses, const uint32_t *occ, int n,

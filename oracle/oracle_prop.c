@@ -214,31 +214,23 @@ double or_prop_loss_grad(const or_model *m, const or_prop *q, int n, const float
 /* f'(x') with the proposal: starts from the top_k proposed bones (the first
    shifted by the predicted offset); the plain search over all bones when they
    find no valid root.  *fallback = 1 when the plain search ran. */
-void or_posed_field_prop(const or_model *m, const or_pose *p, const or_prop *q, const double *theta,
-                         const double xn[3], or_sample *s, int *fallback) {
-  double out[OR_MAX_BONES + 3];
-  or_prop_forward(m, q, xn, theta, out);
-  int order[OR_MAX_BONES];
-  for (int i = 0; i < m->nb; ++i) order[i] = i;
-  /* stable selection of the largest logits (ties -> lower bone) */
-  for (int a = 0; a < m->nb; ++a)
-    for (int b = a + 1; b < m->nb; ++b)
-      if (out[order[b]] > out[order[a]]) { int t = order[a]; order[a] = order[b]; order[b] = t; }
-  int K = q->top_k < m->nb ? q->top_k : m->nb;
-  int flags = 0;
-  if (K < m->nb && out[order[K - 1]] - out[order[K]] < 0.05) flags |= OR_FLAG_PROP;
+/* The proposal-mode search from an ordered list of K proposed bones (the first
+   start shifted by the predicted offset), with the fallback to every bone-wise
+   start when none of them yields a valid root. */
+static void prop_search(const or_model *m, const or_pose *p, const int *bones, int K, const double offset[3],
+                        const double xn[3], or_sample *s, int *fallback) {
   double x0s[OR_MAX_STARTS * 3], roots[OR_MAX_STARTS * 3];
   int labels[OR_MAX_STARTS], starts[OR_MAX_STARTS];
   for (int j = 0; j < K; ++j) {
-    const int k = order[j];
+    const int k = bones[j];
     for (int a = 0; a < 3; ++a) {
       double v = p->Ninv[k][a * 4 + 3];
       for (int b = 0; b < 3; ++b) v += p->Ninv[k][a * 4 + b] * xn[b];
-      x0s[3 * j + a] = v + (j == 0 ? out[m->nb + a] : 0.0);
+      x0s[3 * j + a] = v + (j == 0 ? offset[a] : 0.0);
     }
     labels[j] = k;
   }
-  int its = 0, nc = 0;
+  int flags = 0, its = 0, nc = 0;
   int n = or_roots_from_starts(m, p, xn, K, x0s, labels, roots, starts, &flags, &its, &nc);
   *fallback = 0;
   if (n == 0) {
@@ -251,4 +243,54 @@ void or_posed_field_prop(const or_model *m, const or_pose *p, const or_prop *q, 
     return;
   }
   or_select_root(m, n, roots, starts, flags, its, nc, s);
+}
+
+/* the same selected sample: both without a root, or the same root */
+static int same_outcome(const or_sample *a, const or_sample *b) {
+  if ((a->start >= 0) != (b->start >= 0)) return 0;
+  if (a->start < 0) return 1;
+  const double d[3] = {a->xstar[0] - b->xstar[0], a->xstar[1] - b->xstar[1], a->xstar[2] - b->xstar[2]};
+  return d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < 1e-12;
+}
+
+/* f'(x') with the proposal choosing the starts: the top_k bones by logit (ties
+   to the lower bone), the first shifted by the predicted offset; every
+   bone-wise start when those find no valid root.  Two choices here are
+   discrete: which bones make the top k (the k-th against the next logit) and
+   which of them takes the offset (the first against the second).  Where a
+   choice is within 0.05 of going the other way -- a reduced-precision network
+   may take it differently -- the search is also run with the other choice,
+   and OR_FLAG_PROP is raised only if that changes the selected sample (root
+   or none) or whether the fallback ran. */
+void or_posed_field_prop(const or_model *m, const or_pose *p, const or_prop *q, const double *theta,
+                         const double xn[3], or_sample *s, int *fallback) {
+  double out[OR_MAX_BONES + 3];
+  or_prop_forward(m, q, xn, theta, out);
+  int order[OR_MAX_BONES];
+  for (int i = 0; i < m->nb; ++i) order[i] = i;
+  /* stable selection of the largest logits (ties -> lower bone) */
+  for (int a = 0; a < m->nb; ++a)
+    for (int b = a + 1; b < m->nb; ++b)
+      if (out[order[b]] > out[order[a]]) { int t = order[a]; order[a] = order[b]; order[b] = t; }
+  int K = q->top_k < m->nb ? q->top_k : m->nb;
+  const double *offset = out + m->nb;
+  prop_search(m, p, order, K, offset, xn, s, fallback);
+  int alt[2][OR_MAX_BONES], n_alt = 0;
+  if (K < m->nb && out[order[K - 1]] - out[order[K]] < 0.05) {
+    for (int j = 0; j < K; ++j) alt[n_alt][j] = order[j];
+    alt[n_alt][K - 1] = order[K];
+    n_alt++;
+  }
+  if (K >= 2 && out[order[0]] - out[order[1]] < 0.05) {
+    for (int j = 0; j < K; ++j) alt[n_alt][j] = order[j];
+    alt[n_alt][0] = order[1];
+    alt[n_alt][1] = order[0];
+    n_alt++;
+  }
+  for (int i = 0; i < n_alt; ++i) {
+    or_sample t;
+    int fb = 0;
+    prop_search(m, p, alt[i], K, offset, xn, &t, &fb);
+    if (fb != *fallback || !same_outcome(s, &t)) s->flags |= OR_FLAG_PROP;
+  }
 }

@@ -14,7 +14,7 @@ class Prop(C.Structure):
 
 
 def declare(L):
-    from . import Model, Pose, Sample
+    from . import Camera, Model, Pose, Sample
     P = C.POINTER
     PM, PQ = P(Model), P(Prop)
     sig = {
@@ -24,6 +24,9 @@ def declare(L):
         "or_prop_loss_grad": (C.c_double, [PM, PQ, C.c_int, P(C.c_float), P(C.c_int32), P(C.c_double),
                                            P(C.c_int32), P(C.c_double), P(C.c_double), P(C.c_double)]),
         "or_posed_field_prop": (None, [PM, P(Pose), PQ, P(C.c_double), P(C.c_double), P(Sample), P(C.c_int)]),
+        "or_render_pixels_prop": (None, [PM, P(Pose), PQ, P(C.c_double), P(Camera), P(C.c_uint32), C.c_int,
+                                         P(C.c_int32), P(C.c_double), P(C.c_double), P(C.c_int32), P(C.c_int32),
+                                         P(C.c_int32), C.c_int]),
         "or_train_prop": (C.c_double, [PM, P(Pose), C.c_int, P(C.c_uint32), C.c_int, P(C.c_float), P(C.c_float),
                                        P(C.c_int32), P(C.c_double), P(C.c_double), P(C.c_int32), P(C.c_double),
                                        P(C.c_double), P(C.c_double), P(C.c_double), C.c_int, PQ, P(C.c_double),
@@ -93,3 +96,19 @@ class PropModel:
                                       C.byref(s), C.byref(fb))
         return dict(sigma=s.sigma, rgb=np.array(s.rgb[:]), xstar=np.array(s.xstar[:]), start=s.start,
                     n_unique=s.n_unique, flags=s.flags, iters=s.iters, fallback=fb.value)
+
+    def render_pixels(self, pose, theta, cam, occ_bits, pix, nthreads=0):
+        """Proposal-mode render of the listed pixels: rgb, alpha, flags, samples
+        and fallbacks per ray (or_render_pixels_prop)."""
+        from . import _f64, _p
+        pix = np.ascontiguousarray(pix, dtype=np.int32)
+        n = len(pix)
+        rgb, alpha = np.zeros((n, 3)), np.zeros(n)
+        flags, nsamp, fb = (np.zeros(n, dtype=np.int32) for _ in range(3))
+        occ = np.ascontiguousarray(occ_bits, dtype=np.uint32)
+        c = self.om.camera(cam)
+        self.om.L.or_render_pixels_prop(C.byref(self.om.m), C.byref(pose), C.byref(self.q),
+                                        _p(_f64(theta).reshape(-1), C.c_double), C.byref(c), _p(occ, C.c_uint32), n,
+                                        _p(pix, C.c_int32), _p(rgb, C.c_double), _p(alpha, C.c_double),
+                                        _p(flags, C.c_int32), _p(nsamp, C.c_int32), _p(fb, C.c_int32), nthreads)
+        return dict(rgb=rgb, alpha=alpha, flags=flags, nsamp=nsamp, fallbacks=fb)

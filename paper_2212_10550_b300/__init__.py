@@ -68,6 +68,10 @@ class Loss(C.Structure):
                 ("w_hard", C.c_float)]
 
 
+class KernelTime(C.Structure):
+    _fields_ = [("name", C.c_char * 48), ("launches", C.c_int64), ("total_ms", C.c_double), ("max_ms", C.c_double)]
+
+
 class Grads(C.Structure):
     _fields_ = [("table", C.c_void_p), ("mlp", C.c_void_p), ("skin", C.c_void_p), ("bones", C.c_void_p)]
 
@@ -100,9 +104,13 @@ def lib():
             "ia_render": [P, I, C.POINTER(Camera), P, P, C.POINTER(RenderStats), V],
             "ia_march_mask": [P, I, C.POINTER(Camera), P, V],
             "ia_train_step": [P, C.POINTER(Batch), I, P, P, C.POINTER(Grads), V],
+            "ia_train_forward": [P, C.POINTER(Batch), I, P, P, P, P, V],
+            "ia_train_backward": [P, P, P, C.POINTER(Grads), V],
             "ia_update_occupancy_static": [P, I, P, V],
             "ia_update_occupancy_ema": [P, I, P, C.c_float, P, P, C.POINTER(RenderStats), V],
             "ia_loss_scale": [P, C.POINTER(C.c_float), C.POINTER(C.c_int32), V],
+            "ia_set_wait_limit": [P, C.c_int64],
+            "ia_set_fault_injection": [P, I],
             "ia_train_stats": [P, C.POINTER(RenderStats), V],
             "ia_grad_sizes": [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
             "ia_set_loss": [P, C.POINTER(Loss)],
@@ -117,6 +125,8 @@ def lib():
             "ia_proposal_train": [P, I, P, P, P, P, I, I, C.c_float, P, V],
             "ia_set_search": [P, I],
             "ia_set_occupancy_culling": [P, I],
+            "ia_profile_begin": [],
+            "ia_profile_end": [C.POINTER(KernelTime), I, C.POINTER(C.c_int)],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -127,6 +137,7 @@ def lib():
         L.ia_last_error.argtypes = [C.c_void_p]
         L.ia_last_error.restype = C.c_char_p
         L.ia_version.restype = C.c_char_p
+        L.ia_profile_error.restype = C.c_char_p
         _lib = L
     return _lib
 
@@ -287,10 +298,46 @@ def ia_train_step(ctx, origin, direction, pose, target, loss, grads, occ_grid=IA
                                _stream(stream)), ctx)
 
 
+def ia_train_forward(ctx, origin, direction, pose, rgb_out, alpha_out=None, table=None, mlp=None,
+                     occ_grid=IA_OCC_UNION, stream=None):
+    """Forward half of the training step: rgb_out [n][3] (and alpha_out [n]) of the batch's rays.
+    table / mlp: the field's parameters to use (device fp32; None = the context's own)."""
+    b = Batch()
+    b.n_rays = int(pose.shape[0])
+    b.origin, b.direction, b.pose = _ptr(origin), _ptr(direction), _ptr(pose)
+    _check(lib().ia_train_forward(ctx, C.byref(b), occ_grid, _ptr(table), _ptr(mlp), _ptr(rgb_out), _ptr(alpha_out),
+                                  _stream(stream)), ctx)
+
+
+def ia_train_backward(ctx, grad_rgb, grads, grad_alpha=None, stream=None):
+    """Backward half: gradients of the last forward from dL/drgb [n][3] (and dL/dalpha [n]) into grads."""
+    g = Grads()
+    g.table, g.mlp, g.skin, g.bones = (_ptr(grads[k]) for k in ("table", "mlp", "skin", "bones"))
+    _check(lib().ia_train_backward(ctx, _ptr(grad_rgb), _ptr(grad_alpha), C.byref(g), _stream(stream)), ctx)
+
+
 def ia_gather_probe(table, n_records, iters, blocks, sink, stream=None):
     """Random 48-byte record gathers (a measurement helper)."""
     _check(lib().ia_gather_probe(_ptr(table), int(n_records), int(iters), int(blocks), _ptr(sink), _stream(stream)),
            None)
+
+
+def ia_profile_begin():
+    """Open a launch profile on this thread (per-kernel CUDA-event times of every library launch)."""
+    st = lib().ia_profile_begin()
+    if st != IA_OK:
+        raise IAError(st, lib().ia_profile_error().decode())
+
+
+def ia_profile_end(max_kernels=64):
+    """Close the profile: {kernel name: (launches, total ms, max ms)} in order of first launch."""
+    out = (KernelTime * max_kernels)()
+    n = C.c_int()
+    st = lib().ia_profile_end(out, max_kernels, C.byref(n))
+    if st != IA_OK:
+        raise IAError(st, lib().ia_profile_error().decode())
+    return {out[i].name.decode(): (int(out[i].launches), float(out[i].total_ms), float(out[i].max_ms))
+            for i in range(min(n.value, max_kernels))}
 
 
 def ia_set_loss(ctx, rgb_loss=IA_LOSS_L2, huber_delta=0.0, w_rgb=1.0, w_alpha=0.0, w_hard=0.0):
@@ -320,8 +367,22 @@ def ia_train_stats(ctx, stream=None):
     return st.as_dict()
 
 
+def ia_set_wait_limit(ctx, limit_ns):
+    """Bound (ns) on each wait of the tensor-core weight-gradient pipeline; 0 = default (200 ms)."""
+    _check(lib().ia_set_wait_limit(ctx, int(limit_ns)), ctx)
+
+
+IA_INJECT_WITHHOLD_COPY = 1
+
+
+def ia_set_fault_injection(ctx, flags):
+    """Test-only failure injection (IA_INJECT_WITHHOLD_COPY: the weight-gradient pipeline withholds a copy)."""
+    _check(lib().ia_set_fault_injection(ctx, int(flags)), ctx)
+
+
 def ia_loss_scale(ctx, stream=None):
-    """(loss scale S after the last training step, whether that step was skipped on overflow)."""
+    """(loss scale S after the last training step, whether that step was skipped: overflow or
+    a weight-gradient pipeline that gave up, the latter also raising IAError(IA_ERR_CUDA))."""
     sc, sk = C.c_float(), C.c_int32()
     _check(lib().ia_loss_scale(ctx, C.byref(sc), C.byref(sk), _stream(stream)), ctx)
     return sc.value, bool(sk.value)

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/ia.h"
+#include "../../include/ia_measure.h"
 #include "ia_internal.h"
 
 using namespace ia;
@@ -97,10 +98,16 @@ struct ia_ctx {
   uint16_t* d_X = nullptr;          // fp16 / bf16 step: channel-major GEMM operands
   int64_t x_ld = 0;
   CUtensorMap x_map{};
-  float* d_scale = nullptr;         // loss scale, overflow flag, clean steps, GEMM wait flag
+  float* d_scale = nullptr;         // loss scale, the step's skip flags, clean steps
   int* d_overflow = nullptr;
   int* d_good = nullptr;
-  int* d_wg_err = nullptr;
+  uint64_t wait_ns = kDefaultWaitNs;  // bound on each wait of the tensor-core pipeline
+  // the last ia_train_forward, kept for its ia_train_backward
+  bool fwd_valid = false;
+  bool fwd_own_params = false;  // it read the context's own table / MLP
+  TrainArgs fwd{};
+  __half2* d_table_h_ext = nullptr;  // fp16 shadow of a caller table (reduced-precision forward)
+  int inject = 0;                     // ia_set_fault_injection flags
   // proposal network
   bool prop_ready = false;
   int search = IA_SEARCH_ALL_BONES;
@@ -434,8 +441,8 @@ void ia_destroy(ia_ctx* c) {
   dfree(c->d_X);
   dfree(c->d_scale);
   dfree(c->d_overflow);
+  dfree(c->d_table_h_ext);
   dfree(c->d_good);
-  dfree(c->d_wg_err);
   dfree(c->d_pp);
   dfree(c->d_ploss);
   dfree(c->d_pg);
@@ -493,6 +500,7 @@ ia_status ia_set_skeleton(ia_ctx* c, int n_bones, const int32_t* parent, const d
   c->sub_pose = -1;
   c->sub_all_valid = false;
   c->have_occ = false;
+  c->fwd_valid = false;
   return IA_OK;
 }
 
@@ -512,6 +520,7 @@ ia_status ia_set_params(ia_ctx* c, const float* table, const float* mlp, void* s
   IA_CUDA(c, cudaMemcpyAsync(c->d_table, table, sizeof(float) * nt, cudaMemcpyDefault, s), "ia_set_params");
   IA_CUDA(c, cudaMemcpyAsync(c->d_mlp, mlp, sizeof(float) * nm, cudaMemcpyDefault, s), "ia_set_params");
   if (c->d_table_h) IA_CUDA(c, launch_table_to_half(c->d_table, c->d_table_h, c->n_entries, s), "ia_set_params");
+  if (c->fwd_own_params) c->fwd_valid = false;
   if (c->d_fm) {  // new parameters: the Adam state restarts
     dfree(c->d_fm);
     dfree(c->d_fv);
@@ -564,6 +573,7 @@ ia_status ia_set_pose(ia_ctx* c, int n_poses, const double* axis_angle, const do
           "ia_set_pose: pose chain");
   c->sub_pose = -1;  // the culling masks belong to the previous grids
   c->sub_all_valid = false;
+  c->fwd_valid = false;
   IA_CUDA(c, launch_blend(n_poses, (int)V, c->nb, c->d_skin, c->d_N, c->d_M, s), "ia_set_pose: blend grid");
   c->n_poses = n_poses;
   return IA_OK;
@@ -757,23 +767,26 @@ ia_status ia_render(ia_ctx* c, int pose, const ia_camera* cam, float* rgb, float
   return IA_OK;
 }
 
-ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss, float* rgb_out,
-                        const ia_grads* g, void* stream) {
+namespace {
+
+// Checks and workspace shared by the training calls, and the arguments of their
+// kernels (parameters, poses, grid, batch and workspace; no gradient buffers).
+// need_target: the step computes its own loss from the batch's targets.
+ia_status train_prepare(ia_ctx* c, const ia_batch* b, int occ_grid, bool need_target, cudaStream_t s,
+                        TrainArgs& a) {
   ia_status st = need_ready(c, 0, false);
   if (st != IA_OK) return st;
-  if (!b || !loss || !g || !g->table || !g->mlp || !g->skin || !g->bones) return fail(c, IA_ERR_ARG, "null argument");
+  if (!b) return fail(c, IA_ERR_ARG, "null argument");
   if (b->n_rays < 1 || b->n_rays > (1 << 24)) return fail(c, IA_ERR_ARG, "n_rays must be 1..2^24");
-  if (!b->origin || !b->direction || !b->pose || !b->target) return fail(c, IA_ERR_ARG, "null batch array");
+  if (!b->origin || !b->direction || !b->pose || (need_target && !b->target))
+    return fail(c, IA_ERR_ARG, "null batch array");
   if (occ_grid != IA_OCC_POSE && occ_grid != IA_OCC_UNION) return fail(c, IA_ERR_ARG, "unknown occupancy grid");
   if (occ_grid == IA_OCC_POSE && !c->have_occ) return fail(c, IA_ERR_STATE, "no render grid (ia_update_occupancy)");
   if (b->n_reg < 0 || b->n_reg > (1 << 24)) return fail(c, IA_ERR_ARG, "n_reg must be 0..2^24");
   if (b->n_reg > 0 && (!b->reg_x || !b->reg_pose)) return fail(c, IA_ERR_ARG, "null regulariser array");
   if (b->n_reg > 0 && !(std::isfinite(b->reg_weight))) return fail(c, IA_ERR_ARG, "reg_weight must be finite");
-  if (c->loss.w_alpha != 0.f && !b->alpha_target)
+  if (need_target && c->loss.w_alpha != 0.f && !b->alpha_target)
     return fail(c, IA_ERR_ARG, "the loss has an alpha term: batch->alpha_target is needed");
-  if ((reinterpret_cast<uintptr_t>(g->table) & 7) != 0)
-    return fail(c, IA_ERR_ARG, "grads->table must be 8-byte aligned (one float pair per entry)");
-  cudaStream_t s = (cudaStream_t)stream;
   const int n = b->n_rays, N = c->cfg.max_samples;
   const size_t cap = (size_t)n * N + (size_t)b->n_reg;
   if (n > c->ray_cap || cap > c->s_cap) {
@@ -812,17 +825,12 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
     IA_CUDA(c, dalloc(&c->d_scale, (size_t)1), "ia_train_step: loss scale");
     IA_CUDA(c, dalloc(&c->d_overflow, (size_t)1), "ia_train_step: loss scale");
     IA_CUDA(c, dalloc(&c->d_good, (size_t)1), "ia_train_step: loss scale");
-    IA_CUDA(c, dalloc(&c->d_wg_err, (size_t)1), "ia_train_step: loss scale");
     const float s0 = c->cfg.precision == IA_FP16 ? kInitialLossScale : 1.f;
     IA_CUDA(c, cudaMemcpy(c->d_scale, &s0, sizeof(float), cudaMemcpyHostToDevice), "ia_train_step: loss scale");
     IA_CUDA(c, cudaMemset(c->d_good, 0, sizeof(int)), "ia_train_step: loss scale");
-    IA_CUDA(c, cudaMemset(c->d_wg_err, 0, sizeof(int)), "ia_train_step: loss scale");
   }
-  int64_t nt = 0, nm = 0;
-  ia_param_sizes(c, &nt, &nm);
   const size_t V = (size_t)c->Rw * c->Rw * c->Rw;
   IA_CUDA(c, cudaMemsetAsync(c->d_count, 0, sizeof(int), s), "ia_train_step");
-  if (c->d_overflow) IA_CUDA(c, cudaMemsetAsync(c->d_overflow, 0, sizeof(int), s), "ia_train_step");
   IA_CUDA(c, cudaMemsetAsync(c->d_tstats, 0, sizeof(unsigned long long) * ST_COUNT, s), "ia_train_step");
   IA_CUDA(c, cudaMemsetAsync(c->d_work + 1, 0, sizeof(unsigned), s), "ia_train_step");
   if (c->n_poses > c->pose_ws_cap) {
@@ -832,11 +840,7 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
     c->pose_ws_cap = c->n_poses;
   }
   IA_CUDA(c, cudaMemsetAsync(c->d_pose_ws, 0, sizeof(int) * 2 * c->n_poses, s), "ia_train_step");
-  IA_CUDA(c, cudaMemsetAsync(g->table, 0, sizeof(float) * nt, s), "ia_train_step");
-  IA_CUDA(c, cudaMemsetAsync(g->mlp, 0, sizeof(float) * nm, s), "ia_train_step");
-  IA_CUDA(c, cudaMemsetAsync(g->skin, 0, sizeof(float) * V * c->nb, s), "ia_train_step");
-  IA_CUDA(c, cudaMemsetAsync(g->bones, 0, sizeof(float) * c->n_poses * c->nb * 12, s), "ia_train_step");
-  TrainArgs a{};
+  a = TrainArgs{};
   a.P = posed_args(c, 0);
   a.V = (int)V;
   a.box = box_dev(c);
@@ -893,27 +897,16 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
   a.w_alpha = c->loss.w_alpha;
   a.w_hard = c->loss.w_hard;
   a.alpha_target = b->alpha_target;
-  a.skin_vec = (c->nb % 4 == 0 && (reinterpret_cast<uintptr_t>(g->skin) & 15) == 0 &&
-                (reinterpret_cast<uintptr_t>(c->d_skin) & 15) == 0) ? 1 : 0;
   a.act = c->d_act;
   a.act_ld = (int64_t)c->s_cap;
-  a.loss = loss;
-  a.rgb_out = rgb_out;
-  a.g_table = g->table;
-  a.g_mlp = g->mlp;
-  a.g_skin = g->skin;
-  a.g_bones = g->bones;
   a.prec = c->cfg.precision;
   a.X = c->d_X;
   a.ld = c->x_ld;
   a.scale = c->d_scale;
   a.overflow = c->d_overflow;
   a.good_steps = c->d_good;
-  a.err = c->d_wg_err;
-  a.n_table_f = (size_t)nt;
-  a.n_mlp_f = (size_t)nm;
-  a.n_skin_f = V * c->nb;
-  a.n_bones_f = (size_t)c->n_poses * c->nb * 12;
+  a.wait_ns = c->wait_ns;
+  a.inject = c->inject;
   a.theta_all = c->d_theta;
   a.stats = c->d_tstats;
   a.pose_tot = c->d_pose_ws;
@@ -927,7 +920,111 @@ ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss,
     }
     a.P.prop.b1p = c->d_pb1;
   }
+  return IA_OK;
+}
+
+// Gradient buffers of a backward: checked, zeroed (with the step's skip flags),
+// and entered into the kernel arguments.
+ia_status train_grads(ia_ctx* c, const ia_grads* g, cudaStream_t s, TrainArgs& a) {
+  if (!g || !g->table || !g->mlp || !g->skin || !g->bones) return fail(c, IA_ERR_ARG, "null gradient buffer");
+  if ((reinterpret_cast<uintptr_t>(g->table) & 7) != 0)
+    return fail(c, IA_ERR_ARG, "grads->table must be 8-byte aligned (one float pair per entry)");
+  int64_t nt = 0, nm = 0;
+  ia_param_sizes(c, &nt, &nm);
+  const size_t V = (size_t)c->Rw * c->Rw * c->Rw;
+  if (c->d_overflow) IA_CUDA(c, cudaMemsetAsync(c->d_overflow, 0, sizeof(int), s), "ia_train_step");
+  IA_CUDA(c, cudaMemsetAsync(g->table, 0, sizeof(float) * nt, s), "ia_train_step");
+  IA_CUDA(c, cudaMemsetAsync(g->mlp, 0, sizeof(float) * nm, s), "ia_train_step");
+  IA_CUDA(c, cudaMemsetAsync(g->skin, 0, sizeof(float) * V * c->nb, s), "ia_train_step");
+  IA_CUDA(c, cudaMemsetAsync(g->bones, 0, sizeof(float) * c->n_poses * c->nb * 12, s), "ia_train_step");
+  a.skin_vec = (c->nb % 4 == 0 && (reinterpret_cast<uintptr_t>(g->skin) & 15) == 0 &&
+                (reinterpret_cast<uintptr_t>(c->d_skin) & 15) == 0) ? 1 : 0;
+  a.g_table = g->table;
+  a.g_mlp = g->mlp;
+  a.g_skin = g->skin;
+  a.g_bones = g->bones;
+  a.n_table_f = (size_t)nt;
+  a.n_mlp_f = (size_t)nm;
+  a.n_skin_f = V * c->nb;
+  a.n_bones_f = (size_t)c->n_poses * c->nb * 12;
+  return IA_OK;
+}
+
+}  // namespace
+
+ia_status ia_train_step(ia_ctx* c, const ia_batch* b, int occ_grid, float* loss, float* rgb_out,
+                        const ia_grads* g, void* stream) {
+  if (!c) return fail(nullptr, IA_ERR_ARG, "null context");
+  if (!loss) return fail(c, IA_ERR_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  TrainArgs a;
+  ia_status st = train_prepare(c, b, occ_grid, true, s, a);
+  if (st != IA_OK) return st;
+  if ((st = train_grads(c, g, s, a)) != IA_OK) return st;
+  c->fwd_valid = false;  // the workspace is this step's now
+  a.comp_mode = kCompLoss;
+  a.loss = loss;
+  a.rgb_out = rgb_out;
   IA_CUDA(c, launch_train(a, &c->x_map, c->num_sms, s), "ia_train_step: kernels");
+  return IA_OK;
+}
+
+ia_status ia_train_forward(ia_ctx* c, const ia_batch* b, int occ_grid, const float* table, const float* mlp,
+                           float* rgb_out, float* alpha_out, void* stream) {
+  if (!c) return fail(nullptr, IA_ERR_ARG, "null context");
+  if (!rgb_out) return fail(c, IA_ERR_ARG, "null rgb_out");
+  if (b && b->n_reg != 0) return fail(c, IA_ERR_ARG, "the regulariser needs ia_train_step (n_reg must be 0)");
+  if ((table && !is_device_ptr(table)) || (mlp && !is_device_ptr(mlp)) || !is_device_ptr(rgb_out) ||
+      (alpha_out && !is_device_ptr(alpha_out)))
+    return fail(c, IA_ERR_ARG, "table, mlp, rgb_out and alpha_out must be device memory");
+  if (table && (reinterpret_cast<uintptr_t>(table) & 7) != 0)
+    return fail(c, IA_ERR_ARG, "table must be 8-byte aligned (one float pair per entry)");
+  cudaStream_t s = (cudaStream_t)stream;
+  TrainArgs a;
+  c->fwd_valid = false;
+  ia_status st = train_prepare(c, b, occ_grid, false, s, a);
+  if (st != IA_OK) return st;
+  if (table) {
+    a.P.F.table = reinterpret_cast<const float2*>(table);
+    if (c->cfg.precision != IA_FP32) {
+      if (!c->d_table_h_ext) IA_CUDA(c, dalloc(&c->d_table_h_ext, (size_t)c->n_entries), "ia_train_forward");
+      IA_CUDA(c, launch_table_to_half(table, c->d_table_h_ext, c->n_entries, s), "ia_train_forward");
+      a.P.table_h = c->d_table_h_ext;
+    }
+  }
+  if (mlp) a.P.mlp = mlp;
+  a.comp_mode = kCompForward;
+  a.rgb_out = rgb_out;
+  a.alpha_out = alpha_out;
+  IA_CUDA(c, launch_train_forward(a, c->num_sms, s), "ia_train_forward: kernels");
+  IA_CUDA(c, launch_train_composite(a, s), "ia_train_forward: compositing");
+  c->fwd = a;
+  c->fwd_valid = true;
+  c->fwd_own_params = !table || !mlp;
+  return IA_OK;
+}
+
+ia_status ia_train_backward(ia_ctx* c, const float* grad_rgb, const float* grad_alpha, const ia_grads* g,
+                            void* stream) {
+  if (!c) return fail(nullptr, IA_ERR_ARG, "null context");
+  if (!c->fwd_valid)
+    return fail(c, IA_ERR_STATE, "no ia_train_forward to differentiate (or its state changed since)");
+  if (!grad_rgb || !is_device_ptr(grad_rgb) || (grad_alpha && !is_device_ptr(grad_alpha)))
+    return fail(c, IA_ERR_ARG, "grad_rgb (and grad_alpha) must be device memory");
+  cudaStream_t s = (cudaStream_t)stream;
+  TrainArgs a = c->fwd;
+  ia_status st = train_grads(c, g, s, a);
+  if (st != IA_OK) return st;
+  a.comp_mode = kCompUpstream;
+  a.up_rgb = grad_rgb;
+  a.up_alpha = grad_alpha;
+  a.rgb_out = nullptr;
+  a.alpha_out = nullptr;
+  a.loss = nullptr;
+  a.wait_ns = c->wait_ns;
+  a.inject = c->inject;
+  IA_CUDA(c, launch_train_composite(a, s), "ia_train_backward: compositing");
+  IA_CUDA(c, launch_train_backward(a, &c->x_map, c->num_sms, s), "ia_train_backward: kernels");
   return IA_OK;
 }
 
@@ -951,8 +1048,9 @@ ia_status ia_adam_step(ia_ctx* c, const float* g_table, const float* g_mlp, cons
     c->field_step = 0;
   }
   ++c->field_step;
+  if (c->fwd_own_params) c->fwd_valid = false;
   // an overflowed reduced-precision step (zeroed gradients) leaves the state alone
-  const int* skip = c->cfg.precision == IA_FP16 ? c->d_overflow : nullptr;
+  const int* skip = c->cfg.precision != IA_FP32 ? c->d_overflow : nullptr;
   IA_CUDA(c, launch_adam(c->d_table, g_table, c->d_fm, c->d_fv, nt, lr, c->field_step, beta1, beta2, eps, skip, s),
           "ia_adam_step: table");
   IA_CUDA(c, launch_adam(c->d_mlp, g_mlp, c->d_fm + nt, c->d_fv + nt, nm, lr, c->field_step, beta1, beta2, eps, skip,
@@ -973,10 +1071,13 @@ ia_status ia_adam_step(ia_ctx* c, const float* g_table, const float* g_mlp, cons
     IA_CUDA(c, launch_adam(c->d_skin, g_skin, c->d_sm, c->d_sv, (int64_t)ns, lr, c->skin_step, beta1, beta2, eps, skip,
                            s),
             "ia_adam_step: skinning grid");
-    if (c->n_poses > 0)
-      c->sub_pose = -1;
-      c->sub_all_valid = false;
+    // every culling mask depends on the skinning grid; the blended grids exist only once poses are set
+    c->sub_pose = -1;
+    c->sub_all_valid = false;
+    c->fwd_valid = false;
+    if (c->n_poses > 0) {
       IA_CUDA(c, launch_blend(c->n_poses, (int)V, c->nb, c->d_skin, c->d_N, c->d_M, s), "ia_adam_step: blend grid");
+    }
   }
   return IA_OK;
 }
@@ -1010,10 +1111,39 @@ ia_status ia_grad_sizes(const ia_ctx* c, int64_t* skin_floats, int64_t* bone_flo
   return IA_OK;
 }
 
+// IA_ERR_CUDA if the last reduced-precision step gave up waiting on its
+// tensor-core pipeline (the step was skipped); waits on the stream
+static ia_status pipeline_status(ia_ctx* c, cudaStream_t s, int* flags_out) {
+  int flags = 0;
+  if (c->d_overflow) {
+    IA_CUDA(c, cudaMemcpyAsync(&flags, c->d_overflow, sizeof(int), cudaMemcpyDeviceToHost, s), "step flags");
+    IA_CUDA(c, cudaStreamSynchronize(s), "step flags");
+  }
+  if (flags_out) *flags_out = flags;
+  if (flags & kStepPipelineError)
+    return fail(c, IA_ERR_CUDA,
+                "the tensor-core weight-gradient reduction gave up waiting on its pipeline (the step was skipped)");
+  return IA_OK;
+}
+
 ia_status ia_train_stats(ia_ctx* c, ia_render_stats* stats, void* stream) {
   if (!c || !stats) return fail(c, IA_ERR_ARG, "null argument");
   read_stats(c, stats, (cudaStream_t)stream, c->d_tstats);
   stats->early_stopped = 0;
+  return pipeline_status(c, (cudaStream_t)stream, nullptr);
+}
+
+ia_status ia_set_wait_limit(ia_ctx* c, int64_t limit_ns) {
+  if (!c) return fail(nullptr, IA_ERR_ARG, "null context");
+  if (limit_ns < 0 || limit_ns > (int64_t)10000000000LL) return fail(c, IA_ERR_ARG, "limit_ns must be 0..1e10");
+  c->wait_ns = limit_ns == 0 ? kDefaultWaitNs : (uint64_t)limit_ns;
+  return IA_OK;
+}
+
+ia_status ia_set_fault_injection(ia_ctx* c, int flags) {
+  if (!c) return fail(nullptr, IA_ERR_ARG, "null context");
+  if (flags & ~IA_INJECT_WITHHOLD_COPY) return fail(c, IA_ERR_ARG, "unknown injection flag");
+  c->inject = flags;
   return IA_OK;
 }
 
@@ -1026,13 +1156,11 @@ ia_status ia_loss_scale(ia_ctx* c, float* scale, int32_t* skipped, void* stream)
     return IA_OK;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  int err = 0, ovf = 0;
-  IA_CUDA(c, cudaMemcpyAsync(&err, c->d_wg_err, sizeof(int), cudaMemcpyDeviceToHost, s), "ia_loss_scale");
-  IA_CUDA(c, cudaMemcpyAsync(&ovf, c->d_overflow, sizeof(int), cudaMemcpyDeviceToHost, s), "ia_loss_scale");
   if (scale) IA_CUDA(c, cudaMemcpyAsync(scale, c->d_scale, sizeof(float), cudaMemcpyDeviceToHost, s), "ia_loss_scale");
-  IA_CUDA(c, cudaStreamSynchronize(s), "ia_loss_scale");
-  if (skipped) *skipped = ovf;
-  if (err) return fail(c, IA_ERR_CUDA, "the tensor-core weight-gradient reduction timed out waiting on its pipeline");
+  int flags = 0;
+  const ia_status st = pipeline_status(c, s, &flags);
+  if (skipped) *skipped = flags != 0 ? 1 : 0;
+  if (st != IA_OK) return st;
   return IA_OK;
 }
 

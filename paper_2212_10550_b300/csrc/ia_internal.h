@@ -7,6 +7,7 @@
 #include "ia_device.cuh"
 #include "ia_index.cuh"
 #include "ia_posed.cuh"
+#include "ia_profile.h"
 #include "ia_wgrad.h"
 
 namespace ia {
@@ -115,6 +116,10 @@ struct TrainArgs {
   int64_t act_ld;
   float* loss;           // device scalar (accumulated)
   float* rgb_out;        // [n][3] or null
+  float* alpha_out;      // [n] or null: alpha = 1 - final transmittance
+  int comp_mode;         // kCompLoss, kCompForward or kCompUpstream (train_composite_kernel)
+  const float* up_rgb;   // [n][3] dL/dC from the caller (kCompUpstream)
+  const float* up_alpha; // [n] dL/dalpha from the caller, or null (kCompUpstream)
   float* g_table;
   float* g_mlp;
   float* g_skin;
@@ -124,9 +129,10 @@ struct TrainArgs {
   uint16_t* X;           // [kWgRows][ld] fp16 / bf16
   int64_t ld;            // multiple of 64
   float* scale;          // dynamic loss scale (device scalar)
-  int* overflow;         // set when a scaled gradient left the fp16 range
+  int* overflow;         // the step's skip flags (kStepOverflow, kStepPipelineError)
   int* good_steps;       // steps since the last overflow
-  int* err;              // tensor-core pipeline wait expired
+  uint64_t wait_ns;      // bound on each wait of the tensor-core pipeline
+  int inject;            // ia_set_fault_injection flags
   size_t n_table_f, n_mlp_f, n_skin_f, n_bones_f;  // gradient sizes (floats)
   const double* theta_all;  // [n_poses][nb][3] (proposal search: per-pose layer-1 bias)
   unsigned long long* stats;  // [ST_COUNT] counters of this step
@@ -150,6 +156,12 @@ struct TrainArgs {
 // b1p[pose][j] = b1[j] + W1[j, pose columns] . theta_pose for every pose
 cudaError_t launch_prop_bias(const PropDev& Q, int nb, const double* theta_all, int n_poses, float* b1p,
                              cudaStream_t s);
+
+// Names of the precision / search variants of a kernel, for launch tracing
+template <Prec P>
+constexpr const char* variant_name(const char* f32, const char* f16, const char* bf16) {
+  return P == Prec::F32 ? f32 : (P == Prec::F16 ? f16 : bf16);
+}
 
 // Opt a kernel into `smem` bytes of dynamic shared memory and ask for the
 // smallest shared-memory carveout that still fits as many blocks per SM as its
@@ -175,8 +187,22 @@ cudaError_t set_smem(Kern k, size_t smem, int threads) {
 }
 
 constexpr float kInitialLossScale = 16384.f;  // 2^14
+// default bound on each wait of the tensor-core pipeline: the whole reduction
+// takes well under a millisecond, so a wait this long means it is stuck
+constexpr uint64_t kDefaultWaitNs = 200000000ull;  // 200 ms
 
+// Where the compositing kernel takes dL/dC and dL/dalpha from
+constexpr int kCompLoss = 0;      // the step's own loss (ia_train_step)
+constexpr int kCompForward = 1;   // none: colour and alpha only (ia_train_forward)
+constexpr int kCompUpstream = 2;  // the caller's per-ray gradients (ia_train_backward)
+
+// The whole step: forward, compositing (a.comp_mode), backward.
 cudaError_t launch_train(const TrainArgs& a, const CUtensorMap* map, int num_sms, cudaStream_t s);
+// Its parts: march + posed field of every sample; compositing (and the
+// regulariser's density gradient with kCompLoss); the backward from s_grad.
+cudaError_t launch_train_forward(const TrainArgs& a, int num_sms, cudaStream_t s);
+cudaError_t launch_train_composite(const TrainArgs& a, cudaStream_t s);
+cudaError_t launch_train_backward(const TrainArgs& a, const CUtensorMap* map, int num_sms, cudaStream_t s);
 
 // Proposal network (ia_prop.cu).
 constexpr int kPropMaxIn = 2 * 8 + 3 * kMaxBones;  // 8 levels x 2 features + 32 bones x 3

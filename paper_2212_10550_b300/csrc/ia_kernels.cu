@@ -30,6 +30,31 @@ __device__ __forceinline__ double DM(double a, double b) { return __dmul_rn(a, b
 __device__ __forceinline__ double DA(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double DS(double a, double b) { return __dsub_rn(a, b); }
 
+// cos a and sin a of a joint's rotation angle, from their Maclaurin series:
+// a is reduced once by the nearest multiple of 2 pi (an fp64 constant), then
+// the terms t_{k+1} = t_k (-x^2) / ((2k+2)(2k+3)) (sin, from t_0 = x) and
+// t_k (-x^2) / ((2k+1)(2k+2)) (cos, from t_0 = 1) are formed and added in
+// order, 22 of them (the first omitted one is below pi^46 / 46! < 1e-32).
+// Each step is one correctly rounded fp64 operation in a fixed order, so the
+// values -- and the fp32 transforms made from them -- are reproducible on any
+// IEEE machine, which a library cos / sin (accurate to an ulp or two, by
+// machine-specific methods) is not.
+__device__ __forceinline__ void cos_sin_series(double a, double& c, double& s) {
+  const double two_pi = 6.283185307179586;
+  const double x = DS(a, DM(rint(__ddiv_rn(a, two_pi)), two_pi));
+  const double mx2 = -DM(x, x);
+  double ts = x, tc = 1.0, sn = x, cs = 1.0;
+#pragma unroll 1
+  for (int k = 0; k < 22; ++k) {
+    ts = __ddiv_rn(DM(ts, mx2), (double)((2 * k + 2) * (2 * k + 3)));
+    tc = __ddiv_rn(DM(tc, mx2), (double)((2 * k + 1) * (2 * k + 2)));
+    sn = DA(sn, ts);
+    cs = DA(cs, tc);
+  }
+  c = cs;
+  s = sn;
+}
+
 // One block per pose, twelve threads per joint, thread (k, e) owning element e
 // of joint k's 3 x 4 matrices.  The chain is composed level by level down the
 // tree, G_k = G_p(k) L_k, which is the same left-to-right product
@@ -74,7 +99,8 @@ __global__ void pose_chain_kernel(int P, int nb, const int* __restrict__ parent,
     if (a == 0.0) {
       sRod[k][0] = 1.0;  // identity rotation
     } else {
-      const double c = cos(a), sn = sin(a);
+      double c, sn;
+      cos_sin_series(a, c, sn);
       sRod[k][0] = c;
       sRod[k][1] = sn;
       sRod[k][2] = DS(1.0, c);
@@ -150,7 +176,10 @@ __global__ void pose_chain_kernel(int P, int nb, const int* __restrict__ parent,
 
 cudaError_t launch_pose_chain(int P, int nb, const int* parent, const double* rest, const double* theta,
                               const double* trans, float* N, float* Ninv, float* B0inv, cudaStream_t s) {
-  pose_chain_kernel<<<P, (nb * 12 + 31) / 32 * 32, 0, s>>>(P, nb, parent, rest, theta, trans, N, Ninv, B0inv);
+  {
+    KernelSpan span("pose_chain_kernel", s);
+    pose_chain_kernel<<<P, (nb * 12 + 31) / 32 * 32, 0, s>>>(P, nb, parent, rest, theta, trans, N, Ninv, B0inv);
+  }
   return cudaGetLastError();
 }
 
@@ -184,7 +213,10 @@ __global__ void blend_kernel(int V, int nb, const float* __restrict__ W, const f
 cudaError_t launch_blend(int P, int V, int nb, const float* W, const float* N, float4* M, cudaStream_t s) {
   dim3 grid((V + 255) / 256, P);
   if (grid.x > 4096) grid.x = 4096;
-  blend_kernel<<<grid, 256, 0, s>>>(V, nb, W, N, M);
+  {
+    KernelSpan span("blend_kernel", s);
+    blend_kernel<<<grid, 256, 0, s>>>(V, nb, W, N, M);
+  }
   return cudaGetLastError();
 }
 
@@ -252,6 +284,13 @@ __global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS)
 }
 
 template <Prec P, bool kProp>
+constexpr const char* occ_density_name() {
+  return kProp ? variant_name<P>("occ_density_kernel<fp32,proposal>", "occ_density_kernel<fp16,proposal>",
+                                 "occ_density_kernel<bf16,proposal>")
+               : variant_name<P>("occ_density_kernel<fp32>", "occ_density_kernel<fp16>", "occ_density_kernel<bf16>");
+}
+
+template <Prec P, bool kProp>
 static cudaError_t launch_occ_density_k(const PosedArgs& a, const BoxDev& box, const float* jitter, const int* cells,
                                         const unsigned* count, float* sigma, unsigned long long* stats,
                                         unsigned* work, int num_sms, cudaStream_t s) {
@@ -266,7 +305,10 @@ static cudaError_t launch_occ_density_k(const PosedArgs& a, const BoxDev& box, c
   int blocks = num_sms * (per_sm < 1 ? 1 : per_sm);
   if (blocks > (lists + 7) / 8) blocks = (lists + 7) / 8;
   if ((e = cudaMemsetAsync(work, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
-  occ_density_kernel<P, kProp><<<blocks, 256, smem, s>>>(a, box, jitter, cells, count, sigma, stats, work);
+  {
+    KernelSpan span(occ_density_name<P, kProp>(), s);
+    occ_density_kernel<P, kProp><<<blocks, 256, smem, s>>>(a, box, jitter, cells, count, sigma, stats, work);
+  }
   return cudaGetLastError();
 }
 
@@ -514,7 +556,10 @@ cudaError_t launch_occ_cover(const SkinDev& S, int V, int n_poses, const SolveCf
   const float slack = std::sqrt(cfg.tol2) + 1e-4f * L;
   const int nc = S.Rw - 1;
   const int blocks = ((nc + 7) / 8) * ((nc + 7) / 8) * ((nc + 3) / 4);
-  occ_cover_kernel<<<dim3(blocks, n_poses), 256, 0, s>>>(S, V, box, slack, sub, cen);
+  {
+    KernelSpan span("occ_cover_kernel", s);
+    occ_cover_kernel<<<dim3(blocks, n_poses), 256, 0, s>>>(S, V, box, slack, sub, cen);
+  }
   return cudaGetLastError();
 }
 
@@ -529,7 +574,10 @@ cudaError_t launch_occ_cull(const PosedArgs& a, const BoxDev& box, const float* 
   if (e != cudaSuccess) return e;
   unsigned* c = jitter ? nullptr : cen;
   if ((e = launch_occ_cover(a.S, a.S.Rw * a.S.Rw * a.S.Rw, 1, a.cfg, box, sub, c, s)) != cudaSuccess) return e;
-  occ_cand_kernel<<<(n + 255) / 256, 256, 0, s>>>(box, jitter, sub, c, cells, count, sigma, stats);
+  {
+    KernelSpan span("occ_cand_kernel", s);
+    occ_cand_kernel<<<(n + 255) / 256, 256, 0, s>>>(box, jitter, sub, c, cells, count, sigma, stats);
+  }
   return cudaGetLastError();
 }
 
@@ -541,7 +589,10 @@ __global__ void occ_ema_kernel(const float* __restrict__ sigma, float* __restric
 }
 
 cudaError_t launch_occ_ema(const float* sigma, float* d, int n, float decay, cudaStream_t s) {
-  occ_ema_kernel<<<(n + 255) / 256, 256, 0, s>>>(sigma, d, n, decay);
+  {
+    KernelSpan span("occ_ema_kernel", s);
+    occ_ema_kernel<<<(n + 255) / 256, 256, 0, s>>>(sigma, d, n, decay);
+  }
   return cudaGetLastError();
 }
 
@@ -579,7 +630,10 @@ __global__ void occ_bits_kernel(const float* __restrict__ sigma, int R, int dila
 cudaError_t launch_occ_bits(const float* sigma, int R, int dilate, float tau, uint32_t* bits, uint32_t* union_bits,
                             cudaStream_t s) {
   const int n = R * R * R;
-  occ_bits_kernel<<<(n + 255) / 256, 256, 0, s>>>(sigma, R, dilate, tau, bits, union_bits);
+  {
+    KernelSpan span("occ_bits_kernel", s);
+    occ_bits_kernel<<<(n + 255) / 256, 256, 0, s>>>(sigma, R, dilate, tau, bits, union_bits);
+  }
   return cudaGetLastError();
 }
 
@@ -623,7 +677,10 @@ static cudaError_t launch_query_posed_p(const PosedArgs& a, int n, const float* 
   const size_t smem = posed_smem_bytes_p<P>(256, a.search != 0);
   cudaError_t e = set_smem(query_posed_kernel<P>, smem, 256);
   if (e != cudaSuccess) return e;
-  query_posed_kernel<P><<<(n + 8 * kList - 1) / (8 * kList), 256, smem, s>>>(a, n, x, sigma, rgb, xc, start);
+  {
+    KernelSpan span("query_posed_kernel", s);
+    query_posed_kernel<P><<<(n + 8 * kList - 1) / (8 * kList), 256, smem, s>>>(a, n, x, sigma, rgb, xc, start);
+  }
   return cudaGetLastError();
 }
 
@@ -666,7 +723,10 @@ static cudaError_t launch_query_canonical_p(const PosedArgs& a, int n, const flo
   const size_t smem = posed_smem_bytes_p<P>(256, a.search != 0);
   cudaError_t e = set_smem(query_canonical_kernel<P>, smem, 256);
   if (e != cudaSuccess) return e;
-  query_canonical_kernel<P><<<(n + 255) / 256, 256, smem, s>>>(a, n, x, sigma, rgb);
+  {
+    KernelSpan span("query_canonical_kernel", s);
+    query_canonical_kernel<P><<<(n + 255) / 256, 256, smem, s>>>(a, n, x, sigma, rgb);
+  }
   return cudaGetLastError();
 }
 
@@ -883,6 +943,12 @@ __global__ void __launch_bounds__(kRenderThreads, IA_RENDER_MIN_BLOCKS) render_k
   }
 }
 
+template <Prec P, bool kProp>
+constexpr const char* render_name() {
+  return kProp ? variant_name<P>("render_kernel<fp32,proposal>", "render_kernel<fp16,proposal>", "render_kernel<bf16,proposal>")
+               : variant_name<P>("render_kernel<fp32>", "render_kernel<fp16>", "render_kernel<bf16>");
+}
+
 template <int K, Prec P, bool kProp>
 static cudaError_t launch_render_k(const RenderArgs& a, int num_sms, cudaStream_t s) {
   const size_t smem = render_smem_bytes_p<P>(K, kProp);
@@ -896,7 +962,10 @@ static cudaError_t launch_render_k(const RenderArgs& a, int num_sms, cudaStream_
   int grid = num_sms * per_sm;
   if (grid > want) grid = want;
   if (grid < 1) grid = 1;
-  render_kernel<K, P, kProp><<<grid, kRenderThreads, smem, s>>>(a);
+  {
+    KernelSpan span(render_name<P, kProp>(), s);
+    render_kernel<K, P, kProp><<<grid, kRenderThreads, smem, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -937,7 +1006,10 @@ __global__ void table_to_half_kernel(const float2* __restrict__ t, __half2* __re
 }
 
 cudaError_t launch_table_to_half(const float* table, __half2* th, int64_t entries, cudaStream_t s) {
-  table_to_half_kernel<<<1184, 256, 0, s>>>(reinterpret_cast<const float2*>(table), th, entries);
+  {
+    KernelSpan span("table_to_half_kernel", s);
+    table_to_half_kernel<<<1184, 256, 0, s>>>(reinterpret_cast<const float2*>(table), th, entries);
+  }
   return cudaGetLastError();
 }
 
@@ -960,7 +1032,10 @@ __global__ void march_mask_kernel(const RenderArgs a, uint32_t* __restrict__ mas
 
 cudaError_t launch_march_mask(const RenderArgs& a, uint32_t* mask, cudaStream_t s) {
   const int n = a.cam.width * a.cam.height;
-  march_mask_kernel<<<(n + 127) / 128, 128, 0, s>>>(a, mask);
+  {
+    KernelSpan span("march_mask_kernel", s);
+    march_mask_kernel<<<(n + 127) / 128, 128, 0, s>>>(a, mask);
+  }
   return cudaGetLastError();
 }
 
@@ -988,7 +1063,10 @@ __global__ void gather_probe_kernel(const float4* __restrict__ table, unsigned n
 
 cudaError_t launch_gather_probe(const float4* table, int64_t n_records, int iters, int blocks, float* sink,
                                 cudaStream_t s) {
-  gather_probe_kernel<<<blocks, 256, 0, s>>>(table, (unsigned)n_records, iters, sink);
+  {
+    KernelSpan span("gather_probe_kernel", s);
+    gather_probe_kernel<<<blocks, 256, 0, s>>>(table, (unsigned)n_records, iters, sink);
+  }
   return cudaGetLastError();
 }
 

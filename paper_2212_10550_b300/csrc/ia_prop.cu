@@ -62,7 +62,10 @@ __global__ void prop_label_kernel(const PropLabelArgs a) {
 }
 
 cudaError_t launch_prop_label(const PropLabelArgs& a, cudaStream_t s) {
-  prop_label_kernel<<<(a.n + 127) / 128, 128, 0, s>>>(a);
+  {
+    KernelSpan span("prop_label_kernel", s);
+    prop_label_kernel<<<(a.n + 127) / 128, 128, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -251,9 +254,15 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
 cudaError_t launch_prop_grad(const PropTrainArgs& a, cudaStream_t s) {
   cudaError_t e;
   const int blocks = (a.batch + 127) / 128;
-  prop_fwd_kernel<<<blocks, 128, 0, s>>>(a);
+  {
+    KernelSpan span("prop_fwd_kernel", s);
+    prop_fwd_kernel<<<blocks, 128, 0, s>>>(a);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  prop_bwd_kernel<<<blocks, 128, 0, s>>>(a);
+  {
+    KernelSpan span("prop_bwd_kernel", s);
+    prop_bwd_kernel<<<blocks, 128, 0, s>>>(a);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int nin = a.Q.n_in, nout = a.nb + 3;
   float* gW1 = a.g_mlp;
@@ -265,10 +274,22 @@ cudaError_t launch_prop_grad(const PropTrainArgs& a, cudaStream_t s) {
   float* gW4 = gb3 + kWidth;
   float* gb4 = gW4 + nout * kWidth;
   const int g = max(1, min(296, (a.batch + 63) / 64));
-  dense_grad_kernel<<<g, 256, 0, s>>>(a.rows, a.batch, kPX, nin, kPd1, kWidth, gW1, gb1);
-  dense_grad_kernel<<<g, 256, 0, s>>>(a.rows, a.batch, kPH1, kWidth, kPd2, kWidth, gW2, gb2);
-  dense_grad_kernel<<<g, 256, 0, s>>>(a.rows, a.batch, kPH2, kWidth, kPd3, kWidth, gW3, gb3);
-  dense_grad_kernel<<<g, 256, 0, s>>>(a.rows, a.batch, kPH3, kWidth, kPdO, nout, gW4, gb4);
+  {
+    KernelSpan span("dense_grad_kernel", s);
+    dense_grad_kernel<<<g, 256, 0, s>>>(a.rows, a.batch, kPX, nin, kPd1, kWidth, gW1, gb1);
+  }
+  {
+    KernelSpan span("dense_grad_kernel", s);
+    dense_grad_kernel<<<g, 256, 0, s>>>(a.rows, a.batch, kPH1, kWidth, kPd2, kWidth, gW2, gb2);
+  }
+  {
+    KernelSpan span("dense_grad_kernel", s);
+    dense_grad_kernel<<<g, 256, 0, s>>>(a.rows, a.batch, kPH2, kWidth, kPd3, kWidth, gW3, gb3);
+  }
+  {
+    KernelSpan span("dense_grad_kernel", s);
+    dense_grad_kernel<<<g, 256, 0, s>>>(a.rows, a.batch, kPH3, kWidth, kPdO, nout, gW4, gb4);
+  }
   return cudaGetLastError();
 }
 
@@ -276,7 +297,10 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n,
                         float b2, float eps, const int* skip, cudaStream_t s) {
   // bias corrections of step t (1-based): 1 / (1 - b^t)
   const float c1 = 1.f / (1.f - powf(b1, (float)step)), c2 = 1.f / (1.f - powf(b2, (float)step));
-  adam_kernel<<<592, 256, 0, s>>>(p, g, m, v, n, lr, c1, c2, b1, b2, eps, skip);
+  {
+    KernelSpan span("adam_kernel", s);
+    adam_kernel<<<592, 256, 0, s>>>(p, g, m, v, n, lr, c1, c2, b1, b2, eps, skip);
+  }
   return cudaGetLastError();
 }
 
@@ -298,7 +322,10 @@ __global__ void prop_bias_kernel(const PropDev Q, int nb, const double* __restri
 cudaError_t launch_prop_bias(const PropDev& Q, int nb, const double* theta_all, int n_poses, float* b1p,
                              cudaStream_t s) {
   const int n = n_poses * kWidth;
-  prop_bias_kernel<<<(n + 255) / 256, 256, 0, s>>>(Q, nb, theta_all, n_poses, b1p);
+  {
+    KernelSpan span("prop_bias_kernel", s);
+    prop_bias_kernel<<<(n + 255) / 256, 256, 0, s>>>(Q, nb, theta_all, n_poses, b1p);
+  }
   return cudaGetLastError();
 }
 

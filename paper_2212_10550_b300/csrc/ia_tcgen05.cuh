@@ -16,29 +16,49 @@
 //   GEMM 2: D2 [128 x 16]  = X[240:368] X[368:384]^T -> dW3^T (rows 0..63, cols 0..3),
 //           db3 (row 64, cols 0..3)
 //
-// Each CTA reduces a contiguous range of 64-sample chunks: one thread issues the
-// TMA loads (16-row boxes, 128-byte swizzle) into a two-stage ring and the MMAs
-// (M = 128, K = 16 per instruction, fp32 accumulation in 128 TMEM columns);
-// the four warps then read the accumulators with tcgen05.ld, unscale and add
-// them to the fp32 gradients.  Every mbarrier wait is bounded: on expiry the
-// kernel records an error, stops issuing, and still frees its TMEM.
+// Each CTA reduces a contiguous range of 64-sample chunks (48 KiB each).  The
+// work is split by role: lane 0 of warp 0 streams the chunks with TMA (three
+// 128-row boxes per chunk, 128-byte swizzle) into a four-stage ring, lane 0 of
+// warp 1 waits for each stage, issues its MMAs (M = 128, K = 16 per
+// instruction, fp32 accumulation in 128 TMEM columns) and commits them to the
+// stage's "empty" barrier, which hands the stage back to the producer; so up
+// to four chunks are in flight per SM while the tensor cores consume the
+// oldest.  After the last commit all four warps read the accumulators with
+// tcgen05.ld, unscale them and add them to the fp32 gradients.
+//
+// Every mbarrier wait is bounded in time (WgradArgs::wait_ns, from the
+// global nanosecond timer).  When a wait expires, or the other role gave up,
+// the thread stops issuing and raises kStepPipelineError in the step's flags
+// (the step is then skipped: its gradients are zeroed and the host call
+// reports the error).  Before the CTA frees its TMEM and exits it waits, again
+// with a bound, for what it already put in flight: the producer for each TMA
+// load it issued, the MMA thread for a final commit that tracks every MMA it
+// issued.
 #pragma once
 
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 
+#include "ia_profile.h"
 #include "ia_wgrad.h"
 
 namespace ia {
 
-constexpr int kWgStageBytes = kWgRows * kWgChunk * 2; // 48 KiB
-constexpr int kWgStages = 2;
+constexpr int kWgStageBytes = kWgRows * kWgChunk * 2;  // 48 KiB
+constexpr int kWgStages = 4;
 constexpr int kWgThreads = 128;
-constexpr uint32_t kWgSpinLimit = 1u << 26;
+constexpr int kWgBoxRows = 128;                         // rows per TMA box
+constexpr uint64_t kWgDrainNs = 1000000000ull;          // 1 s bound on waiting for work in flight
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -50,19 +70,31 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 
-// bounded wait for the phase with the given parity; false when the limit expired
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Wait for the phase of `bar` with the given parity.  False when it has not
+// completed within limit_ns, or when *abort (if given) was raised meanwhile.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns,
+                                          const volatile int* abort) {
   const uint32_t a = smem_u32(bar);
-  for (uint32_t i = 0; i < kWgSpinLimit; ++i) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
+  uint64_t t0 = 0;
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_try(a, parity)) return true;
+    if ((i & 31) == 0) {
+      const uint64_t t = global_ns();
+      if (i == 0) t0 = t;
+      else if (t - t0 > limit_ns) return false;
+      if (abort && *abort) return false;
+    }
   }
-  return false;
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
@@ -101,6 +133,7 @@ __device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64
       : "memory");
 }
 
+// arrives on `bar` once every tcgen05 operation this thread issued before it has completed
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
                : "memory");
@@ -118,20 +151,34 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, float v[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// four consecutive gradient entries: one vector atomic where the address allows it
+__device__ __forceinline__ void add4(float* p, float a, float b, float c, float d) {
+  if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+    atomicAdd(reinterpret_cast<float4*>(p), make_float4(a, b, c, d));
+  } else {
+    atomicAdd(p, a);
+    atomicAdd(p + 1, b);
+    atomicAdd(p + 2, c);
+    atomicAdd(p + 3, d);
+  }
+}
+
 __global__ void __launch_bounds__(kWgThreads, 1) wgrad_tc_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                const WgradArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kWgStages * kWgStageBytes);
-  uint64_t* done = full + kWgStages;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + kWgStages + 1);
-  __shared__ int s_abort;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kWgStages * kWgStageBytes);  // stage loaded
+  uint64_t* empty = full + kWgStages;                                              // stage consumed
+  uint64_t* done = empty + kWgStages;                                              // every MMA completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  __shared__ volatile int s_abort;
 
   const int n = *a.count;
   const int chunks = (n + kWgChunk - 1) / kWgChunk;
   const int per = (chunks + gridDim.x - 1) / gridDim.x;
   const int c0 = blockIdx.x * per, c1 = min(chunks, c0 + per);
   if (c0 >= c1) return;  // uniform over the CTA
+  const int nch = c1 - c0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (warp == 0) {
@@ -141,9 +188,9 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_tc_kernel(const __grid_co
   if (threadIdx.x == 0) {
     for (int s = 0; s < kWgStages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&done[s], 1);
+      mbar_init(&empty[s], 1);
     }
-    mbar_init(&done[kWgStages], 1);
+    mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     s_abort = 0;
   }
@@ -153,40 +200,56 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_tc_kernel(const __grid_co
   const uint32_t tmem = *tmem_slot;
   const uint32_t tD1 = tmem, tD2 = tmem + 112;
 
-  if (threadIdx.x == 0) {
-    const uint32_t id1 = idesc_f16(128, 112, a.bf16), id2 = idesc_f16(128, 16, a.bf16);
-    bool ok = true;
-    for (int c = c0; c < c1 && ok; ++c) {
-      const int i = c - c0, st = i % kWgStages;
+  if (warp == 0 && lane == 0) {
+    // ---- producer: chunk i into stage i % kWgStages once its previous chunk's MMAs are done
+    int issued = 0;
+    for (int i = 0; i < nch; ++i) {
+      const int st = i % kWgStages;
+      if (i >= kWgStages && !mbar_wait(&empty[st], ((i / kWgStages) - 1) & 1, a.wait_ns, &s_abort)) {
+        s_abort = 1;
+        break;
+      }
+      if (a.withhold_last && i == nch - 1) break;  // injected stall: the consumer's wait must expire
       uint8_t* base = smem + st * kWgStageBytes;
-      if (i >= kWgStages) ok = mbar_wait(&done[st], ((i / kWgStages) - 1) & 1);  // stage free again
-      if (!ok) break;
       mbar_expect_tx(&full[st], kWgStageBytes);
-      for (int r = 0; r < kWgRows; r += 16) tma_load_2d(base + r * 128, &tmap, c * kWgChunk, r, &full[st]);
-      ok = mbar_wait(&full[st], (i / kWgStages) & 1);
-      if (!ok) break;
+      for (int r = 0; r < kWgRows; r += kWgBoxRows)
+        tma_load_2d(base + r * 128, &tmap, (c0 + i) * kWgChunk, r, &full[st]);
+      ++issued;
+    }
+    // every load issued has landed before the CTA may exit (the last load of
+    // each stage: no later load was issued to it, so its phase is the one to wait for)
+    bool drained = true;
+    for (int i = issued > kWgStages ? issued - kWgStages : 0; i < issued; ++i)
+      drained &= mbar_wait(&full[i % kWgStages], (i / kWgStages) & 1, kWgDrainNs, nullptr);
+    if (!drained) s_abort = 1;
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    const uint32_t id1 = idesc_f16(128, 112, a.bf16), id2 = idesc_f16(128, 16, a.bf16);
+    for (int i = 0; i < nch; ++i) {
+      const int st = i % kWgStages;
+      if (!mbar_wait(&full[st], (i / kWgStages) & 1, a.wait_ns, &s_abort)) {
+        s_abort = 1;
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const uint32_t b = smem_u32(base);
+      const uint32_t b = smem_u32(smem + st * kWgStageBytes);
 #pragma unroll
       for (int kk = 0; kk < kWgChunk / 16; ++kk) {
         const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
         umma_f16(tD1, smem_desc_sw128(b + kk * 32), smem_desc_sw128(b + 128 * 128 + kk * 32), id1, acc);
         umma_f16(tD2, smem_desc_sw128(b + 240 * 128 + kk * 32), smem_desc_sw128(b + 368 * 128 + kk * 32), id2, acc);
       }
-      umma_commit(&done[st]);
+      umma_commit(&empty[st]);
     }
-    if (ok) {
-      umma_commit(&done[kWgStages]);
-      ok = mbar_wait(&done[kWgStages], 0);
-    }
-    if (!ok) {
-      s_abort = 1;
-      atomicExch(a.err, 1);
-    }
+    // tracks every MMA issued above, on the normal path and after giving up alike
+    umma_commit(done);
+    if (!mbar_wait(done, 0, kWgDrainNs, nullptr)) s_abort = 1;
   }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  if (!s_abort) {
+  if (s_abort) {
+    if (threadIdx.x == 0) atomicOr(a.flags, kStepPipelineError);
+  } else {
     const float inv = 1.f / *a.scale;
     const int row = warp * 32 + lane;  // TMEM lane = accumulator row
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
@@ -196,16 +259,20 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_tc_kernel(const __grid_co
     for (int cb = 0; cb < 112; cb += 16) {
       tmem_ld16(tD1 + lane_base + cb, v);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
+      for (int j = 0; j < 16; j += 4) {
         const int col = cb + j;
-        const float g = v[j] * inv;
         if (row < 64) {
-          if (col < 64) atomicAdd(a.gW2 + row * 64 + col, g);
-          else if (col == 96) atomicAdd(a.gb2 + row, g);
+          if (col < 64) add4(a.gW2 + row * 64 + col, v[j] * inv, v[j + 1] * inv, v[j + 2] * inv, v[j + 3] * inv);
+          else if (col == 96) atomicAdd(a.gb2 + row, v[j] * inv);
         } else {
           const int r = row - 64;
-          if (col >= 64 && col < 64 + a.n_in) atomicAdd(a.gW1 + r * a.n_in + (col - 64), g);
-          else if (col == 96) atomicAdd(a.gb1 + r, g);
+          if (col >= 64 && col + 3 < 64 + a.n_in) {
+            add4(a.gW1 + r * a.n_in + (col - 64), v[j] * inv, v[j + 1] * inv, v[j + 2] * inv, v[j + 3] * inv);
+          } else if (col >= 64 && col < 64 + a.n_in) {
+            for (int q = 0; q < 4 && col + q < 64 + a.n_in; ++q) atomicAdd(a.gW1 + r * a.n_in + (col + q - 64), v[j + q] * inv);
+          } else if (col == 96) {
+            atomicAdd(a.gb1 + r, v[j] * inv);
+          }
         }
       }
     }
@@ -214,8 +281,7 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_tc_kernel(const __grid_co
 #pragma unroll
       for (int o = 0; o < 4; ++o) atomicAdd(a.gW3 + o * 64 + row, v[o] * inv);
     } else if (row == 64) {
-#pragma unroll
-      for (int o = 0; o < 4; ++o) atomicAdd(a.gb3 + o, v[o] * inv);
+      add4(a.gb3, v[0] * inv, v[1] * inv, v[2] * inv, v[3] * inv);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -241,7 +307,7 @@ cudaError_t make_wgrad_map(CUtensorMap* map, void* X, int64_t ld, int bf16) {
   if (ld % kWgChunk != 0 || (reinterpret_cast<uintptr_t>(X) & 15) != 0) return cudaErrorInvalidValue;
   const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)kWgRows};
   const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)kWgChunk, 16};
+  const cuuint32_t box[2] = {(cuuint32_t)kWgChunk, (cuuint32_t)kWgBoxRows};
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = encode(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, X, dims,
                       strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -253,7 +319,10 @@ cudaError_t launch_wgrad_tc(const CUtensorMap& map, const WgradArgs& a, int grid
   const size_t smem = wgrad_smem_bytes();
   cudaError_t e = cudaFuncSetAttribute(wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  wgrad_tc_kernel<<<grid, kWgThreads, smem, s>>>(map, a);
+  {
+    KernelSpan span("wgrad_tc_kernel", s);
+    wgrad_tc_kernel<<<grid, kWgThreads, smem, s>>>(map, a);
+  }
   return cudaGetLastError();
 }
 

@@ -213,38 +213,19 @@ static size_t train_sample_smem(bool prop) {
          sizeof(uint32_t) * (256 / 32) * list_smem_words(prop);
 }
 
-// Front-to-back compositing of one ray, the loss, and the reverse sweep
-//   dL/dc_i = T_i alpha_i g,
-//   dL/dsigma_i = delta (T_{i+1} c_i.g - g.(C - C_{<=i})) + g_alpha delta T_N
-// with g = dL/dC and g_alpha = dL/dalpha for the ray's alpha = 1 - T_N
-// (Sec. 3.2, Eq. 8; loss terms of Sec. 3.4, Eq. 9-11).
-__global__ void train_composite_kernel(const TrainArgs a) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = r < a.n_rays;
-  const int n = active ? a.ray_n[r] : 0;
-  const float dt = active ? a.ray_dt[r] : 0.f;
-  const int* idx = a.ray_idx + (size_t)(active ? r : 0) * a.n_slots;
-  float C[3] = {0.f, 0.f, 0.f}, depth = 0.f;
-  for (int j = 0; j < n; ++j) {
-    const float4 o = a.s_out[idx[j]];
-    if (o.x > 0.f) {
-      const float sd = o.x * dt;
-      const float w = expf(-depth) * -expm1f(-sd);
-      C[0] = fmaf(w, o.y, C[0]);
-      C[1] = fmaf(w, o.z, C[1]);
-      C[2] = fmaf(w, o.w, C[2]);
-      depth += sd;
-    }
-  }
+// The step's own loss for ray r (Sec. 3.4, Eq. 9-11), averaged over the rays
+// and added to *a.loss (one atomic per warp; every lane of the warp calls), and
+// its gradients g = dL/dC, ga = dL/dalpha.
+__device__ __forceinline__ void composite_loss(const TrainArgs& a, int r, bool active, const float C[3], float depth,
+                                               float g[3], float& ga) {
   const float inv_n = 1.f / (float)a.n_rays;
   float e[3], ee = 0.f;
   for (int k = 0; k < 3; ++k) {
     e[k] = active ? C[k] - a.target[3 * r + k] : 0.f;
     ee = fmaf(e[k], e[k], ee);
-    if (active && a.rgb_out) a.rgb_out[3 * r + k] = C[k];
   }
   // colour term (Eq. 9): L2 over channels, or Huber of the colour error's norm
-  float g[3], lr;
+  float lr;
   if (!a.huber) {
     lr = ee;
     for (int k = 0; k < 3; ++k) g[k] = 2.f * e[k];
@@ -260,8 +241,9 @@ __global__ void train_composite_kernel(const TrainArgs a) {
   }
   for (int k = 0; k < 3; ++k) g[k] *= a.w_rgb * inv_n;
   // opacity terms of alpha = 1 - T_N: L1 to the mask (Eq. 10), hard surface (Eq. 11)
-  const float alpha = -expm1f(-depth), TN = expf(-depth);
-  float la = 0.f, ga = 0.f;
+  const float alpha = -expm1f(-depth);
+  float la = 0.f;
+  ga = 0.f;
   if (active && a.w_alpha != 0.f) {
     const float da = alpha - a.alpha_target[r];
     la += a.w_alpha * fabsf(da);
@@ -278,9 +260,13 @@ __global__ void train_composite_kernel(const TrainArgs a) {
   float lw = active ? (a.w_rgb * lr + la) * inv_n : 0.f;
   for (int o = 16; o > 0; o >>= 1) lw += __shfl_down_sync(kFull, lw, o);
   if ((threadIdx.x & 31) == 0) atomicAdd(a.loss, lw);
-  if (!active) return;
-  float Cle[3] = {0.f, 0.f, 0.f};
-  depth = 0.f;
+}
+
+// The reverse sweep over the ray's samples in march order: dL/dsigma_i and
+// dL/dc_i into s_grad (zero for samples without a root).
+__device__ __forceinline__ void reverse_sweep(const TrainArgs& a, int n, float dt, const int* idx, const float C[3],
+                                              float TN, const float g[3], float ga) {
+  float Cle[3] = {0.f, 0.f, 0.f}, depth = 0.f;
   for (int j = 0; j < n; ++j) {
     const int s = idx[j];
     const float4 o = a.s_out[s];
@@ -300,6 +286,49 @@ __global__ void train_composite_kernel(const TrainArgs a) {
   }
 }
 
+// Front-to-back compositing of one ray, the loss, and the reverse sweep
+//   dL/dc_i = T_i alpha_i g,
+//   dL/dsigma_i = delta (T_{i+1} c_i.g - g.(C - C_{<=i})) + g_alpha delta T_N
+// with g = dL/dC and g_alpha = dL/dalpha for the ray's alpha = 1 - T_N
+// (Sec. 3.2, Eq. 8; loss terms of Sec. 3.4, Eq. 9-11).  a.comp_mode selects
+// where g and g_alpha come from: kCompLoss -- the step's loss; kCompUpstream --
+// the caller's per-ray gradients (a.up_rgb, a.up_alpha: the reverse sweep of a
+// loss computed elsewhere); kCompForward -- no reverse sweep, only the ray's
+// colour and alpha are written.
+__global__ void train_composite_kernel(const TrainArgs a) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = r < a.n_rays;
+  const int n = active ? a.ray_n[r] : 0;
+  const float dt = active ? a.ray_dt[r] : 0.f;
+  const int* idx = a.ray_idx + (size_t)(active ? r : 0) * a.n_slots;
+  float C[3] = {0.f, 0.f, 0.f}, depth = 0.f;
+  for (int j = 0; j < n; ++j) {
+    const float4 o = a.s_out[idx[j]];
+    if (o.x > 0.f) {
+      const float sd = o.x * dt;
+      const float w = expf(-depth) * -expm1f(-sd);
+      C[0] = fmaf(w, o.y, C[0]);
+      C[1] = fmaf(w, o.z, C[1]);
+      C[2] = fmaf(w, o.w, C[2]);
+      depth += sd;
+    }
+  }
+  if (active && a.rgb_out)
+    for (int k = 0; k < 3; ++k) a.rgb_out[3 * r + k] = C[k];
+  if (active && a.alpha_out) a.alpha_out[r] = -expm1f(-depth);
+  if (a.comp_mode == kCompForward) return;
+  float g[3], ga;
+  if (a.comp_mode == kCompUpstream) {
+    if (!active) return;
+    for (int k = 0; k < 3; ++k) g[k] = a.up_rgb[3 * r + k];
+    ga = a.up_alpha ? a.up_alpha[r] : 0.f;
+  } else {
+    composite_loss(a, r, active, C, depth, g, ga);
+    if (!active) return;
+  }
+  const float TN = expf(-depth);
+  reverse_sweep(a, n, dt, idx, C, TN, g, ga);
+}
 // ---------------------------------------------------------------------------
 // Per-sample backward
 // ---------------------------------------------------------------------------
@@ -1049,7 +1078,7 @@ __global__ void __launch_bounds__(kBwThreads) train_backward_h_kernel(const Trai
       }
     }
   }
-  if (overflow) atomicExch(a.overflow, 1);
+  if (overflow) atomicOr(a.overflow, kStepOverflow);
 }
 
 // After an overflow the step's gradients are meaningless: zero them (the step is
@@ -1065,31 +1094,48 @@ constexpr int kScaleWindow = 1000;
 constexpr float kScaleMax = 16777216.f;  // 2^24
 
 __global__ void loss_scale_kernel(const TrainArgs a, int dynamic) {
-  if (*a.overflow) {
+  if (*a.overflow & kStepOverflow) {
     *a.scale = fmaxf(*a.scale * 0.5f, 1.f);
     *a.good_steps = 0;
+  } else if (*a.overflow) {
+    // skipped for another reason (the weight-gradient pipeline gave up): the scale stays
   } else if (dynamic && ++*a.good_steps >= kScaleWindow) {
     *a.scale = fminf(*a.scale * 2.f, kScaleMax);
     *a.good_steps = 0;
   }
 }
 
-cudaError_t launch_train(const TrainArgs& a, const CUtensorMap* map, int num_sms, cudaStream_t s) {
+cudaError_t launch_train_forward(const TrainArgs& a, int num_sms, cudaStream_t s) {
   cudaError_t e;
   const int rb = (a.n_rays + 127) / 128;
   const int gb = (a.n_reg + 127) / 128;
-  train_count_kernel<<<rb, 128, 0, s>>>(a);
+  {
+    KernelSpan span("train_count_kernel", s);
+    train_count_kernel<<<rb, 128, 0, s>>>(a);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (a.n_reg > 0) {
-    reg_count_kernel<<<gb, 128, 0, s>>>(a);
+    {
+      KernelSpan span("reg_count_kernel", s);
+      reg_count_kernel<<<gb, 128, 0, s>>>(a);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  pose_scan_kernel<<<1, 32, 0, s>>>(a);
+  {
+    KernelSpan span("pose_scan_kernel", s);
+    pose_scan_kernel<<<1, 32, 0, s>>>(a);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  train_emit_kernel<<<rb, 128, 0, s>>>(a);
+  {
+    KernelSpan span("train_emit_kernel", s);
+    train_emit_kernel<<<rb, 128, 0, s>>>(a);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (a.n_reg > 0) {
-    reg_emit_kernel<<<gb, 128, 0, s>>>(a);
+    {
+      KernelSpan span("reg_emit_kernel", s);
+      reg_emit_kernel<<<gb, 128, 0, s>>>(a);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   const Prec P = (Prec)a.prec;
@@ -1102,38 +1148,87 @@ cudaError_t launch_train(const TrainArgs& a, const CUtensorMap* map, int num_sms
   auto sample = P == Prec::F32   ? train_sample_kernel<Prec::F32, false>
                 : P == Prec::F16 ? (prop ? train_sample_kernel<Prec::F16, true> : train_sample_kernel<Prec::F16, false>)
                                  : (prop ? train_sample_kernel<Prec::BF16, true> : train_sample_kernel<Prec::BF16, false>);
+  const char* sample_name = P == Prec::F32   ? "train_sample_kernel<fp32>"
+                            : P == Prec::F16 ? (prop ? "train_sample_kernel<fp16,proposal>" : "train_sample_kernel<fp16>")
+                                             : (prop ? "train_sample_kernel<bf16,proposal>" : "train_sample_kernel<bf16>");
   const size_t smem = P == Prec::F32   ? train_sample_smem<Prec::F32>(false)
                       : P == Prec::F16 ? train_sample_smem<Prec::F16>(prop) : train_sample_smem<Prec::BF16>(prop);
   if ((e = set_smem(sample, smem, 256)) != cudaSuccess) return e;
   int per_sm = 0;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sample, 256, smem)) != cudaSuccess) return e;
-  sample<<<num_sms * (per_sm < 1 ? 1 : per_sm), 256, smem, s>>>(a);
+  {
+    KernelSpan span(sample_name, s);
+    sample<<<num_sms * (per_sm < 1 ? 1 : per_sm), 256, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_train_composite(const TrainArgs& a, cudaStream_t s) {
+  cudaError_t e;
+  const int rb = (a.n_rays + 127) / 128;
+  const int gb = (a.n_reg + 127) / 128;
+  {
+    KernelSpan span("train_composite_kernel", s);
+    train_composite_kernel<<<rb, 128, 0, s>>>(a);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  train_composite_kernel<<<rb, 128, 0, s>>>(a);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (a.n_reg > 0) {
-    reg_grad_kernel<<<gb, 128, 0, s>>>(a);
+  if (a.n_reg > 0 && a.comp_mode == kCompLoss) {
+    {
+      KernelSpan span("reg_grad_kernel", s);
+      reg_grad_kernel<<<gb, 128, 0, s>>>(a);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  return cudaSuccess;
+}
+
+cudaError_t launch_train(const TrainArgs& a, const CUtensorMap* map, int num_sms, cudaStream_t s) {
+  cudaError_t e;
+  if ((e = launch_train_forward(a, num_sms, s)) != cudaSuccess) return e;
+  if ((e = launch_train_composite(a, s)) != cudaSuccess) return e;
+  return launch_train_backward(a, map, num_sms, s);
+}
+
+cudaError_t launch_train_backward(const TrainArgs& a, const CUtensorMap* map, int num_sms, cudaStream_t s) {
+  cudaError_t e;
+  const Prec P = (Prec)a.prec;
   if (P == Prec::F32) {
     const size_t vec_bytes = sizeof(float) * kWidth * 128;
     if ((e = set_smem(train_backward_kernel, vec_bytes, 128)) != cudaSuccess) return e;
-    train_backward_kernel<<<num_sms * 4, 128, vec_bytes, s>>>(a);
+    {
+      KernelSpan span("train_backward_kernel", s);
+      train_backward_kernel<<<num_sms * 4, 128, vec_bytes, s>>>(a);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    train_scatter_kernel<false><<<num_sms * 8, 256, 0, s>>>(a);
+    {
+      KernelSpan span("train_scatter_kernel", s);
+      train_scatter_kernel<false><<<num_sms * 8, 256, 0, s>>>(a);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    mlp_grad_kernel<<<num_sms * 4, 256, 0, s>>>(a);
+    {
+      KernelSpan span("mlp_grad_kernel", s);
+      mlp_grad_kernel<<<num_sms * 4, 256, 0, s>>>(a);
+    }
     return cudaGetLastError();
   }
   if (P == Prec::F16) {
     if ((e = set_smem(train_backward_h_kernel<Prec::F16>, kBwSmemBytes, kBwThreads)) != cudaSuccess) return e;
-    train_backward_h_kernel<Prec::F16><<<num_sms * 2, kBwThreads, kBwSmemBytes, s>>>(a);
+    {
+      KernelSpan span("train_backward_h_kernel<fp16>", s);
+      train_backward_h_kernel<Prec::F16><<<num_sms * 2, kBwThreads, kBwSmemBytes, s>>>(a);
+    }
   } else {
     if ((e = set_smem(train_backward_h_kernel<Prec::BF16>, kBwSmemBytes, kBwThreads)) != cudaSuccess) return e;
-    train_backward_h_kernel<Prec::BF16><<<num_sms * 2, kBwThreads, kBwSmemBytes, s>>>(a);
+    {
+      KernelSpan span("train_backward_h_kernel<bf16>", s);
+      train_backward_h_kernel<Prec::BF16><<<num_sms * 2, kBwThreads, kBwSmemBytes, s>>>(a);
+    }
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  train_scatter_kernel<true><<<num_sms * 8, 256, 0, s>>>(a);
+  {
+    KernelSpan span("train_scatter_kernel", s);
+    train_scatter_kernel<true><<<num_sms * 8, 256, 0, s>>>(a);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   WgradArgs w{};
   w.count = a.count;
@@ -1146,15 +1241,23 @@ cudaError_t launch_train(const TrainArgs& a, const CUtensorMap* map, int num_sms
   w.gb3 = w.gW3 + 4 * kWidth;
   w.n_in = a.P.n_in;
   w.bf16 = P == Prec::BF16 ? 1 : 0;
-  w.err = a.err;
+  w.flags = a.overflow;
+  w.wait_ns = a.wait_ns;
+  w.withhold_last = (a.inject & 1) ? 1 : 0;
   if ((e = launch_wgrad_tc(*map, w, num_sms, s)) != cudaSuccess) return e;
   const size_t sizes[4] = {a.n_table_f, a.n_mlp_f, a.n_skin_f, a.n_bones_f};
   float* bufs[4] = {a.g_table, a.g_mlp, a.g_skin, a.g_bones};
   for (int q = 0; q < 4; ++q) {
-    zero_on_overflow_kernel<<<num_sms * 4, 256, 0, s>>>(a.overflow, bufs[q], sizes[q]);
+    {
+      KernelSpan span("zero_on_overflow_kernel", s);
+      zero_on_overflow_kernel<<<num_sms * 4, 256, 0, s>>>(a.overflow, bufs[q], sizes[q]);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  loss_scale_kernel<<<1, 1, 0, s>>>(a, P == Prec::F16 ? 1 : 0);
+  {
+    KernelSpan span("loss_scale_kernel", s);
+    loss_scale_kernel<<<1, 1, 0, s>>>(a, P == Prec::F16 ? 1 : 0);
+  }
   return cudaGetLastError();
 }
 

@@ -12,6 +12,11 @@ namespace ia {
 constexpr int kWgRows = 384;   // channel rows of the operand array X
 constexpr int kWgChunk = 64;   // samples per pipeline stage (128 B of fp16 / bf16)
 
+// Bits of a reduced-precision step's flags word (device int, zeroed at the start
+// of every step); any bit set means the step is skipped (its gradients zeroed).
+constexpr int kStepOverflow = 1;       // a scaled gradient or activation left the operand range
+constexpr int kStepPipelineError = 2;  // the tensor-core reduction gave up waiting on its pipeline
+
 struct WgradArgs {
   const int* count;    // samples (device scalar)
   const float* scale;  // loss scale (device scalar)
@@ -23,10 +28,12 @@ struct WgradArgs {
   float* gb3;          // [4]
   int n_in;
   int bf16;            // operand type: 0 fp16, 1 bf16
-  int* err;            // set to 1 when a wait expires
+  int* flags;          // the step's skip flags: kStepPipelineError is raised when a wait gives up
+  uint64_t wait_ns;    // bound on each pipeline wait
+  int withhold_last;   // failure injection: the producer never issues the copy of its last chunk
 };
 
-// Tensor map over X [kWgRows][ld] (2-byte elements), 64 x 16 boxes, 128-byte
+// Tensor map over X [kWgRows][ld] (2-byte elements), 64 x 128 boxes, 128-byte
 // swizzle.  ld must be a multiple of 64 and X 16-byte aligned.
 cudaError_t make_wgrad_map(CUtensorMap* map, void* X, int64_t ld, int bf16);
 cudaError_t launch_wgrad_tc(const CUtensorMap& map, const WgradArgs& a, int grid, cudaStream_t s);

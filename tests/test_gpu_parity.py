@@ -44,20 +44,31 @@ def _pose_ctx(ia, sc, table, mlp, seeds, early_T=0.0):
 
 
 def test_transforms_bit_exact(ia, scene):
+    """The fp64 pose chain's fp32 results on 256 seeded poses.  Both sides
+    use the same rounded fp64 operations; the one thing they do not share is
+    the fp64 cosine and sine of the joint angles (CUDA's and the C library's,
+    each within an ulp or two of the exact value), so an fp32 result could in
+    principle differ by one ulp where an fp64 value sits within an ulp of an
+    fp32 rounding boundary.  Any such element is counted and reported; the
+    contract is bit-exact."""
     sc, table, mlp = scene
-    seeds = [0, 1, 2, 3, 4]
+    seeds = list(range(256))
     ctx, poses = _pose_ctx(ia, sc, table, mlp, seeds)
     om = O.OracleModel(sc, table, mlp)
     nb = sc.n_bones
+    differ = checked = 0
     for i, (th, tr) in enumerate(poses):
         N = np.zeros((nb, 12), np.float32)
         Ni = np.zeros((nb, 12), np.float32)
         B0 = np.zeros(12, np.float32)
         ia.ia_get_transforms(ctx, i, N, Ni, B0)
         T = om.transforms(om.pose(th, tr))
-        np.testing.assert_array_equal(N, T["N"].reshape(nb, 12).astype(np.float32))
-        np.testing.assert_array_equal(Ni, T["Ninv"].reshape(nb, 12).astype(np.float32))
-        np.testing.assert_array_equal(B0, T["B0inv"].reshape(12))
+        for got, ref in ((N, T["N"].reshape(nb, 12).astype(np.float32)),
+                         (Ni, T["Ninv"].reshape(nb, 12).astype(np.float32)), (B0, T["B0inv"].reshape(12))):
+            differ += int(np.sum(got.view(np.int32) != ref.view(np.int32)))
+            checked += got.size
+    print(f"pose chain: {checked} fp32 values over {len(poses)} poses, {differ} differing")
+    assert differ == 0
     ia.ia_destroy(ctx)
 
 
@@ -117,7 +128,10 @@ def test_posed_field(ia, scene):
     err_report("posed x*", g_xc[has], ref["xstar"][has])
     assert np.all(np.abs(g_xc[has] - ref["xstar"][has]) <= ATOL_XSTAR)
     assert close(g_sig[has], ref["sigma"][has], RTOL_SIGMA, 1e-9).all()
-    assert close(g_rgb[has], ref["rgb"][has], 1e-4, ATOL_RGB).all()
+    # colour: the stated fp32 bound (1e-5 relative)
+    n_over = int((~close(g_rgb[has], ref["rgb"][has], RTOL_RGB, ATOL_RGB)).any(axis=1).sum())
+    print(f"posed field: {n_over} of {has.sum()} colours beyond 1e-5 relative")
+    assert n_over == 0
     assert np.all(g_sig[ok & (ref["start"] < 0)] == 0)
     # the start label names the first start that reached the selected root; when
     # an earlier start converges only marginally the label may move to a later
@@ -160,15 +174,7 @@ def test_occupancy_end_to_end(ia, scene):
     print("occupancy stats", stats)
     # densities agree where the oracle sees a root; bits agree except where a cell's
     # dilation neighbourhood holds a density within 1e-3 relative of tau
-    amb = np.abs(ref_sig - sc.occ_tau) < 1e-3 * sc.occ_tau
-    amb3 = amb.reshape(R, R, R)
-    near = np.zeros_like(amb3)
-    d = sc.occ_dilate
-    for dz in range(-d, d + 1):
-        for dy in range(-d, d + 1):
-            for dx in range(-d, d + 1):
-                near |= np.roll(amb3, (dz, dy, dx), axis=(0, 1, 2))
-    near = near.reshape(-1)
+    near = _ambiguous_cells(sc, ref_sig)
     g_occ = bits_to_bool(bits.cpu().numpy().view(np.uint32), R ** 3)
     r_occ = bits_to_bool(ref_bits, R ** 3)
     mism = (g_occ != r_occ) & ~near
@@ -179,15 +185,77 @@ def test_occupancy_end_to_end(ia, scene):
 
 
 def _render_case(ia, sc, table, mlp, seed, early_T, width=None, height=None):
+    """A context and the oracle on one pose, both over the oracle's occupancy
+    grid: the GPU builds its own grid first (which also builds the pose's
+    root-culling masks that the render uses), then the oracle's bits replace it."""
     ctx, poses = _pose_ctx(ia, sc, table, mlp, [seed], early_T=early_T)
     om = O.OracleModel(sc, table, mlp, early_T=early_T)
+    p = om.pose(*poses[0])
+    ia.ia_update_occupancy(ctx, 0, ia.IA_OCC_POSE)
+    _, occ = om.occupancy(p)
+    ia.ia_set_occupancy(ctx, occ)
+    cam = S.make_camera(sc, width, height)
+    return ctx, om, p, occ, cam
+
+
+def _ambiguous_cells(sc, ref_sig):
+    """Cells whose dilation neighbourhood holds a density within 1e-3
+    relative of tau: their occupancy bit is an fp32-vs-fp64 coin flip."""
+    R, d = sc.occ_res, sc.occ_dilate
+    amb3 = (np.abs(ref_sig - sc.occ_tau) < 1e-3 * sc.occ_tau).reshape(R, R, R)
+    near = np.zeros_like(amb3)
+    for dz in range(-d, d + 1):
+        for dy in range(-d, d + 1):
+            for dx in range(-d, d + 1):
+                near |= np.roll(amb3, (dz, dy, dx), axis=(0, 1, 2))
+    return near.reshape(-1)
+
+
+def test_render_end_to_end_chain(ia, scene):
+    """The whole chain on each side with nothing shared but the inputs: the
+    GPU's pose chain, occupancy grid (its own densities, threshold, dilation;
+    root culling on) and frame, against the oracle's pose chain, occupancy grid
+    and frame.  The two grids must agree except in cells whose dilation
+    neighbourhood holds a density within 1e-3 of tau; rays crossing such a cell
+    are excluded (reported), as are rays the oracle flags.  Tiny: the whole
+    frame without early termination; full size: 4000 sampled pixels of the
+    540 x 540 frame with early termination at T < 1e-4."""
+    sc, table, mlp = scene
+    early = 0.0 if sc.name == "tiny" else 1e-4
+    ctx, poses = _pose_ctx(ia, sc, table, mlp, [6], early_T=early)
+    om = O.OracleModel(sc, table, mlp, early_T=early)
     p = om.pose(*poses[0])
     R = sc.occ_res
     bits = torch.zeros((R ** 3 + 31) // 32, dtype=torch.int32, device="cuda")
     ia.ia_update_occupancy(ctx, 0, ia.IA_OCC_POSE, None, bits)
-    occ = bits.cpu().numpy().view(np.uint32).copy()
-    cam = S.make_camera(sc, width, height)
-    return ctx, om, p, occ, cam
+    cam = S.make_camera(sc)
+    W, H = cam["width"], cam["height"]
+    rgb = torch.zeros(H * W, 3, device="cuda")
+    alpha = torch.zeros(H * W, device="cuda")
+    ia.ia_render(ctx, 0, camera(ia, cam), rgb, alpha)
+    torch.cuda.synchronize()
+    ref_sig, ref_bits = om.occupancy(p)
+    near = _ambiguous_cells(sc, ref_sig)
+    g_occ = bits_to_bool(bits.cpu().numpy().view(np.uint32), R ** 3)
+    r_occ = bits_to_bool(ref_bits, R ** 3)
+    assert np.sum((g_occ != r_occ) & ~near) == 0
+    near_bits = np.packbits(near.astype(np.uint8), bitorder="little").view(np.uint32)
+    crosses = om.march_mask(p, cam, near_bits).any(axis=1)
+    if sc.name == "tiny":
+        pix = np.arange(W * H)
+    else:
+        pix = np.random.default_rng(9).choice(W * H, 4000, replace=False)
+    ref = om.render_pixels(p, cam, ref_bits, pix)
+    ok = (ref["flags"] == 0) & ~crosses[pix]
+    print(f"end-to-end {sc.name}: {near.sum()} ambiguous cells, {(g_occ != r_occ).sum()} differing bits; "
+          f"{crosses[pix].sum()} of {len(pix)} rays cross an ambiguous cell, {(ref['flags'] != 0).sum()} flagged")
+    g_rgb, g_a = rgb.cpu().numpy()[pix], alpha.cpu().numpy()[pix]
+    err_report(f"end-to-end {sc.name} rgb", g_rgb[ok], ref["rgb"][ok])
+    assert ok.sum() >= 0.98 * len(pix)
+    assert (ref["alpha"][ok] > 0.01).sum() >= 100
+    assert close(g_rgb[ok], ref["rgb"][ok], RTOL_RGB, ATOL_RGB).all()
+    assert close(g_a[ok], ref["alpha"][ok], RTOL_RGB, ATOL_RGB).all()
+    ia.ia_destroy(ctx)
 
 
 def test_march_mask_bit_exact(ia, scene):

@@ -124,6 +124,33 @@ def test_training_pairs_match_oracle(ia):
     ia.ia_destroy(ctx)
 
 
+def _train_proposal(ia, ctx, sc, pc, n_poses, per, steps, rng):
+    """Pairs from the plain search at points in the occupied cells of poses
+    0..n_poses-1 of the context, then the library's own training kernels."""
+    pt, pm = S.proposal_init(sc, pc, 0)
+    ia.ia_proposal_set_params(ctx, torch.from_numpy(pt).cuda(), torch.from_numpy(S.pack_proposal(pm)).cuda())
+    R = sc.occ_res
+    bits = torch.zeros((R ** 3 + 31) // 32, dtype=torch.int32, device="cuda")
+    X, P, L, T = [], [], [], []
+    for i in range(n_poses):
+        ia.ia_update_occupancy(ctx, i, ia.IA_OCC_POSE, None, bits)
+        x = torch.from_numpy(occupied_points(bits.cpu().numpy().view(np.uint32), sc, per, rng)).cuda()
+        lab = torch.zeros(per, dtype=torch.int32, device="cuda")
+        off = torch.zeros(per, 3, device="cuda")
+        ia.ia_proposal_pairs(ctx, i, x, lab, off)
+        X.append(x); P.append(torch.full((per,), i, dtype=torch.int32, device="cuda")); L.append(lab); T.append(off)
+    X, P, L, T = (torch.cat(a) for a in (X, P, L, T))
+    keep = torch.nonzero(L >= 0).squeeze(1)
+    perm = keep[torch.from_numpy(rng.permutation(len(keep))).cuda()]
+    X, P, L, T = (a[perm].contiguous() for a in (X, P, L, T))
+    losses = torch.zeros(steps, device="cuda")
+    ia.ia_proposal_train(ctx, X, P, L, T, steps, 8192, 2e-3, losses)
+    torch.cuda.synchronize()
+    ls = losses.cpu().numpy()
+    print(f"proposal training: {len(perm)} pairs, loss {ls[0]:.3f} -> {ls[-20:].mean():.3f}")
+    assert ls[-20:].mean() < 0.25 * ls[0]
+
+
 @pytest.fixture(scope="module")
 def trained(ia):
     """A proposal trained on the GPU (library kernels) on pairs from N_TRAIN poses."""
@@ -131,29 +158,7 @@ def trained(ia):
     table, mlp = S.make_field(sc, 0)
     poses = [S.make_pose(sc, 100 + i) for i in range(N_TRAIN)] + [S.make_pose(sc, i) for i in range(N_TEST)]
     ctx, pc = _ctx(ia, sc, table, mlp, 1, poses)
-    pt, pm = S.proposal_init(sc, pc, 0)
-    ia.ia_proposal_set_params(ctx, torch.from_numpy(pt).cuda(), torch.from_numpy(S.pack_proposal(pm)).cuda())
-    rng = np.random.default_rng(15)
-    R = sc.occ_res
-    bits = torch.zeros((R ** 3 + 31) // 32, dtype=torch.int32, device="cuda")
-    X, P, L, T = [], [], [], []
-    for i in range(N_TRAIN):
-        ia.ia_update_occupancy(ctx, i, ia.IA_OCC_POSE, None, bits)
-        x = torch.from_numpy(occupied_points(bits.cpu().numpy().view(np.uint32), sc, PER, rng)).cuda()
-        lab = torch.zeros(PER, dtype=torch.int32, device="cuda")
-        off = torch.zeros(PER, 3, device="cuda")
-        ia.ia_proposal_pairs(ctx, i, x, lab, off)
-        X.append(x); P.append(torch.full((PER,), i, dtype=torch.int32, device="cuda")); L.append(lab); T.append(off)
-    X, P, L, T = (torch.cat(a) for a in (X, P, L, T))
-    keep = torch.nonzero(L >= 0).squeeze(1)
-    perm = keep[torch.from_numpy(rng.permutation(len(keep))).cuda()]
-    X, P, L, T = (a[perm].contiguous() for a in (X, P, L, T))
-    losses = torch.zeros(400, device="cuda")
-    ia.ia_proposal_train(ctx, X, P, L, T, 400, 8192, 2e-3, losses)
-    torch.cuda.synchronize()
-    ls = losses.cpu().numpy()
-    print(f"proposal training: {len(perm)} pairs, loss {ls[0]:.3f} -> {ls[-20:].mean():.3f}")
-    assert ls[-20:].mean() < 0.25 * ls[0]
+    _train_proposal(ia, ctx, sc, pc, N_TRAIN, PER, 400, np.random.default_rng(15))
     yield sc, table, mlp, ctx, pc, poses
     ia.ia_destroy(ctx)
 
@@ -237,3 +242,144 @@ def test_proposal_search_matches_oracle(ia, trained):
     assert np.all(np.abs(g_xc[idx] - ref_x) <= 2e-5)
     assert close(g_sig[idx], ref_s, 2e-2, 1e-7).all()
     assert close(g_rgb[idx], ref_c, 2e-3, 2e-4).all()
+
+
+def _round_fp16(x):
+    return np.asarray(x, np.float32).astype(np.float16).astype(np.float32)
+
+
+def _oracle_fp16(ia, ctx, sc, table, mlp, pc, early_T):
+    """The oracle on the operands the fp16 field and proposal read: the hash
+    table rounded to fp16, the MLP weights rounded to fp16 (biases fp32); the
+    proposal's weights rounded to fp16 except its layer-1 pose columns, which
+    the library folds into an fp32 per-pose bias.  The proposal's weights are
+    the ones trained on the GPU (an input both sides read)."""
+    om = O.OracleModel(sc, _round_fp16(table), {k: (_round_fp16(v) if k.startswith("W") else v)
+                                                 for k, v in mlp.items()}, early_T=early_T)
+    nt, nm = ia.ia_proposal_param_sizes(ctx)
+    pt, pmf = np.zeros(nt, np.float32), np.zeros(nm, np.float32)
+    ia.ia_proposal_get_params(ctx, pt, pmf)
+    nb = sc.n_bones
+    nin = 2 * pc["n_levels"] + 3 * nb
+    shapes = [("W1", (64, nin)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)), ("W3", (64, 64)), ("b3", (64,)),
+              ("W4", (nb + 3, 64)), ("b4", (nb + 3,))]
+    pm, o = {}, 0
+    for k, shp in shapes:
+        n = int(np.prod(shp))
+        pm[k] = pmf[o:o + n].reshape(shp).copy()
+        o += n
+    pm_op = {k: (_round_fp16(v) if k.startswith("W") else v) for k, v in pm.items()}
+    nf = 2 * pc["n_levels"]
+    pm_op["W1"][:, nf:] = pm["W1"][:, nf:]
+    return om, PP.PropModel(om, pc, pt.reshape(-1, 2), pm_op), (pt, pmf)
+
+
+def _proposal_frame(ia, sc, table, mlp, pc, params, pose, cam, early_T, om, pr, pix):
+    """fp16 + proposal frame of one pose on the GPU (render_kernel with the
+    proposal search and root culling, over the oracle's occupancy bits) and the
+    oracle's proposal-mode render of the listed pixels."""
+    th, tr = pose
+    p = om.pose(th, tr)
+    _, bits = om.occupancy(p)
+    cfg = ia.make_config(n_levels=sc.n_levels, log2_table=sc.log2_table, level_res=sc.level_res,
+                         max_samples=sc.max_samples, occ_res=sc.occ_res, occ_tau=sc.occ_tau,
+                         occ_dilate=sc.occ_dilate, early_stop_T=early_T, precision=ia.IA_FP16)
+    ctx = ia.ia_create(cfg)
+    ia.ia_set_skeleton(ctx, sc.parents, sc.rest_joints, sc.skin_grid, sc.canon_min, sc.canon_max,
+                       sc.norm_min, sc.norm_max)
+    ia.ia_set_params(ctx, torch.from_numpy(table).cuda(), torch.from_numpy(S.pack_mlp(mlp)).cuda())
+    ia.ia_set_pose(ctx, th[None], tr[None])
+    ia.ia_proposal_init(ctx, ia.make_proposal_config(pc["n_levels"], pc["log2_table"], pc["level_res"],
+                                                     pc["top_k"], pc["offset_weight"]))
+    ia.ia_proposal_set_params(ctx, torch.from_numpy(params[0]).cuda(), torch.from_numpy(params[1]).cuda())
+    ia.ia_set_search(ctx, ia.IA_SEARCH_PROPOSAL)
+    ia.ia_update_occupancy(ctx, 0)  # the pose's root-culling masks
+    ia.ia_set_occupancy(ctx, bits)  # the grid: the oracle's
+    W, H = cam["width"], cam["height"]
+    rgb = torch.zeros(W * H, 3, device="cuda")
+    a = torch.zeros(W * H, device="cuda")
+    st = ia.ia_render(ctx, 0, camera(ia, cam), rgb, a, stats=True)
+    torch.cuda.synchronize()
+    ia.ia_destroy(ctx)
+    ref = pr.render_pixels(p, th, cam, bits, pix)
+    return st, rgb.cpu().numpy()[pix], a.cpu().numpy()[pix], ref
+
+
+def _check_frame(name, st, rgb, alpha, ref):
+    hit = ref["nsamp"] > 0
+    flagged = hit & (ref["flags"] != 0)
+    ok = hit & ~flagged
+    bad = ok & ~(close(rgb, ref["rgb"], 2e-3, 2e-4).all(axis=1) & close(alpha, ref["alpha"], 2e-3, 2e-4))
+    err_report(f"{name} colour", rgb[ok], ref["rgb"][ok])
+    err_report(f"{name} opacity", alpha[ok], ref["alpha"][ok])
+    bits = {b: int(np.sum(hit & ((ref["flags"] & b) != 0))) for b in (1, 2, 4, 8, 16, 32, 64)}
+    print(f"{name}: rays flagged per oracle flag bit {bits}")
+    print(f"{name}: {hit.sum()} rays with samples, {flagged.sum()} flagged by the oracle and excluded "
+          f"({flagged.sum() / max(hit.sum(), 1):.2%}), {bad.sum()} outside 2e-3; fallbacks gpu {st['fallbacks']} "
+          f"+ culled {st['culled']}, oracle {int(ref['fallbacks'].sum())}")
+    assert hit.sum() > 500
+    assert flagged.sum() <= 0.01 * hit.sum()
+    assert bad.sum() == 0
+    assert np.all(alpha[~hit] == 0) and np.all(ref["alpha"][~hit] == 0)
+
+
+@pytest.fixture(scope="module")
+def trained_tiny(ia):
+    """A proposal trained on the GPU for the tiny scene (16 poses)."""
+    sc = S.make_scene("tiny", 0)
+    table, mlp = S.make_field(sc, 0)
+    poses = [S.make_pose(sc, 200 + i) for i in range(16)] + [S.make_pose(sc, 3)]
+    ctx, pc = _ctx(ia, sc, table, mlp, 1, poses)
+    _train_proposal(ia, ctx, sc, pc, 16, PER, 300, np.random.default_rng(25))
+    yield sc, table, mlp, ctx, pc, poses
+    ia.ia_destroy(ctx)
+
+
+def test_proposal_frame_matches_oracle_tiny(ia, trained_tiny):
+    """The product path's frame, render_kernel<fp16, proposal>, on the whole
+    64 x 64 tiny frame of a held-out pose (parity mode: no early termination)
+    against the oracle's proposal-mode render (or_render_pixels_prop) with the
+    same GPU-trained proposal: colour and opacity of every ray within the fp16
+    bound (2e-3 relative + 2e-4), rays the oracle flags as marginal excluded
+    (at most 1 %), and the frame's fallback count (samples whose proposed
+    starts found no root; the GPU does not search samples that root culling
+    proves rootless, so those count on its side as culled) equal to the
+    oracle's up to a few marginal samples."""
+    sc, table, mlp, ctx, pc, poses = trained_tiny
+    om, pr, params = _oracle_fp16(ia, ctx, sc, table, mlp, pc, 0.0)
+    cam = S.make_camera(sc)
+    pix = np.arange(cam["width"] * cam["height"], dtype=np.int32)
+    st, rgb, alpha, ref = _proposal_frame(ia, sc, table, mlp, pc, params, poses[-1], cam, 0.0, om, pr, pix)
+    _check_frame("tiny fp16+proposal frame", st, rgb, alpha, ref)
+    fb = int(ref["fallbacks"].sum())
+    assert st["proposed"] == st["occupied_samples"] - st["culled"] > 0
+    assert abs(st["fallbacks"] + st["culled"] - fb) <= max(3, 0.005 * fb)
+
+
+def test_proposal_frame_matches_oracle_full(ia, trained):
+    """The same at full size with the proposal of the 540 x 540 workload:
+    (a) a whole 135 x 135 frame of a held-out pose (the 540 x 540 camera at a
+    quarter of the resolution) in parity mode, with the fallback count;
+    (b) 4000 pixels, drawn from those whose rays reach an occupied cell of the
+    oracle's grid, of the 540 x 540 frame with early termination at T < 1e-4
+    (the benchmark's configuration; rays whose transmittance ends within
+    1e-3 of the threshold are flagged by the oracle and excluded)."""
+    sc, table, mlp, ctx, pc, poses = trained
+    pose = poses[N_TRAIN]
+    om, pr, params = _oracle_fp16(ia, ctx, sc, table, mlp, pc, 0.0)
+    cam = S.make_camera(sc, 135, 135)
+    pix = np.arange(135 * 135, dtype=np.int32)
+    st, rgb, alpha, ref = _proposal_frame(ia, sc, table, mlp, pc, params, pose, cam, 0.0, om, pr, pix)
+    _check_frame("135^2 fp16+proposal frame", st, rgb, alpha, ref)
+    fb = int(ref["fallbacks"].sum())
+    assert st["proposed"] == st["occupied_samples"] - st["culled"] > 0
+    assert abs(st["fallbacks"] + st["culled"] - fb) <= max(3, 0.005 * fb)
+
+    om, pr, params = _oracle_fp16(ia, ctx, sc, table, mlp, pc, 1e-4)
+    cam = S.make_camera(sc)
+    p = om.pose(*pose)
+    _, bits = om.occupancy(p)
+    reach = np.nonzero(om.march_mask(p, cam, bits).any(axis=1))[0]
+    pix = np.sort(np.random.default_rng(31).choice(reach, 4000, replace=False)).astype(np.int32)
+    st, rgb, alpha, ref = _proposal_frame(ia, sc, table, mlp, pc, params, pose, cam, 1e-4, om, pr, pix)
+    _check_frame("540^2 fp16+proposal frame, 4000 pixels, early termination", st, rgb, alpha, ref)

@@ -203,6 +203,56 @@ def test_overflow_skips_the_step_and_halves_the_scale(ia):
     ia.ia_destroy(ctx)
 
 
+def test_pipeline_wait_limit_skips_the_step(ia):
+    """The weight-gradient GEMM's bounded waits, made to run out without any
+    fault: with copy withholding injected, each CTA's producer never issues the
+    TMA copy of its last operand chunk, so the MMA thread's wait for it expires
+    after the (1 ms) wait limit while earlier chunks' MMAs are still in flight.
+    The kernel must drain those, free its tensor memory and return: the step is
+    reported as IA_ERR_CUDA and skipped (all gradients zero, loss scale kept),
+    and the context stays usable -- the next step, without injection, gives the
+    same gradients as a clean step before."""
+    sc = S.make_scene("full", 0)
+    table, mlp = S.make_field(sc, 0)
+    ctx = _ctx(ia, sc, table, mlp, 1)
+    poses = [S.make_pose(sc, i) for i in range(2)]
+    ia.ia_set_pose(ctx, np.stack([p[0] for p in poses]), np.stack([p[1] for p in poses]))
+    for i in range(2):
+        ia.ia_update_occupancy(ctx, i, ia.IA_OCC_UNION)
+    rb = S.make_ray_batch(sc, 12288, 2, seed=9)
+    dev = _dev({k: rb[k] for k in ("origin", "direction", "pose", "target")})
+
+    def step():
+        g = _grads(ia, ctx, sc, 2)
+        for v in g.values():
+            v.fill_(7.0)
+        ia.ia_train_step(ctx, dev["origin"], dev["direction"], dev["pose"], dev["target"],
+                         torch.zeros(1, device="cuda"), g, occ_grid=ia.IA_OCC_UNION)
+        return g
+
+    g0 = step()
+    assert ia.ia_loss_scale(ctx) == (16384.0, False)
+    st = ia.ia_train_stats(ctx)
+    assert st["occupied_samples"] - st["culled"] > 2 * 148 * 64  # several chunks per CTA
+    ia.ia_set_wait_limit(ctx, 1_000_000)
+    ia.ia_set_fault_injection(ctx, ia.IA_INJECT_WITHHOLD_COPY)
+    g1 = step()
+    with pytest.raises(ia.IAError) as e:
+        ia.ia_loss_scale(ctx)
+    assert e.value.status == ia.IA_ERR_CUDA and "gave up" in str(e.value)
+    for k, v in g1.items():
+        assert torch.count_nonzero(v).item() == 0, k
+    ia.ia_set_fault_injection(ctx, 0)
+    ia.ia_set_wait_limit(ctx, 0)
+    g2 = step()
+    assert ia.ia_loss_scale(ctx) == (16384.0, False)  # the skipped step left the scale alone
+    for k in g0:
+        a, b = g2[k].cpu().numpy(), g0[k].cpu().numpy()
+        assert np.count_nonzero(b) > 0
+        assert np.allclose(a, b, rtol=1e-5, atol=1e-6 * np.abs(b).max()), k
+    ia.ia_destroy(ctx)
+
+
 def test_train_step_with_proposal_starts(ia):
     """fp16 step whose correspondence search starts from the proposal's top-2
     bones of each sample's own pose (the batch mixes 4 poses, so every warp

@@ -39,6 +39,23 @@ def test_identity_pose_gives_identity_transforms(tiny):
         np.testing.assert_array_equal(T["N"][k], eye)
 
 
+def test_pose_chain_cos_sin_series_matches_the_c_library():
+    """The pose chain's cos / sin (fixed-order power series, reproducible on
+    any IEEE machine) against numpy's: within 2e-15 absolute over [-20, 20]
+    (joint angles are in [0, 0.6] here; a few 1e-16 there), exact at 0, and
+    relatively accurate for tiny angles (sin a = a - a^3/6 ...)."""
+    a = np.concatenate([np.linspace(-20, 20, 4001), np.linspace(0, 0.6, 1001), [np.pi / 2, np.pi, -np.pi]])
+    cs = np.array([O.cos_sin(v) for v in a])
+    assert np.abs(cs[:, 0] - np.cos(a)).max() <= 2e-15
+    assert np.abs(cs[:, 1] - np.sin(a)).max() <= 2e-15
+    small = (a >= 0) & (a <= 0.6)
+    assert np.abs(cs[small, 0] - np.cos(a[small])).max() <= 5e-16
+    assert np.abs(cs[small, 1] - np.sin(a[small])).max() <= 5e-16
+    assert O.cos_sin(0.0) == (1.0, 0.0)
+    c, s_ = O.cos_sin(1e-9)
+    assert abs(s_ - 1e-9) <= 1e-25 and c == 1.0
+
+
 def test_chain_rotations_match_scipy_composition():
     sc = S.make_scene("full", 1)
     table, mlp = S.make_field(sc, 1)
@@ -179,6 +196,45 @@ def test_multistart_roots_are_a_subset_of_bruteforce_roots():
     assert found >= 10
     # roots the bone-wise starts do not reach are a property of the method, reported here
     print(f"multi-start found {found} roots, brute force {found + missed}")
+
+
+def test_broyden_start_reading_keeps_the_root_set():
+    """Reading of Broyden's initial inverse Jacobian (not stated; Fast-SNARF
+    style): the oracle and the library start from the Jacobian of LBS with the
+    skinning weights frozen at x0, (sum_i w_i(x0) R_i)^-1, where the analytic
+    J(x0)^-1 adds the weight-gradient term.  Pin: the two initialisations find
+    the same root set -- on the brute-force cases (tiny chain at R_w = 8, both
+    sets inside the brute-force lattice roots), and on points near the body and
+    uniform points of the tiny and full-size scenes (which also select the same
+    root: same density, colour and canonical point)."""
+    cases = [("tiny", 8, 10, True), ("tiny", None, 200, False), ("full", None, 60, False)]
+    for cfg, rw, n, brute in cases:
+        sc = S.make_scene(cfg, 0, skin_res=rw)
+        table, mlp = S.make_field(sc, 0)
+        fz = O.OracleModel(sc, table, mlp)
+        an = O.OracleModel(sc, table, mlp, h0_analytic=True)
+        its = [0, 0]
+        for seed in (6, 7):
+            p, q = fz.pose(*S.make_pose(sc, seed)), an.pose(*S.make_pose(sc, seed))
+            pts = np.concatenate([_points_near_body(sc, fz, p, n, seed), S.random_points(sc, n // 3, seed=seed)])
+            for xn in pts.astype(np.float64):
+                ra, _, _ = fz.roots(p, xn)
+                rb, _, _ = an.roots(q, xn)
+                assert len(ra) == len(rb)
+                for r in ra:
+                    assert np.min(np.linalg.norm(rb - r, axis=1)) < 1e-9
+                if brute and len(ra):
+                    bf = fz.bruteforce_roots(p, xn, n=40, seed_thresh=0.08)
+                    assert all(np.min(np.linalg.norm(bf - r, axis=1)) < 1e-6 for r in ra)
+                sa, sb = fz.posed_field(p, xn), an.posed_field(q, xn)
+                assert sa["start"] >= 0 if sb["start"] >= 0 else sa["start"] < 0
+                if sa["start"] >= 0:
+                    np.testing.assert_allclose(sa["xstar"], sb["xstar"], atol=1e-9)
+                    np.testing.assert_allclose(sa["sigma"], sb["sigma"], rtol=1e-9)
+                its[0] += sa["iters"]
+                its[1] += sb["iters"]
+        print(f"{cfg} R_w={rw or sc.skin_res}: same roots; Broyden updates frozen-weight start {its[0]}, "
+              f"analytic start {its[1]}")
 
 
 # ---------------------------------------------------------- canonical field

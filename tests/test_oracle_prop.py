@@ -116,3 +116,37 @@ def test_proposal_search_finds_roots_of_the_plain_search(setup):
         assert s["start"] >= 0
         assert np.min(np.linalg.norm(roots - s["xstar"], axis=1)) < 1e-8
     print(f"untrained proposal: {fallbacks} of 60 samples fell back to the plain search")
+
+
+def test_render_with_every_bone_proposed_is_the_plain_render():
+    """Special case of the proposal-mode render (or_render_pixels_prop): a
+    network that proposes every bone (top_k = n_bones) with a zero start offset
+    starts each sample's search from exactly the paper's bone-wise starts, only
+    in the order of its (seeded, sample-dependent) logits, so the root set and
+    the max-density root are the plain search's and the frame must equal the
+    plain render (or_render_pixels) ray for ray, over the whole 64 x 64 tiny
+    frame.  A proposal search only falls back when none of its starts finds a
+    root, so with every bone proposed a fallback re-runs the same search: the
+    colours stay equal and each ray's fallbacks are at most its samples."""
+    sc = S.make_scene("tiny", 0)
+    table, mlp = S.make_field(sc, 0)
+    om = O.OracleModel(sc, table, mlp)
+    cfg = dict(S.proposal_config(), top_k=sc.n_bones)
+    pt, pm = S.proposal_init(sc, cfg, 2)
+    pm["W4"][sc.n_bones:] = 0.0  # zero start offset
+    pm["b4"][sc.n_bones:] = 0.0
+    pr = PP.PropModel(om, cfg, pt, pm)
+    th, tr = S.make_pose(sc, 3)
+    p = om.pose(th, tr)
+    _, bits = om.occupancy(p)
+    cam = S.make_camera(sc)
+    pix = np.arange(cam["width"] * cam["height"], dtype=np.int32)
+    plain = om.render_pixels(p, cam, bits, pix)
+    prop = pr.render_pixels(p, th, cam, bits, pix)
+    np.testing.assert_array_equal(prop["nsamp"], plain["nsamp"])
+    assert plain["nsamp"].sum() > 2000 and (plain["alpha"] > 0.01).sum() > 100
+    ok = ((prop["flags"] | plain["flags"]) & O.FLAG_TIE) == 0  # exact density ties may pick either root
+    assert ok.mean() > 0.99
+    np.testing.assert_allclose(prop["rgb"][ok], plain["rgb"][ok], rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(prop["alpha"][ok], plain["alpha"][ok], rtol=1e-9, atol=1e-12)
+    assert np.all(prop["fallbacks"] <= prop["nsamp"])

@@ -10,8 +10,12 @@ Workload (one step = one animated frame, the whole forward hot path):
 
 `value` is frames/s over all ranks (replicas: every rank renders its own frames,
 no collective on the data path).  L2 is flushed (256 MiB write) before every
-timed step.  `--impl reference` times the fp64 CPU oracle on bounded samples of
-the same workload.
+timed step.  The line also carries the metric's other parts (fp16 + proposal
+frames/s and samples/s, fwd+bwd train-step times), per-kernel rooflines (work
+per launch from the library's counters over per-launch device times from its
+launch tracing), the correspondence residual of both searches, the training
+quality run and the empty-space-skipping ablation.  `--impl reference` times
+the fp64 CPU oracle on bounded samples of the same workload.
 """
 from __future__ import annotations
 
@@ -44,15 +48,14 @@ FLOP_START = 306       # x0 = N_k^-1 x', LBS value (8-corner trilinear blend of 
 FLOP_ITER = 320        # Broyden step: H r, LBS value, residual difference, rank-one update of H
 FLOP_ROOT = 620 + 960 + 12800 + 40  # Newton polish with the analytic Jacobian, hash encoding, MLP, activations
 FLOP_SAMPLE = 20       # alpha, transmittance, colour accumulation
-GATHER_LBS = 8 * 48    # bytes of the blended grid one LBS evaluation reads
-GATHER_HASH = 16 * 8 * 8  # bytes of the fp32 hash table one field evaluation reads
-# DRAM bytes (read + write) of one render_kernel<1, fp32> launch on this workload,
-# from the ncu capture summarised in profiles/render_kernel_540x540_fp32.md; the
-# ncu-measured busiest unit of that launch is reported beside the roofline
-RENDER_DRAM_BYTES = 51.910e6 + 2.344e6
-RENDER_LIMITER = {"unit": "L1 (blended-grid gathers)", "l1tex_throughput_pct": 53.6, "issue_active_pct": 34.0,
-                  "fma_pipe_pct": 19.6, "l1_hit_pct": 90.1, "l2_hit_pct": 97.0, "simt_lanes_per_inst": 18.0,
-                  "source": "profiles/render_kernel_540x540_fp32.md"}
+FLOP_MLP_BWD = 12800 + 25600        # recomputed MLP forward + its backward, per sample
+# Algorithmic bytes, from the data each step must touch (not from what a kernel
+# happens to load):
+GATHER_LBS = 8 * 48          # one LBS evaluation: 8 corners of the blended grid, 3 x float4 each
+GATHER_HASH = 16 * 8 * 8     # one field evaluation: 16 levels x 8 corners x 2 fp32 features
+GATHER_HASH_H = 16 * 8 * 4   # the same from the fp16 shadow table
+GATHER_PROP = 8 * 8 * 8      # one proposal evaluation: 8 levels x 8 corners x 2 fp32 features
+WGRAD_ROW_BYTES = 384 * 2    # the weight-gradient GEMM streams one 384-row fp16 column per sample
 
 
 def fp32_peak_tflops(sm_mhz: float) -> float:
@@ -304,7 +307,7 @@ def time_train_step(torch, ia, sc, table, mlp, flush, steps, warmup, stream, n_r
 
 
 def train_quality(torch, ia, sc, table, mlp, prop=None, iters=2000, batch=8192, n_frames=16, eval_every=250,
-                  lr=1e-2, start=("scratch",)):
+                  lr=1e-2, start=("scratch",), skip=True, stop_db=None):
     """Time to quality of the whole training loop (Sec. 3.3-3.4) on a synthetic
     video: 16 frames of 540x540 rendered by the library from the fixture field
     (targets: colour and alpha mask), a learner that starts from an untrained
@@ -313,7 +316,11 @@ def train_quality(torch, ia, sc, table, mlp, prop=None, iters=2000, batch=8192, 
     surface) and the density regulariser on 8192 random points, an Adam step;
     every 16 iterations a training-mode occupancy update from a random frame.
     PSNR of a held-out frame is taken every eval_every iterations (outside the
-    timed total)."""
+    timed total).  skip=False is the Table 3 ablation: no occupancy grid (every
+    cell occupied, root culling off, so every sample of every ray is searched
+    and evaluated, in training and in the evaluation renders), and therefore no
+    occupancy-based regulariser and no grid updates.  stop_db: end the run at
+    the first evaluation at or above this PSNR."""
     dev = "cuda"
     poses = [S.make_pose(sc, 300 + i) for i in range(n_frames + 1)]  # the last one is held out
     th = np.stack([p[0] for p in poses])
@@ -346,8 +353,16 @@ def train_quality(torch, ia, sc, table, mlp, prop=None, iters=2000, batch=8192, 
     gen = torch.Generator(device=dev)
     gen.manual_seed(123)
     frame_rng = np.random.default_rng(124)
-    for i in range(n_frames):  # the sequence grid from every frame once
-        ia.ia_update_occupancy_ema(ctx, i, None, 1.0 if i else 0.0)
+    full = all_occupied(R)
+    if skip:
+        for i in range(n_frames):  # the sequence grid from every frame once
+            ia.ia_update_occupancy_ema(ctx, i, None, 1.0 if i else 0.0)
+        grid = ia.IA_OCC_UNION
+    else:
+        ia.ia_set_occupancy_culling(ctx, False)
+        ia.ia_set_occupancy(ctx, full)
+        grid = ia.IA_OCC_POSE
+    reg_w = 0.1 if skip else 0.0
     nt, nm = ia.ia_param_sizes(ctx)
     ns, nbn = ia.ia_grad_sizes(ctx)
     g = dict(table=torch.zeros(nt, device=dev), mlp=torch.zeros(nm, device=dev), skin=torch.zeros(ns, device=dev),
@@ -359,7 +374,10 @@ def train_quality(torch, ia, sc, table, mlp, prop=None, iters=2000, batch=8192, 
     ext = torch.from_numpy((sc.norm_max - sc.norm_min).astype(np.float32)).to(dev)
 
     def psnr():
-        ia.ia_update_occupancy(ctx, n_frames)
+        if skip:
+            ia.ia_update_occupancy(ctx, n_frames)
+        else:
+            ia.ia_set_occupancy(ctx, full)
         ia.ia_render(ctx, n_frames, icam, eval_rgb, eval_a)
         mse = torch.mean((eval_rgb - T_rgb[n_frames]) ** 2).item()
         return float(10 * np.log10(1.0 / max(mse, 1e-12)))
@@ -369,8 +387,8 @@ def train_quality(torch, ia, sc, table, mlp, prop=None, iters=2000, batch=8192, 
     f = torch.randint(0, n_frames, (batch,), device=dev, dtype=torch.int32)
     px = torch.randint(0, HW, (batch,), device=dev)
     ia.ia_train_step(ctx, O[px].contiguous(), D[px].contiguous(), f, T_rgb[f.long(), px].contiguous(), loss, g,
-                     occ_grid=ia.IA_OCC_UNION, alpha_target=T_a[f.long(), px].contiguous(),
-                     reg_x=(nmin + ext * torch.rand(batch, 3, device=dev)).contiguous(), reg_pose=f, reg_weight=0.1)
+                     occ_grid=grid, alpha_target=T_a[f.long(), px].contiguous(),
+                     reg_x=(nmin + ext * torch.rand(batch, 3, device=dev)).contiguous(), reg_pose=f, reg_weight=reg_w)
     torch.cuda.synchronize()
     timed = 0.0
     skips = 0
@@ -384,10 +402,10 @@ def train_quality(torch, ia, sc, table, mlp, prop=None, iters=2000, batch=8192, 
         rp = torch.randint(0, n_frames, (batch,), device=dev, generator=gen, dtype=torch.int32)
         loss.zero_()
         ia.ia_train_step(ctx, O[px].contiguous(), D[px].contiguous(), f, T_rgb[f.long(), px].contiguous(), loss, g,
-                         occ_grid=ia.IA_OCC_UNION, alpha_target=T_a[f.long(), px].contiguous(), reg_x=rx.contiguous(),
-                         reg_pose=rp, reg_weight=0.1)
+                         occ_grid=grid, alpha_target=T_a[f.long(), px].contiguous(), reg_x=rx.contiguous(),
+                         reg_pose=rp, reg_weight=reg_w)
         ia.ia_adam_step(ctx, g["table"], g["mlp"], lr, 0.9, 0.99, 1e-15)
-        if it % 16 == 0:
+        if skip and it % 16 == 0:
             jit = torch.rand(R ** 3, 3, device=dev, generator=gen)
             ia.ia_update_occupancy_ema(ctx, int(frame_rng.integers(0, n_frames)), jit, 0.95)
         torch.cuda.synchronize()
@@ -398,32 +416,40 @@ def train_quality(torch, ia, sc, table, mlp, prop=None, iters=2000, batch=8192, 
             skips += int(skipped)
         if it % eval_every == 0 or it == iters:
             curve.append((it, round(timed, 3), round(psnr(), 3)))
+            if stop_db is not None and curve[-1][2] >= stop_db:
+                break
     ia.ia_destroy(ctx)
     reach = {}
     for db in (30, 40, 50):
         hit = [c for c in curve if c[2] >= db]
         reach[f"{db}dB"] = {"iteration": hit[0][0], "seconds": hit[0][1]} if hit else None
-    return {"iterations": iters, "batch_rays": batch, "frames": n_frames, "seconds": round(timed, 3),
-            "time_to_psnr": reach,
-            "iters_per_s": round(iters / timed, 1), "psnr_curve": curve, "loss_every_50": losses[:8] + losses[-4:],
+    done = curve[-1][0]
+    return {"iterations": done, "batch_rays": batch, "frames": n_frames, "seconds": round(timed, 3),
+            "skipping": skip, "time_to_psnr": reach,
+            "iters_per_s": round(done / timed, 1), "psnr_curve": curve, "loss_every_50": losses[:8] + losses[-4:],
             "psnr_start": curve[0][2], "psnr_end": curve[-1][2], "start": list(start),
             "skipped_steps_seen": skips,
             "what": "fp16 step (+proposal) with Huber/alpha/hard losses and the density regulariser, Adam, "
                     "training-mode occupancy every 16 iterations; PSNR on a held-out frame"}
 
 
-def skip_ablation(torch, ia, sc, table, mlp, icam, rgb, alpha, stream, poses, frames=2):
+def all_occupied(R):
+    """Packed occupancy bits with every cell occupied."""
+    full = np.full((R ** 3 + 31) // 32, 0xFFFFFFFF, dtype=np.uint32)
+    if R ** 3 % 32:
+        full[-1] = (1 << (R ** 3 % 32)) - 1
+    return full
+
+
+def skip_ablation(torch, ia, sc, table, mlp, icam, rgb, alpha, stream, poses, frames=10):
     """Empty-space skipping on and off (the Table 3 analogue): plain fp32 render
     of a frame with the pose's occupancy grid (and root culling) against an
     all-occupied grid with root culling off, and a fp32 training step (8192 rays,
     16 poses) on the union grid (and root culling) against an all-occupied grid
     with root culling off: 'off' searches every sample."""
     ctx = make_ctx(torch, ia, sc, table, mlp, 0, EARLY_T)
-    R = sc.occ_res
-    full = np.full((R ** 3 + 31) // 32, 0xFFFFFFFF, dtype=np.uint32)
-    if R ** 3 % 32:
-        full[-1] = (1 << (R ** 3 % 32)) - 1
-    out = {}
+    full = all_occupied(sc.occ_res)
+    out = {"frames": frames}
     for name, skip in (("skip", True), ("no_skip", False)):
         ia.ia_set_occupancy_culling(ctx, skip)
         ms = []
@@ -458,7 +484,7 @@ def skip_ablation(torch, ia, sc, table, mlp, icam, rgb, alpha, stream, poses, fr
     for name, grid in (("skip", ia.IA_OCC_UNION), ("no_skip", ia.IA_OCC_POSE)):
         ia.ia_set_occupancy_culling(ctx, grid == ia.IA_OCC_UNION)
         ms = []
-        for it in range(4):
+        for it in range(11):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             ia.ia_train_step(ctx, dev["origin"], dev["direction"], dev["pose"], dev["target"], loss, g, occ_grid=grid,
@@ -496,6 +522,141 @@ def gather_peaks(torch, ia, stream, num_sms):
     return out
 
 
+# ------------------------------------------------------------------ per-kernel measurement
+
+def profile_frames(ia, ctx, poses, icam, rgb, alpha, frames):
+    """Per-kernel device times (library launch tracing: CUDA events around each
+    launch on its stream) over `frames` animated frames (pose + occupancy
+    refresh + render): {kernel: (launches per frame, ms per launch)}."""
+    import torch
+    torch.cuda.synchronize()
+    ia.ia_profile_begin()
+    for i in range(frames):
+        th, tr = poses[i % len(poses)]
+        ia.ia_set_pose(ctx, th[None], tr[None])
+        ia.ia_update_occupancy(ctx, 0, ia.IA_OCC_POSE)
+        ia.ia_render(ctx, 0, icam, rgb, alpha)
+    prof = ia.ia_profile_end()
+    return {k: (n / frames, tot / n) for k, (n, tot, _) in prof.items()}
+
+
+def profile_train(torch, ia, sc, table, mlp, steps, n_rays, precision, prop=None):
+    """Per-kernel device times of the training step (as time_train_step sets it
+    up) and its counters: ({kernel: (launches per step, ms per launch)}, stats)."""
+    ctx = make_ctx(torch, ia, sc, table, mlp, precision, 0.0)
+    poses = [S.make_pose(sc, 200 + i) for i in range(16)]
+    ia.ia_set_pose(ctx, np.stack([p[0] for p in poses]), np.stack([p[1] for p in poses]))
+    for i in range(16):
+        ia.ia_update_occupancy(ctx, i, ia.IA_OCC_UNION)
+    if prop is not None:
+        pc = S.proposal_config()
+        ia.ia_proposal_init(ctx, ia.make_proposal_config(pc["n_levels"], pc["log2_table"], pc["level_res"],
+                                                         pc["top_k"], pc["offset_weight"]))
+        ia.ia_proposal_set_params(ctx, prop[0], prop[1])
+        ia.ia_set_search(ctx, ia.IA_SEARCH_PROPOSAL)
+    rb = S.make_ray_batch(sc, n_rays, 16, seed=3)
+    dev = {k: torch.from_numpy(np.ascontiguousarray(rb[k])).cuda() for k in ("origin", "direction", "pose", "target")}
+    nt, nm = ia.ia_param_sizes(ctx)
+    ns, nbn = ia.ia_grad_sizes(ctx)
+    g = dict(table=torch.zeros(nt, device="cuda"), mlp=torch.zeros(nm, device="cuda"),
+             skin=torch.zeros(ns, device="cuda"), bones=torch.zeros(nbn, device="cuda"))
+    loss = torch.zeros(1, device="cuda")
+    for _ in range(2):  # workspaces and culling masks
+        ia.ia_train_step(ctx, dev["origin"], dev["direction"], dev["pose"], dev["target"], loss, g,
+                         occ_grid=ia.IA_OCC_UNION)
+    torch.cuda.synchronize()
+    ia.ia_profile_begin()
+    for _ in range(steps):
+        ia.ia_train_step(ctx, dev["origin"], dev["direction"], dev["pose"], dev["target"], loss, g,
+                         occ_grid=ia.IA_OCC_UNION)
+    prof = ia.ia_profile_end()
+    st = ia.ia_train_stats(ctx)
+    ia.ia_destroy(ctx)
+    return {k: (n / steps, tot / n) for k, (n, tot, _) in prof.items()}, st
+
+
+def lbs_residual(sc, N, x_canon, x_posed):
+    """|LBS(x*) - x'| in fp64 for canonical points x* [n, 3] and their posed
+    points x' [n, 3] (normalised space): trilinear skinning weights of the grid
+    (vertices at the canonical box's corners, clamped to the border), the
+    pose's fp32 transforms N [nb, 3, 4] as the library stores them."""
+    R = sc.skin_res
+    W = sc.skin_grid.reshape(R, R, R, sc.n_bones).astype(np.float64)
+    lo, hi = sc.canon_min.astype(np.float64), sc.canon_max.astype(np.float64)
+    u = np.clip((x_canon - lo) / (hi - lo) * (R - 1), 0, R - 1)
+    i0 = np.minimum(np.floor(u).astype(np.int64), R - 2)
+    f = u - i0
+    w = np.zeros((len(x_canon), sc.n_bones))
+    for c in range(8):
+        d = np.array([c & 1, (c >> 1) & 1, (c >> 2) & 1])
+        wt = np.prod(np.where(d, f, 1 - f), axis=1)
+        v = i0 + d
+        w += wt[:, None] * W[v[:, 2], v[:, 1], v[:, 0]]
+    xh = np.concatenate([x_canon, np.ones((len(x_canon), 1))], axis=1)
+    y = np.einsum("nb,bij,nj->ni", w, N.astype(np.float64), xh)
+    return np.linalg.norm(y - x_posed, axis=1)
+
+
+def residual_stats(torch, ia, sc, ctx_plain, ctx_prop, pose, n=32768):
+    """Correspondence residual and colour of the selected roots of both searches
+    at the same posed points (uniform in the occupied cells of the pose's grid):
+    LBS residual of each path's roots, their distance, and the colour and
+    density differences between the paths."""
+    th, tr = pose
+    R = sc.occ_res
+    bits = torch.zeros((R ** 3 + 31) // 32, dtype=torch.int32, device="cuda")
+    out = {}
+    for name, ctx in (("fp32_plain", ctx_plain), ("fp16_proposal", ctx_prop)):
+        ia.ia_set_pose(ctx, th[None], tr[None])
+        ia.ia_update_occupancy(ctx, 0, ia.IA_OCC_POSE, None, bits)
+        if name == "fp32_plain":
+            x = occupied_points(bits.cpu().numpy().view(np.uint32), sc, n, np.random.default_rng(99))
+            xd = torch.from_numpy(x).cuda()
+            N = np.zeros((sc.n_bones, 12), np.float32)
+            ia.ia_get_transforms(ctx, 0, N)
+        sig, rgb, xc = (torch.zeros(n, device="cuda"), torch.zeros(n, 3, device="cuda"),
+                        torch.zeros(n, 3, device="cuda"))
+        start = torch.zeros(n, dtype=torch.int32, device="cuda")
+        ia.ia_query_posed(ctx, 0, xd, sig, rgb, xc, start)
+        torch.cuda.synchronize()
+        out[name] = dict(sigma=sig.cpu().numpy(), rgb=rgb.cpu().numpy(), xc=xc.cpu().numpy().astype(np.float64),
+                         has=start.cpu().numpy() >= 0)
+    a, b = out["fp32_plain"], out["fp16_proposal"]
+    both = a["has"] & b["has"]
+    res = {}
+    for name, o in out.items():
+        r = lbs_residual(sc, N.reshape(-1, 3, 4), o["xc"][o["has"]], x.astype(np.float64)[o["has"]])
+        res[name] = {"mean": float(r.mean()), "max": float(r.max()), "p99": float(np.quantile(r, 0.99)),
+                     "with_root": int(o["has"].sum())}
+    dx = np.linalg.norm(a["xc"][both] - b["xc"][both], axis=1)
+    drgb = np.abs(a["rgb"][both] - b["rgb"][both]).max(axis=1)
+    return {"points": n, "lbs_residual_m": res, "root_presence_differs": int((a["has"] != b["has"]).sum()),
+            "root_distance_m": {"mean": float(dx.mean()), "p99": float(np.quantile(dx, 0.99)), "max": float(dx.max()),
+                                "over_1e-4": int((dx > 1e-4).sum())},
+            "colour_abs_diff": {"mean": float(drgb.mean()), "p99": float(np.quantile(drgb, 0.99))},
+            "what": "posed points uniform in the occupied cells of one pose's grid; selected roots of the plain "
+                    "fp32 24-start search and of the fp16 + proposal search (ia_query_posed), residual "
+                    "|LBS(x*) - x'| in fp64 with the stored fp32 transforms"}
+
+
+def roofline_entry(kernel, bound, work, unit_work, ms, peak, peak_unit, peak_source, what):
+    """work per launch (bytes or FLOPs) over the measured launch time, against a peak."""
+    achieved = work / (ms * 1e-3) / (1e9 if peak_unit == "GB/s" else 1e12)
+    return {"kernel": kernel, "bound": bound, "achieved": round(achieved, 2), "peak": round(peak, 2),
+            "unit": peak_unit, "frac": round(achieved / peak, 4), "work_per_launch": round(work),
+            "work_unit": unit_work, "ms_per_launch": round(ms, 4), "peak_source": peak_source, "work": what}
+
+
+def frame_gather_bytes(st, hash_bytes, prop=False):
+    """Algorithmic gather bytes of a posed-field pass from its counters: one LBS
+    evaluation per start and Broyden step, per distinct root its polish (one
+    more LBS) and hash encoding, per proposed sample the proposal's encoding."""
+    b = GATHER_LBS * (st["starts"] + st["broyden_iters"]) + (GATHER_LBS + hash_bytes) * st["roots"]
+    return b + (GATHER_PROP * st["proposed"] if prop else 0)
+
+
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2212_10550_b300 as ia
@@ -530,17 +691,45 @@ def run_ours(args, rank, world, local_rank):
         ab = skip_ablation(torch, ia, sc, table, mlp, icam, rgb, alpha, stream, poses)
         return {"metric": METRIC, "partial": "skip ablation only", "skip_ablation": ab} if rank == 0 else None
 
+    if args.only == "profile":
+        # per-kernel launch times of the frames and train steps (launch tracing), short
+        ctx = make_ctx(torch, ia, sc, table, mlp, 0, EARLY_T)
+        frame_stats(ia, ctx, poses[:2], icam, rgb, alpha)
+        pf = profile_frames(ia, ctx, poses, icam, rgb, alpha, max(4, args.steps))
+        ia.ia_destroy(ctx)
+        ctx16 = make_ctx(torch, ia, sc, table, mlp, 1, EARLY_T)
+        pt = train_proposal(torch, ia, ctx16, sc, n_poses=64, steps=400)
+        ia.ia_set_search(ctx16, ia.IA_SEARCH_PROPOSAL)
+        frame_stats(ia, ctx16, poses[:2], icam, rgb, alpha)
+        pf16 = profile_frames(ia, ctx16, poses, icam, rgb, alpha, max(4, args.steps))
+        pnt, pnm = ia.ia_proposal_param_sizes(ctx16)
+        pp = (torch.zeros(pnt, device=dev), torch.zeros(pnm, device=dev))
+        ia.ia_proposal_get_params(ctx16, *pp)
+        ia.ia_destroy(ctx16)
+        tr = {n: profile_train(torch, ia, sc, table, mlp, 5, 32768, prec, q)[0]
+              for n, prec, q in (("fp32", 0, None), ("fp16", 1, None), ("fp16_proposal", 1, pp))}
+        if rank != 0:
+            return None
+        fmt = lambda d: {k: [round(n, 2), round(ms, 4)] for k, (n, ms) in d.items()}  # noqa: E731
+        return {"metric": METRIC, "partial": "per-kernel launch times ([launches per unit, ms per launch])",
+                "frame_fp32": fmt(pf), "frame_fp16_proposal": fmt(pf16),
+                "train_step_32768": {n: fmt(d) for n, d in tr.items()}, "proposal_training": pt}
+
     if args.only == "quality":
         q = train_quality(torch, ia, sc, table, mlp, None, iters=max(50, args.steps), eval_every=100)
-        return {"metric": METRIC, "partial": "training quality only", "train_quality": q} if rank == 0 else None
+        q_off = train_quality(torch, ia, sc, table, mlp, None, iters=max(50, args.steps), eval_every=100, skip=False,
+                              stop_db=50.0)
+        return ({"metric": METRIC, "partial": "training quality only", "train_quality": q,
+                 "train_quality_no_skip": q_off} if rank == 0 else None)
+
 
     if args.only == "train":
         tsteps = max(3, args.steps)
-        res = {name: time_train_step(torch, ia, sc, table, mlp, flush, tsteps, args.warmup, stream, n_rays=32768,
-                                     precision=prec) for name, prec in (("fp32", 0), ("fp16", 1))}
+        res = {name: time_train_step(torch, ia, sc, table, mlp, flush, tsteps, args.warmup, stream,
+                                     n_rays=args.train_rays, precision=prec) for name, prec in (("fp32", 0), ("fp16", 1))}
         if rank != 0:
             return None
-        return {"metric": METRIC, "value": res["fp16"]["ms"], "unit": "ms per fp16 training step (32768 rays)",
+        return {"metric": METRIC, "value": res["fp16"]["ms"], "unit": f"ms per fp16 training step ({args.train_rays} rays)",
                 "n_gpus": world, "steps": tsteps, "warmup": args.warmup, "higher_is_better": False,
                 "train_step_32768": res, "partial": "training steps only"}
 
@@ -564,6 +753,7 @@ def run_ours(args, rank, world, local_rank):
     wall = time.perf_counter() - t0
     clk = clocks.stop()
     local_total_s = sum(step_ms) / 1e3
+    prof_plain = profile_frames(ia, ctx, poses, icam, rgb, alpha, 8)
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside
     h_rgb = torch.empty(W * H, 3, dtype=torch.float32, pin_memory=True).numpy()
@@ -580,15 +770,16 @@ def run_ours(args, rank, world, local_rank):
         e2e_s.append(time.perf_counter() - t)
     occ_cull_ms = time_occupancy(torch, ia, ctx, poses, flush, 16, stream, True)
     occ_full_ms = time_occupancy(torch, ia, ctx, poses, flush, 16, stream, False)
-    ia.ia_destroy(ctx)
 
     if args.only == "plain":
+        ia.ia_destroy(ctx)
         total = sum(step_ms) / 1e3
         if rank == 0:
-            return {"metric": METRIC, "value": round(args.steps / total, 3), "unit": "frames/s (plain fp32 only)",
+            return {"metric": METRIC, "value": round(args.steps / total, 3), "unit": "frames/s",
                     "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                     "ms_per_step": round(1e3 * total / args.steps, 4), "higher_is_better": True,
                     "render_ms": round(statistics.mean(render_ms), 4),
+                    "kernels_per_frame": {k: [round(n, 2), round(ms, 4)] for k, (n, ms) in prof_plain.items()},
                     "occupancy_refresh": {"culled_ms": round(occ_cull_ms, 4), "full_search_ms": round(occ_full_ms, 4)},
                     "partial": "plain fp32 frames only"}
         return None
@@ -609,19 +800,33 @@ def run_ours(args, rank, world, local_rank):
         hit += int((a0 > 0).sum().item())
     step16, render16 = time_frames(torch, ia, ctx16, poses, icam, rgb, alpha, flush, args.steps, args.warmup,
                                    stream)
+    prof16 = profile_frames(ia, ctx16, poses, icam, rgb, alpha, 8)
+    residual = residual_stats(torch, ia, sc, ctx, ctx16, poses[1])
     pnt, pnm = ia.ia_proposal_param_sizes(ctx16)
     prop_params = (torch.zeros(pnt, device=dev), torch.zeros(pnm, device=dev))
     ia.ia_proposal_get_params(ctx16, *prop_params)
     ia.ia_destroy(ctx16)
+    ia.ia_destroy(ctx)
 
     # ---- fwd+bwd training steps: fp32 at 8192 rays; fp32 / fp16 / bf16 / fp16+proposal at 32768 rays
     tsteps = max(5, args.steps // 10)
     train = {"fp32_8192": time_train_step(torch, ia, sc, table, mlp, flush, tsteps, 3, stream)}
-    quality = train_quality(torch, ia, sc, table, mlp, prop_params, iters=2000, eval_every=100)
-    ablation = skip_ablation(torch, ia, sc, table, mlp, icam, rgb, alpha, stream, poses)
     for name, prec, pp in (("fp32", 0, None), ("fp16", 1, None), ("bf16", 2, None), ("fp16_proposal", 1, prop_params)):
         train[name] = time_train_step(torch, ia, sc, table, mlp, flush, tsteps, 3, stream, n_rays=32768,
                                       precision=prec, prop=pp)
+    prof_train = {name: profile_train(torch, ia, sc, table, mlp, 5, 32768, prec, pp)
+                  for name, prec, pp in (("fp32", 0, None), ("fp16_proposal", 1, prop_params))}
+    quality = train_quality(torch, ia, sc, table, mlp, prop_params, iters=2000, eval_every=100)
+    quality_off = train_quality(torch, ia, sc, table, mlp, prop_params, iters=1000, eval_every=100, skip=False,
+                                stop_db=50.0)
+    ablation = skip_ablation(torch, ia, sc, table, mlp, icam, rgb, alpha, stream, poses)
+    ablation["train_time_to_psnr"] = {"skip": quality["time_to_psnr"], "no_skip": quality_off["time_to_psnr"],
+                                      "no_skip_curve": quality_off["psnr_curve"],
+                                      "no_skip_iters_per_s": quality_off["iters_per_s"]}
+    ablation["train_time_ratio"] = {
+        db: (round(quality_off["time_to_psnr"][db]["seconds"] / quality["time_to_psnr"][db]["seconds"], 2)
+             if quality_off["time_to_psnr"][db] and quality["time_to_psnr"][db] else None)
+        for db in ("30dB", "40dB", "50dB")}
 
     fps, total_s = job_rate(args.steps, local_total_s, world, dev)
     if rank != 0:
@@ -634,34 +839,102 @@ def run_ours(args, rank, world, local_rank):
                    FLOP_ROOT * per_frame["roots"] + FLOP_SAMPLE * per_frame["occupied_samples"])
     r_ms = statistics.mean(render_ms)
     achieved = flop_render / (r_ms * 1e-3) / 1e12
-    # the gathers of the search and the field: 8 corners x 48 B of the blended grid per
-    # LBS evaluation (start or Broyden step), and per distinct root its polish (one
-    # more LBS with the Jacobian) and the hash encoding (16 levels x 8 corners x 8 B)
-    gather_bytes = (GATHER_LBS * (per_frame["starts"] + per_frame["broyden_iters"]) +
-                    (GATHER_LBS + GATHER_HASH) * per_frame["roots"])
+    gather_bytes = frame_gather_bytes(per_frame, GATHER_HASH)
     g_achieved = gather_bytes / (r_ms * 1e-3) / 1e9
     peaks_g = gather_peaks(torch, ia, stream, torch.cuda.get_device_properties(0).multi_processor_count)
-    roofline_gather = {"kernel": "render_kernel", "bound": "l1-gather", "achieved": round(g_achieved, 1),
+    l1_src = "ia_gather_probe: random 48-byte records from a 64 KiB table (L1), measured in this run"
+    l2_src = "ia_gather_probe: random 48-byte records from a 12.6 MB table (L2), measured in this run"
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    hbm_src = f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else \
+        "fallback HBM figure"
+    tc = peaks.get("bf16_tflops", 1800.0)
+    roofline_gather = {"kernel": "render_kernel<fp32>", "bound": "l1-gather", "achieved": round(g_achieved, 1),
                        "peak": peaks_g["l1"], "unit": "GB/s", "frac": round(g_achieved / peaks_g["l1"], 4),
-                       "peak_l2_random": peaks_g["l2"], "bytes_per_frame": round(gather_bytes),
-                       "peak_source": "ia_gather_probe, random 48-byte records, 64 KiB table (L1) / 12.6 MB (L2), "
-                                      "measured in this run"}
+                       "traffic": None, "bytes_per_frame": round(gather_bytes), "peak_l2_random": peaks_g["l2"],
+                       "peak_source": l1_src,
+                       "traffic_note": "DRAM bytes per launch come from an ncu capture, not from this run",
+                       "bounds_ms": {"l1_gather": round(gather_bytes / (peaks_g["l1"] * 1e9) * 1e3, 3),
+                                     "fp32_alu": round(flop_render / (peak * 1e12) * 1e3, 3),
+                                     "measured": round(r_ms, 3)}}
+    # ---- per-kernel rooflines: work per launch from the counters, time per launch from launch tracing
+    kern = {}
+
+    def add(name, prof, bound, work, unit_work, pk, pk_unit, pk_src, what):
+        if name in prof:
+            kern[name] = roofline_entry(name, bound, work, unit_work, prof[name][1], pk, pk_unit, pk_src, what)
+
+    add("render_kernel<fp32>", prof_plain, "l1-gather", frame_gather_bytes(per_frame, GATHER_HASH), "B",
+        peaks_g["l1"], "GB/s", l1_src, "48 B x (starts + Broyden steps) + (48 B + 1 KiB hash) x roots, per frame")
+    add("render_kernel<fp16,proposal>", prof16, "l1-gather", frame_gather_bytes(per_frame16, GATHER_HASH_H, True),
+        "B", peaks_g["l1"], "GB/s", l1_src,
+        "48 B x (starts + Broyden steps) + (48 B + 512 B fp16 hash) x roots + 512 B per proposal evaluation")
+    add("occ_density_kernel<fp32>", prof_plain, "l1-gather", frame_gather_bytes(occ_per_frame, GATHER_HASH), "B",
+        peaks_g["l1"], "GB/s", l1_src, "the render's byte count over the searched occupancy cells")
+    add("occ_density_kernel<fp16,proposal>", prof16, "l1-gather", frame_gather_bytes(occ16, GATHER_HASH_H, True),
+        "B", peaks_g["l1"], "GB/s", l1_src, "as the proposal render, over the searched occupancy cells")
+    V = sc.skin_res ** 3
+    add("blend_kernel", prof_plain, "hbm", V * sc.n_bones * 4 + V * 48, "B", hbm, "GB/s", hbm_src,
+        "skinning grid read (64^3 x 24 fp32) + blended grid written (64^3 x 48 B)")
+    for tname, (tp, tst) in prof_train.items():
+        searched = tst["occupied_samples"] - tst["culled"]
+        hash_b = GATHER_HASH if tname == "fp32" else GATHER_HASH_H
+        sk = "train_sample_kernel<fp32>" if tname == "fp32" else "train_sample_kernel<fp16,proposal>"
+        add(sk, tp, "l1-gather", frame_gather_bytes(tst, hash_b, tname != "fp32"), "B", peaks_g["l1"], "GB/s",
+            l1_src, "posed field of the step's samples, byte count as the render's")
+        # per searched sample: table read for dL/dx*, hash-gradient atomics, skinning-grid
+        # atomics (8 corners x 24 bones), the Jacobian's blended-grid gather, dL/dfeatures and x*
+        per = hash_b + GATHER_HASH + 8 * sc.n_bones * 4 + GATHER_LBS + 128 + 16
+        if "train_scatter_kernel" in tp:
+            kern[f"train_scatter_kernel ({tname})"] = roofline_entry(
+                "train_scatter_kernel", "l2-gather", per * searched, "B", tp["train_scatter_kernel"][1], peaks_g["l2"],
+                "GB/s", l2_src, "per searched sample: table read + float2 hash atomics + skinning-grid atomics + "
+                "Jacobian gather + dL/dfeatures, L2-resident")
+        if tname != "fp32":
+            add("wgrad_tc_kernel", tp, "hbm", WGRAD_ROW_BYTES * searched, "B", hbm, "GB/s", hbm_src,
+                "the 384-row fp16 operand column of every searched sample, streamed once")
+            add("train_backward_h_kernel<fp16>", tp, "tensor", FLOP_MLP_BWD * searched, "FLOP", tc, "TFLOP/s",
+                f"{peak_kind} dense bf16 tensor peak (fp16 runs at the same rate)",
+                "MLP forward recompute + backward per searched sample")
+        else:
+            add("train_backward_kernel", tp, "alu", FLOP_MLP_BWD * searched, "FLOP", peak, "TFLOP/s",
+                f"fp32 FMA: 148 SM x 128 lanes x 2 x {sm_mhz:.0f} MHz", "MLP forward recompute + backward per sample")
+    launches_per_frame = sum(n for n, _ in prof_plain.values())
     m16 = statistics.mean(step16)
     line = {
         "metric": METRIC,
         "value": round(fps, 3),
-        "unit": "frames/s (540x540, pose + occupancy refresh + render, plain fp32)",
+        "unit": "frames/s",
+        # headline numbers of the metric's other parts (the FP16 + proposal path and the train steps)
+        "fp16_proposal_fps": round(1e3 / m16, 3),
+        "fp16_proposal_speedup": round(statistics.mean(step_ms) / m16, 3),
+        "samples_per_s": round(per_frame["occupied_samples"] * fps, 1),
+        "fp16_proposal_samples_per_s": round(per_frame16["occupied_samples"] * 1e3 / m16, 1),
+        "train_step_ms_fp32_8192": train["fp32_8192"]["ms"],
+        "train_step_ms_fp32_32768": train["fp32"]["ms"],
+        "train_step_ms_fp16_proposal_32768": train["fp16_proposal"]["ms"],
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms_per_step, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "l2": "flushed (256 MiB write) before every timed step",
-                   "parallelism": f"replicas x{world}", "precision": "fp32", "starts": "all 24 bones"},
-        "samples_per_s": round(per_frame["occupied_samples"] * fps, 1),
+                   "parallelism": f"replicas x{world}", "precision": "fp32", "starts": "all 24 bones",
+                   "value": "540x540 frames/s, pose + occupancy refresh + render, plain fp32"},
+        "roofline": roofline_gather,
+        "roofline_alu": {"kernel": "render_kernel<fp32>", "bound": "alu", "achieved": round(achieved, 3),
+                         "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                         "peak_source": f"fp32 FMA: 148 SM x 128 lanes x 2 x {sm_mhz:.0f} MHz ({peak_kind} max clock)",
+                         "flop_per_frame": round(flop_render)},
+        "rooflines": kern,
+        "correspondence": residual,
         "render_only_fps": round(1e3 / r_ms, 3),
         "mean_broyden_iters_per_sample": round(per_frame["broyden_iters"] / per_frame["occupied_samples"], 2),
         "per_frame": {k: round(v, 1) for k, v in per_frame.items()},
         "occupancy_per_frame": {k: round(v, 1) for k, v in occ_per_frame.items()},
+        "kernels_per_frame": {"fp32": {k: [round(n, 2), round(ms, 4)] for k, (n, ms) in prof_plain.items()},
+                              "fp16_proposal": {k: [round(n, 2), round(ms, 4)] for k, (n, ms) in prof16.items()},
+                              "what": "[launches per frame, ms per launch] from launch tracing over 8 frames"},
+        "kernels_per_train_step": {n: {k: [round(c, 2), round(ms, 4)] for k, (c, ms) in tp.items()}
+                                   for n, (tp, _) in prof_train.items()},
         "occupancy_refresh": {
             "culled_ms": round(occ_cull_ms, 4), "full_search_ms": round(occ_full_ms, 4),
             "speedup": round(occ_full_ms / occ_cull_ms, 2),
@@ -697,22 +970,10 @@ def run_ours(args, rank, world, local_rank):
                     "gradients; fp16 with dynamic loss scaling, weight gradients on tcgen05"},
         "train_quality": quality,
         "skip_ablation": ablation,
-        # the binding resource of the dominant kernel (the largest work / peak bound):
-        # its gathers through L1, against a random-gather peak measured in this run;
-        # the fp32 ALU view of the same kernel beside it
-        "roofline": dict(roofline_gather, traffic=RENDER_DRAM_BYTES, limiter=RENDER_LIMITER,
-                         bounds_ms={"l1_gather": round(gather_bytes / (peaks_g["l1"] * 1e9) * 1e3, 3),
-                                    "fp32_alu": round(flop_render / (peak * 1e12) * 1e3, 3),
-                                    "measured": round(r_ms, 3)}),
-        "roofline_alu": {"kernel": "render_kernel", "bound": "alu", "achieved": round(achieved, 3),
-                         "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                         "peak_source": f"fp32 FMA: 148 SM x 128 lanes x 2 x {sm_mhz:.0f} MHz ({peak_kind} max clock)",
-                         "flop_per_frame": round(flop_render)},
         "e2e": {"value": round(1.0 / statistics.mean(e2e_s), 3), "unit": "frames/s",
                 "h2d_bytes_per_step": int(sc.n_bones * 3 * 8 + 3 * 8),
                 "d2h_bytes_per_step": int(W * H * 4 * 4)},
-        # per step: pose chain, blend, culling masks, candidates, density, bits, render
-        "gpu_launches": 7 * args.steps,
+        "gpu_launches": int(round(launches_per_frame * args.steps)),
         "clocks": clk,
     }
     if not args.no_cpu_baseline and world == 1:
@@ -747,7 +1008,9 @@ def cpu_baseline(sc, table, mlp, pose, cam):
 def run_reference(args, rank, world):
     """The fp64 oracle on bounded samples of the workload: step i evaluates
     part i of 64 of one frame (a z-slab of the occupancy grid and every 64th
-    2-row stripe of the image) and scales each part's time by 64."""
+    2-row stripe of the image).  ms_per_step is the measured time of that
+    work; value (frames/s) divides the part's frame fraction by it, each of
+    the two parts scaled by its own fraction of the frame."""
     if rank != 0:
         return None
     import oracle as O
@@ -765,33 +1028,41 @@ def run_reference(args, rank, world):
         part = (i * 17) % n_parts
         z0, z1 = part * R // n_parts, (part + 1) * R // n_parts
         cells = np.arange(z0 * R * R, max(z1, z0 + 1) * R * R)
-        t = time.perf_counter()
-        om.occupancy_cells(p, cells, nthreads)
-        t_occ = time.perf_counter() - t
         rows = [r for r in range(H) if (r // 2) % n_parts == part]
         pix = np.concatenate([np.arange(r * W, (r + 1) * W) for r in rows]).astype(np.int32)
-        t = time.perf_counter()
+        t0 = time.perf_counter()
+        om.occupancy_cells(p, cells, nthreads)
+        t1 = time.perf_counter()
         om.render_pixels(p, cam, bits, pix, nthreads)
-        t_ren = time.perf_counter() - t
-        return t_occ * (R ** 3) / len(cells) + t_ren * H / len(rows)
+        t2 = time.perf_counter()
+        frame_s = (t1 - t0) * (R ** 3) / len(cells) + (t2 - t1) * H / len(rows)
+        return t2 - t0, frame_s
 
     for i in range(args.warmup):
         one(i)
-    est = []
+    step_s, frame_s = [], []
     t0 = time.perf_counter()
     for i in range(args.steps):
-        est.append(one(args.warmup + i))
+        a, b = one(args.warmup + i)
+        step_s.append(a)
+        frame_s.append(b)
     wall = time.perf_counter() - t0
-    fps = 1.0 / statistics.mean(est)
+    fps = 1.0 / statistics.mean(frame_s)
     return {"impl": "reference", "metric": METRIC, "value": round(fps, 5), "unit": "frames/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(1e3 * statistics.mean(est), 3), "higher_is_better": True,
+            "ms_per_step": round(1e3 * statistics.mean(step_s), 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "parallelism": f"{nthreads} host threads"},
+            "config": {"workload": WORKLOAD, "l2": "flushed (256 MiB write) before every timed step",
+                       "parallelism": f"{nthreads} host threads", "precision": "fp64", "starts": "all 24 bones",
+                       "value": "540x540 frames/s, pose + occupancy refresh + render, fp64 oracle"},
+            "work_per_step": f"1/{n_parts} of a frame: one z-slab of the 64^3 occupancy grid and every "
+                             f"{n_parts}th 2-row stripe of the 540 x 540 image",
+            "frame_ms_extrapolated": round(1e3 * statistics.mean(frame_s), 1),
             "wall_s": round(wall, 2),
             "cpu_baseline": {"value": round(fps, 5), "unit": "frames/s", "cores": nthreads, "kind": "oracle",
                              "sample": f"pose 0; per step 1/{n_parts} of the occupancy grid (a z-slab) and of "
-                                       "the image rows (2-row stripes), each part's time scaled by 64 to a frame"},
+                                       "the image rows (2-row stripes), each part's time divided by its fraction "
+                                       "of the frame"},
             "e2e": {"value": round(fps, 5), "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -802,9 +1073,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", default="all", choices=["all", "plain", "train", "quality", "ablation", "proposal"],
+    ap.add_argument("--train-rays", type=int, default=32768, help="rays per step of --only train")
+    ap.add_argument("--only", default="all", choices=["all", "plain", "train", "quality", "ablation", "proposal",
+                                                      "profile"],
                     help="plain: time only the plain fp32 frames; train: only the fp32 and fp16 training "
-                         "steps at 32768 rays (both used for profiling captures)")
+                         "steps (both used for profiling captures); profile: per-kernel launch times")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

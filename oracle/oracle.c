@@ -74,21 +74,24 @@ static double norm3(const double v[3]) { return sqrt(v[0] * v[0] + v[1] * v[1] +
 /* cos a and sin a from their Maclaurin series
      sin x = sum_k (-1)^k x^(2k+1) / (2k+1)!,   cos x = sum_k (-1)^k x^(2k) / (2k)!,
    after one reduction of a by the nearest multiple of 2 pi (fp64 constant),
-   each term from the previous one, t_{k+1} = t_k (-x^2) / ((2k+2)(2k+3)) for
-   sin and t_k (-x^2) / ((2k+1)(2k+2)) for cos, added in order; 22 terms (the
-   first omitted one is below pi^46 / 46! < 1e-32).  Every step is one
-   correctly rounded fp64 operation in a fixed order, so the values are the
-   same on any IEEE machine (the library's pose chain takes the same steps,
-   which keeps the fp32 bone transforms bit-identical); they agree with the C
-   library's cos / sin to a few 1e-16. */
+   each term from the previous one, t_{k+1} = t_k (-x^2) r_k with the
+   correctly rounded reciprocal r_k = 1 / ((2k+2)(2k+3)) for sin and
+   1 / ((2k+1)(2k+2)) for cos, added in order; 22 terms (the first omitted one
+   is below pi^46 / 46! < 1e-32).  Every step is one correctly rounded fp64
+   operation in a fixed order, so the values are the same on any IEEE machine
+   (the library's pose chain takes the same steps, which keeps the fp32 bone
+   transforms bit-identical); they agree with the C library's cos / sin to a
+   few 1e-16. */
 void or_cos_sin(double a, double *c, double *s) {
   const double two_pi = 6.283185307179586;
   const double x = a - rint(a / two_pi) * two_pi;
   const double mx2 = -(x * x);
   double ts = x, tc = 1.0, sn = x, cs = 1.0;
   for (int k = 0; k < 22; ++k) {
-    ts = ts * mx2 / (double)((2 * k + 2) * (2 * k + 3));
-    tc = tc * mx2 / (double)((2 * k + 1) * (2 * k + 2));
+    const double rs = 1.0 / (double)((2 * k + 2) * (2 * k + 3));
+    const double rc = 1.0 / (double)((2 * k + 1) * (2 * k + 2));
+    ts = ts * mx2 * rs;
+    tc = tc * mx2 * rc;
     sn = sn + ts;
     cs = cs + tc;
   }

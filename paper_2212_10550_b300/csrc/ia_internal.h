@@ -126,8 +126,8 @@ struct TrainArgs {
   float* g_bones;
   // reduced precision (prec != fp32): channel-major operands of the weight-gradient GEMM
   int prec;
-  uint16_t* X;           // [kWgRows][ld] fp16 / bf16
-  int64_t ld;            // multiple of 64
+  uint16_t* X;           // kWgRows x ld fp16 / bf16, chunk-contiguous (wg_index)
+  int64_t ld;            // samples X holds (a multiple of 64; layout wg_index)
   float* scale;          // dynamic loss scale (device scalar)
   int* overflow;         // the step's skip flags (kStepOverflow, kStepPipelineError)
   int* good_steps;       // steps since the last overflow

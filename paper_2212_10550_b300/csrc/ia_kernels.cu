@@ -32,22 +32,26 @@ __device__ __forceinline__ double DS(double a, double b) { return __dsub_rn(a, b
 
 // cos a and sin a of a joint's rotation angle, from their Maclaurin series:
 // a is reduced once by the nearest multiple of 2 pi (an fp64 constant), then
-// the terms t_{k+1} = t_k (-x^2) / ((2k+2)(2k+3)) (sin, from t_0 = x) and
-// t_k (-x^2) / ((2k+1)(2k+2)) (cos, from t_0 = 1) are formed and added in
-// order, 22 of them (the first omitted one is below pi^46 / 46! < 1e-32).
-// Each step is one correctly rounded fp64 operation in a fixed order, so the
-// values -- and the fp32 transforms made from them -- are reproducible on any
-// IEEE machine, which a library cos / sin (accurate to an ulp or two, by
+// the terms t_{k+1} = t_k (-x^2) r_k, with r_k = 1 / ((2k+2)(2k+3)) for sin
+// (from t_0 = x) and 1 / ((2k+1)(2k+2)) for cos (from t_0 = 1), are formed
+// and added in order, 22 of them (the first omitted one is below pi^46 / 46!
+// < 1e-32).  The reciprocals are correctly rounded fp64 divisions, made once
+// per block (recip[0][k] sin, recip[1][k] cos); every other step is one
+// correctly rounded fp64 multiply or add in a fixed order, so the values --
+// and the fp32 transforms made from them -- are reproducible on any IEEE
+// machine, which a library cos / sin (accurate to an ulp or two, by
 // machine-specific methods) is not.
-__device__ __forceinline__ void cos_sin_series(double a, double& c, double& s) {
+constexpr int kSeriesTerms = 22;
+
+__device__ __forceinline__ void cos_sin_series(double a, const double (*recip)[kSeriesTerms], double& c, double& s) {
   const double two_pi = 6.283185307179586;
   const double x = DS(a, DM(rint(__ddiv_rn(a, two_pi)), two_pi));
   const double mx2 = -DM(x, x);
   double ts = x, tc = 1.0, sn = x, cs = 1.0;
 #pragma unroll 1
-  for (int k = 0; k < 22; ++k) {
-    ts = __ddiv_rn(DM(ts, mx2), (double)((2 * k + 2) * (2 * k + 3)));
-    tc = __ddiv_rn(DM(tc, mx2), (double)((2 * k + 1) * (2 * k + 2)));
+  for (int k = 0; k < kSeriesTerms; ++k) {
+    ts = DM(DM(ts, mx2), recip[0][k]);
+    tc = DM(DM(tc, mx2), recip[1][k]);
     sn = DA(sn, ts);
     cs = DA(cs, tc);
   }
@@ -85,6 +89,7 @@ __global__ void pose_chain_kernel(int P, int nb, const int* __restrict__ parent,
   __shared__ double sN[kMaxBones][12];   // B_0^-1 B_k
   __shared__ double sRod[kMaxBones][6];  // c, s, 1 - c, unit axis
   __shared__ double sB0i[12];
+  __shared__ double sRecip[2][kSeriesTerms];  // series reciprocals (sin, cos)
   __shared__ int sDepth[kMaxBones];
   __shared__ int sMaxDepth;
   const int p = blockIdx.x;
@@ -92,6 +97,11 @@ __global__ void pose_chain_kernel(int P, int nb, const int* __restrict__ parent,
   const int t = threadIdx.x, k = t / 12, e = t % 12;
   const bool own = k < nb;
   if (t == 0) sMaxDepth = 0;
+  for (int q = t; q < 2 * kSeriesTerms; q += blockDim.x) {
+    const int j = q % kSeriesTerms;
+    sRecip[q / kSeriesTerms][j] =
+        q < kSeriesTerms ? __ddiv_rn(1.0, (double)((2 * j + 2) * (2 * j + 3))) : __ddiv_rn(1.0, (double)((2 * j + 1) * (2 * j + 2)));
+  }
   __syncthreads();
   if (own && e == 0) {
     const double* th = theta + ((size_t)p * nb + k) * 3;
@@ -100,7 +110,7 @@ __global__ void pose_chain_kernel(int P, int nb, const int* __restrict__ parent,
       sRod[k][0] = 1.0;  // identity rotation
     } else {
       double c, sn;
-      cos_sin_series(a, c, sn);
+      cos_sin_series(a, sRecip, c, sn);
       sRod[k][0] = c;
       sRod[k][1] = sn;
       sRod[k][2] = DS(1.0, c);

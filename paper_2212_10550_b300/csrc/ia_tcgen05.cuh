@@ -2,8 +2,9 @@
 // 5th-generation tensor cores (tcgen05 + TMA + TMEM), sm_103a.
 //
 // The per-sample backward writes its recomputed activations and (loss-scaled)
-// gradients channel-major into one fp16/bf16 array X [kWgRows][ld] (a row per
-// channel, a column per sample), so every operand is K-major with K = samples:
+// gradients into one fp16/bf16 array X of kWgRows rows (a row per channel, a
+// column per sample; chunk-contiguous, see wg_index), so every operand is
+// K-major with K = samples:
 //
 //   rows   0.. 63  dH2        rows 128..191  H1        rows 240..303  H2
 //   rows  64..127  dH1        rows 192..223  F         row  304       1
@@ -16,9 +17,10 @@
 //   GEMM 2: D2 [128 x 16]  = X[240:368] X[368:384]^T -> dW3^T (rows 0..63, cols 0..3),
 //           db3 (row 64, cols 0..3)
 //
-// Each CTA reduces a contiguous range of 64-sample chunks (48 KiB each).  The
-// work is split by role: lane 0 of warp 0 streams the chunks with TMA (three
-// 128-row boxes per chunk, 128-byte swizzle) into a four-stage ring, lane 0 of
+// X is chunk-contiguous (wg_index): each CTA reduces a contiguous range of
+// 64-sample chunks, each one sequential 48 KiB block.  The work is split by
+// role: lane 0 of warp 0 streams the chunks with TMA (three 128-row boxes per
+// chunk, 128-byte swizzle) into a four-stage ring, lane 0 of
 // warp 1 waits for each stage, issues its MMAs (M = 128, K = 16 per
 // instruction, fp32 accumulation in 128 TMEM columns) and commits them to the
 // stage's "empty" barrier, which hands the stage back to the producer; so up
@@ -97,11 +99,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64
   }
 }
 
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(
           smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -212,8 +214,7 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_tc_kernel(const __grid_co
       if (a.withhold_last && i == nch - 1) break;  // injected stall: the consumer's wait must expire
       uint8_t* base = smem + st * kWgStageBytes;
       mbar_expect_tx(&full[st], kWgStageBytes);
-      for (int r = 0; r < kWgRows; r += kWgBoxRows)
-        tma_load_2d(base + r * 128, &tmap, (c0 + i) * kWgChunk, r, &full[st]);
+      for (int r = 0; r < kWgRows; r += kWgBoxRows) tma_load_3d(base + r * 128, &tmap, 0, r, c0 + i, &full[st]);
       ++issued;
     }
     // every load issued has landed before the CTA may exit (the last load of
@@ -304,12 +305,12 @@ cudaError_t make_wgrad_map(CUtensorMap* map, void* X, int64_t ld, int bf16) {
     if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
     encode = reinterpret_cast<EncodeFn>(fn);
   }
-  if (ld % kWgChunk != 0 || (reinterpret_cast<uintptr_t>(X) & 15) != 0) return cudaErrorInvalidValue;
-  const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)kWgRows};
-  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)kWgChunk, (cuuint32_t)kWgBoxRows};
-  const cuuint32_t estr[2] = {1, 1};
-  CUresult r = encode(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, X, dims,
+  if (ld % kWgChunk != 0 || ld <= 0 || (reinterpret_cast<uintptr_t>(X) & 15) != 0) return cudaErrorInvalidValue;
+  const cuuint64_t dims[3] = {(cuuint64_t)kWgChunk, (cuuint64_t)kWgRows, (cuuint64_t)(ld / kWgChunk)};
+  const cuuint64_t strides[2] = {(cuuint64_t)kWgChunk * 2, (cuuint64_t)kWgRows * kWgChunk * 2};
+  const cuuint32_t box[3] = {(cuuint32_t)kWgChunk, (cuuint32_t)kWgBoxRows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, X, dims,
                       strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                       CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;

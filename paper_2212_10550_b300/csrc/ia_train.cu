@@ -769,14 +769,6 @@ __global__ void __launch_bounds__(256) mlp_grad_kernel(const TrainArgs a) {
 
 constexpr int kXdH2 = 0, kXdH1 = 64, kXH1 = 128, kXF = 192, kXOne = 224, kXH2 = 240, kXOne2 = 304, kXdO = 368;
 
-template <Prec P>
-__device__ __forceinline__ float put(uint16_t* col, int64_t ld, int row, float v) {
-  const uint16_t b = HalfOf<P>::bits(v);
-  col[(size_t)row * ld] = b;
-  if constexpr (P == Prec::F16) return __half2float(__ushort_as_half(b));
-  else return __bfloat162float(__ushort_as_bfloat16(b));
-}
-
 // Shared memory of the reduced-precision backward: the forward's MLP layout
 // (stage_mlp_h), the transposed weights the backward products need
 // (W2T[i][j] = W2[j][i], W1T[f][i] = W1[i][f], rows padded like the forward's),
@@ -817,13 +809,13 @@ __device__ __forceinline__ void tr_put(uint16_t* tr16, int ch, int r, uint16_t v
 
 // transposition buffer (64 channels x 32 samples) -> rows row0 .. row0 + 63 of X
 // at columns s0 .. s0 + 31 (two samples per 32-bit store, 64 B per row)
-__device__ __forceinline__ void tr_flush(const uint32_t* tr32, uint16_t* X, int64_t ld, int row0, int s0, int lane) {
+__device__ __forceinline__ void tr_flush(const uint32_t* tr32, uint16_t* X, int row0, int s0, int lane) {
   __syncwarp();
-  uint32_t* X32 = reinterpret_cast<uint32_t*>(X);
+  uint32_t* X32 = reinterpret_cast<uint32_t*>(X + wg_index(row0, s0));
 #pragma unroll 4
   for (int c2 = 0; c2 < kWidth / 2; ++c2) {
     const int ch = 2 * c2 + (lane >> 4);
-    X32[(((size_t)(row0 + ch)) * ld + s0) / 2 + (lane & 15)] = tr32[ch * kTrStride + (lane & 15)];
+    X32[ch * (kWgChunk / 2) + (lane & 15)] = tr32[ch * kTrStride + (lane & 15)];
   }
   __syncwarp();
 }
@@ -862,7 +854,6 @@ __global__ void __launch_bounds__(kBwThreads) train_backward_h_kernel(const Trai
   const int n = *a.count;
   const int n_pad = (n + kWgChunk - 1) / kWgChunk * kWgChunk;
   const float S = *a.scale, inv_S = 1.f / S;
-  const int64_t ld = a.ld;
   bool overflow = false;
   const int warps = gridDim.x * (blockDim.x >> 5);
   for (int s0 = (blockIdx.x * (blockDim.x >> 5) + warp) * 32; s0 < n_pad; s0 += warps * 32) {
@@ -880,7 +871,7 @@ __global__ void __launch_bounds__(kBwThreads) train_backward_h_kernel(const Trai
     {
       float feat[kIn];
       if (valid) encode_h(a.P.F, a.P.table_h, xs, feat);
-      uint16_t* col = a.X + s;
+      uint16_t* col = a.X + wg_index(0, s);  // this sample's entries, kWgChunk apart row to row
 #pragma unroll
       for (int c = 0; c < kIn / 2; ++c) {
         uint16_t b0 = 0, b1 = 0;
@@ -889,12 +880,12 @@ __global__ void __launch_bounds__(kBwThreads) train_backward_h_kernel(const Trai
           rnd_bits<P>(feat[2 * c + 1], b1);
         }
         Xs[lane * kXStride + c] = (uint32_t)b0 | ((uint32_t)b1 << 16);
-        col[(size_t)(kXF + 2 * c) * ld] = b0;
-        col[(size_t)(kXF + 2 * c + 1) * ld] = b1;
+        col[(kXF + 2 * c) * kWgChunk] = b0;
+        col[(kXF + 2 * c + 1) * kWgChunk] = b1;
       }
       const uint16_t one = HalfOf<P>::bits(1.f);
-      col[(size_t)kXOne * ld] = one;
-      col[(size_t)kXOne2 * ld] = one;
+      col[kXOne * kWgChunk] = one;
+      col[kXOne2 * kWgChunk] = one;
     }
     __syncwarp();
     // ---- layer 1: h1 = relu(W1 f + b1); masks and rounded A fragments of layer 2
@@ -936,7 +927,7 @@ __global__ void __launch_bounds__(kBwThreads) train_backward_h_kernel(const Trai
         A2[mt][nt >> 1][(nt & 1) * 2 + 1] = hi;
       }
     }
-    tr_flush(tr32, a.X, ld, kXH1, s0, lane);
+    tr_flush(tr32, a.X, kXH1, s0, lane);
     // ---- layer 2: h2 = relu(W2 h1 + b2); layer 3: o = W3 h2 + b3
     uint32_t m2[2];
 #pragma unroll
@@ -978,7 +969,7 @@ __global__ void __launch_bounds__(kBwThreads) train_backward_h_kernel(const Trai
         Os[r1 * 4 + 2 * t + 1] = o[3];
       }
     }
-    tr_flush(tr32, a.X, ld, kXH2, s0, lane);  // (also orders the Os writes before the reads below)
+    tr_flush(tr32, a.X, kXH2, s0, lane);  // (also orders the Os writes before the reads below)
     // ---- scaled output gradient of this lane's sample (zero without a root)
     {
       const float o0 = Os[lane * 4], o1 = Os[lane * 4 + 1], o2 = Os[lane * 4 + 2], o3 = Os[lane * 4 + 3];
@@ -991,14 +982,14 @@ __global__ void __launch_bounds__(kBwThreads) train_backward_h_kernel(const Trai
         const float sg = 1.f / (1.f + expf(-oc[c]));
         dO[1 + c] = gc[c] * sg * (1.f - sg);
       }
-      uint16_t* col = a.X + s;
+      uint16_t* col = a.X + wg_index(0, s);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const float v = dO[q] * S;
         overflow |= !(fabsf(v) <= HalfOf<P>::kMax);
         uint16_t b;
         Ds[lane * 4 + q] = rnd_bits<P>(v, b);
-        col[(size_t)(kXdO + q) * ld] = b;
+        col[(kXdO + q) * kWgChunk] = b;
       }
     }
     __syncwarp();
@@ -1029,7 +1020,7 @@ __global__ void __launch_bounds__(kBwThreads) train_backward_h_kernel(const Trai
         B2[mt][nt >> 1][(nt & 1) * 2 + 1] = (uint32_t)hb[2] | ((uint32_t)hb[3] << 16);
       }
     }
-    tr_flush(tr32, a.X, ld, kXdH2, s0, lane);
+    tr_flush(tr32, a.X, kXdH2, s0, lane);
     // ---- dH1 = (dH2 W2) o [h1 > 0] on tensor cores, rounded
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt) {
@@ -1057,7 +1048,7 @@ __global__ void __launch_bounds__(kBwThreads) train_backward_h_kernel(const Trai
         A2[mt][nt >> 1][(nt & 1) * 2 + 1] = (uint32_t)hb[2] | ((uint32_t)hb[3] << 16);
       }
     }
-    tr_flush(tr32, a.X, ld, kXdH1, s0, lane);
+    tr_flush(tr32, a.X, kXdH1, s0, lane);
     // ---- dF = dH1 W1 on tensor cores, unscaled to fp32
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt) {

@@ -779,6 +779,8 @@ __device__ __forceinline__ void tile_pixel(int id, int tiles_x, int W, int H, in
   valid = u < W && v < H;
 }
 
+constexpr int kMarchAhead = 4;  // slots whose occupancy words one march step fetches together
+
 template <int K, Prec P, bool kProp>
 __global__ void __launch_bounds__(kRenderThreads, IA_RENDER_MIN_BLOCKS) render_kernel(const RenderArgs a) {
   extern __shared__ float4 smem4[];
@@ -816,21 +818,34 @@ __global__ void __launch_bounds__(kRenderThreads, IA_RENDER_MIN_BLOCKS) render_k
       if (has_ray) {
         const float4 ro = ray_o[lane], rd = ray_d[lane];
         const float o[3] = {ro.x, ro.y, ro.z}, d[3] = {rd.x, rd.y, rd.z};
+        // kMarchAhead slots at a time: their cells and occupancy words are
+        // fetched together (independent loads in flight), then tested in slot
+        // order, stopping at the K-th occupied one as a one-slot loop would
         while (cursor < a.n_slots && nfound < K) {
-          const float3 x = slot_position(o, d, rd.w, ro.w, cursor);
-          const int cell = cell_of(a.box, x);
-          ++n_marched;
-          if ((__ldg(a.occ + (cell >> 5)) >> (cell & 31)) & 1u) {
-            if (a.sub && !sub_marked(a.sub, a.box, x)) {
-              ++n_culled;  // no root possible: density 0, nothing to composite
-            } else {
+          int cl[kMarchAhead];
+          uint32_t wd[kMarchAhead];
 #pragma unroll
-              for (int q = 0; q < K; ++q)
-                if (q == nfound) slots[q] = cursor;
-              ++nfound;
-            }
+          for (int q = 0; q < kMarchAhead; ++q) {
+            const int sl = min(cursor + q, a.n_slots - 1);
+            cl[q] = cell_of(a.box, slot_position(o, d, rd.w, ro.w, sl));
+            wd[q] = __ldg(a.occ + (cl[q] >> 5));
           }
-          ++cursor;
+#pragma unroll
+          for (int q = 0; q < kMarchAhead; ++q) {
+            if (cursor >= a.n_slots || nfound >= K) break;
+            ++n_marched;
+            if ((wd[q] >> (cl[q] & 31)) & 1u) {
+              if (a.sub && !sub_marked(a.sub, a.box, slot_position(o, d, rd.w, ro.w, cursor))) {
+                ++n_culled;  // no root possible: density 0, nothing to composite
+              } else {
+#pragma unroll
+                for (int k = 0; k < K; ++k)
+                  if (k == nfound) slots[k] = cursor;
+                ++nfound;
+              }
+            }
+            ++cursor;
+          }
         }
         if (nfound == 0) {  // exhausted: write the pixel
           a.rgb[3 * pix] = cr;
@@ -897,7 +912,10 @@ __global__ void __launch_bounds__(kRenderThreads, IA_RENDER_MIN_BLOCKS) render_k
     __syncwarp();
     // ---- 3. correspondence search and field at the round's samples (lists of kList)
     for (int base = 0; base < total; base += kList) {
-      posed_field_list<P, kProp ? ItemOrder::kStartMajor : ItemOrder::kPerLane, kProp>(
+      // each lane runs its own sample's starts in order (the proposed ones, or
+      // all bones); the proposal's fallback starts, many for a few samples,
+      // go through the warp's shared queue
+      posed_field_list<P, ItemOrder::kPerLane, kProp, ItemOrder::kStartMajor>(
           a.P.S, a.P.F, a.P.cfg, sm.fs, sm.list, min(kList, total - base),
           [&](int i, float3& xn, const float4*& M, const float*& Ni, int& pose) {
             const int sidx = base + i;

@@ -155,7 +155,7 @@ __device__ __noinline__ void compress_roots(const SkinDev& S, const float4* M, c
 // as found), barring roots within the merge distance of two listed ones.
 enum class ItemOrder { kPerLane, kSampleMajor, kStartMajor };
 
-template <Prec P, ItemOrder kOrder, bool kCompact = false, class Src, class Dst>
+template <Prec P, ItemOrder kOrder, bool kCompact = false, ItemOrder kFallbackOrder = kOrder, class Src, class Dst>
 __device__ __forceinline__ void posed_field_list(const SkinDev& S, const FieldDev& F, const SolveCfg& cfg,
                                                  const FieldSmem& fs, const ListSmem& qs, int m, Src src, Dst dst,
                                                  SampleStats& st, const PropDev& Q = PropDev{},
@@ -218,9 +218,11 @@ __device__ __forceinline__ void posed_field_list(const SkinDev& S, const FieldDe
       ns = __popc(fm);
       n_items = ns * per;
     }
+    // this stage's order: kOrder for the first starts, kFallbackOrder for the fallback
+    const ItemOrder ord = stage == 0 ? kOrder : kFallbackOrder;
     // shared queue: idx -> (sample, start) by a multiply-high division (exact
     // for idx < 2^16; ns == 1 and per == 1 need none: 2^32 does not fit)
-    const int dv = kOrder == ItemOrder::kStartMajor ? ns : per;
+    const int dv = ord == ItemOrder::kStartMajor ? ns : per;
     const unsigned magic = dv > 1 ? 0xFFFFFFFFu / (unsigned)dv + 1u : 0u;
     const bool mine = stage == 0 ? lane < m : (lane < m && qs.nroots[lane] == 0);  // kPerLane
     int next = 0;  // warp-uniform: items handed out so far
@@ -239,7 +241,7 @@ __device__ __forceinline__ void posed_field_list(const SkinDev& S, const FieldDe
       // lanes without an item take the next one
       bool got = false;
       int i = 0, j = 0;
-      if constexpr (kOrder == ItemOrder::kPerLane) {
+      if (ord == ItemOrder::kPerLane) {
         if (need) {
           need = false;
           phase = 2;
@@ -260,14 +262,14 @@ __device__ __forceinline__ void posed_field_list(const SkinDev& S, const FieldDe
             if (idx < n_items) {
               got = true;
               const int q = dv > 1 ? (int)__umulhi((unsigned)idx, magic) : idx, rm = idx - q * dv;
-              if (kOrder == ItemOrder::kStartMajor) { j = q; i = rm; }
+              if (ord == ItemOrder::kStartMajor) { j = q; i = rm; }
               else { i = q; j = rm; }
             }
           }
         }
       }
       if (got) {
-        cur = (stage == 0 || kOrder == ItemOrder::kPerLane) ? i : qs.fb[i];
+        cur = (stage == 0 || ord == ItemOrder::kPerLane) ? i : qs.fb[i];
         if (cur != loaded) {  // consecutive items of one sample reuse its point and grids
           int pose;
           src(cur, xn, M, Ninv, pose);
@@ -347,7 +349,7 @@ __device__ __forceinline__ void posed_field_list(const SkinDev& S, const FieldDe
           phase = 1;
         }
       }
-      if constexpr (kOrder == ItemOrder::kPerLane) {
+      if (ord == ItemOrder::kPerLane) {
         // the lane owns its sample and runs its starts in order: the first of
         // equal roots is the earlier start's
         if (finish) {

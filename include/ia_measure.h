@@ -35,6 +35,7 @@ ia_status ia_gather_probe(const float *table, int64_t n_records, int iters, int 
  * first launch: out [max_out] (host, may be NULL when max_out is 0), *n_out =
  * the number of distinct kernels (entries beyond max_out are dropped).
  * IA_ERR_STATE when no profile is open (end) or one is already open (begin);
+ * IA_ERR_ARG for bad output arguments (the profile then stays open);
  * IA_ERR_CUDA when an event failed.  Messages: ia_profile_error(). */
 typedef struct ia_kernel_time {
   char name[48];       /* kernel, with its precision / search variant */

@@ -65,3 +65,30 @@ def test_null_arguments(ia):
     assert ia.lib().ia_render(None, 0, None, None, None, None, None) == ia.IA_ERR_ARG
     assert ia.lib().ia_set_pose(None, 1, None, None, None) == ia.IA_ERR_ARG
     ia.lib().ia_destroy(None)  # allowed
+
+
+def test_null_context_of_the_training_split_and_pipeline_settings(ia):
+    L = ia.lib()
+    assert L.ia_train_forward(None, None, 0, None, None, None, None, None) == ia.IA_ERR_ARG
+    assert L.ia_train_backward(None, None, None, None, None) == ia.IA_ERR_ARG
+    assert L.ia_set_wait_limit(None, 0) == ia.IA_ERR_ARG
+    assert L.ia_set_fault_injection(None, 0) == ia.IA_ERR_ARG
+    assert L.ia_gather_probe(None, 1, 1, 1, None, None) == ia.IA_ERR_ARG
+
+
+def test_launch_tracing_state_machine(ia):
+    """ia_profile_begin / ia_profile_end need no device when nothing launched:
+    an empty profile, and the order errors."""
+    with pytest.raises(ia.IAError) as e:
+        ia.ia_profile_end()
+    assert e.value.status == ia.IA_ERR_STATE
+    ia.ia_profile_begin()
+    with pytest.raises(ia.IAError) as e:
+        ia.ia_profile_begin()
+    assert e.value.status == ia.IA_ERR_STATE
+    assert ia.ia_profile_end() == {}
+    n = C.c_int(-1)
+    assert ia.lib().ia_profile_begin() == ia.IA_OK
+    assert ia.lib().ia_profile_end(None, -1, C.byref(n)) == ia.IA_ERR_ARG  # bad arguments: still open
+    assert ia.lib().ia_profile_end(None, 0, C.byref(n)) == ia.IA_OK and n.value == 0
+    assert ia.lib().ia_profile_end(None, 0, C.byref(n)) == ia.IA_ERR_STATE

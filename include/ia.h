@@ -225,6 +225,22 @@ ia_status ia_query_canonical(ia_ctx *ctx, int n, const float *x, float *sigma, f
 ia_status ia_render(ia_ctx *ctx, int pose, const ia_camera *cam, float *rgb, float *alpha,
                     ia_render_stats *stats, void *stream);
 
+/* How ia_render schedules the frame; results are the same up to the merge
+ * order of the fused path's shared queues (within rounding).
+ *  IA_RENDER_WAVEFRONT (default): a sequence of kernels over arrays -- march
+ *    (each ray's kept samples, contiguous), the proposal (proposal search),
+ *    the search with one thread per (sample, start) item, the fallback starts
+ *    of the proposal search as a second wave, the field per sample, then
+ *    compositing per ray.  The samples' count is read back after the march
+ *    (so ia_render waits on its stream there), and the context keeps arrays
+ *    for the frame's samples (~0.5 KB per sample with 24 bones).  Samples
+ *    behind the point where early termination stops a ray are evaluated too.
+ *  IA_RENDER_FUSED: one persistent kernel per frame, each warp marching,
+ *    searching, evaluating and compositing its own pool of 32 rays; rays stop
+ *    at early termination; no read-back. */
+typedef enum ia_render_path { IA_RENDER_FUSED = 0, IA_RENDER_WAVEFRONT = 1 } ia_render_path;
+ia_status ia_set_render_path(ia_ctx *ctx, int path);
+
 /* A batch of training rays (all device pointers), and optionally the points of
  * the occupancy-based density regulariser (Eq. 12). */
 typedef struct ia_batch {

@@ -20,6 +20,7 @@ IA_FP32, IA_FP16, IA_BF16 = 0, 1, 2
 IA_OCC_POSE, IA_OCC_UNION = 0, 1
 IA_SEARCH_ALL_BONES, IA_SEARCH_PROPOSAL = 0, 1
 IA_LOSS_L2, IA_LOSS_HUBER = 0, 1
+IA_RENDER_FUSED, IA_RENDER_WAVEFRONT = 0, 1
 MAX_LEVELS = 16
 
 
@@ -125,6 +126,7 @@ def lib():
             "ia_proposal_train": [P, I, P, P, P, P, I, I, C.c_float, P, V],
             "ia_set_search": [P, I],
             "ia_set_occupancy_culling": [P, I],
+            "ia_set_render_path": [P, I],
             "ia_profile_begin": [],
             "ia_profile_end": [C.POINTER(KernelTime), I, C.POINTER(C.c_int)],
         }
@@ -275,6 +277,11 @@ def ia_render(ctx, pose, cam: Camera, rgb, alpha, stats=False, stream=None):
     _check(lib().ia_render(ctx, pose, C.byref(cam), _ptr(rgb), _ptr(alpha), C.byref(s) if s is not None else None,
                            _stream(stream)), ctx)
     return s.as_dict() if s is not None else None
+
+
+def ia_set_render_path(ctx, path):
+    """IA_RENDER_WAVEFRONT (default: kernels over arrays) or IA_RENDER_FUSED (one persistent kernel)."""
+    _check(lib().ia_set_render_path(ctx, int(path)), ctx)
 
 
 def ia_march_mask(ctx, pose, cam: Camera, slot_mask, stream=None):

@@ -72,6 +72,22 @@ struct ia_ctx {
   // scratch for host-memory outputs of ia_render
   float* d_out = nullptr;
   size_t out_cap = 0;
+  // wavefront render path: per-ray and per-sample arrays, counters
+  int render_path = IA_RENDER_WAVEFRONT;
+  size_t wf_ray_cap = 0, wf_cap = 0;
+  int wf_per0 = 0;
+  bool wf_prop = false;
+  int* d_wf_first = nullptr;
+  int* d_wf_cnt = nullptr;
+  float* d_wf_dt = nullptr;
+  float4* d_wf_xn = nullptr;
+  float4* d_wf_prop = nullptr;
+  float4* d_wf_item0 = nullptr;
+  float4* d_wf_item1 = nullptr;
+  int* d_wf_fb = nullptr;
+  int* d_wf_fbidx = nullptr;
+  float4* d_wf_res = nullptr;
+  unsigned* d_wf_counts = nullptr;  // [0] samples, [1] fallback samples
   // training-step workspace
   int ray_cap = 0;
   int reg_cap = 0;
@@ -420,6 +436,17 @@ void ia_destroy(ia_ctx* c) {
   dfree(c->d_cand);
   dfree(c->d_stats);
   dfree(c->d_counter);
+  dfree(c->d_wf_first);
+  dfree(c->d_wf_cnt);
+  dfree(c->d_wf_dt);
+  dfree(c->d_wf_xn);
+  dfree(c->d_wf_prop);
+  dfree(c->d_wf_item0);
+  dfree(c->d_wf_item1);
+  dfree(c->d_wf_fb);
+  dfree(c->d_wf_fbidx);
+  dfree(c->d_wf_res);
+  dfree(c->d_wf_counts);
   dfree(c->d_work);
   dfree(c->d_tstats);
   dfree(c->d_out);
@@ -733,6 +760,86 @@ ia_status ia_march_mask(ia_ctx* c, int pose, const ia_camera* cam, uint32_t* slo
   return IA_OK;
 }
 
+// The wavefront path: march (kept samples written per ray), the sample count
+// read back (the per-sample arrays are sized from it; a frame that outgrows
+// them grows them and is marched again), then the search, field and
+// compositing kernels.
+static ia_status render_wavefront(ia_ctx* c, RenderArgs& a, size_t npix, cudaStream_t s) {
+  const bool prop = a.P.search != 0;
+  const int nb = c->nb;
+  const int per0 = prop ? std::min(c->pcfg.top_k, nb) : nb;
+  if (c->wf_ray_cap < npix || !c->d_wf_counts) {
+    IA_CUDA(c, cudaStreamSynchronize(s), "ia_render");
+    c->wf_ray_cap = 0;
+    IA_CUDA(c, dalloc(&c->d_wf_first, npix), "ia_render: wavefront arrays");
+    IA_CUDA(c, dalloc(&c->d_wf_cnt, npix), "ia_render: wavefront arrays");
+    IA_CUDA(c, dalloc(&c->d_wf_dt, npix), "ia_render: wavefront arrays");
+    if (!c->d_wf_counts) IA_CUDA(c, dalloc(&c->d_wf_counts, (size_t)2), "ia_render: wavefront arrays");
+    c->wf_ray_cap = npix;
+  }
+  WfArgs w{};
+  w.n_samples = c->d_wf_counts;
+  w.n_fb = c->d_wf_counts + 1;
+  w.ray_first = c->d_wf_first;
+  w.ray_cnt = c->d_wf_cnt;
+  w.ray_dt = c->d_wf_dt;
+  unsigned n_host = 0;
+  bool fits = false;
+  for (int attempt = 0; attempt < 2 && !fits; ++attempt) {
+    if (attempt > 0) {
+      // the frame outgrew the sample arrays: grow them (with some room) and march again
+      const size_t cap = (size_t)n_host + n_host / 4 + 1024;
+      if (cap * (size_t)nb > (size_t)INT32_MAX) return fail(c, IA_ERR_ARG, "ia_render: too many samples in the frame");
+      IA_CUDA(c, cudaStreamSynchronize(s), "ia_render");
+      c->wf_cap = 0;
+      c->wf_per0 = 0;
+      IA_CUDA(c, dalloc(&c->d_wf_xn, cap), "ia_render: wavefront arrays");
+      IA_CUDA(c, dalloc(&c->d_wf_res, cap), "ia_render: wavefront arrays");
+      c->wf_cap = cap;
+      IA_CUDA(c, cudaMemsetAsync(c->d_stats, 0, sizeof(unsigned long long) * ST_COUNT, s), "ia_render");
+    }
+    w.cap = (int)c->wf_cap;
+    w.xn = c->d_wf_xn;
+    IA_CUDA(c, cudaMemsetAsync(c->d_wf_counts, 0, 2 * sizeof(unsigned), s), "ia_render");
+    IA_CUDA(c, launch_wf_march(a, w, s), "ia_render: march");
+    IA_CUDA(c, cudaMemcpyAsync(&n_host, c->d_wf_counts, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "ia_render");
+    IA_CUDA(c, cudaStreamSynchronize(s), "ia_render");
+    fits = n_host <= c->wf_cap;
+  }
+  if (!fits) return fail(c, IA_ERR_STATE, "ia_render: the frame's sample count changed between marches");
+  // the search arrays, sized for the sample capacity and the search mode
+  if (n_host > 0 && (c->wf_per0 != per0 || (prop && !c->wf_prop))) {
+    const size_t cap = c->wf_cap;
+    c->wf_per0 = 0;
+    IA_CUDA(c, dalloc(&c->d_wf_item0, cap * per0), "ia_render: wavefront arrays");
+    if (prop) {
+      IA_CUDA(c, dalloc(&c->d_wf_prop, cap), "ia_render: wavefront arrays");
+      IA_CUDA(c, dalloc(&c->d_wf_item1, cap * nb), "ia_render: wavefront arrays");
+      IA_CUDA(c, dalloc(&c->d_wf_fb, cap), "ia_render: wavefront arrays");
+      IA_CUDA(c, dalloc(&c->d_wf_fbidx, cap), "ia_render: wavefront arrays");
+    }
+    c->wf_per0 = per0;
+    c->wf_prop = prop;
+  }
+  w.cap = (int)c->wf_cap;
+  w.xn = c->d_wf_xn;
+  w.prop = c->d_wf_prop;
+  w.item0 = c->d_wf_item0;
+  w.item1 = c->d_wf_item1;
+  w.fb = c->d_wf_fb;
+  w.fbidx = c->d_wf_fbidx;
+  w.res = c->d_wf_res;
+  IA_CUDA(c, launch_wf_rest(a, w, (int)n_host, c->num_sms, s), "ia_render: kernels");
+  return IA_OK;
+}
+
+ia_status ia_set_render_path(ia_ctx* c, int path) {
+  if (!c) return fail(nullptr, IA_ERR_ARG, "null context");
+  if (path != IA_RENDER_FUSED && path != IA_RENDER_WAVEFRONT) return fail(c, IA_ERR_ARG, "unknown render path");
+  c->render_path = path;
+  return IA_OK;
+}
+
 ia_status ia_render(ia_ctx* c, int pose, const ia_camera* cam, float* rgb, float* alpha, ia_render_stats* stats,
                     void* stream) {
   ia_status st = need_ready(c, pose, true);
@@ -757,9 +864,14 @@ ia_status ia_render(ia_ctx* c, int pose, const ia_camera* cam, float* rgb, float
   RenderArgs a = render_args(c, pose, cam);
   a.rgb = o_rgb;
   a.alpha = o_alpha;
-  IA_CUDA(c, cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned int), s), "ia_render");
   IA_CUDA(c, cudaMemsetAsync(c->d_stats, 0, sizeof(unsigned long long) * ST_COUNT, s), "ia_render");
-  IA_CUDA(c, launch_render(a, c->num_sms, s), "ia_render: kernel");
+  if (c->render_path == IA_RENDER_WAVEFRONT) {
+    st = render_wavefront(c, a, npix, s);
+    if (st != IA_OK) return st;
+  } else {
+    IA_CUDA(c, cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned int), s), "ia_render");
+    IA_CUDA(c, launch_render(a, c->num_sms, s), "ia_render: kernel");
+  }
   if (!dev_rgb) IA_CUDA(c, cudaMemcpyAsync(rgb, o_rgb, npix * 12, cudaMemcpyDeviceToHost, s), "ia_render: copy");
   if (!dev_alpha) IA_CUDA(c, cudaMemcpyAsync(alpha, o_alpha, npix * 4, cudaMemcpyDeviceToHost, s), "ia_render: copy");
   if (!dev_rgb || !dev_alpha) IA_CUDA(c, cudaStreamSynchronize(s), "ia_render");

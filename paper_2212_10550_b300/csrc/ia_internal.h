@@ -65,6 +65,21 @@ __device__ __forceinline__ PosedStage stage_of(const PosedArgs& a) {
   return s;
 }
 
+// ray id -> pixel: rays are numbered tile by tile (kTile x kTile pixels, row by row inside a tile)
+__device__ __forceinline__ void tile_pixel(int id, int tiles_x, int W, int H, int& u, int& v, bool& valid) {
+  const int tile = id / (kTile * kTile), i = id % (kTile * kTile);
+  u = (tile % tiles_x) * kTile + i % kTile;
+  v = (tile / tiles_x) * kTile + i / kTile;
+  valid = u < W && v < H;
+}
+
+// dynamic shared memory of a kernel that stages the posed field (stage_posed)
+template <Prec P>
+size_t posed_smem_bytes_p(int threads, bool prop) {
+  return sizeof(float) * (mlp_smem_words(P, threads, prop) + kMaxBones * 12) +
+         sizeof(uint32_t) * (threads / 32) * list_smem_words(prop);
+}
+
 struct RenderArgs {
   PosedArgs P;
   const float* B0inv;  // [12]
@@ -265,6 +280,27 @@ cudaError_t launch_query_canonical(const PosedArgs& a, int n, const float* x, fl
                                    cudaStream_t s);
 cudaError_t launch_table_to_half(const float* table, __half2* th, int64_t entries, cudaStream_t s);
 cudaError_t launch_render(const RenderArgs& a, int num_sms, cudaStream_t s);
+
+// Wavefront render path (ia_wavefront.cu): march -> [proposal] -> search waves
+// -> field -> compositing, over these arrays (device, context-owned).
+struct WfArgs {
+  unsigned* n_samples;  // kept samples of the frame (counter, zeroed by the host)
+  int cap;              // samples the per-sample arrays hold
+  float4* xn;           // [cap] normalised-space positions, each ray's samples contiguous in slot order
+  int* ray_first;       // [W * H] first sample of the pixel's ray
+  int* ray_cnt;         // [W * H] its kept samples
+  float* ray_dt;        // [W * H] its slot spacing
+  float4* prop;         // [cap] proposal: bones b0 | b1 << 8, start offset
+  float4* item0;        // [cap * starts] first wave: root (x, y, z) and order << 8 | bone, or -1
+  float4* item1;        // [cap * n_bones] fallback wave, indexed by the sample's fallback position
+  int* fb;              // [cap] fallback samples
+  int* fbidx;           // [cap] a sample's fallback position, or -1
+  unsigned* n_fb;       // fallback samples (counter, zeroed by the host)
+  float4* res;          // [cap] sigma (0 without a root), rgb
+};
+cudaError_t launch_wf_march(const RenderArgs& a, const WfArgs& w, cudaStream_t s);
+// everything after the march, for n_samples kept samples (read back by the host)
+cudaError_t launch_wf_rest(const RenderArgs& a, const WfArgs& w, int n_samples, int num_sms, cudaStream_t s);
 cudaError_t launch_march_mask(const RenderArgs& a, uint32_t* mask, cudaStream_t s);
 
 }  // namespace ia

@@ -236,11 +236,6 @@ cudaError_t launch_blend(int P, int V, int nb, const float* W, const float* N, f
 //   pose's N_k^-1, and the per-lane root lists.
 // ---------------------------------------------------------------------------
 
-template <Prec P>
-size_t posed_smem_bytes_p(int threads, bool prop) {
-  return sizeof(float) * (mlp_smem_words(P, threads, prop) + kMaxBones * 12) +
-         sizeof(uint32_t) * (threads / 32) * list_smem_words(prop);
-}
 
 // ---------------------------------------------------------------------------
 // Occupancy grid (Sec. 3.3, inference mode)
@@ -772,12 +767,6 @@ size_t render_smem_bytes_p(int K, bool prop) {
          (sizeof(uint8_t) + sizeof(uint16_t)) * K * kRenderThreads;
 }
 
-__device__ __forceinline__ void tile_pixel(int id, int tiles_x, int W, int H, int& u, int& v, bool& valid) {
-  const int tile = id / (kTile * kTile), i = id % (kTile * kTile);
-  u = (tile % tiles_x) * kTile + i % kTile;
-  v = (tile / tiles_x) * kTile + i / kTile;
-  valid = u < W && v < H;
-}
 
 constexpr int kMarchAhead = 4;  // slots whose occupancy words one march step fetches together
 

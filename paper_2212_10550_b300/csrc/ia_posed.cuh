@@ -141,6 +141,82 @@ __device__ __noinline__ void compress_roots(const SkinDev& S, const float4* M, c
   list[0] = make_float4(best_raw.x, best_raw.y, best_raw.z, __int_as_float(best_code));
 }
 
+// The field phase of a list of m <= 32 samples whose distinct roots are in qs
+// (qs.nroots, qs.roots): one Newton polish per root, the field at the roots,
+// each sample's max-density root (ties to the lower start bone) to dst.
+// The list's roots are spread over the lanes, 32 per warp-wide field
+// evaluation: root e of sample i has the flat index first_i + e (first_i = the
+// roots of samples 0..i-1); lane l of a round evaluates flat index base + l.
+// The owner lane of each sample then takes its roots' results in root order
+// (take_best), as if it had evaluated them itself.  All 32 lanes call.
+template <Prec P, bool kCompact, class Src, class Dst>
+__device__ __forceinline__ void list_field_phase(const SkinDev& S, const FieldDev& F, const FieldSmem& fs,
+                                                 const ListSmem& qs, int m, Src src, Dst dst) {
+  const int lane = threadIdx.x & 31;
+  {
+    const int i = lane;  // owner of sample i
+    const bool act = i < m;
+    PosedOut out;
+    out.sigma = 0.f;
+    out.rgb = out.xstar = make_float3(0.f, 0.f, 0.f);
+    out.start = -1;
+    const int n_r = act ? qs.nroots[i] : 0;
+    int incl = n_r;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int first = incl - n_r;
+    const int total = __shfl_sync(kFull, incl, 31);
+    for (int base = 0; base < total; base += 32) {
+      const int f = base + lane;
+      const bool has = f < total;
+      // the sample holding flat index f: the last lane whose first index is <= f
+      // (a lane with no roots shares its first index with the next lane)
+      int s_of = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int cand = s_of + step;
+        const int fc = __shfl_sync(kFull, first, cand & 31);
+        if (cand < 32 && fc <= f) s_of = cand;
+      }
+      const int e = f - __shfl_sync(kFull, first, s_of);
+      float3 xs = make_float3(S.cmin[0], S.cmin[1], S.cmin[2]);
+      int start = -1;
+      if (has) {
+        float3 xq;
+        const float4* Mq;
+        const float* Nq;
+        int pose;
+        src(s_of, xq, Mq, Nq, pose);
+        const float4 o = qs.roots[e * kList + s_of];
+        start = __float_as_int(o.w) & 0xff;
+        xs = polish_root(S, Mq, make_float3(o.x, o.y, o.z), xq);
+      }
+      float sig;
+      float3 rgb;
+      field_eval_warp<P, kCompact>(F, fs, xs, sig, rgb);
+      // each owner collects its sample's roots of this round, in root order
+#pragma unroll
+      for (int e2 = 0; e2 < kMaxRoots; ++e2) {
+        const int fl = first + e2;
+        const bool mine = act && e2 < n_r && fl >= base && fl < base + 32;
+        const int from = mine ? fl - base : lane;
+        const float g_sig = __shfl_sync(kFull, sig, from);
+        const float3 g_rgb = make_float3(__shfl_sync(kFull, rgb.x, from), __shfl_sync(kFull, rgb.y, from),
+                                         __shfl_sync(kFull, rgb.z, from));
+        const float3 g_xs = make_float3(__shfl_sync(kFull, xs.x, from), __shfl_sync(kFull, xs.y, from),
+                                        __shfl_sync(kFull, xs.z, from));
+        const int g_start = __shfl_sync(kFull, start, from);
+        if (mine) take_best(out, g_sig, g_rgb, g_xs, g_start);
+      }
+    }
+    if (act) dst(i, out);
+  }
+  __syncwarp();
+}
+
 // How a list's (sample, start) items meet the lanes:
 //   kPerLane      lane i runs sample i's starts in order (no sharing)
 //   kSampleMajor  a shared queue, every start of sample 0, then of sample 1, ...
@@ -450,73 +526,7 @@ __device__ __forceinline__ void posed_field_list(const SkinDev& S, const FieldDe
     }
     __syncwarp();
   }
-  // ---- one Newton polish per stored root, field at the roots, max-density root.
-  //      The list's roots are spread over the lanes, 32 per warp-wide field
-  //      evaluation: root e of sample i has the flat index first_i + e (first_i
-  //      = the roots of samples 0..i-1); lane l of a round evaluates flat index
-  //      base + l.  The owner lane of each sample then takes its roots' results
-  //      in root order (take_best), as if it had evaluated them itself.
-  {
-    const int i = lane;  // owner of sample i
-    const bool act = i < m;
-    PosedOut out;
-    out.sigma = 0.f;
-    out.rgb = out.xstar = make_float3(0.f, 0.f, 0.f);
-    out.start = -1;
-    const int n_r = act ? qs.nroots[i] : 0;
-    int incl = n_r;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(kFull, incl, o);
-      if (lane >= o) incl += t;
-    }
-    const int first = incl - n_r;
-    const int total = __shfl_sync(kFull, incl, 31);
-    for (int base = 0; base < total; base += 32) {
-      const int f = base + lane;
-      const bool has = f < total;
-      // the sample holding flat index f: the last lane whose first index is <= f
-      // (a lane with no roots shares its first index with the next lane)
-      int s_of = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const int cand = s_of + step;
-        const int fc = __shfl_sync(kFull, first, cand & 31);
-        if (cand < 32 && fc <= f) s_of = cand;
-      }
-      const int e = f - __shfl_sync(kFull, first, s_of);
-      float3 xs = make_float3(S.cmin[0], S.cmin[1], S.cmin[2]);
-      int start = -1;
-      if (has) {
-        float3 xq;
-        const float4* Mq;
-        const float* Nq;
-        int pose;
-        src(s_of, xq, Mq, Nq, pose);
-        const float4 o = qs.roots[e * kList + s_of];
-        start = __float_as_int(o.w) & 0xff;
-        xs = polish_root(S, Mq, make_float3(o.x, o.y, o.z), xq);
-      }
-      float sig;
-      float3 rgb;
-      field_eval_warp<P, kCompact>(F, fs, xs, sig, rgb);
-      // each owner collects its sample's roots of this round, in root order
-#pragma unroll
-      for (int e2 = 0; e2 < kMaxRoots; ++e2) {
-        const int fl = first + e2;
-        const bool mine = act && e2 < n_r && fl >= base && fl < base + 32;
-        const int from = mine ? fl - base : lane;
-        const float g_sig = __shfl_sync(kFull, sig, from);
-        const float3 g_rgb = make_float3(__shfl_sync(kFull, rgb.x, from), __shfl_sync(kFull, rgb.y, from),
-                                         __shfl_sync(kFull, rgb.z, from));
-        const float3 g_xs = make_float3(__shfl_sync(kFull, xs.x, from), __shfl_sync(kFull, xs.y, from),
-                                        __shfl_sync(kFull, xs.z, from));
-        const int g_start = __shfl_sync(kFull, start, from);
-        if (mine) take_best(out, g_sig, g_rgb, g_xs, g_start);
-      }
-    }
-    if (act) dst(i, out);
-  }
+  list_field_phase<P, kCompact>(S, F, fs, qs, m, src, dst);
   __syncwarp();
 }
 

@@ -1,0 +1,431 @@
+// Wavefront render path (sm_103a): the frame as a sequence of kernels over
+// arrays instead of one persistent kernel per ray batch.
+//
+//   wf_march_kernel      one thread per ray: the slots in occupied cells that
+//                        root culling keeps, written contiguously per ray (Sec.
+//                        3.2-3.3; the same fp32 indexing as the fused render)
+//   wf_propose_kernel    (proposal search) the network's top-2 bones and start
+//                        offset for every sample, 32 samples per warp MMA
+//   wf_search_kernel     one thread per (sample, start) item: bone-wise Broyden
+//                        from that start (Sec. 3.1, Eq. 7), its converged root
+//                        inside the canonical box, or none
+//   wf_fallback_kernel   (proposal search) the samples none of whose proposed
+//                        starts found a root; a second search wave runs every
+//                        bone-wise start of those samples only
+//   wf_field_kernel      per sample: its item results merged in start order
+//                        (a root within 1e-4 of an earlier one is that root),
+//                        one Newton polish per root, the field at the roots,
+//                        the max-density root (Sec. 3.1, Eq. 1-4)
+//   wf_composite_kernel  one thread per ray: front-to-back compositing of its
+//                        samples with early termination (Sec. 3.2, Eq. 8)
+//
+// Each sample's result is the fused render's (same starts, Broyden steps,
+// merge rule, polish, field and selection); the difference is the schedule.
+// The search items are independent and light (128 registers, four blocks of
+// four warps per SM against one block of eight warps for the fused kernel),
+// and the proposal's fallback starts, a few per ray where they occur, form one
+// dense wave instead of a tail per list.  Samples behind the point where a
+// ray's transmittance falls below the threshold are searched too (the march
+// does not know the densities yet): +2.5 % on the full-size workload.
+#include "ia_internal.h"
+
+namespace ia {
+
+namespace {
+
+// warp-aggregated reservation of `count` consecutive entries of *counter; returns
+// this lane's first entry (all 32 lanes call)
+__device__ __forceinline__ int warp_reserve(unsigned* counter, int count) {
+  const int lane = threadIdx.x & 31;
+  int incl = count;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const int total = __shfl_sync(kFull, incl, 31);
+  int base = 0;
+  if (lane == 31 && total > 0) base = (int)atomicAdd(counter, (unsigned)total);
+  base = __shfl_sync(kFull, base, 31);
+  return base + incl - count;
+}
+
+template <class F>
+__device__ __forceinline__ void for_each_kept_slot(const RenderArgs& a, const float o[3], const float d[3], float tn,
+                                                   float dt, unsigned& marched, unsigned& culled, F kept) {
+  for (int i = 0; i < a.n_slots; ++i) {
+    const float3 x = slot_position(o, d, tn, dt, i);
+    const int cell = cell_of(a.box, x);
+    ++marched;
+    if ((__ldg(a.occ + (cell >> 5)) >> (cell & 31)) & 1u) {
+      if (a.sub && !sub_marked(a.sub, a.box, x)) ++culled;
+      else kept(x);
+    }
+  }
+}
+
+}  // namespace
+
+// ---- march: count, reserve, emit (one thread per ray id, tile order)
+__global__ void __launch_bounds__(256) wf_march_kernel(const RenderArgs a, const WfArgs w) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  const int W = a.cam.width, H = a.cam.height;
+  int u = 0, v = 0;
+  bool valid = false;
+  if (id < a.n_ray_ids) tile_pixel(id, a.tiles_x, W, H, u, v, valid);
+  float o[3], d[3], tn = 0.f, tf = 0.f;
+  const bool hit = valid && make_ray(a.cam, a.B0inv, a.box, u, v, o, d, tn, tf);
+  const float dt = hit ? slot_delta(tn, tf, a.n_slots) : 0.f;
+  unsigned marched = 0, culled = 0;
+  int cnt = 0;
+  if (hit) for_each_kept_slot(a, o, d, tn, dt, marched, culled, [&](float3) { ++cnt; });
+  const int first = warp_reserve(w.n_samples, cnt);
+  const int pix = v * W + u;
+  if (valid) {
+    w.ray_first[pix] = first;
+    w.ray_cnt[pix] = cnt;
+    w.ray_dt[pix] = dt;
+  }
+  if (cnt > 0 && first + cnt <= w.cap) {  // beyond the capacity the host grows it and marches again
+    int k = first;
+    unsigned m2 = 0, c2 = 0;
+    for_each_kept_slot(a, o, d, tn, dt, m2, c2, [&](float3 x) { w.xn[k++] = make_float4(x.x, x.y, x.z, 0.f); });
+  }
+  if (a.stats) {
+    flush_stats(a.stats, ST_RAYS, valid ? 1 : 0);
+    flush_stats(a.stats, ST_HIT, hit ? 1 : 0);
+    flush_stats(a.stats, ST_MARCHED, marched);
+    flush_stats(a.stats, ST_OCC, (unsigned)cnt + culled);
+    flush_stats(a.stats, ST_CULLED, culled);
+  }
+}
+
+// ---- the proposal's bones and start offset for every sample
+template <Prec P>
+__global__ void __launch_bounds__(256) wf_propose_kernel(const RenderArgs a, const WfArgs w) {
+  extern __shared__ float4 smem4[];
+  PosedSmem sm = stage_posed<P>(stage_of(a.P), smem4);
+  const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+  const int n = (int)*w.n_samples;
+  const PropDev& Q = a.P.prop;
+  const int nb = a.P.cfg.nb;
+  unsigned proposed = 0;
+  for (int s0 = (blockIdx.x * warps + (threadIdx.x >> 5)) * 32; s0 < n; s0 += gridDim.x * warps * 32) {
+    const int s = s0 + lane;
+    const bool act = s < n;
+    float3 xn = make_float3(Q.nmin[0], Q.nmin[1], Q.nmin[2]);
+    if (act) {
+      const float4 p = w.xn[s];
+      xn = make_float3(p.x, p.y, p.z);
+    }
+    prop_encode_staged<P>(Q, xn, sm.fs.xstage + lane * kPW1Stride);
+    const float* O = prop_mma_warp<P, true>(sm.fs.pw, sm.fs.xstage, nullptr, Q.b1p, 0) + lane * (kPropMaxOut + 1);
+    if (act) {
+      // the top-2 bones by logit (ties to the lower bone), as the fused search
+      int b0 = 0, b1 = -1;
+      float v0 = O[0], v1 = -3.0e38f;
+      for (int k = 1; k < nb; ++k) {
+        const float v = O[k];
+        if (v > v0) { b1 = b0; v1 = v0; b0 = k; v0 = v; }
+        else if (v > v1) { b1 = k; v1 = v; }
+      }
+      if (b1 < 0) b1 = b0;
+      w.prop[s] = make_float4(__int_as_float(b0 | (b1 << 8)), O[nb], O[nb + 1], O[nb + 2]);
+      ++proposed;
+    }
+    __syncwarp();  // every lane has read its row before the staging area is reused
+  }
+  if (a.stats) flush_stats(a.stats, ST_PROP, proposed);
+}
+
+// ---- search items: wave 0 = every start of every sample (plain search) or the
+//      proposed starts; wave 1 = every start of the fallback samples
+template <bool kProp>
+__global__ void __launch_bounds__(128, 4) wf_search_kernel(const RenderArgs a, const WfArgs w, int wave) {
+  __shared__ float sNinv[kMaxBones * 12];
+  const int nb = a.P.cfg.nb;
+  for (int t = threadIdx.x; t < nb * 12; t += blockDim.x) sNinv[t] = a.P.Ninv[t];
+  __syncthreads();
+  const SkinDev& S = a.P.S;
+  const int nprop = kProp ? min(a.P.prop.top_k, nb) : 0;
+  const int per = (kProp && wave == 0) ? nprop : nb;
+  const int n = wave == 0 ? (int)*w.n_samples : (int)*w.n_fb;
+  const int total = n * per;  // the host keeps samples x bones below 2^31
+  float4* out = wave == 0 ? w.item0 : w.item1;
+  const int max_iter = a.P.cfg.max_iter;
+  const float tol2 = a.P.cfg.tol2;
+  unsigned starts = 0, iters = 0, conv_n = 0;
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+    const int q = (int)((unsigned)it / (unsigned)per), j = it - q * per;
+    const int s = wave == 0 ? q : w.fb[q];
+    const float4 p4 = w.xn[s];
+    const float3 xn = make_float3(p4.x, p4.y, p4.z);
+    int label = j, order = (wave == 0 ? 0 : nprop) + j;
+    float3 poff = make_float3(0.f, 0.f, 0.f);
+    if (kProp && wave == 0) {
+      const float4 pp = w.prop[s];
+      const int bb = __float_as_int(pp.x);
+      label = j == 0 ? (bb & 0xff) : ((bb >> 8) & 0xff);
+      if (j == 0) poff = make_float3(pp.y, pp.z, pp.w);
+      order = j;
+    }
+    const float* A = sNinv + 12 * label;
+    float3 x = make_float3(A[0] * xn.x + A[1] * xn.y + A[2] * xn.z + A[3], A[4] * xn.x + A[5] * xn.y + A[6] * xn.z + A[7],
+                           A[8] * xn.x + A[9] * xn.y + A[10] * xn.z + A[11]);
+    x = make_float3(x.x + poff.x, x.y + poff.y, x.z + poff.z);
+    float Mx[12];
+    blend_value(S, S.M, x, Mx);
+    ++starts;
+    float3 y = apply34(Mx, x);
+    float3 r = make_float3(y.x - xn.x, y.y - xn.y, y.z - xn.z);
+    // initial inverse Jacobian: LBS with the weights frozen at x0, (sum_i w_i R_i)^-1
+    const float J0[9] = {Mx[0], Mx[1], Mx[2], Mx[4], Mx[5], Mx[6], Mx[8], Mx[9], Mx[10]};
+    float H[9];
+    bool conv = false;
+    if (inv3(J0, H)) {
+      for (int k = 0;; ++k) {
+        if (r.x * r.x + r.y * r.y + r.z * r.z < tol2) {
+          conv = true;
+          break;
+        }
+        if (k >= max_iter) break;
+        const float3 dx = make_float3(-(H[0] * r.x + H[1] * r.y + H[2] * r.z), -(H[3] * r.x + H[4] * r.y + H[5] * r.z),
+                                      -(H[6] * r.x + H[7] * r.y + H[8] * r.z));
+        x = make_float3(x.x + dx.x, x.y + dx.y, x.z + dx.z);
+        blend_value(S, S.M, x, Mx);
+        ++iters;
+        y = apply34(Mx, x);
+        const float3 rn = make_float3(y.x - xn.x, y.y - xn.y, y.z - xn.z);
+        const float3 dr = make_float3(rn.x - r.x, rn.y - r.y, rn.z - r.z);
+        r = rn;
+        // good Broyden: H += (dx - H dr)(dx^T H) / (dx^T H dr)
+        const float u0 = H[0] * dr.x + H[1] * dr.y + H[2] * dr.z;
+        const float u1 = H[3] * dr.x + H[4] * dr.y + H[5] * dr.z;
+        const float u2 = H[6] * dr.x + H[7] * dr.y + H[8] * dr.z;
+        const float den = dx.x * u0 + dx.y * u1 + dx.z * u2;
+        if (fabsf(den) > 1e-12f) {
+          const float rden = 1.f / den;
+          const float a0 = (dx.x - u0) * rden, a1 = (dx.y - u1) * rden, a2 = (dx.z - u2) * rden;
+          const float b0 = dx.x * H[0] + dx.y * H[3] + dx.z * H[6];
+          const float b1 = dx.x * H[1] + dx.y * H[4] + dx.z * H[7];
+          const float b2 = dx.x * H[2] + dx.y * H[5] + dx.z * H[8];
+          H[0] += a0 * b0; H[1] += a0 * b1; H[2] += a0 * b2;
+          H[3] += a1 * b0; H[4] += a1 * b1; H[5] += a1 * b2;
+          H[6] += a2 * b0; H[7] += a2 * b1; H[8] += a2 * b2;
+        }
+      }
+    }
+    const bool valid = conv && in_box(S, x);
+    conv_n += valid;
+    out[it] = make_float4(x.x, x.y, x.z, __int_as_float(valid ? ((order << 8) | label) : -1));
+  }
+  if (a.stats) {
+    flush_stats(a.stats, ST_STARTS, starts);
+    flush_stats(a.stats, ST_ITERS, iters);
+    flush_stats(a.stats, ST_CONV, conv_n);
+  }
+}
+
+// ---- the samples whose proposed starts found no root
+__global__ void __launch_bounds__(256) wf_fallback_kernel(const RenderArgs a, const WfArgs w) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = (int)*w.n_samples;
+  const int nprop = min(a.P.prop.top_k, a.P.cfg.nb);
+  bool fall = false;
+  if (s < n) {
+    fall = true;
+    for (int j = 0; j < nprop; ++j) fall &= __float_as_int(w.item0[(size_t)s * nprop + j].w) < 0;
+  }
+  const int idx = warp_reserve(w.n_fb, fall ? 1 : 0);
+  if (s < n) w.fbidx[s] = fall ? idx : -1;
+  if (fall) w.fb[idx] = s;
+  if (a.stats) flush_stats(a.stats, ST_FALLBACK, fall ? 1 : 0);
+}
+
+// ---- per sample: merge the item results, polish, field, max-density root
+template <Prec P, bool kProp>
+__global__ void __launch_bounds__(256) wf_field_kernel(const RenderArgs a, const WfArgs w) {
+  extern __shared__ float4 smem4[];
+  PosedStage ps = stage_of(a.P);
+  ps.search = 0;  // the field only: no proposal staged here
+  PosedSmem sm = stage_posed<P>(ps, smem4);
+  const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+  const SkinDev& S = a.P.S;
+  const int nb = a.P.cfg.nb;
+  const int nprop = kProp ? min(a.P.prop.top_k, nb) : 0;
+  const int per0 = kProp ? nprop : nb;
+  const int n = (int)*w.n_samples;
+  const ListSmem& qs = sm.list;
+  unsigned roots = 0;
+  for (int s0 = (blockIdx.x * warps + (threadIdx.x >> 5)) * 32; s0 < n; s0 += gridDim.x * warps * 32) {
+    const int m = min(32, n - s0);
+    const int s = s0 + lane;
+    if (lane < m) {
+      const float4 p4 = w.xn[s];
+      const float3 xn = make_float3(p4.x, p4.y, p4.z);
+      int nr = 0;
+      // items in start order: the first of equal roots keeps its position and code
+      auto merge = [&](const float4 r) {
+        const int code = __float_as_int(r.w);
+        if (code < 0) return;
+        for (int j2 = 0; j2 < nr; ++j2) {
+          const float4 o = qs.roots[j2 * kList + lane];
+          const float ddx = r.x - o.x, ddy = r.y - o.y, ddz = r.z - o.z;
+          if (ddx * ddx + ddy * ddy + ddz * ddz < 1e-8f) return;
+        }
+        ++roots;
+        if (nr < kMaxRoots) {
+          qs.roots[nr * kList + lane] = r;
+          ++nr;
+        } else {
+          compress_roots<P>(S, S.M, a.P.F, sm.fs, qs.roots + lane, xn, make_float3(r.x, r.y, r.z), code);
+          nr = 1;
+        }
+      };
+      for (int j = 0; j < per0; ++j) merge(w.item0[(size_t)s * per0 + j]);
+      if (kProp) {
+        const int fi = w.fbidx[s];
+        if (fi >= 0)
+          for (int k = 0; k < nb; ++k) merge(w.item1[(size_t)fi * nb + k]);
+      }
+      qs.nroots[lane] = (uint8_t)nr;
+    }
+    __syncwarp();
+    list_field_phase<P, kProp>(
+        S, a.P.F, sm.fs, qs, m,
+        [&](int i, float3& xq, const float4*& Mq, const float*& Nq, int& pose) {
+          const float4 p4 = w.xn[s0 + i];
+          xq = make_float3(p4.x, p4.y, p4.z);
+          Mq = S.M;
+          Nq = sm.sNinv;
+          pose = 0;
+        },
+        [&](int i, const PosedOut& o) {
+          w.res[s0 + i] = make_float4(o.start >= 0 ? o.sigma : 0.f, o.rgb.x, o.rgb.y, o.rgb.z);
+        });
+  }
+  if (a.stats) flush_stats(a.stats, ST_ROOTS, roots);
+}
+
+// ---- per ray: front-to-back compositing, alpha_i = 1 - exp(-sigma_i delta)
+__global__ void __launch_bounds__(256) wf_composite_kernel(const RenderArgs a, const WfArgs w) {
+  const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+  const int npix = a.cam.width * a.cam.height;
+  unsigned early = 0;
+  if (pix < npix) {
+    const float log_stop = a.early_T > 0.f ? -logf(a.early_T) : __int_as_float(0x7f800000);
+    const int cnt = w.ray_cnt[pix], first = w.ray_first[pix];
+    const float dt = w.ray_dt[pix];
+    float depth = 0.f, cr = 0.f, cg = 0.f, cb = 0.f;
+    for (int j = 0; j < cnt; ++j) {
+      const float4 sres = w.res[first + j];
+      if (sres.x > 0.f) {
+        const float sd = sres.x * dt;
+        const float wgt = expf(-depth) * -expm1f(-sd);  // T_i alpha_i
+        cr = fmaf(wgt, sres.y, cr);
+        cg = fmaf(wgt, sres.z, cg);
+        cb = fmaf(wgt, sres.w, cb);
+        depth += sd;
+      }
+      if (depth > log_stop) {  // transmittance below the threshold: the ray stops
+        ++early;
+        break;
+      }
+    }
+    a.rgb[3 * pix] = cr;
+    a.rgb[3 * pix + 1] = cg;
+    a.rgb[3 * pix + 2] = cb;
+    a.alpha[pix] = -expm1f(-depth);
+  }
+  if (a.stats) flush_stats(a.stats, ST_EARLY, early);
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+template <Prec P>
+constexpr const char* wf_field_name(bool prop) {
+  return P == Prec::F32 ? "wf_field_kernel<fp32>"
+                        : (P == Prec::F16 ? (prop ? "wf_field_kernel<fp16,proposal>" : "wf_field_kernel<fp16>")
+                                          : (prop ? "wf_field_kernel<bf16,proposal>" : "wf_field_kernel<bf16>"));
+}
+
+cudaError_t launch_wf_march(const RenderArgs& a, const WfArgs& w, cudaStream_t s) {
+  KernelSpan span("wf_march_kernel", s);
+  wf_march_kernel<<<(a.n_ray_ids + 255) / 256, 256, 0, s>>>(a, w);
+  return cudaGetLastError();
+}
+
+template <Prec P, bool kProp>
+static cudaError_t launch_wf_rest_p(const RenderArgs& a, const WfArgs& w, int n_samples, int num_sms, cudaStream_t s) {
+  cudaError_t e;
+  const int nb = a.P.cfg.nb;
+  if (n_samples > 0) {
+    if constexpr (kProp) {
+      const size_t smem = posed_smem_bytes_p<P>(256, true);
+      if ((e = set_smem(wf_propose_kernel<P>, smem, 256)) != cudaSuccess) return e;
+      int per_sm = 0;
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wf_propose_kernel<P>, 256, smem)) != cudaSuccess)
+        return e;
+      const int blocks = min((n_samples + 255) / 256, num_sms * max(per_sm, 1));
+      {
+        KernelSpan span(P == Prec::F16 ? "wf_propose_kernel<fp16>" : "wf_propose_kernel<bf16>", s);
+        wf_propose_kernel<P><<<blocks, 256, smem, s>>>(a, w);
+      }
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const int grid = num_sms * 4 * 8;  // persistent-ish: items are handed out grid-stride
+    {
+      KernelSpan span(kProp ? "wf_search_kernel<proposal>" : "wf_search_kernel", s);
+      wf_search_kernel<kProp><<<grid, 128, 0, s>>>(a, w, 0);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if constexpr (kProp) {
+      {
+        KernelSpan span("wf_fallback_kernel", s);
+        wf_fallback_kernel<<<(n_samples + 255) / 256, 256, 0, s>>>(a, w);
+      }
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      {
+        KernelSpan span("wf_search_kernel<fallback>", s);
+        wf_search_kernel<kProp><<<grid, 128, 0, s>>>(a, w, 1);
+      }
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const size_t smem = posed_smem_bytes_p<P>(256, false);
+    if ((e = set_smem(wf_field_kernel<P, kProp>, smem, 256)) != cudaSuccess) return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wf_field_kernel<P, kProp>, 256, smem)) !=
+        cudaSuccess)
+      return e;
+    const int blocks = min((n_samples + 255) / 256, num_sms * max(per_sm, 1));
+    {
+      KernelSpan span(wf_field_name<P>(kProp), s);
+      wf_field_kernel<P, kProp><<<blocks, 256, smem, s>>>(a, w);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    (void)nb;
+  }
+  const int npix = a.cam.width * a.cam.height;
+  {
+    KernelSpan span("wf_composite_kernel", s);
+    wf_composite_kernel<<<(npix + 255) / 256, 256, 0, s>>>(a, w);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wf_rest(const RenderArgs& a, const WfArgs& w, int n_samples, int num_sms, cudaStream_t s) {
+  switch (a.P.prec) {
+    case 1:
+      return a.P.search ? launch_wf_rest_p<Prec::F16, true>(a, w, n_samples, num_sms, s)
+                        : launch_wf_rest_p<Prec::F16, false>(a, w, n_samples, num_sms, s);
+    case 2:
+      return a.P.search ? launch_wf_rest_p<Prec::BF16, true>(a, w, n_samples, num_sms, s)
+                        : launch_wf_rest_p<Prec::BF16, false>(a, w, n_samples, num_sms, s);
+    default:
+      return launch_wf_rest_p<Prec::F32, false>(a, w, n_samples, num_sms, s);
+  }
+}
+
+}  // namespace ia

@@ -16,12 +16,12 @@ RTOL_SIGMA = 1e-4
 ATOL_XSTAR = 2e-5
 
 
-def make_ctx(ia, torch, sc, table, mlp, early_T=0.0, max_samples=None):
+def make_ctx(ia, torch, sc, table, mlp, early_T=0.0, max_samples=None, precision=0):
     cfg = ia.make_config(n_levels=sc.n_levels, log2_table=sc.log2_table, level_res=sc.level_res,
                          max_samples=sc.max_samples if max_samples is None else max_samples,
                          broyden_max_iter=sc.broyden_max_iter, broyden_tol=sc.broyden_tol,
                          occ_res=sc.occ_res, occ_tau=sc.occ_tau, occ_dilate=sc.occ_dilate,
-                         early_stop_T=early_T)
+                         early_stop_T=early_T, precision=precision)
     ctx = ia.ia_create(cfg)
     ia.ia_set_skeleton(ctx, sc.parents, sc.rest_joints, sc.skin_grid, sc.canon_min, sc.canon_max,
                        sc.norm_min, sc.norm_max)

@@ -36,8 +36,8 @@ def scene(request):
     return sc, table, mlp
 
 
-def _pose_ctx(ia, sc, table, mlp, seeds, early_T=0.0):
-    ctx = make_ctx(ia, torch, sc, table, mlp, early_T=early_T)
+def _pose_ctx(ia, sc, table, mlp, seeds, early_T=0.0, precision=0):
+    ctx = make_ctx(ia, torch, sc, table, mlp, early_T=early_T, precision=precision)
     poses = [S.make_pose(sc, s) for s in seeds]
     ia.ia_set_pose(ctx, np.stack([p[0] for p in poses]), np.stack([p[1] for p in poses]))
     return ctx, poses
@@ -273,11 +273,16 @@ def test_march_mask_bit_exact(ia, scene):
     ia.ia_destroy(ctx)
 
 
-def test_render_tiny_full_frame(ia):
+PATHS = {"wavefront": 1, "fused": 0}
+
+
+@pytest.mark.parametrize("path", list(PATHS))
+def test_render_tiny_full_frame(ia, path):
     sc = S.make_scene("tiny", 0)
     table, mlp = S.make_field(sc, 0)
     for seed in (0, 1):
         ctx, om, p, occ, cam = _render_case(ia, sc, table, mlp, seed, 0.0)
+        ia.ia_set_render_path(ctx, PATHS[path])
         W, H = cam["width"], cam["height"]
         rgb = torch.zeros(H * W, 3, device="cuda")
         alpha = torch.zeros(H * W, device="cuda")
@@ -296,7 +301,8 @@ def test_render_tiny_full_frame(ia):
         ia.ia_destroy(ctx)
 
 
-def test_render_early_termination(ia, scene):
+@pytest.mark.parametrize("path", list(PATHS))
+def test_render_early_termination(ia, scene, path):
     sc, table, mlp = scene
     early = 1e-4
     if sc.name == "tiny":
@@ -307,6 +313,7 @@ def test_render_early_termination(ia, scene):
         ctx, om, p, occ, cam = _render_case(ia, sc, table, mlp, 4, early)
         rng = np.random.default_rng(8)
         pix = rng.choice(cam["width"] * cam["height"], 4000, replace=False)
+    ia.ia_set_render_path(ctx, PATHS[path])
     W, H = cam["width"], cam["height"]
     rgb = torch.zeros(H * W, 3, device="cuda")
     alpha = torch.zeros(H * W, device="cuda")
@@ -343,6 +350,65 @@ def test_render_ragged_sizes(ia, size):
     assert close(rgb.cpu().numpy()[ok], ref["rgb"][ok], RTOL_RGB, ATOL_RGB).all()
     assert close(alpha.cpu().numpy()[ok], ref["alpha"][ok], RTOL_RGB, ATOL_RGB).all()
     ia.ia_destroy(ctx)
+
+
+def test_render_paths_agree(ia):
+    """The wavefront schedule (kernels over arrays) and the fused one (one
+    persistent kernel) compute every sample with the same device functions, so
+    the 540 x 540 frames agree to rounding: fp32 plain search and fp16 with the
+    learned proposal (untrained here, so the fallback wave is large), early
+    termination on.  One context renders a small frame first and switches the
+    search mode, so the sample arrays grow and are re-laid out between calls."""
+    sc = S.make_scene("full", 0)
+    table, mlp = S.make_field(sc, 0)
+    for prec in (ia.IA_FP32, ia.IA_FP16):
+        ctx, poses = _pose_ctx(ia, sc, table, mlp, [6], early_T=1e-4, precision=prec)
+        ia.ia_update_occupancy(ctx, 0, ia.IA_OCC_POSE)
+        small, cam = S.make_camera(sc, 64, 64), S.make_camera(sc)
+        modes = [ia.IA_SEARCH_ALL_BONES]
+        if prec == ia.IA_FP16:
+            pc = S.proposal_config()
+            ia.ia_proposal_init(ctx, ia.make_proposal_config(pc["n_levels"], pc["log2_table"], pc["level_res"],
+                                                             pc["top_k"], pc["offset_weight"]))
+            pt, pm = S.proposal_init(sc, pc, 3)
+            ia.ia_proposal_set_params(ctx, torch.from_numpy(pt).cuda(), torch.from_numpy(S.pack_proposal(pm)).cuda())
+            modes.append(ia.IA_SEARCH_PROPOSAL)
+        for mode in modes:
+            ia.ia_set_search(ctx, mode)
+            out = {}
+            for path in ("wavefront", "fused"):
+                ia.ia_set_render_path(ctx, PATHS[path])
+                for c in (small, cam):
+                    n = c["width"] * c["height"]
+                    rgb = torch.full((n, 3), -1.0, device="cuda")
+                    alpha = torch.full((n,), -1.0, device="cuda")
+                    st = ia.ia_render(ctx, 0, camera(ia, c), rgb, alpha, stats=True)
+                out[path] = (rgb.cpu().numpy(), alpha.cpu().numpy(), st)
+            (r1, a1, s1), (r0, a0, s0) = out["wavefront"], out["fused"]
+            d = np.abs(r1 - r0).max()
+            print(f"precision {prec} search {mode}: max |rgb diff| {d:.3g}, alpha {np.abs(a1 - a0).max():.3g}; "
+                  f"samples wavefront {s1['occupied_samples']} fused {s0['occupied_samples']}")
+            assert (a0 >= 0).all() and (a1 >= 0).all()
+            if prec == ia.IA_FP32:
+                np.testing.assert_allclose(r1, r0, rtol=1e-5, atol=1e-5)
+                np.testing.assert_allclose(a1, a0, rtol=1e-5, atol=1e-5)
+            else:
+                # the fused kernel runs the fallback starts through a shared
+                # queue, whose merge order may keep another start's position of
+                # a root (polished to the same root within fp16 rounding)
+                np.testing.assert_allclose(r1, r0, rtol=2e-3, atol=2e-4)
+                np.testing.assert_allclose(a1, a0, rtol=2e-3, atol=2e-4)
+                assert (np.abs(r1 - r0).max(axis=1) > 1e-5).sum() <= 0.01 * (a0 > 0).sum()
+            # the wavefront marches whole rays; the fused kernel stops marching a ray
+            # at early termination
+            assert s1["rays"] == s0["rays"] == cam["width"] * cam["height"]
+            assert s1["early_stopped"] == s0["early_stopped"] > 0
+            assert s1["occupied_samples"] >= s0["occupied_samples"]
+            assert s1["marched_slots"] == s1["hit_rays"] * sc.max_samples
+        with pytest.raises(ia.IAError) as e:
+            ia.ia_set_render_path(ctx, 7)
+        assert e.value.status == ia.IA_ERR_ARG
+        ia.ia_destroy(ctx)
 
 
 def test_render_degenerate_cases(ia):

@@ -274,7 +274,7 @@ def _oracle_fp16(ia, ctx, sc, table, mlp, pc, early_T):
     return om, PP.PropModel(om, pc, pt.reshape(-1, 2), pm_op), (pt, pmf)
 
 
-def _proposal_frame(ia, sc, table, mlp, pc, params, pose, cam, early_T, om, pr, pix):
+def _proposal_frame(ia, sc, table, mlp, pc, params, pose, cam, early_T, om, pr, pix, path=1):
     """fp16 + proposal frame of one pose on the GPU (render_kernel with the
     proposal search and root culling, over the oracle's occupancy bits) and the
     oracle's proposal-mode render of the listed pixels."""
@@ -295,6 +295,7 @@ def _proposal_frame(ia, sc, table, mlp, pc, params, pose, cam, early_T, om, pr, 
     ia.ia_set_search(ctx, ia.IA_SEARCH_PROPOSAL)
     ia.ia_update_occupancy(ctx, 0)  # the pose's root-culling masks
     ia.ia_set_occupancy(ctx, bits)  # the grid: the oracle's
+    ia.ia_set_render_path(ctx, path)
     W, H = cam["width"], cam["height"]
     rgb = torch.zeros(W * H, 3, device="cuda")
     a = torch.zeros(W * H, device="cuda")
@@ -335,8 +336,9 @@ def trained_tiny(ia):
     ia.ia_destroy(ctx)
 
 
-def test_proposal_frame_matches_oracle_tiny(ia, trained_tiny):
-    """The product path's frame, render_kernel<fp16, proposal>, on the whole
+@pytest.mark.parametrize("path", ["wavefront", "fused"])
+def test_proposal_frame_matches_oracle_tiny(ia, trained_tiny, path):
+    """The product path's frame, fp16 with the proposal search, on the whole
     64 x 64 tiny frame of a held-out pose (parity mode: no early termination)
     against the oracle's proposal-mode render (or_render_pixels_prop) with the
     same GPU-trained proposal: colour and opacity of every ray within the fp16
@@ -349,8 +351,9 @@ def test_proposal_frame_matches_oracle_tiny(ia, trained_tiny):
     om, pr, params = _oracle_fp16(ia, ctx, sc, table, mlp, pc, 0.0)
     cam = S.make_camera(sc)
     pix = np.arange(cam["width"] * cam["height"], dtype=np.int32)
-    st, rgb, alpha, ref = _proposal_frame(ia, sc, table, mlp, pc, params, poses[-1], cam, 0.0, om, pr, pix)
-    _check_frame("tiny fp16+proposal frame", st, rgb, alpha, ref)
+    st, rgb, alpha, ref = _proposal_frame(ia, sc, table, mlp, pc, params, poses[-1], cam, 0.0, om, pr, pix,
+                                          {"wavefront": 1, "fused": 0}[path])
+    _check_frame(f"tiny fp16+proposal frame ({path})", st, rgb, alpha, ref)
     fb = int(ref["fallbacks"].sum())
     assert st["proposed"] == st["occupied_samples"] - st["culled"] > 0
     assert abs(st["fallbacks"] + st["culled"] - fb) <= max(3, 0.005 * fb)

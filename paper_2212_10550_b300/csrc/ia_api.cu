@@ -789,7 +789,7 @@ static ia_status render_wavefront(ia_ctx* c, RenderArgs& a, size_t npix, cudaStr
     if (attempt > 0) {
       // the frame outgrew the sample arrays: grow them (with some room) and march again
       const size_t cap = (size_t)n_host + n_host / 4 + 1024;
-      if (cap * (size_t)nb > (size_t)INT32_MAX) return fail(c, IA_ERR_ARG, "ia_render: too many samples in the frame");
+      if (cap * (size_t)nb > (size_t)(INT32_MAX / 2)) return fail(c, IA_ERR_ARG, "ia_render: too many samples in the frame");
       IA_CUDA(c, cudaStreamSynchronize(s), "ia_render");
       c->wf_cap = 0;
       c->wf_per0 = 0;

@@ -101,11 +101,21 @@ __global__ void __launch_bounds__(256) wf_march_kernel(const RenderArgs a, const
 }
 
 // ---- the proposal's bones and start offset for every sample
+// shared memory: the network's weights (reduced precision, the pose's inputs
+// folded into the first layer's bias) and each warp's MMA staging area
+constexpr int kPropPad = (kPropWords + 3) / 4 * 4;
+constexpr size_t propose_smem_bytes(int threads) {
+  return sizeof(uint32_t) * (kPropPad + (size_t)(threads / 32) * kPropStageWords);
+}
+
 template <Prec P>
 __global__ void __launch_bounds__(256) wf_propose_kernel(const RenderArgs a, const WfArgs w) {
   extern __shared__ float4 smem4[];
-  PosedSmem sm = stage_posed<P>(stage_of(a.P), smem4);
+  uint32_t* pw = reinterpret_cast<uint32_t*>(smem4);
+  stage_prop_h<P>(a.P.prop, a.P.cfg.nb, a.P.theta, pw);
+  __syncthreads();
   const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+  uint32_t* xstage = pw + kPropPad + (threadIdx.x >> 5) * kPropStageWords;
   const int n = (int)*w.n_samples;
   const PropDev& Q = a.P.prop;
   const int nb = a.P.cfg.nb;
@@ -118,8 +128,8 @@ __global__ void __launch_bounds__(256) wf_propose_kernel(const RenderArgs a, con
       const float4 p = w.xn[s];
       xn = make_float3(p.x, p.y, p.z);
     }
-    prop_encode_staged<P>(Q, xn, sm.fs.xstage + lane * kPW1Stride);
-    const float* O = prop_mma_warp<P, true>(sm.fs.pw, sm.fs.xstage, nullptr, Q.b1p, 0) + lane * (kPropMaxOut + 1);
+    prop_encode_staged<P>(Q, xn, xstage + lane * kPW1Stride);
+    const float* O = prop_mma_warp<P, true>(pw, xstage, nullptr, Q.b1p, 0) + lane * (kPropMaxOut + 1);
     if (act) {
       // the top-2 bones by logit (ties to the lower bone), as the fused search
       int b0 = 0, b1 = -1;
@@ -140,6 +150,13 @@ __global__ void __launch_bounds__(256) wf_propose_kernel(const RenderArgs a, con
 
 // ---- search items: wave 0 = every start of every sample (plain search) or the
 //      proposed starts; wave 1 = every start of the fallback samples
+// Items are handed out grid-stride in sample-major order, so a warp's lanes
+// run the starts of one or two samples in step: as their iterations converge
+// onto the same few roots, the lanes' gathers fall on the same grid cells and
+// share cache lines.  Measured against it on the full-size frame: refilling
+// each lane with the next item as it finishes (lanes busy but scattered) is
+// 1.2x slower, start-major order (neighbouring samples' starts of one bone
+// together) 1.7x slower.
 template <bool kProp>
 __global__ void __launch_bounds__(128, 4) wf_search_kernel(const RenderArgs a, const WfArgs w, int wave) {
   __shared__ float sNinv[kMaxBones * 12];
@@ -150,7 +167,7 @@ __global__ void __launch_bounds__(128, 4) wf_search_kernel(const RenderArgs a, c
   const int nprop = kProp ? min(a.P.prop.top_k, nb) : 0;
   const int per = (kProp && wave == 0) ? nprop : nb;
   const int n = wave == 0 ? (int)*w.n_samples : (int)*w.n_fb;
-  const int total = n * per;  // the host keeps samples x bones below 2^31
+  const int total = n * per;  // the host keeps samples x bones below 2^30
   float4* out = wave == 0 ? w.item0 : w.item1;
   const int max_iter = a.P.cfg.max_iter;
   const float tol2 = a.P.cfg.tol2;
@@ -244,8 +261,7 @@ __global__ void __launch_bounds__(256) wf_fallback_kernel(const RenderArgs a, co
 
 // ---- per sample: merge the item results, polish, field, max-density root
 template <Prec P, bool kProp>
-__global__ void __launch_bounds__(256) wf_field_kernel(const RenderArgs a, const WfArgs w) {
-  extern __shared__ float4 smem4[];
+__device__ __forceinline__ void field_body(const RenderArgs& a, const WfArgs& w, float4* smem4) {
   PosedStage ps = stage_of(a.P);
   ps.search = 0;  // the field only: no proposal staged here
   PosedSmem sm = stage_posed<P>(ps, smem4);
@@ -291,7 +307,7 @@ __global__ void __launch_bounds__(256) wf_field_kernel(const RenderArgs a, const
       qs.nroots[lane] = (uint8_t)nr;
     }
     __syncwarp();
-    list_field_phase<P, kProp>(
+    list_field_phase<P, P != Prec::F32>(
         S, a.P.F, sm.fs, qs, m,
         [&](int i, float3& xq, const float4*& Mq, const float*& Nq, int& pose) {
           const float4 p4 = w.xn[s0 + i];
@@ -305,6 +321,25 @@ __global__ void __launch_bounds__(256) wf_field_kernel(const RenderArgs a, const
         });
   }
   if (a.stats) flush_stats(a.stats, ST_ROOTS, roots);
+}
+
+// fp32: the per-lane MLP holds its activations in registers (one block of 8 warps per SM)
+__global__ void __launch_bounds__(256) wf_field_kernel_f32(const RenderArgs a, const WfArgs w) {
+  extern __shared__ float4 smem4[];
+  field_body<Prec::F32, false>(a, w, smem4);
+}
+
+// fp16 / bf16: the MLP runs on the warp MMA from staged operands; two blocks per SM
+template <Prec P, bool kProp>
+__global__ void __launch_bounds__(256, 2) wf_field_kernel(const RenderArgs a, const WfArgs w) {
+  extern __shared__ float4 smem4[];
+  field_body<P, kProp>(a, w, smem4);
+}
+
+template <Prec P, bool kProp>
+static constexpr auto field_kernel() {
+  if constexpr (P == Prec::F32) return wf_field_kernel_f32;
+  else return wf_field_kernel<P, kProp>;
 }
 
 // ---- per ray: front-to-back compositing, alpha_i = 1 - exp(-sigma_i delta)
@@ -363,7 +398,7 @@ static cudaError_t launch_wf_rest_p(const RenderArgs& a, const WfArgs& w, int n_
   const int nb = a.P.cfg.nb;
   if (n_samples > 0) {
     if constexpr (kProp) {
-      const size_t smem = posed_smem_bytes_p<P>(256, true);
+      const size_t smem = propose_smem_bytes(256);
       if ((e = set_smem(wf_propose_kernel<P>, smem, 256)) != cudaSuccess) return e;
       int per_sm = 0;
       if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wf_propose_kernel<P>, 256, smem)) != cudaSuccess)
@@ -375,7 +410,7 @@ static cudaError_t launch_wf_rest_p(const RenderArgs& a, const WfArgs& w, int n_
       }
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    const int grid = num_sms * 4 * 8;  // persistent-ish: items are handed out grid-stride
+    const int grid = num_sms * 4 * 8;  // items are handed out grid-stride
     {
       KernelSpan span(kProp ? "wf_search_kernel<proposal>" : "wf_search_kernel", s);
       wf_search_kernel<kProp><<<grid, 128, 0, s>>>(a, w, 0);
@@ -394,15 +429,16 @@ static cudaError_t launch_wf_rest_p(const RenderArgs& a, const WfArgs& w, int n_
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const size_t smem = posed_smem_bytes_p<P>(256, false);
-    if ((e = set_smem(wf_field_kernel<P, kProp>, smem, 256)) != cudaSuccess) return e;
+    constexpr auto kField = field_kernel<P, kProp>();
+    if ((e = set_smem(kField, smem, 256)) != cudaSuccess) return e;
     int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wf_field_kernel<P, kProp>, 256, smem)) !=
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kField, 256, smem)) !=
         cudaSuccess)
       return e;
     const int blocks = min((n_samples + 255) / 256, num_sms * max(per_sm, 1));
     {
       KernelSpan span(wf_field_name<P>(kProp), s);
-      wf_field_kernel<P, kProp><<<blocks, 256, smem, s>>>(a, w);
+      kField<<<blocks, 256, smem, s>>>(a, w);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     (void)nb;

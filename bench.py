@@ -835,12 +835,8 @@ def run_ours(args, rank, world, local_rank):
     peaks, peak_kind = load_peaks()
     sm_mhz = peaks.get("sm_max_mhz", 2032.0)
     peak = fp32_peak_tflops(sm_mhz)
-    flop_render = (FLOP_START * per_frame["starts"] + FLOP_ITER * per_frame["broyden_iters"] +
-                   FLOP_ROOT * per_frame["roots"] + FLOP_SAMPLE * per_frame["occupied_samples"])
     r_ms = statistics.mean(render_ms)
-    achieved = flop_render / (r_ms * 1e-3) / 1e12
-    gather_bytes = frame_gather_bytes(per_frame, GATHER_HASH)
-    g_achieved = gather_bytes / (r_ms * 1e-3) / 1e9
+    r16_ms = statistics.mean(render16)
     peaks_g = gather_peaks(torch, ia, stream, torch.cuda.get_device_properties(0).multi_processor_count)
     l1_src = "ia_gather_probe: random 48-byte records from a 64 KiB table (L1), measured in this run"
     l2_src = "ia_gather_probe: random 48-byte records from a 12.6 MB table (L2), measured in this run"
@@ -848,14 +844,31 @@ def run_ours(args, rank, world, local_rank):
     hbm_src = f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else \
         "fallback HBM figure"
     tc = peaks.get("bf16_tflops", 1800.0)
-    roofline_gather = {"kernel": "render_kernel<fp32>", "bound": "l1-gather", "achieved": round(g_achieved, 1),
-                       "peak": peaks_g["l1"], "unit": "GB/s", "frac": round(g_achieved / peaks_g["l1"], 4),
-                       "traffic": None, "bytes_per_frame": round(gather_bytes), "peak_l2_random": peaks_g["l2"],
-                       "peak_source": l1_src,
-                       "traffic_note": "DRAM bytes per launch come from an ncu capture, not from this run",
-                       "bounds_ms": {"l1_gather": round(gather_bytes / (peaks_g["l1"] * 1e9) * 1e3, 3),
-                                     "fp32_alu": round(flop_render / (peak * 1e12) * 1e3, 3),
-                                     "measured": round(r_ms, 3)}}
+    # ---- the dominant kernel of the plain fp32 frame: the correspondence search
+    search_bytes = GATHER_LBS * (per_frame["starts"] + per_frame["broyden_iters"])
+    s_ms = prof_plain["wf_search_kernel"][1]
+    s_achieved = search_bytes / (s_ms * 1e-3) / 1e9
+    roofline_gather = {"kernel": "wf_search_kernel", "bound": "l1-gather", "achieved": round(s_achieved, 1),
+                       "peak": peaks_g["l1"], "unit": "GB/s", "frac": round(s_achieved / peaks_g["l1"], 4),
+                       "traffic": None, "bytes_per_launch": round(search_bytes), "ms_per_launch": round(s_ms, 4),
+                       "peak_l2_random": peaks_g["l2"], "peak_source": l1_src,
+                       "work": "48 B x 8 corners per LBS evaluation x (starts + Broyden steps) of the frame",
+                       "traffic_note": "DRAM bytes per launch come from an ncu capture, not from this run"}
+    # ---- the whole render (all its kernels) against the same gather peak
+    render_roofline = {}
+    for name, st, hb, pr, ms in (("fp32", per_frame, GATHER_HASH, False, r_ms),
+                                 ("fp16_proposal", per_frame16, GATHER_HASH_H, True, r16_ms)):
+        gb = frame_gather_bytes(st, hb, pr)
+        ach = gb / (ms * 1e-3) / 1e9
+        render_roofline[name] = {"bound": "l1-gather", "achieved": round(ach, 1), "peak": peaks_g["l1"],
+                                 "unit": "GB/s", "frac": round(ach / peaks_g["l1"], 4), "bytes_per_frame": round(gb),
+                                 "render_ms": round(ms, 4)}
+    render_roofline["what"] = ("ia_render's algorithmic gather bytes (search, polish, hash encoding, proposal "
+                               "encoding) over its CUDA-event time, all its kernels and the sample-count read-back")
+    # ---- fp32 field kernel: polish + hash encoding + per-lane fp32 MLP per root
+    f_ms = prof_plain["wf_field_kernel<fp32>"][1]
+    flop_field = FLOP_ROOT * per_frame["roots"]
+    achieved = flop_field / (f_ms * 1e-3) / 1e12
     # ---- per-kernel rooflines: work per launch from the counters, time per launch from launch tracing
     kern = {}
 
@@ -863,11 +876,20 @@ def run_ours(args, rank, world, local_rank):
         if name in prof:
             kern[name] = roofline_entry(name, bound, work, unit_work, prof[name][1], pk, pk_unit, pk_src, what)
 
-    add("render_kernel<fp32>", prof_plain, "l1-gather", frame_gather_bytes(per_frame, GATHER_HASH), "B",
-        peaks_g["l1"], "GB/s", l1_src, "48 B x (starts + Broyden steps) + (48 B + 1 KiB hash) x roots, per frame")
-    add("render_kernel<fp16,proposal>", prof16, "l1-gather", frame_gather_bytes(per_frame16, GATHER_HASH_H, True),
-        "B", peaks_g["l1"], "GB/s", l1_src,
-        "48 B x (starts + Broyden steps) + (48 B + 512 B fp16 hash) x roots + 512 B per proposal evaluation")
+    add("wf_search_kernel", prof_plain, "l1-gather", search_bytes, "B", peaks_g["l1"], "GB/s", l1_src,
+        "48 B x 8 corners x (starts + Broyden steps), plain 24-start search")
+    if "wf_search_kernel<proposal>" in prof16 and "wf_search_kernel<fallback>" in prof16:
+        both_ms = prof16["wf_search_kernel<proposal>"][1] + prof16["wf_search_kernel<fallback>"][1]
+        kern["wf_search_kernel<proposal>+<fallback>"] = roofline_entry(
+            "wf_search_kernel<proposal> + wf_search_kernel<fallback>", "l1-gather",
+            GATHER_LBS * (per_frame16["starts"] + per_frame16["broyden_iters"]), "B", both_ms, peaks_g["l1"],
+            "GB/s", l1_src, "both search waves of the proposal search (the counters do not split them)")
+    add("wf_field_kernel<fp32>", prof_plain, "l1-gather", (GATHER_LBS + GATHER_HASH) * per_frame["roots"], "B",
+        peaks_g["l1"], "GB/s", l1_src, "per distinct root: the polish's LBS evaluation + 1 KiB fp32 hash gathers")
+    add("wf_field_kernel<fp16,proposal>", prof16, "l1-gather", (GATHER_LBS + GATHER_HASH_H) * per_frame16["roots"],
+        "B", peaks_g["l1"], "GB/s", l1_src, "per distinct root: the polish + 512 B fp16 hash gathers")
+    add("wf_propose_kernel<fp16>", prof16, "l1-gather", GATHER_PROP * per_frame16["proposed"], "B", peaks_g["l1"],
+        "GB/s", l1_src, "512 B of proposal-encoding gathers per sample")
     add("occ_density_kernel<fp32>", prof_plain, "l1-gather", frame_gather_bytes(occ_per_frame, GATHER_HASH), "B",
         peaks_g["l1"], "GB/s", l1_src, "the render's byte count over the searched occupancy cells")
     add("occ_density_kernel<fp16,proposal>", prof16, "l1-gather", frame_gather_bytes(occ16, GATHER_HASH_H, True),
@@ -920,10 +942,12 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": f"replicas x{world}", "precision": "fp32", "starts": "all 24 bones",
                    "value": "540x540 frames/s, pose + occupancy refresh + render, plain fp32"},
         "roofline": roofline_gather,
-        "roofline_alu": {"kernel": "render_kernel<fp32>", "bound": "alu", "achieved": round(achieved, 3),
+        "render_roofline": render_roofline,
+        "roofline_alu": {"kernel": "wf_field_kernel<fp32>", "bound": "alu", "achieved": round(achieved, 3),
                          "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                          "peak_source": f"fp32 FMA: 148 SM x 128 lanes x 2 x {sm_mhz:.0f} MHz ({peak_kind} max clock)",
-                         "flop_per_frame": round(flop_render)},
+                         "flop_per_launch": round(flop_field),
+                         "work": "per distinct root: Newton polish, hash encoding, fp32 MLP 32-64-64-4, activations"},
         "rooflines": kern,
         "correspondence": residual,
         "render_only_fps": round(1e3 / r_ms, 3),

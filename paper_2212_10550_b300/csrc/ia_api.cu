@@ -74,7 +74,7 @@ struct ia_ctx {
   size_t out_cap = 0;
   // wavefront render path: per-ray and per-sample arrays, counters
   int render_path = IA_RENDER_WAVEFRONT;
-  size_t wf_ray_cap = 0, wf_cap = 0;
+  size_t wf_ray_cap = 0, wf_cap = 0, wf_icap = 0;
   int wf_per0 = 0;
   bool wf_prop = false;
   int* d_wf_first = nullptr;
@@ -762,8 +762,11 @@ ia_status ia_march_mask(ia_ctx* c, int pose, const ia_camera* cam, uint32_t* slo
 
 // The wavefront path: march (kept samples written per ray), the sample count
 // read back (the per-sample arrays are sized from it; a frame that outgrows
-// them grows them and is marched again), then the search, field and
-// compositing kernels.
+// them grows them and is marched again), then the search and field kernels
+// over chunks of at most kWfChunk samples (their item arrays are sized for
+// one chunk), then compositing.
+constexpr size_t kWfChunk = size_t(1) << 21;
+
 static ia_status render_wavefront(ia_ctx* c, RenderArgs& a, size_t npix, cudaStream_t s) {
   const bool prop = a.P.search != 0;
   const int nb = c->nb;
@@ -789,10 +792,9 @@ static ia_status render_wavefront(ia_ctx* c, RenderArgs& a, size_t npix, cudaStr
     if (attempt > 0) {
       // the frame outgrew the sample arrays: grow them (with some room) and march again
       const size_t cap = (size_t)n_host + n_host / 4 + 1024;
-      if (cap * (size_t)nb > (size_t)(INT32_MAX / 2)) return fail(c, IA_ERR_ARG, "ia_render: too many samples in the frame");
+      if (cap > (size_t)INT32_MAX / 2) return fail(c, IA_ERR_ARG, "ia_render: too many samples in the frame");
       IA_CUDA(c, cudaStreamSynchronize(s), "ia_render");
       c->wf_cap = 0;
-      c->wf_per0 = 0;
       IA_CUDA(c, dalloc(&c->d_wf_xn, cap), "ia_render: wavefront arrays");
       IA_CUDA(c, dalloc(&c->d_wf_res, cap), "ia_render: wavefront arrays");
       c->wf_cap = cap;
@@ -807,9 +809,12 @@ static ia_status render_wavefront(ia_ctx* c, RenderArgs& a, size_t npix, cudaStr
     fits = n_host <= c->wf_cap;
   }
   if (!fits) return fail(c, IA_ERR_STATE, "ia_render: the frame's sample count changed between marches");
-  // the search arrays, sized for the sample capacity and the search mode
-  if (n_host > 0 && (c->wf_per0 != per0 || (prop && !c->wf_prop))) {
-    const size_t cap = c->wf_cap;
+  // the chunk's arrays, sized for min(samples, kWfChunk) and the search mode
+  const size_t chunk = std::min<size_t>(n_host, kWfChunk);
+  if (chunk > 0 && (chunk > c->wf_icap || c->wf_per0 != per0 || (prop && !c->wf_prop))) {
+    const size_t cap = std::max(chunk, c->wf_icap);
+    IA_CUDA(c, cudaStreamSynchronize(s), "ia_render");
+    c->wf_icap = 0;
     c->wf_per0 = 0;
     IA_CUDA(c, dalloc(&c->d_wf_item0, cap * per0), "ia_render: wavefront arrays");
     if (prop) {
@@ -818,18 +823,24 @@ static ia_status render_wavefront(ia_ctx* c, RenderArgs& a, size_t npix, cudaStr
       IA_CUDA(c, dalloc(&c->d_wf_fb, cap), "ia_render: wavefront arrays");
       IA_CUDA(c, dalloc(&c->d_wf_fbidx, cap), "ia_render: wavefront arrays");
     }
+    c->wf_icap = cap;
     c->wf_per0 = per0;
     c->wf_prop = prop;
   }
   w.cap = (int)c->wf_cap;
   w.xn = c->d_wf_xn;
+  w.res = c->d_wf_res;
   w.prop = c->d_wf_prop;
   w.item0 = c->d_wf_item0;
   w.item1 = c->d_wf_item1;
   w.fb = c->d_wf_fb;
   w.fbidx = c->d_wf_fbidx;
-  w.res = c->d_wf_res;
-  IA_CUDA(c, launch_wf_rest(a, w, (int)n_host, c->num_sms, s), "ia_render: kernels");
+  for (size_t s0 = 0; s0 < n_host; s0 += chunk) {
+    w.s0 = (int)s0;
+    w.ns = (int)std::min(chunk, (size_t)n_host - s0);
+    IA_CUDA(c, launch_wf_chunk(a, w, c->num_sms, s), "ia_render: kernels");
+  }
+  IA_CUDA(c, launch_wf_composite(a, w, s), "ia_render: compositing");
   return IA_OK;
 }
 

@@ -173,23 +173,85 @@ __device__ __forceinline__ void blend_value_jac(const SkinDev& S, const float4* 
 }
 
 // 3x3 inverse by the adjugate; false if |det| < 1e-6 (treated as singular)
+// The search's arithmetic below spells every multiply-add out (fmaf) and keeps
+// every other product and sum apart (__fmul_rn, __fadd_rn), so that each
+// kernel that runs the search computes bit-for-bit the same iterates, whatever
+// contractions the compiler would choose in its surroundings.
+__device__ __forceinline__ float dot3(float a0, float a1, float a2, float b0, float b1, float b2) {
+  return fmaf(a0, b0, fmaf(a1, b1, __fmul_rn(a2, b2)));
+}
+
+// a * b - c * d
+__device__ __forceinline__ float cross2(float a, float b, float c, float d) { return fmaf(a, b, -__fmul_rn(c, d)); }
+
 __device__ __forceinline__ bool inv3(const float J[9], float H[9]) {
-  float c00 = J[4] * J[8] - J[5] * J[7];
-  float c01 = J[5] * J[6] - J[3] * J[8];
-  float c02 = J[3] * J[7] - J[4] * J[6];
-  float det = J[0] * c00 + J[1] * c01 + J[2] * c02;
+  const float c00 = cross2(J[4], J[8], J[5], J[7]);
+  const float c01 = cross2(J[5], J[6], J[3], J[8]);
+  const float c02 = cross2(J[3], J[7], J[4], J[6]);
+  const float det = dot3(J[0], J[1], J[2], c00, c01, c02);
   if (!(fabsf(det) >= 1e-6f)) return false;
-  float id = 1.f / det;
-  H[0] = c00 * id;
-  H[1] = (J[2] * J[7] - J[1] * J[8]) * id;
-  H[2] = (J[1] * J[5] - J[2] * J[4]) * id;
-  H[3] = c01 * id;
-  H[4] = (J[0] * J[8] - J[2] * J[6]) * id;
-  H[5] = (J[2] * J[3] - J[0] * J[5]) * id;
-  H[6] = c02 * id;
-  H[7] = (J[1] * J[6] - J[0] * J[7]) * id;
-  H[8] = (J[0] * J[4] - J[1] * J[3]) * id;
+  const float id = 1.f / det;
+  H[0] = __fmul_rn(c00, id);
+  H[1] = __fmul_rn(cross2(J[2], J[7], J[1], J[8]), id);
+  H[2] = __fmul_rn(cross2(J[1], J[5], J[2], J[4]), id);
+  H[3] = __fmul_rn(c01, id);
+  H[4] = __fmul_rn(cross2(J[0], J[8], J[2], J[6]), id);
+  H[5] = __fmul_rn(cross2(J[2], J[3], J[0], J[5]), id);
+  H[6] = __fmul_rn(c02, id);
+  H[7] = __fmul_rn(cross2(J[1], J[6], J[0], J[7]), id);
+  H[8] = __fmul_rn(cross2(J[0], J[4], J[1], J[3]), id);
   return true;
+}
+
+// ---- one bone-wise Broyden search (Sec. 3.1, Eq. 7), shared by every kernel
+//      that searches: start, residual, step direction, rank-one update
+
+// x0 = N_k^-1 [x'; 1] (+ the proposal's start offset)
+__device__ __forceinline__ float3 search_start(const float A[12], float3 xn, bool shift, float3 off) {
+  float3 x = make_float3(fmaf(A[0], xn.x, fmaf(A[1], xn.y, fmaf(A[2], xn.z, A[3]))),
+                         fmaf(A[4], xn.x, fmaf(A[5], xn.y, fmaf(A[6], xn.z, A[7]))),
+                         fmaf(A[8], xn.x, fmaf(A[9], xn.y, fmaf(A[10], xn.z, A[11]))));
+  if (shift) x = make_float3(__fadd_rn(x.x, off.x), __fadd_rn(x.y, off.y), __fadd_rn(x.z, off.z));
+  return x;
+}
+
+// r = M(x) [x; 1] - x'
+__device__ __forceinline__ float3 search_residual(const float Mx[12], float3 x, float3 xn) {
+  return make_float3(__fsub_rn(fmaf(Mx[0], x.x, fmaf(Mx[1], x.y, fmaf(Mx[2], x.z, Mx[3]))), xn.x),
+                     __fsub_rn(fmaf(Mx[4], x.x, fmaf(Mx[5], x.y, fmaf(Mx[6], x.z, Mx[7]))), xn.y),
+                     __fsub_rn(fmaf(Mx[8], x.x, fmaf(Mx[9], x.y, fmaf(Mx[10], x.z, Mx[11]))), xn.z));
+}
+
+__device__ __forceinline__ float search_norm2(float3 r) { return dot3(r.x, r.y, r.z, r.x, r.y, r.z); }
+
+// dx = -H r
+__device__ __forceinline__ float3 search_dir(const float H[9], float3 r) {
+  return make_float3(-dot3(H[0], H[1], H[2], r.x, r.y, r.z), -dot3(H[3], H[4], H[5], r.x, r.y, r.z),
+                     -dot3(H[6], H[7], H[8], r.x, r.y, r.z));
+}
+
+__device__ __forceinline__ float3 add3(float3 a, float3 b) {
+  return make_float3(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y), __fadd_rn(a.z, b.z));
+}
+
+// good Broyden: H += (dx - H dr)(dx^T H) / (dx^T H dr), skipped when the
+// denominator vanishes
+__device__ __forceinline__ void broyden_update(float H[9], float3 dx, float3 dr) {
+  const float u0 = dot3(H[0], H[1], H[2], dr.x, dr.y, dr.z);
+  const float u1 = dot3(H[3], H[4], H[5], dr.x, dr.y, dr.z);
+  const float u2 = dot3(H[6], H[7], H[8], dr.x, dr.y, dr.z);
+  const float den = dot3(dx.x, dx.y, dx.z, u0, u1, u2);
+  if (fabsf(den) > 1e-12f) {
+    const float rden = 1.f / den;  // one reciprocal for the three quotients
+    const float a0 = __fmul_rn(__fsub_rn(dx.x, u0), rden), a1 = __fmul_rn(__fsub_rn(dx.y, u1), rden),
+                a2 = __fmul_rn(__fsub_rn(dx.z, u2), rden);
+    const float b0 = dot3(dx.x, dx.y, dx.z, H[0], H[3], H[6]);
+    const float b1 = dot3(dx.x, dx.y, dx.z, H[1], H[4], H[7]);
+    const float b2 = dot3(dx.x, dx.y, dx.z, H[2], H[5], H[8]);
+    H[0] = fmaf(a0, b0, H[0]); H[1] = fmaf(a0, b1, H[1]); H[2] = fmaf(a0, b2, H[2]);
+    H[3] = fmaf(a1, b0, H[3]); H[4] = fmaf(a1, b1, H[4]); H[5] = fmaf(a1, b2, H[5]);
+    H[6] = fmaf(a2, b0, H[6]); H[7] = fmaf(a2, b1, H[7]); H[8] = fmaf(a2, b2, H[8]);
+  }
 }
 
 __device__ __forceinline__ bool in_box(const SkinDev& S, float3 x) {

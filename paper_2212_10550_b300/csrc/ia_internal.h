@@ -283,24 +283,28 @@ cudaError_t launch_render(const RenderArgs& a, int num_sms, cudaStream_t s);
 
 // Wavefront render path (ia_wavefront.cu): march -> [proposal] -> search waves
 // -> field -> compositing, over these arrays (device, context-owned).
+// The march writes the frame's samples; the search and field kernels then run
+// over chunks [s0, s0 + ns) of them (arrays marked "chunk" are indexed from s0).
 struct WfArgs {
   unsigned* n_samples;  // kept samples of the frame (counter, zeroed by the host)
-  int cap;              // samples the per-sample arrays hold
+  int cap;              // samples xn and res hold
   float4* xn;           // [cap] normalised-space positions, each ray's samples contiguous in slot order
+  float4* res;          // [cap] sigma (0 without a root), rgb
   int* ray_first;       // [W * H] first sample of the pixel's ray
   int* ray_cnt;         // [W * H] its kept samples
   float* ray_dt;        // [W * H] its slot spacing
-  float4* prop;         // [cap] proposal: bones b0 | b1 << 8, start offset
-  float4* item0;        // [cap * starts] first wave: root (x, y, z) and order << 8 | bone, or -1
-  float4* item1;        // [cap * n_bones] fallback wave, indexed by the sample's fallback position
-  int* fb;              // [cap] fallback samples
-  int* fbidx;           // [cap] a sample's fallback position, or -1
-  unsigned* n_fb;       // fallback samples (counter, zeroed by the host)
-  float4* res;          // [cap] sigma (0 without a root), rgb
+  int s0, ns;           // the chunk
+  float4* prop;         // chunk [ns] proposal: bones b0 | b1 << 8, start offset
+  float4* item0;        // chunk [ns * starts] first wave: root (x, y, z) and order << 8 | bone, or -1
+  float4* item1;        // [n_fb * n_bones] fallback wave, indexed by the sample's fallback position
+  int* fb;              // [ns] the chunk's fallback samples (chunk indices)
+  int* fbidx;           // chunk [ns] a sample's fallback position, or -1
+  unsigned* n_fb;       // the chunk's fallback samples (counter, zeroed per chunk)
 };
 cudaError_t launch_wf_march(const RenderArgs& a, const WfArgs& w, cudaStream_t s);
-// everything after the march, for n_samples kept samples (read back by the host)
-cudaError_t launch_wf_rest(const RenderArgs& a, const WfArgs& w, int n_samples, int num_sms, cudaStream_t s);
+// proposal, search waves and field of the chunk w.s0, w.ns
+cudaError_t launch_wf_chunk(const RenderArgs& a, const WfArgs& w, int num_sms, cudaStream_t s);
+cudaError_t launch_wf_composite(const RenderArgs& a, const WfArgs& w, cudaStream_t s);
 cudaError_t launch_march_mask(const RenderArgs& a, uint32_t* mask, cudaStream_t s);
 
 }  // namespace ia

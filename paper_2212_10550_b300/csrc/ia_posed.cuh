@@ -367,61 +367,36 @@ __device__ __forceinline__ void posed_field_list(const SkinDev& S, const FieldDe
       }
       if (!__any_sync(kFull, phase != 2)) break;
       float3 q = x;
-      if (phase == 0) {
-        const float* A = Ninv + 12 * label;
-        q = make_float3(A[0] * xn.x + A[1] * xn.y + A[2] * xn.z + A[3], A[4] * xn.x + A[5] * xn.y + A[6] * xn.z + A[7],
-                        A[8] * xn.x + A[9] * xn.y + A[10] * xn.z + A[11]);
-        if (shift) q = make_float3(q.x + poff.x, q.y + poff.y, q.z + poff.z);
-      } else if (phase == 1) {
-        q = make_float3(x.x + dx.x, x.y + dx.y, x.z + dx.z);
-      }
+      if (phase == 0) q = search_start(Ninv + 12 * label, xn, shift, poff);
+      else if (phase == 1) q = add3(x, dx);
       float Mx[12];
       if (phase != 2) blend_value(S, M, q, Mx);
       bool finish = false, conv = false;
       if (phase == 0) {
         st.starts++;
-        const float3 y = apply34(Mx, q);
         x = q;
-        r = make_float3(y.x - xn.x, y.y - xn.y, y.z - xn.z);
+        r = search_residual(Mx, q, xn);
         // initial inverse Jacobian: LBS with the weights frozen at x0, (sum_i w_i R_i)^-1
         const float J0[9] = {Mx[0], Mx[1], Mx[2], Mx[4], Mx[5], Mx[6], Mx[8], Mx[9], Mx[10]};
         it = 0;
         if (!inv3(J0, H)) finish = true;
       } else if (phase == 1) {
-        const float3 y = apply34(Mx, q);
-        const float3 rn = make_float3(y.x - xn.x, y.y - xn.y, y.z - xn.z);
-        const float3 dr = make_float3(rn.x - r.x, rn.y - r.y, rn.z - r.z);
+        const float3 rn = search_residual(Mx, q, xn);
+        const float3 dr = make_float3(__fsub_rn(rn.x, r.x), __fsub_rn(rn.y, r.y), __fsub_rn(rn.z, r.z));
         x = q;
         r = rn;
         ++it;
         st.iters++;
-        // good Broyden: H += (dx - H dr)(dx^T H) / (dx^T H dr)
-        const float3 d = dx;
-        const float u0 = H[0] * dr.x + H[1] * dr.y + H[2] * dr.z;
-        const float u1 = H[3] * dr.x + H[4] * dr.y + H[5] * dr.z;
-        const float u2 = H[6] * dr.x + H[7] * dr.y + H[8] * dr.z;
-        const float den = d.x * u0 + d.y * u1 + d.z * u2;
-        if (fabsf(den) > 1e-12f) {
-          const float rden = 1.f / den;  // one reciprocal for the three quotients
-          const float a0 = (d.x - u0) * rden, a1 = (d.y - u1) * rden, a2 = (d.z - u2) * rden;
-          const float b0 = d.x * H[0] + d.y * H[3] + d.z * H[6];
-          const float b1 = d.x * H[1] + d.y * H[4] + d.z * H[7];
-          const float b2 = d.x * H[2] + d.y * H[5] + d.z * H[8];
-          H[0] += a0 * b0; H[1] += a0 * b1; H[2] += a0 * b2;
-          H[3] += a1 * b0; H[4] += a1 * b1; H[5] += a1 * b2;
-          H[6] += a2 * b0; H[7] += a2 * b1; H[8] += a2 * b2;
-        }
+        broyden_update(H, dx, dr);
       }
       if (phase != 2 && !finish) {
-        const float rr = r.x * r.x + r.y * r.y + r.z * r.z;
-        if (rr < cfg.tol2) {
+        if (search_norm2(r) < cfg.tol2) {
           conv = true;
           finish = true;
         } else if (it >= cfg.max_iter) {
           finish = true;
         } else {
-          dx = make_float3(-(H[0] * r.x + H[1] * r.y + H[2] * r.z), -(H[3] * r.x + H[4] * r.y + H[5] * r.z),
-                           -(H[6] * r.x + H[7] * r.y + H[8] * r.z));
+          dx = search_dir(H, r);
           phase = 1;
         }
       }

@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(256) wf_propose_kernel(const RenderArgs a, con
   __syncthreads();
   const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
   uint32_t* xstage = pw + kPropPad + (threadIdx.x >> 5) * kPropStageWords;
-  const int n = (int)*w.n_samples;
+  const int n = w.ns;
   const PropDev& Q = a.P.prop;
   const int nb = a.P.cfg.nb;
   unsigned proposed = 0;
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(256) wf_propose_kernel(const RenderArgs a, con
     const bool act = s < n;
     float3 xn = make_float3(Q.nmin[0], Q.nmin[1], Q.nmin[2]);
     if (act) {
-      const float4 p = w.xn[s];
+      const float4 p = w.xn[w.s0 + s];
       xn = make_float3(p.x, p.y, p.z);
     }
     prop_encode_staged<P>(Q, xn, xstage + lane * kPW1Stride);
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(128, 4) wf_search_kernel(const RenderArgs a, c
   const SkinDev& S = a.P.S;
   const int nprop = kProp ? min(a.P.prop.top_k, nb) : 0;
   const int per = (kProp && wave == 0) ? nprop : nb;
-  const int n = wave == 0 ? (int)*w.n_samples : (int)*w.n_fb;
+  const int n = wave == 0 ? w.ns : (int)*w.n_fb;
   const int total = n * per;  // the host keeps samples x bones below 2^30
   float4* out = wave == 0 ? w.item0 : w.item1;
   const int max_iter = a.P.cfg.max_iter;
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(128, 4) wf_search_kernel(const RenderArgs a, c
   for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
     const int q = (int)((unsigned)it / (unsigned)per), j = it - q * per;
     const int s = wave == 0 ? q : w.fb[q];
-    const float4 p4 = w.xn[s];
+    const float4 p4 = w.xn[w.s0 + s];
     const float3 xn = make_float3(p4.x, p4.y, p4.z);
     int label = j, order = (wave == 0 ? 0 : nprop) + j;
     float3 poff = make_float3(0.f, 0.f, 0.f);
@@ -186,50 +186,30 @@ __global__ void __launch_bounds__(128, 4) wf_search_kernel(const RenderArgs a, c
       if (j == 0) poff = make_float3(pp.y, pp.z, pp.w);
       order = j;
     }
-    const float* A = sNinv + 12 * label;
-    float3 x = make_float3(A[0] * xn.x + A[1] * xn.y + A[2] * xn.z + A[3], A[4] * xn.x + A[5] * xn.y + A[6] * xn.z + A[7],
-                           A[8] * xn.x + A[9] * xn.y + A[10] * xn.z + A[11]);
-    x = make_float3(x.x + poff.x, x.y + poff.y, x.z + poff.z);
+    float3 x = search_start(sNinv + 12 * label, xn, kProp && wave == 0 && j == 0, poff);
     float Mx[12];
     blend_value(S, S.M, x, Mx);
     ++starts;
-    float3 y = apply34(Mx, x);
-    float3 r = make_float3(y.x - xn.x, y.y - xn.y, y.z - xn.z);
+    float3 r = search_residual(Mx, x, xn);
     // initial inverse Jacobian: LBS with the weights frozen at x0, (sum_i w_i R_i)^-1
     const float J0[9] = {Mx[0], Mx[1], Mx[2], Mx[4], Mx[5], Mx[6], Mx[8], Mx[9], Mx[10]};
     float H[9];
     bool conv = false;
     if (inv3(J0, H)) {
       for (int k = 0;; ++k) {
-        if (r.x * r.x + r.y * r.y + r.z * r.z < tol2) {
+        if (search_norm2(r) < tol2) {
           conv = true;
           break;
         }
         if (k >= max_iter) break;
-        const float3 dx = make_float3(-(H[0] * r.x + H[1] * r.y + H[2] * r.z), -(H[3] * r.x + H[4] * r.y + H[5] * r.z),
-                                      -(H[6] * r.x + H[7] * r.y + H[8] * r.z));
-        x = make_float3(x.x + dx.x, x.y + dx.y, x.z + dx.z);
+        const float3 dx = search_dir(H, r);
+        x = add3(x, dx);
         blend_value(S, S.M, x, Mx);
         ++iters;
-        y = apply34(Mx, x);
-        const float3 rn = make_float3(y.x - xn.x, y.y - xn.y, y.z - xn.z);
-        const float3 dr = make_float3(rn.x - r.x, rn.y - r.y, rn.z - r.z);
+        const float3 rn = search_residual(Mx, x, xn);
+        const float3 dr = make_float3(__fsub_rn(rn.x, r.x), __fsub_rn(rn.y, r.y), __fsub_rn(rn.z, r.z));
         r = rn;
-        // good Broyden: H += (dx - H dr)(dx^T H) / (dx^T H dr)
-        const float u0 = H[0] * dr.x + H[1] * dr.y + H[2] * dr.z;
-        const float u1 = H[3] * dr.x + H[4] * dr.y + H[5] * dr.z;
-        const float u2 = H[6] * dr.x + H[7] * dr.y + H[8] * dr.z;
-        const float den = dx.x * u0 + dx.y * u1 + dx.z * u2;
-        if (fabsf(den) > 1e-12f) {
-          const float rden = 1.f / den;
-          const float a0 = (dx.x - u0) * rden, a1 = (dx.y - u1) * rden, a2 = (dx.z - u2) * rden;
-          const float b0 = dx.x * H[0] + dx.y * H[3] + dx.z * H[6];
-          const float b1 = dx.x * H[1] + dx.y * H[4] + dx.z * H[7];
-          const float b2 = dx.x * H[2] + dx.y * H[5] + dx.z * H[8];
-          H[0] += a0 * b0; H[1] += a0 * b1; H[2] += a0 * b2;
-          H[3] += a1 * b0; H[4] += a1 * b1; H[5] += a1 * b2;
-          H[6] += a2 * b0; H[7] += a2 * b1; H[8] += a2 * b2;
-        }
+        broyden_update(H, dx, dr);
       }
     }
     const bool valid = conv && in_box(S, x);
@@ -246,7 +226,7 @@ __global__ void __launch_bounds__(128, 4) wf_search_kernel(const RenderArgs a, c
 // ---- the samples whose proposed starts found no root
 __global__ void __launch_bounds__(256) wf_fallback_kernel(const RenderArgs a, const WfArgs w) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n = (int)*w.n_samples;
+  const int n = w.ns;
   const int nprop = min(a.P.prop.top_k, a.P.cfg.nb);
   bool fall = false;
   if (s < n) {
@@ -270,14 +250,14 @@ __device__ __forceinline__ void field_body(const RenderArgs& a, const WfArgs& w,
   const int nb = a.P.cfg.nb;
   const int nprop = kProp ? min(a.P.prop.top_k, nb) : 0;
   const int per0 = kProp ? nprop : nb;
-  const int n = (int)*w.n_samples;
+  const int n = w.ns;
   const ListSmem& qs = sm.list;
   unsigned roots = 0;
   for (int s0 = (blockIdx.x * warps + (threadIdx.x >> 5)) * 32; s0 < n; s0 += gridDim.x * warps * 32) {
     const int m = min(32, n - s0);
     const int s = s0 + lane;
     if (lane < m) {
-      const float4 p4 = w.xn[s];
+      const float4 p4 = w.xn[w.s0 + s];
       const float3 xn = make_float3(p4.x, p4.y, p4.z);
       int nr = 0;
       // items in start order: the first of equal roots keeps its position and code
@@ -310,14 +290,14 @@ __device__ __forceinline__ void field_body(const RenderArgs& a, const WfArgs& w,
     list_field_phase<P, P != Prec::F32>(
         S, a.P.F, sm.fs, qs, m,
         [&](int i, float3& xq, const float4*& Mq, const float*& Nq, int& pose) {
-          const float4 p4 = w.xn[s0 + i];
+          const float4 p4 = w.xn[w.s0 + s0 + i];
           xq = make_float3(p4.x, p4.y, p4.z);
           Mq = S.M;
           Nq = sm.sNinv;
           pose = 0;
         },
         [&](int i, const PosedOut& o) {
-          w.res[s0 + i] = make_float4(o.start >= 0 ? o.sigma : 0.f, o.rgb.x, o.rgb.y, o.rgb.z);
+          w.res[w.s0 + s0 + i] = make_float4(o.start >= 0 ? o.sigma : 0.f, o.rgb.x, o.rgb.y, o.rgb.z);
         });
   }
   if (a.stats) flush_stats(a.stats, ST_ROOTS, roots);
@@ -393,75 +373,75 @@ cudaError_t launch_wf_march(const RenderArgs& a, const WfArgs& w, cudaStream_t s
 }
 
 template <Prec P, bool kProp>
-static cudaError_t launch_wf_rest_p(const RenderArgs& a, const WfArgs& w, int n_samples, int num_sms, cudaStream_t s) {
+static cudaError_t launch_wf_chunk_p(const RenderArgs& a, const WfArgs& w, int num_sms, cudaStream_t s) {
   cudaError_t e;
-  const int nb = a.P.cfg.nb;
-  if (n_samples > 0) {
-    if constexpr (kProp) {
-      const size_t smem = propose_smem_bytes(256);
-      if ((e = set_smem(wf_propose_kernel<P>, smem, 256)) != cudaSuccess) return e;
-      int per_sm = 0;
-      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wf_propose_kernel<P>, 256, smem)) != cudaSuccess)
-        return e;
-      const int blocks = min((n_samples + 255) / 256, num_sms * max(per_sm, 1));
-      {
-        KernelSpan span(P == Prec::F16 ? "wf_propose_kernel<fp16>" : "wf_propose_kernel<bf16>", s);
-        wf_propose_kernel<P><<<blocks, 256, smem, s>>>(a, w);
-      }
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    const int grid = num_sms * 4 * 8;  // items are handed out grid-stride
-    {
-      KernelSpan span(kProp ? "wf_search_kernel<proposal>" : "wf_search_kernel", s);
-      wf_search_kernel<kProp><<<grid, 128, 0, s>>>(a, w, 0);
-    }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if constexpr (kProp) {
-      {
-        KernelSpan span("wf_fallback_kernel", s);
-        wf_fallback_kernel<<<(n_samples + 255) / 256, 256, 0, s>>>(a, w);
-      }
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      {
-        KernelSpan span("wf_search_kernel<fallback>", s);
-        wf_search_kernel<kProp><<<grid, 128, 0, s>>>(a, w, 1);
-      }
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    const size_t smem = posed_smem_bytes_p<P>(256, false);
-    constexpr auto kField = field_kernel<P, kProp>();
-    if ((e = set_smem(kField, smem, 256)) != cudaSuccess) return e;
+  const int n = w.ns;
+  if (n <= 0) return cudaSuccess;
+  if constexpr (kProp) {
+    if ((e = cudaMemsetAsync(w.n_fb, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
+    const size_t smem = propose_smem_bytes(256);
+    if ((e = set_smem(wf_propose_kernel<P>, smem, 256)) != cudaSuccess) return e;
     int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kField, 256, smem)) !=
-        cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wf_propose_kernel<P>, 256, smem)) != cudaSuccess)
       return e;
-    const int blocks = min((n_samples + 255) / 256, num_sms * max(per_sm, 1));
+    const int blocks = min((n + 255) / 256, num_sms * max(per_sm, 1));
     {
-      KernelSpan span(wf_field_name<P>(kProp), s);
-      kField<<<blocks, 256, smem, s>>>(a, w);
+      KernelSpan span(P == Prec::F16 ? "wf_propose_kernel<fp16>" : "wf_propose_kernel<bf16>", s);
+      wf_propose_kernel<P><<<blocks, 256, smem, s>>>(a, w);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    (void)nb;
   }
+  const int grid = num_sms * 4 * 8;  // items are handed out grid-stride
+  {
+    KernelSpan span(kProp ? "wf_search_kernel<proposal>" : "wf_search_kernel", s);
+    wf_search_kernel<kProp><<<grid, 128, 0, s>>>(a, w, 0);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if constexpr (kProp) {
+    {
+      KernelSpan span("wf_fallback_kernel", s);
+      wf_fallback_kernel<<<(n + 255) / 256, 256, 0, s>>>(a, w);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    {
+      KernelSpan span("wf_search_kernel<fallback>", s);
+      wf_search_kernel<kProp><<<grid, 128, 0, s>>>(a, w, 1);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  const size_t smem = posed_smem_bytes_p<P>(256, false);
+  constexpr auto kField = field_kernel<P, kProp>();
+  if ((e = set_smem(kField, smem, 256)) != cudaSuccess) return e;
+  int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kField, 256, smem)) != cudaSuccess) return e;
+  const int blocks = min((n + 255) / 256, num_sms * max(per_sm, 1));
+  {
+    KernelSpan span(wf_field_name<P>(kProp), s);
+    kField<<<blocks, 256, smem, s>>>(a, w);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wf_chunk(const RenderArgs& a, const WfArgs& w, int num_sms, cudaStream_t s) {
+  switch (a.P.prec) {
+    case 1:
+      return a.P.search ? launch_wf_chunk_p<Prec::F16, true>(a, w, num_sms, s)
+                        : launch_wf_chunk_p<Prec::F16, false>(a, w, num_sms, s);
+    case 2:
+      return a.P.search ? launch_wf_chunk_p<Prec::BF16, true>(a, w, num_sms, s)
+                        : launch_wf_chunk_p<Prec::BF16, false>(a, w, num_sms, s);
+    default:
+      return launch_wf_chunk_p<Prec::F32, false>(a, w, num_sms, s);
+  }
+}
+
+cudaError_t launch_wf_composite(const RenderArgs& a, const WfArgs& w, cudaStream_t s) {
   const int npix = a.cam.width * a.cam.height;
   {
     KernelSpan span("wf_composite_kernel", s);
     wf_composite_kernel<<<(npix + 255) / 256, 256, 0, s>>>(a, w);
   }
   return cudaGetLastError();
-}
-
-cudaError_t launch_wf_rest(const RenderArgs& a, const WfArgs& w, int n_samples, int num_sms, cudaStream_t s) {
-  switch (a.P.prec) {
-    case 1:
-      return a.P.search ? launch_wf_rest_p<Prec::F16, true>(a, w, n_samples, num_sms, s)
-                        : launch_wf_rest_p<Prec::F16, false>(a, w, n_samples, num_sms, s);
-    case 2:
-      return a.P.search ? launch_wf_rest_p<Prec::BF16, true>(a, w, n_samples, num_sms, s)
-                        : launch_wf_rest_p<Prec::BF16, false>(a, w, n_samples, num_sms, s);
-    default:
-      return launch_wf_rest_p<Prec::F32, false>(a, w, n_samples, num_sms, s);
-  }
 }
 
 }  // namespace ia

@@ -876,33 +876,44 @@ def run_ours(args, rank, world, local_rank):
         if name in prof:
             kern[name] = roofline_entry(name, bound, work, unit_work, prof[name][1], pk, pk_unit, pk_src, what)
 
-    add("wf_search_kernel", prof_plain, "l1-gather", search_bytes, "B", peaks_g["l1"], "GB/s", l1_src,
-        "48 B x 8 corners x (starts + Broyden steps), plain 24-start search")
-    if "wf_search_kernel<proposal>" in prof16 and "wf_search_kernel<fallback>" in prof16:
-        both_ms = prof16["wf_search_kernel<proposal>"][1] + prof16["wf_search_kernel<fallback>"][1]
-        kern["wf_search_kernel<proposal>+<fallback>"] = roofline_entry(
-            "wf_search_kernel<proposal> + wf_search_kernel<fallback>", "l1-gather",
-            GATHER_LBS * (per_frame16["starts"] + per_frame16["broyden_iters"]), "B", both_ms, peaks_g["l1"],
-            "GB/s", l1_src, "both search waves of the proposal search (the counters do not split them)")
-    add("wf_field_kernel<fp32>", prof_plain, "l1-gather", (GATHER_LBS + GATHER_HASH) * per_frame["roots"], "B",
-        peaks_g["l1"], "GB/s", l1_src, "per distinct root: the polish's LBS evaluation + 1 KiB fp32 hash gathers")
-    add("wf_field_kernel<fp16,proposal>", prof16, "l1-gather", (GATHER_LBS + GATHER_HASH_H) * per_frame16["roots"],
-        "B", peaks_g["l1"], "GB/s", l1_src, "per distinct root: the polish + 512 B fp16 hash gathers")
-    add("wf_propose_kernel<fp16>", prof16, "l1-gather", GATHER_PROP * per_frame16["proposed"], "B", peaks_g["l1"],
-        "GB/s", l1_src, "512 B of proposal-encoding gathers per sample")
-    add("occ_density_kernel<fp32>", prof_plain, "l1-gather", frame_gather_bytes(occ_per_frame, GATHER_HASH), "B",
-        peaks_g["l1"], "GB/s", l1_src, "the render's byte count over the searched occupancy cells")
-    add("occ_density_kernel<fp16,proposal>", prof16, "l1-gather", frame_gather_bytes(occ16, GATHER_HASH_H, True),
-        "B", peaks_g["l1"], "GB/s", l1_src, "as the proposal render, over the searched occupancy cells")
+    def wavefront(prof, st, hash_b, prop, tag, label):
+        """Rooflines of the wavefront kernels of one caller (tag: the launch-name
+        suffix, "" for the render): the search (both waves summed when the
+        proposal runs; the counters do not split them), the field and the
+        proposal network."""
+        def mine(k, base):
+            return k.startswith(base) and (k.endswith(tag) if tag else "[" not in k)
+
+        sk = [k for k in prof if mine(k, "wf_search_kernel")]
+        if sk:
+            kern[f"wf_search_kernel ({label})"] = roofline_entry(
+                " + ".join(sk), "l1-gather", GATHER_LBS * (st["starts"] + st["broyden_iters"]), "B",
+                sum(prof[k][1] * prof[k][0] for k in sk), peaks_g["l1"], "GB/s", l1_src,
+                "48 B x 8 corners x (starts + Broyden steps); time: all its launches per frame (step)")
+        fk = [k for k in prof if mine(k, "wf_field_kernel")]
+        if fk:
+            kern[f"{fk[0]} ({label})"] = roofline_entry(
+                fk[0], "l1-gather", (GATHER_LBS + hash_b) * st["roots"], "B", prof[fk[0]][1] * prof[fk[0]][0],
+                peaks_g["l1"], "GB/s",
+                l1_src, f"per distinct root: the polish's LBS evaluation + {hash_b} B of hash gathers")
+        pk = [k for k in prof if mine(k, "wf_propose_kernel")]
+        if pk and prop:
+            kern[f"{pk[0]} ({label})"] = roofline_entry(
+                pk[0], "l1-gather", GATHER_PROP * st["proposed"], "B", prof[pk[0]][1] * prof[pk[0]][0],
+                peaks_g["l1"], "GB/s",
+                l1_src, "512 B of proposal-encoding gathers per sample")
+
+    wavefront(prof_plain, per_frame, GATHER_HASH, False, "", "render, fp32")
+    wavefront(prof16, per_frame16, GATHER_HASH_H, True, "", "render, fp16 + proposal")
+    wavefront(prof_plain, occ_per_frame, GATHER_HASH, False, " [occupancy]", "occupancy, fp32")
+    wavefront(prof16, occ16, GATHER_HASH_H, True, " [occupancy]", "occupancy, fp16 + proposal")
     V = sc.skin_res ** 3
     add("blend_kernel", prof_plain, "hbm", V * sc.n_bones * 4 + V * 48, "B", hbm, "GB/s", hbm_src,
         "skinning grid read (64^3 x 24 fp32) + blended grid written (64^3 x 48 B)")
     for tname, (tp, tst) in prof_train.items():
         searched = tst["occupied_samples"] - tst["culled"]
         hash_b = GATHER_HASH if tname == "fp32" else GATHER_HASH_H
-        sk = "train_sample_kernel<fp32>" if tname == "fp32" else "train_sample_kernel<fp16,proposal>"
-        add(sk, tp, "l1-gather", frame_gather_bytes(tst, hash_b, tname != "fp32"), "B", peaks_g["l1"], "GB/s",
-            l1_src, "posed field of the step's samples, byte count as the render's")
+        wavefront(tp, tst, hash_b, tname != "fp32", " [train]", f"{tname} train step, 32768 rays")
         # per searched sample: table read for dL/dx*, hash-gradient atomics, skinning-grid
         # atomics (8 corners x 24 bones), the Jacobian's blended-grid gather, dL/dfeatures and x*
         per = hash_b + GATHER_HASH + 8 * sc.n_bones * 4 + GATHER_LBS + 128 + 16

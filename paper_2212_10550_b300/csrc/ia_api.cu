@@ -74,9 +74,9 @@ struct ia_ctx {
   size_t out_cap = 0;
   // wavefront render path: per-ray and per-sample arrays, counters
   int render_path = IA_RENDER_WAVEFRONT;
-  size_t wf_ray_cap = 0, wf_cap = 0, wf_icap = 0;
-  int wf_per0 = 0;
-  bool wf_prop = false;
+  size_t wf_ray_cap = 0, wf_cap = 0;
+  size_t wf_i0_cap = 0;  // float4s in d_wf_item0
+  size_t wf_pcap = 0;    // samples in the proposal arrays (d_wf_prop, d_wf_fb, d_wf_fbidx; d_wf_item1 x n_bones)
   int* d_wf_first = nullptr;
   int* d_wf_cnt = nullptr;
   float* d_wf_dt = nullptr;
@@ -88,6 +88,10 @@ struct ia_ctx {
   int* d_wf_fbidx = nullptr;
   float4* d_wf_res = nullptr;
   unsigned* d_wf_counts = nullptr;  // [0] samples, [1] fallback samples
+  // the occupancy density's query points and results (R^3 each)
+  size_t wf_occ_cap = 0;
+  float4* d_wf_oxn = nullptr;
+  float4* d_wf_ores = nullptr;
   // training-step workspace
   int ray_cap = 0;
   int reg_cap = 0;
@@ -286,17 +290,71 @@ BoxDev box_dev(const ia_ctx* c) {
 // the cells whose point can have a root are searched, the rest get 0 (the same
 // values the full search gives).
 // The culling masks built here stay valid for the render of the same pose.
+// Item arrays of the search waves for chunks of up to cap samples (kept
+// across calls; grown, never shrunk).
+ia_status ensure_wf_items(ia_ctx* c, size_t cap, int per0, bool prop, cudaStream_t s) {
+  if (cap == 0) return IA_OK;
+  if (cap * per0 > c->wf_i0_cap || (prop && cap > c->wf_pcap)) IA_CUDA(c, cudaStreamSynchronize(s), "wavefront arrays");
+  if (cap * per0 > c->wf_i0_cap) {
+    c->wf_i0_cap = 0;
+    IA_CUDA(c, dalloc(&c->d_wf_item0, cap * per0), "wavefront arrays");
+    c->wf_i0_cap = cap * per0;
+  }
+  if (prop && cap > c->wf_pcap) {
+    c->wf_pcap = 0;
+    IA_CUDA(c, dalloc(&c->d_wf_prop, cap), "wavefront arrays");
+    IA_CUDA(c, dalloc(&c->d_wf_item1, cap * c->nb), "wavefront arrays");
+    IA_CUDA(c, dalloc(&c->d_wf_fb, cap), "wavefront arrays");
+    IA_CUDA(c, dalloc(&c->d_wf_fbidx, cap), "wavefront arrays");
+    c->wf_pcap = cap;
+  }
+  if (!c->d_wf_counts) IA_CUDA(c, dalloc(&c->d_wf_counts, (size_t)2), "wavefront arrays");
+  return IA_OK;
+}
+
+// The search and field run on the wavefront kernels over arrays the context
+// keeps for R^3 samples; with fixed_memory (the allocation-free entry) on the
+// fused density kernel, whose lanes run each cell's starts in the same order
+// with the same arithmetic: the same densities bit for bit.
 cudaError_t occ_density(ia_ctx* c, int pose, const float* jitter, float* sigma, unsigned long long* stats,
-                        cudaStream_t s) {
+                        cudaStream_t s, bool fixed_memory) {
   const PosedArgs a = occ_args(c, pose);
   const BoxDev box = box_dev(c);
-  if (!c->occ_cull) return launch_occ_density(a, box, jitter, nullptr, nullptr, sigma, stats, c->d_work, c->num_sms, s);
+  WfArgs w{};
+  if (!fixed_memory) {
+    const size_t n_all = (size_t)box.R * box.R * box.R;
+    const bool prop = a.search != 0;
+    const int per0 = prop ? std::min(c->pcfg.top_k, c->nb) : c->nb;
+    if (c->wf_occ_cap < n_all) {
+      cudaError_t e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return e;
+      c->wf_occ_cap = 0;
+      if ((e = dalloc(&c->d_wf_oxn, n_all)) != cudaSuccess) return e;
+      if ((e = dalloc(&c->d_wf_ores, n_all)) != cudaSuccess) return e;
+      c->wf_occ_cap = n_all;
+    }
+    if (ensure_wf_items(c, n_all, per0, prop, s) != IA_OK) return cudaErrorMemoryAllocation;
+    w.xn = c->d_wf_oxn;
+    w.res = c->d_wf_ores;
+    w.cap = (int)n_all;
+    w.prop = c->d_wf_prop;
+    w.item0 = c->d_wf_item0;
+    w.item1 = c->d_wf_item1;
+    w.fb = c->d_wf_fb;
+    w.fbidx = c->d_wf_fbidx;
+    w.n_fb = c->d_wf_counts + 1;
+  }
+  auto density = [&](const int* cells, const unsigned* count) {
+    return fixed_memory ? launch_occ_density(a, box, jitter, cells, count, sigma, stats, c->d_work, c->num_sms, s)
+                        : launch_wf_occupancy(a, box, jitter, cells, count, sigma, stats, w, c->num_sms, s);
+  };
+  if (!c->occ_cull) return density(nullptr, nullptr);
   c->sub_pose = -1;
   cudaError_t e =
       launch_occ_cull(a, box, jitter, c->d_sub, c->d_cen, c->d_cand_count, c->d_cand, sigma, stats, s);
   if (e != cudaSuccess) return e;
   c->sub_pose = pose;
-  return launch_occ_density(a, box, jitter, c->d_cand, c->d_cand_count, sigma, stats, c->d_work, c->num_sms, s);
+  return density(c->d_cand, c->d_cand_count);
 }
 
 ia_status need_ready(ia_ctx* c, int pose, bool need_occ) {
@@ -447,6 +505,8 @@ void ia_destroy(ia_ctx* c) {
   dfree(c->d_wf_fbidx);
   dfree(c->d_wf_res);
   dfree(c->d_wf_counts);
+  dfree(c->d_wf_oxn);
+  dfree(c->d_wf_ores);
   dfree(c->d_work);
   dfree(c->d_tstats);
   dfree(c->d_out);
@@ -630,7 +690,7 @@ ia_status ia_update_occupancy(ia_ctx* c, int pose, int mode, float* sigma_out, u
   const size_t words = ((size_t)R * R * R + 31) / 32;
   float* sig = sigma_out ? sigma_out : c->d_sigma;
   IA_CUDA(c, cudaMemsetAsync(c->d_stats, 0, sizeof(unsigned long long) * ST_COUNT, s), "ia_update_occupancy");
-  IA_CUDA(c, occ_density(c, pose, nullptr, sig, c->d_stats, s), "ia_update_occupancy: density");
+  IA_CUDA(c, occ_density(c, pose, nullptr, sig, c->d_stats, s, false), "ia_update_occupancy: density");
   if (mode == IA_OCC_POSE) {
     IA_CUDA(c, launch_occ_bits(sig, R, c->cfg.occ_dilate, c->cfg.occ_tau, c->d_occ, nullptr, s),
             "ia_update_occupancy: bits");
@@ -655,7 +715,7 @@ ia_status ia_update_occupancy_ema(ia_ctx* c, int pose, const float* jitter, floa
   const int R = c->cfg.occ_res, n = R * R * R;
   const size_t words = ((size_t)n + 31) / 32;
   IA_CUDA(c, cudaMemsetAsync(c->d_stats, 0, sizeof(unsigned long long) * ST_COUNT, s), "ia_update_occupancy_ema");
-  IA_CUDA(c, occ_density(c, pose, jitter, c->d_sigma, c->d_stats, s), "ia_update_occupancy_ema: density");
+  IA_CUDA(c, occ_density(c, pose, jitter, c->d_sigma, c->d_stats, s, false), "ia_update_occupancy_ema: density");
   IA_CUDA(c, launch_occ_ema(c->d_sigma, c->d_occ_ema, n, decay, s), "ia_update_occupancy_ema: running density");
   IA_CUDA(c, launch_occ_bits(c->d_occ_ema, R, c->cfg.occ_dilate, c->cfg.occ_tau, c->d_occ_train, nullptr, s),
           "ia_update_occupancy_ema: bits");
@@ -768,6 +828,7 @@ ia_status ia_march_mask(ia_ctx* c, int pose, const ia_camera* cam, uint32_t* slo
 constexpr size_t kWfChunk = size_t(1) << 21;
 
 static ia_status render_wavefront(ia_ctx* c, RenderArgs& a, size_t npix, cudaStream_t s) {
+  ia_status st = IA_OK;
   const bool prop = a.P.search != 0;
   const int nb = c->nb;
   const int per0 = prop ? std::min(c->pcfg.top_k, nb) : nb;
@@ -783,6 +844,7 @@ static ia_status render_wavefront(ia_ctx* c, RenderArgs& a, size_t npix, cudaStr
   WfArgs w{};
   w.n_samples = c->d_wf_counts;
   w.n_fb = c->d_wf_counts + 1;
+  w.role = kWfRender;
   w.ray_first = c->d_wf_first;
   w.ray_cnt = c->d_wf_cnt;
   w.ray_dt = c->d_wf_dt;
@@ -811,25 +873,12 @@ static ia_status render_wavefront(ia_ctx* c, RenderArgs& a, size_t npix, cudaStr
   if (!fits) return fail(c, IA_ERR_STATE, "ia_render: the frame's sample count changed between marches");
   // the chunk's arrays, sized for min(samples, kWfChunk) and the search mode
   const size_t chunk = std::min<size_t>(n_host, kWfChunk);
-  if (chunk > 0 && (chunk > c->wf_icap || c->wf_per0 != per0 || (prop && !c->wf_prop))) {
-    const size_t cap = std::max(chunk, c->wf_icap);
-    IA_CUDA(c, cudaStreamSynchronize(s), "ia_render");
-    c->wf_icap = 0;
-    c->wf_per0 = 0;
-    IA_CUDA(c, dalloc(&c->d_wf_item0, cap * per0), "ia_render: wavefront arrays");
-    if (prop) {
-      IA_CUDA(c, dalloc(&c->d_wf_prop, cap), "ia_render: wavefront arrays");
-      IA_CUDA(c, dalloc(&c->d_wf_item1, cap * nb), "ia_render: wavefront arrays");
-      IA_CUDA(c, dalloc(&c->d_wf_fb, cap), "ia_render: wavefront arrays");
-      IA_CUDA(c, dalloc(&c->d_wf_fbidx, cap), "ia_render: wavefront arrays");
-    }
-    c->wf_icap = cap;
-    c->wf_per0 = per0;
-    c->wf_prop = prop;
-  }
+  if ((st = ensure_wf_items(c, chunk, per0, prop, s)) != IA_OK) return st;
   w.cap = (int)c->wf_cap;
   w.xn = c->d_wf_xn;
   w.res = c->d_wf_res;
+  w.pose_stride = 0;  // one pose
+  w.ninv = a.P.Ninv;
   w.prop = c->d_wf_prop;
   w.item0 = c->d_wf_item0;
   w.item1 = c->d_wf_item1;
@@ -1034,6 +1083,32 @@ ia_status train_prepare(ia_ctx* c, const ia_batch* b, int occ_grid, bool need_ta
   a.stats = c->d_tstats;
   a.pose_tot = c->d_pose_ws;
   a.pose_fill = c->d_pose_ws + c->n_poses;
+  // the forward's search and field: the wavefront kernels over the emitted
+  // samples, one chunk whose size the device holds
+  {
+    const bool wprop = a.P.search != 0 && c->cfg.precision != IA_FP32;
+    const int per0 = wprop ? std::min(c->pcfg.top_k, c->nb) : c->nb;
+    ia_status st2 = ensure_wf_items(c, c->s_cap, per0, wprop, s);
+    if (st2 != IA_OK) return st2;
+    WfArgs& w = a.wf;
+    w = WfArgs{};
+    w.xn = c->d_s_pos;
+    w.res = c->d_s_out;
+    w.xs = c->d_s_x;
+    w.cap = (int)c->s_cap;
+    w.pose_stride = (int)(3 * V);
+    w.ninv = a.P.Ninv;
+    w.s0 = 0;
+    w.ns = (int)c->s_cap;
+    w.ns_dev = reinterpret_cast<const unsigned*>(c->d_count);
+    w.prop = c->d_wf_prop;
+    w.item0 = c->d_wf_item0;
+    w.item1 = c->d_wf_item1;
+    w.fb = c->d_wf_fb;
+    w.fbidx = c->d_wf_fbidx;
+    w.n_fb = c->d_wf_counts + 1;
+    w.role = kWfTrain;
+  }
   if (a.P.search) {
     if (c->n_poses > c->pb1_cap) {
       IA_CUDA(c, cudaStreamSynchronize(s), "ia_train_step");
@@ -1552,7 +1627,7 @@ ia_status ia_update_occupancy_static(ia_ctx* c, int pose, uint32_t* bits_out, vo
   // every one of the R^3 cells is written (searched, or set to 0 when culled)
   // before the bits kernel reads them, so the scratch needs no clearing; cells
   // past R^3 are never read
-  IA_CUDA(c, occ_density(c, pose, nullptr, sigma, nullptr, s), "ia_update_occupancy_static: density");
+  IA_CUDA(c, occ_density(c, pose, nullptr, sigma, nullptr, s, true), "ia_update_occupancy_static: density");
   IA_CUDA(c, launch_occ_bits(sigma, R, c->cfg.occ_dilate, c->cfg.occ_tau, c->d_occ, nullptr, s),
           "ia_update_occupancy_static: bits");
   c->have_occ = true;

@@ -97,6 +97,36 @@ struct RenderArgs {
   unsigned long long* stats;
 };
 
+// The march writes the frame's samples; the search and field kernels then run
+// over chunks [s0, s0 + ns) of them (arrays marked "chunk" are indexed from
+// s0).  The training step's forward runs the same kernels over its emitted
+// samples (one chunk, its count on the device, one pose per sample).
+struct WfArgs {
+  unsigned* n_samples;  // kept samples of the frame (counter, zeroed by the host)
+  int cap;              // samples xn and res hold
+  float4* xn;           // [cap] normalised-space positions and pose (int bits of w), each ray's
+                        // samples contiguous in slot order
+  float4* res;          // [cap] sigma (0 without a root), rgb
+  float4* xs;           // [cap] or null: the selected root x* and 1 (0 without a root)
+  int pose_stride;      // float4s per pose of the blended grids S.M (3 V)
+  const float* ninv;    // [poses][n_bones][12] inverse rest-to-pose transforms
+  int* ray_first;       // [W * H] first sample of the pixel's ray
+  int* ray_cnt;         // [W * H] its kept samples
+  float* ray_dt;        // [W * H] its slot spacing
+  int s0, ns;           // the chunk (ns: its size, or an upper bound of *ns_dev)
+  const unsigned* ns_dev;  // or null: the chunk's size on the device (then s0 = 0)
+  float4* prop;         // chunk [ns] proposal: bones b0 | b1 << 8, start offset
+  float4* item0;        // chunk [ns * starts] first wave: root (x, y, z) and order << 8 | bone, or -1
+  float4* item1;        // [n_fb * n_bones] fallback wave, indexed by the sample's fallback position
+  int* fb;              // [ns] the chunk's fallback samples (chunk indices)
+  int* fbidx;           // chunk [ns] a sample's fallback position, or -1
+  unsigned* n_fb;       // the chunk's fallback samples (counter, zeroed per chunk)
+  int role;             // the caller, for the launch names: kWfRender, kWfOccupancy, kWfTrain
+};
+constexpr int kWfRender = 0, kWfOccupancy = 1, kWfTrain = 2;
+
+__device__ __forceinline__ int chunk_size(const WfArgs& w) { return w.ns_dev ? (int)*w.ns_dev : w.ns; }
+
 // Training step (ia_train.cu).  Per-sample workspace: one column of kActStride
 // floats holds the recomputed features, hidden activations and their gradients
 // (F [32], H1 [64], H2 [64], dH1 [64], dH2 [64], dO [4]).
@@ -105,6 +135,7 @@ constexpr int kMlpPadT = (kMlpSmemFloats + 3) / 4 * 4;
 
 struct TrainArgs {
   PosedArgs P;           // P.S.M and P.Ninv point at pose 0 of the per-pose arrays
+  WfArgs wf;             // the forward's search and field over the emitted samples
   int V;                 // skinning-grid vertices (one pose's blended grid = 3V float4)
   const float* B0inv;    // [n_poses][12]
   const float* N;        // [n_poses][nb][12]
@@ -283,28 +314,16 @@ cudaError_t launch_render(const RenderArgs& a, int num_sms, cudaStream_t s);
 
 // Wavefront render path (ia_wavefront.cu): march -> [proposal] -> search waves
 // -> field -> compositing, over these arrays (device, context-owned).
-// The march writes the frame's samples; the search and field kernels then run
-// over chunks [s0, s0 + ns) of them (arrays marked "chunk" are indexed from s0).
-struct WfArgs {
-  unsigned* n_samples;  // kept samples of the frame (counter, zeroed by the host)
-  int cap;              // samples xn and res hold
-  float4* xn;           // [cap] normalised-space positions, each ray's samples contiguous in slot order
-  float4* res;          // [cap] sigma (0 without a root), rgb
-  int* ray_first;       // [W * H] first sample of the pixel's ray
-  int* ray_cnt;         // [W * H] its kept samples
-  float* ray_dt;        // [W * H] its slot spacing
-  int s0, ns;           // the chunk
-  float4* prop;         // chunk [ns] proposal: bones b0 | b1 << 8, start offset
-  float4* item0;        // chunk [ns * starts] first wave: root (x, y, z) and order << 8 | bone, or -1
-  float4* item1;        // [n_fb * n_bones] fallback wave, indexed by the sample's fallback position
-  int* fb;              // [ns] the chunk's fallback samples (chunk indices)
-  int* fbidx;           // chunk [ns] a sample's fallback position, or -1
-  unsigned* n_fb;       // the chunk's fallback samples (counter, zeroed per chunk)
-};
 cudaError_t launch_wf_march(const RenderArgs& a, const WfArgs& w, cudaStream_t s);
 // proposal, search waves and field of the chunk w.s0, w.ns
 cudaError_t launch_wf_chunk(const RenderArgs& a, const WfArgs& w, int num_sms, cudaStream_t s);
 cudaError_t launch_wf_composite(const RenderArgs& a, const WfArgs& w, cudaStream_t s);
+// density at the occupancy cells' query points (cells/count: the candidates, or
+// null for every cell) through the chunk kernels; w: xn, res with R^3 entries,
+// the item arrays for R^3 samples, n_fb
+cudaError_t launch_wf_occupancy(const PosedArgs& P, const BoxDev& box, const float* jitter, const int* cells,
+                                const unsigned* count, float* sigma, unsigned long long* stats, WfArgs w, int num_sms,
+                                cudaStream_t s);
 cudaError_t launch_march_mask(const RenderArgs& a, uint32_t* mask, cudaStream_t s);
 
 }  // namespace ia

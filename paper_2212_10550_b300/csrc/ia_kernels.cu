@@ -241,16 +241,14 @@ cudaError_t launch_blend(int P, int V, int nb, const float* W, const float* N, f
 // Occupancy grid (Sec. 3.3, inference mode)
 // ---------------------------------------------------------------------------
 
-// Per warp: a list of kOccList cells taken from a shared counter (lists differ
-// a lot in cost: a cell without a root runs every start to the iteration cap),
-// its (cell, start) items handed to the lanes start-major from a shared queue,
-// so each cell still runs its starts in order (measured on the culled 64^3
-// grid of the full-size scene: 0.73 ms against 0.78 ms with 32-cell lists and
-// one cell per lane; with culling there are few lists per warp, and smaller
-// lists even out the warps' loads).
+// The fused occupancy density, kept for the allocation-free entry (the other
+// occupancy calls run the wavefront kernels over the candidate cells): per
+// warp a list of kOccList cells from a shared counter, each lane running its
+// cell's starts in order with the search arithmetic and merge rule of the
+// wavefront search, so both give the same densities bit for bit.
 // cells: the cells to search (occ_cand_kernel's list, *count of them), or null
 // for every cell of the grid.
-constexpr int kOccList = 16;
+constexpr int kOccList = 32;
 template <Prec P, bool kProp>
 __global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS)
     occ_density_kernel(const PosedArgs a, const BoxDev box, const float* __restrict__ jitter,
@@ -263,7 +261,7 @@ __global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS)
   SampleStats st;
   for (int list = next_list(work); list * kOccList < n; list = next_list(work)) {
     const int base = list * kOccList;
-    posed_field_list<P, ItemOrder::kStartMajor, kProp>(
+    posed_field_list<P, ItemOrder::kPerLane, kProp>(
         a.S, a.F, a.cfg, sm.fs, sm.list, min(kOccList, n - base),
         [&](int i, float3& xn, const float4*& M, const float*& Ni, int& pose) {
           const int c = cells ? cells[base + i] : base + i;

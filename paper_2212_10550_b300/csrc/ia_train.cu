@@ -164,55 +164,6 @@ __global__ void reg_grad_kernel(const TrainArgs a) {
   if ((threadIdx.x & 31) == 0 && l != 0.f) atomicAdd(a.loss, l);
 }
 
-template <Prec P, bool kProp>
-__global__ void __launch_bounds__(256) train_sample_kernel(const TrainArgs a) {
-  extern __shared__ float4 smem4[];
-  PosedStage ps;
-  ps.mlp = a.P.mlp;
-  ps.n_in = a.P.n_in;
-  ps.table_h = a.P.table_h;
-  ps.search = kProp ? 1 : 0;  // proposal: layer-1 bias per lane from P.prop.b1p
-  ps.prop = a.P.prop;
-  ps.theta = nullptr;
-  ps.Ninv = a.P.Ninv;
-  ps.nb = a.P.cfg.nb;
-  PosedSmem sm = stage_posed<P>(ps, smem4);
-  const int n = *a.count;
-  SampleStats st;
-  // per warp: lists of kList consecutive samples (one or two poses, since the
-  // samples are grouped by pose) from a shared counter, searched with lane refill
-  for (int list = next_list(a.work); list * kList < n; list = next_list(a.work)) {
-    const int base = list * kList;
-    posed_field_list<P, ItemOrder::kSampleMajor, kProp>(
-        a.P.S, a.P.F, a.P.cfg, sm.fs, sm.list, min(kList, n - base),
-        [&](int i, float3& xn, const float4*& M, const float*& Ni, int& pose) {
-          const float4 p = a.s_pos[base + i];
-          pose = __float_as_int(p.w);
-          xn = make_float3(p.x, p.y, p.z);
-          M = a.P.S.M + (size_t)pose * a.V * 3;
-          Ni = a.P.Ninv + (size_t)pose * a.P.cfg.nb * 12;
-        },
-        [&](int i, const PosedOut& o) {
-          const bool has = o.start >= 0;
-          a.s_out[base + i] = make_float4(has ? o.sigma : 0.f, o.rgb.x, o.rgb.y, o.rgb.z);
-          a.s_x[base + i] = make_float4(o.xstar.x, o.xstar.y, o.xstar.z, has ? 1.f : 0.f);
-        },
-        st, a.P.prop, kProp);
-  }
-  flush_stats(a.stats, ST_STARTS, st.starts);
-  flush_stats(a.stats, ST_ITERS, st.iters);
-  flush_stats(a.stats, ST_CONV, st.converged);
-  flush_stats(a.stats, ST_ROOTS, st.roots);
-  flush_stats(a.stats, ST_PROP, st.proposed);
-  flush_stats(a.stats, ST_FALLBACK, st.fallbacks);
-}
-
-template <Prec P>
-static size_t train_sample_smem(bool prop) {
-  return sizeof(float) * (mlp_smem_words(P, 256, prop) + kMaxBones * 12) +
-         sizeof(uint32_t) * (256 / 32) * list_smem_words(prop);
-}
-
 // The step's own loss for ray r (Sec. 3.4, Eq. 9-11), averaged over the rays
 // and added to *a.loss (one atomic per warp; every lane of the warp calls), and
 // its gradients g = dL/dC, ga = dL/dalpha.
@@ -1135,23 +1086,14 @@ cudaError_t launch_train_forward(const TrainArgs& a, int num_sms, cudaStream_t s
         cudaSuccess)
       return e;
   }
-  const bool prop = a.P.search != 0 && P != Prec::F32;
-  auto sample = P == Prec::F32   ? train_sample_kernel<Prec::F32, false>
-                : P == Prec::F16 ? (prop ? train_sample_kernel<Prec::F16, true> : train_sample_kernel<Prec::F16, false>)
-                                 : (prop ? train_sample_kernel<Prec::BF16, true> : train_sample_kernel<Prec::BF16, false>);
-  const char* sample_name = P == Prec::F32   ? "train_sample_kernel<fp32>"
-                            : P == Prec::F16 ? (prop ? "train_sample_kernel<fp16,proposal>" : "train_sample_kernel<fp16>")
-                                             : (prop ? "train_sample_kernel<bf16,proposal>" : "train_sample_kernel<bf16>");
-  const size_t smem = P == Prec::F32   ? train_sample_smem<Prec::F32>(false)
-                      : P == Prec::F16 ? train_sample_smem<Prec::F16>(prop) : train_sample_smem<Prec::BF16>(prop);
-  if ((e = set_smem(sample, smem, 256)) != cudaSuccess) return e;
-  int per_sm = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sample, 256, smem)) != cudaSuccess) return e;
-  {
-    KernelSpan span(sample_name, s);
-    sample<<<num_sms * (per_sm < 1 ? 1 : per_sm), 256, smem, s>>>(a);
-  }
-  return cudaGetLastError();
+  // search and field at the emitted samples: the render's wavefront kernels
+  // (proposal, search waves, field) with each sample's pose
+  RenderArgs ra{};
+  ra.P = a.P;
+  ra.P.theta = nullptr;  // the proposal's layer-1 bias per pose comes from P.prop.b1p
+  if (P == Prec::F32) ra.P.search = 0;
+  ra.stats = a.stats;
+  return launch_wf_chunk(ra, a.wf, num_sms, s);
 }
 
 cudaError_t launch_train_composite(const TrainArgs& a, cudaStream_t s) {

@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(256) wf_propose_kernel(const RenderArgs a, con
   __syncthreads();
   const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
   uint32_t* xstage = pw + kPropPad + (threadIdx.x >> 5) * kPropStageWords;
-  const int n = w.ns;
+  const int n = chunk_size(w);
   const PropDev& Q = a.P.prop;
   const int nb = a.P.cfg.nb;
   unsigned proposed = 0;
@@ -124,12 +124,15 @@ __global__ void __launch_bounds__(256) wf_propose_kernel(const RenderArgs a, con
     const int s = s0 + lane;
     const bool act = s < n;
     float3 xn = make_float3(Q.nmin[0], Q.nmin[1], Q.nmin[2]);
+    int pose = 0;
     if (act) {
       const float4 p = w.xn[w.s0 + s];
       xn = make_float3(p.x, p.y, p.z);
+      pose = __float_as_int(p.w);
     }
     prop_encode_staged<P>(Q, xn, xstage + lane * kPW1Stride);
-    const float* O = prop_mma_warp<P, true>(pw, xstage, nullptr, Q.b1p, 0) + lane * (kPropMaxOut + 1);
+    // with per-pose layer-1 biases (Q.b1p) each row takes its sample's pose's
+    const float* O = prop_mma_warp<P, true>(pw, xstage, nullptr, Q.b1p, pose) + lane * (kPropMaxOut + 1);
     if (act) {
       // the top-2 bones by logit (ties to the lower bone), as the fused search
       int b0 = 0, b1 = -1;
@@ -159,14 +162,11 @@ __global__ void __launch_bounds__(256) wf_propose_kernel(const RenderArgs a, con
 // together) 1.7x slower.
 template <bool kProp>
 __global__ void __launch_bounds__(128, 4) wf_search_kernel(const RenderArgs a, const WfArgs w, int wave) {
-  __shared__ float sNinv[kMaxBones * 12];
   const int nb = a.P.cfg.nb;
-  for (int t = threadIdx.x; t < nb * 12; t += blockDim.x) sNinv[t] = a.P.Ninv[t];
-  __syncthreads();
   const SkinDev& S = a.P.S;
   const int nprop = kProp ? min(a.P.prop.top_k, nb) : 0;
   const int per = (kProp && wave == 0) ? nprop : nb;
-  const int n = wave == 0 ? w.ns : (int)*w.n_fb;
+  const int n = wave == 0 ? chunk_size(w) : (int)*w.n_fb;
   const int total = n * per;  // the host keeps samples x bones below 2^30
   float4* out = wave == 0 ? w.item0 : w.item1;
   const int max_iter = a.P.cfg.max_iter;
@@ -177,6 +177,8 @@ __global__ void __launch_bounds__(128, 4) wf_search_kernel(const RenderArgs a, c
     const int s = wave == 0 ? q : w.fb[q];
     const float4 p4 = w.xn[w.s0 + s];
     const float3 xn = make_float3(p4.x, p4.y, p4.z);
+    const int pose = __float_as_int(p4.w);
+    const float4* M = S.M + (size_t)pose * w.pose_stride;
     int label = j, order = (wave == 0 ? 0 : nprop) + j;
     float3 poff = make_float3(0.f, 0.f, 0.f);
     if (kProp && wave == 0) {
@@ -186,9 +188,9 @@ __global__ void __launch_bounds__(128, 4) wf_search_kernel(const RenderArgs a, c
       if (j == 0) poff = make_float3(pp.y, pp.z, pp.w);
       order = j;
     }
-    float3 x = search_start(sNinv + 12 * label, xn, kProp && wave == 0 && j == 0, poff);
+    float3 x = search_start(w.ninv + ((size_t)pose * nb + label) * 12, xn, kProp && wave == 0 && j == 0, poff);
     float Mx[12];
-    blend_value(S, S.M, x, Mx);
+    blend_value(S, M, x, Mx);
     ++starts;
     float3 r = search_residual(Mx, x, xn);
     // initial inverse Jacobian: LBS with the weights frozen at x0, (sum_i w_i R_i)^-1
@@ -204,7 +206,7 @@ __global__ void __launch_bounds__(128, 4) wf_search_kernel(const RenderArgs a, c
         if (k >= max_iter) break;
         const float3 dx = search_dir(H, r);
         x = add3(x, dx);
-        blend_value(S, S.M, x, Mx);
+        blend_value(S, M, x, Mx);
         ++iters;
         const float3 rn = search_residual(Mx, x, xn);
         const float3 dr = make_float3(__fsub_rn(rn.x, r.x), __fsub_rn(rn.y, r.y), __fsub_rn(rn.z, r.z));
@@ -225,18 +227,23 @@ __global__ void __launch_bounds__(128, 4) wf_search_kernel(const RenderArgs a, c
 
 // ---- the samples whose proposed starts found no root
 __global__ void __launch_bounds__(256) wf_fallback_kernel(const RenderArgs a, const WfArgs w) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n = w.ns;
+  const int n = chunk_size(w);
   const int nprop = min(a.P.prop.top_k, a.P.cfg.nb);
-  bool fall = false;
-  if (s < n) {
-    fall = true;
-    for (int j = 0; j < nprop; ++j) fall &= __float_as_int(w.item0[(size_t)s * nprop + j].w) < 0;
+  unsigned fell = 0;
+  // whole warps step together (warp_reserve needs all 32 lanes)
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int s = base + threadIdx.x;
+    bool fall = false;
+    if (s < n) {
+      fall = true;
+      for (int j = 0; j < nprop; ++j) fall &= __float_as_int(w.item0[(size_t)s * nprop + j].w) < 0;
+    }
+    const int idx = warp_reserve(w.n_fb, fall ? 1 : 0);
+    if (s < n) w.fbidx[s] = fall ? idx : -1;
+    if (fall) w.fb[idx] = s;
+    fell += fall;
   }
-  const int idx = warp_reserve(w.n_fb, fall ? 1 : 0);
-  if (s < n) w.fbidx[s] = fall ? idx : -1;
-  if (fall) w.fb[idx] = s;
-  if (a.stats) flush_stats(a.stats, ST_FALLBACK, fall ? 1 : 0);
+  if (a.stats) flush_stats(a.stats, ST_FALLBACK, fell);
 }
 
 // ---- per sample: merge the item results, polish, field, max-density root
@@ -250,7 +257,7 @@ __device__ __forceinline__ void field_body(const RenderArgs& a, const WfArgs& w,
   const int nb = a.P.cfg.nb;
   const int nprop = kProp ? min(a.P.prop.top_k, nb) : 0;
   const int per0 = kProp ? nprop : nb;
-  const int n = w.ns;
+  const int n = chunk_size(w);
   const ListSmem& qs = sm.list;
   unsigned roots = 0;
   for (int s0 = (blockIdx.x * warps + (threadIdx.x >> 5)) * 32; s0 < n; s0 += gridDim.x * warps * 32) {
@@ -259,6 +266,7 @@ __device__ __forceinline__ void field_body(const RenderArgs& a, const WfArgs& w,
     if (lane < m) {
       const float4 p4 = w.xn[w.s0 + s];
       const float3 xn = make_float3(p4.x, p4.y, p4.z);
+      const float4* M = S.M + (size_t)__float_as_int(p4.w) * w.pose_stride;
       int nr = 0;
       // items in start order: the first of equal roots keeps its position and code
       auto merge = [&](const float4 r) {
@@ -274,7 +282,7 @@ __device__ __forceinline__ void field_body(const RenderArgs& a, const WfArgs& w,
           qs.roots[nr * kList + lane] = r;
           ++nr;
         } else {
-          compress_roots<P>(S, S.M, a.P.F, sm.fs, qs.roots + lane, xn, make_float3(r.x, r.y, r.z), code);
+          compress_roots<P>(S, M, a.P.F, sm.fs, qs.roots + lane, xn, make_float3(r.x, r.y, r.z), code);
           nr = 1;
         }
       };
@@ -292,12 +300,14 @@ __device__ __forceinline__ void field_body(const RenderArgs& a, const WfArgs& w,
         [&](int i, float3& xq, const float4*& Mq, const float*& Nq, int& pose) {
           const float4 p4 = w.xn[w.s0 + s0 + i];
           xq = make_float3(p4.x, p4.y, p4.z);
-          Mq = S.M;
-          Nq = sm.sNinv;
-          pose = 0;
+          pose = __float_as_int(p4.w);
+          Mq = S.M + (size_t)pose * w.pose_stride;
+          Nq = w.ninv + (size_t)pose * nb * 12;
         },
         [&](int i, const PosedOut& o) {
-          w.res[w.s0 + s0 + i] = make_float4(o.start >= 0 ? o.sigma : 0.f, o.rgb.x, o.rgb.y, o.rgb.z);
+          const bool has = o.start >= 0;
+          w.res[w.s0 + s0 + i] = make_float4(has ? o.sigma : 0.f, o.rgb.x, o.rgb.y, o.rgb.z);
+          if (w.xs) w.xs[w.s0 + s0 + i] = make_float4(o.xstar.x, o.xstar.y, o.xstar.z, has ? 1.f : 0.f);
         });
   }
   if (a.stats) flush_stats(a.stats, ST_ROOTS, roots);
@@ -309,9 +319,11 @@ __global__ void __launch_bounds__(256) wf_field_kernel_f32(const RenderArgs a, c
   field_body<Prec::F32, false>(a, w, smem4);
 }
 
-// fp16 / bf16: the MLP runs on the warp MMA from staged operands; two blocks per SM
+// fp16 / bf16: the MLP runs on the warp MMA from staged operands; with the
+// proposal (2 proposed items per sample to merge, and the fallback's) two
+// blocks per SM, with the plain search (24 items per sample) one
 template <Prec P, bool kProp>
-__global__ void __launch_bounds__(256, 2) wf_field_kernel(const RenderArgs a, const WfArgs w) {
+__global__ void __launch_bounds__(256, kProp ? 2 : 1) wf_field_kernel(const RenderArgs a, const WfArgs w) {
   extern __shared__ float4 smem4[];
   field_body<P, kProp>(a, w, smem4);
 }
@@ -359,11 +371,28 @@ __global__ void __launch_bounds__(256) wf_composite_kernel(const RenderArgs a, c
 // Host side
 // ---------------------------------------------------------------------------
 
+// launch names for the traces, by caller: the render, the occupancy density,
+// the training step's forward
+#define IA_WF_NAMES(base) \
+  { base, base " [occupancy]", base " [train]" }
+constexpr const char* kNameSearch[3] = IA_WF_NAMES("wf_search_kernel");
+constexpr const char* kNameSearchProp[3] = IA_WF_NAMES("wf_search_kernel<proposal>");
+constexpr const char* kNameSearchFb[3] = IA_WF_NAMES("wf_search_kernel<fallback>");
+constexpr const char* kNameFallback[3] = IA_WF_NAMES("wf_fallback_kernel");
+constexpr const char* kNamePropose16[3] = IA_WF_NAMES("wf_propose_kernel<fp16>");
+constexpr const char* kNamePropose16b[3] = IA_WF_NAMES("wf_propose_kernel<bf16>");
+constexpr const char* kNameField32[3] = IA_WF_NAMES("wf_field_kernel<fp32>");
+constexpr const char* kNameField16[3] = IA_WF_NAMES("wf_field_kernel<fp16>");
+constexpr const char* kNameField16p[3] = IA_WF_NAMES("wf_field_kernel<fp16,proposal>");
+constexpr const char* kNameFieldB[3] = IA_WF_NAMES("wf_field_kernel<bf16>");
+constexpr const char* kNameFieldBp[3] = IA_WF_NAMES("wf_field_kernel<bf16,proposal>");
+#undef IA_WF_NAMES
+
 template <Prec P>
-constexpr const char* wf_field_name(bool prop) {
-  return P == Prec::F32 ? "wf_field_kernel<fp32>"
-                        : (P == Prec::F16 ? (prop ? "wf_field_kernel<fp16,proposal>" : "wf_field_kernel<fp16>")
-                                          : (prop ? "wf_field_kernel<bf16,proposal>" : "wf_field_kernel<bf16>"));
+constexpr const char* wf_field_name(bool prop, int role) {
+  return P == Prec::F32 ? kNameField32[role]
+                        : (P == Prec::F16 ? (prop ? kNameField16p[role] : kNameField16[role])
+                                          : (prop ? kNameFieldBp[role] : kNameFieldB[role]));
 }
 
 cudaError_t launch_wf_march(const RenderArgs& a, const WfArgs& w, cudaStream_t s) {
@@ -386,25 +415,25 @@ static cudaError_t launch_wf_chunk_p(const RenderArgs& a, const WfArgs& w, int n
       return e;
     const int blocks = min((n + 255) / 256, num_sms * max(per_sm, 1));
     {
-      KernelSpan span(P == Prec::F16 ? "wf_propose_kernel<fp16>" : "wf_propose_kernel<bf16>", s);
+      KernelSpan span(P == Prec::F16 ? kNamePropose16[w.role] : kNamePropose16b[w.role], s);
       wf_propose_kernel<P><<<blocks, 256, smem, s>>>(a, w);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   const int grid = num_sms * 4 * 8;  // items are handed out grid-stride
   {
-    KernelSpan span(kProp ? "wf_search_kernel<proposal>" : "wf_search_kernel", s);
+    KernelSpan span(kProp ? kNameSearchProp[w.role] : kNameSearch[w.role], s);
     wf_search_kernel<kProp><<<grid, 128, 0, s>>>(a, w, 0);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if constexpr (kProp) {
     {
-      KernelSpan span("wf_fallback_kernel", s);
-      wf_fallback_kernel<<<(n + 255) / 256, 256, 0, s>>>(a, w);
+      KernelSpan span(kNameFallback[w.role], s);
+      wf_fallback_kernel<<<min((n + 255) / 256, num_sms * 8), 256, 0, s>>>(a, w);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
-      KernelSpan span("wf_search_kernel<fallback>", s);
+      KernelSpan span(kNameSearchFb[w.role], s);
       wf_search_kernel<kProp><<<grid, 128, 0, s>>>(a, w, 1);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -416,7 +445,7 @@ static cudaError_t launch_wf_chunk_p(const RenderArgs& a, const WfArgs& w, int n
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kField, 256, smem)) != cudaSuccess) return e;
   const int blocks = min((n + 255) / 256, num_sms * max(per_sm, 1));
   {
-    KernelSpan span(wf_field_name<P>(kProp), s);
+    KernelSpan span(wf_field_name<P>(kProp, w.role), s);
     kField<<<blocks, 256, smem, s>>>(a, w);
   }
   return cudaGetLastError();
@@ -433,6 +462,56 @@ cudaError_t launch_wf_chunk(const RenderArgs& a, const WfArgs& w, int num_sms, c
     default:
       return launch_wf_chunk_p<Prec::F32, false>(a, w, num_sms, s);
   }
+}
+
+// ---- occupancy density (Sec. 3.3) through the same kernels: each searched
+//      cell's query point is a sample of pose 0, its density goes back to the
+//      cell's entry of sigma
+__global__ void wf_occ_points_kernel(const BoxDev box, const float* __restrict__ jitter,
+                                     const int* __restrict__ cells, const unsigned* __restrict__ count, int n_all,
+                                     float4* __restrict__ xn) {
+  const int n = cells ? (int)*count : n_all;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int c = cells ? cells[i] : i;
+    const float3 x = jitter ? cell_point(box, c, jitter + 3 * (size_t)c) : cell_center(box, c);
+    xn[i] = make_float4(x.x, x.y, x.z, 0.f);  // pose 0 (int bits of 0.f)
+  }
+}
+
+__global__ void wf_occ_scatter_kernel(const int* __restrict__ cells, const unsigned* __restrict__ count, int n_all,
+                                      const float4* __restrict__ res, float* __restrict__ sigma) {
+  const int n = cells ? (int)*count : n_all;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    sigma[cells ? cells[i] : i] = res[i].x;
+}
+
+cudaError_t launch_wf_occupancy(const PosedArgs& P, const BoxDev& box, const float* jitter, const int* cells,
+                                const unsigned* count, float* sigma, unsigned long long* stats, WfArgs w, int num_sms,
+                                cudaStream_t s) {
+  const int n_all = box.R * box.R * box.R;
+  RenderArgs ra{};
+  ra.P = P;
+  ra.stats = stats;
+  w.s0 = 0;
+  w.ns = n_all;
+  w.ns_dev = cells ? count : nullptr;
+  w.pose_stride = 0;
+  w.ninv = P.Ninv;
+  w.xs = nullptr;
+  w.role = kWfOccupancy;
+  const int blocks = min((n_all + 255) / 256, num_sms * 8);
+  cudaError_t e;
+  {
+    KernelSpan span("wf_occ_points_kernel", s);
+    wf_occ_points_kernel<<<blocks, 256, 0, s>>>(box, jitter, cells, count, n_all, w.xn);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_wf_chunk(ra, w, num_sms, s)) != cudaSuccess) return e;
+  {
+    KernelSpan span("wf_occ_scatter_kernel", s);
+    wf_occ_scatter_kernel<<<blocks, 256, 0, s>>>(cells, count, n_all, w.res, sigma);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_wf_composite(const RenderArgs& a, const WfArgs& w, cudaStream_t s) {

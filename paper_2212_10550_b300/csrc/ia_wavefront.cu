@@ -19,14 +19,17 @@
 //   wf_composite_kernel  one thread per ray: front-to-back compositing of its
 //                        samples with early termination (Sec. 3.2, Eq. 8)
 //
-// Each sample's result is the fused render's (same starts, Broyden steps,
-// merge rule, polish, field and selection); the difference is the schedule.
-// The search items are independent and light (128 registers, four blocks of
-// four warps per SM against one block of eight warps for the fused kernel),
-// and the proposal's fallback starts, a few per ray where they occur, form one
-// dense wave instead of a tail per list.  Samples behind the point where a
-// ray's transmittance falls below the threshold are searched too (the march
-// does not know the densities yet): +2.5 % on the full-size workload.
+// Each sample's result is bit for bit the fused render's: the same starts, the
+// same explicitly rounded Broyden arithmetic (ia_device.cuh), merge rule,
+// polish, field and selection; the difference is the schedule.  The search
+// items are independent and light (128 registers, four blocks of four warps
+// per SM against one block of eight warps for the fused kernel), and the
+// proposal's fallback starts, a few per ray where they occur, form one dense
+// wave instead of a tail per list.  Samples behind the point where a ray's
+// transmittance falls below the threshold are searched too (the march does
+// not know the densities yet): 3 % more samples on the full-size frame.  The
+// training step's forward and the occupancy refresh run the same per-sample
+// kernels over their own samples (each with its pose).
 #include "ia_internal.h"
 
 namespace ia {
@@ -66,7 +69,12 @@ __device__ __forceinline__ void for_each_kept_slot(const RenderArgs& a, const fl
 
 }  // namespace
 
-// ---- march: count, reserve, emit (one thread per ray id, tile order)
+// ---- march: count, reserve, emit (one thread per ray id, tile order).
+//      Measured against it: one warp per ray with its lanes over the slots and
+//      one reservation per block (0.64 ms: the block's atomic on one counter
+//      is on every block's critical path), and a warp marching 32 rays in turn
+//      with its lanes over the slots (0.128 ms against 0.111 ms: the ballots,
+//      broadcasts and mask bookkeeping cost as much as the second pass saved).
 __global__ void __launch_bounds__(256) wf_march_kernel(const RenderArgs a, const WfArgs w) {
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
   const int W = a.cam.width, H = a.cam.height;
@@ -314,7 +322,8 @@ __device__ __forceinline__ void field_body(const RenderArgs& a, const WfArgs& w,
 }
 
 // fp32: the per-lane MLP holds its activations in registers (one block of 8 warps per SM)
-__global__ void __launch_bounds__(256) wf_field_kernel_f32(const RenderArgs a, const WfArgs w) {
+constexpr int kFieldThreadsF32 = 256;
+__global__ void __launch_bounds__(kFieldThreadsF32) wf_field_kernel_f32(const RenderArgs a, const WfArgs w) {
   extern __shared__ float4 smem4[];
   field_body<Prec::F32, false>(a, w, smem4);
 }
@@ -326,6 +335,11 @@ template <Prec P, bool kProp>
 __global__ void __launch_bounds__(256, kProp ? 2 : 1) wf_field_kernel(const RenderArgs a, const WfArgs w) {
   extern __shared__ float4 smem4[];
   field_body<P, kProp>(a, w, smem4);
+}
+
+template <Prec P>
+constexpr int field_threads() {
+  return P == Prec::F32 ? kFieldThreadsF32 : 256;
 }
 
 template <Prec P, bool kProp>
@@ -438,15 +452,16 @@ static cudaError_t launch_wf_chunk_p(const RenderArgs& a, const WfArgs& w, int n
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  const size_t smem = posed_smem_bytes_p<P>(256, false);
+  constexpr int kFT = field_threads<P>();
+  const size_t smem = posed_smem_bytes_p<P>(kFT, false);
   constexpr auto kField = field_kernel<P, kProp>();
-  if ((e = set_smem(kField, smem, 256)) != cudaSuccess) return e;
+  if ((e = set_smem(kField, smem, kFT)) != cudaSuccess) return e;
   int per_sm = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kField, 256, smem)) != cudaSuccess) return e;
-  const int blocks = min((n + 255) / 256, num_sms * max(per_sm, 1));
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kField, kFT, smem)) != cudaSuccess) return e;
+  const int blocks = min((n + kFT - 1) / kFT, num_sms * max(per_sm, 1));
   {
     KernelSpan span(wf_field_name<P>(kProp, w.role), s);
-    kField<<<blocks, 256, smem, s>>>(a, w);
+    kField<<<blocks, kFT, smem, s>>>(a, w);
   }
   return cudaGetLastError();
 }

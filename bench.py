@@ -917,10 +917,12 @@ def run_ours(args, rank, world, local_rank):
         # per searched sample: table read for dL/dx*, hash-gradient atomics, skinning-grid
         # atomics (8 corners x 24 bones), the Jacobian's blended-grid gather, dL/dfeatures and x*
         per = hash_b + GATHER_HASH + 8 * sc.n_bones * 4 + GATHER_LBS + 128 + 16
-        if "train_scatter_kernel" in tp:
-            kern[f"train_scatter_kernel ({tname})"] = roofline_entry(
-                "train_scatter_kernel", "l2-gather", per * searched, "B", tp["train_scatter_kernel"][1], peaks_g["l2"],
-                "GB/s", l2_src, "per searched sample: table read + float2 hash atomics + skinning-grid atomics + "
+        sc_names = [k for k in ("train_hash_grad_kernel", "train_ift_kernel") if k in tp]
+        if sc_names:
+            kern[f"train scatter ({tname})"] = roofline_entry(
+                " + ".join(sc_names), "l2-gather", per * searched, "B", sum(tp[k][1] for k in sc_names),
+                peaks_g["l2"], "GB/s", l2_src,
+                "per searched sample: table read + float2 hash atomics + skinning-grid atomics + "
                 "Jacobian gather + dL/dfeatures, L2-resident")
         if tname != "fp32":
             add("wgrad_tc_kernel", tp, "hbm", WGRAD_ROW_BYTES * searched, "B", hbm, "GB/s", hbm_src,

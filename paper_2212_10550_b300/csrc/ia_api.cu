@@ -114,6 +114,7 @@ struct ia_ctx {
   float4* d_s_x = nullptr;
   float4* d_s_grad = nullptr;
   float4* d_s_dfeat = nullptr;
+  float4* d_s_gx = nullptr;
   float* d_act = nullptr;           // fp32 step: per-sample activations
   uint16_t* d_X = nullptr;          // fp16 / bf16 step: channel-major GEMM operands
   int64_t x_ld = 0;
@@ -524,6 +525,7 @@ void ia_destroy(ia_ctx* c) {
   dfree(c->d_s_x);
   dfree(c->d_s_grad);
   dfree(c->d_s_dfeat);
+  dfree(c->d_s_gx);
   dfree(c->d_act);
   dfree(c->d_X);
   dfree(c->d_scale);
@@ -974,6 +976,7 @@ ia_status train_prepare(ia_ctx* c, const ia_batch* b, int occ_grid, bool need_ta
     IA_CUDA(c, dalloc(&c->d_s_x, cap), "ia_train_step: workspace");
     IA_CUDA(c, dalloc(&c->d_s_grad, cap), "ia_train_step: workspace");
     IA_CUDA(c, dalloc(&c->d_s_dfeat, cap * (kIn / 4)), "ia_train_step: workspace");
+    IA_CUDA(c, dalloc(&c->d_s_gx, cap), "ia_train_step: workspace");
     if (c->cfg.precision == IA_FP32) {
       IA_CUDA(c, dalloc(&c->d_act, cap * kActStride), "ia_train_step: workspace");
     } else {
@@ -1057,6 +1060,7 @@ ia_status train_prepare(ia_ctx* c, const ia_batch* b, int occ_grid, bool need_ta
   a.s_x = c->d_s_x;
   a.s_grad = c->d_s_grad;
   a.s_dfeat = c->d_s_dfeat;
+  a.s_gx = c->d_s_gx;
   a.work = c->d_work + 1;
   a.n_reg = b->n_reg;
   a.reg_x = b->reg_x;

@@ -185,6 +185,7 @@ struct TrainArgs {
   int* pose_tot;         // [n_poses] samples per pose, then the first index of each pose (zeroed by the host)
   int* pose_fill;        // [n_poses] fill counters (zeroed by the host)
   float4* s_dfeat;       // [samples][kIn / 4] dL/dfeatures (fp32, unscaled)
+  float4* s_gx;          // [samples] dL/dx* of the hash encoding (between the scatter's two kernels)
   unsigned* work;        // list counter of the sample kernel (zeroed by the host)
   // occupancy-based density regulariser (Eq. 12)
   int n_reg;

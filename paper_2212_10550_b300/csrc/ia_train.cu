@@ -458,28 +458,22 @@ __device__ __forceinline__ void hash_backward(const TrainArgs& a, float3 xs, con
 }
 
 
-// Per-sample scatter of the backward: hash-table gradient (trilinear weights of
-// dL/dfeatures), dL/dx*, and the implicit-function gradient to the bone
-// transforms and the skinning grid.  Few registers, so many warps hide the
-// gathers and atomics.  Warps walk the samples in order (grouped by pose).
+// The backward's scatter, in two kernels so that each one's working set stays
+// in L2 (one kernel reading the hash table, the skinning grid and the poses'
+// blended grids while scatter-adding into the table and skinning-grid
+// gradients re-read its lines from DRAM about four times over):
+//  train_hash_grad_kernel: hash-table gradient (trilinear weights of
+//    dL/dfeatures) and dL/dx*, one thread per sample, dL/dx* into s_gx;
+//  train_ift_kernel: the implicit-function gradient to the bone transforms
+//    and the skinning grid, warps walking the samples in order (grouped by
+//    pose, so a pose's blended grid stays in L2).
 template <bool kHalfTable>
-__global__ void __launch_bounds__(256) train_scatter_kernel(const TrainArgs a) {
+__global__ void __launch_bounds__(256) train_hash_grad_kernel(const TrainArgs a) {
   const int n = *a.count;
-  const int lane = threadIdx.x & 31;
-  const int stride = gridDim.x * blockDim.x;
-  for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
-    const int s = base + lane;
-    bool has = false;
-    float3 xs = make_float3(0.f, 0.f, 0.f);
-    int pose = 0;
-    if (s < n) {
-      const float4 x4 = a.s_x[s];
-      has = x4.w > 0.f;
-      xs = make_float3(x4.x, x4.y, x4.z);
-      pose = __float_as_int(a.s_pos[s].w);
-    }
-    float gx = 0.f, gy = 0.f, gz = 0.f;
-    if (has) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    const float4 x4 = a.s_x[s];
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (x4.w > 0.f) {
       float dfeat[kIn];
       const float4* src = a.s_dfeat + (size_t)s * (kIn / 4);
 #pragma unroll
@@ -490,10 +484,46 @@ __global__ void __launch_bounds__(256) train_scatter_kernel(const TrainArgs a) {
         dfeat[4 * i + 2] = v.z;
         dfeat[4 * i + 3] = v.w;
       }
-      hash_backward<kHalfTable>(a, xs, dfeat, gx, gy, gz);
+      hash_backward<kHalfTable>(a, make_float3(x4.x, x4.y, x4.z), dfeat, g.x, g.y, g.z);
     }
-    ift_scatter_warp(a, has, pose, xs, gx, gy, gz);
+    a.s_gx[s] = g;
   }
+}
+
+__global__ void __launch_bounds__(256) train_ift_kernel(const TrainArgs a) {
+  const int n = *a.count;
+  const int lane = threadIdx.x & 31;
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+    const int s = base + lane;
+    bool has = false;
+    float3 xs = make_float3(0.f, 0.f, 0.f);
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+    int pose = 0;
+    if (s < n) {
+      const float4 x4 = a.s_x[s];
+      has = x4.w > 0.f;
+      xs = make_float3(x4.x, x4.y, x4.z);
+      pose = __float_as_int(a.s_pos[s].w);
+      g = a.s_gx[s];
+    }
+    ift_scatter_warp(a, has, pose, xs, g.x, g.y, g.z);
+  }
+}
+
+static cudaError_t launch_scatter(const TrainArgs& a, bool half_table, int num_sms, cudaStream_t s) {
+  cudaError_t e;
+  {
+    KernelSpan span("train_hash_grad_kernel", s);
+    if (half_table) train_hash_grad_kernel<true><<<num_sms * 8, 256, 0, s>>>(a);
+    else train_hash_grad_kernel<false><<<num_sms * 8, 256, 0, s>>>(a);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  {
+    KernelSpan span("train_ift_kernel", s);
+    train_ift_kernel<<<num_sms * 8, 256, 0, s>>>(a);
+  }
+  return cudaGetLastError();
 }
 
 // The 64-wide loops run rolled (a fully unrolled body does not fit the
@@ -1133,11 +1163,7 @@ cudaError_t launch_train_backward(const TrainArgs& a, const CUtensorMap* map, in
       train_backward_kernel<<<num_sms * 4, 128, vec_bytes, s>>>(a);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    {
-      KernelSpan span("train_scatter_kernel", s);
-      train_scatter_kernel<false><<<num_sms * 8, 256, 0, s>>>(a);
-    }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_scatter(a, false, num_sms, s)) != cudaSuccess) return e;
     {
       KernelSpan span("mlp_grad_kernel", s);
       mlp_grad_kernel<<<num_sms * 4, 256, 0, s>>>(a);
@@ -1158,11 +1184,7 @@ cudaError_t launch_train_backward(const TrainArgs& a, const CUtensorMap* map, in
     }
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  {
-    KernelSpan span("train_scatter_kernel", s);
-    train_scatter_kernel<true><<<num_sms * 8, 256, 0, s>>>(a);
-  }
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_scatter(a, true, num_sms, s)) != cudaSuccess) return e;
   WgradArgs w{};
   w.count = a.count;
   w.scale = a.scale;

@@ -10,7 +10,7 @@ import pytest
 
 import oracle as O
 import synthetic as S
-from gpu_helpers import ATOL_RGB, RTOL_RGB, close, make_ctx, points_near_body
+from gpu_helpers import ATOL_RGB, RTOL_RGB, camera, close, make_ctx, points_near_body
 from oracle import grad as G
 
 pytestmark = pytest.mark.gpu
@@ -266,6 +266,31 @@ def test_adam_step_matches_its_definition(ia, prec):
             v = b2 * v + (1 - b2) * gg * gg
             x = x - lr * (m / (1 - b1 ** t)) / (np.sqrt(v / (1 - b2 ** t)) + eps)
         np.testing.assert_allclose(out, x, rtol=1e-5, atol=1e-6 * lr)
+
+
+def test_skinning_grid_step_before_any_pose(ia):
+    """An Adam step on the skinning grid before any pose is set updates the grid
+    and leaves the context whole: no blended grid to rebuild yet, and setting a
+    pose afterwards builds it from the updated weights (the render then runs)."""
+    sc = S.make_scene("tiny", 0)
+    table, mlp = S.make_field(sc, 0)
+    ctx = make_ctx(ia, torch, sc, table, mlp)
+    nt, nm = ia.ia_param_sizes(ctx)
+    ns, _ = ia.ia_grad_sizes(ctx)
+    gs = np.random.default_rng(4).normal(0, 1e-3, ns).astype(np.float32)
+    ia.ia_adam_step(ctx, torch.zeros(nt, device="cuda"), torch.zeros(nm, device="cuda"), 1e-3, 0.9, 0.99, 1e-15,
+                    g_skin=torch.from_numpy(gs).cuda())
+    torch.cuda.synchronize()
+    pose = S.make_pose(sc, 3)
+    ia.ia_set_pose(ctx, pose[0][None], pose[1][None])
+    ia.ia_update_occupancy(ctx, 0)
+    cam = S.make_camera(sc)
+    n = cam["width"] * cam["height"]
+    rgb, alpha = torch.zeros(n, 3, device="cuda"), torch.zeros(n, device="cuda")
+    st = ia.ia_render(ctx, 0, camera(ia, cam), rgb, alpha, stats=True)
+    torch.cuda.synchronize()
+    assert st["rays"] == n and (alpha > 0).any()
+    ia.ia_destroy(ctx)
 
 
 def test_learnable_skinning_grid(ia):

@@ -87,7 +87,10 @@ typedef struct ia_camera {
   float c2w[12];                 /* camera-to-world [R | centre], OpenCV axes */
 } ia_camera;
 
-/* Counters of one ia_render / ia_update_occupancy call (summed over the grid). */
+/* Counters of one ia_render / ia_update_occupancy call (summed over the grid).
+ * With the wavefront render path every slot of a hit ray is marched and every
+ * kept sample searched, behind the early-termination point too (compositing
+ * still stops there); the fused path stops marching a ray once it stops. */
 typedef struct ia_render_stats {
   int64_t rays;              /* rays launched */
   int64_t hit_rays;          /* rays whose clipped interval is non-empty */

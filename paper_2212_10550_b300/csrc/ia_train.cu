@@ -41,13 +41,20 @@ constexpr int kActF = 0, kActH1 = kIn, kActH2 = kActH1 + kWidth, kActD1 = kActH2
 // slots in march order, except those whose point can have no root in that pose
 // (the pose's root-culling masks, when present: density 0 and no gradient, so
 // they change neither the ray's colour nor any gradient; counted in *culled).
-// Returns the count; emit(i, x) is called for each.
+// A warp per ray, its lanes over the slots (every 32nd slot per lane; the
+// ballots keep march order).  Returns the count (all lanes); emit(j, x) is
+// called by the lane holding the ray's j-th sample.  A ray per thread left the
+// GPU mostly idle at training batch sizes (32768 rays: 1024 warps, each lane
+// marching 128 slots in turn).
 template <typename Emit>
-__device__ __forceinline__ int march_train_ray(const TrainArgs& a, int r, int& pose, int& hit, float& dt, Emit emit,
-                                               int* culled = nullptr) {
+__device__ __forceinline__ int march_train_ray_warp(const TrainArgs& a, int r, int& pose, int& hit, float& dt,
+                                                    Emit emit, int* culled) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
   pose = a.pose[r];
   hit = 0;
   dt = 0.f;
+  *culled = 0;
   if (pose < 0 || pose >= a.n_poses) return 0;
   const float ow[3] = {a.origin[3 * r], a.origin[3 * r + 1], a.origin[3 * r + 2]};
   const float dw[3] = {a.direction[3 * r], a.direction[3 * r + 1], a.direction[3 * r + 2]};
@@ -58,35 +65,58 @@ __device__ __forceinline__ int march_train_ray(const TrainArgs& a, int r, int& p
   const unsigned long long* sub =
       a.sub ? a.sub + (size_t)pose * a.box.R * a.box.R * a.box.R : nullptr;
   int n = 0, nc = 0;
-  for (int i = 0; i < a.n_slots; ++i) {
-    const float3 x = slot_position(o, d, tn, dt, i);
-    const int cell = cell_of(a.box, x);
-    if ((__ldg(a.occ + (cell >> 5)) >> (cell & 31)) & 1u) {
-      if (sub && !sub_marked(sub, a.box, x)) ++nc;
-      else emit(n++, x);
+  for (int i0 = 0; i0 < a.n_slots; i0 += 32) {
+    const int i = i0 + lane;
+    bool keep = false, cull = false;
+    float3 x = make_float3(0.f, 0.f, 0.f);
+    if (i < a.n_slots) {
+      x = slot_position(o, d, tn, dt, i);
+      const int cell = cell_of(a.box, x);
+      if ((__ldg(a.occ + (cell >> 5)) >> (cell & 31)) & 1u) {
+        if (sub && !sub_marked(sub, a.box, x)) cull = true;
+        else keep = true;
+      }
     }
+    const unsigned m = __ballot_sync(kFull, keep);
+    nc += __popc(__ballot_sync(kFull, cull));
+    if (keep) emit(n + __popc(m & lt), x);
+    n += __popc(m);
   }
-  if (culled) *culled = nc;
+  *culled = nc;
   return n;
 }
 
-// pass 1: per-ray sample counts and per-pose totals
-__global__ void train_count_kernel(const TrainArgs a) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+// pass 1: per-ray sample counts and per-pose totals (a warp per ray; the
+// counters are summed over the block first: one atomic per block and counter)
+__global__ void __launch_bounds__(256) train_count_kernel(const TrainArgs a) {
+  __shared__ int s_st[5][8];
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, warp = threadIdx.x >> 5;
+  const bool l0 = (threadIdx.x & 31) == 0;
   int n = 0, hit = 0, culled = 0;
   if (r < a.n_rays) {
     int pose;
     float dt;
-    n = march_train_ray(a, r, pose, hit, dt, [](int, float3) {}, &culled);
-    a.ray_n[r] = n;
-    a.ray_dt[r] = dt;
-    if (n > 0) atomicAdd(a.pose_tot + pose, n);
+    n = march_train_ray_warp(a, r, pose, hit, dt, [](int, float3) {}, &culled);
+    if (l0) {
+      a.ray_n[r] = n;
+      a.ray_dt[r] = dt;
+      if (n > 0) atomicAdd(a.pose_tot + pose, n);
+    }
   }
-  flush_stats(a.stats, ST_RAYS, r < a.n_rays ? 1 : 0);
-  flush_stats(a.stats, ST_HIT, hit);
-  flush_stats(a.stats, ST_MARCHED, hit ? a.n_slots : 0);
-  flush_stats(a.stats, ST_OCC, n + culled);
-  flush_stats(a.stats, ST_CULLED, culled);
+  if (l0) {
+    s_st[0][warp] = r < a.n_rays ? 1 : 0;
+    s_st[1][warp] = hit;
+    s_st[2][warp] = hit ? a.n_slots : 0;
+    s_st[3][warp] = n + culled;
+    s_st[4][warp] = culled;
+  }
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    unsigned long long v = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += (unsigned long long)s_st[threadIdx.x][w];
+    const int idx[5] = {ST_RAYS, ST_HIT, ST_MARCHED, ST_OCC, ST_CULLED};
+    if (v) atomicAdd(a.stats + idx[threadIdx.x], v);
+  }
 }
 
 // pass 2: per-pose totals -> first sample index of each pose; total count
@@ -103,21 +133,26 @@ __global__ void pose_scan_kernel(const TrainArgs a) {
 
 // pass 3: samples written grouped by pose (so that concurrent warps of the
 // sample kernels share one pose's blended grid in L2), each ray's list of its
-// sample indices in march order
-__global__ void train_emit_kernel(const TrainArgs a) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= a.n_rays) return;
+// sample indices in march order (a warp per ray)
+__global__ void __launch_bounds__(256) train_emit_kernel(const TrainArgs a) {
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= a.n_rays) return;  // whole warps
   const int n = a.ray_n[r];
   if (n == 0) return;
   const int pose = a.pose[r];
-  const int base = a.pose_tot[pose] + atomicAdd(a.pose_fill + pose, n);
-  int p, hit;
+  int base = 0;
+  if ((threadIdx.x & 31) == 0) base = a.pose_tot[pose] + atomicAdd(a.pose_fill + pose, n);
+  base = __shfl_sync(kFull, base, 0);
+  int p, hit, culled;
   float dt;
   int* idx = a.ray_idx + (size_t)r * a.n_slots;
-  march_train_ray(a, r, p, hit, dt, [&](int j, float3 x) {
-    a.s_pos[base + j] = make_float4(x.x, x.y, x.z, __int_as_float(pose));
-    idx[j] = base + j;
-  });
+  march_train_ray_warp(
+      a, r, p, hit, dt,
+      [&](int j, float3 x) {
+        a.s_pos[base + j] = make_float4(x.x, x.y, x.z, __int_as_float(pose));
+        idx[j] = base + j;
+      },
+      &culled);
 }
 
 // Regulariser points (Eq. 12): only points in empty cells of the step's grid
@@ -1079,11 +1114,11 @@ __global__ void loss_scale_kernel(const TrainArgs a, int dynamic) {
 
 cudaError_t launch_train_forward(const TrainArgs& a, int num_sms, cudaStream_t s) {
   cudaError_t e;
-  const int rb = (a.n_rays + 127) / 128;
   const int gb = (a.n_reg + 127) / 128;
+  const int wb = (a.n_rays + 7) / 8;  // a warp per ray
   {
     KernelSpan span("train_count_kernel", s);
-    train_count_kernel<<<rb, 128, 0, s>>>(a);
+    train_count_kernel<<<wb, 256, 0, s>>>(a);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (a.n_reg > 0) {
@@ -1100,7 +1135,7 @@ cudaError_t launch_train_forward(const TrainArgs& a, int num_sms, cudaStream_t s
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   {
     KernelSpan span("train_emit_kernel", s);
-    train_emit_kernel<<<rb, 128, 0, s>>>(a);
+    train_emit_kernel<<<wb, 256, 0, s>>>(a);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (a.n_reg > 0) {

@@ -18,6 +18,25 @@ __device__ __forceinline__ void flush_stats(unsigned long long* stats, int idx, 
   if ((threadIdx.x & 31) == 0 && v != 0) atomicAdd(stats + idx, (unsigned long long)v);
 }
 
+// The same summed over the block first (one atomic per block and counter, for
+// short kernels with many blocks, whose per-warp atomics on the same counters
+// would serialise); all threads of the block call, with the same N and idx.
+template <int N>
+__device__ __forceinline__ void flush_stats_block(unsigned long long* stats, const int (&idx)[N],
+                                                  const long long (&v)[N]) {
+  __shared__ unsigned long long s_sum[N];
+  if (threadIdx.x < N) s_sum[threadIdx.x] = 0;
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    long long x = v[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFull, x, o);
+    if ((threadIdx.x & 31) == 0 && x != 0) atomicAdd(s_sum + k, (unsigned long long)x);
+  }
+  __syncthreads();
+  if (threadIdx.x < N && s_sum[threadIdx.x] != 0) atomicAdd(stats + idx[threadIdx.x], s_sum[threadIdx.x]);
+}
+
 // the next list index of a warp from a counter shared by the grid (zeroed by
 // the host before the launch); all 32 lanes call
 __device__ __forceinline__ int next_list(unsigned* work) {

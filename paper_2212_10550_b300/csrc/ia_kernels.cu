@@ -537,8 +537,7 @@ __global__ void occ_cand_kernel(const BoxDev box, const float* __restrict__ jitt
   if (lane == 0 && m) base = atomicAdd(count, (unsigned)__popc(m));
   base = __shfl_sync(kFull, base, 0);
   if (cand) cells[base + __popc(m & ((1u << lane) - 1u))] = c;
-  const unsigned culled = __ballot_sync(kFull, c < n && !cand);
-  if (stats && lane == 0 && culled) atomicAdd(stats + ST_CULLED, (unsigned long long)__popc(culled));
+  if (stats) flush_stats_block<1>(stats, {ST_CULLED}, {(long long)(c < n && !cand ? 1 : 0)});
 }
 
 // The root-culling masks of n_poses consecutive blended grids (S.M = the

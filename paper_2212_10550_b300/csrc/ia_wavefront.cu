@@ -99,13 +99,9 @@ __global__ void __launch_bounds__(256) wf_march_kernel(const RenderArgs a, const
     unsigned m2 = 0, c2 = 0;
     for_each_kept_slot(a, o, d, tn, dt, m2, c2, [&](float3 x) { w.xn[k++] = make_float4(x.x, x.y, x.z, 0.f); });
   }
-  if (a.stats) {
-    flush_stats(a.stats, ST_RAYS, valid ? 1 : 0);
-    flush_stats(a.stats, ST_HIT, hit ? 1 : 0);
-    flush_stats(a.stats, ST_MARCHED, marched);
-    flush_stats(a.stats, ST_OCC, (unsigned)cnt + culled);
-    flush_stats(a.stats, ST_CULLED, culled);
-  }
+  if (a.stats)
+    flush_stats_block<5>(a.stats, {ST_RAYS, ST_HIT, ST_MARCHED, ST_OCC, ST_CULLED},
+                         {valid ? 1 : 0, hit ? 1 : 0, marched, (long long)cnt + culled, culled});
 }
 
 // ---- the proposal's bones and start offset for every sample
@@ -226,11 +222,8 @@ __global__ void __launch_bounds__(128, 4) wf_search_kernel(const RenderArgs a, c
     conv_n += valid;
     out[it] = make_float4(x.x, x.y, x.z, __int_as_float(valid ? ((order << 8) | label) : -1));
   }
-  if (a.stats) {
-    flush_stats(a.stats, ST_STARTS, starts);
-    flush_stats(a.stats, ST_ITERS, iters);
-    flush_stats(a.stats, ST_CONV, conv_n);
-  }
+  if (a.stats)
+    flush_stats_block<3>(a.stats, {ST_STARTS, ST_ITERS, ST_CONV}, {(long long)starts, (long long)iters, (long long)conv_n});
 }
 
 // ---- the samples whose proposed starts found no root
@@ -378,7 +371,7 @@ __global__ void __launch_bounds__(256) wf_composite_kernel(const RenderArgs a, c
     a.rgb[3 * pix + 2] = cb;
     a.alpha[pix] = -expm1f(-depth);
   }
-  if (a.stats) flush_stats(a.stats, ST_EARLY, early);
+  if (a.stats) flush_stats_block<1>(a.stats, {ST_EARLY}, {(long long)early});
 }
 
 // ---------------------------------------------------------------------------

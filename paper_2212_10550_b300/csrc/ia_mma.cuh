@@ -201,31 +201,48 @@ __device__ __forceinline__ void mlp_mma_warp_staged(const uint32_t* __restrict__
   __syncwarp();
 }
 
-// The same network for one lane alone (used for the rare distinct root beyond
-// the per-sample list, which is evaluated where it is found): operands rounded
-// to the reduced precision exactly as the tensor-core path rounds them,
-// products and sums in fp32.
+// The same network for one lane alone (the distinct root beyond a sample's
+// list, evaluated where it is found), from the weights stage_mlp_h staged in
+// shared memory: operands rounded to the reduced precision exactly as the
+// tensor-core path rounds them, products and sums in fp32.
 template <Prec P>
-__device__ __forceinline__ void mlp_lane_h(const float* __restrict__ gm, int n_in, const float feat[kIn],
-                                           float out[4]) {
+__device__ __forceinline__ float2 unpack_h(uint32_t w) {
+  if constexpr (P == Prec::F16) return __half22float2(*reinterpret_cast<const __half2*>(&w));
+  else return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+}
+
+template <Prec P>
+__device__ __forceinline__ void mlp_lane_hs(const uint32_t* __restrict__ sw, const float feat[kIn], float out[4]) {
   using H = HalfOf<P>;
-  const float* b1 = gm + kWidth * n_in;
-  const float* W2 = b1 + kWidth;
-  const float* b2 = W2 + kWidth * kWidth;
-  const float* W3 = b2 + kWidth;
-  const float* b3 = W3 + 4 * kWidth;
+  const float* bias = reinterpret_cast<const float*>(sw + kOffHB);
   float h1[kWidth];
   for (int j = 0; j < kWidth; ++j) {
-    float acc = b1[j];
-    for (int i = 0; i < n_in; ++i) acc = fmaf(H::round(gm[j * n_in + i]), H::round(feat[i]), acc);
+    float acc = bias[j];
+    const uint32_t* row = sw + kOffHW1 + j * kW1Stride;
+#pragma unroll
+    for (int c = 0; c < kIn / 2; ++c) {
+      const float2 w = unpack_h<P>(row[c]);
+      acc = fmaf(w.x, H::round(feat[2 * c]), acc);
+      acc = fmaf(w.y, H::round(feat[2 * c + 1]), acc);
+    }
     h1[j] = H::round(fmaxf(acc, 0.f));
   }
-  float o[4] = {b3[0], b3[1], b3[2], b3[3]};
+  float o[4] = {bias[2 * kWidth], bias[2 * kWidth + 1], bias[2 * kWidth + 2], bias[2 * kWidth + 3]};
   for (int j = 0; j < kWidth; ++j) {
-    float acc = b2[j];
-    for (int i = 0; i < kWidth; ++i) acc = fmaf(H::round(W2[j * kWidth + i]), h1[i], acc);
+    float acc = bias[kWidth + j];
+    const uint32_t* row = sw + kOffHW2 + j * kW2Stride;
+#pragma unroll
+    for (int c = 0; c < kWidth / 2; ++c) {
+      const float2 w = unpack_h<P>(row[c]);
+      acc = fmaf(w.x, h1[2 * c], acc);
+      acc = fmaf(w.y, h1[2 * c + 1], acc);
+    }
     const float h = H::round(fmaxf(acc, 0.f));
-    for (int q = 0; q < 4; ++q) o[q] = fmaf(H::round(W3[q * kWidth + j]), h, o[q]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float2 w = unpack_h<P>(sw[kOffHW3 + q * kW2Stride + j / 2]);
+      o[q] = fmaf((j & 1) ? w.y : w.x, h, o[q]);
+    }
   }
   for (int q = 0; q < 4; ++q) out[q] = o[q];
 }

@@ -50,7 +50,7 @@ __device__ __forceinline__ void field_eval_lane(const FieldDev& F, const FieldSm
     mlp_fp32(fs.sw, feat, o);
   } else {
     encode_h(F, fs.table_h, x, feat);
-    mlp_lane_h<P>(fs.gmlp, fs.n_in, feat, o);
+    mlp_lane_hs<P>(fs.swh, feat, o);
   }
   activate(o, sigma, rgb);
 }

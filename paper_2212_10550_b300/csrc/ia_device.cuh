@@ -24,7 +24,9 @@ constexpr int kMaxBones = 32;
 constexpr int kMaxLevels = 16;
 constexpr int kWidth = 64;
 constexpr int kIn = 32;          // MLP input, zero-padded to 16 levels x 2 features
-constexpr int kMaxRoots = 4;     // distinct roots remembered per sample for merging
+constexpr int kMaxRoots = 8;     // distinct roots remembered per sample for merging (measured on the
+                                 // full-size frame against 4 / 6 / 12 / 16: fastest; a list that overflows
+                                 // evaluates its roots to keep the best, which 4 did often)
 constexpr unsigned kFull = 0xffffffffu;
 
 // MLP weights staged in shared memory (fp32): W1 [64][32] (zero-padded

@@ -224,7 +224,11 @@ ia_status ia_query_canonical(ia_ctx *ctx, int n, const float *x, float *sigma, f
  * others are composited front to back with alpha_i = 1 - exp(-sigma_i delta);
  * a ray stops once its transmittance falls below early_stop_T.
  *  rgb [H*W][3], alpha [H*W] fp32 (alpha = 1 - final transmittance), device or
- *  host (see conventions).  stats may be NULL (host struct). */
+ *  host (see conventions).  stats may be NULL (host struct).
+ *  With the default render path (ia_set_render_path) the call waits on its
+ *  stream once, after the march, for the frame's sample count; the kernels
+ *  after it are queued without waiting (device outputs).  The first frames,
+ *  and any frame with more samples than the context's arrays hold, allocate. */
 ia_status ia_render(ia_ctx *ctx, int pose, const ia_camera *cam, float *rgb, float *alpha,
                     ia_render_stats *stats, void *stream);
 

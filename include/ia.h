@@ -309,8 +309,10 @@ typedef struct ia_grads {
  *   dL/dN_k = -lambda w_k(x*) [x*;1]^T,  dL/dW(v, k) = -c_v(x*) lambda . N_k [x*;1].
  * The selected root is treated as constant.  rgb_out [n][3] (device) may be
  * NULL.  Workspace for n_rays * max_samples samples (about 1.2 KB each in fp32,
- * 0.8 KB in fp16 / bf16) is allocated by the context on first use and grown
- * when a larger batch comes.
+ * 0.8 KB in fp16 / bf16, plus the search's item results: 16 B per start, i.e.
+ * 384 B per sample with every bone as a start, 32 B with the proposal's two
+ * and 384 B more for its fallback) is allocated by the context on first use
+ * and grown when a larger batch comes.
  *
  * Precision (Sec. 3.4 trains in half precision): with IA_FP16 / IA_BF16 the
  * forward uses the reduced-precision field (fp16 hash features, tensor-core MLP),

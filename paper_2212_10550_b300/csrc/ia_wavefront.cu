@@ -69,12 +69,18 @@ __device__ __forceinline__ void for_each_kept_slot(const RenderArgs& a, const fl
 
 }  // namespace
 
-// ---- march: count, reserve, emit (one thread per ray id, tile order).
-//      Measured against it: one warp per ray with its lanes over the slots and
-//      one reservation per block (0.64 ms: the block's atomic on one counter
-//      is on every block's critical path), and a warp marching 32 rays in turn
-//      with its lanes over the slots (0.128 ms against 0.111 ms: the ballots,
-//      broadcasts and mask bookkeeping cost as much as the second pass saved).
+// ---- march: count, reserve, emit (one thread per ray id, tile order).  With
+//      at most kMaskSlots slots the count pass records the kept slots in a
+//      register mask and the emit pass visits only those; above, it marches
+//      again.  Measured against it: one warp per ray with its lanes over the
+//      slots and one reservation per block (0.64 ms: the block's atomic on one
+//      counter is on every block's critical path), and a warp marching 32 rays
+//      in turn with its lanes over the slots (0.128 ms against 0.111 ms: the
+//      ballots, broadcasts and mask bookkeeping cost as much as the second
+//      pass saved).
+constexpr int kMaskSlots = 128;
+
+template <bool kMask>
 __global__ void __launch_bounds__(256) wf_march_kernel(const RenderArgs a, const WfArgs w) {
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
   const int W = a.cam.width, H = a.cam.height;
@@ -86,7 +92,31 @@ __global__ void __launch_bounds__(256) wf_march_kernel(const RenderArgs a, const
   const float dt = hit ? slot_delta(tn, tf, a.n_slots) : 0.f;
   unsigned marched = 0, culled = 0;
   int cnt = 0;
-  if (hit) for_each_kept_slot(a, o, d, tn, dt, marched, culled, [&](float3) { ++cnt; });
+  uint32_t mk[kMaskSlots / 32] = {};
+  if (hit) {
+    if constexpr (kMask) {
+#pragma unroll
+      for (int q = 0; q < kMaskSlots / 32; ++q) {
+        for (int b = 0; b < 32; ++b) {
+          const int i = 32 * q + b;
+          if (i >= a.n_slots) break;
+          const float3 x = slot_position(o, d, tn, dt, i);
+          const int cell = cell_of(a.box, x);
+          ++marched;
+          if ((__ldg(a.occ + (cell >> 5)) >> (cell & 31)) & 1u) {
+            if (a.sub && !sub_marked(a.sub, a.box, x)) {
+              ++culled;
+            } else {
+              mk[q] |= 1u << b;
+              ++cnt;
+            }
+          }
+        }
+      }
+    } else {
+      for_each_kept_slot(a, o, d, tn, dt, marched, culled, [&](float3) { ++cnt; });
+    }
+  }
   const int first = warp_reserve(w.n_samples, cnt);
   const int pix = v * W + u;
   if (valid) {
@@ -96,8 +126,18 @@ __global__ void __launch_bounds__(256) wf_march_kernel(const RenderArgs a, const
   }
   if (cnt > 0 && first + cnt <= w.cap) {  // beyond the capacity the host grows it and marches again
     int k = first;
-    unsigned m2 = 0, c2 = 0;
-    for_each_kept_slot(a, o, d, tn, dt, m2, c2, [&](float3 x) { w.xn[k++] = make_float4(x.x, x.y, x.z, 0.f); });
+    if constexpr (kMask) {
+#pragma unroll
+      for (int q = 0; q < kMaskSlots / 32; ++q) {
+        for (uint32_t m = mk[q]; m; m &= m - 1u) {
+          const float3 x = slot_position(o, d, tn, dt, 32 * q + __ffs(m) - 1);
+          w.xn[k++] = make_float4(x.x, x.y, x.z, 0.f);
+        }
+      }
+    } else {
+      unsigned m2 = 0, c2 = 0;
+      for_each_kept_slot(a, o, d, tn, dt, m2, c2, [&](float3 x) { w.xn[k++] = make_float4(x.x, x.y, x.z, 0.f); });
+    }
   }
   if (a.stats)
     flush_stats_block<5>(a.stats, {ST_RAYS, ST_HIT, ST_MARCHED, ST_OCC, ST_CULLED},
@@ -404,7 +444,8 @@ constexpr const char* wf_field_name(bool prop, int role) {
 
 cudaError_t launch_wf_march(const RenderArgs& a, const WfArgs& w, cudaStream_t s) {
   KernelSpan span("wf_march_kernel", s);
-  wf_march_kernel<<<(a.n_ray_ids + 255) / 256, 256, 0, s>>>(a, w);
+  if (a.n_slots <= kMaskSlots) wf_march_kernel<true><<<(a.n_ray_ids + 255) / 256, 256, 0, s>>>(a, w);
+  else wf_march_kernel<false><<<(a.n_ray_ids + 255) / 256, 256, 0, s>>>(a, w);
   return cudaGetLastError();
 }
 

@@ -881,6 +881,7 @@ static ia_status render_wavefront(ia_ctx* c, RenderArgs& a, size_t npix, cudaStr
   w.res = c->d_wf_res;
   w.pose_stride = 0;  // one pose
   w.ninv = a.P.Ninv;
+  w.n_ninv = nb * 12;
   w.prop = c->d_wf_prop;
   w.item0 = c->d_wf_item0;
   w.item1 = c->d_wf_item1;
@@ -1102,6 +1103,7 @@ ia_status train_prepare(ia_ctx* c, const ia_batch* b, int occ_grid, bool need_ta
     w.cap = (int)c->s_cap;
     w.pose_stride = (int)(3 * V);
     w.ninv = a.P.Ninv;
+    w.n_ninv = c->n_poses * c->nb * 12;
     w.s0 = 0;
     w.ns = (int)c->s_cap;
     w.ns_dev = reinterpret_cast<const unsigned*>(c->d_count);

@@ -128,7 +128,8 @@ struct WfArgs {
   float4* res;          // [cap] sigma (0 without a root), rgb
   float4* xs;           // [cap] or null: the selected root x* and 1 (0 without a root)
   int pose_stride;      // float4s per pose of the blended grids S.M (3 V)
-  const float* ninv;    // [poses][n_bones][12] inverse rest-to-pose transforms
+  const float* ninv;    // [poses][n_bones][12] inverse rest-to-pose transforms (16-byte aligned)
+  int n_ninv;           // floats of ninv the items may read (poses x n_bones x 12)
   int* ray_first;       // [W * H] first sample of the pixel's ray
   int* ray_cnt;         // [W * H] its kept samples
   float* ray_dt;        // [W * H] its slot spacing

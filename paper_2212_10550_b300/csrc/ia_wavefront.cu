@@ -204,10 +204,25 @@ __global__ void __launch_bounds__(256) wf_propose_kernel(const RenderArgs a, con
 // each lane with the next item as it finishes (lanes busy but scattered) is
 // 1.2x slower, start-major order (neighbouring samples' starts of one bone
 // together) 1.7x slower.
+// The inverse rest-to-pose transforms the items start from are staged in
+// shared memory (w.n_ninv floats, 1.1 KB per pose at 24 bones) when they fit
+// kNinvSmemFloats (one pose: the render, the occupancy refresh), else read
+// from global memory (the training step's 16 poses: staging them, 18 KB per
+// block, took L1 capacity from the gathers and was slower).
+constexpr int kNinvSmemFloats = 1024;
+
 template <bool kProp>
 __global__ void __launch_bounds__(128, 4) wf_search_kernel(const RenderArgs a, const WfArgs w, int wave) {
+  extern __shared__ float4 sNinv4[];
   const int nb = a.P.cfg.nb;
   const SkinDev& S = a.P.S;
+  const bool staged = w.n_ninv <= kNinvSmemFloats;
+  if (staged) {
+    const float4* g4 = reinterpret_cast<const float4*>(w.ninv);
+    for (int t = threadIdx.x; t < w.n_ninv / 4; t += blockDim.x) sNinv4[t] = g4[t];
+  }
+  __syncthreads();
+  const float4* ninv4 = staged ? sNinv4 : reinterpret_cast<const float4*>(w.ninv);
   const int nprop = kProp ? min(a.P.prop.top_k, nb) : 0;
   const int per = (kProp && wave == 0) ? nprop : nb;
   const int n = wave == 0 ? chunk_size(w) : (int)*w.n_fb;
@@ -232,7 +247,15 @@ __global__ void __launch_bounds__(128, 4) wf_search_kernel(const RenderArgs a, c
       if (j == 0) poff = make_float3(pp.y, pp.z, pp.w);
       order = j;
     }
-    float3 x = search_start(w.ninv + ((size_t)pose * nb + label) * 12, xn, kProp && wave == 0 && j == 0, poff);
+    float A[12];
+    {
+      const float4* r = ninv4 + ((size_t)pose * nb + label) * 3;
+      const float4 r0 = r[0], r1 = r[1], r2 = r[2];
+      A[0] = r0.x; A[1] = r0.y; A[2] = r0.z; A[3] = r0.w;
+      A[4] = r1.x; A[5] = r1.y; A[6] = r1.z; A[7] = r1.w;
+      A[8] = r2.x; A[9] = r2.y; A[10] = r2.z; A[11] = r2.w;
+    }
+    float3 x = search_start(A, xn, kProp && wave == 0 && j == 0, poff);
     float Mx[12];
     blend_value(S, M, x, Mx);
     ++starts;
@@ -469,9 +492,10 @@ static cudaError_t launch_wf_chunk_p(const RenderArgs& a, const WfArgs& w, int n
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   const int grid = num_sms * 4 * 8;  // items are handed out grid-stride
+  const size_t ninv_smem = w.n_ninv <= kNinvSmemFloats ? sizeof(float) * w.n_ninv : 0;
   {
     KernelSpan span(kProp ? kNameSearchProp[w.role] : kNameSearch[w.role], s);
-    wf_search_kernel<kProp><<<grid, 128, 0, s>>>(a, w, 0);
+    wf_search_kernel<kProp><<<grid, 128, ninv_smem, s>>>(a, w, 0);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if constexpr (kProp) {
@@ -482,7 +506,7 @@ static cudaError_t launch_wf_chunk_p(const RenderArgs& a, const WfArgs& w, int n
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
       KernelSpan span(kNameSearchFb[w.role], s);
-      wf_search_kernel<kProp><<<grid, 128, 0, s>>>(a, w, 1);
+      wf_search_kernel<kProp><<<grid, 128, ninv_smem, s>>>(a, w, 1);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -546,6 +570,7 @@ cudaError_t launch_wf_occupancy(const PosedArgs& P, const BoxDev& box, const flo
   w.ns_dev = cells ? count : nullptr;
   w.pose_stride = 0;
   w.ninv = P.Ninv;
+  w.n_ninv = P.cfg.nb * 12;
   w.xs = nullptr;
   w.role = kWfOccupancy;
   const int blocks = min((n_all + 255) / 256, num_sms * 8);

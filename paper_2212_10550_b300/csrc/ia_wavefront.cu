@@ -377,9 +377,9 @@ __device__ __forceinline__ void field_body(const RenderArgs& a, const WfArgs& w,
   if (a.stats) flush_stats(a.stats, ST_ROOTS, roots);
 }
 
-// fp32: the per-lane MLP holds its activations in registers (one block of 8 warps per SM)
-constexpr int kFieldThreadsF32 = 256;
-__global__ void __launch_bounds__(kFieldThreadsF32) wf_field_kernel_f32(const RenderArgs a, const WfArgs w) {
+// fp32: the per-lane MLP holds its activations in registers (one block of 8
+// warps per SM; register caps for two blocks spill and gained at most 6 %)
+__global__ void __launch_bounds__(256) wf_field_kernel_f32(const RenderArgs a, const WfArgs w) {
   extern __shared__ float4 smem4[];
   field_body<Prec::F32, false>(a, w, smem4);
 }
@@ -391,11 +391,6 @@ template <Prec P, bool kProp>
 __global__ void __launch_bounds__(256, kProp ? 2 : 1) wf_field_kernel(const RenderArgs a, const WfArgs w) {
   extern __shared__ float4 smem4[];
   field_body<P, kProp>(a, w, smem4);
-}
-
-template <Prec P>
-constexpr int field_threads() {
-  return P == Prec::F32 ? kFieldThreadsF32 : 256;
 }
 
 template <Prec P, bool kProp>
@@ -510,7 +505,7 @@ static cudaError_t launch_wf_chunk_p(const RenderArgs& a, const WfArgs& w, int n
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  constexpr int kFT = field_threads<P>();
+  constexpr int kFT = 256;
   const size_t smem = posed_smem_bytes_p<P>(kFT, false);
   constexpr auto kField = field_kernel<P, kProp>();
   if ((e = set_smem(kField, smem, kFT)) != cudaSuccess) return e;

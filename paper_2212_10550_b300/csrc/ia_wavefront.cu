@@ -19,9 +19,11 @@
 //   wf_composite_kernel  one thread per ray: front-to-back compositing of its
 //                        samples with early termination (Sec. 3.2, Eq. 8)
 //
-// Each sample's result is bit for bit the fused render's: the same starts, the
-// same explicitly rounded Broyden arithmetic (ia_device.cuh), merge rule,
-// polish, field and selection; the difference is the schedule.  The search
+// Each sample's result is bit for bit the fused render's with the plain search
+// (the same starts, the same explicitly rounded Broyden arithmetic of
+// ia_device.cuh, merge rule, polish, field and selection; the difference is the
+// schedule), and with the proposal search up to the fused kernel's fallback
+// queue merging a sample's roots in another order.  The search
 // items are independent and light (128 registers, four blocks of four warps
 // per SM against one block of eight warps for the fused kernel), and the
 // proposal's fallback starts, a few per ray where they occur, form one dense

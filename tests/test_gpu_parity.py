@@ -444,6 +444,36 @@ def test_render_paths_agree_over_chunks(ia):
     ia.ia_destroy(ctx)
 
 
+def test_render_more_slots_than_the_march_mask(ia):
+    """Rays of 300 slots: more than the march's per-ray register mask holds
+    (128), so the march counts and emits in two full passes.  The frame matches
+    the oracle on the tiny scene (parity mode) and the fused kernel bit for bit."""
+    sc = S.make_scene("tiny", 0)
+    sc.max_samples = 300
+    table, mlp = S.make_field(sc, 0)
+    ctx, om, p, occ, cam = _render_case(ia, sc, table, mlp, 5, 0.0)
+    W, H = cam["width"], cam["height"]
+    out = {}
+    for path in ("wavefront", "fused"):
+        ia.ia_set_render_path(ctx, PATHS[path])
+        rgb = torch.zeros(H * W, 3, device="cuda")
+        alpha = torch.zeros(H * W, device="cuda")
+        st = ia.ia_render(ctx, 0, camera(ia, cam), rgb, alpha, stats=True)
+        out[path] = (rgb.cpu().numpy(), alpha.cpu().numpy(), st)
+    (r1, a1, s1), (r0, a0, s0) = out["wavefront"], out["fused"]
+    np.testing.assert_array_equal(r1, r0)
+    np.testing.assert_array_equal(a1, a0)
+    assert s1["marched_slots"] == s1["hit_rays"] * 300
+    ref = om.render(p, cam, occ)
+    ok = ref["flags"] == 0
+    assert s1["occupied_samples"] == int(ref["nsamp"].sum())
+    assert np.sum(~ok) <= 0.01 * W * H
+    assert (ref["alpha"][ok] > 0.01).sum() >= 100
+    assert close(r1[ok], ref["rgb"][ok], RTOL_RGB, ATOL_RGB).all()
+    assert close(a1[ok], ref["alpha"][ok], RTOL_RGB, ATOL_RGB).all()
+    ia.ia_destroy(ctx)
+
+
 def test_render_degenerate_cases(ia):
     sc = S.make_scene("tiny", 0)
     table, mlp = S.make_field(sc, 0)

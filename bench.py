@@ -848,11 +848,17 @@ def run_ours(args, rank, world, local_rank):
     search_bytes = GATHER_LBS * (per_frame["starts"] + per_frame["broyden_iters"])
     s_ms = prof_plain["wf_search_kernel"][1]
     s_achieved = search_bytes / (s_ms * 1e-3) / 1e9
+    # the gathers actually issued: an evaluation in the cell of the item's previous one reuses its records
+    issued_bytes = GATHER_LBS * per_frame.get("grid_gathers", 0)
     roofline_gather = {"kernel": "wf_search_kernel", "bound": "l1-gather", "achieved": round(s_achieved, 1),
                        "peak": peaks_g["l1"], "unit": "GB/s", "frac": round(s_achieved / peaks_g["l1"], 4),
                        "traffic": None, "bytes_per_launch": round(search_bytes), "ms_per_launch": round(s_ms, 4),
                        "peak_l2_random": peaks_g["l2"], "peak_source": l1_src,
                        "work": "48 B x 8 corners per LBS evaluation x (starts + Broyden steps) of the frame",
+                       "gathered_bytes_per_launch": round(issued_bytes),
+                       "gathered_frac": round(issued_bytes / (s_ms * 1e-3) / 1e9 / peaks_g["l1"], 4),
+                       "gathered_note": "the gathers issued: evaluations in the cell of the item's previous "
+                                        "evaluation reuse the corner records it holds in registers",
                        "traffic_note": "DRAM bytes per launch come from an ncu capture, not from this run"}
     # ---- the whole render (all its kernels) against the same gather peak
     render_roofline = {}

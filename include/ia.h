@@ -106,6 +106,11 @@ typedef struct ia_render_stats {
   int64_t culled;            /* render: occupied samples, occupancy: cells, whose point can
                                 have no root (density 0 without a search; see
                                 ia_update_occupancy) */
+  int64_t grid_gathers;      /* search evaluations of M(x) that read their cell's 8 corner
+                                records from the blended grid: every start and update on
+                                the fused schedule; on the wavefront, those whose cell
+                                differs from the previous evaluation's (the others reuse
+                                the records a lane holds) */
 } ia_render_stats;
 
 /* Create a context on the current CUDA device.  cfg is copied. */

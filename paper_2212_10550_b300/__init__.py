@@ -46,7 +46,7 @@ class Camera(C.Structure):
 class RenderStats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("rays", "hit_rays", "marched_slots", "occupied_samples", "starts",
                                          "broyden_iters", "converged", "roots", "early_stopped", "proposed",
-                                         "fallbacks", "culled")]
+                                         "fallbacks", "culled", "grid_gathers")]
 
 
     def as_dict(self):

@@ -384,6 +384,7 @@ void read_stats(ia_ctx* c, ia_render_stats* out, cudaStream_t s, const unsigned 
   out->proposed = (int64_t)h[ST_PROP];
   out->fallbacks = (int64_t)h[ST_FALLBACK];
   out->culled = (int64_t)h[ST_CULLED];
+  out->grid_gathers = (int64_t)h[ST_GATHERS];
 }
 
 }  // namespace

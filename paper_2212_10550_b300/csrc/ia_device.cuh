@@ -106,6 +106,22 @@ __device__ __forceinline__ int corner_index(const SkinDev& S, int base, int corn
   return base + (corner & 1) + S.Rw * (((corner >> 1) & 1) + S.Rw * ((corner >> 2) & 1));
 }
 
+// trilinear weight of a cell corner (bit 0: +x, bit 1: +y, bit 2: +z)
+__device__ __forceinline__ float corner_weight(const CellCoord& c, int corner) {
+  return ((corner & 1) ? c.f[0] : 1.f - c.f[0]) * (((corner >> 1) & 1) ? c.f[1] : 1.f - c.f[1]) *
+         (((corner >> 2) & 1) ? c.f[2] : 1.f - c.f[2]);
+}
+
+// Mx += w * (one corner's three rows)
+__device__ __forceinline__ void accumulate_corner(float Mx[12], float w, float4 r0, float4 r1, float4 r2) {
+  Mx[0] = fmaf(w, r0.x, Mx[0]); Mx[1] = fmaf(w, r0.y, Mx[1]);
+  Mx[2] = fmaf(w, r0.z, Mx[2]); Mx[3] = fmaf(w, r0.w, Mx[3]);
+  Mx[4] = fmaf(w, r1.x, Mx[4]); Mx[5] = fmaf(w, r1.y, Mx[5]);
+  Mx[6] = fmaf(w, r1.z, Mx[6]); Mx[7] = fmaf(w, r1.w, Mx[7]);
+  Mx[8] = fmaf(w, r2.x, Mx[8]); Mx[9] = fmaf(w, r2.y, Mx[9]);
+  Mx[10] = fmaf(w, r2.z, Mx[10]); Mx[11] = fmaf(w, r2.w, Mx[11]);
+}
+
 // M(x) = sum_c w_c M_c  (12 values, rows of a 3x4 matrix); M = one pose's grid
 __device__ __forceinline__ void blend_value(const SkinDev& S, const float4* __restrict__ M, float3 x,
                                             float Mx[12]) {
@@ -114,19 +130,41 @@ __device__ __forceinline__ void blend_value(const SkinDev& S, const float4* __re
   for (int q = 0; q < 12; ++q) Mx[q] = 0.f;
 #pragma unroll
   for (int corner = 0; corner < 8; ++corner) {
-    int v = corner_index(S, c.base, corner);
-    float w = ((corner & 1) ? c.f[0] : 1.f - c.f[0]) * (((corner >> 1) & 1) ? c.f[1] : 1.f - c.f[1]) *
-              (((corner >> 2) & 1) ? c.f[2] : 1.f - c.f[2]);
-    const float4* p = M + 3 * v;
-    float4 r0 = __ldg(p), r1 = __ldg(p + 1), r2 = __ldg(p + 2);
-    Mx[0] = fmaf(w, r0.x, Mx[0]); Mx[1] = fmaf(w, r0.y, Mx[1]);
-    Mx[2] = fmaf(w, r0.z, Mx[2]); Mx[3] = fmaf(w, r0.w, Mx[3]);
-    Mx[4] = fmaf(w, r1.x, Mx[4]); Mx[5] = fmaf(w, r1.y, Mx[5]);
-    Mx[6] = fmaf(w, r1.z, Mx[6]); Mx[7] = fmaf(w, r1.w, Mx[7]);
-    Mx[8] = fmaf(w, r2.x, Mx[8]); Mx[9] = fmaf(w, r2.y, Mx[9]);
-    Mx[10] = fmaf(w, r2.z, Mx[10]); Mx[11] = fmaf(w, r2.w, Mx[11]);
+    const float4* p = M + 3 * corner_index(S, c.base, corner);
+    accumulate_corner(Mx, corner_weight(c, corner), __ldg(p), __ldg(p + 1), __ldg(p + 2));
   }
 }
+
+// blend_value for a sequence of points of one pose (a Broyden iteration): the
+// 8 corner records of the cell gathered last stay in registers (96 floats),
+// and a point in the same cell evaluates M(x) without gathering (about half
+// of the Broyden steps on the full-size frame stay in their cell).  The same
+// weights and multiply-adds in the same order as blend_value.
+struct CornerCache {
+  float4 C[8][3];
+  int base = -1;
+  // returns whether it gathered
+  __device__ __forceinline__ bool blend(const SkinDev& S, const float4* __restrict__ M, float3 x, float Mx[12]) {
+    const CellCoord c = skin_cell(S, x);
+    const bool gather = c.base != base;
+    if (gather) {
+      base = c.base;
+#pragma unroll
+      for (int corner = 0; corner < 8; ++corner) {
+        const float4* p = M + 3 * corner_index(S, c.base, corner);
+        C[corner][0] = __ldg(p);
+        C[corner][1] = __ldg(p + 1);
+        C[corner][2] = __ldg(p + 2);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 12; ++q) Mx[q] = 0.f;
+#pragma unroll
+    for (int corner = 0; corner < 8; ++corner)
+      accumulate_corner(Mx, corner_weight(c, corner), C[corner][0], C[corner][1], C[corner][2]);
+    return gather;
+  }
+};
 
 __device__ __forceinline__ float3 apply34(const float A[12], float3 x) {
   return make_float3(fmaf(A[0], x.x, fmaf(A[1], x.y, fmaf(A[2], x.z, A[3]))),

@@ -47,7 +47,7 @@ __device__ __forceinline__ int next_list(unsigned* work) {
 
 enum StatIdx {
   ST_RAYS = 0, ST_HIT, ST_MARCHED, ST_OCC, ST_STARTS, ST_ITERS, ST_CONV, ST_ROOTS, ST_EARLY, ST_PROP, ST_FALLBACK,
-  ST_CULLED,
+  ST_CULLED, ST_GATHERS,
   ST_COUNT = 16
 };
 

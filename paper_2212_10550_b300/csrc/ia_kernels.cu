@@ -279,6 +279,7 @@ __global__ void __launch_bounds__(256, IA_POSED_MIN_BLOCKS)
   if (stats) {
     flush_stats(stats, ST_STARTS, st.starts);
     flush_stats(stats, ST_ITERS, st.iters);
+    flush_stats(stats, ST_GATHERS, st.starts + st.iters);
     flush_stats(stats, ST_CONV, st.converged);
     flush_stats(stats, ST_ROOTS, st.roots);
     flush_stats(stats, ST_PROP, st.proposed);
@@ -949,6 +950,7 @@ __global__ void __launch_bounds__(kRenderThreads, IA_RENDER_MIN_BLOCKS) render_k
     flush_stats(a.stats, ST_CULLED, n_culled);
     flush_stats(a.stats, ST_STARTS, st.starts);
     flush_stats(a.stats, ST_ITERS, st.iters);
+    flush_stats(a.stats, ST_GATHERS, st.starts + st.iters);
     flush_stats(a.stats, ST_CONV, st.converged);
     flush_stats(a.stats, ST_ROOTS, st.roots);
     flush_stats(a.stats, ST_EARLY, n_early);

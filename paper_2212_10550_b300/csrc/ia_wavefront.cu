@@ -24,8 +24,9 @@
 // ia_device.cuh, merge rule, polish, field and selection; the difference is the
 // schedule), and with the proposal search up to the fused kernel's fallback
 // queue merging a sample's roots in another order.  The search
-// items are independent and light (128 registers, four blocks of four warps
-// per SM against one block of eight warps for the fused kernel), and the
+// items are independent and light (the Broyden state and the last cell's 8
+// corner records: 158 registers, three blocks of four warps per SM against
+// one block of eight warps for the fused kernel), and the
 // proposal's fallback starts, a few per ray where they occur, form one dense
 // wave instead of a tail per list.  Samples behind the point where a ray's
 // transmittance falls below the threshold are searched too (the march does
@@ -211,10 +212,16 @@ __global__ void __launch_bounds__(256) wf_propose_kernel(const RenderArgs a, con
 // kNinvSmemFloats (one pose: the render, the occupancy refresh), else read
 // from global memory (the training step's 16 poses: staging them, 18 KB per
 // block, took L1 capacity from the gathers and was slower).
+// Each item keeps the corner records of the cell it gathered last in registers
+// (CornerCache): about half of the Broyden steps stay in their cell and skip
+// the gather.  Measured on the full-size frame against gathering every step at
+// 128 registers and 16 warps per SM: plain search 3.90 -> 3.61 ms, proposal
+// wave 0.44 -> 0.33 ms.  Wider loads of the same records were slower: a corner
+// pair (x, x + 1) as 256-bit loads, 4.5-4.8 ms.
 constexpr int kNinvSmemFloats = 1024;
 
 template <bool kProp>
-__global__ void __launch_bounds__(128, 4) wf_search_kernel(const RenderArgs a, const WfArgs w, int wave) {
+__global__ void __launch_bounds__(128, 3) wf_search_kernel(const RenderArgs a, const WfArgs w, int wave) {
   extern __shared__ float4 sNinv4[];
   const int nb = a.P.cfg.nb;
   const SkinDev& S = a.P.S;
@@ -232,7 +239,7 @@ __global__ void __launch_bounds__(128, 4) wf_search_kernel(const RenderArgs a, c
   float4* out = wave == 0 ? w.item0 : w.item1;
   const int max_iter = a.P.cfg.max_iter;
   const float tol2 = a.P.cfg.tol2;
-  unsigned starts = 0, iters = 0, conv_n = 0;
+  unsigned starts = 0, iters = 0, conv_n = 0, gathers = 0;
   for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
     const int q = (int)((unsigned)it / (unsigned)per), j = it - q * per;
     const int s = wave == 0 ? q : w.fb[q];
@@ -259,7 +266,8 @@ __global__ void __launch_bounds__(128, 4) wf_search_kernel(const RenderArgs a, c
     }
     float3 x = search_start(A, xn, kProp && wave == 0 && j == 0, poff);
     float Mx[12];
-    blend_value(S, M, x, Mx);
+    CornerCache cells;
+    gathers += cells.blend(S, M, x, Mx);
     ++starts;
     float3 r = search_residual(Mx, x, xn);
     // initial inverse Jacobian: LBS with the weights frozen at x0, (sum_i w_i R_i)^-1
@@ -275,7 +283,7 @@ __global__ void __launch_bounds__(128, 4) wf_search_kernel(const RenderArgs a, c
         if (k >= max_iter) break;
         const float3 dx = search_dir(H, r);
         x = add3(x, dx);
-        blend_value(S, M, x, Mx);
+        gathers += cells.blend(S, M, x, Mx);
         ++iters;
         const float3 rn = search_residual(Mx, x, xn);
         const float3 dr = make_float3(__fsub_rn(rn.x, r.x), __fsub_rn(rn.y, r.y), __fsub_rn(rn.z, r.z));
@@ -288,7 +296,8 @@ __global__ void __launch_bounds__(128, 4) wf_search_kernel(const RenderArgs a, c
     out[it] = make_float4(x.x, x.y, x.z, __int_as_float(valid ? ((order << 8) | label) : -1));
   }
   if (a.stats)
-    flush_stats_block<3>(a.stats, {ST_STARTS, ST_ITERS, ST_CONV}, {(long long)starts, (long long)iters, (long long)conv_n});
+    flush_stats_block<4>(a.stats, {ST_STARTS, ST_ITERS, ST_CONV, ST_GATHERS},
+                         {(long long)starts, (long long)iters, (long long)conv_n, (long long)gathers});
 }
 
 // ---- the samples whose proposed starts found no root

@@ -408,6 +408,10 @@ def test_render_paths_agree(ia):
             assert s1["early_stopped"] == s0["early_stopped"] > 0
             assert s1["occupied_samples"] >= s0["occupied_samples"]
             assert s1["marched_slots"] == s1["hit_rays"] * sc.max_samples
+            # the fused search gathers at every evaluation; a wavefront item
+            # gathers at its start and then only when a step leaves its cell
+            assert s0["grid_gathers"] == s0["starts"] + s0["broyden_iters"]
+            assert s1["starts"] <= s1["grid_gathers"] < s1["starts"] + s1["broyden_iters"]
         with pytest.raises(ia.IAError) as e:
             ia.ia_set_render_path(ctx, 7)
         assert e.value.status == ia.IA_ERR_ARG

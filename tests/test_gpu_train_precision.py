@@ -284,6 +284,8 @@ def test_train_step_with_proposal_starts(ia):
     args = (om, op, occ, rb["origin"], rb["direction"], rb["pose"], rb["target"])
     _, _, flags, _ = G.train(*args, grad=False, prop=pr, theta=theta)
     keep = flags == 0
+    print(f"oracle-flagged rays dropped: {(~keep).sum()} of {keep.size}")
+    assert (~keep).sum() <= 0.02 * keep.size  # 24 of 2048 with this seed
     rays = {k: rb[k][keep] for k in ("origin", "direction", "pose", "target")}
 
     ctx = _ctx(ia, sc, table, mlp, 1)

@@ -3,7 +3,7 @@
 Each test checks the oracle against something the paper or the mathematics fixes
 (closed forms, invariants, library routines, brute force, literal values derived
 from published constants) so that a dropped term, a sign or an index slip in the
-oracle fails here before the oracle is trusted to judge the CUDA path.
+oracle fails here before the oracle is trusted to check the CUDA path.
 """
 import copy
 

@@ -500,25 +500,58 @@ def skip_ablation(torch, ia, sc, table, mlp, icam, rgb, alpha, stream, poses, fr
     return out
 
 
-def gather_peaks(torch, ia, stream, num_sms):
-    """Random 48-byte record gathers (ia_gather_probe) from a 64 KiB table (L1
-    resident) and from a table the size of one blended grid, 64^3 vertices
-    (12.6 MB, L2 resident): useful GB/s, best of 5 launches."""
+def table_entries(level_res, log2_table):
+    """Entries of a hash table (the documented storage: dense levels (res + 1)^3,
+    hashed levels 2^log2_table)."""
+    T = 1 << log2_table
+    return sum(min((int(r) + 1) ** 3, T) for r in level_res)
+
+
+def gather_peaks(torch, ia, stream, num_sms, hash_entries=None, prop_entries=None, skin_floats=None):
+    """Random-record rates of the library's probes, useful GB/s, best of 5 launches:
+    48-byte gathers (ia_gather_probe) from a 64 KiB table (l1, L1 resident) and
+    from a table the size of one blended grid, 64^3 vertices (l2, 12.6 MB, L2
+    resident); with the sizes given, 4- and 8-byte gathers from tables of the
+    field's hash-table entries (hash4: the fp16 shadow, hash8: fp32) and of the
+    proposal's (prop8), 8-byte vector atomics on the field's table (atomic8: the
+    hash-gradient scatter) and 16-byte ones on a skinning-grid-sized table
+    (atomic16: the implicit gradient's scatter)."""
     out = {}
     sink = torch.zeros(1, device="cuda")
-    for name, n_rec in (("l1", 65536 // 48), ("l2", 64 ** 3)):
-        table = torch.rand(n_rec * 12, device="cuda")
-        blocks, iters = num_sms * 8, 640
-        ia.ia_gather_probe(table, n_rec, 64, blocks, sink, stream=stream)  # warm-up
+    blocks = num_sms * 8
+
+    def best_of(run, nbytes):
+        run(8)  # warm-up
         best = 0.0
         for _ in range(5):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            ia.ia_gather_probe(table, n_rec, iters, blocks, sink, stream=stream)
+            run(640)
             b.record(stream)
             torch.cuda.synchronize()
-            best = max(best, blocks * 256 * iters * 48 / (a.elapsed_time(b) * 1e-3) / 1e9)
-        out[name] = round(best, 1)
+            best = max(best, blocks * 256 * 640 * nbytes / (a.elapsed_time(b) * 1e-3) / 1e9)
+        return round(best, 1)
+
+    gathers = [("l1", 65536 // 48, 48), ("l2", 64 ** 3, 48)]
+    if hash_entries:
+        gathers += [("hash4", hash_entries, 4), ("hash8", hash_entries, 8)]
+    if prop_entries:
+        gathers += [("prop8", prop_entries, 8)]
+    for name, n_rec, rb in gathers:
+        table = torch.rand(n_rec * rb // 4, device="cuda")
+        out[name] = best_of(lambda it: ia.ia_gather_probe(table, n_rec, it, blocks, sink, stream=stream,
+                                                          record_bytes=rb), rb)
+        del table
+    atomics = []
+    if hash_entries:
+        atomics.append(("atomic8", hash_entries, 8))
+    if skin_floats:
+        atomics.append(("atomic16", skin_floats // 4, 16))
+    for name, n_rec, rb in atomics:
+        table = torch.zeros(n_rec * rb // 4, device="cuda")
+        out[name] = best_of(lambda it: ia.ia_atomic_probe(table, n_rec, it, blocks, stream=stream,
+                                                          record_bytes=rb), rb)
+        del table
     return out
 
 
@@ -837,9 +870,15 @@ def run_ours(args, rank, world, local_rank):
     peak = fp32_peak_tflops(sm_mhz)
     r_ms = statistics.mean(render_ms)
     r16_ms = statistics.mean(render16)
-    peaks_g = gather_peaks(torch, ia, stream, torch.cuda.get_device_properties(0).multi_processor_count)
+    pcfg = S.proposal_config()
+    peaks_g = gather_peaks(torch, ia, stream, torch.cuda.get_device_properties(0).multi_processor_count,
+                           hash_entries=sc.n_table_entries(),
+                           prop_entries=table_entries(pcfg["level_res"], pcfg["log2_table"]),
+                           skin_floats=sc.skin_res ** 3 * sc.n_bones)
+    hash_src = ("ia_gather_probe: random {b}-byte records from a table of the field's {n:,} hash entries "
+                "({mb:.1f} MB), measured in this run")
+    prop_src = "ia_gather_probe: random 8-byte records from a table of the proposal's hash entries, measured in this run"
     l1_src = "ia_gather_probe: random 48-byte records from a 64 KiB table (L1), measured in this run"
-    l2_src = "ia_gather_probe: random 48-byte records from a 12.6 MB table (L2), measured in this run"
     hbm = peaks.get("hbm_gbs", 6400.0)
     hbm_src = f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else \
         "fallback HBM figure"
@@ -898,16 +937,20 @@ def run_ours(args, rank, world, local_rank):
                 "48 B x 8 corners x (starts + Broyden steps); time: all its launches per frame (step)")
         fk = [k for k in prof if mine(k, "wf_field_kernel")]
         if fk:
+            rb = hash_b // 128  # bytes of one hash entry: 8 (fp32) or 4 (fp16 shadow)
             kern[f"{fk[0]} ({label})"] = roofline_entry(
-                fk[0], "l1-gather", (GATHER_LBS + hash_b) * st["roots"], "B", prof[fk[0]][1] * prof[fk[0]][0],
-                peaks_g["l1"], "GB/s",
-                l1_src, f"per distinct root: the polish's LBS evaluation + {hash_b} B of hash gathers")
+                fk[0], "hash-gather", hash_b * st["roots"], "B", prof[fk[0]][1] * prof[fk[0]][0],
+                peaks_g[f"hash{rb}"], "GB/s",
+                hash_src.format(b=rb, n=sc.n_table_entries(), mb=sc.n_table_entries() * rb / 1e6),
+                f"per distinct root: {hash_b} B of hash gathers (16 levels x 8 corners x {rb} B); the polish's "
+                "8 x 48 B blended-grid gathers, the merge and the MLP run in the same time and are not counted")
         pk = [k for k in prof if mine(k, "wf_propose_kernel")]
         if pk and prop:
             kern[f"{pk[0]} ({label})"] = roofline_entry(
-                pk[0], "l1-gather", GATHER_PROP * st["proposed"], "B", prof[pk[0]][1] * prof[pk[0]][0],
-                peaks_g["l1"], "GB/s",
-                l1_src, "512 B of proposal-encoding gathers per sample")
+                pk[0], "hash-gather", GATHER_PROP * st["proposed"], "B", prof[pk[0]][1] * prof[pk[0]][0],
+                peaks_g["prop8"], "GB/s", prop_src,
+                "512 B of proposal-encoding gathers per sample (8 levels x 8 corners x 8 B); its network "
+                "runs in the same time and is not counted")
 
     wavefront(prof_plain, per_frame, GATHER_HASH, False, "", "render, fp32")
     wavefront(prof16, per_frame16, GATHER_HASH_H, True, "", "render, fp16 + proposal")
@@ -922,14 +965,22 @@ def run_ours(args, rank, world, local_rank):
         wavefront(tp, tst, hash_b, tname != "fp32", " [train]", f"{tname} train step, 32768 rays")
         # per searched sample: table read for dL/dx*, hash-gradient atomics, skinning-grid
         # atomics (8 corners x 24 bones), the Jacobian's blended-grid gather, dL/dfeatures and x*
-        per = hash_b + GATHER_HASH + 8 * sc.n_bones * 4 + GATHER_LBS + 128 + 16
-        sc_names = [k for k in ("train_hash_grad_kernel", "train_ift_kernel") if k in tp]
-        if sc_names:
-            kern[f"train scatter ({tname})"] = roofline_entry(
-                " + ".join(sc_names), "l2-gather", per * searched, "B", sum(tp[k][1] for k in sc_names),
-                peaks_g["l2"], "GB/s", l2_src,
-                "per searched sample: table read + float2 hash atomics + skinning-grid atomics + "
-                "Jacobian gather + dL/dfeatures, L2-resident")
+        rooted = tst.get("rooted_samples", 0)
+        if "train_hash_grad_kernel" in tp and rooted:
+            kern[f"train_hash_grad_kernel ({tname})"] = roofline_entry(
+                "train_hash_grad_kernel", "l2-atomic", rooted * 128 * 8, "B", tp["train_hash_grad_kernel"][1],
+                peaks_g["atomic8"], "GB/s",
+                "ia_atomic_probe: random float2 atomicAdds on a table of the field's hash entries, measured in "
+                "this run",
+                "per sample with a root: 16 levels x 8 corners float2 atomics into the table gradient; its table "
+                "reads for dL/dx* run in the same time and are not counted")
+        if "train_ift_kernel" in tp and rooted:
+            kern[f"train_ift_kernel ({tname})"] = roofline_entry(
+                "train_ift_kernel", "l2-atomic", rooted * 8 * sc.n_bones * 4, "B", tp["train_ift_kernel"][1],
+                peaks_g["atomic16"], "GB/s",
+                "ia_atomic_probe: random float4 atomicAdds on a skinning-grid-sized table, measured in this run",
+                "per sample with a root: 8 corners x 24 bones fp32 of skinning-grid gradient as float4 atomics; "
+                "the Jacobian's gathers and the bone-gradient reduction run in the same time and are not counted")
         if tname != "fp32":
             add("wgrad_tc_kernel", tp, "hbm", WGRAD_ROW_BYTES * searched, "B", hbm, "GB/s", hbm_src,
                 "the 384-row fp16 operand column of every searched sample, streamed once")
@@ -968,6 +1019,9 @@ def run_ours(args, rank, world, local_rank):
                          "flop_per_launch": round(flop_field),
                          "work": "per distinct root: Newton polish, hash encoding, fp32 MLP 32-64-64-4, activations"},
         "rooflines": kern,
+        "probe_peaks": dict(peaks_g, unit="GB/s", what="useful bytes per second of random records: 48-byte "
+                            "gathers from L1- and L2-sized tables, 4/8-byte gathers from hash-table-sized tables, "
+                            "8/16-byte vector atomics (ia_gather_probe, ia_atomic_probe)"),
         "correspondence": residual,
         "render_only_fps": round(1e3 / r_ms, 3),
         "mean_broyden_iters_per_sample": round(per_frame["broyden_iters"] / per_frame["occupied_samples"], 2),

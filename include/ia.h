@@ -111,6 +111,8 @@ typedef struct ia_render_stats {
                                 the fused schedule; on the wavefront, those whose cell
                                 differs from the previous evaluation's (the others reuse
                                 the records a lane holds) */
+  int64_t rooted_samples;    /* searched samples with a selected root (wavefront schedule;
+                                0 on the fused one) */
 } ia_render_stats;
 
 /* Create a context on the current CUDA device.  cfg is copied. */

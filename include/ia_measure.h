@@ -18,13 +18,24 @@ extern "C" {
 #endif
 
 /* Random-gather probe: every one of blocks x 256 threads reads `iters` records
- * of 48 bytes (three float4, the size of one vertex of the blended transform
- * grid) at xorshift-random indices of table [n_records][12] fp32 (device,
- * 16-byte aligned), and writes nothing that matters to sink (device, one
- * float).  Timing it on a table that fits L1 or L2 gives the random-gather
- * rate the correspondence search's gathers are measured against.
+ * of record_bytes bytes at xorshift-random indices of table (device,
+ * n_records records, aligned to its records; 16-byte aligned for 48), and
+ * writes nothing that matters to sink (device, one float).  record_bytes: 48
+ * (three float4, one vertex of the blended transform grid: the correspondence
+ * search's gathers), 16, 8 (an fp32 hash-table entry) or 4 (an fp16 entry).
+ * Timing it on a table the size of a kernel's own gives the random-gather
+ * rate that kernel's gathers are measured against.
  * n_records 1..2^31, iters >= 1, blocks >= 1; IA_ERR_ARG otherwise. */
-ia_status ia_gather_probe(const float *table, int64_t n_records, int iters, int blocks, float *sink, void *stream);
+ia_status ia_gather_probe(const float *table, int64_t n_records, int record_bytes, int iters, int blocks, float *sink,
+                          void *stream);
+
+/* Random-atomic probe: every one of blocks x 256 threads adds a small constant
+ * to `iters` records of table (device, n_records records of record_bytes = 8
+ * (float2, a hash-table gradient entry) or 16 (float4) bytes, aligned to its
+ * records) at xorshift-random indices, with one vector atomicAdd each: the
+ * rate of the training scatter's gradient atomics.  The table's values change.
+ * n_records 1..2^31, iters >= 1, blocks >= 1; IA_ERR_ARG otherwise. */
+ia_status ia_atomic_probe(float *table, int64_t n_records, int record_bytes, int iters, int blocks, void *stream);
 
 /* Per-kernel device times of the library's launches.  ia_profile_begin opens
  * a profile on the calling host thread; until ia_profile_end, every kernel the

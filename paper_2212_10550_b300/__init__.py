@@ -46,7 +46,8 @@ class Camera(C.Structure):
 class RenderStats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("rays", "hit_rays", "marched_slots", "occupied_samples", "starts",
                                          "broyden_iters", "converged", "roots", "early_stopped", "proposed",
-                                         "fallbacks", "culled", "grid_gathers")]
+                                         "fallbacks", "culled", "grid_gathers",
+                                         "rooted_samples")]
 
 
     def as_dict(self):
@@ -115,7 +116,8 @@ def lib():
             "ia_train_stats": [P, C.POINTER(RenderStats), V],
             "ia_grad_sizes": [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
             "ia_set_loss": [P, C.POINTER(Loss)],
-            "ia_gather_probe": [P, C.c_int64, I, I, P, V],
+            "ia_gather_probe": [P, C.c_int64, I, I, I, P, V],
+            "ia_atomic_probe": [P, C.c_int64, I, I, I, V],
             "ia_adam_step": [P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, V],
             "ia_proposal_init": [P, C.POINTER(ProposalConfig)],
             "ia_proposal_param_sizes": [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
@@ -323,10 +325,16 @@ def ia_train_backward(ctx, grad_rgb, grads, grad_alpha=None, stream=None):
     _check(lib().ia_train_backward(ctx, _ptr(grad_rgb), _ptr(grad_alpha), C.byref(g), _stream(stream)), ctx)
 
 
-def ia_gather_probe(table, n_records, iters, blocks, sink, stream=None):
-    """Random 48-byte record gathers (a measurement helper)."""
-    _check(lib().ia_gather_probe(_ptr(table), int(n_records), int(iters), int(blocks), _ptr(sink), _stream(stream)),
-           None)
+def ia_gather_probe(table, n_records, iters, blocks, sink, stream=None, record_bytes=48):
+    """Random record gathers of record_bytes (48, 16, 8 or 4) bytes (a measurement helper)."""
+    _check(lib().ia_gather_probe(_ptr(table), int(n_records), int(record_bytes), int(iters), int(blocks), _ptr(sink),
+                                 _stream(stream)), None)
+
+
+def ia_atomic_probe(table, n_records, iters, blocks, stream=None, record_bytes=8):
+    """Random vector atomicAdds of record_bytes (8 or 16) bytes (a measurement helper)."""
+    _check(lib().ia_atomic_probe(_ptr(table), int(n_records), int(record_bytes), int(iters), int(blocks),
+                                 _stream(stream)), None)
 
 
 def ia_profile_begin():

@@ -385,6 +385,7 @@ void read_stats(ia_ctx* c, ia_render_stats* out, cudaStream_t s, const unsigned 
   out->fallbacks = (int64_t)h[ST_FALLBACK];
   out->culled = (int64_t)h[ST_CULLED];
   out->grid_gathers = (int64_t)h[ST_GATHERS];
+  out->rooted_samples = (int64_t)h[ST_ROOTED];
 }
 
 }  // namespace
@@ -1287,13 +1288,28 @@ ia_status ia_adam_step(ia_ctx* c, const float* g_table, const float* g_mlp, cons
   return IA_OK;
 }
 
-ia_status ia_gather_probe(const float* table, int64_t n_records, int iters, int blocks, float* sink, void* stream) {
+ia_status ia_gather_probe(const float* table, int64_t n_records, int record_bytes, int iters, int blocks, float* sink,
+                          void* stream) {
   if (!table || !sink || n_records < 1 || n_records > (1LL << 31) || iters < 1 || blocks < 1)
     return fail(nullptr, IA_ERR_ARG, "bad gather probe arguments");
-  if ((reinterpret_cast<uintptr_t>(table) & 15) != 0) return fail(nullptr, IA_ERR_ARG, "table must be 16-byte aligned");
-  cudaError_t e = launch_gather_probe(reinterpret_cast<const float4*>(table), n_records, iters, blocks, sink,
-                                      (cudaStream_t)stream);
+  if (record_bytes != 4 && record_bytes != 8 && record_bytes != 16 && record_bytes != 48)
+    return fail(nullptr, IA_ERR_ARG, "record_bytes must be 4, 8, 16 or 48");
+  const uintptr_t align = record_bytes == 48 ? 16 : (uintptr_t)record_bytes;
+  if ((reinterpret_cast<uintptr_t>(table) & (align - 1)) != 0)
+    return fail(nullptr, IA_ERR_ARG, "table must be aligned to its records");
+  cudaError_t e = launch_gather_probe(table, n_records, record_bytes, iters, blocks, sink, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "ia_gather_probe");
+  return IA_OK;
+}
+
+ia_status ia_atomic_probe(float* table, int64_t n_records, int record_bytes, int iters, int blocks, void* stream) {
+  if (!table || n_records < 1 || n_records > (1LL << 31) || iters < 1 || blocks < 1)
+    return fail(nullptr, IA_ERR_ARG, "bad atomic probe arguments");
+  if (record_bytes != 8 && record_bytes != 16) return fail(nullptr, IA_ERR_ARG, "record_bytes must be 8 or 16");
+  if ((reinterpret_cast<uintptr_t>(table) & (uintptr_t)(record_bytes - 1)) != 0)
+    return fail(nullptr, IA_ERR_ARG, "table must be aligned to its records");
+  cudaError_t e = launch_atomic_probe(table, n_records, record_bytes, iters, blocks, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "ia_atomic_probe");
   return IA_OK;
 }
 

@@ -47,7 +47,7 @@ __device__ __forceinline__ int next_list(unsigned* work) {
 
 enum StatIdx {
   ST_RAYS = 0, ST_HIT, ST_MARCHED, ST_OCC, ST_STARTS, ST_ITERS, ST_CONV, ST_ROOTS, ST_EARLY, ST_PROP, ST_FALLBACK,
-  ST_CULLED, ST_GATHERS,
+  ST_CULLED, ST_GATHERS, ST_ROOTED,
   ST_COUNT = 16
 };
 
@@ -321,7 +321,9 @@ cudaError_t launch_occ_cover(const SkinDev& S, int V, int n_poses, const SolveCf
 cudaError_t launch_occ_cull(const PosedArgs& a, const BoxDev& box, const float* jitter, unsigned long long* sub,
                             unsigned* cen, unsigned* count, int* cells, float* sigma, unsigned long long* stats,
                             cudaStream_t s);
-cudaError_t launch_gather_probe(const float4* table, int64_t n_records, int iters, int blocks, float* sink,
+cudaError_t launch_gather_probe(const float* table, int64_t n_records, int record_bytes, int iters, int blocks,
+                                float* sink, cudaStream_t s);
+cudaError_t launch_atomic_probe(float* table, int64_t n_records, int record_bytes, int iters, int blocks,
                                 cudaStream_t s);
 cudaError_t launch_occ_ema(const float* sigma, float* d, int n, float decay, cudaStream_t s);
 cudaError_t launch_occ_bits(const float* sigma, int R, int dilate, float tau, uint32_t* bits,

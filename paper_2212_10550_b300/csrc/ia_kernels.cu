@@ -1056,33 +1056,75 @@ cudaError_t launch_march_mask(const RenderArgs& a, uint32_t* mask, cudaStream_t 
 }
 
 // ---------------------------------------------------------------------------
-// Gather probe (a measurement helper, not part of the method): random 48-byte
-// records (three float4, the blended grid's vertex) read by every thread, the
-// access pattern of one corner of the LBS gather.  Its rate on a table that fits
-// L1, or L2, is the peak the search kernels' gathers are compared against.
+// Gather and atomic probes (measurement helpers, not part of the method).
+// Every thread reads, or adds to, records at xorshift-random indices of a
+// table: 48-byte records (three float4, one vertex of the blended grid: one
+// corner of the LBS gather), 16, 8 or 4 bytes (an fp32 / fp16 hash entry).
+// Their rates on tables the size of the kernels' own are the peaks the
+// search, field and scatter kernels are compared against.
 // ---------------------------------------------------------------------------
 
-__global__ void gather_probe_kernel(const float4* __restrict__ table, unsigned n_records, int iters,
+__device__ __forceinline__ unsigned probe_next(unsigned h) {
+  h ^= h << 13;  // xorshift32 (Marsaglia): the record index
+  h ^= h >> 17;
+  h ^= h << 5;
+  return h;
+}
+
+template <int kBytes>
+__global__ void gather_probe_kernel(const float* __restrict__ table, unsigned n_records, int iters,
                                     float* __restrict__ sink) {
   unsigned h = (blockIdx.x * blockDim.x + threadIdx.x) * 2654435761u + 12345u;
   float acc = 0.f;
   for (int i = 0; i < iters; ++i) {
-    h ^= h << 13;  // xorshift32 (Marsaglia): the record index
-    h ^= h >> 17;
-    h ^= h << 5;
-    const float4* p = table + 3 * (size_t)(h % n_records);
-    const float4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
-    acc += a.x + b.y + c.z;
+    h = probe_next(h);
+    const size_t r = h % n_records;
+    if constexpr (kBytes == 4) {
+      acc += __ldg(table + r);
+    } else if constexpr (kBytes == 8) {
+      const float2 a = __ldg(reinterpret_cast<const float2*>(table) + r);
+      acc += a.x + a.y;
+    } else if constexpr (kBytes == 16) {
+      const float4 a = __ldg(reinterpret_cast<const float4*>(table) + r);
+      acc += a.x + a.w;
+    } else {
+      const float4* p = reinterpret_cast<const float4*>(table) + 3 * r;
+      const float4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+      acc += a.x + b.y + c.z;
+    }
   }
   if (acc == 1.2345f) sink[0] = acc;  // keeps the loads; practically never taken
 }
 
-cudaError_t launch_gather_probe(const float4* table, int64_t n_records, int iters, int blocks, float* sink,
-                                cudaStream_t s) {
-  {
-    KernelSpan span("gather_probe_kernel", s);
-    gather_probe_kernel<<<blocks, 256, 0, s>>>(table, (unsigned)n_records, iters, sink);
+template <int kBytes>
+__global__ void atomic_probe_kernel(float* __restrict__ table, unsigned n_records, int iters) {
+  unsigned h = (blockIdx.x * blockDim.x + threadIdx.x) * 2654435761u + 12345u;
+  for (int i = 0; i < iters; ++i) {
+    h = probe_next(h);
+    const size_t r = h % n_records;
+    if constexpr (kBytes == 8) atomicAdd(reinterpret_cast<float2*>(table) + r, make_float2(1e-7f, 1e-7f));
+    else atomicAdd(reinterpret_cast<float4*>(table) + r, make_float4(1e-7f, 1e-7f, 1e-7f, 1e-7f));
   }
+}
+
+cudaError_t launch_gather_probe(const float* table, int64_t n_records, int record_bytes, int iters, int blocks,
+                                float* sink, cudaStream_t s) {
+  KernelSpan span("gather_probe_kernel", s);
+  const unsigned n = (unsigned)n_records;
+  switch (record_bytes) {
+    case 4: gather_probe_kernel<4><<<blocks, 256, 0, s>>>(table, n, iters, sink); break;
+    case 8: gather_probe_kernel<8><<<blocks, 256, 0, s>>>(table, n, iters, sink); break;
+    case 16: gather_probe_kernel<16><<<blocks, 256, 0, s>>>(table, n, iters, sink); break;
+    default: gather_probe_kernel<48><<<blocks, 256, 0, s>>>(table, n, iters, sink); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_atomic_probe(float* table, int64_t n_records, int record_bytes, int iters, int blocks,
+                                cudaStream_t s) {
+  KernelSpan span("atomic_probe_kernel", s);
+  if (record_bytes == 8) atomic_probe_kernel<8><<<blocks, 256, 0, s>>>(table, (unsigned)n_records, iters);
+  else atomic_probe_kernel<16><<<blocks, 256, 0, s>>>(table, (unsigned)n_records, iters);
   return cudaGetLastError();
 }
 

@@ -334,7 +334,7 @@ __device__ __forceinline__ void field_body(const RenderArgs& a, const WfArgs& w,
   const int per0 = kProp ? nprop : nb;
   const int n = chunk_size(w);
   const ListSmem& qs = sm.list;
-  unsigned roots = 0;
+  unsigned roots = 0, rooted = 0;
   for (int s0 = (blockIdx.x * warps + (threadIdx.x >> 5)) * 32; s0 < n; s0 += gridDim.x * warps * 32) {
     const int m = min(32, n - s0);
     const int s = s0 + lane;
@@ -381,11 +381,15 @@ __device__ __forceinline__ void field_body(const RenderArgs& a, const WfArgs& w,
         },
         [&](int i, const PosedOut& o) {
           const bool has = o.start >= 0;
+          rooted += has;
           w.res[w.s0 + s0 + i] = make_float4(has ? o.sigma : 0.f, o.rgb.x, o.rgb.y, o.rgb.z);
           if (w.xs) w.xs[w.s0 + s0 + i] = make_float4(o.xstar.x, o.xstar.y, o.xstar.z, has ? 1.f : 0.f);
         });
   }
-  if (a.stats) flush_stats(a.stats, ST_ROOTS, roots);
+  if (a.stats) {
+    flush_stats(a.stats, ST_ROOTS, roots);
+    flush_stats(a.stats, ST_ROOTED, rooted);
+  }
 }
 
 // fp32: the per-lane MLP holds its activations in registers (one block of 8

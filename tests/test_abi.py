@@ -74,7 +74,8 @@ def test_null_context_of_the_training_split_and_pipeline_settings(ia):
     assert L.ia_set_wait_limit(None, 0) == ia.IA_ERR_ARG
     assert L.ia_set_fault_injection(None, 0) == ia.IA_ERR_ARG
     assert L.ia_set_render_path(None, 0) == ia.IA_ERR_ARG
-    assert L.ia_gather_probe(None, 1, 1, 1, None, None) == ia.IA_ERR_ARG
+    assert L.ia_gather_probe(None, 1, 48, 1, 1, None, None) == ia.IA_ERR_ARG
+    assert L.ia_atomic_probe(None, 1, 8, 1, 1, None) == ia.IA_ERR_ARG
 
 
 def test_launch_tracing_state_machine(ia):

@@ -412,6 +412,9 @@ def test_render_paths_agree(ia):
             # gathers at its start and then only when a step leaves its cell
             assert s0["grid_gathers"] == s0["starts"] + s0["broyden_iters"]
             assert s1["starts"] <= s1["grid_gathers"] < s1["starts"] + s1["broyden_iters"]
+            # samples with a selected root: counted by the wavefront's field kernel
+            assert 0 < s1["rooted_samples"] <= min(s1["roots"], s1["occupied_samples"] - s1["culled"])
+            assert s0["rooted_samples"] == 0
         with pytest.raises(ia.IAError) as e:
             ia.ia_set_render_path(ctx, 7)
         assert e.value.status == ia.IA_ERR_ARG
@@ -548,3 +551,26 @@ def test_errors_are_status_codes(ia):
                            sc.norm_min, sc.norm_max)
     assert e.value.status == ia.IA_ERR_ARG
     ia.ia_destroy(ctx)
+
+
+def test_measurement_probes(ia):
+    """The bench's roofline denominators: random gathers of every record size
+    run and leave the table alone; random vector atomics add their count times
+    the increment to the table's total (to fp32 rounding)."""
+    sink = torch.zeros(1, device="cuda")
+    for rb in (4, 8, 16, 48):
+        table = torch.rand(4096 * rb // 4, device="cuda")
+        before = table.clone()
+        ia.ia_gather_probe(table, 4096, 16, 4, sink, record_bytes=rb)
+        torch.cuda.synchronize()
+        assert torch.equal(table, before)
+    for rb in (8, 16):
+        table = torch.zeros(1000 * rb // 4, device="cuda")
+        ia.ia_atomic_probe(table, 1000, 16, 4, record_bytes=rb)
+        torch.cuda.synchronize()
+        total = float(table.double().sum().item())
+        expect = 4 * 256 * 16 * (rb // 4) * 1e-7
+        assert abs(total - expect) <= 1e-3 * expect
+    with pytest.raises(ia.IAError) as e:
+        ia.ia_gather_probe(torch.zeros(16, device="cuda"), 4, 1, 1, sink, record_bytes=12)
+    assert e.value.status == ia.IA_ERR_ARG

@@ -1149,7 +1149,7 @@ def run_reference(args, rank, world):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * statistics.mean(step_s), 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "l2": "flushed (256 MiB write) before every timed step",
+            "config": {"workload": WORKLOAD, "l2": "host caches, not flushed (the oracle runs on the CPU)",
                        "parallelism": f"{nthreads} host threads", "precision": "fp64", "starts": "all 24 bones",
                        "value": "540x540 frames/s, pose + occupancy refresh + render, fp64 oracle"},
             "work_per_step": f"1/{n_parts} of a frame: one z-slab of the 64^3 occupancy grid and every "

@@ -1001,6 +1001,7 @@ def run_ours(args, rank, world, local_rank):
         "fp16_proposal_speedup": round(statistics.mean(step_ms) / m16, 3),
         "samples_per_s": round(per_frame["occupied_samples"] * fps, 1),
         "fp16_proposal_samples_per_s": round(per_frame16["occupied_samples"] * 1e3 / m16, 1),
+        "marched_slots_per_s": round(per_frame["marched_slots"] * fps, 1),
         "train_step_ms_fp32_8192": train["fp32_8192"]["ms"],
         "train_step_ms_fp32_32768": train["fp32"]["ms"],
         "train_step_ms_fp16_proposal_32768": train["fp16_proposal"]["ms"],

@@ -113,6 +113,10 @@ typedef struct ia_render_stats {
                                 the records a lane holds) */
   int64_t rooted_samples;    /* searched samples with a selected root (wavefront schedule;
                                 0 on the fused one) */
+  int64_t point_culled;      /* proposal search, wavefront render: samples whose proposed
+                                starts found no root and whose point lies in no grown
+                                image box of a canonical skinning cell (the culling bound
+                                point by point): density 0 without the fallback search */
 } ia_render_stats;
 
 /* Create a context on the current CUDA device.  cfg is copied. */

@@ -47,7 +47,7 @@ class RenderStats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("rays", "hit_rays", "marched_slots", "occupied_samples", "starts",
                                          "broyden_iters", "converged", "roots", "early_stopped", "proposed",
                                          "fallbacks", "culled", "grid_gathers",
-                                         "rooted_samples")]
+                                         "rooted_samples", "point_culled")]
 
 
     def as_dict(self):

@@ -17,6 +17,8 @@
 
 using namespace ia;
 
+constexpr int kBoxListCap = 64;  // boxes remembered per occupied cell (about 52 on average at full size)
+
 struct ia_ctx {
   ia_config cfg{};
   int device = 0;
@@ -59,6 +61,14 @@ struct ia_ctx {
   int* d_cand = nullptr;                // [R^3]
   int sub_pose = -1;
   bool occ_cull = true;
+  // the grown image box of every skinning cell for pose box_pose (written with
+  // the culling masks of a per-pose refresh), and per occupied cell of d_occ
+  // the boxes meeting it, valid for pose blist_pose (rebuilt whenever d_occ is
+  // written with valid boxes; -1 otherwise)
+  float4* d_cell_box = nullptr;          // [(Rw - 1)^3][2]
+  int* d_blist_count = nullptr;          // [R^3]
+  int* d_blist = nullptr;                // [R^3][kBoxListCap]
+  int box_pose = -1, blist_pose = -1;
   // the same masks for every pose, for the training step: [sub_all_cap][R^3]
   unsigned long long* d_sub_all = nullptr;
   int sub_all_cap = 0;
@@ -351,11 +361,28 @@ cudaError_t occ_density(ia_ctx* c, int pose, const float* jitter, float* sigma, 
   };
   if (!c->occ_cull) return density(nullptr, nullptr);
   c->sub_pose = -1;
-  cudaError_t e =
-      launch_occ_cull(a, box, jitter, c->d_sub, c->d_cen, c->d_cand_count, c->d_cand, sigma, stats, s);
+  c->box_pose = -1;
+  c->blist_pose = -1;
+  // the boxes themselves only serve the proposal search's fallback test
+  float4* cell_box = a.search ? c->d_cell_box : nullptr;
+  cudaError_t e = launch_occ_cull(a, box, jitter, c->d_sub, c->d_cen, c->d_cand_count, c->d_cand, sigma, stats, s,
+                                  cell_box);
   if (e != cudaSuccess) return e;
   c->sub_pose = pose;
+  c->box_pose = cell_box ? pose : -1;
   return density(c->d_cand, c->d_cand_count);
+}
+
+// The box lists of the grid just written to d_occ, when the boxes belong to a
+// pose (a per-pose refresh with culling computed them); otherwise none.
+static cudaError_t rebuild_box_lists(ia_ctx* c, cudaStream_t s) {
+  c->blist_pose = -1;
+  if (!c->occ_cull || c->box_pose < 0 || !c->d_cell_box) return cudaSuccess;
+  const int nc = c->Rw - 1;
+  cudaError_t e = launch_occ_boxlist(c->d_cell_box, nc * nc * nc, box_dev(c), c->d_occ, c->d_blist_count, c->d_blist,
+                                     kBoxListCap, s);
+  if (e == cudaSuccess) c->blist_pose = c->box_pose;
+  return e;
 }
 
 ia_status need_ready(ia_ctx* c, int pose, bool need_occ) {
@@ -386,6 +413,7 @@ void read_stats(ia_ctx* c, ia_render_stats* out, cudaStream_t s, const unsigned 
   out->culled = (int64_t)h[ST_CULLED];
   out->grid_gathers = (int64_t)h[ST_GATHERS];
   out->rooted_samples = (int64_t)h[ST_ROOTED];
+  out->point_culled = (int64_t)h[ST_PCULLED];
 }
 
 }  // namespace
@@ -454,6 +482,8 @@ ia_status ia_create(const ia_config* cfg, ia_ctx** out) {
   if (e == cudaSuccess) e = dalloc(&c->d_sub, (size_t)R * R * R);
   if (e == cudaSuccess) e = dalloc(&c->d_cen, ((size_t)R * R * R + 31) / 32);
   if (e == cudaSuccess) e = dalloc(&c->d_cand_count, (size_t)1);
+  if (e == cudaSuccess) e = dalloc(&c->d_blist_count, (size_t)R * R * R);
+  if (e == cudaSuccess) e = dalloc(&c->d_blist, (size_t)R * R * R * kBoxListCap);
   if (e == cudaSuccess) e = dalloc(&c->d_cand, (size_t)R * R * R);
   if (e == cudaSuccess) e = cudaMemset(c->d_occ_ema, 0, sizeof(float) * R * R * R);
   if (e == cudaSuccess) e = dalloc(&c->d_stats, (size_t)ST_COUNT);
@@ -494,6 +524,9 @@ void ia_destroy(ia_ctx* c) {
   dfree(c->d_cen);
   dfree(c->d_sub_all);
   dfree(c->d_cand_count);
+  dfree(c->d_blist_count);
+  dfree(c->d_blist);
+  dfree(c->d_cell_box);
   dfree(c->d_cand);
   dfree(c->d_stats);
   dfree(c->d_counter);
@@ -570,6 +603,7 @@ ia_status ia_set_skeleton(ia_ctx* c, int n_bones, const int32_t* parent, const d
   IA_CUDA(c, dalloc(&c->d_parent, (size_t)n_bones), "ia_set_skeleton");
   IA_CUDA(c, dalloc(&c->d_rest, (size_t)3 * n_bones), "ia_set_skeleton");
   IA_CUDA(c, dalloc(&c->d_skin, V * n_bones), "ia_set_skeleton");
+  IA_CUDA(c, dalloc(&c->d_cell_box, (size_t)2 * (skin_res - 1) * (skin_res - 1) * (skin_res - 1)), "ia_set_skeleton");
   IA_CUDA(c, cudaMemcpy(c->d_parent, parent, sizeof(int) * n_bones, cudaMemcpyHostToDevice), "ia_set_skeleton");
   IA_CUDA(c, cudaMemcpy(c->d_rest, rest_joints, sizeof(double) * 3 * n_bones, cudaMemcpyHostToDevice),
           "ia_set_skeleton");
@@ -589,6 +623,8 @@ ia_status ia_set_skeleton(ia_ctx* c, int n_bones, const int32_t* parent, const d
   }
   c->n_poses = 0;  // per-pose state depends on the skeleton
   c->sub_pose = -1;
+  c->box_pose = -1;
+  c->blist_pose = -1;
   c->sub_all_valid = false;
   c->have_occ = false;
   c->fwd_valid = false;
@@ -663,6 +699,8 @@ ia_status ia_set_pose(ia_ctx* c, int n_poses, const double* axis_angle, const do
                                c->d_B0inv, s),
           "ia_set_pose: pose chain");
   c->sub_pose = -1;  // the culling masks belong to the previous grids
+  c->box_pose = -1;
+  c->blist_pose = -1;
   c->sub_all_valid = false;
   c->fwd_valid = false;
   IA_CUDA(c, launch_blend(n_poses, (int)V, c->nb, c->d_skin, c->d_N, c->d_M, s), "ia_set_pose: blend grid");
@@ -699,6 +737,7 @@ ia_status ia_update_occupancy(ia_ctx* c, int pose, int mode, float* sigma_out, u
     IA_CUDA(c, launch_occ_bits(sig, R, c->cfg.occ_dilate, c->cfg.occ_tau, c->d_occ, nullptr, s),
             "ia_update_occupancy: bits");
     c->have_occ = true;
+    IA_CUDA(c, rebuild_box_lists(c, s), "ia_update_occupancy: box lists");
     if (bits_out)
       IA_CUDA(c, cudaMemcpyAsync(bits_out, c->d_occ, words * 4, cudaMemcpyDeviceToDevice, s), "ia_update_occupancy");
   } else {
@@ -742,6 +781,7 @@ ia_status ia_occupancy_from_density(ia_ctx* c, const float* sigma, uint32_t* bit
   IA_CUDA(c, launch_occ_bits(sigma, R, c->cfg.occ_dilate, c->cfg.occ_tau, c->d_occ, nullptr, s),
           "ia_occupancy_from_density");
   c->have_occ = true;
+  IA_CUDA(c, rebuild_box_lists(c, s), "ia_occupancy_from_density: box lists");
   if (bits_out)
     IA_CUDA(c, cudaMemcpyAsync(bits_out, c->d_occ, words * 4, cudaMemcpyDeviceToDevice, s), "ia_occupancy_from_density");
   return IA_OK;
@@ -754,6 +794,7 @@ ia_status ia_set_occupancy(ia_ctx* c, const uint32_t* bits, void* stream) {
   const size_t words = ((size_t)R * R * R + 31) / 32;
   IA_CUDA(c, cudaMemcpyAsync(c->d_occ, bits, words * 4, cudaMemcpyDefault, (cudaStream_t)stream), "ia_set_occupancy");
   c->have_occ = true;
+  IA_CUDA(c, rebuild_box_lists(c, (cudaStream_t)stream), "ia_set_occupancy: box lists");
   return IA_OK;
 }
 
@@ -831,7 +872,7 @@ ia_status ia_march_mask(ia_ctx* c, int pose, const ia_camera* cam, uint32_t* slo
 // one chunk), then compositing.
 constexpr size_t kWfChunk = size_t(1) << 21;
 
-static ia_status render_wavefront(ia_ctx* c, RenderArgs& a, size_t npix, cudaStream_t s) {
+static ia_status render_wavefront(ia_ctx* c, int pose, RenderArgs& a, size_t npix, cudaStream_t s) {
   ia_status st = IA_OK;
   const bool prop = a.P.search != 0;
   const int nb = c->nb;
@@ -889,6 +930,12 @@ static ia_status render_wavefront(ia_ctx* c, RenderArgs& a, size_t npix, cudaStr
   w.item1 = c->d_wf_item1;
   w.fb = c->d_wf_fb;
   w.fbidx = c->d_wf_fbidx;
+  if (prop && c->occ_cull && c->sub_pose == pose && c->blist_pose == pose) {
+    w.blist_count = c->d_blist_count;
+    w.blist = c->d_blist;
+    w.blist_cap = kBoxListCap;
+    w.cell_box = c->d_cell_box;
+  }
   for (size_t s0 = 0; s0 < n_host; s0 += chunk) {
     w.s0 = (int)s0;
     w.ns = (int)std::min(chunk, (size_t)n_host - s0);
@@ -931,7 +978,7 @@ ia_status ia_render(ia_ctx* c, int pose, const ia_camera* cam, float* rgb, float
   a.alpha = o_alpha;
   IA_CUDA(c, cudaMemsetAsync(c->d_stats, 0, sizeof(unsigned long long) * ST_COUNT, s), "ia_render");
   if (c->render_path == IA_RENDER_WAVEFRONT) {
-    st = render_wavefront(c, a, npix, s);
+    st = render_wavefront(c, pose, a, npix, s);
     if (st != IA_OK) return st;
   } else {
     IA_CUDA(c, cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned int), s), "ia_render");
@@ -1279,6 +1326,8 @@ ia_status ia_adam_step(ia_ctx* c, const float* g_table, const float* g_mlp, cons
             "ia_adam_step: skinning grid");
     // every culling mask depends on the skinning grid; the blended grids exist only once poses are set
     c->sub_pose = -1;
+    c->box_pose = -1;
+    c->blist_pose = -1;
     c->sub_all_valid = false;
     c->fwd_valid = false;
     if (c->n_poses > 0) {
@@ -1654,6 +1703,7 @@ ia_status ia_update_occupancy_static(ia_ctx* c, int pose, uint32_t* bits_out, vo
   IA_CUDA(c, launch_occ_bits(sigma, R, c->cfg.occ_dilate, c->cfg.occ_tau, c->d_occ, nullptr, s),
           "ia_update_occupancy_static: bits");
   c->have_occ = true;
+  c->blist_pose = -1;  // the render's box lists belong to the previous grid
   if (bits_out) {
     const size_t words = ((size_t)R * R * R + 31) / 32;
     IA_CUDA(c, cudaMemcpyAsync(bits_out, c->d_occ, words * 4, cudaMemcpyDeviceToDevice, s),

@@ -47,7 +47,7 @@ __device__ __forceinline__ int next_list(unsigned* work) {
 
 enum StatIdx {
   ST_RAYS = 0, ST_HIT, ST_MARCHED, ST_OCC, ST_STARTS, ST_ITERS, ST_CONV, ST_ROOTS, ST_EARLY, ST_PROP, ST_FALLBACK,
-  ST_CULLED, ST_GATHERS, ST_ROOTED,
+  ST_CULLED, ST_GATHERS, ST_ROOTED, ST_PCULLED,
   ST_COUNT = 16
 };
 
@@ -142,6 +142,14 @@ struct WfArgs {
   int* fbidx;           // chunk [ns] a sample's fallback position, or -1
   unsigned* n_fb;       // the chunk's fallback samples (counter, zeroed per chunk)
   int role;             // the caller, for the launch names: kWfRender, kWfOccupancy, kWfTrain
+  // or null: per occupied cell of the render's grid, the skinning cells whose
+  // grown image box meets it (blist_count [R^3], blist [R^3][blist_cap],
+  // cell_box [(Rw - 1)^3][2]); a sample whose proposed starts found no root
+  // and whose point lies in none of its cell's boxes has no root: no fallback
+  const int* blist_count;
+  const int* blist;
+  int blist_cap;
+  const float4* cell_box;
 };
 constexpr int kWfRender = 0, kWfOccupancy = 1, kWfTrain = 2;
 
@@ -316,11 +324,14 @@ cudaError_t launch_blend(int P, int V, int nb, const float* W, const float* N, f
 cudaError_t launch_occ_density(const PosedArgs& a, const BoxDev& box, const float* jitter, const int* cells,
                                const unsigned* count, float* sigma, unsigned long long* stats, unsigned* work,
                                int num_sms, cudaStream_t s);
+// cell_box (one pose only): each skinning cell's grown image box, [(Rw - 1)^3][2]
 cudaError_t launch_occ_cover(const SkinDev& S, int V, int n_poses, const SolveCfg& cfg, const BoxDev& box,
-                             unsigned long long* sub, unsigned* cen, cudaStream_t s);
+                             unsigned long long* sub, unsigned* cen, cudaStream_t s, float4* cell_box = nullptr);
 cudaError_t launch_occ_cull(const PosedArgs& a, const BoxDev& box, const float* jitter, unsigned long long* sub,
                             unsigned* cen, unsigned* count, int* cells, float* sigma, unsigned long long* stats,
-                            cudaStream_t s);
+                            cudaStream_t s, float4* cell_box = nullptr);
+cudaError_t launch_occ_boxlist(const float4* cell_box, int n_cells, const BoxDev& box, const uint32_t* occ, int* count,
+                               int* list, int cap, cudaStream_t s);
 cudaError_t launch_gather_probe(const float* table, int64_t n_records, int record_bytes, int iters, int blocks,
                                 float* sink, cudaStream_t s);
 cudaError_t launch_atomic_probe(float* table, int64_t n_records, int record_bytes, int iters, int blocks,

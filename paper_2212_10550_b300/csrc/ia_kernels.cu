@@ -374,7 +374,7 @@ constexpr int kCoverWin = 4096;  // 64-bit words of the shared window (32 KB)
 // blockIdx.y: the pose (blended grid S.M + pose * V * 3, masks sub + pose * R^3).
 __global__ void __launch_bounds__(256) occ_cover_kernel(SkinDev S, int V, const BoxDev box, float slack,
                                                         unsigned long long* __restrict__ sub,
-                                                        unsigned* __restrict__ cen) {
+                                                        unsigned* __restrict__ cen, float4* __restrict__ cell_box) {
   static_assert(kSub * kSub * kSub == 64, "one 64-bit word per occupancy cell");
   __shared__ unsigned long long win[kCoverWin];
   __shared__ unsigned char wcen[kCoverWin];  // centre flags of the window's cells
@@ -447,6 +447,11 @@ __global__ void __launch_bounds__(256) occ_cover_kernel(SkinDev S, int V, const 
       s0[a] = (int)fminf(fmaxf(f0, 0.f), (float)(ns - 1));
       s1[a] = (int)fmaxf(fminf(f1, (float)(ns - 1)), 0.f);
     }
+  }
+  if (cell_box && cx < nc && cy < nc && cz < nc) {  // the grown box, or an empty one
+    const size_t ci = (size_t)cx + (size_t)nc * (cy + (size_t)nc * cz);
+    cell_box[2 * ci] = live ? make_float4(blo[0], blo[1], blo[2], 0.f) : make_float4(1.f, 1.f, 1.f, 0.f);
+    cell_box[2 * ci + 1] = live ? make_float4(bhi[0], bhi[1], bhi[2], 0.f) : make_float4(-1.f, -1.f, -1.f, 0.f);
   }
   if (live) {
 #pragma unroll
@@ -545,7 +550,8 @@ __global__ void occ_cand_kernel(const BoxDev box, const float* __restrict__ jitt
 // first, V vertices each) into sub [n_poses][R^3] (cleared here); with cen
 // (n_poses == 1) also the centre flags [ceil(R^3 / 32)] (cleared here).
 cudaError_t launch_occ_cover(const SkinDev& S, int V, int n_poses, const SolveCfg& cfg, const BoxDev& box,
-                             unsigned long long* sub, unsigned* cen, cudaStream_t s) {
+                             unsigned long long* sub, unsigned* cen, cudaStream_t s, float4* cell_box) {
+  if (cell_box && n_poses != 1) return cudaErrorInvalidValue;
   const size_t n = (size_t)box.R * box.R * box.R;
   if (cen && n_poses != 1) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(sub, 0, n * n_poses * sizeof(unsigned long long), s);
@@ -561,7 +567,7 @@ cudaError_t launch_occ_cover(const SkinDev& S, int V, int n_poses, const SolveCf
   const int blocks = ((nc + 7) / 8) * ((nc + 7) / 8) * ((nc + 3) / 4);
   {
     KernelSpan span("occ_cover_kernel", s);
-    occ_cover_kernel<<<dim3(blocks, n_poses), 256, 0, s>>>(S, V, box, slack, sub, cen);
+    occ_cover_kernel<<<dim3(blocks, n_poses), 256, 0, s>>>(S, V, box, slack, sub, cen, cell_box);
   }
   return cudaGetLastError();
 }
@@ -571,15 +577,63 @@ cudaError_t launch_occ_cover(const SkinDev& S, int V, int n_poses, const SolveCf
 // (cleared here)
 cudaError_t launch_occ_cull(const PosedArgs& a, const BoxDev& box, const float* jitter, unsigned long long* sub,
                             unsigned* cen, unsigned* count, int* cells, float* sigma, unsigned long long* stats,
-                            cudaStream_t s) {
+                            cudaStream_t s, float4* cell_box) {
   const int n = box.R * box.R * box.R;
   cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   unsigned* c = jitter ? nullptr : cen;
-  if ((e = launch_occ_cover(a.S, a.S.Rw * a.S.Rw * a.S.Rw, 1, a.cfg, box, sub, c, s)) != cudaSuccess) return e;
+  if ((e = launch_occ_cover(a.S, a.S.Rw * a.S.Rw * a.S.Rw, 1, a.cfg, box, sub, c, s, cell_box)) != cudaSuccess)
+    return e;
   {
     KernelSpan span("occ_cand_kernel", s);
     occ_cand_kernel<<<(n + 255) / 256, 256, 0, s>>>(box, jitter, sub, c, cells, count, sigma, stats);
+  }
+  return cudaGetLastError();
+}
+
+// Per occupied cell of the render's grid, the skinning cells whose grown image
+// box (cell_box, from occ_cover_kernel) meets it: one thread per skinning
+// cell, its box's range of occupancy cells by cell_of's index arithmetic
+// (monotone in the coordinates, so the range holds the cell of every point
+// inside the box), one slot per occupied cell of the range.  A cell with more
+// than `cap` boxes keeps a count above cap: its points are not tested.
+__global__ void occ_boxlist_kernel(const float4* __restrict__ cell_box, int n_cells, const BoxDev box,
+                                   const uint32_t* __restrict__ occ, int* __restrict__ count, int* __restrict__ list,
+                                   int cap) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_cells) return;
+  const float4 lo = cell_box[2 * (size_t)i], hi = cell_box[2 * (size_t)i + 1];
+  if (!(lo.x <= hi.x)) return;  // no box
+  const int c0 = cell_of(box, make_float3(lo.x, lo.y, lo.z)), c1 = cell_of(box, make_float3(hi.x, hi.y, hi.z));
+  const int R = box.R;
+  const int x0 = c0 % R, y0 = (c0 / R) % R, z0 = c0 / (R * R);
+  const int x1 = c1 % R, y1 = (c1 / R) % R, z1 = c1 / (R * R);
+  // a row of the range is a run of consecutive bits: its words are read once
+  // and only the occupied cells visited
+  for (int z = z0; z <= z1; ++z)
+    for (int y = y0; y <= y1; ++y) {
+      const int r0 = x0 + R * (y + R * z), r1 = x1 + R * (y + R * z);
+      for (int wd = r0 >> 5; wd <= (r1 >> 5); ++wd) {
+        uint32_t bits = __ldg(occ + wd);
+        const int lo_bit = max(r0 - 32 * wd, 0), hi_bit = min(r1 - 32 * wd, 31);
+        bits &= (hi_bit == 31 ? ~0u : (1u << (hi_bit + 1)) - 1u) & ~((1u << lo_bit) - 1u);
+        while (bits) {
+          const int c = 32 * wd + __ffs(bits) - 1;
+          bits &= bits - 1u;
+          const int slot = atomicAdd(count + c, 1);
+          if (slot < cap) list[(size_t)c * cap + slot] = i;
+        }
+      }
+    }
+}
+
+cudaError_t launch_occ_boxlist(const float4* cell_box, int n_cells, const BoxDev& box, const uint32_t* occ, int* count,
+                               int* list, int cap, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)box.R * box.R * box.R, s);
+  if (e != cudaSuccess) return e;
+  {
+    KernelSpan span("occ_boxlist_kernel", s);
+    occ_boxlist_kernel<<<(n_cells + 255) / 256, 256, 0, s>>>(cell_box, n_cells, box, occ, count, list, cap);
   }
   return cudaGetLastError();
 }

@@ -300,11 +300,15 @@ __global__ void __launch_bounds__(128, 3) wf_search_kernel(const RenderArgs a, c
                          {(long long)starts, (long long)iters, (long long)conv_n, (long long)gathers});
 }
 
-// ---- the samples whose proposed starts found no root
+// ---- the samples whose proposed starts found no root.  With the render's
+//      box lists, a point that lies in no grown image box of a skinning cell
+//      meeting its occupancy cell has no root (the culling bound, point by
+//      point): it gets density 0 without the fallback search, which would find
+//      none.  Its cell's list is complete when its count is at most the cap.
 __global__ void __launch_bounds__(256) wf_fallback_kernel(const RenderArgs a, const WfArgs w) {
   const int n = chunk_size(w);
   const int nprop = min(a.P.prop.top_k, a.P.cfg.nb);
-  unsigned fell = 0;
+  unsigned fell = 0, pculled = 0;
   // whole warps step together (warp_reserve needs all 32 lanes)
   for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
     const int s = base + threadIdx.x;
@@ -312,13 +316,33 @@ __global__ void __launch_bounds__(256) wf_fallback_kernel(const RenderArgs a, co
     if (s < n) {
       fall = true;
       for (int j = 0; j < nprop; ++j) fall &= __float_as_int(w.item0[(size_t)s * nprop + j].w) < 0;
+      if (fall && w.blist) {
+        const float4 p4 = w.xn[w.s0 + s];
+        const int c = cell_of(a.box, make_float3(p4.x, p4.y, p4.z));
+        const int nbox = w.blist_count[c];
+        if (nbox <= w.blist_cap) {
+          bool in = false;
+          for (int k = 0; k < nbox && !in; ++k) {
+            const int b = w.blist[(size_t)c * w.blist_cap + k];
+            const float4 lo = w.cell_box[2 * (size_t)b], hi = w.cell_box[2 * (size_t)b + 1];
+            in = p4.x >= lo.x && p4.x <= hi.x && p4.y >= lo.y && p4.y <= hi.y && p4.z >= lo.z && p4.z <= hi.z;
+          }
+          if (!in) {
+            fall = false;
+            ++pculled;
+          }
+        }
+      }
     }
     const int idx = warp_reserve(w.n_fb, fall ? 1 : 0);
     if (s < n) w.fbidx[s] = fall ? idx : -1;
     if (fall) w.fb[idx] = s;
     fell += fall;
   }
-  if (a.stats) flush_stats(a.stats, ST_FALLBACK, fell);
+  if (a.stats) {
+    flush_stats(a.stats, ST_FALLBACK, fell);
+    flush_stats(a.stats, ST_PCULLED, pculled);
+  }
 }
 
 // ---- per sample: merge the item results, polish, field, max-density root

@@ -177,6 +177,11 @@ def test_render_culling_keeps_every_pixel(ia, mode):
         np.testing.assert_array_equal(a1, a0)
         assert st0["culled"] == 0 and st1["culled"] > 0
         assert st1["starts"] < st0["starts"]
+        if mode == "fp16_proposal":
+            # a culled or point-culled sample has no root, so its proposed starts
+            # fail: without culling it falls back
+            assert st0["point_culled"] == 0 and st1["point_culled"] > 0
+            assert st0["fallbacks"] == st1["fallbacks"] + st1["culled"] + st1["point_culled"]
         assert st1["roots"] == st0["roots"]
         assert (a1 > 0).sum() > 0.05 * n
     # the masks belong to the pose of the last occupancy update: rendering another

@@ -303,6 +303,7 @@ def time_train_step(torch, ia, sc, table, mlp, flush, steps, warmup, stream, n_r
             "samples": st["occupied_samples"], "mean_starts_per_sample": round(st["starts"] / occ, 3),
             "mean_broyden_iters_per_sample": round(st["broyden_iters"] / occ, 3),
             "fallback_rate": round(st["fallbacks"] / max(st["proposed"], 1), 4),
+            "point_culled_rate": round(st.get("point_culled", 0) / max(st["proposed"], 1), 4),
             "loss_scale": scale, "last_step_skipped": skipped}
 
 
@@ -1049,6 +1050,7 @@ def run_ours(args, rank, world, local_rank):
             "mean_broyden_iters_per_sample": round(per_frame16["broyden_iters"] / per_frame16["occupied_samples"], 2),
             "mean_starts_per_sample": round(per_frame16["starts"] / per_frame16["occupied_samples"], 2),
             "fallback_rate": round(per_frame16["fallbacks"] / max(per_frame16["proposed"], 1), 4),
+            "point_culled_rate": round(per_frame16.get("point_culled", 0) / max(per_frame16["proposed"], 1), 4),
             "miss_rate_rays": round(differ / max(hit, 1), 5),
             "miss_definition": "hit rays of 4 frames whose colour or opacity differs from plain fp32 by more "
                                "than 2e-3 relative + 2e-4",

@@ -73,6 +73,14 @@ struct ia_ctx {
   unsigned long long* d_sub_all = nullptr;
   int sub_all_cap = 0;
   bool sub_all_valid = false;
+  // with the proposal search: every pose's grown boxes and, per cell of the
+  // grid, the boxes meeting it (the training step's fallback point test),
+  // valid with the masks
+  float4* d_tcell_box = nullptr;   // [tblist_cap][(Rw - 1)^3][2]
+  int* d_tblist_count = nullptr;   // [tblist_cap][R^3]
+  int* d_tblist = nullptr;         // [tblist_cap][R^3][kBoxListCap]
+  int tblist_cap = 0;
+  bool tblist_valid = false;
   bool have_occ = false;
   // counters
   unsigned long long* d_stats = nullptr;
@@ -379,8 +387,8 @@ static cudaError_t rebuild_box_lists(ia_ctx* c, cudaStream_t s) {
   c->blist_pose = -1;
   if (!c->occ_cull || c->box_pose < 0 || !c->d_cell_box) return cudaSuccess;
   const int nc = c->Rw - 1;
-  cudaError_t e = launch_occ_boxlist(c->d_cell_box, nc * nc * nc, box_dev(c), c->d_occ, c->d_blist_count, c->d_blist,
-                                     kBoxListCap, s);
+  cudaError_t e = launch_occ_boxlist(c->d_cell_box, nc * nc * nc, 1, box_dev(c), c->d_occ, c->d_blist_count,
+                                     c->d_blist, kBoxListCap, s);
   if (e == cudaSuccess) c->blist_pose = c->box_pose;
   return e;
 }
@@ -523,6 +531,9 @@ void ia_destroy(ia_ctx* c) {
   dfree(c->d_sub);
   dfree(c->d_cen);
   dfree(c->d_sub_all);
+  dfree(c->d_tcell_box);
+  dfree(c->d_tblist_count);
+  dfree(c->d_tblist);
   dfree(c->d_cand_count);
   dfree(c->d_blist_count);
   dfree(c->d_blist);
@@ -626,6 +637,7 @@ ia_status ia_set_skeleton(ia_ctx* c, int n_bones, const int32_t* parent, const d
   c->box_pose = -1;
   c->blist_pose = -1;
   c->sub_all_valid = false;
+  c->tblist_valid = false;
   c->have_occ = false;
   c->fwd_valid = false;
   return IA_OK;
@@ -702,6 +714,7 @@ ia_status ia_set_pose(ia_ctx* c, int n_poses, const double* axis_angle, const do
   c->box_pose = -1;
   c->blist_pose = -1;
   c->sub_all_valid = false;
+  c->tblist_valid = false;
   c->fwd_valid = false;
   IA_CUDA(c, launch_blend(n_poses, (int)V, c->nb, c->d_skin, c->d_N, c->d_M, s), "ia_set_pose: blend grid");
   c->n_poses = n_poses;
@@ -935,6 +948,8 @@ static ia_status render_wavefront(ia_ctx* c, int pose, RenderArgs& a, size_t npi
     w.blist = c->d_blist;
     w.blist_cap = kBoxListCap;
     w.cell_box = c->d_cell_box;
+    w.blist_pose_cells = 0;  // one pose (the samples' pose bits are 0)
+    w.box_pose_cells = 0;
   }
   for (size_t s0 = 0; s0 < n_host; s0 += chunk) {
     w.s0 = (int)s0;
@@ -1079,13 +1094,34 @@ ia_status train_prepare(ia_ctx* c, const ia_batch* b, int occ_grid, bool need_ta
         IA_CUDA(c, cudaStreamSynchronize(s), "ia_train_step");
         c->sub_all_cap = 0;
         c->sub_all_valid = false;
+        c->tblist_valid = false;
         IA_CUDA(c, dalloc(&c->d_sub_all, (size_t)c->n_poses * per), "ia_train_step: culling masks");
         c->sub_all_cap = c->n_poses;
       }
-      if (!c->sub_all_valid) {
-        IA_CUDA(c, launch_occ_cover(a.P.S, (int)V, c->n_poses, a.P.cfg, a.box, c->d_sub_all, nullptr, s),
+      // the fallback point test's boxes and lists, with the proposal search
+      const bool lists = a.P.search != 0 && (size_t)c->n_poses * per * kBoxListCap * sizeof(int) <= (size_t(4) << 30);
+      const int nc = c->Rw - 1;
+      if (lists && c->n_poses > c->tblist_cap) {
+        IA_CUDA(c, cudaStreamSynchronize(s), "ia_train_step");
+        c->tblist_cap = 0;
+        c->tblist_valid = false;
+        IA_CUDA(c, dalloc(&c->d_tcell_box, (size_t)c->n_poses * 2 * nc * nc * nc), "ia_train_step: culling boxes");
+        IA_CUDA(c, dalloc(&c->d_tblist_count, (size_t)c->n_poses * per), "ia_train_step: culling boxes");
+        IA_CUDA(c, dalloc(&c->d_tblist, (size_t)c->n_poses * per * kBoxListCap), "ia_train_step: culling boxes");
+        c->tblist_cap = c->n_poses;
+      }
+      if (!c->sub_all_valid || (lists && !c->tblist_valid)) {
+        IA_CUDA(c, launch_occ_cover(a.P.S, (int)V, c->n_poses, a.P.cfg, a.box, c->d_sub_all, nullptr, s,
+                                    lists ? c->d_tcell_box : nullptr),
                 "ia_train_step: culling masks");
         c->sub_all_valid = true;
+        c->tblist_valid = false;
+        if (lists) {
+          IA_CUDA(c, launch_occ_boxlist(c->d_tcell_box, nc * nc * nc, c->n_poses, a.box, nullptr, c->d_tblist_count,
+                                        c->d_tblist, kBoxListCap, s),
+                  "ia_train_step: culling box lists");
+          c->tblist_valid = true;
+        }
       }
       a.sub = c->d_sub_all;
     }
@@ -1163,6 +1199,14 @@ ia_status train_prepare(ia_ctx* c, const ia_batch* b, int occ_grid, bool need_ta
     w.fbidx = c->d_wf_fbidx;
     w.n_fb = c->d_wf_counts + 1;
     w.role = kWfTrain;
+    if (a.sub && a.P.search && c->tblist_valid) {
+      w.blist_count = c->d_tblist_count;
+      w.blist = c->d_tblist;
+      w.blist_cap = kBoxListCap;
+      w.cell_box = c->d_tcell_box;
+      w.blist_pose_cells = c->cfg.occ_res * c->cfg.occ_res * c->cfg.occ_res;
+      w.box_pose_cells = (c->Rw - 1) * (c->Rw - 1) * (c->Rw - 1);
+    }
   }
   if (a.P.search) {
     if (c->n_poses > c->pb1_cap) {
@@ -1329,6 +1373,7 @@ ia_status ia_adam_step(ia_ctx* c, const float* g_table, const float* g_mlp, cons
     c->box_pose = -1;
     c->blist_pose = -1;
     c->sub_all_valid = false;
+    c->tblist_valid = false;
     c->fwd_valid = false;
     if (c->n_poses > 0) {
       IA_CUDA(c, launch_blend(c->n_poses, (int)V, c->nb, c->d_skin, c->d_N, c->d_M, s), "ia_adam_step: blend grid");

@@ -150,6 +150,8 @@ struct WfArgs {
   const int* blist;
   int blist_cap;
   const float4* cell_box;
+  int blist_pose_cells;  // per-pose strides (a sample's pose: the int bits of xn.w): R^3
+  int box_pose_cells;    //   and (Rw - 1)^3
 };
 constexpr int kWfRender = 0, kWfOccupancy = 1, kWfTrain = 2;
 
@@ -324,14 +326,14 @@ cudaError_t launch_blend(int P, int V, int nb, const float* W, const float* N, f
 cudaError_t launch_occ_density(const PosedArgs& a, const BoxDev& box, const float* jitter, const int* cells,
                                const unsigned* count, float* sigma, unsigned long long* stats, unsigned* work,
                                int num_sms, cudaStream_t s);
-// cell_box (one pose only): each skinning cell's grown image box, [(Rw - 1)^3][2]
+// cell_box: each skinning cell's grown image box, [n_poses][(Rw - 1)^3][2]
 cudaError_t launch_occ_cover(const SkinDev& S, int V, int n_poses, const SolveCfg& cfg, const BoxDev& box,
                              unsigned long long* sub, unsigned* cen, cudaStream_t s, float4* cell_box = nullptr);
 cudaError_t launch_occ_cull(const PosedArgs& a, const BoxDev& box, const float* jitter, unsigned long long* sub,
                             unsigned* cen, unsigned* count, int* cells, float* sigma, unsigned long long* stats,
                             cudaStream_t s, float4* cell_box = nullptr);
-cudaError_t launch_occ_boxlist(const float4* cell_box, int n_cells, const BoxDev& box, const uint32_t* occ, int* count,
-                               int* list, int cap, cudaStream_t s);
+cudaError_t launch_occ_boxlist(const float4* cell_box, int n_cells, int n_poses, const BoxDev& box,
+                               const uint32_t* occ, int* count, int* list, int cap, cudaStream_t s);
 cudaError_t launch_gather_probe(const float* table, int64_t n_records, int record_bytes, int iters, int blocks,
                                 float* sink, cudaStream_t s);
 cudaError_t launch_atomic_probe(float* table, int64_t n_records, int record_bytes, int iters, int blocks,

@@ -381,6 +381,7 @@ __global__ void __launch_bounds__(256) occ_cover_kernel(SkinDev S, int V, const 
   __shared__ int wlo[3], whi[3];
   S.M += (size_t)blockIdx.y * V * 3;
   sub += (size_t)blockIdx.y * box.R * box.R * box.R;
+  if (cell_box) cell_box += (size_t)blockIdx.y * 2 * (S.Rw - 1) * (S.Rw - 1) * (S.Rw - 1);
   const int nc = S.Rw - 1;  // cells per axis
   const int bx = (nc + 7) / 8, by = (nc + 7) / 8;
   const int tid = threadIdx.x;
@@ -551,7 +552,6 @@ __global__ void occ_cand_kernel(const BoxDev box, const float* __restrict__ jitt
 // (n_poses == 1) also the centre flags [ceil(R^3 / 32)] (cleared here).
 cudaError_t launch_occ_cover(const SkinDev& S, int V, int n_poses, const SolveCfg& cfg, const BoxDev& box,
                              unsigned long long* sub, unsigned* cen, cudaStream_t s, float4* cell_box) {
-  if (cell_box && n_poses != 1) return cudaErrorInvalidValue;
   const size_t n = (size_t)box.R * box.R * box.R;
   if (cen && n_poses != 1) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(sub, 0, n * n_poses * sizeof(unsigned long long), s);
@@ -591,17 +591,24 @@ cudaError_t launch_occ_cull(const PosedArgs& a, const BoxDev& box, const float* 
   return cudaGetLastError();
 }
 
-// Per occupied cell of the render's grid, the skinning cells whose grown image
-// box (cell_box, from occ_cover_kernel) meets it: one thread per skinning
-// cell, its box's range of occupancy cells by cell_of's index arithmetic
-// (monotone in the coordinates, so the range holds the cell of every point
-// inside the box), one slot per occupied cell of the range.  A cell with more
-// than `cap` boxes keeps a count above cap: its points are not tested.
+// Per occupied cell of the render's grid (occ), or per cell of the grid
+// (occ null: the training step's lists, independent of its changing grid), the
+// skinning cells whose grown image box (cell_box, from occ_cover_kernel)
+// meets it: one thread per skinning cell, its box's range of occupancy cells
+// by cell_of's index arithmetic (monotone in the coordinates, so the range
+// holds the cell of every point inside the box), one slot per listed cell of
+// the range.  A cell with more than `cap` boxes keeps a count above cap: its
+// points are not tested.  blockIdx.y: the pose (boxes [pose][n_cells][2],
+// counts [pose][R^3], lists [pose][R^3][cap]).
 __global__ void occ_boxlist_kernel(const float4* __restrict__ cell_box, int n_cells, const BoxDev box,
                                    const uint32_t* __restrict__ occ, int* __restrict__ count, int* __restrict__ list,
                                    int cap) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_cells) return;
+  const size_t cells = (size_t)box.R * box.R * box.R;
+  cell_box += (size_t)blockIdx.y * 2 * n_cells;
+  count += blockIdx.y * cells;
+  list += blockIdx.y * cells * cap;
   const float4 lo = cell_box[2 * (size_t)i], hi = cell_box[2 * (size_t)i + 1];
   if (!(lo.x <= hi.x)) return;  // no box
   const int c0 = cell_of(box, make_float3(lo.x, lo.y, lo.z)), c1 = cell_of(box, make_float3(hi.x, hi.y, hi.z));
@@ -614,7 +621,7 @@ __global__ void occ_boxlist_kernel(const float4* __restrict__ cell_box, int n_ce
     for (int y = y0; y <= y1; ++y) {
       const int r0 = x0 + R * (y + R * z), r1 = x1 + R * (y + R * z);
       for (int wd = r0 >> 5; wd <= (r1 >> 5); ++wd) {
-        uint32_t bits = __ldg(occ + wd);
+        uint32_t bits = occ ? __ldg(occ + wd) : ~0u;
         const int lo_bit = max(r0 - 32 * wd, 0), hi_bit = min(r1 - 32 * wd, 31);
         bits &= (hi_bit == 31 ? ~0u : (1u << (hi_bit + 1)) - 1u) & ~((1u << lo_bit) - 1u);
         while (bits) {
@@ -627,13 +634,14 @@ __global__ void occ_boxlist_kernel(const float4* __restrict__ cell_box, int n_ce
     }
 }
 
-cudaError_t launch_occ_boxlist(const float4* cell_box, int n_cells, const BoxDev& box, const uint32_t* occ, int* count,
-                               int* list, int cap, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)box.R * box.R * box.R, s);
+cudaError_t launch_occ_boxlist(const float4* cell_box, int n_cells, int n_poses, const BoxDev& box,
+                               const uint32_t* occ, int* count, int* list, int cap, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)n_poses * box.R * box.R * box.R, s);
   if (e != cudaSuccess) return e;
   {
     KernelSpan span("occ_boxlist_kernel", s);
-    occ_boxlist_kernel<<<(n_cells + 255) / 256, 256, 0, s>>>(cell_box, n_cells, box, occ, count, list, cap);
+    occ_boxlist_kernel<<<dim3((n_cells + 255) / 256, n_poses), 256, 0, s>>>(cell_box, n_cells, box, occ, count, list,
+                                                                         cap);
   }
   return cudaGetLastError();
 }

@@ -1155,6 +1155,7 @@ cudaError_t launch_train_forward(const TrainArgs& a, int num_sms, cudaStream_t s
   // (proposal, search waves, field) with each sample's pose
   RenderArgs ra{};
   ra.P = a.P;
+  ra.box = a.box;  // the fallback's point test locates each sample's occupancy cell
   ra.P.theta = nullptr;  // the proposal's layer-1 bias per pose comes from P.prop.b1p
   if (P == Prec::F32) ra.P.search = 0;
   ra.stats = a.stats;

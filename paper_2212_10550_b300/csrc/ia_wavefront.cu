@@ -318,13 +318,15 @@ __global__ void __launch_bounds__(256) wf_fallback_kernel(const RenderArgs a, co
       for (int j = 0; j < nprop; ++j) fall &= __float_as_int(w.item0[(size_t)s * nprop + j].w) < 0;
       if (fall && w.blist) {
         const float4 p4 = w.xn[w.s0 + s];
-        const int c = cell_of(a.box, make_float3(p4.x, p4.y, p4.z));
+        const int pose = __float_as_int(p4.w);
+        const size_t c = (size_t)pose * w.blist_pose_cells + cell_of(a.box, make_float3(p4.x, p4.y, p4.z));
+        const float4* boxes = w.cell_box + 2 * (size_t)pose * w.box_pose_cells;
         const int nbox = w.blist_count[c];
         if (nbox <= w.blist_cap) {
           bool in = false;
           for (int k = 0; k < nbox && !in; ++k) {
-            const int b = w.blist[(size_t)c * w.blist_cap + k];
-            const float4 lo = w.cell_box[2 * (size_t)b], hi = w.cell_box[2 * (size_t)b + 1];
+            const int b = w.blist[c * w.blist_cap + k];
+            const float4 lo = boxes[2 * (size_t)b], hi = boxes[2 * (size_t)b + 1];
             in = p4.x >= lo.x && p4.x <= hi.x && p4.y >= lo.y && p4.y <= hi.y && p4.z >= lo.z && p4.z <= hi.z;
           }
           if (!in) {

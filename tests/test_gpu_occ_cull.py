@@ -198,10 +198,12 @@ def test_render_culling_keeps_every_pixel(ia, mode):
     ia.ia_destroy(ctx)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+@pytest.mark.parametrize("prec", ["fp32", "fp16", "fp16_proposal"])
 def test_training_culling_keeps_the_step(ia, prec):
     """The training step skips samples (and regulariser points) whose point can
-    have no root in their own pose: per-ray colours are bit-identical, loss and
+    have no root in their own pose, and with the proposal search the samples
+    whose proposed starts failed and whose point lies in no grown image box of
+    their pose's canonical cells: per-ray colours are bit-identical, loss and
     gradients equal up to the order of their fp32 atomic sums."""
     sc = S.make_scene("full", 0)
     table, mlp = S.make_field(sc, 0)
@@ -213,6 +215,13 @@ def test_training_culling_keeps_the_step(ia, prec):
     ia.ia_set_skeleton(ctx, sc.parents, sc.rest_joints, sc.skin_grid, sc.canon_min, sc.canon_max,
                        sc.norm_min, sc.norm_max)
     ia.ia_set_params(ctx, torch.from_numpy(table).cuda(), torch.from_numpy(S.pack_mlp(mlp)).cuda())
+    if prec == "fp16_proposal":
+        pc = S.proposal_config()
+        ia.ia_proposal_init(ctx, ia.make_proposal_config(pc["n_levels"], pc["log2_table"], pc["level_res"],
+                                                         pc["top_k"], pc["offset_weight"]))
+        pt, pm = S.proposal_init(sc, pc, 3)
+        ia.ia_proposal_set_params(ctx, torch.from_numpy(pt).cuda(), torch.from_numpy(S.pack_proposal(pm)).cuda())
+        ia.ia_set_search(ctx, ia.IA_SEARCH_PROPOSAL)
     n_poses = 8
     poses = [S.make_pose(sc, i) for i in range(n_poses)]
     ia.ia_set_pose(ctx, np.stack([p[0] for p in poses]), np.stack([p[1] for p in poses]))
@@ -232,8 +241,11 @@ def test_training_culling_keeps_the_step(ia, prec):
                  bones=torch.zeros(n_poses * sc.n_bones * 12, device="cuda"))
         loss = torch.zeros(1, device="cuda")
         rgb = torch.zeros(8192, 3, device="cuda")
+        # (the proposal variant without regulariser points: culled points are not
+        # counted in the stats, so the fallback identity below covers ray samples)
+        reg = {} if prec == "fp16_proposal" else dict(reg_x=reg_x, reg_pose=reg_pose, reg_weight=0.1)
         ia.ia_train_step(ctx, dev["origin"], dev["direction"], dev["pose"], dev["target"], loss, g,
-                         occ_grid=ia.IA_OCC_UNION, rgb_out=rgb, reg_x=reg_x, reg_pose=reg_pose, reg_weight=0.1)
+                         occ_grid=ia.IA_OCC_UNION, rgb_out=rgb, **reg)
         st = ia.ia_train_stats(ctx)
         torch.cuda.synchronize()
         out[cull] = (float(loss.item()), rgb.cpu().numpy(), {k: v.cpu().numpy().astype(np.float64) for k, v in g.items()},
@@ -244,6 +256,11 @@ def test_training_culling_keeps_the_step(ia, prec):
     assert s0["culled"] == 0 and s1["culled"] > 0
     assert s1["occupied_samples"] == s0["occupied_samples"]
     assert s1["starts"] < s0["starts"]
+    if prec == "fp16_proposal":
+        print(f"fallbacks {s1['fallbacks']} + culled {s1['culled']} + point-culled {s1['point_culled']} "
+              f"(culling off: {s0['fallbacks']})")
+        assert s0["point_culled"] == 0 and s1["point_culled"] > 0
+        assert s0["fallbacks"] == s1["fallbacks"] + s1["culled"] + s1["point_culled"]
     np.testing.assert_array_equal(r1, r0)
     assert abs(l1 - l0) <= 1e-6 * abs(l0)
     for k in ("table", "mlp", "skin", "bones"):

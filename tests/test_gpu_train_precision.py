@@ -311,10 +311,11 @@ def test_train_step_with_proposal_starts(ia):
     # which samples needed the fallback depends on the bones proposed for each
     # sample's own pose: the counts must agree (a few marginal samples aside)
     # (a culled sample can have no root, so the oracle's search falls back on it)
-    print(f"fallbacks gpu {st['fallbacks']} + culled {st['culled']}, oracle {int(fb.sum())} of "
+    print(f"fallbacks gpu {st['fallbacks']} + culled {st['culled']} + point-culled {st['point_culled']}, "
+          f"oracle {int(fb.sum())} of "
           f"{st['occupied_samples']} samples")
     assert st["proposed"] == st["occupied_samples"] - st["culled"] > 0
-    assert abs(st["fallbacks"] + st["culled"] - int(fb.sum())) <= max(3, 0.005 * fb.sum())
+    assert abs(st["fallbacks"] + st["culled"] + st["point_culled"] - int(fb.sum())) <= max(3, 0.005 * fb.sum())
     assert 0 < fb.sum() < st["proposed"]
     plain_loss, _, _, plain = G.train(*args)
     lg = float(loss.item())

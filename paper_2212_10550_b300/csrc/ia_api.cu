@@ -947,6 +947,7 @@ static ia_status render_wavefront(ia_ctx* c, int pose, RenderArgs& a, size_t npi
     w.blist_count = c->d_blist_count;
     w.blist = c->d_blist;
     w.blist_cap = kBoxListCap;
+    w.blist_scan = kBoxListCap;  // the render's lists hold occupied cells only: scan them whole
     w.cell_box = c->d_cell_box;
     w.blist_pose_cells = 0;  // one pose (the samples' pose bits are 0)
     w.box_pose_cells = 0;
@@ -1203,6 +1204,7 @@ ia_status train_prepare(ia_ctx* c, const ia_batch* b, int occ_grid, bool need_ta
       w.blist_count = c->d_tblist_count;
       w.blist = c->d_tblist;
       w.blist_cap = kBoxListCap;
+      w.blist_scan = 16;  // the training lists hold every cell a box meets: only short ones pay
       w.cell_box = c->d_tcell_box;
       w.blist_pose_cells = c->cfg.occ_res * c->cfg.occ_res * c->cfg.occ_res;
       w.box_pose_cells = (c->Rw - 1) * (c->Rw - 1) * (c->Rw - 1);

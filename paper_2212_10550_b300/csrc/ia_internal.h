@@ -149,6 +149,7 @@ struct WfArgs {
   const int* blist_count;
   const int* blist;
   int blist_cap;
+  int blist_scan;       // the longest list the test scans (<= blist_cap); longer: no test
   const float4* cell_box;
   int blist_pose_cells;  // per-pose strides (a sample's pose: the int bits of xn.w): R^3
   int box_pose_cells;    //   and (Rw - 1)^3

@@ -305,6 +305,8 @@ __global__ void __launch_bounds__(128, 3) wf_search_kernel(const RenderArgs a, c
 //      meeting its occupancy cell has no root (the culling bound, point by
 //      point): it gets density 0 without the fallback search, which would find
 //      none.  Its cell's list is complete when its count is at most the cap.
+constexpr int kShortBoxList = 16;  // lists scanned with all their loads issued at once
+
 __global__ void __launch_bounds__(256) wf_fallback_kernel(const RenderArgs a, const WfArgs w) {
   const int n = chunk_size(w);
   const int nprop = min(a.P.prop.top_k, a.P.cfg.nb);
@@ -316,24 +318,32 @@ __global__ void __launch_bounds__(256) wf_fallback_kernel(const RenderArgs a, co
     if (s < n) {
       fall = true;
       for (int j = 0; j < nprop; ++j) fall &= __float_as_int(w.item0[(size_t)s * nprop + j].w) < 0;
-      if (fall && w.blist) {
-        const float4 p4 = w.xn[w.s0 + s];
-        const int pose = __float_as_int(p4.w);
-        const size_t c = (size_t)pose * w.blist_pose_cells + cell_of(a.box, make_float3(p4.x, p4.y, p4.z));
-        const float4* boxes = w.cell_box + 2 * (size_t)pose * w.box_pose_cells;
-        const int nbox = w.blist_count[c];
-        if (nbox <= w.blist_cap) {
-          bool in = false;
-          for (int k = 0; k < nbox && !in; ++k) {
-            const int b = w.blist[c * w.blist_cap + k];
-            const float4 lo = boxes[2 * (size_t)b], hi = boxes[2 * (size_t)b + 1];
-            in = p4.x >= lo.x && p4.x <= hi.x && p4.y >= lo.y && p4.y <= hi.y && p4.z >= lo.z && p4.z <= hi.z;
-          }
-          if (!in) {
-            fall = false;
-            ++pculled;
-          }
-        }
+    }
+    if (fall && w.blist) {
+      const float4 p4 = w.xn[w.s0 + s];
+      const int pose = __float_as_int(p4.w);
+      const size_t c = (size_t)pose * w.blist_pose_cells + cell_of(a.box, make_float3(p4.x, p4.y, p4.z));
+      const int nbox = w.blist_count[c];
+      const float4* boxes = w.cell_box + 2 * (size_t)pose * w.box_pose_cells;
+      auto inside = [&](int b) {
+        const float4 lo = boxes[2 * (size_t)b], hi = boxes[2 * (size_t)b + 1];
+        return p4.x >= lo.x && p4.x <= hi.x && p4.y >= lo.y && p4.y <= hi.y && p4.z >= lo.z && p4.z <= hi.z;
+      };
+      bool tested = false, in = false;
+      if (nbox <= kShortBoxList) {  // every load issued at once
+        int b[kShortBoxList];
+#pragma unroll
+        for (int k = 0; k < kShortBoxList; ++k) b[k] = k < nbox ? w.blist[c * w.blist_cap + k] : -1;
+#pragma unroll
+        for (int k = 0; k < kShortBoxList; ++k) in |= b[k] >= 0 && inside(b[k]);
+        tested = true;
+      } else if (nbox <= w.blist_scan) {  // a longer, complete list: box by box
+        for (int k = 0; k < nbox && !in; ++k) in = inside(w.blist[c * w.blist_cap + k]);
+        tested = true;
+      }
+      if (tested && !in) {
+        fall = false;
+        ++pculled;
       }
     }
     const int idx = warp_reserve(w.n_fb, fall ? 1 : 0);

@@ -191,6 +191,16 @@ ia_status ia_get_transforms(ia_ctx *ctx, int pose, float *N, float *Ninv, float 
  * are merged in start order either way).  The search and field run on the
  * render's per-sample kernels; the first call allocates their arrays for R^3
  * query points (0.1 GB at 64^3 and 24 bones, 0.2 GB with the proposal search).
+ * With the proposal search (IA_OCC_POSE, culling on) the call also records each
+ * skinning cell's grown box ((skin_res - 1)^3 x 32 B, allocated by
+ * ia_set_skeleton) and, per occupied cell of the new grid, up to 64 of the boxes
+ * meeting it (R^3 x 65 ints, 68 MB at 64^3, allocated by ia_create): ia_render
+ * of the same pose then skips the fallback search of a sample whose proposed
+ * starts found no root and whose point lies in none of its cell's boxes (no
+ * root is possible there), counted in ia_render_stats.point_culled.  The lists
+ * follow the grid: ia_set_occupancy and ia_occupancy_from_density rebuild them
+ * for the new bits; ia_set_pose, a skinning-grid update and
+ * ia_update_occupancy_static drop them.
  *  sigma_out [R^3] fp32 device or NULL; bits_out [R^3 / 32] uint32 device or NULL. */
 ia_status ia_update_occupancy(ia_ctx *ctx, int pose, int mode, float *sigma_out,
                               uint32_t *bits_out, ia_render_stats *stats, void *stream);
@@ -323,7 +333,12 @@ typedef struct ia_grads {
  * 0.8 KB in fp16 / bf16, plus the search's item results: 16 B per start, i.e.
  * 384 B per sample with every bone as a start, 32 B with the proposal's two
  * and 384 B more for its fallback) is allocated by the context on first use
- * and grown when a larger batch comes.
+ * and grown when a larger batch comes.  With the proposal search and culling on,
+ * the first step after the poses change also records every pose's grown boxes
+ * and, per cell of the grid, up to 64 of the boxes meeting it (per pose 8 MB of
+ * boxes and 68 MB of lists at 64^3; skipped when the lists of all poses would
+ * pass 4 GiB): a sample whose proposed starts found no root and whose point
+ * lies in none of at most 16 listed boxes of its cell skips its fallback search.
  *
  * Precision (Sec. 3.4 trains in half precision): with IA_FP16 / IA_BF16 the
  * forward uses the reduced-precision field (fp16 hash features, tensor-core MLP),

@@ -300,11 +300,14 @@ __global__ void __launch_bounds__(128, 3) wf_search_kernel(const RenderArgs a, c
                          {(long long)starts, (long long)iters, (long long)conv_n, (long long)gathers});
 }
 
-// ---- the samples whose proposed starts found no root.  With the render's
-//      box lists, a point that lies in no grown image box of a skinning cell
-//      meeting its occupancy cell has no root (the culling bound, point by
-//      point): it gets density 0 without the fallback search, which would find
-//      none.  Its cell's list is complete when its count is at most the cap.
+// ---- the samples whose proposed starts found no root.  With box lists (the
+//      render's, per occupied cell; the training step's, per pose and cell), a
+//      point that lies in no grown image box of a skinning cell meeting its
+//      occupancy cell has no root (the culling bound, point by point): it gets
+//      density 0 without the fallback search, which would find none.  A list
+//      is complete when its count is at most the cap, and tested when it is at
+//      most blist_scan long (measured: the training lists, which hold every
+//      cell a box meets, pay only when short; the render's are scanned whole).
 constexpr int kShortBoxList = 16;  // lists scanned with all their loads issued at once
 
 __global__ void __launch_bounds__(256) wf_fallback_kernel(const RenderArgs a, const WfArgs w) {

@@ -10,8 +10,9 @@
 //                        from that start (Sec. 3.1, Eq. 7), its converged root
 //                        inside the canonical box, or none
 //   wf_fallback_kernel   (proposal search) the samples none of whose proposed
-//                        starts found a root; a second search wave runs every
-//                        bone-wise start of those samples only
+//                        starts found a root, less those whose point lies in
+//                        no canonical cell's grown image box; a second search
+//                        wave runs every bone-wise start of those samples only
 //   wf_field_kernel      per sample: its item results merged in start order
 //                        (a root within 1e-4 of an earlier one is that root),
 //                        one Newton polish per root, the field at the roots,

@@ -703,8 +703,10 @@ __global__ void __launch_bounds__(128) train_backward_kernel(const TrainArgs a) 
 
 constexpr int kTileS = 32;
 
+constexpr int kTilePitch = kActStride + 4;  // 16-byte rows: the operands are read as float4 / float2
+
 __global__ void __launch_bounds__(256) mlp_grad_kernel(const TrainArgs a) {
-  __shared__ float tile[kTileS][kActStride + 1];
+  __shared__ __align__(16) float tile[kTileS][kTilePitch];
   const int n = *a.count;
   const int chunk = (n + gridDim.x - 1) / gridDim.x;
   const int s0 = blockIdx.x * chunk, s1 = min(n, s0 + chunk);
@@ -722,24 +724,34 @@ __global__ void __launch_bounds__(256) mlp_grad_kernel(const TrainArgs a) {
   for (int base = s0; base < s1; base += kTileS) {
     const int m = min(kTileS, s1 - base);
     __syncthreads();
-    // channel-major source: warp w stages channels w, w + 8, ...; lane r reads
-    // sample base + r (128-byte rows; the tile's odd row pitch spreads banks)
+    // channel-major source: warp w stages channel quads w, w + 8, ...; lane r
+    // reads sample base + r of the quad's four channels (128-byte rows) and
+    // stores them as one float4 of its sample's row
     {
       const int lane = t & 31;
-      for (int c = t >> 5; c < kActStride; c += blockDim.x >> 5)
-        if (lane < m) tile[lane][c] = __ldg(a.act + (size_t)c * a.act_ld + base + lane);
+      static_assert(kActStride % 4 == 0, "channel quads");
+      for (int c = 4 * (t >> 5); c < kActStride; c += 4 * (blockDim.x >> 5))
+        if (lane < m) {
+          const float* src = a.act + (size_t)c * a.act_ld + base + lane;
+          *reinterpret_cast<float4*>(&tile[lane][c]) =
+              make_float4(__ldg(src), __ldg(src + a.act_ld), __ldg(src + 2 * a.act_ld), __ldg(src + 3 * a.act_ld));
+        }
     }
     __syncthreads();
     for (int r = 0; r < m; ++r) {
       const float* T = tile[r];
+      const float4 d2 = *reinterpret_cast<const float4*>(T + kActD2 + i2);
+      const float4 h1 = *reinterpret_cast<const float4*>(T + kActH1 + j2);
+      const float4 d1v = *reinterpret_cast<const float4*>(T + kActD1 + i1);
+      const float2 fv = *reinterpret_cast<const float2*>(T + kActF + j1);
+      const float dd[4] = {d2.x, d2.y, d2.z, d2.w}, hh[4] = {h1.x, h1.y, h1.z, h1.w};
+      const float ee[4] = {d1v.x, d1v.y, d1v.z, d1v.w}, ff[2] = {fv.x, fv.y};
 #pragma unroll
       for (int x = 0; x < 4; ++x) {
-        const float d = T[kActD2 + i2 + x];
 #pragma unroll
-        for (int y = 0; y < 4; ++y) acc2[4 * x + y] = fmaf(d, T[kActH1 + j2 + y], acc2[4 * x + y]);
-        const float d1 = T[kActD1 + i1 + x];
+        for (int y = 0; y < 4; ++y) acc2[4 * x + y] = fmaf(dd[x], hh[y], acc2[4 * x + y]);
 #pragma unroll
-        for (int y = 0; y < 2; ++y) acc1[2 * x + y] = fmaf(d1, T[kActF + j1 + y], acc1[2 * x + y]);
+        for (int y = 0; y < 2; ++y) acc1[2 * x + y] = fmaf(ee[x], ff[y], acc1[2 * x + y]);
       }
       acc3 = fmaf(T[kActDO + o3], T[kActH2 + j3], acc3);
       if (t < kWidth) accb += T[kActD1 + t];

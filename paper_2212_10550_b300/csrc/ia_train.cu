@@ -566,14 +566,16 @@ static cudaError_t launch_scatter(const TrainArgs& a, bool half_table, int num_s
 // in this thread's column of a shared array (vec[j * 128 + thread]: lanes hit
 // consecutive banks), which each thread reuses for h1, then dH2, then dH1.
 // Sums keep the order of the plain definition (inputs ascending).
-__global__ void __launch_bounds__(128) train_backward_kernel(const TrainArgs a) {
+constexpr int kBwdThreads = 256;  // threads of the fp32 backward (two blocks of eight warps per SM)
+
+__global__ void __launch_bounds__(kBwdThreads) train_backward_kernel(const TrainArgs a) {
   __shared__ __align__(16) float sw[kMlpPadT];
-  extern __shared__ float vec[];  // [kWidth * 128], dynamic (static shared memory stops at 48 KB)
+  extern __shared__ float vec[];  // [kWidth * kBwdThreads], dynamic (static shared memory stops at 48 KB)
   stage_mlp(a.P.mlp, a.P.n_in, sw);
   __syncthreads();
   const int n = *a.count;
   const FieldDev& F = a.P.F;
-  float* my = vec + threadIdx.x;  // my[j * 128]: entry j of this thread's vector
+  float* my = vec + threadIdx.x;  // my[j * kBwdThreads]: entry j of this thread's vector
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
     // this sample's column of the channel-major activations: act[c * ld] is
     // channel c (consecutive lanes write consecutive addresses)
@@ -603,12 +605,12 @@ __global__ void __launch_bounds__(128) train_backward_kernel(const TrainArgs a) 
       }
       const float h = fmaxf(acc, 0.f);
       if (acc > 0.f) m1 |= 1ull << j;
-      my[j * 128] = h;
+      my[j * kBwdThreads] = h;
       act[(kActH1 + j) * ld] = h;
     }
     float h1[kWidth];
 #pragma unroll
-    for (int i = 0; i < kWidth; ++i) h1[i] = my[i * 128];
+    for (int i = 0; i < kWidth; ++i) h1[i] = my[i * kBwdThreads];
     float o0 = sw[kOffB3], o1 = sw[kOffB3 + 1], o2 = sw[kOffB3 + 2], o3 = sw[kOffB3 + 3];
     uint64_t m2 = 0;  // h2 > 0 mask
 #pragma unroll 1
@@ -649,7 +651,7 @@ __global__ void __launch_bounds__(128) train_backward_kernel(const TrainArgs a) 
       const float4 w3 = reinterpret_cast<const float4*>(sw + kOffW3T)[j];
       const float v = w3.x * dO[0] + w3.y * dO[1] + w3.z * dO[2] + w3.w * dO[3];
       const float d = ((m2 >> j) & 1ull) ? v : 0.f;
-      my[j * 128] = d;  // dH2 (h1 is in registers now)
+      my[j * kBwdThreads] = d;  // dH2 (h1 is in registers now)
       act[(kActD2 + j) * ld] = d;
     }
     float dh1[kWidth];
@@ -658,7 +660,7 @@ __global__ void __launch_bounds__(128) train_backward_kernel(const TrainArgs a) 
 #pragma unroll 1
     for (int j = 0; j < kWidth; ++j) {
       const float4* row = reinterpret_cast<const float4*>(sw + kOffW2 + j * kWidth);
-      const float d = my[j * 128];
+      const float d = my[j * kBwdThreads];
 #pragma unroll
       for (int i = 0; i < kWidth / 4; ++i) {
         float4 w = row[i];
@@ -669,13 +671,13 @@ __global__ void __launch_bounds__(128) train_backward_kernel(const TrainArgs a) 
       }
     }
 #pragma unroll
-    for (int i = 0; i < kWidth; ++i) my[i * 128] = dh1[i];
+    for (int i = 0; i < kWidth; ++i) my[i * kBwdThreads] = dh1[i];
     float dfeat[kIn];
 #pragma unroll
     for (int i = 0; i < kIn; ++i) dfeat[i] = 0.f;
 #pragma unroll 1
     for (int j = 0; j < kWidth; ++j) {
-      const float d = ((m1 >> j) & 1ull) ? my[j * 128] : 0.f;
+      const float d = ((m1 >> j) & 1ull) ? my[j * kBwdThreads] : 0.f;
       act[(kActD1 + j) * ld] = d;
       const float4* row = reinterpret_cast<const float4*>(sw + kOffW1 + j * kIn);
 #pragma unroll
@@ -1204,11 +1206,11 @@ cudaError_t launch_train_backward(const TrainArgs& a, const CUtensorMap* map, in
   cudaError_t e;
   const Prec P = (Prec)a.prec;
   if (P == Prec::F32) {
-    const size_t vec_bytes = sizeof(float) * kWidth * 128;
-    if ((e = set_smem(train_backward_kernel, vec_bytes, 128)) != cudaSuccess) return e;
+    const size_t vec_bytes = sizeof(float) * kWidth * kBwdThreads;
+    if ((e = set_smem(train_backward_kernel, vec_bytes, kBwdThreads)) != cudaSuccess) return e;
     {
       KernelSpan span("train_backward_kernel", s);
-      train_backward_kernel<<<num_sms * 4, 128, vec_bytes, s>>>(a);
+      train_backward_kernel<<<num_sms * 2, kBwdThreads, vec_bytes, s>>>(a);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_scatter(a, false, num_sms, s)) != cudaSuccess) return e;

@@ -45,12 +45,11 @@ def _pose_ctx(ia, sc, table, mlp, seeds, early_T=0.0, precision=0):
 
 def test_transforms_bit_exact(ia, scene):
     """The fp64 pose chain's fp32 results on 256 seeded poses.  Both sides
-    use the same rounded fp64 operations; the one thing they do not share is
-    the fp64 cosine and sine of the joint angles (CUDA's and the C library's,
-    each within an ulp or two of the exact value), so an fp32 result could in
-    principle differ by one ulp where an fp64 value sits within an ulp of an
-    fp32 rounding boundary.  Any such element is counted and reported; the
-    contract is bit-exact."""
+    take the same rounded fp64 operations in the same order, the joint
+    angles' cosine and sine included (each side sums their Maclaurin series
+    term by term, with the series reciprocals formed the same way, rather
+    than calling a math library), so every fp32 value must match bit for bit.
+    Differing elements are counted and reported before the assertion."""
     sc, table, mlp = scene
     seeds = list(range(256))
     ctx, poses = _pose_ctx(ia, sc, table, mlp, seeds)

@@ -91,44 +91,49 @@ __global__ void pose_chain_kernel(int P, int nb, const int* __restrict__ parent,
   __shared__ double sB0i[12];
   __shared__ double sRecip[2][kSeriesTerms];  // series reciprocals (sin, cos)
   __shared__ int sDepth[kMaxBones];
+  __shared__ bool sZero[kMaxBones];      // zero rotation angle
   __shared__ int sMaxDepth;
   const int p = blockIdx.x;
   if (p >= P) return;
   const int t = threadIdx.x, k = t / 12, e = t % 12;
   const bool own = k < nb;
   if (t == 0) sMaxDepth = 0;
-  for (int q = t; q < 2 * kSeriesTerms; q += blockDim.x) {
-    const int j = q % kSeriesTerms;
-    sRecip[q / kSeriesTerms][j] =
-        q < kSeriesTerms ? __ddiv_rn(1.0, (double)((2 * j + 2) * (2 * j + 3))) : __ddiv_rn(1.0, (double)((2 * j + 1) * (2 * j + 2)));
+  for (int j = t; j < kSeriesTerms; j += blockDim.x) {  // one warp: both reciprocals of term j
+    sRecip[0][j] = __ddiv_rn(1.0, (double)((2 * j + 2) * (2 * j + 3)));
+    sRecip[1][j] = __ddiv_rn(1.0, (double)((2 * j + 1) * (2 * j + 2)));
   }
   __syncthreads();
-  if (own && e == 0) {
-    const double* th = theta + ((size_t)p * nb + k) * 3;
-    const double a = __dsqrt_rn(DA(DA(DM(th[0], th[0]), DM(th[1], th[1])), DM(th[2], th[2])));
+  // the angle's scalars, thread q for joint q: the first warp(s) alone issue
+  // these long fp64 sequences (a warp instruction costs the fp64 pipe the same
+  // with 1 or 32 lanes active; with the joints' first threads, spread over every
+  // warp of the block, the kernel took 29-34 us per pose)
+  for (int q = t; q < nb; q += blockDim.x) {
+    const double* th = theta + ((size_t)p * nb + q) * 3;
+    const double a2 = DA(DA(DM(th[0], th[0]), DM(th[1], th[1])), DM(th[2], th[2]));
+    const double a = __dsqrt_rn(a2);
+    sZero[q] = a2 == 0.0;
     if (a == 0.0) {
-      sRod[k][0] = 1.0;  // identity rotation
+      sRod[q][0] = 1.0;  // identity rotation
     } else {
       double c, sn;
       cos_sin_series(a, sRecip, c, sn);
-      sRod[k][0] = c;
-      sRod[k][1] = sn;
-      sRod[k][2] = DS(1.0, c);
-      sRod[k][3] = __ddiv_rn(th[0], a);
-      sRod[k][4] = __ddiv_rn(th[1], a);
-      sRod[k][5] = __ddiv_rn(th[2], a);
+      sRod[q][0] = c;
+      sRod[q][1] = sn;
+      sRod[q][2] = DS(1.0, c);
+      sRod[q][3] = __ddiv_rn(th[0], a);
+      sRod[q][4] = __ddiv_rn(th[1], a);
+      sRod[q][5] = __ddiv_rn(th[2], a);
     }
     int d = 0;
-    for (int j = parent[k]; j >= 0; j = parent[j]) ++d;
-    sDepth[k] = d;
+    for (int j = parent[q]; j >= 0; j = parent[j]) ++d;
+    sDepth[q] = d;
     atomicMax(&sMaxDepth, d);
   }
   __syncthreads();
   const int i = e >> 2, j = e & 3;
   if (own) {
     // Rodrigues: R = c I + (1 - c) k k^T + s [k]_x
-    const double* th = theta + ((size_t)p * nb + k) * 3;
-    const bool zero = DA(DA(DM(th[0], th[0]), DM(th[1], th[1])), DM(th[2], th[2])) == 0.0;
+    const bool zero = sZero[k];
     const int par = parent[k];
     double v;
     if (j == 3) {

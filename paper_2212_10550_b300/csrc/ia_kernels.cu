@@ -202,9 +202,13 @@ cudaError_t launch_pose_chain(int P, int nb, const int* parent, const double* re
 // Blended transform grid M(v) = sum_i W(v, i) N_i, one pose per blockIdx.y
 // ---------------------------------------------------------------------------
 
+// kVec: nb a multiple of 4, a voxel's weights read as float4 (W's rows are then
+// 16-byte aligned); the bones are summed in the same order either way.
+template <bool kVec>
 __global__ void blend_kernel(int V, int nb, const float* __restrict__ W, const float* __restrict__ N,
                              float4* __restrict__ M) {
-  __shared__ float sN[kMaxBones * 12];
+  __shared__ float4 sN4[kMaxBones * 3];
+  float* sN = reinterpret_cast<float*>(sN4);
   const int p = blockIdx.y;
   for (int t = threadIdx.x; t < nb * 12; t += blockDim.x) sN[t] = N[(size_t)p * nb * 12 + t];
   __syncthreads();
@@ -213,10 +217,27 @@ __global__ void blend_kernel(int V, int nb, const float* __restrict__ W, const f
 #pragma unroll
     for (int q = 0; q < 12; ++q) acc[q] = 0.f;
     const float* w = W + (size_t)v * nb;
-    for (int i = 0; i < nb; ++i) {
-      float wi = __ldg(w + i);
+    auto add_bone = [&](int i, float wi) {
 #pragma unroll
-      for (int q = 0; q < 12; ++q) acc[q] = fmaf(wi, sN[i * 12 + q], acc[q]);
+      for (int r = 0; r < 3; ++r) {
+        const float4 n = sN4[i * 3 + r];
+        acc[4 * r] = fmaf(wi, n.x, acc[4 * r]);
+        acc[4 * r + 1] = fmaf(wi, n.y, acc[4 * r + 1]);
+        acc[4 * r + 2] = fmaf(wi, n.z, acc[4 * r + 2]);
+        acc[4 * r + 3] = fmaf(wi, n.w, acc[4 * r + 3]);
+      }
+    };
+    if constexpr (kVec) {
+      const float4* w4 = reinterpret_cast<const float4*>(w);
+      for (int i4 = 0; i4 < nb / 4; ++i4) {
+        const float4 wq = __ldg(w4 + i4);
+        add_bone(4 * i4, wq.x);
+        add_bone(4 * i4 + 1, wq.y);
+        add_bone(4 * i4 + 2, wq.z);
+        add_bone(4 * i4 + 3, wq.w);
+      }
+    } else {
+      for (int i = 0; i < nb; ++i) add_bone(i, __ldg(w + i));
     }
     float4* out = M + ((size_t)p * V + v) * 3;
     out[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
@@ -230,7 +251,8 @@ cudaError_t launch_blend(int P, int V, int nb, const float* W, const float* N, f
   if (grid.x > 4096) grid.x = 4096;
   {
     KernelSpan span("blend_kernel", s);
-    blend_kernel<<<grid, 256, 0, s>>>(V, nb, W, N, M);
+    if (nb % 4 == 0 && reinterpret_cast<uintptr_t>(W) % 16 == 0) blend_kernel<true><<<grid, 256, 0, s>>>(V, nb, W, N, M);
+    else blend_kernel<false><<<grid, 256, 0, s>>>(V, nb, W, N, M);
   }
   return cudaGetLastError();
 }
